@@ -1,0 +1,359 @@
+"""Pins of the FP64 oracle to things other than itself (CPU only).
+
+Each test checks one oracle function against an independent statement of
+what the paper fixes: exact rational arithmetic, Python big integers, dict /
+Counter brute force on tiny inputs, the worked Example 2 (Sect. 3.2), the
+MinHash collision law (Eq. 2), and invariants of SILK (Alg. 4).
+"""
+import json
+import math
+import os
+import random
+from collections import Counter, defaultdict
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+M64 = 1 << 64
+
+
+def hbig(A, B, x):
+    return ((int(A) * int(x) + int(B)) % M64) >> 32
+
+
+# ----------------------------------------------------------------- E2LSH --
+def exact_codes(x, a, b, w):
+    n, d = x.shape
+    F = a.shape[0]
+    out = np.empty((n, F), dtype=np.int64)
+    gap = np.empty((n, F))
+    for i in range(n):
+        for f in range(F):
+            v = sum(Fraction(float(a[f, j])) * Fraction(float(x[i, j])) for j in range(d))
+            t = (v + Fraction(float(b[f]))) / Fraction(w)
+            fl = math.floor(t)
+            out[i, f] = fl
+            gap[i, f] = float(min(t - fl, fl + 1 - t))
+    return out, gap
+
+
+def test_e2lsh_matches_exact_rational_floor(orc):
+    rng = np.random.default_rng(1)
+    n, d, F = 40, 7, 5  # d != F so a transposed operand cannot pass
+    x = (rng.standard_normal((n, d)) * 20).astype(np.float32)
+    a = rng.standard_normal((F, d)).astype(np.float32)
+    b = (rng.random(F) * 4).astype(np.float32)
+    got = orc.e2lsh(x, a, b, 4.0)
+    want, gap = exact_codes(x, a, b, 4.0)
+    near = gap < 1e-9
+    assert near.sum() == 0  # random inputs: no exact-boundary ambiguity
+    assert np.array_equal(got, want)
+    # a non-power-of-two width exercises the rounded division
+    got3 = orc.e2lsh(x, a, b, 3.0)
+    want3, gap3 = exact_codes(x, a, b, 3.0)
+    assert np.array_equal(got3[gap3 > 1e-9], want3[gap3 > 1e-9])
+
+
+def test_e2lsh_handcrafted_boundaries(orc):
+    # a.x + b lands exactly on / just beside multiples of w, and negative
+    # values check floor (not truncation toward zero)
+    a = np.array([[0.5, 0.0], [1.0, -1.0]], dtype=np.float32)
+    b = np.array([0.0, 0.5], dtype=np.float32)
+    x = np.array([[8.0, 3.0], [-2.0, 0.0], [7.999999, 1.0], [-8.0, 4.0], [0.0, 0.5]], dtype=np.float32)
+    got = orc.e2lsh(x, a, b, 4.0)
+    want, _ = exact_codes(x, a, b, 4.0)
+    assert np.array_equal(got, want)
+    assert got[0, 0] == 1 and got[1, 0] == -1 and got[2, 0] == 0 and got[3, 0] == -1
+    # property: floor(t) <= t < floor(t) + 1 for every element
+    rng = np.random.default_rng(2)
+    xs = (rng.standard_normal((20, 3)) * 9).astype(np.float32)
+    aa = rng.standard_normal((4, 3)).astype(np.float32)
+    bb = (rng.random(4) * 4).astype(np.float32)
+    c = orc.e2lsh(xs, aa, bb, 4.0)
+    t = (xs.astype(np.float64) @ aa.T.astype(np.float64) + bb) / 4.0
+    assert np.all(c <= t + 1e-9) and np.all(t < c + 1 + 1e-9)
+
+
+def test_e2lsh_overflow_is_reported(orc):
+    x = np.array([[3e38]], dtype=np.float32)
+    a = np.array([[1.0]], dtype=np.float32)
+    with pytest.raises(RuntimeError):
+        orc.e2lsh(x, a, np.zeros(1, np.float32), 4.0)
+
+
+def test_srp_matches_exact_sign(orc):
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((30, 6)).astype(np.float32)
+    a = rng.standard_normal((9, 6)).astype(np.float32)
+    x[0] = 0.0  # a.x == 0 exactly counts as >= 0
+    got = orc.srp(x, a)
+    for i in range(30):
+        for f in range(9):
+            v = sum(Fraction(float(a[f, j])) * Fraction(float(x[i, j])) for j in range(6))
+            assert got[i, f] == (1 if v >= 0 else 0)
+
+
+# --------------------------------------------------------------- MinHash --
+def test_hash32_against_big_integers(orc):
+    rng = random.Random(4)
+    for _ in range(2000):
+        A, B, x = rng.getrandbits(64), rng.getrandbits(64), rng.getrandbits(32)
+        assert orc.hash32(A, B, x) == hbig(A, B, x)
+    assert orc.hash32(M64 - 1, M64 - 1, 0xFFFFFFFF) == hbig(M64 - 1, M64 - 1, 0xFFFFFFFF)
+
+
+def test_minhash_explicit_minima(orc):
+    rng = np.random.default_rng(5)
+    sets = [sorted(rng.choice(1 << 20, size=s, replace=False).tolist()) for s in [1, 2, 5, 33, 64, 100]]
+    off = np.zeros(len(sets) + 1, np.int64)
+    off[1:] = np.cumsum([len(s) for s in sets])
+    items = np.array([i for s in sets for i in s], np.uint32)
+    A = rng.integers(0, 2**63, 11, dtype=np.uint64) * np.uint64(2) + np.uint64(1)
+    B = rng.integers(0, 2**63, 11, dtype=np.uint64)
+    got = orc.minhash_csr(off, items, A, B)
+    for i, s in enumerate(sets):
+        for f in range(11):
+            assert got[i, f] == min(hbig(A[f], B[f], v) for v in s)
+    # the empty set (undefined in the paper) maps to 0xFFFFFFFF
+    e = orc.minhash_csr(np.array([0, 0], np.int64), np.zeros(0, np.uint32), A[:1], B[:1])
+    assert e[0, 0] == 0xFFFFFFFF
+
+
+def test_minhash_collision_rate_equals_jaccard(orc):
+    """Eq. 2: Pr[h(A) = h(B)] = J(A, B); 20,000 independent hashes, 4 sigma."""
+    rng = np.random.default_rng(6)
+    univ = rng.choice(1 << 20, size=150, replace=False)
+    A_set = np.sort(univ[:90])
+    B_set = np.sort(univ[45:135])  # |A n B| = 45, |A u B| = 135 -> J = 1/3
+    J = 45 / 135
+    T = 20000
+    ca = rng.integers(0, np.iinfo(np.uint64).max, T, dtype=np.uint64, endpoint=True)
+    cb = rng.integers(0, np.iinfo(np.uint64).max, T, dtype=np.uint64, endpoint=True)
+    off = np.array([0, 90, 180], np.int64)
+    mh = orc.minhash_csr(off, np.concatenate([A_set, B_set]).astype(np.uint32), ca, cb)
+    rate = np.mean(mh[0] == mh[1])
+    sigma = math.sqrt(J * (1 - J) / T)
+    assert abs(rate - J) < 4 * sigma, (rate, J)
+
+
+# -------------------------------------------------------------- grouping --
+def test_sort_rows_is_stable_lexicographic(orc):
+    rng = np.random.default_rng(7)
+    for n in [1, 17, 70000]:
+        keys = rng.integers(-3, 3, size=(n, 3)).astype(np.int64)
+        perm = np.empty(n, np.int32)
+        orc.lib().orc_sort_rows(n, 3, orc._p(keys), orc._p(perm))
+        want = np.lexsort((np.arange(n), keys[:, 2], keys[:, 1], keys[:, 0]))
+        assert np.array_equal(perm, want)
+
+
+def test_group_against_dict(orc):
+    rng = np.random.default_rng(8)
+    L, n, W = 3, 500, 4
+    keys = rng.integers(-2, 2, size=(L, n, W)).astype(np.int64)
+    bk = orc.group(keys)
+    for l in range(L):
+        groups = defaultdict(list)
+        for i in range(n):
+            groups[tuple(keys[l, i])].append(i)
+        ordered = sorted(groups)
+        assert bk.n_buckets[l] == len(ordered)
+        for r, kk in enumerate(ordered):
+            g = bk.table_base[l] + r
+            mem = bk.bmem[bk.boff[g]:bk.boff[g + 1]].tolist()
+            assert mem == groups[kk]  # ascending ids inside the bucket
+            for i in groups[kk]:
+                assert bk.obj_bucket[l, i] == r
+
+
+# ------------------------------------------------------------------ SILK --
+def test_example2_vote_forced_bins(orc):
+    """Sect. 3.2, Example 2: majority voting on the printed bins of T1."""
+    g = json.load(open(os.path.join(GOLD, "example2_silk.json")))
+    names = sorted(g["buckets"], key=lambda s: int(s[1:]))
+    buckets = [g["buckets"][nm] for nm in names]
+    idx = {nm: i for i, nm in enumerate(names)}
+    bins = [[idx[b] for b in g["bins_T1"][k]] for k in ["Bin1", "Bin2", "Bin3"]]
+    got = orc.vote_bins(bins, buckets, g["delta"])
+    assert got[0] == tuple(g["expected_C_shared_T1"]["Bin1"])
+    assert got[1] == tuple(g["expected_C_shared_T1"]["Bin2"])
+    assert got[2] == ()  # |Bin3| <= 1: ignored
+    # the strict "more than half" rule: an object in exactly half is dropped
+    assert orc.vote_bins([[0, 1]], [[1, 2], [2, 3]], 1) == [(2,)]
+    # delta filter
+    assert orc.vote_bins([[0, 1]], [[1, 2], [1, 2]], 3) == [()]
+
+
+def test_example2_dedup_forced_bins(orc):
+    """Sect. 3.2, Example 2: the multiset from both tables deduplicates to the
+    four printed seeds when the two copies of {x1,x2,x4} share a bin."""
+    g = json.load(open(os.path.join(GOLD, "example2_silk.json")))
+    ms = [tuple(s) for s in g["multiset_after_both_tables"]]
+    bins = [[0, 2], [1], [3], [4]]
+    got = orc.dedup_bins(ms, bins, g["delta"])
+    assert sorted(got) == sorted(tuple(s) for s in g["expected_final_seeds"])
+    assert got == sorted(got)  # canonical order
+    # a bin of several sets whose vote is below delta keeps its smallest member
+    assert orc.dedup_bins([(1, 2), (3, 4)], [[0, 1]], 1) == [(1, 2)]
+
+
+def silk_brute(buckets, Ks, Ls, delta, A, B, dA, dB):
+    """Alg. 4 restated with dicts and Counters on tiny inputs."""
+    def sig(s, a, b):
+        return tuple(min(hbig(a[k], b[k], i) for i in s) for k in range(len(a)))
+    C = []
+    for t in range(Ls):
+        a, b = A[t * Ks:(t + 1) * Ks], B[t * Ks:(t + 1) * Ks]
+        bins = defaultdict(list)
+        for bk in buckets:
+            bins[sig(bk, a, b)].append(bk)
+        for mem in bins.values():
+            if len(mem) <= 1:
+                continue
+            cnt = Counter(i for bk in mem for i in bk)
+            cs = tuple(sorted(i for i, c in cnt.items() if 2 * c > len(mem)))
+            if len(cs) >= delta:
+                C.append(cs)
+    bins = defaultdict(list)
+    for s in C:
+        bins[sig(s, dA, dB)].append(s)
+    D = []
+    for mem in bins.values():
+        if len(mem) == 1:
+            D.append(mem[0])
+            continue
+        cnt = Counter(i for s in mem for i in s)
+        vs = tuple(sorted(i for i, c in cnt.items() if 2 * c > len(mem)))
+        D.append(vs if len(vs) >= delta else min(mem))
+    return sorted(set(D)), len(C)
+
+
+def small_hash_coeffs(rng, m, modulus_bits=3):
+    # coefficients chosen so that collisions (and hence non-trivial bins)
+    # are frequent on tiny inputs: A*x+B with tiny A keeps the high word small
+    A = rng.integers(0, 1 << modulus_bits, m, dtype=np.uint64) << np.uint64(29)
+    B = rng.integers(0, 1 << 40, m, dtype=np.uint64)
+    return A, B
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_silk_against_brute_force(orc, seed):
+    rng = np.random.default_rng(100 + seed)
+    n = 30
+    buckets = []
+    for _ in range(40):
+        s = int(rng.integers(1, 7))
+        buckets.append(tuple(sorted(rng.choice(n, size=s, replace=False).tolist())))
+    Ks, Ls, delta = int(rng.integers(1, 3)), int(rng.integers(1, 5)), int(rng.integers(1, 3))
+    A, B = small_hash_coeffs(rng, Ks * Ls)
+    dA, dB = small_hash_coeffs(rng, Ks)
+    boff = np.zeros(len(buckets) + 1, np.int64)
+    boff[1:] = np.cumsum([len(b) for b in buckets])
+    bmem = np.array([i for b in buckets for i in b], np.int32)
+    got = orc.silk(boff, bmem, Ks, Ls, delta, A, B, dA, dB)
+    want, nC = silk_brute(buckets, Ks, Ls, delta, A, B, dA, dB)
+    assert got.sets() == want
+    assert got.n_multiset == nC
+    # bucket order must not matter (bins are sets of buckets)
+    perm = rng.permutation(len(buckets))
+    pb = [buckets[i] for i in perm]
+    boff2 = np.zeros(len(pb) + 1, np.int64)
+    boff2[1:] = np.cumsum([len(b) for b in pb])
+    bmem2 = np.array([i for b in pb for i in b], np.int32)
+    assert orc.silk(boff2, bmem2, Ks, Ls, delta, A, B, dA, dB).sets() == want
+
+
+def test_silk_more_tables_more_candidates(orc):
+    """Example 3: more SILK tables can only add C_shared sets to the multiset
+    (the first tables' hashes are shared)."""
+    import synth
+    wl = synth.make(synth.config("c1", n=4000))
+    codes, bk = orc.hash_dense(wl["x"], wl["a"], wl["b"], wl["w"], 4, 8)
+    sp = wl["silk"]
+    prev = -1
+    for Ls in [1, 5, 10, 20]:
+        s = orc.silk(bk.boff, bk.bmem, sp["Ks"], Ls, sp["delta"], sp["mh_a"][: Ls * sp["Ks"]],
+                     sp["mh_b"][: Ls * sp["Ks"]], sp["dd_a"], sp["dd_b"])
+        assert s.n_multiset >= prev
+        prev = s.n_multiset
+        for j in range(s.k):  # canonical: ascending members, distinct seeds
+            m = s.ids[s.off[j]:s.off[j + 1]]
+            assert m.size >= 1 and np.all(np.diff(m) > 0)
+        assert s.sets() == sorted(set(s.sets()))
+
+
+# ------------------------------------------------------------ assignment --
+def test_centroids_exact_mean_within_one_ulp(orc):
+    rng = np.random.default_rng(9)
+    x = (rng.standard_normal((60, 5)) * 13).astype(np.float32)
+    sets = [sorted(rng.choice(60, size=s, replace=False).tolist()) for s in [1, 2, 3, 7, 31, 60]]
+    seeds = orc.Seeds(np.concatenate([[0], np.cumsum([len(s) for s in sets])]).astype(np.int64),
+                      np.array([i for s in sets for i in s], np.int32), len(sets))
+    c = orc.centroids(x, seeds)
+    for j, s in enumerate(sets):
+        for t in range(5):
+            exact = sum(Fraction(float(x[i, t])) for i in s) / len(s)
+            assert abs(Fraction(c[j, t]) - exact) <= Fraction(np.spacing(abs(c[j, t])))
+
+
+def test_assign_dense_exhaustive_exact(orc):
+    rng = np.random.default_rng(10)
+    x = (rng.standard_normal((120, 4)) * 5).astype(np.float32)
+    c = rng.standard_normal((9, 4)) * 5
+    c[7] = c[2]  # exact tie: the smaller index must win
+    lab, dist = orc.assign_dense(x, c)
+    for i in range(120):
+        D = [sum((Fraction(float(x[i, t])) - Fraction(c[j, t])) ** 2 for t in range(4)) for j in range(9)]
+        m = min(D)
+        assert lab[i] == D.index(m)
+        assert abs(dist[i] - float(m)) <= 1e-12 * float(m) + 1e-300
+    assert not np.any(lab == 7)
+    lab0, _ = orc.assign_dense(x, np.zeros((0, 4)))
+    assert np.all(lab0 == -1)
+
+
+def test_modes_and_categorical_assignment(orc):
+    rng = np.random.default_rng(11)
+    n, A = 80, 6
+    attrs = rng.integers(0, 4, size=(n, A)).astype(np.int64)
+    sets = [sorted(rng.choice(n, size=s, replace=False).tolist()) for s in [1, 2, 4, 9, 20]]
+    seeds = orc.Seeds(np.concatenate([[0], np.cumsum([len(s) for s in sets])]).astype(np.int64),
+                      np.array([i for s in sets for i in s], np.int32), len(sets))
+    m = orc.modes(attrs, seeds)
+    for j, s in enumerate(sets):
+        for a in range(A):
+            cnt = Counter(int(attrs[i, a]) for i in s)
+            top = max(cnt.values())
+            assert m[j, a] == min(v for v, c in cnt.items() if c == top)
+    lab, mt = orc.assign_cat(attrs, m)
+    for i in range(n):
+        scores = [int(np.sum(attrs[i] == m[j])) for j in range(len(sets))]
+        assert mt[i] == max(scores) and lab[i] == scores.index(max(scores))
+
+
+def test_sparse_centres_and_jaccard(orc):
+    rng = np.random.default_rng(12)
+    n = 50
+    sets = [sorted(rng.choice(40, size=int(rng.integers(1, 12)), replace=False).tolist()) for _ in range(n)]
+    off = np.zeros(n + 1, np.int64)
+    off[1:] = np.cumsum([len(s) for s in sets])
+    items = np.array([i for s in sets for i in s], np.uint32)
+    seed_sets = [sorted(rng.choice(n, size=s, replace=False).tolist()) for s in [1, 3, 4, 8]]
+    seeds = orc.Seeds(np.concatenate([[0], np.cumsum([len(s) for s in seed_sets])]).astype(np.int64),
+                      np.array([i for s in seed_sets for i in s], np.int32), len(seed_sets))
+    coff, cit = orc.sparse_centres(off, items, seeds)
+    cents = []
+    for j, ss in enumerate(seed_sets):
+        cnt = Counter(v for i in ss for v in sets[i])
+        want = sorted(v for v, c in cnt.items() if 2 * c > len(ss))
+        assert cit[coff[j]:coff[j + 1]].tolist() == want
+        cents.append(set(want))
+    cents.append(set())  # an empty centre: similarity 0
+    coff2 = np.concatenate([coff, [coff[-1]]])
+    lab, inter, uni = orc.assign_jaccard(off, items, coff2, cit)
+    for i, s in enumerate(sets):
+        J = [Fraction(len(set(s) & c), len(set(s) | c)) if (s or c) else Fraction(0) for c in cents]
+        assert lab[i] == J.index(max(J))
+        assert Fraction(int(inter[i]), int(uni[i])) == max(J)
