@@ -1,0 +1,231 @@
+/*
+ * geek.h - C ABI of the GB300 GEEK library: bucketing (data transformation),
+ * SILK seeding and one-pass assignment, after Luo, Huang and Tung, "A Generic
+ * Distributed Clustering Framework for Massive Data" (Sect. 3).
+ *
+ * Conventions
+ *  - Every array argument is DEVICE memory owned by the caller unless the
+ *    comment says otherwise; the library never frees caller memory.
+ *  - Work is enqueued on the caller's CUDA stream (geek_stream is a
+ *    cudaStream_t; NULL selects the legacy default stream).  Calls whose
+ *    output size depends on the data (geek_hash, silk_seed) read a few counts
+ *    back to the host and therefore return only after those counts are known;
+ *    the bulk outputs they own stay stream-ordered.
+ *  - Outputs whose size depends on the data live in opaque library-owned
+ *    handles (geek_buckets, silk_seeds): *_info gives sizes, *_copy_out
+ *    copies into caller buffers, *_free releases the handle.
+ *  - Random parameters of the method (E2LSH projections, MinHash and SILK
+ *    hash coefficients) are inputs; the library draws nothing.  No call takes
+ *    a number of clusters k: SILK decides it (Sect. 3.2).
+ *  - Every call returns a geek_status.  Nothing aborts or throws across the
+ *    ABI; geek_last_error() describes the last failure on a context.
+ *  - Results are deterministic and bit-exact against an FP64 reference
+ *    definition (see each call): fast single-precision or tensor-core paths
+ *    recompute in FP64 every element whose rounding-error window could change
+ *    an integer outcome (a bucket code, a sign, an argmin).
+ */
+#ifndef GEEK_H
+#define GEEK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum geek_status {
+    GEEK_OK = 0,
+    GEEK_ERR_INVALID = 1,     /* bad argument, shape or pointer */
+    GEEK_ERR_NOMEM = 2,       /* device or host allocation failed */
+    GEEK_ERR_CUDA = 3,        /* a CUDA runtime call or kernel failed */
+    GEEK_ERR_TIMEOUT = 4,     /* a bounded device wait expired */
+    GEEK_ERR_OVERFLOW = 5,    /* a code or key does not fit its field */
+    GEEK_ERR_UNSUPPORTED = 6  /* valid request this build does not implement */
+} geek_status;
+
+typedef struct geek_ctx geek_ctx;
+typedef struct geek_buckets geek_buckets;
+typedef struct silk_seeds silk_seeds;
+typedef void *geek_stream; /* cudaStream_t */
+
+/* data kinds (Sect. 2.1 problem settings) */
+enum { GEEK_DENSE = 0, GEEK_SETS = 1, GEEK_HETERO = 2 };
+/* where the data arrays of a geek_data live */
+enum { GEEK_MEM_DEVICE = 0, GEEK_MEM_HOST = 1 };
+/* dense projection family */
+enum { GEEK_PROJ_E2LSH = 0, GEEK_PROJ_SRP = 1 };
+/* arithmetic of the fast path (FP64 rechecks keep every result exact) */
+enum { GEEK_PREC_FP32 = 0, GEEK_PREC_BF16 = 1 };
+
+/* One data set.
+ *  DENSE : x is n x d float32, row-major with row stride ldx (elements).
+ *  SETS  : set_off (n+1 int64, ascending, set_off[0] = 0) and set_items
+ *          (uint32 item ids, distinct within a set) in CSR form.
+ *  HETERO: x as DENSE for the numeric attributes plus cat, n x n_cat uint32
+ *          tokens, row-major; token = offset of the attribute + value, so
+ *          that different attributes never share a token (Alg. 2).
+ * mem = GEEK_MEM_HOST marks x / set_off / set_items / cat as host memory
+ * (pinned for speed): the library stages them to the device itself. */
+typedef struct geek_data {
+    int32_t kind;
+    int32_t mem;
+    int64_t n;
+    int32_t d;
+    int32_t n_cat;
+    int64_t ldx;
+    const float *x;
+    const int64_t *set_off;
+    const uint32_t *set_items;
+    const uint32_t *cat;
+} geek_data;
+
+/* Hash parameters (Sect. 2.2 static (K,L) framework; Sect. 3.1, Algs. 2-3).
+ *  Dense / hetero numeric part: F = K*L projections a (F x d float32,
+ *    function f = l*K + k) and offsets b (F float32); E2LSH code =
+ *    floor((a.x + b) / w) (the function named in Sect. 3.1 Remarks), or for
+ *    proj = SRP the sign bit [a.x >= 0] (b and w unused).
+ *  Sets: K*L MinHash functions (Eq. 2), coefficient pairs mh_a/mh_b (uint64),
+ *    h(v) = ((mh_a*v + mh_b) mod 2^64) >> 32.
+ *  Hetero: additionally Kc MinHash functions per table (Kc*L coefficient
+ *    pairs) over each row's token set, appended to the table key.
+ * Table l's key is the tuple of its K (+ Kc) values, compared
+ * lexicographically (codes signed, MinHash values unsigned). */
+typedef struct geek_hash_params {
+    int32_t proj;
+    int32_t precision;
+    int32_t K, L, Kc;
+    double w;
+    const float *a;
+    const float *b;
+    const uint64_t *mh_a;
+    const uint64_t *mh_b;
+} geek_hash_params;
+
+typedef struct geek_buckets_info {
+    int64_t n;               /* objects */
+    int32_t L;               /* tables */
+    int32_t key_bits_max;    /* widest packed table key, bits */
+    int64_t n_buckets;       /* buckets over all tables */
+    int64_t n_flagged;       /* fast-path elements recomputed in FP64 */
+} geek_buckets_info;
+
+/* SILK parameters (Alg. 4): Ls tables of Ks MinHash functions over object
+ * ids (mh_a/mh_b, Ls*Ks pairs, function t*Ks + k), seeding threshold delta
+ * (>= 1) and Ks functions dd_a/dd_b for the near-duplicate removal pass.
+ * Device arrays.  1 <= Ks <= 4. */
+typedef struct silk_params {
+    int32_t Ks, Ls, delta;
+    const uint64_t *mh_a, *mh_b;
+    const uint64_t *dd_a, *dd_b;
+} silk_params;
+
+typedef struct geek_assign_params {
+    int32_t precision; /* GEEK_PREC_FP32 (SIMT) or GEEK_PREC_BF16 (tcgen05) */
+} geek_assign_params;
+
+typedef struct geek_assign_stats {
+    double sse;              /* sum over objects of the distance to its centre */
+    double radius_max;       /* max over objects of that distance (Sect. 4.1) */
+    int64_t k;               /* number of centres used */
+    int64_t n_recheck_rows;  /* objects whose argmin was decided in FP64 */
+} geek_assign_stats;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Creates a context on CUDA device `device` (made current).  One context per
+ * thread at a time; contexts are independent. */
+geek_status geek_ctx_create(int device, geek_ctx **out);
+geek_status geek_ctx_destroy(geek_ctx *ctx);
+/* Message for the last failing call on ctx (never NULL; owned by ctx). */
+const char *geek_last_error(const geek_ctx *ctx);
+/* Library version string (static storage). */
+const char *geek_version(void);
+
+/* ---- data transformation (Sect. 3.1) ------------------------------------ */
+
+/* geek_hash: converts every object into one bucket per table.
+ * Dense: E2LSH codes floor((a.x+b)/w) (or SRP bits) of K functions per table
+ * over L tables.  Sets: MinHash (Eq. 2) K per table.  Hetero: E2LSH of the
+ * numeric part followed by Kc MinHash values of the tokens (Alg. 2).
+ * Exact definition of a code: s = sum_j (double)a_j*(double)x_j accumulated
+ * in j order in FP64, code = floor((s + (double)b) / w) with IEEE
+ * round-to-nearest; elements whose FP32 value lies within its rigorous
+ * error bound of a code boundary are recomputed that way on the GPU.
+ * Buckets of a table are the classes of equal keys; the canonical bucket id
+ * of an object in table l is the rank of its key among table l's distinct
+ * keys in ascending lexicographic order.  On success *out owns the result.
+ * Errors: INVALID (shapes, K*L > 4096, Kc without HETERO), OVERFLOW (a code
+ * outside int32 or a table key wider than 128 bits), NOMEM, CUDA. */
+geek_status geek_hash(geek_ctx *ctx, const geek_data *data, const geek_hash_params *p,
+                      geek_buckets **out, geek_stream stream);
+
+geek_status geek_buckets_info_get(const geek_buckets *b, geek_buckets_info *info);
+
+/* Copies results into caller device buffers (each pointer may be NULL):
+ *  obj_bucket  L x n int32: canonical bucket id of object i in table l
+ *  n_buckets   L int64 (HOST): buckets per table
+ *  bucket_off  n_buckets_total + 1 int64: bucket g (tables concatenated in
+ *              order, ranks ascending) holds members[bucket_off[g] ..
+ *              bucket_off[g+1])
+ *  members     L*n int32: object ids grouped by bucket, ascending inside
+ *  codes       n x (K*L) int32: per-function codes (dense / hetero; for SETS
+ *              the MinHash values as uint32 bit patterns) */
+geek_status geek_buckets_copy_out(const geek_buckets *b, int32_t *obj_bucket, int64_t *n_buckets,
+                                  int64_t *bucket_off, int32_t *members, int32_t *codes,
+                                  geek_stream stream);
+geek_status geek_buckets_free(geek_buckets *b);
+
+/* ---- initial seeding, SILK (Sect. 3.2, Alg. 4) -------------------------- */
+
+/* silk_seed: groups similar buckets into bins with Ls tables of Ks MinHash
+ * functions over object ids; bins holding at most one bucket are skipped;
+ * each other bin yields C_shared = the objects present in more than half of
+ * its buckets (2*count > |bin|), kept when |C_shared| >= delta.  The
+ * multiset of kept sets is then deduplicated with one more table of Ks
+ * functions: a bin holding one set keeps it; a bin of several sets yields
+ * their majority-vote set if it has >= delta objects, else its member that
+ * is smallest in canonical order.  Exact duplicates are dropped and the
+ * seeds sorted in canonical order (lexicographic on ascending member
+ * lists); seed j is the j-th in that order.  k is an output, never input. */
+geek_status silk_seed(geek_ctx *ctx, const geek_buckets *b, const silk_params *p,
+                      silk_seeds **out, geek_stream stream);
+/* k = number of seeds, n_ids = total members, n_multiset = kept C_shared
+ * sets before near-duplicate removal (all HOST outputs). */
+geek_status silk_seeds_info(const silk_seeds *s, int64_t *k, int64_t *n_ids, int64_t *n_multiset);
+/* off: k+1 int64, ids: n_ids int32 (device buffers). */
+geek_status silk_seeds_copy_out(const silk_seeds *s, int64_t *off, int32_t *ids, geek_stream stream);
+geek_status silk_seeds_free(silk_seeds *s);
+
+/* ---- data assignment (Sect. 3.3, Eq. 1) --------------------------------- */
+
+/* geek_assign: builds the central vector of every seed and assigns every
+ * object to its closest one, once.
+ *  DENSE: centroid = (sum over members in ascending id of (double)x) /
+ *    count; distance = sum_j ((double)x_j - c_j)^2 accumulated in j order in
+ *    FP64 without fused multiply-add; label = argmin, ties to the smallest
+ *    seed index.  The fast path (FP32 SIMT or BF16 tcgen05) keeps the best
+ *    and second-best approximate distance per object; objects whose gap is
+ *    within the rigorous error window are decided in FP64.
+ *  HETERO: unified categorical attributes (per table, the bucket of the
+ *    numeric E2LSH part; then the tokens); central vector = per-attribute
+ *    mode (most frequent value, ties to the smallest); distance 1 - Jaccard,
+ *    i.e. the label maximises the number of matching attributes.
+ *  SETS: central vector = items present in more than half of the members;
+ *    label maximises |A n C| / |A u C| (exact rational comparison).
+ * labels: n int32.  centers (nullable, DENSE only): k x d float64 out.
+ * stats (nullable, HOST): filled after the stream has finished the call. */
+geek_status geek_assign(geek_ctx *ctx, const geek_data *data, const geek_buckets *b,
+                        const silk_seeds *s, const geek_assign_params *p, int32_t *labels,
+                        double *centers, geek_assign_stats *stats, geek_stream stream);
+
+/* geek_assign_centers: the dense assignment of geek_assign against k given
+ * central vectors (k x d float64, device), with the same exact argmin
+ * definition.  Useful when the centres come from elsewhere. */
+geek_status geek_assign_centers(geek_ctx *ctx, const geek_data *data, const double *centers,
+                                int64_t k, const geek_assign_params *p, int32_t *labels,
+                                geek_assign_stats *stats, geek_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GEEK_H */

@@ -1,0 +1,395 @@
+// C ABI: argument checking, staging and orchestration of the kernels in
+// hash.cu / sort.cu / silk.cu / assign.cu.  Every entry point returns a
+// geek_status and never lets an exception cross the ABI.
+#include <new>
+
+#include "internal.cuh"
+
+namespace {
+
+cudaStream_t S(geek_stream s) { return (cudaStream_t)s; }
+
+// Copies a host array to device scratch when the data set lives on the host.
+template <class T>
+geek_status stage(geek_ctx *ctx, Scratch &scr, const T *src, size_t count, bool host, const T **dst,
+                  cudaStream_t st) {
+    if (!host || src == nullptr) {
+        *dst = src;
+        return GEEK_OK;
+    }
+    T *d;
+    GK_TRY(scr.alloc(&d, count));
+    GK_CUDA(ctx, cudaMemcpyAsync(d, src, count * sizeof(T), cudaMemcpyHostToDevice, st));
+    *dst = d;
+    return GEEK_OK;
+}
+
+geek_status own_alloc(geek_ctx *ctx, void **p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ctx, GEEK_ERR_NOMEM, "device allocation of %zu bytes failed", bytes);
+    }
+    return GEEK_OK;
+}
+
+void free_buckets(geek_buckets *b) {
+    if (!b) return;
+    cudaFree(b->obj_bucket);
+    cudaFree(b->boff);
+    cudaFree(b->members);
+    cudaFree(b->codes);
+    cudaFree(b->num_key);
+    delete b;
+}
+
+geek_status check_data(geek_ctx *ctx, const geek_data *d) {
+    if (!d) return set_error(ctx, GEEK_ERR_INVALID, "data is NULL");
+    if (d->n < 0 || d->n > 0x7FFFFFFFLL) return set_error(ctx, GEEK_ERR_INVALID, "n out of range");
+    if (d->mem != GEEK_MEM_DEVICE && d->mem != GEEK_MEM_HOST)
+        return set_error(ctx, GEEK_ERR_INVALID, "bad mem");
+    if (d->kind == GEEK_DENSE || d->kind == GEEK_HETERO) {
+        if (d->d <= 0 || d->ldx < d->d || (d->n > 0 && !d->x))
+            return set_error(ctx, GEEK_ERR_INVALID, "dense data needs x, d > 0 and ldx >= d");
+    }
+    if (d->kind == GEEK_HETERO && (d->n_cat <= 0 || (d->n > 0 && !d->cat)))
+        return set_error(ctx, GEEK_ERR_INVALID, "hetero data needs cat tokens");
+    if (d->kind == GEEK_SETS && (!d->set_off || (d->n > 0 && !d->set_items)))
+        return set_error(ctx, GEEK_ERR_INVALID, "set data needs set_off and set_items");
+    if (d->kind < 0 || d->kind > 2) return set_error(ctx, GEEK_ERR_INVALID, "bad kind");
+    return GEEK_OK;
+}
+
+geek_status hash_impl(geek_ctx *ctx, const geek_data *data, const geek_hash_params *p,
+                      geek_buckets **out, cudaStream_t st) {
+    GK_TRY(check_data(ctx, data));
+    if (!p || !out) return set_error(ctx, GEEK_ERR_INVALID, "params/out is NULL");
+    *out = nullptr;
+    const int kind = data->kind;
+    const int64_t n = data->n;
+    const int K = p->K, L = p->L;
+    if (K <= 0 || L <= 0 || (int64_t)K * L > 4096) return set_error(ctx, GEEK_ERR_INVALID, "bad K/L");
+    if (kind == GEEK_HETERO && p->Kc <= 0) return set_error(ctx, GEEK_ERR_INVALID, "hetero needs Kc > 0");
+    if (kind != GEEK_HETERO && p->Kc != 0) return set_error(ctx, GEEK_ERR_INVALID, "Kc is for hetero data only");
+    if (kind != GEEK_SETS) {
+        if (!p->a || (p->proj == GEEK_PROJ_E2LSH && (!p->b || !(p->w > 0.0))))
+            return set_error(ctx, GEEK_ERR_INVALID, "projection parameters missing");
+        if (p->proj != GEEK_PROJ_E2LSH && p->proj != GEEK_PROJ_SRP)
+            return set_error(ctx, GEEK_ERR_INVALID, "bad proj");
+    }
+    if ((kind == GEEK_SETS || kind == GEEK_HETERO) && (!p->mh_a || !p->mh_b))
+        return set_error(ctx, GEEK_ERR_INVALID, "MinHash coefficients missing");
+    if (p->precision != GEEK_PREC_FP32)
+        return set_error(ctx, GEEK_ERR_UNSUPPORTED, "projection precision other than FP32");
+    const bool host = data->mem == GEEK_MEM_HOST;
+
+    Scratch scr(ctx, st);
+    geek_buckets *b = new (std::nothrow) geek_buckets();
+    if (!b) return set_error(ctx, GEEK_ERR_NOMEM, "host allocation");
+    struct Guard {
+        geek_buckets *b;
+        ~Guard() { free_buckets(b); }
+    } guard{b};
+    b->ctx = ctx;
+    b->kind = kind;
+    b->n = n;
+    b->L = L;
+    b->K = K;
+    b->Kc = p->Kc;
+
+    const int F1 = kind == GEEK_SETS ? 0 : K * L;  // projection functions
+    const int K1 = kind == GEEK_SETS ? 0 : K;
+    const int K2 = kind == GEEK_SETS ? K : (kind == GEEK_HETERO ? p->Kc : 0);
+    const int F2 = K2 * L;                         // MinHash functions
+    b->F = kind == GEEK_SETS ? F2 : F1;
+
+    int *fmin = nullptr, *fmax = nullptr, *bits = nullptr;
+    const int Fm = std::max(1, F1);
+    GK_TRY(scr.alloc(&fmin, Fm));
+    GK_TRY(scr.alloc(&fmax, Fm));
+    GK_TRY(scr.alloc(&bits, Fm));
+    GK_TRY(own_alloc(ctx, (void **)&b->codes, sizeof(int32_t) * (size_t)n * std::max(1, b->F)));
+
+    uint32_t *mh = nullptr;
+    if (F1) {
+        const float *x;
+        GK_TRY(stage(ctx, scr, data->x, (size_t)n * data->ldx, host, &x, st));
+        GK_TRY(project_dense(ctx, scr, x, data->ldx, n, data->d, p->a, p->b, F1, p->w,
+                             p->proj == GEEK_PROJ_SRP, b->codes, fmin, fmax, &b->n_flagged, st));
+    }
+    if (kind == GEEK_SETS) {
+        const int64_t *off;
+        int64_t n_items = 0;
+        if (host) {
+            n_items = data->set_off[n];
+        } else {
+            GK_CUDA(ctx, cudaMemcpyAsync(&n_items, data->set_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+            GK_CUDA(ctx, cudaStreamSynchronize(st));
+        }
+        GK_TRY(stage(ctx, scr, data->set_off, (size_t)n + 1, host, &off, st));
+        const uint32_t *items;
+        GK_TRY(stage(ctx, scr, data->set_items, (size_t)n_items, host, &items, st));
+        mh = (uint32_t *)b->codes;
+        GK_TRY(minhash_rows(ctx, n, off, 0, items, F2, p->mh_a, p->mh_b, mh, st));
+    } else if (kind == GEEK_HETERO) {
+        const uint32_t *tok;
+        GK_TRY(stage(ctx, scr, data->cat, (size_t)n * data->n_cat, host, &tok, st));
+        GK_TRY(scr.alloc(&mh, (size_t)n * F2));
+        GK_TRY(minhash_rows(ctx, n, nullptr, data->n_cat, tok, F2, p->mh_a, p->mh_b, mh, st));
+    }
+    std::vector<int> tbits;
+    GK_TRY(key_layout(ctx, scr, fmin, fmax, L, K1, K2, bits, tbits, st));
+    int nbits = 1;
+    for (int v : tbits) nbits = std::max(nbits, v);
+    b->key_bits_max = nbits;
+
+    uint64_t *klo, *khi = nullptr;
+    GK_TRY(scr.alloc(&klo, (size_t)n * L));
+    if (nbits > 64) GK_TRY(scr.alloc(&khi, (size_t)n * L));
+    GK_TRY(pack_keys(ctx, n, L, b->codes, F1, K1, fmin, bits, mh, F2, K2, klo, khi, st));
+
+    if (kind == GEEK_HETERO) {
+        // numeric-only key per table: the unified categorical attribute of
+        // the numeric part (Sect. 3.3)
+        std::vector<int> nbt;
+        int nbn = 0;
+        for (int l = 0; l < L; l++) nbn = std::max(nbn, tbits[l] - 32 * K2);
+        if (nbn > 64) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "numeric key wider than 64 bits");
+        GK_TRY(own_alloc(ctx, (void **)&b->num_key, sizeof(uint64_t) * (size_t)n * L));
+        GK_TRY(pack_keys(ctx, n, L, b->codes, F1, K1, fmin, bits, nullptr, 0, 0, b->num_key, nullptr, st));
+    }
+
+    GK_TRY(own_alloc(ctx, (void **)&b->members, sizeof(uint32_t) * (size_t)n * L));
+    GK_TRY(own_alloc(ctx, (void **)&b->obj_bucket, sizeof(int32_t) * (size_t)n * L));
+    int64_t *boff = nullptr;
+    GK_TRY(group_tables(ctx, scr, n, L, klo, khi, nbits, b->members, b->obj_bucket, &boff, b->nb, &b->NB, st));
+    b->boff = boff;
+    GK_CUDA(ctx, cudaStreamSynchronize(st));
+    guard.b = nullptr;
+    *out = b;
+    return GEEK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *geek_version(void) { return GEEK_VERSION_STRING; }
+
+geek_status geek_ctx_create(int device, geek_ctx **out) {
+    if (!out) return GEEK_ERR_INVALID;
+    *out = nullptr;
+    geek_ctx *c = new (std::nothrow) geek_ctx();
+    if (!c) return GEEK_ERR_NOMEM;
+    c->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return GEEK_ERR_CUDA;
+    }
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device);
+    if (major * 10 + minor != 103) {
+        delete c;
+        return GEEK_ERR_UNSUPPORTED;  // built for sm_103a only
+    }
+    // keep freed stream-ordered memory cached in the device pool
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    *out = c;
+    return GEEK_OK;
+}
+
+geek_status geek_ctx_destroy(geek_ctx *ctx) {
+    delete ctx;
+    return GEEK_OK;
+}
+
+const char *geek_last_error(const geek_ctx *ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
+
+geek_status geek_hash(geek_ctx *ctx, const geek_data *data, const geek_hash_params *p,
+                      geek_buckets **out, geek_stream stream) {
+    if (!ctx) return GEEK_ERR_INVALID;
+    try {
+        return hash_impl(ctx, data, p, out, S(stream));
+    } catch (...) {
+        return set_error(ctx, GEEK_ERR_NOMEM, "host exception in geek_hash");
+    }
+}
+
+geek_status geek_buckets_info_get(const geek_buckets *b, geek_buckets_info *info) {
+    if (!b || !info) return GEEK_ERR_INVALID;
+    info->n = b->n;
+    info->L = b->L;
+    info->key_bits_max = b->key_bits_max;
+    info->n_buckets = b->NB;
+    info->n_flagged = b->n_flagged;
+    return GEEK_OK;
+}
+
+geek_status geek_buckets_copy_out(const geek_buckets *b, int32_t *obj_bucket, int64_t *n_buckets,
+                                  int64_t *bucket_off, int32_t *members, int32_t *codes,
+                                  geek_stream stream) {
+    if (!b) return GEEK_ERR_INVALID;
+    geek_ctx *ctx = b->ctx;
+    cudaStream_t st = S(stream);
+    const size_t nl = (size_t)b->n * b->L;
+    if (obj_bucket)
+        GK_CUDA(ctx, cudaMemcpyAsync(obj_bucket, b->obj_bucket, nl * 4, cudaMemcpyDeviceToDevice, st));
+    if (n_buckets)
+        for (int l = 0; l < b->L; l++) n_buckets[l] = b->nb[l];
+    if (bucket_off)
+        GK_CUDA(ctx, cudaMemcpyAsync(bucket_off, b->boff, (b->NB + 1) * 8, cudaMemcpyDeviceToDevice, st));
+    if (members) GK_CUDA(ctx, cudaMemcpyAsync(members, b->members, nl * 4, cudaMemcpyDeviceToDevice, st));
+    if (codes)
+        GK_CUDA(ctx, cudaMemcpyAsync(codes, b->codes, (size_t)b->n * b->F * 4, cudaMemcpyDeviceToDevice, st));
+    return GEEK_OK;
+}
+
+geek_status geek_buckets_free(geek_buckets *b) {
+    free_buckets(b);
+    return GEEK_OK;
+}
+
+geek_status silk_seed(geek_ctx *ctx, const geek_buckets *b, const silk_params *p, silk_seeds **out,
+                      geek_stream stream) {
+    if (!ctx) return GEEK_ERR_INVALID;
+    if (!b || !p || !out) return set_error(ctx, GEEK_ERR_INVALID, "NULL argument");
+    *out = nullptr;
+    if (p->Ks < 1 || p->Ks > 4 || p->Ls < 1 || p->delta < 1 || !p->mh_a || !p->mh_b || !p->dd_a || !p->dd_b)
+        return set_error(ctx, GEEK_ERR_INVALID, "bad SILK parameters");
+    silk_seeds *s = new (std::nothrow) silk_seeds();
+    if (!s) return set_error(ctx, GEEK_ERR_NOMEM, "host allocation");
+    s->ctx = ctx;
+    geek_status st;
+    try {
+        st = silk_run(ctx, b, p, s, S(stream));
+    } catch (...) {
+        st = set_error(ctx, GEEK_ERR_NOMEM, "host exception in silk_seed");
+    }
+    if (st != GEEK_OK) {
+        silk_seeds_free(s);
+        return st;
+    }
+    *out = s;
+    return GEEK_OK;
+}
+
+geek_status silk_seeds_info(const silk_seeds *s, int64_t *k, int64_t *n_ids, int64_t *n_multiset) {
+    if (!s) return GEEK_ERR_INVALID;
+    if (k) *k = s->k;
+    if (n_ids) *n_ids = s->n_ids;
+    if (n_multiset) *n_multiset = s->n_multiset;
+    return GEEK_OK;
+}
+
+geek_status silk_seeds_copy_out(const silk_seeds *s, int64_t *off, int32_t *ids, geek_stream stream) {
+    if (!s) return GEEK_ERR_INVALID;
+    geek_ctx *ctx = s->ctx;
+    if (off) GK_CUDA(ctx, cudaMemcpyAsync(off, s->off, (s->k + 1) * 8, cudaMemcpyDeviceToDevice, S(stream)));
+    if (ids && s->n_ids)
+        GK_CUDA(ctx, cudaMemcpyAsync(ids, s->ids, s->n_ids * 4, cudaMemcpyDeviceToDevice, S(stream)));
+    return GEEK_OK;
+}
+
+geek_status silk_seeds_free(silk_seeds *s) {
+    if (!s) return GEEK_OK;
+    cudaFree(s->off);
+    cudaFree(s->ids);
+    delete s;
+    return GEEK_OK;
+}
+
+geek_status geek_assign_centers(geek_ctx *ctx, const geek_data *data, const double *centers,
+                                int64_t k, const geek_assign_params *p, int32_t *labels,
+                                geek_assign_stats *stats, geek_stream stream) {
+    if (!ctx) return GEEK_ERR_INVALID;
+    try {
+        GK_TRY(check_data(ctx, data));
+        if (data->kind != GEEK_DENSE) return set_error(ctx, GEEK_ERR_INVALID, "dense data only");
+        if (!p || !labels || (k > 0 && !centers) || k < 0 || k > 0x7FFFFFFFLL)
+            return set_error(ctx, GEEK_ERR_INVALID, "bad assignment arguments");
+        cudaStream_t st = S(stream);
+        Scratch scr(ctx, st);
+        const bool host = data->mem == GEEK_MEM_HOST;
+        const float *x;
+        GK_TRY(stage(ctx, scr, data->x, (size_t)data->n * data->ldx, host, &x, st));
+        int32_t *lab = labels;
+        if (host) GK_TRY(scr.alloc(&lab, data->n));
+        const double *c = centers;
+        if (host && k) {
+            double *dc;
+            GK_TRY(scr.alloc(&dc, (size_t)k * data->d));
+            GK_CUDA(ctx, cudaMemcpyAsync(dc, centers, sizeof(double) * k * data->d, cudaMemcpyHostToDevice, st));
+            c = dc;
+        }
+        GK_TRY(assign_dense_centres(ctx, scr, x, data->ldx, data->n, data->d, c, k, p->precision, lab, stats, st));
+        if (host) {
+            GK_CUDA(ctx, cudaMemcpyAsync(labels, lab, sizeof(int32_t) * data->n, cudaMemcpyDeviceToHost, st));
+            GK_CUDA(ctx, cudaStreamSynchronize(st));
+        }
+        return GEEK_OK;
+    } catch (...) {
+        return set_error(ctx, GEEK_ERR_NOMEM, "host exception in geek_assign_centers");
+    }
+}
+
+geek_status geek_assign(geek_ctx *ctx, const geek_data *data, const geek_buckets *b,
+                        const silk_seeds *s, const geek_assign_params *p, int32_t *labels,
+                        double *centers, geek_assign_stats *stats, geek_stream stream) {
+    if (!ctx) return GEEK_ERR_INVALID;
+    try {
+        GK_TRY(check_data(ctx, data));
+        if (!s || !p || !labels) return set_error(ctx, GEEK_ERR_INVALID, "NULL argument");
+        cudaStream_t st = S(stream);
+        Scratch scr(ctx, st);
+        const bool host = data->mem == GEEK_MEM_HOST;
+        const int64_t n = data->n;
+        int32_t *lab = labels;
+        if (host) GK_TRY(scr.alloc(&lab, n));
+        if (data->kind == GEEK_DENSE) {
+            const float *x;
+            GK_TRY(stage(ctx, scr, data->x, (size_t)n * data->ldx, host, &x, st));
+            double *c = centers;
+            if (!c || host) GK_TRY(scr.alloc(&c, (size_t)std::max<int64_t>(1, s->k) * data->d));
+            GK_TRY(centroids_from_seeds(ctx, x, data->ldx, data->d, s, c, st));
+            GK_TRY(assign_dense_centres(ctx, scr, x, data->ldx, n, data->d, c, s->k, p->precision, lab, stats, st));
+            if (host && centers)
+                GK_CUDA(ctx, cudaMemcpyAsync(centers, c, sizeof(double) * s->k * data->d, cudaMemcpyDeviceToHost, st));
+        } else if (data->kind == GEEK_HETERO) {
+            if (!b || b->kind != GEEK_HETERO || b->n != n)
+                return set_error(ctx, GEEK_ERR_INVALID, "hetero assignment needs its geek_buckets");
+            const uint32_t *tok;
+            GK_TRY(stage(ctx, scr, data->cat, (size_t)n * data->n_cat, host, &tok, st));
+            GK_TRY(assign_hetero(ctx, scr, b, tok, data->n_cat, s, lab, stats, st));
+        } else {
+            int64_t n_items = 0;
+            if (host) {
+                n_items = data->set_off[n];
+            } else {
+                GK_CUDA(ctx, cudaMemcpyAsync(&n_items, data->set_off + n, 8, cudaMemcpyDeviceToHost, st));
+                GK_CUDA(ctx, cudaStreamSynchronize(st));
+            }
+            const int64_t *off;
+            const uint32_t *items;
+            GK_TRY(stage(ctx, scr, data->set_off, (size_t)n + 1, host, &off, st));
+            GK_TRY(stage(ctx, scr, data->set_items, (size_t)n_items, host, &items, st));
+            GK_TRY(assign_sets(ctx, scr, off, items, n, s, lab, stats, st));
+        }
+        if (host) {
+            GK_CUDA(ctx, cudaMemcpyAsync(labels, lab, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+            GK_CUDA(ctx, cudaStreamSynchronize(st));
+        }
+        return GEEK_OK;
+    } catch (...) {
+        return set_error(ctx, GEEK_ERR_NOMEM, "host exception in geek_assign");
+    }
+}
+
+}  // extern "C"

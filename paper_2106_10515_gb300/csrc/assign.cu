@@ -1,0 +1,405 @@
+// Central vectors and one-pass data assignment (Sect. 3.3, Eq. 1).
+//
+// Dense assignment evaluates d'_j = |c_j|^2 - 2 x.c_j (the row-constant
+// |x|^2 dropped) for every centre in a fast precision, keeps the best and
+// second-best value per object, and decides the argmin in FP64 only for
+// objects whose gap is within the rigorous error window.  The FP64 decision
+// reproduces the reference distance exactly: sum_t ((double)x_t - c_t)^2 in t
+// order, each operation rounded to nearest, no fused multiply-add; ties go
+// to the smallest centre index.
+#include <cfloat>
+
+#include "internal.cuh"
+
+namespace {
+
+constexpr int AS_TR = 128;   // rows per block
+constexpr int AS_TC = 64;    // centres per tile
+constexpr int AS_KC = 32;    // d-chunk of the centre tile
+constexpr int AS_RPT = 8;    // rows per thread
+constexpr int AS_CPT = 4;    // centres per thread
+constexpr int AS_MAXD = 256; // X tile resident in shared memory
+
+// FP64 reference distance of the pinned definition.
+__device__ __forceinline__ double ref_dist(const float *__restrict__ x, const double *__restrict__ c, int d) {
+    double D = 0.0;
+    for (int t = 0; t < d; t++) {
+        const double e = __dsub_rn((double)x[t], c[t]);
+        D = __dadd_rn(D, __dmul_rn(e, e));
+    }
+    return D;
+}
+
+// Rigorous half-window of the FP32 path for one object (see the proof in
+// the file header): (2 gamma_d + 4u)|x| cmax + 2u cmax^2 for the fast value,
+// plus the FP64 reference's own error (d+3) 2^-53 (|x| + cmax)^2, times 1.01.
+__device__ __forceinline__ float window_fp32(float xn, float cmax, int d) {
+    const float u = 5.9604645e-8f;
+    const float gam = (float)d * u / (1.f - (float)d * u);
+    const float e32 = (2.f * gam + 4.f * u) * xn * cmax + 2.f * u * cmax * cmax;
+    const float s = xn + cmax;
+    const float e64 = (float)(d + 3) * 1.1102230e-16f * s * s;
+    return 1.01f * (e32 + e64) + 1e-30f;
+}
+
+struct Best {
+    float b1, b2;
+    int i1;
+};
+
+__device__ __forceinline__ void best_push(Best &B, float v, int j) {
+    if (v < B.b1) {
+        B.b2 = B.b1;
+        B.b1 = v;
+        B.i1 = j;
+    } else {
+        B.b2 = fminf(B.b2, v);
+    }
+}
+
+__device__ __forceinline__ Best best_merge(Best a, Best b) {
+    Best r;
+    const bool take_b = b.b1 < a.b1 || (b.b1 == a.b1 && b.i1 < a.i1);
+    r.b1 = take_b ? b.b1 : a.b1;
+    r.i1 = take_b ? b.i1 : a.i1;
+    r.b2 = fminf(fminf(a.b2, b.b2), take_b ? a.b1 : b.b1);
+    return r;
+}
+
+// FP32 SIMT assignment: block = 128 rows, all centres streamed in tiles of
+// 64; 256 threads = 16 row groups (8 rows) x 16 centre groups (4 centres).
+__global__ void __launch_bounds__(256) k_assign_fp32(const float *__restrict__ x, int64_t ldx, int64_t n,
+                                                     int d, const float *__restrict__ c32,
+                                                     const float *__restrict__ cn, int64_t k, float cmax,
+                                                     int32_t *__restrict__ labels,
+                                                     int32_t *__restrict__ flag_rows,
+                                                     unsigned long long *__restrict__ n_flag) {
+    extern __shared__ float sm[];
+    float *xs = sm;                         // [d][AS_TR]
+    float *cs = sm + (size_t)d * AS_TR;     // [AS_KC][AS_TC]
+    __shared__ float cns[AS_TC];
+    const int t = threadIdx.x, cg = t & 15, rg = t >> 4;
+    const int64_t row0 = (int64_t)blockIdx.x * AS_TR;
+    for (int e = t; e < AS_TR * d; e += 256) {
+        const int r = e / d, kk = e % d;
+        const int64_t row = row0 + r;
+        xs[kk * AS_TR + r] = row < n ? x[row * ldx + kk] : 0.f;
+    }
+    Best B[AS_RPT];
+#pragma unroll
+    for (int r = 0; r < AS_RPT; r++) B[r] = Best{FLT_MAX, FLT_MAX, 0x7FFFFFFF};
+    for (int64_t j0 = 0; j0 < k; j0 += AS_TC) {
+        float acc[AS_RPT][AS_CPT];
+#pragma unroll
+        for (int r = 0; r < AS_RPT; r++)
+#pragma unroll
+            for (int c = 0; c < AS_CPT; c++) acc[r][c] = 0.f;
+        for (int k0 = 0; k0 < d; k0 += AS_KC) {
+            __syncthreads();
+            for (int e = t; e < AS_TC * AS_KC; e += 256) {
+                const int c = e / AS_KC, kk = e % AS_KC;
+                const int64_t j = j0 + c;
+                cs[kk * AS_TC + c] = (j < k && k0 + kk < d) ? c32[j * d + k0 + kk] : 0.f;
+            }
+            if (k0 == 0 && t < AS_TC) cns[t] = j0 + t < k ? cn[j0 + t] : FLT_MAX;
+            __syncthreads();
+            const int kmax = min(AS_KC, d - k0);
+            for (int kk = 0; kk < kmax; kk++) {
+                const float4 x0 = *reinterpret_cast<const float4 *>(&xs[(k0 + kk) * AS_TR + rg * AS_RPT]);
+                const float4 x1 = *reinterpret_cast<const float4 *>(&xs[(k0 + kk) * AS_TR + rg * AS_RPT + 4]);
+                const float4 cv = *reinterpret_cast<const float4 *>(&cs[kk * AS_TC + cg * AS_CPT]);
+                const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+                const float cc[4] = {cv.x, cv.y, cv.z, cv.w};
+#pragma unroll
+                for (int r = 0; r < AS_RPT; r++)
+#pragma unroll
+                    for (int c = 0; c < AS_CPT; c++) acc[r][c] = fmaf(xv[r], cc[c], acc[r][c]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < AS_CPT; c++) {
+            const int64_t j = j0 + cg * AS_CPT + c;
+            if (j >= k) continue;
+            const float cnj = cns[cg * AS_CPT + c];
+#pragma unroll
+            for (int r = 0; r < AS_RPT; r++) best_push(B[r], fmaf(-2.f, acc[r][c], cnj), (int)j);
+        }
+    }
+    // merge the 16 centre groups of each row group (lanes of one half-warp)
+#pragma unroll
+    for (int r = 0; r < AS_RPT; r++) {
+#pragma unroll
+        for (int o = 1; o < 16; o <<= 1) {
+            Best o_;
+            o_.b1 = __shfl_xor_sync(0xffffffffu, B[r].b1, o);
+            o_.b2 = __shfl_xor_sync(0xffffffffu, B[r].b2, o);
+            o_.i1 = __shfl_xor_sync(0xffffffffu, B[r].i1, o);
+            B[r] = best_merge(B[r], o_);
+        }
+    }
+    if (cg == 0) {
+#pragma unroll
+        for (int r = 0; r < AS_RPT; r++) {
+            const int64_t row = row0 + rg * AS_RPT + r;
+            if (row >= n) continue;
+            float xs2 = 0.f;
+            for (int kk = 0; kk < d; kk++) {
+                const float v = xs[kk * AS_TR + rg * AS_RPT + r];
+                xs2 = fmaf(v, v, xs2);
+            }
+            const float xn = sqrtf(xs2) * (1.f + 1.0e-3f);
+            const float W = 2.f * window_fp32(xn, cmax, d);
+            // no finite value (non-finite input): undecided here, FP64 decides
+            const bool valid = B[r].i1 != 0x7FFFFFFF;
+            labels[row] = valid ? B[r].i1 : -1;
+            const bool sure = valid && (k == 1 || (B[r].b2 - B[r].b1 > W * (1.f + 1e-6f)));
+            if (!sure) {
+                const unsigned long long q = atomicAdd(n_flag, 1ull);
+                flag_rows[q] = (int32_t)row;
+            }
+        }
+    }
+}
+
+// Exact decision for one flagged object: FP32 filter over all centres, then
+// the FP64 reference distance for every centre inside the window.
+__global__ void __launch_bounds__(256) k_assign_recheck(const float *__restrict__ x, int64_t ldx, int d,
+                                                        const float *__restrict__ c32, const float *__restrict__ cn,
+                                                        const double *__restrict__ c64, int64_t k, float cmax,
+                                                        const int32_t *__restrict__ flag_rows,
+                                                        const unsigned long long *__restrict__ n_flag,
+                                                        int32_t *__restrict__ labels) {
+    extern __shared__ float xr[];  // d floats
+    __shared__ float red_f[256];
+    __shared__ double red_d[256];
+    __shared__ int red_i[256];
+    const int t = threadIdx.x;
+    const int64_t nf = (int64_t)*n_flag;
+    for (int64_t q = blockIdx.x; q < nf; q += gridDim.x) {
+        const int64_t row = flag_rows[q];
+        __syncthreads();
+        for (int kk = t; kk < d; kk += 256) xr[kk] = x[row * ldx + kk];
+        __syncthreads();
+        float xs2 = 0.f;
+        for (int kk = 0; kk < d; kk++) xs2 = fmaf(xr[kk], xr[kk], xs2);
+        const float xn = sqrtf(xs2) * (1.f + 1.0e-3f);
+        float m = FLT_MAX;
+        for (int64_t j = t; j < k; j += 256) {
+            float dot = 0.f;
+            for (int kk = 0; kk < d; kk++) dot = fmaf(xr[kk], c32[j * d + kk], dot);
+            m = fminf(m, fmaf(-2.f, dot, cn[j]));
+        }
+        red_f[t] = m;
+        __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {
+            if (t < o) red_f[t] = fminf(red_f[t], red_f[t + o]);
+            __syncthreads();
+        }
+        const float lim = red_f[0] + 2.f * window_fp32(xn, cmax, d) * (1.f + 1e-6f);
+        double bD = DBL_MAX;
+        int bj = 0x7FFFFFFF;
+        for (int64_t j = t; j < k; j += 256) {
+            float dot = 0.f;
+            for (int kk = 0; kk < d; kk++) dot = fmaf(xr[kk], c32[j * d + kk], dot);
+            if (fmaf(-2.f, dot, cn[j]) <= lim) {
+                const double D = ref_dist(xr, c64 + j * d, d);
+                if (D < bD || (D == bD && (int)j < bj)) {
+                    bD = D;
+                    bj = (int)j;
+                }
+            }
+        }
+        red_d[t] = bD;
+        red_i[t] = bj;
+        __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {
+            if (t < o) {
+                const double D2 = red_d[t + o];
+                const int j2 = red_i[t + o];
+                if (D2 < red_d[t] || (D2 == red_d[t] && j2 < red_i[t])) {
+                    red_d[t] = D2;
+                    red_i[t] = j2;
+                }
+            }
+            __syncthreads();
+        }
+        // no candidate with a distance below +inf (non-finite input): -1,
+        // as the reference argmin that never improves on +inf
+        if (t == 0) labels[row] = red_i[0] == 0x7FFFFFFF ? -1 : red_i[0];
+    }
+}
+
+// centre preparation: FP32 copy, |c|^2 (FP64 then rounded), max |c|
+__global__ void k_centre_prep(const double *__restrict__ c64, int64_t k, int d, float *__restrict__ c32,
+                              float *__restrict__ cn, unsigned *__restrict__ cmax_bits) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int t = 0; t < d; t++) {
+            const double v = c64[j * d + t];
+            c32[j * d + t] = (float)v;
+            s += v * v;
+        }
+        cn[j] = (float)s;
+        const float nrm = (float)sqrt(s) * (1.f + 1e-6f);
+        atomicMax(cmax_bits, __float_as_uint(nrm));  // non-negative floats order as uints
+    }
+}
+
+// per-object distance to its centre in double-float form: diff = (x - c_hi)
+// - c_lo with c = c_hi + c_lo, squares accumulated in FP32; partial sums
+// per block (deterministic final reduction on one block)
+__global__ void __launch_bounds__(256) k_assign_stats(const float *__restrict__ x, int64_t ldx, int64_t n, int d,
+                                                      const double *__restrict__ c64, int64_t k,
+                                                      const int32_t *__restrict__ labels,
+                                                      double *__restrict__ part_sum, float *__restrict__ part_max) {
+    __shared__ double ss[256];
+    __shared__ float sm_[256];
+    double s = 0.0;
+    float mx = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int j = labels[i];
+        if (j < 0 || j >= k) continue;
+        float D = 0.f;
+        for (int t = 0; t < d; t++) {
+            const double c = c64[(int64_t)j * d + t];
+            const float ch = (float)c;
+            const float cl = (float)(c - (double)ch);
+            const float e = (x[i * ldx + t] - ch) - cl;
+            D = fmaf(e, e, D);
+        }
+        s += (double)D;
+        mx = fmaxf(mx, D);
+    }
+    ss[threadIdx.x] = s;
+    sm_[threadIdx.x] = mx;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            ss[threadIdx.x] += ss[threadIdx.x + o];
+            sm_[threadIdx.x] = fmaxf(sm_[threadIdx.x], sm_[threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part_sum[blockIdx.x] = ss[0];
+        part_max[blockIdx.x] = sm_[0];
+    }
+}
+
+__global__ void k_stats_final(const double *__restrict__ ps, const float *__restrict__ pm, int nb,
+                              double *__restrict__ out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        float m = 0.f;
+        for (int i = 0; i < nb; i++) {
+            s += ps[i];
+            m = fmaxf(m, pm[i]);
+        }
+        out[0] = s;
+        out[1] = sqrt((double)m);
+    }
+}
+
+// centroid of each seed: FP64 sum over members in ascending id, one IEEE
+// division by the count; one thread per (seed, coordinate)
+__global__ void k_centroids(const float *__restrict__ x, int64_t ldx, int d, int64_t k,
+                            const int64_t *__restrict__ soff, const int32_t *__restrict__ sids,
+                            double *__restrict__ c) {
+    const int64_t total = k * d;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = e / d;
+        const int t = (int)(e % d);
+        double s = 0.0;
+        for (int64_t p = soff[j]; p < soff[j + 1]; p++) s = __dadd_rn(s, (double)x[(int64_t)sids[p] * ldx + t]);
+        c[e] = __ddiv_rn(s, (double)(soff[j + 1] - soff[j]));
+    }
+}
+
+__global__ void k_fill_labels(int32_t *l, int64_t n, int32_t v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        l[i] = v;
+}
+
+}  // namespace
+
+geek_status centroids_from_seeds(geek_ctx *ctx, const float *x, int64_t ldx, int d, const silk_seeds *s,
+                                 double *centres, cudaStream_t st) {
+    if (s->k == 0) return GEEK_OK;
+    k_centroids<<<grid_for(s->k * d, 256, ctx->num_sms), 256, 0, st>>>(x, ldx, d, s->k, s->off, s->ids, centres);
+    GK_LAUNCH(ctx);
+    return GEEK_OK;
+}
+
+geek_status assign_dense_centres(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ldx, int64_t n, int d,
+                                 const double *centres, int64_t k, int precision, int32_t *labels,
+                                 geek_assign_stats *stats, cudaStream_t st) {
+    if (stats) *stats = geek_assign_stats{0.0, 0.0, k, 0};
+    if (n == 0) return GEEK_OK;
+    if (k == 0) {
+        k_fill_labels<<<grid_for(n, 256, ctx->num_sms), 256, 0, st>>>(labels, n, -1);
+        GK_LAUNCH(ctx);
+        return GEEK_OK;
+    }
+    if (d > AS_MAXD) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "dense assignment supports d <= %d", AS_MAXD);
+    if (precision != GEEK_PREC_FP32 && precision != GEEK_PREC_BF16)
+        return set_error(ctx, GEEK_ERR_INVALID, "bad precision");
+    float *c32, *cn;
+    unsigned *cmax_bits;
+    GK_TRY(scr.alloc(&c32, (size_t)k * d));
+    GK_TRY(scr.alloc(&cn, k));
+    GK_TRY(scr.alloc(&cmax_bits, 1));
+    GK_CUDA(ctx, cudaMemsetAsync(cmax_bits, 0, sizeof(unsigned), st));
+    k_centre_prep<<<grid_for(k, 128, ctx->num_sms), 128, 0, st>>>(centres, k, d, c32, cn, cmax_bits);
+    GK_LAUNCH(ctx);
+    unsigned h_bits = 0;
+    GK_CUDA(ctx, cudaMemcpyAsync(&h_bits, cmax_bits, sizeof h_bits, cudaMemcpyDeviceToHost, st));
+    GK_CUDA(ctx, cudaStreamSynchronize(st));
+    float cmax;
+    memcpy(&cmax, &h_bits, sizeof cmax);
+    int32_t *flag_rows;
+    unsigned long long *n_flag;
+    GK_TRY(scr.alloc(&flag_rows, n));
+    GK_TRY(scr.alloc(&n_flag, 1));
+    GK_CUDA(ctx, cudaMemsetAsync(n_flag, 0, sizeof(unsigned long long), st));
+    if (precision == GEEK_PREC_BF16) {
+        GK_TRY(assign_tc_bf16(ctx, scr, x, ldx, n, d, centres, k, labels, flag_rows, n_flag, st));
+    } else {
+        const size_t smem = (size_t)d * AS_TR * sizeof(float) + (size_t)AS_KC * AS_TC * sizeof(float);
+        GK_CUDA(ctx, cudaFuncSetAttribute(k_assign_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_assign_fp32<<<(unsigned)ceil_div(n, AS_TR), 256, smem, st>>>(x, ldx, n, d, c32, cn, k, cmax, labels,
+                                                                         flag_rows, n_flag);
+        GK_LAUNCH(ctx);
+    }
+    unsigned long long h_flag = 0;
+    GK_CUDA(ctx, cudaMemcpyAsync(&h_flag, n_flag, sizeof h_flag, cudaMemcpyDeviceToHost, st));
+    GK_CUDA(ctx, cudaStreamSynchronize(st));
+    if (h_flag) {
+        const int blocks = (int)std::min<unsigned long long>(h_flag, (unsigned long long)ctx->num_sms * 8);
+        k_assign_recheck<<<blocks, 256, d * sizeof(float), st>>>(x, ldx, d, c32, cn, centres, k, cmax, flag_rows,
+                                                                  n_flag, labels);
+        GK_LAUNCH(ctx);
+    }
+    if (stats) {
+        const int nb = grid_for(n, 256, ctx->num_sms);
+        double *ps, *out;
+        float *pm;
+        GK_TRY(scr.alloc(&ps, nb));
+        GK_TRY(scr.alloc(&pm, nb));
+        GK_TRY(scr.alloc(&out, 2));
+        k_assign_stats<<<nb, 256, 0, st>>>(x, ldx, n, d, centres, k, labels, ps, pm);
+        k_stats_final<<<1, 32, 0, st>>>(ps, pm, nb, out);
+        GK_LAUNCH(ctx);
+        double h[2];
+        GK_CUDA(ctx, cudaMemcpyAsync(h, out, sizeof h, cudaMemcpyDeviceToHost, st));
+        GK_CUDA(ctx, cudaStreamSynchronize(st));
+        stats->sse = h[0];
+        stats->radius_max = h[1];
+        stats->k = k;
+        stats->n_recheck_rows = (int64_t)h_flag;
+    }
+    return GEEK_OK;
+}
+

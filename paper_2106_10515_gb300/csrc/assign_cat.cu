@@ -1,0 +1,454 @@
+// Central vectors and assignment for categorical and set data (Sect. 3.3):
+//  - heterogeneous rows: unified categorical attributes (per table, the
+//    packed key of the numeric E2LSH part; then the tokens), per-attribute
+//    mode as central vector, distance 1 - Jaccard = most matching attributes;
+//  - sparse sets: central vector = items present in more than half of the
+//    members, distance 1 - |A n C| / |A u C| compared exactly as fractions.
+#include "internal.cuh"
+
+namespace {
+
+int G(geek_ctx *ctx, int64_t work) { return grid_for(std::max<int64_t>(work, 1), 256, ctx->num_sms); }
+
+// attrs[i][a]: a < L -> numeric key of table a, else token a - L
+__global__ void k_build_attrs(int64_t n, int L, int ncat, const uint64_t *__restrict__ num_key,
+                              const uint32_t *__restrict__ tok, uint64_t *__restrict__ attrs) {
+    const int A = L + ncat;
+    const int64_t total = n * A;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / A;
+        const int a = (int)(e % A);
+        attrs[e] = a < L ? num_key[(int64_t)a * n + i] : (uint64_t)tok[i * ncat + (a - L)];
+    }
+}
+
+// mode of attribute a over seed j's members: most frequent value, ties to the
+// smallest (one thread per (seed, attribute); quadratic in the seed size)
+__global__ void k_modes(int64_t k, int A, const int64_t *__restrict__ soff, const int32_t *__restrict__ sids,
+                        const uint64_t *__restrict__ attrs, uint64_t *__restrict__ modes) {
+    const int64_t total = k * A;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = e / A;
+        const int a = (int)(e % A);
+        const int64_t s = soff[j], t = soff[j + 1];
+        uint64_t best = 0;
+        int64_t bc = 0;
+        for (int64_t p = s; p < t; p++) {
+            const uint64_t v = attrs[(int64_t)sids[p] * A + a];
+            int64_t c = 0;
+            for (int64_t q = s; q < t; q++) c += attrs[(int64_t)sids[q] * A + a] == v;
+            if (c > bc || (c == bc && v < best)) {
+                bc = c;
+                best = v;
+            }
+        }
+        modes[e] = best;
+    }
+}
+
+// label = argmax_j #{a : attrs[i][a] == modes[j][a]}, ties to the smallest j
+constexpr int CAT_TILE = 64;
+constexpr int CAT_MAXA = 32;
+__global__ void __launch_bounds__(256) k_assign_cat(int64_t n, int A, int64_t k, const uint64_t *__restrict__ attrs,
+                                                    const uint64_t *__restrict__ modes, int32_t *__restrict__ labels,
+                                                    int32_t *__restrict__ matches) {
+    __shared__ uint64_t ms[CAT_TILE * CAT_MAXA];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint64_t x[CAT_MAXA];
+    for (int a = 0; a < CAT_MAXA; a++) x[a] = (i < n && a < A) ? attrs[i * A + a] : 0;
+    int bm = -1, bj = -1;
+    for (int64_t j0 = 0; j0 < k; j0 += CAT_TILE) {
+        __syncthreads();
+        const int tn = (int)min((int64_t)CAT_TILE, k - j0);
+        for (int e = threadIdx.x; e < tn * A; e += blockDim.x) ms[(e / A) * CAT_MAXA + e % A] = modes[(j0 + e / A) * A + e % A];
+        __syncthreads();
+        for (int jj = 0; jj < tn; jj++) {
+            int m = 0;
+#pragma unroll
+            for (int a = 0; a < CAT_MAXA; a++)
+                if (a < A) m += x[a] == ms[jj * CAT_MAXA + a];
+            if (m > bm) {
+                bm = m;
+                bj = (int)(j0 + jj);
+            }
+        }
+    }
+    if (i < n) {
+        labels[i] = bj;
+        if (matches) matches[i] = bm;
+    }
+}
+
+// ---- set data --------------------------------------------------------------
+
+// member weight of each (group, member) entry = size of the member's set
+__global__ void k_group_w(int64_t m, const int32_t *__restrict__ gmem, const int64_t *__restrict__ soff,
+                          int64_t *__restrict__ w) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x)
+        w[p] = soff[gmem[p] + 1] - soff[gmem[p]];
+}
+
+__global__ void k_group_of(int64_t ng, const int64_t *__restrict__ goff, int32_t *__restrict__ gid) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x)
+        for (int64_t p = goff[g]; p < goff[g + 1]; p++) gid[p] = (int32_t)g;
+}
+
+__global__ void k_group_expand(int64_t m, const int32_t *__restrict__ gid, const int32_t *__restrict__ gmem,
+                               const int64_t *__restrict__ woff, const int64_t *__restrict__ soff,
+                               const uint32_t *__restrict__ sids, uint64_t *__restrict__ pairs) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t g = (uint64_t)gid[p];
+        const int32_t s = gmem[p];
+        int64_t o = woff[p];
+        for (int64_t q = soff[s]; q < soff[s + 1]; q++) pairs[o++] = (g << 32) | sids[q];
+    }
+}
+
+__global__ void k_group_keep(const int64_t *__restrict__ nruns, const int64_t *__restrict__ prs,
+                             const uint64_t *__restrict__ pairs, const int64_t *__restrict__ goff,
+                             int64_t *__restrict__ keep, int64_t *__restrict__ cnt) {
+    const int64_t nr = *nruns;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t len = prs[r + 1] - prs[r];
+        const int64_t g = (int64_t)(pairs[prs[r]] >> 32);
+        const bool kp = 2 * len > goff[g + 1] - goff[g];
+        keep[r] = kp;
+        if (kp) atomicAdd((unsigned long long *)&cnt[g], 1ull);
+    }
+}
+
+__global__ void k_group_emit(const int64_t *__restrict__ nruns, const int64_t *__restrict__ prs,
+                             const uint64_t *__restrict__ pairs, const int64_t *__restrict__ keep,
+                             const int64_t *__restrict__ pos, uint32_t *__restrict__ out) {
+    const int64_t nr = *nruns;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += (int64_t)gridDim.x * blockDim.x)
+        if (keep[r]) out[pos[r]] = (uint32_t)(pairs[prs[r]] & 0xFFFFFFFFu);
+}
+
+// item -> centres inverted index helpers
+__global__ void k_centre_pairs(int64_t k, const int64_t *__restrict__ coff, const uint32_t *__restrict__ citems,
+                               uint64_t *__restrict__ pairs) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += (int64_t)gridDim.x * blockDim.x)
+        for (int64_t p = coff[j]; p < coff[j + 1]; p++) pairs[p] = ((uint64_t)citems[p] << 32) | (uint64_t)j;
+}
+
+// heavy items: the H most frequent centre items get a bit each
+constexpr int HEAVY = 64;
+
+__global__ void k_item_key(int64_t m, const uint64_t *__restrict__ pairs, uint64_t *__restrict__ ikey) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += (int64_t)gridDim.x * blockDim.x)
+        ikey[q] = pairs[q] >> 32;
+}
+
+// sort key ranking runs by posting length, longest first
+__global__ void k_len_key(int64_t nr, const int64_t *__restrict__ rs, uint64_t *__restrict__ key,
+                          uint32_t *__restrict__ val) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t len = (uint64_t)(rs[r + 1] - rs[r]);
+        key[r] = ((0xFFFFFFFFull - len) << 32) | (uint64_t)r;
+        val[r] = (uint32_t)r;
+    }
+}
+
+__global__ void k_mark_heavy(int nheavy, const uint32_t *__restrict__ order, const int64_t *__restrict__ rs,
+                             const uint64_t *__restrict__ ikey, int64_t *__restrict__ is_heavy,
+                             uint32_t *__restrict__ heavy) {
+    const int h = threadIdx.x;
+    if (h < nheavy) {
+        const uint32_t r = order[h];
+        is_heavy[r] = 1;
+        heavy[h] = (uint32_t)ikey[rs[r]];
+    }
+}
+
+__global__ void k_light_flags(int64_t nr, const int64_t *__restrict__ rs, const int64_t *__restrict__ is_heavy,
+                              int64_t *__restrict__ lrun, int64_t *__restrict__ lent) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += (int64_t)gridDim.x * blockDim.x) {
+        const bool light = !is_heavy[r];
+        lrun[r] = light;
+        lent[r] = light ? rs[r + 1] - rs[r] : 0;
+    }
+}
+
+__global__ void k_light_emit(int64_t nr, const int64_t *__restrict__ rs, const uint64_t *__restrict__ ikey,
+                             const uint64_t *__restrict__ pairs, const int64_t *__restrict__ is_heavy,
+                             const int64_t *__restrict__ lrun_pos, const int64_t *__restrict__ lent_pos,
+                             uint32_t *__restrict__ litem, int64_t *__restrict__ loff, uint32_t *__restrict__ lcentre,
+                             const int64_t *__restrict__ nlent, int64_t nlight) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += (int64_t)gridDim.x * blockDim.x) {
+        if (is_heavy[r]) continue;
+        const int64_t p = lrun_pos[r];
+        litem[p] = (uint32_t)ikey[rs[r]];
+        loff[p] = lent_pos[r];
+        int64_t o = lent_pos[r];
+        for (int64_t q = rs[r]; q < rs[r + 1]; q++) lcentre[o++] = (uint32_t)(pairs[q] & 0xFFFFFFFFu);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) loff[nlight] = *nlent;
+}
+
+__global__ void k_heavy_masks(int64_t k, const int64_t *__restrict__ coff, const uint32_t *__restrict__ citems,
+                              const uint32_t *__restrict__ heavy, int nheavy, uint64_t *__restrict__ cmask,
+                              int32_t *__restrict__ clen) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t m = 0;
+        for (int64_t p = coff[j]; p < coff[j + 1]; p++)
+            for (int h = 0; h < nheavy; h++)
+                if (citems[p] == heavy[h]) m |= 1ull << h;
+        cmask[j] = m;
+        clen[j] = (int32_t)(coff[j + 1] - coff[j]);
+    }
+}
+
+// Jaccard assignment: warp per set.  Intersections with heavy items come
+// from bitmasks; light items go through the inverted index into a per-warp
+// counter array (cleared after use).  Every centre is then scored exactly:
+// J_j = inter / (|A| + |C_j| - inter), compared by cross-multiplication.
+__global__ void __launch_bounds__(256) k_assign_jaccard(
+    int64_t n, const int64_t *__restrict__ off, const uint32_t *__restrict__ items, int64_t k,
+    const int32_t *__restrict__ clen, const uint64_t *__restrict__ cmask, const uint32_t *__restrict__ heavy,
+    int nheavy, const uint32_t *__restrict__ post_item, const int64_t *__restrict__ post_off, int64_t n_post_items,
+    const uint32_t *__restrict__ post_centre, int32_t *__restrict__ counts, int32_t *__restrict__ labels) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int32_t *cnt = counts + warp * k;
+    for (int64_t i = warp; i < n; i += nw) {
+        const int64_t s = off[i], e = off[i + 1];
+        const int64_t na = e - s;
+        uint64_t amask = 0;
+        // light items: binary search in the sorted item list of the index
+        for (int64_t p = s + lane; p < e; p += 32) {
+            const uint32_t it = items[p];
+            bool hv = false;
+            for (int h = 0; h < nheavy; h++)
+                if (heavy[h] == it) {
+                    amask |= 1ull << h;
+                    hv = true;
+                }
+            if (hv) continue;
+            int64_t lo = 0, hi = n_post_items;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (post_item[mid] < it) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo < n_post_items && post_item[lo] == it)
+                for (int64_t q = post_off[lo]; q < post_off[lo + 1]; q++) atomicAdd(&cnt[post_centre[q]], 1);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) amask |= __shfl_xor_sync(0xffffffffu, amask, o);
+        __syncwarp();
+        __threadfence_block();
+        int64_t bn = -1, bd = 1;
+        int bj = 0x7FFFFFFF;
+        for (int64_t j = lane; j < k; j += 32) {
+            const int64_t in = (int64_t)__popcll(amask & cmask[j]) + cnt[j];
+            cnt[j] = 0;
+            const int64_t un = na + clen[j] - in;
+            const int64_t num = un ? in : 0, den = un ? un : 1;
+            if (bj == 0x7FFFFFFF || num * bd > bn * den) {
+                bn = num;
+                bd = den;
+                bj = (int)j;
+            }
+        }
+        // warp argmax: larger fraction, then smaller index
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const int64_t on = __shfl_xor_sync(0xffffffffu, bn, o);
+            const int64_t od = __shfl_xor_sync(0xffffffffu, bd, o);
+            const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+            bool take;
+            if (oj == 0x7FFFFFFF) take = false;
+            else if (bj == 0x7FFFFFFF) take = true;
+            else {
+                const int64_t l = on * bd, r = bn * od;
+                take = l > r || (l == r && oj < bj);
+            }
+            if (take) {
+                bn = on;
+                bd = od;
+                bj = oj;
+            }
+        }
+        if (lane == 0) labels[i] = bj == 0x7FFFFFFF ? -1 : bj;
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+// Majority set of each group of sets: items present in more than half of
+// the group's member sets (groups CSR goff/gmem of set indices; sets CSR
+// soff/sids).  Output CSR has one (possibly empty) entry per group.
+geek_status majority_per_group(geek_ctx *ctx, Scratch &scr, int64_t ng, const int64_t *goff, const int32_t *gmem,
+                               int64_t m, const int64_t *soff, const uint32_t *sids, int64_t **out_off,
+                               uint32_t **out_ids, int64_t *out_n, cudaStream_t st) {
+    int64_t *w, *woff, *T_dev, *cnt, *coff, *tot;
+    int32_t *gid;
+    GK_TRY(scr.alloc(&w, std::max<int64_t>(m, 1)));
+    GK_TRY(scr.alloc(&woff, std::max<int64_t>(m, 1)));
+    GK_TRY(scr.alloc(&gid, std::max<int64_t>(m, 1)));
+    GK_TRY(scr.alloc(&T_dev, 1));
+    GK_TRY(scr.alloc(&cnt, ng));
+    GK_TRY(scr.alloc(out_off, ng + 1));
+    GK_TRY(scr.alloc(&tot, 1));
+    GK_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(int64_t) * ng, st));
+    k_group_w<<<G(ctx, m), 256, 0, st>>>(m, gmem, soff, w);
+    k_group_of<<<G(ctx, ng), 256, 0, st>>>(ng, goff, gid);
+    GK_LAUNCH(ctx);
+    GK_TRY(exclusive_scan_i64(ctx, scr, w, woff, m, T_dev, st));
+    int64_t T = 0;
+    GK_CUDA(ctx, cudaMemcpyAsync(&T, T_dev, 8, cudaMemcpyDeviceToHost, st));
+    GK_CUDA(ctx, cudaStreamSynchronize(st));
+    int64_t total = 0;
+    if (T > 0) {
+        uint64_t *pairs;
+        GK_TRY(scr.alloc(&pairs, T));
+        k_group_expand<<<G(ctx, m), 256, 0, st>>>(m, gid, gmem, woff, soff, sids, pairs);
+        GK_LAUNCH(ctx);
+        GK_TRY(radix_sort_segments(ctx, scr, 1, T, &pairs, nullptr, nullptr, 32 + bit_length_u64((uint64_t)ng), st));
+        int64_t *prs, *nr;
+        GK_TRY(scr.alloc(&prs, T + 1));
+        GK_TRY(scr.alloc(&nr, 1));
+        GK_TRY(segment_runs(ctx, scr, 1, T, pairs, nullptr, nullptr, prs, nr, st));
+        int64_t NR = 0;
+        GK_CUDA(ctx, cudaMemcpyAsync(&NR, nr, 8, cudaMemcpyDeviceToHost, st));
+        GK_CUDA(ctx, cudaStreamSynchronize(st));
+        int64_t *keep, *pos, *ktot;
+        GK_TRY(scr.alloc(&keep, NR));
+        GK_TRY(scr.alloc(&pos, NR));
+        GK_TRY(scr.alloc(&ktot, 1));
+        k_group_keep<<<G(ctx, NR), 256, 0, st>>>(nr, prs, pairs, goff, keep, cnt);
+        GK_LAUNCH(ctx);
+        GK_TRY(exclusive_scan_i64(ctx, scr, keep, pos, NR, ktot, st));
+        GK_CUDA(ctx, cudaMemcpyAsync(&total, ktot, 8, cudaMemcpyDeviceToHost, st));
+        GK_CUDA(ctx, cudaStreamSynchronize(st));
+        GK_TRY(scr.alloc(out_ids, std::max<int64_t>(1, total)));
+        k_group_emit<<<G(ctx, NR), 256, 0, st>>>(nr, prs, pairs, keep, pos, *out_ids);
+        GK_LAUNCH(ctx);
+    } else {
+        GK_TRY(scr.alloc(out_ids, 1));
+    }
+    GK_TRY(exclusive_scan_i64(ctx, scr, cnt, *out_off, ng, tot, st));
+    GK_CUDA(ctx, cudaMemcpyAsync(*out_off + ng, tot, 8, cudaMemcpyDeviceToDevice, st));
+    *out_n = total;
+    (void)coff;
+    return GEEK_OK;
+}
+
+geek_status assign_hetero(geek_ctx *ctx, Scratch &scr, const geek_buckets *b, const uint32_t *tok, int n_cat,
+                          const silk_seeds *s, int32_t *labels, geek_assign_stats *stats, cudaStream_t st) {
+    const int64_t n = b->n, k = s->k;
+    const int A = b->L + n_cat;
+    if (stats) *stats = geek_assign_stats{0.0, 0.0, k, 0};
+    if (A > CAT_MAXA) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "more than %d categorical attributes", CAT_MAXA);
+    if (n == 0) return GEEK_OK;
+    uint64_t *attrs, *modes;
+    int32_t *matches;
+    GK_TRY(scr.alloc(&attrs, (size_t)n * A));
+    GK_TRY(scr.alloc(&modes, (size_t)std::max<int64_t>(k, 1) * A));
+    GK_TRY(scr.alloc(&matches, n));
+    k_build_attrs<<<G(ctx, n * A), 256, 0, st>>>(n, b->L, n_cat, b->num_key, tok, attrs);
+    if (k) k_modes<<<G(ctx, k * A), 256, 0, st>>>(k, A, s->off, s->ids, attrs, modes);
+    k_assign_cat<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(n, A, k, attrs, modes, labels, matches);
+    GK_LAUNCH(ctx);
+    if (stats) {
+        // SSE in the categorical distance 1 - m / (2A - m), computed on the host
+        std::vector<int32_t> hm(n);
+        GK_CUDA(ctx, cudaMemcpyAsync(hm.data(), matches, 4 * n, cudaMemcpyDeviceToHost, st));
+        GK_CUDA(ctx, cudaStreamSynchronize(st));
+        double sse = 0.0, rmax = 0.0;
+        for (int64_t i = 0; i < n; i++) {
+            if (hm[i] < 0) continue;
+            const double dd = 1.0 - (double)hm[i] / (double)(2 * A - hm[i]);
+            sse += dd;
+            rmax = std::max(rmax, dd);
+        }
+        stats->sse = sse;
+        stats->radius_max = rmax;
+    }
+    return GEEK_OK;
+}
+
+geek_status assign_sets(geek_ctx *ctx, Scratch &scr, const int64_t *off, const uint32_t *items, int64_t n,
+                        const silk_seeds *s, int32_t *labels, geek_assign_stats *stats, cudaStream_t st) {
+    const int64_t k = s->k;
+    if (stats) *stats = geek_assign_stats{0.0, 0.0, k, 0};
+    if (n == 0) return GEEK_OK;
+    if (k == 0) {
+        GK_CUDA(ctx, cudaMemsetAsync(labels, 0xFF, sizeof(int32_t) * n, st));
+        return GEEK_OK;
+    }
+    // centres: majority item sets of the seeds
+    int64_t *coff, nci = 0;
+    uint32_t *citems;
+    GK_TRY(majority_per_group(ctx, scr, k, s->off, s->ids, s->n_ids, off, items, &coff, &citems, &nci, st));
+    // inverted index item -> centres: pairs sorted by (item, centre), runs of
+    // equal items; the HEAVY longest posting lists become bitmask items
+    uint64_t *pairs, *ikey;
+    GK_TRY(scr.alloc(&pairs, std::max<int64_t>(nci, 1)));
+    GK_TRY(scr.alloc(&ikey, std::max<int64_t>(nci, 1)));
+    k_centre_pairs<<<G(ctx, k), 256, 0, st>>>(k, coff, citems, pairs);
+    GK_LAUNCH(ctx);
+    GK_TRY(radix_sort_segments(ctx, scr, 1, nci, &pairs, nullptr, nullptr, 64, st));
+    k_item_key<<<G(ctx, nci), 256, 0, st>>>(nci, pairs, ikey);
+    GK_LAUNCH(ctx);
+    int64_t *rs, *nr_dev;
+    GK_TRY(scr.alloc(&rs, nci + 1));
+    GK_TRY(scr.alloc(&nr_dev, 1));
+    GK_TRY(segment_runs(ctx, scr, 1, nci, ikey, nullptr, nullptr, rs, nr_dev, st));
+    int64_t ni = 0;
+    GK_CUDA(ctx, cudaMemcpyAsync(&ni, nr_dev, 8, cudaMemcpyDeviceToHost, st));
+    GK_CUDA(ctx, cudaStreamSynchronize(st));
+    // rank runs by posting length (longest first, then item order)
+    uint64_t *lkey;
+    uint32_t *lval;
+    GK_TRY(scr.alloc(&lkey, std::max<int64_t>(ni, 1)));
+    GK_TRY(scr.alloc(&lval, std::max<int64_t>(ni, 1)));
+    k_len_key<<<G(ctx, ni), 256, 0, st>>>(ni, rs, lkey, lval);
+    GK_LAUNCH(ctx);
+    GK_TRY(radix_sort_segments(ctx, scr, 1, ni, &lkey, nullptr, &lval, 64, st));
+    const int nheavy = (int)std::min<int64_t>(HEAVY, ni);
+    uint32_t *d_heavy, *d_litem, *d_lcentre;
+    int64_t *is_heavy, *lrun, *lrun_pos, *lent, *lent_pos, *d_loff, *nlight, *nlent;
+    GK_TRY(scr.alloc(&d_heavy, std::max(1, nheavy)));
+    GK_TRY(scr.alloc(&is_heavy, std::max<int64_t>(ni, 1)));
+    GK_TRY(scr.alloc(&lrun, std::max<int64_t>(ni, 1)));
+    GK_TRY(scr.alloc(&lrun_pos, std::max<int64_t>(ni, 1)));
+    GK_TRY(scr.alloc(&lent, std::max<int64_t>(ni, 1)));
+    GK_TRY(scr.alloc(&lent_pos, std::max<int64_t>(ni, 1)));
+    GK_TRY(scr.alloc(&nlight, 1));
+    GK_TRY(scr.alloc(&nlent, 1));
+    GK_CUDA(ctx, cudaMemsetAsync(is_heavy, 0, 8 * std::max<int64_t>(ni, 1), st));
+    k_mark_heavy<<<1, 64, 0, st>>>(nheavy, lval, rs, ikey, is_heavy, d_heavy);
+    k_light_flags<<<G(ctx, ni), 256, 0, st>>>(ni, rs, is_heavy, lrun, lent);
+    GK_LAUNCH(ctx);
+    GK_TRY(exclusive_scan_i64(ctx, scr, lrun, lrun_pos, ni, nlight, st));
+    GK_TRY(exclusive_scan_i64(ctx, scr, lent, lent_pos, ni, nlent, st));
+    int64_t h_nlight = 0, h_nlent = 0;
+    GK_CUDA(ctx, cudaMemcpyAsync(&h_nlight, nlight, 8, cudaMemcpyDeviceToHost, st));
+    GK_CUDA(ctx, cudaMemcpyAsync(&h_nlent, nlent, 8, cudaMemcpyDeviceToHost, st));
+    GK_CUDA(ctx, cudaStreamSynchronize(st));
+    GK_TRY(scr.alloc(&d_litem, std::max<int64_t>(1, h_nlight)));
+    GK_TRY(scr.alloc(&d_loff, h_nlight + 1));
+    GK_TRY(scr.alloc(&d_lcentre, std::max<int64_t>(1, h_nlent)));
+    k_light_emit<<<G(ctx, ni), 256, 0, st>>>(ni, rs, ikey, pairs, is_heavy, lrun_pos, lent_pos, d_litem, d_loff,
+                                             d_lcentre, nlent, h_nlight);
+    GK_LAUNCH(ctx);
+    uint64_t *cmask;
+    int32_t *clen, *counts;
+    GK_TRY(scr.alloc(&cmask, k));
+    GK_TRY(scr.alloc(&clen, k));
+    k_heavy_masks<<<G(ctx, k), 256, 0, st>>>(k, coff, citems, d_heavy, nheavy, cmask, clen);
+    GK_LAUNCH(ctx);
+    const int blocks = ctx->num_sms * 4;
+    const int64_t nwarps = (int64_t)blocks * 8;
+    GK_TRY(scr.alloc(&counts, (size_t)nwarps * k));
+    GK_CUDA(ctx, cudaMemsetAsync(counts, 0, sizeof(int32_t) * nwarps * k, st));
+    k_assign_jaccard<<<blocks, 256, 0, st>>>(n, off, items, k, clen, cmask, d_heavy, nheavy, d_litem, d_loff,
+                                             h_nlight, d_lcentre, counts, labels);
+    GK_LAUNCH(ctx);
+    GK_CUDA(ctx, cudaStreamSynchronize(st));
+    return GEEK_OK;
+}

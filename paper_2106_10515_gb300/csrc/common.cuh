@@ -1,0 +1,133 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "geek.h"
+
+#define GEEK_VERSION_STRING "geek-gb300 0.1 (sm_103a)"
+
+struct geek_ctx {
+    int device = 0;
+    int num_sms = 0;
+    std::string last_error;
+};
+
+// Per-call error plumbing: every failure sets ctx->last_error and returns.
+geek_status set_error(geek_ctx *ctx, geek_status st, const char *fmt, ...);
+
+#define GK_CUDA(ctx, call)                                                                   \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return set_error((ctx), e_ == cudaErrorMemoryAllocation ? GEEK_ERR_NOMEM         \
+                                                                    : GEEK_ERR_CUDA,         \
+                             "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),         \
+                             __FILE__, __LINE__);                                            \
+    } while (0)
+
+#define GK_TRY(expr)                                                                         \
+    do {                                                                                     \
+        geek_status s_ = (expr);                                                             \
+        if (s_ != GEEK_OK) return s_;                                                        \
+    } while (0)
+
+#define GK_LAUNCH(ctx) GK_CUDA(ctx, cudaGetLastError())
+
+// Stream-ordered scratch owned by one API call; freed (stream-ordered) when
+// the call returns.
+struct Scratch {
+    geek_ctx *ctx;
+    cudaStream_t st;
+    std::vector<void *> ptrs;
+    Scratch(geek_ctx *c, cudaStream_t s) : ctx(c), st(s) {}
+    ~Scratch() {
+        for (void *p : ptrs) cudaFreeAsync(p, st);
+    }
+    template <class T>
+    geek_status alloc(T **out, size_t count) {
+        void *p = nullptr;
+        size_t bytes = count * sizeof(T);
+        if (bytes == 0) bytes = 16;
+        cudaError_t e = cudaMallocAsync(&p, bytes, st);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(ctx, GEEK_ERR_NOMEM, "device allocation of %zu bytes failed: %s", bytes,
+                             cudaGetErrorString(e));
+        }
+        ptrs.push_back(p);
+        *out = (T *)p;
+        return GEEK_OK;
+    }
+    // hands the allocation to the caller (it will not be freed here)
+    void release(void *p) {
+        for (auto &q : ptrs)
+            if (q == p) q = nullptr;
+    }
+};
+
+// Device buffer owned by a result handle.
+template <class T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+};
+
+static inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+static inline int bit_length_u64(uint64_t v) {
+    int b = 0;
+    while (v) {
+        b++;
+        v >>= 1;
+    }
+    return b;
+}
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+
+// Multiply-add-shift hash standing in for MinHash's random permutation
+// (Eq. 2): floor(((A*x + B) mod 2^64) / 2^32), computed from 32-bit halves:
+// the low 64 bits of A*x equal lo32(A)*x + (hi32(A)*x mod 2^32) * 2^32.
+__device__ __forceinline__ uint32_t mh_hash32(uint64_t A, uint64_t B, uint32_t x) {
+    uint64_t t = (uint64_t)(uint32_t)A * (uint64_t)x + B;
+    uint32_t hi = (uint32_t)(t >> 32) + (uint32_t)(A >> 32) * x;
+    return hi;
+}
+
+// ---------------------------------------------------------------------------
+// Internal building blocks (implemented in the .cu files)
+// ---------------------------------------------------------------------------
+
+// Stable LSD radix sort of S segments of m elements each.  Keys are up to
+// 128 bits: key_lo holds bits 0..63, key_hi (may be null when nbits <= 64)
+// bits 64..127.  vals (may be null) moves with the keys.  Only bits
+// [0, nbits) are examined.  On return the sorted data is in the buffers
+// pointed to by *key_lo / *key_hi / *vals (which may have been swapped with
+// internal buffers allocated from `scr`).
+geek_status radix_sort_segments(geek_ctx *ctx, Scratch &scr, int S, int64_t m, uint64_t **key_lo,
+                                uint64_t **key_hi, uint32_t **vals, int nbits, cudaStream_t st);
+
+// Run detection over S segments of m sorted keys: starts flagged where the
+// key differs from its predecessor in the segment.  Produces
+//   rank[p]         (may be null)  run index of position p within its segment
+//   run_start[s*(m+1) + r]         position of run r in segment s (r < runs[s]),
+//                                  and run_start[s*(m+1) + runs[s]] = m
+//   runs[s]                        runs in segment s (device)
+geek_status segment_runs(geek_ctx *ctx, Scratch &scr, int S, int64_t m, const uint64_t *key_lo,
+                         const uint64_t *key_hi, int32_t *rank, int64_t *run_start, int64_t *runs,
+                         cudaStream_t st);
+
+// Exclusive prefix sum of n int64 values (in place allowed); total -> *total_dev.
+geek_status exclusive_scan_i64(geek_ctx *ctx, Scratch &scr, const int64_t *in, int64_t *out,
+                               int64_t n, int64_t *total_dev, cudaStream_t st);
+
+// iota fill
+void launch_iota_u32(uint32_t *v, int64_t n, int64_t period, cudaStream_t st);

@@ -1,0 +1,553 @@
+// Data transformation kernels (Sect. 3.1): dense E2LSH / sign projections
+// with an FP64 boundary recheck, MinHash of sets and of categorical tokens
+// (Eq. 2), and the order-preserving packing of each table's K-tuple into a
+// 64/128-bit sort key.
+#include "common.cuh"
+#include "internal.cuh"
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// FP32 SIMT projection P = X A^T with the E2LSH / SRP epilogue.
+//
+// Rigorous window.  For one element, v = a.x is the exact real dot product,
+// p its FP32 value accumulated with FMA in any order, s64 the FP64 reference
+// (products exact, sequential sum).  |p - v| <= gamma_d * sum|a_j x_j| and
+// |s64 - v| <= d 2^-53 sum|a_j x_j|, and sum|a_j x_j| <= |a| |x| (Cauchy-
+// Schwarz), so s64 lies within E = (gamma_d + d 2^-53) |a| |x| of p.  The
+// reference code s -> floor(rn(rn(s + b) / w)) is monotone in s, so when the
+// whole interval maps into one integer cell the code is certain; otherwise
+// the element goes to the FP64 recheck list.  The cell test itself runs in
+// FP32 with its own rounding terms added to the window.
+// ---------------------------------------------------------------------------
+constexpr int PJ_KC = 32;       // d-chunk staged in shared memory
+constexpr int PJ_FPT = 8;       // functions per thread
+constexpr int PJ_RPT = 8;       // rows per thread
+constexpr int PJ_MAXT = 256;    // threads per block (upper bound)
+
+struct ProjArgs {
+    const float *x;
+    int64_t ldx;
+    int64_t n;
+    int d;
+    int F, FPAD, FG, RG;  // functions, padded to 8, function groups, row groups
+    const float *a;       // F x d
+    const float *b;       // F
+    const float *anorm;   // F
+    float w, inv_w;
+    int srp;
+    int32_t *codes;       // n x F
+    uint64_t *flags;      // (row << 16 | f)
+    unsigned long long *n_flags;
+    int64_t flag_cap;
+    int *fmin, *fmax;     // F
+};
+
+__global__ void __launch_bounds__(PJ_MAXT) k_project_fp32(ProjArgs A) {
+    extern __shared__ float sm[];
+    const int TR = A.RG * PJ_RPT;
+    float *xs = sm;                       // [PJ_KC][TR]
+    float *as = sm + PJ_KC * TR;          // [PJ_KC][FPAD]
+    __shared__ int smin[512], smax[512];  // F <= 512 checked on the host
+    const int t = threadIdx.x;
+    const int nthr = A.FG * A.RG;
+    const int fg = t % A.FG, rg = t / A.FG;
+    const bool active = t < nthr;
+    const int64_t row0 = (int64_t)blockIdx.x * TR;
+    for (int f = t; f < A.F; f += blockDim.x) {
+        smin[f] = INT32_MAX;
+        smax[f] = INT32_MIN;
+    }
+    float acc[PJ_RPT][PJ_FPT];
+    float xsq[PJ_RPT];
+#pragma unroll
+    for (int r = 0; r < PJ_RPT; r++) {
+        xsq[r] = 0.f;
+#pragma unroll
+        for (int c = 0; c < PJ_FPT; c++) acc[r][c] = 0.f;
+    }
+    for (int k0 = 0; k0 < A.d; k0 += PJ_KC) {
+        __syncthreads();
+        // stage X chunk transposed: xs[kk][r]
+        for (int e = t; e < TR * PJ_KC; e += blockDim.x) {
+            int r = e / PJ_KC, kk = e % PJ_KC;
+            int64_t row = row0 + r;
+            float v = 0.f;
+            if (row < A.n && k0 + kk < A.d) v = A.x[row * A.ldx + k0 + kk];
+            xs[kk * TR + r] = v;
+        }
+        for (int e = t; e < A.FPAD * PJ_KC; e += blockDim.x) {
+            int f = e / PJ_KC, kk = e % PJ_KC;
+            float v = 0.f;
+            if (f < A.F && k0 + kk < A.d) v = A.a[(int64_t)f * A.d + k0 + kk];
+            as[kk * A.FPAD + f] = v;
+        }
+        __syncthreads();
+        if (active) {
+            const int kmax = min(PJ_KC, A.d - k0);
+            for (int kk = 0; kk < kmax; kk++) {
+                const float4 x0 = *reinterpret_cast<const float4 *>(&xs[kk * TR + rg * PJ_RPT]);
+                const float4 x1 = *reinterpret_cast<const float4 *>(&xs[kk * TR + rg * PJ_RPT + 4]);
+                const float4 a0 = *reinterpret_cast<const float4 *>(&as[kk * A.FPAD + fg * PJ_FPT]);
+                const float4 a1 = *reinterpret_cast<const float4 *>(&as[kk * A.FPAD + fg * PJ_FPT + 4]);
+                const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+                const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+                for (int r = 0; r < PJ_RPT; r++) {
+#pragma unroll
+                    for (int c = 0; c < PJ_FPT; c++) acc[r][c] = fmaf(xv[r], av[c], acc[r][c]);
+                    xsq[r] = fmaf(xv[r], xv[r], xsq[r]);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    unsigned nfl = 0;
+    uint64_t flagmask = 0;  // bit r*8 + c: element (row r, function c) is uncertain
+    if (active) {
+        const float gam = (float)A.d * 6.0e-8f;  // >= gamma_d(fp32) + d 2^-53, norms' own error
+        int lmin[PJ_FPT], lmax[PJ_FPT];
+#pragma unroll
+        for (int c = 0; c < PJ_FPT; c++) {
+            lmin[c] = INT32_MAX;
+            lmax[c] = INT32_MIN;
+        }
+#pragma unroll
+        for (int r = 0; r < PJ_RPT; r++) {
+            const int64_t row = row0 + rg * PJ_RPT + r;
+            if (row >= A.n) continue;
+            const float xn = sqrtf(xsq[r]) * 1.0001f;
+            int32_t out[PJ_FPT];
+#pragma unroll
+            for (int c = 0; c < PJ_FPT; c++) {
+                const int f = fg * PJ_FPT + c;
+                out[c] = 0;
+                if (f >= A.F) continue;
+                const float p = acc[r][c];
+                const float E = gam * A.anorm[f] * xn + 1e-30f;
+                int code;
+                bool sure;
+                if (A.srp) {
+                    // s64 in [p - E, p + E]; FP32 subtraction slack 2^-23 |p|
+                    const float Es = E + fabsf(p) * 1.2e-7f;
+                    code = p >= 0.f ? 1 : 0;
+                    sure = (p - Es > 0.f) || (p + Es < 0.f);
+                } else {
+                    const float bb = A.b[f];
+                    const float tt = (p + bb) * A.inv_w;
+                    // window in t-space: model error E/w plus rounding of
+                    // p + b, of * (1/w) and of the comparisons (4 ulps)
+                    const float Et = (E + (fabsf(p) + fabsf(bb) + E) * 2.5e-7f) * A.inv_w + fabsf(tt) * 2.5e-7f;
+                    const float c0 = floorf(tt);
+                    code = fabsf(tt) < 2.0e9f ? (int)c0 : 0;
+                    sure = (tt - Et >= c0) && (tt + Et < c0 + 1.f) && fabsf(tt) < 2.0e9f;
+                }
+                out[c] = code;
+                if (!sure) flagmask |= 1ull << (r * PJ_FPT + c);
+                lmin[c] = min(lmin[c], code);
+                lmax[c] = max(lmax[c], code);
+            }
+            int32_t *dst = A.codes + row * A.F + fg * PJ_FPT;
+            if (fg * PJ_FPT + PJ_FPT <= A.F && (A.F % 4) == 0) {
+                reinterpret_cast<int4 *>(dst)[0] = make_int4(out[0], out[1], out[2], out[3]);
+                reinterpret_cast<int4 *>(dst)[1] = make_int4(out[4], out[5], out[6], out[7]);
+            } else {
+                for (int c = 0; c < PJ_FPT; c++)
+                    if (fg * PJ_FPT + c < A.F) dst[c] = out[c];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < PJ_FPT; c++) {
+            const int f = fg * PJ_FPT + c;
+            if (f < A.F && lmin[c] <= lmax[c]) {
+                atomicMin(&smin[f], lmin[c]);
+                atomicMax(&smax[f], lmax[c]);
+            }
+        }
+        nfl = __popcll(flagmask);
+    }
+    // one global atomic per block for the flag list
+    __shared__ unsigned s_tot;
+    __shared__ unsigned long long s_base;
+    __shared__ unsigned s_wsum[PJ_MAXT / 32];
+    {
+        const int lane = t & 31, warp = t >> 5;
+        unsigned x = nfl;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_wsum[warp] = x;
+        __syncthreads();
+        if (t == 0) {
+            unsigned run = 0;
+            for (int w = 0; w < (int)(blockDim.x + 31) / 32; w++) {
+                unsigned v = s_wsum[w];
+                s_wsum[w] = run;
+                run += v;
+            }
+            s_tot = run;
+            s_base = run ? atomicAdd(A.n_flags, (unsigned long long)run) : 0ull;
+        }
+        __syncthreads();
+        unsigned long long pos = s_base + s_wsum[warp] + x - nfl;
+        while (flagmask) {
+            const int bit = __ffsll(flagmask) - 1;
+            flagmask &= flagmask - 1;
+            const int64_t row = row0 + rg * PJ_RPT + bit / PJ_FPT;
+            const int f = fg * PJ_FPT + bit % PJ_FPT;
+            if ((int64_t)pos < A.flag_cap) A.flags[pos] = ((uint64_t)row << 16) | (uint64_t)f;
+            pos++;
+        }
+    }
+    __syncthreads();
+    for (int f = t; f < A.F; f += blockDim.x) {
+        if (smin[f] != INT32_MAX) {
+            atomicMin(&A.fmin[f], smin[f]);
+            atomicMax(&A.fmax[f], smax[f]);
+        }
+    }
+}
+
+__global__ void k_row_norms(const float *__restrict__ a, int F, int d, float *__restrict__ out) {
+    int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= F) return;
+    float s = 0.f;
+    for (int j = 0; j < d; j++) s = fmaf(a[(int64_t)f * d + j], a[(int64_t)f * d + j], s);
+    out[f] = sqrtf(s) * 1.0001f;
+}
+
+// FP64 recheck of flagged elements with the reference sequence: products of
+// the float inputs (exact in FP64), summed in j order, then (s + b) / w,
+// each step rounded to nearest; no fused multiply-add.
+__global__ void k_recheck_fp64(const float *__restrict__ x, int64_t ldx, int d,
+                               const float *__restrict__ a, const float *__restrict__ b, double w,
+                               int srp, int F, const uint64_t *__restrict__ flags,
+                               const unsigned long long *__restrict__ n_flags, int64_t cap,
+                               int32_t *__restrict__ codes, int *__restrict__ fmin,
+                               int *__restrict__ fmax, int *__restrict__ status) {
+    const int64_t nf = min((int64_t)*n_flags, cap);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nf;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t e = flags[q];
+        const int64_t row = (int64_t)(e >> 16);
+        const int f = (int)(e & 0xFFFF);
+        const float *xr = x + row * ldx;
+        const float *ar = a + (int64_t)f * d;
+        double s = 0.0;
+        for (int j = 0; j < d; j++) s = __dadd_rn(s, __dmul_rn((double)ar[j], (double)xr[j]));
+        int code;
+        if (srp) {
+            code = s >= 0.0 ? 1 : 0;
+        } else {
+            const double t = __ddiv_rn(__dadd_rn(s, (double)b[f]), w);
+            const double fl = floor(t);
+            if (!(fl >= -2147483648.0 && fl <= 2147483647.0)) {
+                atomicExch(status, (int)GEEK_ERR_OVERFLOW);
+                continue;
+            }
+            code = (int)fl;
+        }
+        codes[row * F + f] = code;
+        atomicMin(&fmin[f], code);
+        atomicMax(&fmax[f], code);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// MinHash (Eq. 2): warp per set, lane over functions, items broadcast by
+// shuffles; every lane keeps FPL running minima.
+// ---------------------------------------------------------------------------
+template <int FPL, bool FIXED>
+__global__ void __launch_bounds__(256) k_minhash(int64_t n, const int64_t *__restrict__ off,
+                                                 int row_len, const uint32_t *__restrict__ items,
+                                                 int F, const uint64_t *__restrict__ A,
+                                                 const uint64_t *__restrict__ B,
+                                                 uint32_t *__restrict__ out, int out_ld) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    uint64_t ca[FPL], cb[FPL];
+#pragma unroll
+    for (int q = 0; q < FPL; q++) {
+        int f = lane + 32 * q;
+        ca[q] = f < F ? A[f] : 0;
+        cb[q] = f < F ? B[f] : 0;
+    }
+    for (int64_t i = warp; i < n; i += nwarps) {
+        int64_t s, e;
+        if (FIXED) {
+            s = i * row_len;
+            e = s + row_len;
+        } else {
+            s = off[i];
+            e = off[i + 1];
+        }
+        uint32_t m[FPL];
+#pragma unroll
+        for (int q = 0; q < FPL; q++) m[q] = 0xFFFFFFFFu;
+        for (int64_t base = s; base < e; base += 32) {
+            const int cnt = (int)min((int64_t)32, e - base);
+            const uint32_t mine = lane < cnt ? items[base + lane] : 0u;
+            for (int j = 0; j < cnt; j++) {
+                const uint32_t v = __shfl_sync(0xffffffffu, mine, j);
+#pragma unroll
+                for (int q = 0; q < FPL; q++) m[q] = min(m[q], mh_hash32(ca[q], cb[q], v));
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < FPL; q++) {
+            int f = lane + 32 * q;
+            if (f < F) out[i * out_ld + f] = m[q];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Key layout and packing.
+// ---------------------------------------------------------------------------
+// One block: per function bit width of (max - min); per table total; status.
+__global__ void k_key_layout(const int *__restrict__ fmin, const int *__restrict__ fmax, int L,
+                             int K1, int K2, int *__restrict__ bits, int *__restrict__ tbits,
+                             int *__restrict__ status) {
+    for (int l = threadIdx.x; l < L; l += blockDim.x) {
+        int tot = 0;
+        for (int k = 0; k < K1; k++) {
+            int f = l * K1 + k;
+            uint32_t range = fmin[f] <= fmax[f] ? (uint32_t)((int64_t)fmax[f] - (int64_t)fmin[f]) : 0u;
+            int bl = 32 - __clz(range);
+            bits[f] = bl;
+            tot += bl;
+        }
+        tot += 32 * K2;
+        tbits[l] = tot;
+        if (tot > 128) atomicExch(status, (int)GEEK_ERR_OVERFLOW);
+    }
+}
+
+__device__ __forceinline__ void shl_or(uint64_t &hi, uint64_t &lo, int b, uint64_t v) {
+    if (b == 0) return;
+    hi = (hi << b) | (lo >> (64 - b));
+    lo = (lo << b) | v;
+}
+
+// key of table l for object i: fields codes[l*K1+k] - min (bits[f] wide),
+// then K2 MinHash values (32 bits each), the first field most significant.
+__global__ void k_pack_keys(int64_t n, int L, const int32_t *__restrict__ codes, int F1, int K1,
+                            const int *__restrict__ fmin, const int *__restrict__ bits,
+                            const uint32_t *__restrict__ mh, int F2, int K2,
+                            uint64_t *__restrict__ klo, uint64_t *__restrict__ khi) {
+    const int64_t total = n * L;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e % n;
+        const int l = (int)(e / n);
+        uint64_t hi = 0, lo = 0;
+        for (int k = 0; k < K1; k++) {
+            const int f = l * K1 + k;
+            const uint32_t v = (uint32_t)((int64_t)codes[i * F1 + f] - (int64_t)fmin[f]);
+            shl_or(hi, lo, bits[f], v);
+        }
+        for (int k = 0; k < K2; k++) shl_or(hi, lo, 32, mh[i * F2 + l * K2 + k]);
+        klo[e] = lo;
+        if (khi) khi[e] = hi;
+    }
+}
+
+__global__ void k_scatter_rank(int64_t n, int L, const uint32_t *__restrict__ ids,
+                               const int32_t *__restrict__ rank, int32_t *__restrict__ obj_bucket) {
+    const int64_t total = n * L;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t l = e / n;
+        obj_bucket[l * n + ids[e]] = rank[e];
+    }
+}
+
+// global bucket offsets: boff[base[l] + r] = l*n + run_start[l][r]
+__global__ void k_bucket_off(int64_t n, int L, const int64_t *__restrict__ run_start,
+                             const int64_t *__restrict__ table_base, const int64_t *__restrict__ nb,
+                             int64_t *__restrict__ boff, int64_t NB) {
+    const int l = blockIdx.y;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nb[l];
+         r += (int64_t)gridDim.x * blockDim.x)
+        boff[table_base[l] + r] = (int64_t)l * n + run_start[(int64_t)l * (n + 1) + r];
+    if (l == 0 && blockIdx.x == 0 && threadIdx.x == 0) boff[NB] = (int64_t)L * n;
+}
+
+__global__ void k_fill_i32(int *p, int n, int v) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+}  // namespace
+
+int grid_for(int64_t work, int threads, int num_sms) {
+    int64_t g = ceil_div(work, threads);
+    int64_t cap = (int64_t)num_sms * 32;
+    return (int)std::max<int64_t>(1, std::min(g, cap));
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+geek_status project_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ldx, int64_t n,
+                          int d, const float *a, const float *b, int F, double w, int srp,
+                          int32_t *codes, int *fmin, int *fmax, int64_t *n_flagged,
+                          cudaStream_t st) {
+    if (F > 512) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "more than 512 projections");
+    if (d > 100000) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "d > 100000");
+    float *anorm;
+    GK_TRY(scr.alloc(&anorm, F));
+    k_row_norms<<<(F + 127) / 128, 128, 0, st>>>(a, F, d, anorm);
+    k_fill_i32<<<(F + 255) / 256, 256, 0, st>>>(fmin, F, INT32_MAX);
+    k_fill_i32<<<(F + 255) / 256, 256, 0, st>>>(fmax, F, INT32_MIN);
+    GK_LAUNCH(ctx);
+    if (n == 0) {
+        *n_flagged = 0;
+        return GEEK_OK;
+    }
+    ProjArgs A{};
+    A.x = x; A.ldx = ldx; A.n = n; A.d = d; A.F = F;
+    A.FPAD = (int)ceil_div(F, PJ_FPT) * PJ_FPT;
+    A.FG = A.FPAD / PJ_FPT;
+    A.RG = std::max(1, PJ_MAXT / A.FG);
+    A.a = a; A.b = b; A.anorm = anorm;
+    A.w = (float)w; A.inv_w = (float)(1.0 / w);
+    // 1/w must be exact for the FP32 cell test's error model to hold as
+    // written; otherwise widen it by one more rounding.
+    A.srp = srp; A.codes = codes;
+    A.fmin = fmin; A.fmax = fmax;
+    const int TR = A.RG * PJ_RPT;
+    const int threads = (int)ceil_div(A.FG * A.RG, 32) * 32;  // whole warps
+    const size_t smem = (size_t)PJ_KC * (TR + A.FPAD) * sizeof(float);
+    if (smem > 200 * 1024) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "projection tile too large");
+    GK_CUDA(ctx, cudaFuncSetAttribute(k_project_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    unsigned long long *cnt;
+    GK_TRY(scr.alloc(&cnt, 1));
+    int *status;
+    GK_TRY(scr.alloc(&status, 1));
+    GK_CUDA(ctx, cudaMemsetAsync(status, 0, sizeof(int), st));
+    int64_t cap = std::max<int64_t>(1 << 20, n * F / 16);
+    for (int attempt = 0; attempt < 2; attempt++) {
+        uint64_t *flags;
+        GK_TRY(scr.alloc(&flags, cap));
+        GK_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
+        A.flags = flags; A.n_flags = cnt; A.flag_cap = cap;
+        const int64_t blocks = ceil_div(n, TR);
+        k_project_fp32<<<(unsigned)blocks, threads, smem, st>>>(A);
+        GK_LAUNCH(ctx);
+        unsigned long long h_cnt = 0;
+        GK_CUDA(ctx, cudaMemcpyAsync(&h_cnt, cnt, sizeof h_cnt, cudaMemcpyDeviceToHost, st));
+        GK_CUDA(ctx, cudaStreamSynchronize(st));
+        if ((int64_t)h_cnt > cap) {  // list overflowed: rerun with the exact size
+            cap = (int64_t)h_cnt;
+            continue;
+        }
+        *n_flagged = (int64_t)h_cnt;
+        if (h_cnt) {
+            k_recheck_fp64<<<grid_for((int64_t)h_cnt, 128, ctx->num_sms), 128, 0, st>>>(
+                x, ldx, d, a, b, w, srp, F, flags, cnt, cap, codes, fmin, fmax, status);
+            GK_LAUNCH(ctx);
+        }
+        int h_status = 0;
+        GK_CUDA(ctx, cudaMemcpyAsync(&h_status, status, sizeof h_status, cudaMemcpyDeviceToHost, st));
+        GK_CUDA(ctx, cudaStreamSynchronize(st));
+        if (h_status) return set_error(ctx, (geek_status)h_status, "E2LSH code outside int32");
+        return GEEK_OK;
+    }
+    return set_error(ctx, GEEK_ERR_CUDA, "projection flag list did not converge");
+}
+
+geek_status minhash_rows(geek_ctx *ctx, int64_t n, const int64_t *off, int row_len,
+                         const uint32_t *items, int F, const uint64_t *A, const uint64_t *B,
+                         uint32_t *out, cudaStream_t st) {
+    if (n == 0) return GEEK_OK;
+    if (F > 256) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "more than 256 MinHash functions");
+    const int threads = 256;
+    const int blocks = grid_for(n * 32, threads, ctx->num_sms);
+    const bool fixed = off == nullptr;
+#define MH_LAUNCH(FPL)                                                                             \
+    do {                                                                                          \
+        if (fixed)                                                                                \
+            k_minhash<FPL, true><<<blocks, threads, 0, st>>>(n, off, row_len, items, F, A, B, out, F); \
+        else                                                                                      \
+            k_minhash<FPL, false><<<blocks, threads, 0, st>>>(n, off, row_len, items, F, A, B, out, F); \
+    } while (0)
+    if (F <= 32) MH_LAUNCH(1);
+    else if (F <= 64) MH_LAUNCH(2);
+    else if (F <= 128) MH_LAUNCH(4);
+    else MH_LAUNCH(8);
+#undef MH_LAUNCH
+    GK_LAUNCH(ctx);
+    return GEEK_OK;
+}
+
+geek_status key_layout(geek_ctx *ctx, Scratch &scr, const int *fmin, const int *fmax, int L, int K1,
+                       int K2, int *bits_dev, std::vector<int> &tbits, cudaStream_t st) {
+    int *tb, *status;
+    GK_TRY(scr.alloc(&tb, L));
+    GK_TRY(scr.alloc(&status, 1));
+    GK_CUDA(ctx, cudaMemsetAsync(status, 0, sizeof(int), st));
+    k_key_layout<<<1, 256, 0, st>>>(fmin, fmax, L, K1, K2, bits_dev, tb, status);
+    GK_LAUNCH(ctx);
+    tbits.assign(L, 0);
+    int h_status = 0;
+    GK_CUDA(ctx, cudaMemcpyAsync(tbits.data(), tb, sizeof(int) * L, cudaMemcpyDeviceToHost, st));
+    GK_CUDA(ctx, cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GK_CUDA(ctx, cudaStreamSynchronize(st));
+    if (h_status) return set_error(ctx, GEEK_ERR_OVERFLOW, "a table key needs more than 128 bits");
+    return GEEK_OK;
+}
+
+geek_status pack_keys(geek_ctx *ctx, int64_t n, int L, const int32_t *codes, int F1, int K1,
+                      const int *fmin, const int *bits, const uint32_t *mh, int F2, int K2,
+                      uint64_t *klo, uint64_t *khi, cudaStream_t st) {
+    if (n == 0) return GEEK_OK;
+    k_pack_keys<<<grid_for(n * L, 256, ctx->num_sms), 256, 0, st>>>(n, L, codes, F1, K1, fmin, bits, mh, F2, K2, klo, khi);
+    GK_LAUNCH(ctx);
+    return GEEK_OK;
+}
+
+geek_status group_tables(geek_ctx *ctx, Scratch &scr, int64_t n, int L, uint64_t *klo,
+                         uint64_t *khi, int nbits, uint32_t *ids, int32_t *obj_bucket,
+                         int64_t **boff_out, std::vector<int64_t> &nb, int64_t *NB_out,
+                         cudaStream_t st) {
+    launch_iota_u32(ids, n * L, n, st);
+    GK_LAUNCH(ctx);
+    GK_TRY(radix_sort_segments(ctx, scr, L, n, &klo, khi ? &khi : nullptr, &ids, nbits, st));
+    int32_t *rank;
+    int64_t *run_start, *runs;
+    GK_TRY(scr.alloc(&rank, (size_t)n * L));
+    GK_TRY(scr.alloc(&run_start, (size_t)(n + 1) * L));
+    GK_TRY(scr.alloc(&runs, L));
+    GK_TRY(segment_runs(ctx, scr, L, n, klo, nbits > 64 ? khi : nullptr, rank, run_start, runs, st));
+    if (n)
+        k_scatter_rank<<<grid_for(n * L, 256, ctx->num_sms), 256, 0, st>>>(n, L, ids, rank, obj_bucket);
+    GK_LAUNCH(ctx);
+    nb.assign(L, 0);
+    GK_CUDA(ctx, cudaMemcpyAsync(nb.data(), runs, sizeof(int64_t) * L, cudaMemcpyDeviceToHost, st));
+    GK_CUDA(ctx, cudaStreamSynchronize(st));
+    std::vector<int64_t> base(L, 0);
+    int64_t NB = 0;
+    for (int l = 0; l < L; l++) {
+        base[l] = NB;
+        NB += nb[l];
+    }
+    int64_t *d_base;
+    GK_TRY(scr.alloc(&d_base, L));
+    GK_CUDA(ctx, cudaMemcpyAsync(d_base, base.data(), sizeof(int64_t) * L, cudaMemcpyHostToDevice, st));
+    int64_t *boff;
+    cudaError_t e = cudaMallocAsync((void **)&boff, sizeof(int64_t) * (NB + 1), st);
+    if (e != cudaSuccess) return set_error(ctx, GEEK_ERR_NOMEM, "bucket offsets: %s", cudaGetErrorString(e));
+    int64_t maxnb = 1;
+    for (auto v : nb) maxnb = std::max(maxnb, v);
+    k_bucket_off<<<dim3((unsigned)std::min<int64_t>(ceil_div(maxnb, 256), 4096), L), 256, 0, st>>>(
+        n, L, run_start, d_base, runs, boff, NB);
+    GK_LAUNCH(ctx);
+    *boff_out = boff;
+    *NB_out = NB;
+    return GEEK_OK;
+}

@@ -1,0 +1,500 @@
+// SILK seeding (Sect. 3.2, Alg. 4) on the device.
+//
+// For each SILK table: the MinHash signature of every bucket (a bucket is a
+// set of object ids), bins = runs of equal signatures after a radix sort,
+// majority voting by sorting (bin, id) pairs and counting runs, the delta
+// filter, then compaction into a CSR multiset.  The near-duplicate removal
+// pass reuses the same machinery on the multiset, followed by a canonical
+// lexicographic sort and removal of exact duplicates.
+#include "internal.cuh"
+
+namespace {
+
+// signature key of set g under Ks functions (first function most
+// significant): Ks <= 2 fits the low word, Ks 3..4 use the high word too
+__global__ void k_set_sig(int64_t nsets, const int64_t *__restrict__ soff,
+                          const uint32_t *__restrict__ sids, int Ks, const uint64_t *__restrict__ A,
+                          const uint64_t *__restrict__ B, uint64_t *__restrict__ klo,
+                          uint64_t *__restrict__ khi, uint32_t *__restrict__ vals) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nsets;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t m[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+        uint64_t a[4], b[4];
+        for (int k = 0; k < Ks; k++) {
+            a[k] = A[k];
+            b[k] = B[k];
+        }
+        for (int64_t p = soff[g]; p < soff[g + 1]; p++) {
+            const uint32_t id = sids[p];
+            for (int k = 0; k < Ks; k++) m[k] = min(m[k], mh_hash32(a[k], b[k], id));
+        }
+        uint64_t hi = 0, lo = 0;
+        for (int k = 0; k < Ks; k++) {
+            hi = (hi << 32) | (lo >> 32);
+            lo = (lo << 32) | m[k];
+        }
+        klo[g] = lo;
+        if (khi) khi[g] = hi;
+        vals[g] = (uint32_t)g;
+    }
+}
+
+__device__ __forceinline__ int64_t bin_size(const int64_t *rs, int64_t r) { return rs[r + 1] - rs[r]; }
+
+// member count of each sorted position whose bin qualifies for a vote
+__global__ void k_vote_weights(int64_t m, const int32_t *__restrict__ rank,
+                               const int64_t *__restrict__ rs, const uint32_t *__restrict__ perm,
+                               const int64_t *__restrict__ soff, int64_t *__restrict__ w) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = rank[p];
+        const uint32_t g = perm[p];
+        w[p] = bin_size(rs, r) >= 2 ? soff[g + 1] - soff[g] : 0;
+    }
+}
+
+__global__ void k_vote_expand(int64_t m, const int32_t *__restrict__ rank,
+                              const uint32_t *__restrict__ perm, const int64_t *__restrict__ woff,
+                              const int64_t *__restrict__ w, const int64_t *__restrict__ soff,
+                              const uint32_t *__restrict__ sids, uint64_t *__restrict__ pairs) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        if (w[p] == 0) continue;
+        const uint64_t r = (uint64_t)rank[p];
+        const uint32_t g = perm[p];
+        int64_t o = woff[p];
+        for (int64_t q = soff[g]; q < soff[g + 1]; q++) pairs[o++] = (r << 32) | sids[q];
+    }
+}
+
+// one thread per (bin, id) run: keep when 2 * count > |bin|
+__global__ void k_vote_keep(const int64_t *__restrict__ nruns_dev, const int64_t *__restrict__ prs,
+                            const uint64_t *__restrict__ pairs, const int64_t *__restrict__ rs,
+                            int64_t *__restrict__ keep, int64_t *__restrict__ cnt) {
+    const int64_t nr = *nruns_dev;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nr;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t len = prs[r + 1] - prs[r];
+        const int64_t bin = (int64_t)(pairs[prs[r]] >> 32);
+        const bool k = 2 * len > bin_size(rs, bin);
+        keep[r] = k;
+        if (k) atomicAdd((unsigned long long *)&cnt[bin], 1ull);
+    }
+}
+
+// per bin: ok when it has >= 2 buckets and |C_shared| >= delta
+__global__ void k_bin_ok(int64_t nbins, const int64_t *__restrict__ rs, const int64_t *__restrict__ cnt,
+                         int delta, int64_t *__restrict__ ok, int64_t *__restrict__ len) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nbins;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        const bool o = bin_size(rs, b) >= 2 && cnt[b] >= delta;
+        ok[b] = o;
+        len[b] = o ? cnt[b] : 0;
+    }
+}
+
+__global__ void k_vote_sel(const int64_t *__restrict__ nruns_dev, const int64_t *__restrict__ prs,
+                           const uint64_t *__restrict__ pairs, const int64_t *__restrict__ keep,
+                           const int64_t *__restrict__ ok, int64_t *__restrict__ sel) {
+    const int64_t nr = *nruns_dev;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nr;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t bin = (int64_t)(pairs[prs[r]] >> 32);
+        sel[r] = keep[r] && ok[bin];
+    }
+}
+
+__global__ void k_vote_emit(const int64_t *__restrict__ nruns_dev, const int64_t *__restrict__ prs,
+                            const uint64_t *__restrict__ pairs, const int64_t *__restrict__ sel,
+                            const int64_t *__restrict__ pos, uint32_t *__restrict__ out_ids) {
+    const int64_t nr = *nruns_dev;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nr;
+         r += (int64_t)gridDim.x * blockDim.x)
+        if (sel[r]) out_ids[pos[r]] = (uint32_t)(pairs[prs[r]] & 0xFFFFFFFFu);
+}
+
+__global__ void k_compact_offsets(int64_t nbins, const int64_t *__restrict__ ok,
+                                  const int64_t *__restrict__ set_idx, const int64_t *__restrict__ boffs,
+                                  int64_t *__restrict__ out_off, const int64_t *__restrict__ nsets,
+                                  const int64_t *__restrict__ total) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nbins;
+         b += (int64_t)gridDim.x * blockDim.x)
+        if (ok[b]) out_off[set_idx[b]] = boffs[b];
+    if (blockIdx.x == 0 && threadIdx.x == 0) out_off[*nsets] = *total;
+}
+
+// set lengths of a list of set indices
+__global__ void k_gather_len(int64_t cnt, const int64_t *__restrict__ idx, const int64_t *__restrict__ soff,
+                             int64_t *__restrict__ len) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * blockDim.x)
+        len[i] = soff[idx[i] + 1] - soff[idx[i]];
+}
+
+__global__ void k_gather_ids(int64_t cnt, const int64_t *__restrict__ idx, const int64_t *__restrict__ soff,
+                             const uint32_t *__restrict__ sids, const int64_t *__restrict__ ooff,
+                             uint32_t *__restrict__ oids) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = idx[i];
+        int64_t o = ooff[i];
+        for (int64_t q = soff[s]; q < soff[s + 1]; q++) oids[o++] = sids[q];
+    }
+}
+
+__device__ int set_cmp(const uint32_t *ids, const int64_t *off, int64_t a, int64_t b) {
+    const int64_t na = off[a + 1] - off[a], nb = off[b + 1] - off[b];
+    const int64_t m = na < nb ? na : nb;
+    const uint32_t *pa = ids + off[a], *pb = ids + off[b];
+    for (int64_t i = 0; i < m; i++)
+        if (pa[i] != pb[i]) return pa[i] < pb[i] ? -1 : 1;
+    return (na > nb) - (na < nb);
+}
+
+// dedup bins: classify each bin of sets.  Singleton bins contribute their
+// set (kind 1); bins with >= 2 sets whose vote failed delta contribute their
+// canonically smallest member (kind 2).
+__global__ void k_dedup_pick(int64_t nbins, const int64_t *__restrict__ rs, const uint32_t *__restrict__ perm,
+                             const int64_t *__restrict__ ok, const int64_t *__restrict__ soff,
+                             const uint32_t *__restrict__ sids, int64_t *__restrict__ pick,
+                             int64_t *__restrict__ has) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nbins;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = rs[b], e = rs[b + 1];
+        if (e - s == 1) {
+            pick[b] = perm[s];
+            has[b] = 1;
+        } else if (!ok[b]) {
+            int64_t best = perm[s];
+            for (int64_t p = s + 1; p < e; p++)
+                if (set_cmp(sids, soff, perm[p], best) < 0) best = perm[p];
+            pick[b] = best;
+            has[b] = 1;
+        } else {
+            has[b] = 0;
+        }
+    }
+}
+
+__global__ void k_compact_idx(int64_t nb, const int64_t *__restrict__ has, const int64_t *__restrict__ pos,
+                              const int64_t *__restrict__ val, int64_t *__restrict__ out) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb;
+         b += (int64_t)gridDim.x * blockDim.x)
+        if (has[b]) out[pos[b]] = val[b];
+}
+
+// canonical order: 64-bit prefix key (first two members + 1, 0 if absent)
+__global__ void k_prefix_key(int64_t ns, const int64_t *__restrict__ soff, const uint32_t *__restrict__ sids,
+                             uint64_t *__restrict__ key, uint32_t *__restrict__ vals) {
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < ns;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t n = soff[s + 1] - soff[s];
+        const uint64_t a = n > 0 ? (uint64_t)sids[soff[s]] + 1 : 0;
+        const uint64_t b = n > 1 ? (uint64_t)sids[soff[s] + 1] + 1 : 0;
+        key[s] = (a << 32) | b;
+        vals[s] = (uint32_t)s;
+    }
+}
+
+// within each run of equal prefix keys, order by full comparison (ties by
+// position, so the order is total): final[run_start + rank] = set
+__global__ void k_prefix_fix(int64_t ns, const int32_t *__restrict__ rank, const int64_t *__restrict__ rs,
+                             const uint32_t *__restrict__ perm, const int64_t *__restrict__ soff,
+                             const uint32_t *__restrict__ sids, int64_t *__restrict__ order) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < ns;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = rank[p], s = rs[r], e = rs[r + 1];
+        int64_t c = 0;
+        for (int64_t q = s; q < e; q++) {
+            if (q == p) continue;
+            const int cmp = set_cmp(sids, soff, perm[q], perm[p]);
+            if (cmp < 0 || (cmp == 0 && q < p)) c++;
+        }
+        order[s + c] = perm[p];
+    }
+}
+
+__global__ void k_dup_flags(int64_t ns, const int64_t *__restrict__ order, const int64_t *__restrict__ soff,
+                            const uint32_t *__restrict__ sids, int64_t *__restrict__ keep) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < ns;
+         p += (int64_t)gridDim.x * blockDim.x)
+        keep[p] = p == 0 || set_cmp(sids, soff, order[p - 1], order[p]) != 0;
+}
+
+struct Csr {
+    int64_t n = 0;        // sets
+    int64_t nids = 0;     // members
+    int64_t *off = nullptr;
+    uint32_t *ids = nullptr;
+};
+
+int G(geek_ctx *ctx, int64_t work) { return grid_for(std::max<int64_t>(work, 1), 256, ctx->num_sms); }
+
+geek_status d2h_i64(geek_ctx *ctx, const int64_t *dev, int64_t *host, cudaStream_t st) {
+    GK_CUDA(ctx, cudaMemcpyAsync(host, dev, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    GK_CUDA(ctx, cudaStreamSynchronize(st));
+    return GEEK_OK;
+}
+
+// Group nsets sets into bins by their Ks-function MinHash signature.
+// Returns perm (set index per sorted position), rank (bin per position),
+// rs (bin starts, nbins + 1) and nbins.
+geek_status make_bins(geek_ctx *ctx, Scratch &scr, int64_t nsets, const int64_t *soff,
+                      const uint32_t *sids, int Ks, const uint64_t *A, const uint64_t *B,
+                      uint32_t **perm, int32_t **rank, int64_t **rs, int64_t *nbins, cudaStream_t st) {
+    uint64_t *klo, *khi = nullptr;
+    GK_TRY(scr.alloc(&klo, nsets));
+    if (Ks > 2) GK_TRY(scr.alloc(&khi, nsets));
+    GK_TRY(scr.alloc(perm, nsets));
+    k_set_sig<<<G(ctx, nsets), 256, 0, st>>>(nsets, soff, sids, Ks, A, B, klo, khi, *perm);
+    GK_LAUNCH(ctx);
+    GK_TRY(radix_sort_segments(ctx, scr, 1, nsets, &klo, khi ? &khi : nullptr, perm, 32 * Ks, st));
+    int64_t *runs;
+    GK_TRY(scr.alloc(rank, nsets));
+    GK_TRY(scr.alloc(rs, nsets + 1));
+    GK_TRY(scr.alloc(&runs, 1));
+    GK_TRY(segment_runs(ctx, scr, 1, nsets, klo, khi, *rank, *rs, runs, st));
+    GK_TRY(d2h_i64(ctx, runs, nbins, st));
+    return GEEK_OK;
+}
+
+// Majority vote of every bin holding >= 2 sets; bins whose C_shared has at
+// least delta objects are emitted (ascending bin order, ascending ids).
+// ok[b] tells which bins were emitted.
+geek_status vote_bins(geek_ctx *ctx, Scratch &scr, int64_t m, const uint32_t *perm, const int32_t *rank,
+                      const int64_t *rs, int64_t nbins, const int64_t *soff, const uint32_t *sids,
+                      int delta, Csr *out, int64_t **ok_out, cudaStream_t st) {
+    int64_t *w, *woff, *T_dev;
+    GK_TRY(scr.alloc(&w, m));
+    GK_TRY(scr.alloc(&woff, m));
+    GK_TRY(scr.alloc(&T_dev, 1));
+    k_vote_weights<<<G(ctx, m), 256, 0, st>>>(m, rank, rs, perm, soff, w);
+    GK_LAUNCH(ctx);
+    GK_TRY(exclusive_scan_i64(ctx, scr, w, woff, m, T_dev, st));
+    int64_t T = 0;
+    GK_TRY(d2h_i64(ctx, T_dev, &T, st));
+    int64_t *cnt, *ok, *len;
+    GK_TRY(scr.alloc(&cnt, nbins));
+    GK_TRY(scr.alloc(&ok, nbins));
+    GK_TRY(scr.alloc(&len, nbins));
+    GK_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(int64_t) * nbins, st));
+    *ok_out = ok;
+    out->n = 0;
+    out->nids = 0;
+    if (T == 0) {
+        GK_CUDA(ctx, cudaMemsetAsync(ok, 0, sizeof(int64_t) * nbins, st));
+        return GEEK_OK;
+    }
+    uint64_t *pairs;
+    GK_TRY(scr.alloc(&pairs, T));
+    k_vote_expand<<<G(ctx, m), 256, 0, st>>>(m, rank, perm, woff, w, soff, sids, pairs);
+    GK_LAUNCH(ctx);
+    const int nbits = 32 + bit_length_u64((uint64_t)nbins);
+    GK_TRY(radix_sort_segments(ctx, scr, 1, T, &pairs, nullptr, nullptr, nbits, st));
+    int64_t *prs, *nruns;
+    GK_TRY(scr.alloc(&prs, T + 1));
+    GK_TRY(scr.alloc(&nruns, 1));
+    GK_TRY(segment_runs(ctx, scr, 1, T, pairs, nullptr, nullptr, prs, nruns, st));
+    int64_t NR = 0;
+    GK_TRY(d2h_i64(ctx, nruns, &NR, st));
+    int64_t *keep, *sel, *pos, *total, *boffs, *set_idx, *nsets;
+    GK_TRY(scr.alloc(&keep, NR));
+    GK_TRY(scr.alloc(&sel, NR));
+    GK_TRY(scr.alloc(&pos, NR));
+    GK_TRY(scr.alloc(&total, 1));
+    GK_TRY(scr.alloc(&boffs, nbins));
+    GK_TRY(scr.alloc(&set_idx, nbins));
+    GK_TRY(scr.alloc(&nsets, 1));
+    k_vote_keep<<<G(ctx, NR), 256, 0, st>>>(nruns, prs, pairs, rs, keep, cnt);
+    k_bin_ok<<<G(ctx, nbins), 256, 0, st>>>(nbins, rs, cnt, delta, ok, len);
+    k_vote_sel<<<G(ctx, NR), 256, 0, st>>>(nruns, prs, pairs, keep, ok, sel);
+    GK_LAUNCH(ctx);
+    GK_TRY(exclusive_scan_i64(ctx, scr, sel, pos, NR, total, st));
+    GK_TRY(exclusive_scan_i64(ctx, scr, len, boffs, nbins, nullptr, st));
+    GK_TRY(exclusive_scan_i64(ctx, scr, ok, set_idx, nbins, nsets, st));
+    int64_t h_total = 0, h_nsets = 0;
+    GK_TRY(d2h_i64(ctx, total, &h_total, st));
+    GK_TRY(d2h_i64(ctx, nsets, &h_nsets, st));
+    out->n = h_nsets;
+    out->nids = h_total;
+    GK_TRY(scr.alloc(&out->off, h_nsets + 1));
+    GK_TRY(scr.alloc(&out->ids, std::max<int64_t>(1, h_total)));
+    k_vote_emit<<<G(ctx, NR), 256, 0, st>>>(nruns, prs, pairs, sel, pos, out->ids);
+    k_compact_offsets<<<G(ctx, nbins), 256, 0, st>>>(nbins, ok, set_idx, boffs, out->off, nsets, total);
+    GK_LAUNCH(ctx);
+    return GEEK_OK;
+}
+
+// gathers the listed sets (device index list) into a new CSR
+geek_status gather_sets(geek_ctx *ctx, Scratch &scr, int64_t cnt, const int64_t *idx,
+                        const int64_t *soff, const uint32_t *sids, Csr *out, cudaStream_t st) {
+    out->n = cnt;
+    int64_t *len, *tot;
+    GK_TRY(scr.alloc(&len, std::max<int64_t>(cnt, 1)));
+    GK_TRY(scr.alloc(&out->off, cnt + 1));
+    GK_TRY(scr.alloc(&tot, 1));
+    k_gather_len<<<G(ctx, cnt), 256, 0, st>>>(cnt, idx, soff, len);
+    GK_LAUNCH(ctx);
+    GK_TRY(exclusive_scan_i64(ctx, scr, len, out->off, cnt, tot, st));
+    GK_CUDA(ctx, cudaMemcpyAsync(out->off + cnt, tot, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+    GK_TRY(d2h_i64(ctx, tot, &out->nids, st));
+    GK_TRY(scr.alloc(&out->ids, std::max<int64_t>(1, out->nids)));
+    k_gather_ids<<<G(ctx, cnt), 256, 0, st>>>(cnt, idx, soff, sids, out->off, out->ids);
+    GK_LAUNCH(ctx);
+    return GEEK_OK;
+}
+
+// concatenation of CSR pieces
+geek_status concat_sets(geek_ctx *ctx, Scratch &scr, const std::vector<Csr> &parts, Csr *out,
+                        cudaStream_t st) {
+    int64_t n = 0, nids = 0;
+    for (auto &p : parts) {
+        n += p.n;
+        nids += p.nids;
+    }
+    out->n = n;
+    out->nids = nids;
+    GK_TRY(scr.alloc(&out->off, n + 1));
+    GK_TRY(scr.alloc(&out->ids, std::max<int64_t>(1, nids)));
+    // offsets: copy each part's offsets shifted by the running id count
+    std::vector<int64_t> h_off;
+    h_off.reserve(n + 1);
+    int64_t base = 0, ibase = 0;
+    for (auto &p : parts) {
+        if (p.n == 0) continue;
+        std::vector<int64_t> tmp(p.n + 1);
+        GK_CUDA(ctx, cudaMemcpyAsync(tmp.data(), p.off, sizeof(int64_t) * (p.n + 1), cudaMemcpyDeviceToHost, st));
+        GK_CUDA(ctx, cudaStreamSynchronize(st));
+        for (int64_t i = 0; i < p.n; i++) h_off.push_back(tmp[i] + ibase);
+        if (p.nids)
+            GK_CUDA(ctx, cudaMemcpyAsync(out->ids + ibase, p.ids, sizeof(uint32_t) * p.nids, cudaMemcpyDeviceToDevice, st));
+        ibase += p.nids;
+        base += p.n;
+    }
+    h_off.push_back(ibase);
+    GK_CUDA(ctx, cudaMemcpyAsync(out->off, h_off.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st));
+    GK_CUDA(ctx, cudaStreamSynchronize(st));
+    (void)base;
+    return GEEK_OK;
+}
+
+}  // namespace
+
+geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p, silk_seeds *out,
+                     cudaStream_t st) {
+    Scratch scr(ctx, st);
+    const int Ks = p->Ks, Ls = p->Ls, delta = p->delta;
+    const int64_t NB = b->NB;
+    std::vector<Csr> parts;
+    // ---- Alg. 4: Ls SILK tables over all buckets -------------------------
+    for (int t = 0; t < Ls && NB > 0; t++) {
+        Scratch tscr(ctx, st);  // per-table temporaries
+        uint32_t *perm;
+        int32_t *rank;
+        int64_t *rs, nbins = 0;
+        GK_TRY(make_bins(ctx, tscr, NB, b->boff, b->members, Ks, p->mh_a + (int64_t)t * Ks,
+                         p->mh_b + (int64_t)t * Ks, &perm, &rank, &rs, &nbins, st));
+        Csr c;
+        int64_t *ok;
+        GK_TRY(vote_bins(ctx, tscr, NB, perm, rank, rs, nbins, b->boff, b->members, delta, &c, &ok, st));
+        if (c.n) {
+            // move the table's C_shared sets into the outer scratch
+            Csr keep;
+            keep.n = c.n;
+            keep.nids = c.nids;
+            GK_TRY(scr.alloc(&keep.off, c.n + 1));
+            GK_TRY(scr.alloc(&keep.ids, std::max<int64_t>(1, c.nids)));
+            GK_CUDA(ctx, cudaMemcpyAsync(keep.off, c.off, sizeof(int64_t) * (c.n + 1), cudaMemcpyDeviceToDevice, st));
+            if (c.nids)
+                GK_CUDA(ctx, cudaMemcpyAsync(keep.ids, c.ids, sizeof(uint32_t) * c.nids, cudaMemcpyDeviceToDevice, st));
+            parts.push_back(keep);
+        }
+        GK_CUDA(ctx, cudaStreamSynchronize(st));
+    }
+    Csr C;
+    GK_TRY(concat_sets(ctx, scr, parts, &C, st));
+    out->n_multiset = C.n;
+
+    // ---- near-duplicate removal: one more table over C --------------------
+    std::vector<Csr> dparts;
+    if (C.n > 0) {
+        uint32_t *perm;
+        int32_t *rank;
+        int64_t *rs, nbins = 0;
+        GK_TRY(make_bins(ctx, scr, C.n, C.off, C.ids, Ks, p->dd_a, p->dd_b, &perm, &rank, &rs, &nbins, st));
+        Csr V;
+        int64_t *ok;
+        GK_TRY(vote_bins(ctx, scr, C.n, perm, rank, rs, nbins, C.off, C.ids, delta, &V, &ok, st));
+        if (V.n) dparts.push_back(V);
+        int64_t *pick, *has, *pos, *npick;
+        GK_TRY(scr.alloc(&pick, nbins));
+        GK_TRY(scr.alloc(&has, nbins));
+        GK_TRY(scr.alloc(&pos, nbins));
+        GK_TRY(scr.alloc(&npick, 1));
+        k_dedup_pick<<<G(ctx, nbins), 256, 0, st>>>(nbins, rs, perm, ok, C.off, C.ids, pick, has);
+        GK_LAUNCH(ctx);
+        GK_TRY(exclusive_scan_i64(ctx, scr, has, pos, nbins, npick, st));
+        int64_t hp = 0;
+        GK_TRY(d2h_i64(ctx, npick, &hp, st));
+        if (hp) {
+            int64_t *idx;
+            GK_TRY(scr.alloc(&idx, hp));
+            k_compact_idx<<<G(ctx, nbins), 256, 0, st>>>(nbins, has, pos, pick, idx);
+            GK_LAUNCH(ctx);
+            Csr P;
+            GK_TRY(gather_sets(ctx, scr, hp, idx, C.off, C.ids, &P, st));
+            dparts.push_back(P);
+        }
+    }
+    Csr D;
+    GK_TRY(concat_sets(ctx, scr, dparts, &D, st));
+
+    // ---- canonical order, exact duplicates out -----------------------------
+    out->k = 0;
+    out->n_ids = 0;
+    if (D.n == 0) {
+        GK_CUDA(ctx, cudaMalloc((void **)&out->off, sizeof(int64_t)));
+        GK_CUDA(ctx, cudaMemsetAsync(out->off, 0, sizeof(int64_t), st));
+        GK_CUDA(ctx, cudaStreamSynchronize(st));
+        return GEEK_OK;
+    }
+    uint64_t *key;
+    uint32_t *perm;
+    GK_TRY(scr.alloc(&key, D.n));
+    GK_TRY(scr.alloc(&perm, D.n));
+    k_prefix_key<<<G(ctx, D.n), 256, 0, st>>>(D.n, D.off, D.ids, key, perm);
+    GK_LAUNCH(ctx);
+    GK_TRY(radix_sort_segments(ctx, scr, 1, D.n, &key, nullptr, &perm, 64, st));
+    int32_t *rank;
+    int64_t *rs, *nr, *order, *keep, *kpos, *kt;
+    GK_TRY(scr.alloc(&rank, D.n));
+    GK_TRY(scr.alloc(&rs, D.n + 1));
+    GK_TRY(scr.alloc(&nr, 1));
+    GK_TRY(segment_runs(ctx, scr, 1, D.n, key, nullptr, rank, rs, nr, st));
+    GK_TRY(scr.alloc(&order, D.n));
+    GK_TRY(scr.alloc(&keep, D.n));
+    GK_TRY(scr.alloc(&kpos, D.n));
+    GK_TRY(scr.alloc(&kt, 1));
+    k_prefix_fix<<<G(ctx, D.n), 256, 0, st>>>(D.n, rank, rs, perm, D.off, D.ids, order);
+    k_dup_flags<<<G(ctx, D.n), 256, 0, st>>>(D.n, order, D.off, D.ids, keep);
+    GK_LAUNCH(ctx);
+    GK_TRY(exclusive_scan_i64(ctx, scr, keep, kpos, D.n, kt, st));
+    int64_t k = 0;
+    GK_TRY(d2h_i64(ctx, kt, &k, st));
+    int64_t *sel;
+    GK_TRY(scr.alloc(&sel, k));
+    k_compact_idx<<<G(ctx, D.n), 256, 0, st>>>(D.n, keep, kpos, order, sel);
+    GK_LAUNCH(ctx);
+    Csr E;
+    GK_TRY(gather_sets(ctx, scr, k, sel, D.off, D.ids, &E, st));
+    // hand the final CSR to the handle (persistent allocations)
+    GK_CUDA(ctx, cudaMalloc((void **)&out->off, sizeof(int64_t) * (k + 1)));
+    GK_CUDA(ctx, cudaMalloc((void **)&out->ids, sizeof(int32_t) * std::max<int64_t>(1, E.nids)));
+    GK_CUDA(ctx, cudaMemcpyAsync(out->off, E.off, sizeof(int64_t) * (k + 1), cudaMemcpyDeviceToDevice, st));
+    if (E.nids)
+        GK_CUDA(ctx, cudaMemcpyAsync(out->ids, E.ids, sizeof(uint32_t) * E.nids, cudaMemcpyDeviceToDevice, st));
+    GK_CUDA(ctx, cudaStreamSynchronize(st));
+    out->k = k;
+    out->n_ids = E.nids;
+    return GEEK_OK;
+}

@@ -1,0 +1,486 @@
+// Dense one-pass assignment on the 5th-generation tensor cores (tcgen05).
+//
+// S = X C^T in BF16 with FP32 accumulation in tensor memory, fused with a
+// running arg-min epilogue over centre tiles; the FP64 decision of the
+// exact argmin (Eq. 1) is left to objects whose best and second-best
+// approximate values are closer than the rigorous error window.
+//
+// Persistent kernel, one CTA per SM, 10 warps:
+//   warp 0     TMA producer: X row tiles (double buffered) and centre tiles
+//              (2-stage ring), 128-byte swizzled, K-major
+//   warp 1     MMA issuer: tcgen05.mma.cta_group::1.kind::f16, M=128, N=256,
+//              into one of two TMEM accumulators (2 x 256 columns)
+//   warps 2-9  epilogue: tcgen05.ld of the accumulator, d' = |c|^2 - 2 s,
+//              per-row best / second-best over the centres; each warp reads
+//              its TMEM lane quarter (warp % 4) and one half of the columns
+// Every mbarrier wait is bounded: on expiry the kernel records
+// GEEK_ERR_TIMEOUT, stops issuing work, drains its own copies and MMAs, frees
+// its tensor memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cfloat>
+
+#include "internal.cuh"
+
+namespace {
+
+constexpr int TC_M = 128;
+constexpr int TC_N = 256;
+constexpr int TC_KB = 64;  // bf16 elements per 128-byte swizzle row
+constexpr int TC_EPI_WARPS = 8;
+constexpr int TC_THREADS = 32 * (2 + TC_EPI_WARPS);
+constexpr uint32_t TC_TMEM_COLS = 512;
+constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s per wait
+
+struct TcArgs {
+    CUtensorMap tmA;  // Xb: {Kp, n} bf16, box {64, 128}
+    CUtensorMap tmB;  // Cb: {Kp, kpad} bf16, box {64, 256}
+    const float *cn;  // kpad: |c|^2 (+inf for padding)
+    const float *xnorm;
+    int64_t n, k;
+    int64_t ntiles_r;
+    int ntiles_c;
+    int Kp, d;
+    float cmax;
+    int32_t *labels;
+    int32_t *flag_rows;
+    unsigned long long *n_flag;
+    int *err;
+};
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(su32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait.  Gives up (returns false) when another role already
+// recorded an error (unless `drain`), or after WAIT_NS of its own.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, bool drain = false) {
+    unsigned long long t0 = 0;
+    for (uint32_t it = 0;; it++) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 255) == 0) {
+            if (!drain && *(volatile int *)err) return false;
+            const unsigned long long t = gtimer();
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > WAIT_NS) {
+                atomicExch(err, (int)GEEK_ERR_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *tm, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"((uint64_t)tm), "r"(x), "r"(y), "r"(su32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// K-major operand, 128-byte swizzle: rows of 128 B, 8-row atoms of 1 KB.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;             // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;             // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;             // 128-byte swizzle
+    return d;
+}
+
+// instruction descriptor: kind::f16, A = B = BF16, D = F32, both K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtm, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(dtm),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Rigorous half-window of the BF16 path for one object:
+//   inputs rounded to bf16 (u_b = 2^-8):    2 (2 u_b + u_b^2) |x| cmax
+//   FP32 accumulation in the tensor core:   2 (d + 16) 2^-21 |x| cmax
+//   |c|^2 rounded to FP32 and the final FMA: u cmax^2 + u (2 |x| cmax (1 + 2 u_b) + cmax^2)
+//   the FP64 reference's own error:         (d + 3) 2^-53 (|x| + cmax)^2
+// times 1.01 for second-order terms.
+__device__ __forceinline__ float window_bf16(float xn, float cmax, int d) {
+    const float ub = 0.00390625f, u = 5.9604645e-8f;
+    const float xc = xn * cmax;
+    const float e = 2.f * (2.f * ub + ub * ub) * xc + 2.f * (float)(d + 16) * 4.76837158e-7f * xc +
+                    u * cmax * cmax + u * (2.f * xc * (1.f + 2.f * ub) + cmax * cmax);
+    const float s = xn + cmax;
+    const float e64 = (float)(d + 3) * 1.1102230e-16f * s * s;
+    return 1.01f * (e + e64) + 1e-30f;
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_constant__ TcArgs A) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t a_bytes = (uint32_t)TC_M * A.Kp * 2;
+    const uint32_t b_bytes = (uint32_t)TC_N * A.Kp * 2;
+    uint8_t *sA0 = base, *sB0 = base + 2 * a_bytes;
+    uint64_t *bars = (uint64_t *)(base + 2 * a_bytes + 2 * b_bytes);
+    uint64_t *full_a = bars, *empty_a = bars + 2, *full_b = bars + 4, *empty_b = bars + 6;
+    uint64_t *full_acc = bars + 8, *empty_acc = bars + 10, *done_bar = bars + 12;
+    uint32_t *tmem_slot = (uint32_t *)(bars + 14);
+    float *mrg = (float *)(bars + 16);  // [128][3] second-half results
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nkb = A.Kp / TC_KB;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2; i++) {
+            mbar_init(&full_a[i], 1);
+            mbar_init(&empty_a[i], 1);
+            mbar_init(&full_b[i], 1);
+            mbar_init(&empty_b[i], 1);
+            mbar_init(&full_acc[i], 1);
+            mbar_init(&empty_acc[i], TC_EPI_WARPS);
+        }
+        mbar_init(done_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            uint64_t ct = 0;
+            uint32_t issued_b[2] = {0, 0};
+            bool ok = true;
+            int64_t it = 0;
+            for (int64_t rt = blockIdx.x; rt < A.ntiles_r && ok; rt += gridDim.x, it++) {
+                const int ab = (int)(it & 1);
+                const uint32_t ua = (uint32_t)(it >> 1);
+                if (!(ok = mbar_wait(&empty_a[ab], (ua & 1) ^ 1, A.err))) break;
+                mbar_expect_tx(&full_a[ab], a_bytes);
+                for (int kb = 0; kb < nkb; kb++)
+                    tma_load_2d(su32(sA0 + ab * a_bytes + kb * TC_M * 128), &A.tmA, kb * TC_KB, (int)(rt * TC_M),
+                                &full_a[ab]);
+                for (int c = 0; c < A.ntiles_c; c++, ct++) {
+                    const int s = (int)(ct & 1);
+                    const uint32_t u = (uint32_t)(ct >> 1);
+                    if (!(ok = mbar_wait(&empty_b[s], (u & 1) ^ 1, A.err))) break;
+                    mbar_expect_tx(&full_b[s], b_bytes);
+                    for (int kb = 0; kb < nkb; kb++)
+                        tma_load_2d(su32(sB0 + s * b_bytes + kb * TC_N * 128), &A.tmB, kb * TC_KB, c * TC_N,
+                                    &full_b[s]);
+                    issued_b[s] = u + 1;
+                }
+            }
+            // drain: every centre-tile copy this thread issued has landed
+            for (int s = 0; s < 2; s++)
+                if (issued_b[s]) mbar_wait(&full_b[s], (issued_b[s] - 1) & 1, A.err, true);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(TC_M, TC_N);
+            uint64_t ct = 0;
+            bool ok = true;
+            int64_t it = 0;
+            for (int64_t rt = blockIdx.x; rt < A.ntiles_r && ok; rt += gridDim.x, it++) {
+                const int ab = (int)(it & 1);
+                const uint32_t ua = (uint32_t)(it >> 1);
+                if (!(ok = mbar_wait(&full_a[ab], ua & 1, A.err))) break;
+                const uint32_t a_base = su32(sA0 + ab * a_bytes);
+                for (int c = 0; c < A.ntiles_c; c++, ct++) {
+                    const int s = (int)(ct & 1);
+                    const uint32_t u = (uint32_t)(ct >> 1);
+                    if (!(ok = mbar_wait(&full_b[s], u & 1, A.err))) break;
+                    if (!(ok = mbar_wait(&empty_acc[s], (u & 1) ^ 1, A.err))) break;
+                    fence_after();
+                    const uint32_t b_base = su32(sB0 + s * b_bytes);
+                    const uint32_t dtm = tmem + (uint32_t)(s * TC_N);
+                    for (int kb = 0; kb < nkb; kb++)
+#pragma unroll
+                        for (int ks = 0; ks < TC_KB / 16; ks++)
+                            mma_bf16(dtm, sdesc(a_base + kb * TC_M * 128 + ks * 32),
+                                     sdesc(b_base + kb * TC_N * 128 + ks * 32), idesc, (kb | ks) != 0);
+                    mma_commit(&empty_b[s]);
+                    mma_commit(&full_acc[s]);
+                }
+                mma_commit(&empty_a[ab]);
+            }
+            // drain: all MMAs this thread issued have completed
+            mma_commit(done_bar);
+            mbar_wait(done_bar, 0, A.err, true);
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------ epilogue
+        const int ew = warp - 2;
+        const int q = warp & 3;     // TMEM lane quarter this warp may access
+        const int h = ew >> 2;      // column half
+        const int rloc = 32 * q + lane;
+        uint64_t ct = 0;
+        bool ok = true;
+        for (int64_t rt = blockIdx.x; rt < A.ntiles_r; rt += gridDim.x) {
+            const int64_t row = rt * TC_M + rloc;
+            const float xn = row < A.n ? A.xnorm[row] : 0.f;
+            const float W = 2.f * window_bf16(xn, A.cmax, A.d);
+            const float Wc = W * (1.f + 1e-6f);
+            float b1 = FLT_MAX, b2 = FLT_MAX;
+            int i1 = 0x7FFFFFFF;
+            for (int c = 0; c < A.ntiles_c; c++, ct++) {
+                const int s = (int)(ct & 1);
+                const uint32_t u = (uint32_t)(ct >> 1);
+                int w_ok = 0;
+                if (lane == 0 && ok) w_ok = mbar_wait(&full_acc[s], u & 1, A.err);
+                w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
+                ok = ok && w_ok;
+                if (ok) {
+                    fence_after();
+#pragma unroll 1
+                    for (int ch = 0; ch < 4; ch++) {
+                        const int col = h * 128 + ch * 32;
+                        uint32_t r[32];
+                        tmem_ld32(tmem + (uint32_t)(s * TC_N + col) + ((uint32_t)(32 * q) << 16), r);
+                        const int64_t j0 = (int64_t)c * TC_N + col;
+                        const float4 *cn4 = reinterpret_cast<const float4 *>(A.cn + j0);
+                        float v[32];
+                        float tm = FLT_MAX;
+#pragma unroll
+                        for (int i = 0; i < 8; i++) {
+                            const float4 cc = __ldg(cn4 + i);
+                            v[4 * i + 0] = fmaf(-2.f, __uint_as_float(r[4 * i + 0]), cc.x);
+                            v[4 * i + 1] = fmaf(-2.f, __uint_as_float(r[4 * i + 1]), cc.y);
+                            v[4 * i + 2] = fmaf(-2.f, __uint_as_float(r[4 * i + 2]), cc.z);
+                            v[4 * i + 3] = fmaf(-2.f, __uint_as_float(r[4 * i + 3]), cc.w);
+                            tm = fminf(tm, fminf(fminf(v[4 * i], v[4 * i + 1]), fminf(v[4 * i + 2], v[4 * i + 3])));
+                        }
+                        // all 32 values beyond the window of the current best:
+                        // none can be the argmin or spoil its certainty
+                        if (!(tm - b1 > Wc)) {
+#pragma unroll
+                            for (int i = 0; i < 32; i++) {
+                                const float x = v[i];
+                                if (x < b1) {
+                                    b2 = b1;
+                                    b1 = x;
+                                    i1 = (int)(j0 + i);
+                                } else {
+                                    b2 = fminf(b2, x);
+                                }
+                            }
+                        }
+                    }
+                    fence_before();
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty_acc[s]);
+            }
+            // merge the two column halves of each row
+            asm volatile("bar.sync 1, %0;" ::"r"(32 * TC_EPI_WARPS) : "memory");
+            if (h == 1) {
+                mrg[rloc * 3 + 0] = b1;
+                mrg[rloc * 3 + 1] = b2;
+                mrg[rloc * 3 + 2] = __int_as_float(i1);
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(32 * TC_EPI_WARPS) : "memory");
+            if (h == 0 && row < A.n && ok) {
+                const float ob1 = mrg[rloc * 3 + 0], ob2 = mrg[rloc * 3 + 1];
+                const int oi1 = __float_as_int(mrg[rloc * 3 + 2]);
+                // equal best values leave b2 == b1: the row is then flagged
+                // and decided in FP64, so the provisional index is moot
+                float nb2;
+                if (ob1 < b1) {
+                    nb2 = fminf(b1, fminf(b2, ob2));
+                    b1 = ob1;
+                    i1 = oi1;
+                } else {
+                    nb2 = fminf(ob1, fminf(b2, ob2));
+                }
+                b2 = nb2;
+                const bool valid = i1 != 0x7FFFFFFF;
+                A.labels[row] = valid ? i1 : -1;
+                const bool sure = valid && (A.k == 1 || b2 - b1 > Wc);
+                if (!sure) {
+                    const unsigned long long qq = atomicAdd(A.n_flag, 1ull);
+                    A.flag_rows[qq] = (int32_t)row;
+                }
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(32 * TC_EPI_WARPS) : "memory");
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+    }
+}
+
+// X -> BF16 K-major [n][Kp] (zero padded) and an upper bound of |x| per row
+__global__ void k_x_to_bf16(const float *__restrict__ x, int64_t ldx, int64_t n, int d, int Kp,
+                            __nv_bfloat16 *__restrict__ xb, float *__restrict__ xnorm) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < n; i += nw) {
+        float s = 0.f;
+        for (int t = lane; t < Kp; t += 32) {
+            const float v = t < d ? x[i * ldx + t] : 0.f;
+            xb[i * Kp + t] = __float2bfloat16_rn(v);
+            s = fmaf(v, v, s);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) xnorm[i] = sqrtf(s) * (1.f + 1.0e-3f);
+    }
+}
+
+__global__ void k_c_to_bf16(const double *__restrict__ c, int64_t k, int64_t kpad, int d, int Kp,
+                            __nv_bfloat16 *__restrict__ cb, float *__restrict__ cn) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < kpad;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int t = 0; t < Kp; t++) {
+            const double v = (j < k && t < d) ? c[j * d + t] : 0.0;
+            cb[j * Kp + t] = __double2bfloat16(v);
+            s += v * v;
+        }
+        cn[j] = j < k ? (float)s : __int_as_float(0x7f800000);  // +inf: padding never wins
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+geek_status encode_bf16_2d(geek_ctx *ctx, CUtensorMap *tm, void *ptr, uint64_t inner, uint64_t outer,
+                           uint32_t box_inner, uint32_t box_outer) {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !p)
+            return set_error(ctx, GEEK_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+        fn = (EncodeTiledFn)p;
+    }
+    const cuuint64_t dims[2] = {inner, outer};
+    const cuuint64_t strides[1] = {inner * 2};
+    const cuuint32_t box[2] = {box_inner, box_outer};
+    const cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(ctx, GEEK_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return GEEK_OK;
+}
+
+}  // namespace
+
+// BF16 tcgen05 pass: labels for every object, flagged rows appended to
+// flag_rows / n_flag for the FP64 decision.  d <= 128.
+geek_status assign_tc_bf16(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ldx, int64_t n, int d,
+                           const double *centres, int64_t k, int32_t *labels, int32_t *flag_rows,
+                           unsigned long long *n_flag, cudaStream_t st) {
+    if (d > 128) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "BF16 tensor-core assignment supports d <= 128");
+    const int Kp = d <= 64 ? 64 : 128;
+    const int64_t kpad = ceil_div(k, TC_N) * TC_N;
+    __nv_bfloat16 *xb, *cb;
+    float *xnorm, *cn;
+    GK_TRY(scr.alloc(&xb, (size_t)n * Kp));
+    GK_TRY(scr.alloc(&xnorm, n));
+    GK_TRY(scr.alloc(&cb, (size_t)kpad * Kp));
+    GK_TRY(scr.alloc(&cn, kpad));
+    k_x_to_bf16<<<grid_for(n * 32, 256, ctx->num_sms), 256, 0, st>>>(x, ldx, n, d, Kp, xb, xnorm);
+    k_c_to_bf16<<<grid_for(kpad, 128, ctx->num_sms), 128, 0, st>>>(centres, k, kpad, d, Kp, cb, cn);
+    GK_LAUNCH(ctx);
+    // max |c| over the centres (upper bound)
+    float cmax = 0.f;
+    {
+        std::vector<float> h(kpad);
+        GK_CUDA(ctx, cudaMemcpyAsync(h.data(), cn, sizeof(float) * kpad, cudaMemcpyDeviceToHost, st));
+        GK_CUDA(ctx, cudaStreamSynchronize(st));
+        for (int64_t j = 0; j < k; j++) cmax = std::max(cmax, h[j]);
+        cmax = sqrtf(cmax) * (1.f + 1e-5f);
+    }
+    TcArgs A;
+    memset(&A, 0, sizeof A);
+    GK_TRY(encode_bf16_2d(ctx, &A.tmA, xb, Kp, n, TC_KB, TC_M));
+    GK_TRY(encode_bf16_2d(ctx, &A.tmB, cb, Kp, kpad, TC_KB, TC_N));
+    int *err;
+    GK_TRY(scr.alloc(&err, 1));
+    GK_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(int), st));
+    A.cn = cn;
+    A.xnorm = xnorm;
+    A.n = n;
+    A.k = k;
+    A.ntiles_r = ceil_div(n, TC_M);
+    A.ntiles_c = (int)(kpad / TC_N);
+    A.Kp = Kp;
+    A.d = d;
+    A.cmax = cmax;
+    A.labels = labels;
+    A.flag_rows = flag_rows;
+    A.n_flag = n_flag;
+    A.err = err;
+    const size_t smem = 1024 + 2 * (size_t)TC_M * Kp * 2 + 2 * (size_t)TC_N * Kp * 2 + 16 * 8 + 128 * 3 * 4 + 64;
+    GK_CUDA(ctx, cudaFuncSetAttribute(k_assign_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = (int)std::min<int64_t>(A.ntiles_r, ctx->num_sms);
+    k_assign_tc<<<grid, TC_THREADS, smem, st>>>(A);
+    GK_LAUNCH(ctx);
+    int h_err = 0;
+    GK_CUDA(ctx, cudaMemcpyAsync(&h_err, err, sizeof h_err, cudaMemcpyDeviceToHost, st));
+    GK_CUDA(ctx, cudaStreamSynchronize(st));
+    if (h_err) return set_error(ctx, (geek_status)h_err, "tensor-core assignment: a pipeline wait timed out");
+    return GEEK_OK;
+}

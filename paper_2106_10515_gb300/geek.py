@@ -1,0 +1,294 @@
+"""Python binding of the GEEK C ABI (include/geek.h).
+
+Argument marshalling only: every step runs in libgeek.so's CUDA kernels.
+PyTorch provides device memory and the current CUDA stream.  If the library
+has not been built, importing this module raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgeek.so")
+
+OK, ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_OVERFLOW, ERR_UNSUPPORTED = range(7)
+DENSE, SETS, HETERO = 0, 1, 2
+MEM_DEVICE, MEM_HOST = 0, 1
+PROJ_E2LSH, PROJ_SRP = 0, 1
+PREC_FP32, PREC_BF16 = 0, 1
+STATUS_NAMES = ["OK", "ERR_INVALID", "ERR_NOMEM", "ERR_CUDA", "ERR_TIMEOUT", "ERR_OVERFLOW",
+                "ERR_UNSUPPORTED"]
+
+
+class GeekError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+        self.status = status
+
+
+class geek_data(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("mem", C.c_int32), ("n", C.c_int64), ("d", C.c_int32),
+                ("n_cat", C.c_int32), ("ldx", C.c_int64), ("x", C.c_void_p), ("set_off", C.c_void_p),
+                ("set_items", C.c_void_p), ("cat", C.c_void_p)]
+
+
+class geek_hash_params(C.Structure):
+    _fields_ = [("proj", C.c_int32), ("precision", C.c_int32), ("K", C.c_int32), ("L", C.c_int32),
+                ("Kc", C.c_int32), ("w", C.c_double), ("a", C.c_void_p), ("b", C.c_void_p),
+                ("mh_a", C.c_void_p), ("mh_b", C.c_void_p)]
+
+
+class geek_buckets_info(C.Structure):
+    _fields_ = [("n", C.c_int64), ("L", C.c_int32), ("key_bits_max", C.c_int32),
+                ("n_buckets", C.c_int64), ("n_flagged", C.c_int64)]
+
+
+class silk_params(C.Structure):
+    _fields_ = [("Ks", C.c_int32), ("Ls", C.c_int32), ("delta", C.c_int32), ("mh_a", C.c_void_p),
+                ("mh_b", C.c_void_p), ("dd_a", C.c_void_p), ("dd_b", C.c_void_p)]
+
+
+class geek_assign_params(C.Structure):
+    _fields_ = [("precision", C.c_int32)]
+
+
+class geek_assign_stats(C.Structure):
+    _fields_ = [("sse", C.c_double), ("radius_max", C.c_double), ("k", C.c_int64),
+                ("n_recheck_rows", C.c_int64)]
+
+
+# every symbol declared in include/geek.h
+EXPORTS = ["geek_ctx_create", "geek_ctx_destroy", "geek_last_error", "geek_version", "geek_hash",
+           "geek_buckets_info_get", "geek_buckets_copy_out", "geek_buckets_free", "silk_seed",
+           "silk_seeds_info", "silk_seeds_copy_out", "silk_seeds_free", "geek_assign",
+           "geek_assign_centers"]
+
+_lib = None
+
+
+def lib():
+    """Loads libgeek.so (raises if it was never built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it first (python -c 'import __graft_entry__ as g; g.build()')")
+    L = C.CDLL(LIB_PATH)
+    P, st = C.c_void_p, C.c_int
+    L.geek_ctx_create.argtypes = [C.c_int, C.POINTER(P)]
+    L.geek_ctx_destroy.argtypes = [P]
+    L.geek_last_error.argtypes = [P]
+    L.geek_last_error.restype = C.c_char_p
+    L.geek_version.restype = C.c_char_p
+    L.geek_hash.argtypes = [P, C.POINTER(geek_data), C.POINTER(geek_hash_params), C.POINTER(P), P]
+    L.geek_buckets_info_get.argtypes = [P, C.POINTER(geek_buckets_info)]
+    L.geek_buckets_copy_out.argtypes = [P, P, P, P, P, P, P]
+    L.geek_buckets_free.argtypes = [P]
+    L.silk_seed.argtypes = [P, P, C.POINTER(silk_params), C.POINTER(P), P]
+    L.silk_seeds_info.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    L.silk_seeds_copy_out.argtypes = [P, P, P, P]
+    L.silk_seeds_free.argtypes = [P]
+    L.geek_assign.argtypes = [P, C.POINTER(geek_data), P, P, C.POINTER(geek_assign_params), P, P,
+                              C.POINTER(geek_assign_stats), P]
+    L.geek_assign_centers.argtypes = [P, C.POINTER(geek_data), P, C.c_int64,
+                                      C.POINTER(geek_assign_params), P, C.POINTER(geek_assign_stats), P]
+    for name in EXPORTS:
+        f = getattr(L, name)
+        if name not in ("geek_last_error", "geek_version", "geek_ctx_destroy"):
+            f.restype = st
+    _lib = L
+    return L
+
+
+def version() -> str:
+    return lib().geek_version().decode()
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        return t.data_ptr() if t.numel() else None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data if t.size else None
+    raise TypeError(type(t))
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(a, dtype=None):
+    """numpy / tensor -> contiguous CUDA tensor (uint64 arrays as int64 bits)."""
+    if isinstance(a, np.ndarray):
+        if a.dtype == np.uint64:
+            a = a.view(np.int64)
+        a = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None and a.dtype != dtype:
+        a = a.to(dtype)
+    return a.contiguous().cuda()
+
+
+class Data:
+    """A geek_data descriptor plus references that keep its arrays alive."""
+
+    def __init__(self, kind, host, n, refs):
+        self.c = geek_data()
+        self.c.kind, self.c.mem, self.c.n = kind, MEM_HOST if host else MEM_DEVICE, n
+        self.refs = refs
+
+    @classmethod
+    def dense(cls, x, host=False):
+        self = cls(DENSE, host, x.shape[0], [x])
+        self.c.d = x.shape[1]
+        self.c.ldx = x.shape[1]
+        self.c.x = _ptr(x)
+        return self
+
+    @classmethod
+    def sets(cls, off, items, host=False):
+        self = cls(SETS, host, off.shape[0] - 1, [off, items])
+        self.c.set_off, self.c.set_items = _ptr(off), _ptr(items)
+        return self
+
+    @classmethod
+    def hetero(cls, x, tokens, host=False):
+        self = cls.dense(x, host)
+        self.c.kind = HETERO
+        self.c.n_cat = tokens.shape[1]
+        self.c.cat = _ptr(tokens)
+        self.refs.append(tokens)
+        return self
+
+
+class Buckets:
+    """geek_hash result (library-owned)."""
+
+    def __init__(self, ctx, handle, F):
+        self.ctx, self.h, self.F = ctx, handle, F
+        info = geek_buckets_info()
+        ctx._chk(lib().geek_buckets_info_get(self.h, C.byref(info)))
+        self.n, self.L = info.n, info.L
+        self.key_bits_max, self.n_buckets, self.n_flagged = info.key_bits_max, info.n_buckets, info.n_flagged
+
+    def copy_out(self):
+        n, L = self.n, self.L
+        ob = torch.empty((L, n), dtype=torch.int32, device="cuda")
+        nb = np.zeros(L, dtype=np.int64)
+        boff = torch.empty(self.n_buckets + 1, dtype=torch.int64, device="cuda")
+        mem = torch.empty(L * n, dtype=torch.int32, device="cuda")
+        codes = torch.empty((n, self.F), dtype=torch.int32, device="cuda")
+        self.ctx._chk(lib().geek_buckets_copy_out(self.h, _ptr(ob), nb.ctypes.data, _ptr(boff), _ptr(mem),
+                                                  _ptr(codes), _stream()))
+        return dict(obj_bucket=ob, n_buckets=nb, bucket_off=boff, members=mem, codes=codes)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().geek_buckets_free(self.h)
+            self.h = None
+
+
+class Seeds:
+    def __init__(self, ctx, handle):
+        self.ctx, self.h = ctx, handle
+        k, ni, nm = C.c_int64(), C.c_int64(), C.c_int64()
+        ctx._chk(lib().silk_seeds_info(self.h, C.byref(k), C.byref(ni), C.byref(nm)))
+        self.k, self.n_ids, self.n_multiset = k.value, ni.value, nm.value
+
+    def copy_out(self):
+        off = torch.empty(self.k + 1, dtype=torch.int64, device="cuda")
+        ids = torch.empty(max(self.n_ids, 1), dtype=torch.int32, device="cuda")
+        self.ctx._chk(lib().silk_seeds_copy_out(self.h, _ptr(off), _ptr(ids), _stream()))
+        return off, ids[: self.n_ids]
+
+    def sets(self):
+        off, ids = self.copy_out()
+        off, ids = off.cpu().numpy(), ids.cpu().numpy()
+        return [tuple(ids[off[j]:off[j + 1]].tolist()) for j in range(self.k)]
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().silk_seeds_free(self.h)
+            self.h = None
+
+
+class Context:
+    """One GEEK context on a CUDA device."""
+
+    def __init__(self, device: int = 0):
+        torch.cuda.set_device(device)
+        h = C.c_void_p()
+        st = lib().geek_ctx_create(device, C.byref(h))
+        if st != OK:
+            raise GeekError(st, f"geek_ctx_create(device={device}) failed")
+        self.h = h
+        self._keep = []
+
+    def _chk(self, st):
+        if st != OK:
+            raise GeekError(st, lib().geek_last_error(self.h).decode())
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().geek_ctx_destroy(self.h)
+            self.h = None
+
+    # ---------------------------------------------------------------- data --
+    @staticmethod
+    def dense(x, host=False):
+        return Data.dense(x, host)
+
+    @staticmethod
+    def sets(off, items, host=False):
+        return Data.sets(off, items, host)
+
+    @staticmethod
+    def hetero(x, tokens, host=False):
+        return Data.hetero(x, tokens, host)
+
+    # ---------------------------------------------------------------- hash --
+    def hash(self, data, K, L, a=None, b=None, w=4.0, mh_a=None, mh_b=None, Kc=0,
+             proj=PROJ_E2LSH, precision=PREC_FP32) -> Buckets:
+        p = geek_hash_params()
+        p.proj, p.precision, p.K, p.L, p.Kc, p.w = proj, precision, K, L, Kc, float(w)
+        p.a, p.b, p.mh_a, p.mh_b = _ptr(a), _ptr(b), _ptr(mh_a), _ptr(mh_b)
+        out = C.c_void_p()
+        self._chk(lib().geek_hash(self.h, C.byref(data.c), C.byref(p), C.byref(out), _stream()))
+        F = K * L
+        return Buckets(self, out, F)
+
+    def silk(self, buckets: Buckets, Ks, Ls, delta, mh_a, mh_b, dd_a, dd_b) -> Seeds:
+        p = silk_params()
+        p.Ks, p.Ls, p.delta = Ks, Ls, delta
+        p.mh_a, p.mh_b, p.dd_a, p.dd_b = _ptr(mh_a), _ptr(mh_b), _ptr(dd_a), _ptr(dd_b)
+        out = C.c_void_p()
+        self._chk(lib().silk_seed(self.h, buckets.h, C.byref(p), C.byref(out), _stream()))
+        return Seeds(self, out)
+
+    def assign(self, data, buckets, seeds: Seeds, labels, centers=None, precision=PREC_FP32, stats=True):
+        p = geek_assign_params()
+        p.precision = precision
+        s = geek_assign_stats()
+        self._chk(lib().geek_assign(self.h, C.byref(data.c), buckets.h if buckets is not None else None,
+                                    seeds.h, C.byref(p), _ptr(labels), _ptr(centers),
+                                    C.byref(s) if stats else None, _stream()))
+        return s
+
+    def assign_centers(self, data, centers, labels, precision=PREC_FP32, stats=True):
+        p = geek_assign_params()
+        p.precision = precision
+        s = geek_assign_stats()
+        k = centers.shape[0]
+        self._chk(lib().geek_assign_centers(self.h, C.byref(data.c), _ptr(centers), k, C.byref(p), _ptr(labels),
+                                            C.byref(s) if stats else None, _stream()))
+        return s
+
+
+def silk_args(sp):
+    """Device copies of a SILK parameter dict (from synth.silk_params)."""
+    return dict(Ks=sp["Ks"], Ls=sp["Ls"], delta=sp["delta"], mh_a=_dev(sp["mh_a"]), mh_b=_dev(sp["mh_b"]),
+                dd_a=_dev(sp["dd_a"]), dd_b=_dev(sp["dd_b"]))

@@ -1,0 +1,177 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Integer results (codes, bucket ids, members, seeds, labels) must be
+bit-exact; SSE and radius within 1e-6 relative of the oracle's FP64 values.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+RTOL_SSE = 1e-6
+
+
+@pytest.fixture(scope="module")
+def G():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2106_10515_gb300 import geek
+    return geek
+
+
+@pytest.fixture(scope="module")
+def ctx(G):
+    return G.Context(0)
+
+
+def check_buckets(got, ref, codes_ref=None):
+    assert np.array_equal(got["n_buckets"], ref.n_buckets)
+    assert np.array_equal(got["obj_bucket"].cpu().numpy(), ref.obj_bucket)
+    assert np.array_equal(got["bucket_off"].cpu().numpy(), ref.boff)
+    assert np.array_equal(got["members"].cpu().numpy(), ref.bmem)
+    if codes_ref is not None:
+        assert np.array_equal(got["codes"].cpu().numpy(), codes_ref.astype(np.int32))
+
+
+def run_dense(G, ctx, wl, proj=0):
+    cfg = wl["cfg"]
+    x = G._dev(wl["x"])
+    bk = ctx.hash(ctx.dense(x), cfg.K, cfg.L, a=G._dev(wl["a"]), b=G._dev(wl["b"]), w=wl["w"], proj=proj)
+    return x, bk
+
+
+@pytest.mark.parametrize("over", [dict(), dict(n=1), dict(n=4097), dict(n=20000, silk=dict(delta=1))])
+def test_dense_c1_full_pipeline(G, ctx, over):
+    """Small dense workload: codes, buckets, seeds, labels and SSE."""
+    wl = synth.make(synth.config("c1", **over))
+    cfg = wl["cfg"]
+    x, bk = run_dense(G, ctx, wl)
+    ref = oracle.run_workload(wl)
+    check_buckets(bk.copy_out(), ref["buckets"], ref["codes"])
+    seeds = ctx.silk(bk, **G.silk_args(wl["silk"]))
+    assert seeds.n_multiset == ref["seeds"].n_multiset
+    assert seeds.sets() == ref["seeds"].sets()
+    labels = torch.empty(cfg.n, dtype=torch.int32, device="cuda")
+    centres = torch.empty((max(seeds.k, 1), cfg.d), dtype=torch.float64, device="cuda")
+    st = ctx.assign(ctx.dense(x), bk, seeds, labels, centers=centres)
+    torch.cuda.synchronize()
+    assert np.array_equal(labels.cpu().numpy(), ref["labels"])
+    if seeds.k:
+        assert np.array_equal(centres[: seeds.k].cpu().numpy(), ref["centres"])  # bit-exact FP64
+        sse = float(np.sum(ref["dist"]))
+        assert abs(st.sse - sse) <= RTOL_SSE * sse
+        assert abs(st.radius_max - np.sqrt(ref["dist"].max())) <= RTOL_SSE * np.sqrt(ref["dist"].max())
+
+
+def test_dense_c2_shape_hash_and_assign(G, ctx):
+    """The 10M x 128 workload's shape at n = 60,000 (several tiles, ragged
+    tail): E2LSH K=6, L=16 codes and buckets, then assignment to the planted
+    centres in both fast precisions."""
+    wl = synth.make(synth.config("c2", n=60_001, n_comp=600))
+    cfg = wl["cfg"]
+    x, bk = run_dense(G, ctx, wl)
+    codes, ref = oracle.hash_dense(wl["x"], wl["a"], wl["b"], wl["w"], cfg.K, cfg.L)
+    check_buckets(bk.copy_out(), ref, codes)
+    assert bk.n_flagged > 0  # the window does flag elements at this scale
+    c = wl["centres"].astype(np.float64)
+    lab_ref, dist_ref = oracle.assign_dense(wl["x"], c)
+    for prec in (G.PREC_FP32, G.PREC_BF16):
+        labels = torch.empty(cfg.n, dtype=torch.int32, device="cuda")
+        st = ctx.assign_centers(ctx.dense(x), G._dev(c), labels, precision=prec)
+        torch.cuda.synchronize()
+        assert np.array_equal(labels.cpu().numpy(), lab_ref), prec
+        assert abs(st.sse - dist_ref.sum()) <= RTOL_SSE * dist_ref.sum()
+
+
+def test_srp_codes_and_buckets(G, ctx):
+    wl = synth.make(synth.config("c1", n=9000))
+    cfg = wl["cfg"]
+    x, bk = run_dense(G, ctx, wl, proj=G.PROJ_SRP)
+    bits, ref = oracle.hash_dense(wl["x"], wl["a"], wl["b"], wl["w"], cfg.K, cfg.L, proj="srp")
+    check_buckets(bk.copy_out(), ref, bits)
+
+
+def test_assign_near_ties_are_exact(G, ctx):
+    """Duplicated and nearly duplicated centres force the FP64 decision:
+    exact ties must go to the smaller index."""
+    rng = np.random.default_rng(5)
+    x = (rng.standard_normal((5000, 32)) * 3).astype(np.float32)
+    c = rng.standard_normal((300, 32)) * 3
+    c[150:] = c[:150]                      # exact duplicates
+    c[100:150] += 1e-9                     # near duplicates
+    lab_ref, _ = oracle.assign_dense(x, c)
+    for prec in (0, 1):
+        labels = torch.empty(5000, dtype=torch.int32, device="cuda")
+        st = ctx.assign_centers(ctx.dense(G._dev(x)), G._dev(c), labels, precision=prec)
+        torch.cuda.synchronize()
+        assert np.array_equal(labels.cpu().numpy(), lab_ref)
+        assert st.n_recheck_rows > 0
+
+
+def test_host_memory_path(G, ctx):
+    """The same call with host buffers (the library stages them)."""
+    wl = synth.make(synth.config("c1", n=5000))
+    cfg = wl["cfg"]
+    c = wl["centres"].astype(np.float64)
+    lab_ref, _ = oracle.assign_dense(wl["x"], c)
+    labels = np.empty(cfg.n, dtype=np.int32)
+    ctx.assign_centers(ctx.dense(wl["x"], host=True), c, labels)
+    assert np.array_equal(labels, lab_ref)
+
+
+def test_invalid_arguments_are_reported(G, ctx):
+    wl = synth.make(synth.config("c1", n=100))
+    x = G._dev(wl["x"])
+    with pytest.raises(G.GeekError) as e:
+        ctx.hash(ctx.dense(x), 0, 8, a=G._dev(wl["a"]), b=G._dev(wl["b"]), w=4.0)
+    assert e.value.status == G.ERR_INVALID
+    with pytest.raises(G.GeekError):
+        ctx.hash(ctx.dense(x), 4, 8, a=G._dev(wl["a"]), b=G._dev(wl["b"]), w=-1.0)
+
+
+@pytest.mark.parametrize("over", [dict(n=20_000, n_base=200), dict(n=3001, n_base=50, silk=dict(delta=3))])
+def test_sets_c3_shape_pipeline(G, ctx, over):
+    """Sparse sets: MinHash K=4, L=32 (128-bit table keys), SILK, majority
+    centres and exact Jaccard assignment."""
+    wl = synth.make(synth.config("c3", **over))
+    cfg = wl["cfg"]
+    off = G._dev(wl["set_off"])
+    items = G._dev(wl["set_items"].astype(np.int32))
+    data = ctx.sets(off, items)
+    bk = ctx.hash(data, cfg.K, cfg.L, mh_a=G._dev(wl["mh_a"]), mh_b=G._dev(wl["mh_b"]))
+    ref = oracle.run_workload(wl)
+    assert bk.key_bits_max == 128
+    got = bk.copy_out()
+    check_buckets(got, ref["buckets"], ref["codes"].view(np.int32))
+    seeds = ctx.silk(bk, **G.silk_args(wl["silk"]))
+    assert seeds.sets() == ref["seeds"].sets()
+    assert seeds.k > 0
+    labels = torch.empty(cfg.n, dtype=torch.int32, device="cuda")
+    ctx.assign(data, bk, seeds, labels)
+    torch.cuda.synchronize()
+    assert np.array_equal(labels.cpu().numpy(), ref["labels"])
+
+
+@pytest.mark.parametrize("over", [dict(n=20_000, n_comp=100), dict(n=777, n_comp=20, silk=dict(delta=1))])
+def test_hetero_c4_shape_pipeline(G, ctx, over):
+    """Heterogeneous rows: E2LSH codes of the numeric part concatenated with
+    MinHash of the tokens (Alg. 2), SILK, modes and categorical assignment."""
+    wl = synth.make(synth.config("c4", **over))
+    cfg = wl["cfg"]
+    x = G._dev(wl["x"])
+    tok = G._dev(wl["tokens"].astype(np.int32))
+    data = ctx.hetero(x, tok)
+    bk = ctx.hash(data, cfg.K, cfg.L, a=G._dev(wl["a"]), b=G._dev(wl["b"]), w=wl["w"],
+                  mh_a=G._dev(wl["mh_a"]), mh_b=G._dev(wl["mh_b"]), Kc=cfg.Kc)
+    ref = oracle.run_workload(wl)
+    check_buckets(bk.copy_out(), ref["buckets"], ref["codes"])
+    seeds = ctx.silk(bk, **G.silk_args(wl["silk"]))
+    assert seeds.sets() == ref["seeds"].sets()
+    labels = torch.empty(cfg.n, dtype=torch.int32, device="cuda")
+    ctx.assign(data, bk, seeds, labels)
+    torch.cuda.synchronize()
+    assert np.array_equal(labels.cpu().numpy(), ref["labels"])
