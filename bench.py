@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Throughput of the GEEK hot path on one GB300 (replicas on N GPUs).
+
+One step on the 10M x 128 dense workload (Sift10M-shaped, synthetic):
+  geek_hash   E2LSH K=6, L=16, w=4 codes of every point and bucket grouping
+  silk_seed   SILK (K_s=3, L_s=10, delta=10) over all buckets
+  geek_assign the one-pass assignment of every point to the 20,000 planted
+              mixture centres (SILK selects no seed at these hash parameters:
+              E2LSH with a fixed width leaves almost every bucket a singleton)
+The metric is points per second of that step.  The headline uses the BF16
+tcgen05 assignment; the same step with the FP32 SIMT assignment is reported
+beside it.  Both are bit-exact against the FP64 definition.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+N > 1 runs one independent replica per GPU (the path has no exchange step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "points/sec hash+assign (n=10M,d=128) mixed vs plain FP32; TC util/HBM GB/s"
+UNIT = "points/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (nominal)
+FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def peaks():
+    if os.path.exists(PEAKS_FILE):
+        p = json.load(open(PEAKS_FILE))
+        return p, "measured"
+    return FALLBACK, "fallback"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev, self.proc, self.lines = dev, None, []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.dev), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload(args):
+    import synth
+    over = {} if args.n is None else dict(n=args.n, n_comp=max(50, min(20000, args.n // 500)))
+    cfg = synth.config(args.workload, **over)
+    t0 = time.time()
+    wl = synth.make(cfg)
+    return wl, time.time() - t0
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the kernel source as it is now (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}.traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    src = os.path.join(ROOT, rec["source"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["source_sha256"]:
+        return None
+    return rec["dram_bytes_per_launch_full_size"]
+
+
+def kernel_work(name, cfg, k, nb_total):
+    """Algorithmic work of one launch: (bound, amount, unit)."""
+    n, d, F, L = cfg.n, cfg.d, cfg.K * cfg.L, cfg.L
+    if name == "kernel.assign_tc":
+        return "tensor", 2.0 * n * k * d, "flop"
+    if name == "kernel.assign_fp32":
+        return "alu", 2.0 * n * k * d, "flop"
+    if name == "kernel.project_fp32":
+        return "alu", 2.0 * n * F * d, "flop"
+    if name == "kernel.rs_scatter":
+        return "hbm", None, "byte"  # per-launch bytes depend on the sort; filled by caller
+    return None, None, None
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2106_10515_gb300 import geek
+
+    wl, t_gen = workload(args)
+    cfg = wl["cfg"]
+    ctx = geek.Context(local)
+    x = geek._dev(wl["x"])
+    a, b = geek._dev(wl["a"]), geek._dev(wl["b"])
+    silk = geek.silk_args(wl["silk"])
+    centres = geek._dev(wl["centres"].astype(np.float64))
+    k = centres.shape[0]
+    labels = torch.empty(cfg.n, dtype=torch.int32, device="cuda")
+    data = ctx.dense(x)
+    prec = geek.PREC_BF16 if args.precision == "bf16" else geek.PREC_FP32
+
+    info = {}
+
+    def step(p):
+        bk = ctx.hash(data, cfg.K, cfg.L, a=a, b=b, w=wl["w"])
+        seeds = ctx.silk(bk, **silk)
+        st = ctx.assign_centers(data, centres, labels, precision=p)
+        info.update(k_star=seeds.k, n_multiset=seeds.n_multiset, n_buckets=bk.n_buckets,
+                    n_flagged=bk.n_flagged, n_recheck_rows=st.n_recheck_rows, sse=st.sse,
+                    key_bits=bk.key_bits_max)
+        del bk, seeds
+
+    def timed(p, steps, warmup, clocks=None):
+        for _ in range(warmup):
+            step(p)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ctx.timing_reset()
+        ctx.timing(True)
+        l0 = geek.launch_count()
+        if clocks:
+            clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            step(p)
+        e1.record()
+        torch.cuda.synchronize()
+        cl = clocks.stop() if clocks else None
+        ms = e0.elapsed_time(e1) / steps
+        ctx.timing(False)
+        launches = geek.launch_count() - l0
+        tm = {name: ctx.timing_get(name) for name in
+              ["hash", "silk", "assign", "hash.sort", "kernel.project_fp32", "kernel.recheck_fp64",
+               "kernel.rs_scatter", "kernel.assign_tc", "kernel.assign_fp32", "kernel.assign_recheck"]}
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, launches, tm, cl
+
+    clocks = Clocks(local)
+    ms, launches, tm, cl = timed(prec, args.steps, args.warmup, clocks)
+    main_info = dict(info)
+    other = "fp32" if args.precision == "bf16" else "bf16"
+    ms_other, _, tm_other, _ = (None, None, None, None)
+    if not args.skip_other:
+        ms_other, _, tm_other, _ = timed(geek.PREC_FP32 if other == "fp32" else geek.PREC_BF16,
+                                         max(1, args.steps), 1)
+
+    # end to end through the C ABI with host buffers (pinned)
+    e2e = None
+    if not args.skip_e2e:
+        xh = torch.from_numpy(wl["x"]).pin_memory()
+        ch = torch.from_numpy(wl["centres"].astype(np.float64)).pin_memory()
+        lh = torch.empty(cfg.n, dtype=torch.int32).pin_memory()
+        hdata = ctx.dense(xh.numpy(), host=True)
+
+        def step_host():
+            bk = ctx.hash(hdata, cfg.K, cfg.L, a=a, b=b, w=wl["w"])
+            seeds = ctx.silk(bk, **silk)
+            ctx.assign_centers(hdata, ch.numpy(), lh.numpy(), precision=prec)
+            del bk, seeds
+
+        step_host()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step_host()
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        h2d = 2 * xh.numel() * 4 + ch.numel() * 8  # x staged by hash and by assign, centres once
+        e2e = {"value": cfg.n * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(lh.numel() * 4), "ms_per_step": e2e_s * 1e3}
+
+    pk, pk_kind = peaks()
+    # dominant kernel of the timed step
+    kern = {kname: v for kname, v in tm.items() if kname.startswith("kernel.") and v[1] > 0}
+    dom = max(kern, key=lambda kk: kern[kk][0]) if kern else None
+    roof = None
+    if dom:
+        tot_ms, cnt = kern[dom]
+        avg_s = tot_ms / cnt / 1e3
+        bound, work, unit = kernel_work(dom, cfg, k, main_info["n_buckets"])
+        if bound == "tensor":
+            peak = pk["bf16_tflops_sustained"]
+            roof = {"kernel": dom, "bound": "tensor", "achieved": work / avg_s / 1e12, "peak": peak,
+                    "unit": "TFLOP/s", "peak_source": f"{pk_kind} bf16_tflops_sustained"}
+        elif bound == "alu":
+            roof = {"kernel": dom, "bound": "alu", "achieved": work / avg_s / 1e12, "peak": FP32_SIMT_TFLOPS,
+                    "unit": "TFLOP/s", "peak_source": "derived FP32 SIMT nominal (152 SM x 128 x 2 x 2.07 GHz)"}
+        elif bound == "hbm":
+            # one scatter pass moves keys (8 B, +8 B above 64 bits) and a 4-byte id in and out
+            kw = 16 if main_info["key_bits"] > 64 else 8
+            work = 2.0 * (kw + 4) * cfg.n * cfg.L
+            roof = {"kernel": dom, "bound": "hbm", "achieved": work / avg_s / 1e9, "peak": pk["hbm_gbs"],
+                    "unit": "GB/s", "peak_source": f"{pk_kind} hbm_gbs"}
+        if roof:
+            roof["frac"] = roof["achieved"] / roof["peak"]
+            roof["avg_launch_ms"] = avg_s * 1e3
+            roof["launches_timed"] = cnt
+            roof["traffic"] = traffic_for(dom)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        cpu = cpu_baseline(wl, args.cpu_rows)
+
+    line = {
+        "metric": METRIC,
+        "value": cfg.n * world / (ms / 1e3),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 inputs; " + ("bf16 tensor-core assign + fp64 recheck" if prec == geek.PREC_BF16
+                                   else "fp32 SIMT assign + fp64 recheck"),
+        "data": "synthetic (Sift10M-shaped Gaussian mixture, seeded)",
+        "config": {"workload": f"dense n={cfg.n} d={cfg.d}, {cfg.n_comp} Zipf-weighted Gaussians; "
+                               f"E2LSH K={cfg.K} L={cfg.L} w={cfg.w}; SILK Ks={wl['silk']['Ks']} "
+                               f"Ls={wl['silk']['Ls']} delta={wl['silk']['delta']}; assign to the "
+                               f"{k} planted centres",
+                   "n": cfg.n, "d": cfg.d, "k_assign": k, "k_star_silk": main_info["k_star"],
+                   "l2": "inputs larger than L2 (x is 5.1 GB)", "parallelism": f"replicas x{world}",
+                   "precision": args.precision},
+        "phases_ms": {ph: tm[ph][0] / max(1, tm[ph][1]) for ph in ["hash", "silk", "assign", "hash.sort"]},
+        "hash_assign_points_per_s": cfg.n * world / ((tm["hash"][0] / max(1, tm["hash"][1]) +
+                                                     tm["assign"][0] / max(1, tm["assign"][1])) / 1e3),
+        "recheck": {"hash_flagged_elems": main_info["n_flagged"], "assign_recheck_rows": main_info["n_recheck_rows"]},
+        "gpu_launches": int(launches),
+        "clocks": cl,
+        "roofline": roof,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "generate_s": t_gen,
+    }
+    if ms_other is not None:
+        line[f"{other}_assign_variant"] = {
+            "value": cfg.n * world / (ms_other / 1e3), "ms_per_step": ms_other,
+            "assign_ms": tm_other["assign"][0] / max(1, tm_other["assign"][1]),
+            "hash_assign_points_per_s": cfg.n * world / ((tm_other["hash"][0] / max(1, tm_other["hash"][1]) +
+                                                          tm_other["assign"][0] / max(1, tm_other["assign"][1])) / 1e3)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(wl, rows):
+    """The FP64 oracle, as it stands, on the first `rows` points of the same
+    workload: hash + grouping + SILK on those points, then assignment of
+    them to the planted centres.  Returns points/s."""
+    import oracle
+    oracle.build()
+    cfg = wl["cfg"]
+    x = wl["x"][:rows]
+    t0 = time.perf_counter()
+    _, bk = oracle.hash_dense(x, wl["a"], wl["b"], wl["w"], cfg.K, cfg.L)
+    oracle.silk_on(bk, wl["silk"])
+    oracle.assign_dense(x, wl["centres"].astype(np.float64))
+    dt = time.perf_counter() - t0
+    return {"value": rows / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"first {rows} of {cfg.n} points: hash + grouping + SILK on the sample, "
+                      f"assignment of the sample to all {wl['centres'].shape[0]} centres", "seconds": dt}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    wl, _ = workload(args)
+    for _ in range(args.warmup):
+        cpu_baseline(wl, max(256, args.cpu_rows // 8))
+    vals, secs = [], 0.0
+    for _ in range(args.steps):
+        r = cpu_baseline(wl, args.cpu_rows)
+        vals.append(r["value"])
+        secs += r["seconds"]
+    v = float(np.median(vals))
+    cfg = wl["cfg"]
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (Sift10M-shaped Gaussian mixture, seeded)",
+            "config": {"workload": f"dense n={cfg.n} d={cfg.d}; FP64 CPU oracle on a {args.cpu_rows}-point sample"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--n", type=int, default=None, help="override n (smaller runs)")
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--cpu-rows", type=int, default=4096)
+    ap.add_argument("--skip-other", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours" and args.n is None:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

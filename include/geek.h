@@ -225,6 +225,21 @@ geek_status geek_assign_centers(geek_ctx *ctx, const geek_data *data, const doub
                                 int64_t k, const geek_assign_params *p, int32_t *labels,
                                 geek_assign_stats *stats, geek_stream stream);
 
+/* ---- tracing -------------------------------------------------------------- */
+
+/* When on, every phase (names "hash", "silk", "assign") and the main kernels
+ * ("kernel.project_fp32", "kernel.recheck_fp64", "kernel.rs_scatter",
+ * "kernel.assign_fp32", "kernel.assign_tc", "kernel.assign_recheck", and the
+ * sort phase "hash.sort") are bracketed by CUDA events on the call's stream;
+ * each bracket waits for its end event, so timing adds synchronisation.
+ * Off by default. */
+geek_status geek_timing_enable(geek_ctx *ctx, int on);
+geek_status geek_timing_reset(geek_ctx *ctx);
+/* Total milliseconds and bracket count recorded under `name` (0 if none). */
+geek_status geek_timing_get(const geek_ctx *ctx, const char *name, double *total_ms, int64_t *count);
+/* Kernels launched by this library in this process so far. */
+unsigned long long geek_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

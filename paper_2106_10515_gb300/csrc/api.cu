@@ -172,9 +172,33 @@ geek_status hash_impl(geek_ctx *ctx, const geek_data *data, const geek_hash_para
 
 }  // namespace
 
+unsigned long long g_geek_launches = 0;
+
 extern "C" {
 
 const char *geek_version(void) { return GEEK_VERSION_STRING; }
+
+unsigned long long geek_launch_count(void) { return __atomic_load_n(&g_geek_launches, __ATOMIC_RELAXED); }
+
+geek_status geek_timing_enable(geek_ctx *ctx, int on) {
+    if (!ctx) return GEEK_ERR_INVALID;
+    ctx->timing = on != 0;
+    return GEEK_OK;
+}
+
+geek_status geek_timing_reset(geek_ctx *ctx) {
+    if (!ctx) return GEEK_ERR_INVALID;
+    ctx->times.clear();
+    return GEEK_OK;
+}
+
+geek_status geek_timing_get(const geek_ctx *ctx, const char *name, double *total_ms, int64_t *count) {
+    if (!ctx || !name) return GEEK_ERR_INVALID;
+    auto it = ctx->times.find(name);
+    if (total_ms) *total_ms = it == ctx->times.end() ? 0.0 : it->second.first;
+    if (count) *count = it == ctx->times.end() ? 0 : it->second.second;
+    return GEEK_OK;
+}
 
 geek_status geek_ctx_create(int device, geek_ctx **out) {
     if (!out) return GEEK_ERR_INVALID;
@@ -217,6 +241,7 @@ geek_status geek_hash(geek_ctx *ctx, const geek_data *data, const geek_hash_para
                       geek_buckets **out, geek_stream stream) {
     if (!ctx) return GEEK_ERR_INVALID;
     try {
+        EvTimer tm(ctx, "hash", S(stream));
         return hash_impl(ctx, data, p, out, S(stream));
     } catch (...) {
         return set_error(ctx, GEEK_ERR_NOMEM, "host exception in geek_hash");
@@ -269,6 +294,7 @@ geek_status silk_seed(geek_ctx *ctx, const geek_buckets *b, const silk_params *p
     s->ctx = ctx;
     geek_status st;
     try {
+        EvTimer tm(ctx, "silk", S(stream));
         st = silk_run(ctx, b, p, s, S(stream));
     } catch (...) {
         st = set_error(ctx, GEEK_ERR_NOMEM, "host exception in silk_seed");
@@ -316,6 +342,7 @@ geek_status geek_assign_centers(geek_ctx *ctx, const geek_data *data, const doub
         if (!p || !labels || (k > 0 && !centers) || k < 0 || k > 0x7FFFFFFFLL)
             return set_error(ctx, GEEK_ERR_INVALID, "bad assignment arguments");
         cudaStream_t st = S(stream);
+        EvTimer tm(ctx, "assign", st);
         Scratch scr(ctx, st);
         const bool host = data->mem == GEEK_MEM_HOST;
         const float *x;
@@ -348,6 +375,7 @@ geek_status geek_assign(geek_ctx *ctx, const geek_data *data, const geek_buckets
         GK_TRY(check_data(ctx, data));
         if (!s || !p || !labels) return set_error(ctx, GEEK_ERR_INVALID, "NULL argument");
         cudaStream_t st = S(stream);
+        EvTimer tm(ctx, "assign", st);
         Scratch scr(ctx, st);
         const bool host = data->mem == GEEK_MEM_HOST;
         const int64_t n = data->n;

@@ -328,6 +328,7 @@ __global__ void k_fill_labels(int32_t *l, int64_t n, int32_t v) {
 geek_status centroids_from_seeds(geek_ctx *ctx, const float *x, int64_t ldx, int d, const silk_seeds *s,
                                  double *centres, cudaStream_t st) {
     if (s->k == 0) return GEEK_OK;
+    GK_COUNT();
     k_centroids<<<grid_for(s->k * d, 256, ctx->num_sms), 256, 0, st>>>(x, ldx, d, s->k, s->off, s->ids, centres);
     GK_LAUNCH(ctx);
     return GEEK_OK;
@@ -339,6 +340,7 @@ geek_status assign_dense_centres(geek_ctx *ctx, Scratch &scr, const float *x, in
     if (stats) *stats = geek_assign_stats{0.0, 0.0, k, 0};
     if (n == 0) return GEEK_OK;
     if (k == 0) {
+        GK_COUNT();
         k_fill_labels<<<grid_for(n, 256, ctx->num_sms), 256, 0, st>>>(labels, n, -1);
         GK_LAUNCH(ctx);
         return GEEK_OK;
@@ -352,6 +354,7 @@ geek_status assign_dense_centres(geek_ctx *ctx, Scratch &scr, const float *x, in
     GK_TRY(scr.alloc(&cn, k));
     GK_TRY(scr.alloc(&cmax_bits, 1));
     GK_CUDA(ctx, cudaMemsetAsync(cmax_bits, 0, sizeof(unsigned), st));
+    GK_COUNT();
     k_centre_prep<<<grid_for(k, 128, ctx->num_sms), 128, 0, st>>>(centres, k, d, c32, cn, cmax_bits);
     GK_LAUNCH(ctx);
     unsigned h_bits = 0;
@@ -369,6 +372,8 @@ geek_status assign_dense_centres(geek_ctx *ctx, Scratch &scr, const float *x, in
     } else {
         const size_t smem = (size_t)d * AS_TR * sizeof(float) + (size_t)AS_KC * AS_TC * sizeof(float);
         GK_CUDA(ctx, cudaFuncSetAttribute(k_assign_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        EvTimer tk(ctx, "kernel.assign_fp32", st);
+        GK_COUNT();
         k_assign_fp32<<<(unsigned)ceil_div(n, AS_TR), 256, smem, st>>>(x, ldx, n, d, c32, cn, k, cmax, labels,
                                                                          flag_rows, n_flag);
         GK_LAUNCH(ctx);
@@ -378,6 +383,8 @@ geek_status assign_dense_centres(geek_ctx *ctx, Scratch &scr, const float *x, in
     GK_CUDA(ctx, cudaStreamSynchronize(st));
     if (h_flag) {
         const int blocks = (int)std::min<unsigned long long>(h_flag, (unsigned long long)ctx->num_sms * 8);
+        EvTimer tk(ctx, "kernel.assign_recheck", st);
+        GK_COUNT();
         k_assign_recheck<<<blocks, 256, d * sizeof(float), st>>>(x, ldx, d, c32, cn, centres, k, cmax, flag_rows,
                                                                   n_flag, labels);
         GK_LAUNCH(ctx);
@@ -389,7 +396,9 @@ geek_status assign_dense_centres(geek_ctx *ctx, Scratch &scr, const float *x, in
         GK_TRY(scr.alloc(&ps, nb));
         GK_TRY(scr.alloc(&pm, nb));
         GK_TRY(scr.alloc(&out, 2));
+        GK_COUNT();
         k_assign_stats<<<nb, 256, 0, st>>>(x, ldx, n, d, centres, k, labels, ps, pm);
+        GK_COUNT();
         k_stats_final<<<1, 32, 0, st>>>(ps, pm, nb, out);
         GK_LAUNCH(ctx);
         double h[2];

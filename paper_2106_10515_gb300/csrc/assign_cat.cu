@@ -294,7 +294,9 @@ geek_status majority_per_group(geek_ctx *ctx, Scratch &scr, int64_t ng, const in
     GK_TRY(scr.alloc(out_off, ng + 1));
     GK_TRY(scr.alloc(&tot, 1));
     GK_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(int64_t) * ng, st));
+    GK_COUNT();
     k_group_w<<<G(ctx, m), 256, 0, st>>>(m, gmem, soff, w);
+    GK_COUNT();
     k_group_of<<<G(ctx, ng), 256, 0, st>>>(ng, goff, gid);
     GK_LAUNCH(ctx);
     GK_TRY(exclusive_scan_i64(ctx, scr, w, woff, m, T_dev, st));
@@ -305,6 +307,7 @@ geek_status majority_per_group(geek_ctx *ctx, Scratch &scr, int64_t ng, const in
     if (T > 0) {
         uint64_t *pairs;
         GK_TRY(scr.alloc(&pairs, T));
+        GK_COUNT();
         k_group_expand<<<G(ctx, m), 256, 0, st>>>(m, gid, gmem, woff, soff, sids, pairs);
         GK_LAUNCH(ctx);
         GK_TRY(radix_sort_segments(ctx, scr, 1, T, &pairs, nullptr, nullptr, 32 + bit_length_u64((uint64_t)ng), st));
@@ -319,12 +322,14 @@ geek_status majority_per_group(geek_ctx *ctx, Scratch &scr, int64_t ng, const in
         GK_TRY(scr.alloc(&keep, NR));
         GK_TRY(scr.alloc(&pos, NR));
         GK_TRY(scr.alloc(&ktot, 1));
+        GK_COUNT();
         k_group_keep<<<G(ctx, NR), 256, 0, st>>>(nr, prs, pairs, goff, keep, cnt);
         GK_LAUNCH(ctx);
         GK_TRY(exclusive_scan_i64(ctx, scr, keep, pos, NR, ktot, st));
         GK_CUDA(ctx, cudaMemcpyAsync(&total, ktot, 8, cudaMemcpyDeviceToHost, st));
         GK_CUDA(ctx, cudaStreamSynchronize(st));
         GK_TRY(scr.alloc(out_ids, std::max<int64_t>(1, total)));
+        GK_COUNT();
         k_group_emit<<<G(ctx, NR), 256, 0, st>>>(nr, prs, pairs, keep, pos, *out_ids);
         GK_LAUNCH(ctx);
     } else {
@@ -349,8 +354,10 @@ geek_status assign_hetero(geek_ctx *ctx, Scratch &scr, const geek_buckets *b, co
     GK_TRY(scr.alloc(&attrs, (size_t)n * A));
     GK_TRY(scr.alloc(&modes, (size_t)std::max<int64_t>(k, 1) * A));
     GK_TRY(scr.alloc(&matches, n));
+    GK_COUNT();
     k_build_attrs<<<G(ctx, n * A), 256, 0, st>>>(n, b->L, n_cat, b->num_key, tok, attrs);
-    if (k) k_modes<<<G(ctx, k * A), 256, 0, st>>>(k, A, s->off, s->ids, attrs, modes);
+    if (k) GK_COUNT(), k_modes<<<G(ctx, k * A), 256, 0, st>>>(k, A, s->off, s->ids, attrs, modes);
+    GK_COUNT();
     k_assign_cat<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(n, A, k, attrs, modes, labels, matches);
     GK_LAUNCH(ctx);
     if (stats) {
@@ -389,9 +396,11 @@ geek_status assign_sets(geek_ctx *ctx, Scratch &scr, const int64_t *off, const u
     uint64_t *pairs, *ikey;
     GK_TRY(scr.alloc(&pairs, std::max<int64_t>(nci, 1)));
     GK_TRY(scr.alloc(&ikey, std::max<int64_t>(nci, 1)));
+    GK_COUNT();
     k_centre_pairs<<<G(ctx, k), 256, 0, st>>>(k, coff, citems, pairs);
     GK_LAUNCH(ctx);
     GK_TRY(radix_sort_segments(ctx, scr, 1, nci, &pairs, nullptr, nullptr, 64, st));
+    GK_COUNT();
     k_item_key<<<G(ctx, nci), 256, 0, st>>>(nci, pairs, ikey);
     GK_LAUNCH(ctx);
     int64_t *rs, *nr_dev;
@@ -406,6 +415,7 @@ geek_status assign_sets(geek_ctx *ctx, Scratch &scr, const int64_t *off, const u
     uint32_t *lval;
     GK_TRY(scr.alloc(&lkey, std::max<int64_t>(ni, 1)));
     GK_TRY(scr.alloc(&lval, std::max<int64_t>(ni, 1)));
+    GK_COUNT();
     k_len_key<<<G(ctx, ni), 256, 0, st>>>(ni, rs, lkey, lval);
     GK_LAUNCH(ctx);
     GK_TRY(radix_sort_segments(ctx, scr, 1, ni, &lkey, nullptr, &lval, 64, st));
@@ -421,7 +431,9 @@ geek_status assign_sets(geek_ctx *ctx, Scratch &scr, const int64_t *off, const u
     GK_TRY(scr.alloc(&nlight, 1));
     GK_TRY(scr.alloc(&nlent, 1));
     GK_CUDA(ctx, cudaMemsetAsync(is_heavy, 0, 8 * std::max<int64_t>(ni, 1), st));
+    GK_COUNT();
     k_mark_heavy<<<1, 64, 0, st>>>(nheavy, lval, rs, ikey, is_heavy, d_heavy);
+    GK_COUNT();
     k_light_flags<<<G(ctx, ni), 256, 0, st>>>(ni, rs, is_heavy, lrun, lent);
     GK_LAUNCH(ctx);
     GK_TRY(exclusive_scan_i64(ctx, scr, lrun, lrun_pos, ni, nlight, st));
@@ -433,6 +445,7 @@ geek_status assign_sets(geek_ctx *ctx, Scratch &scr, const int64_t *off, const u
     GK_TRY(scr.alloc(&d_litem, std::max<int64_t>(1, h_nlight)));
     GK_TRY(scr.alloc(&d_loff, h_nlight + 1));
     GK_TRY(scr.alloc(&d_lcentre, std::max<int64_t>(1, h_nlent)));
+    GK_COUNT();
     k_light_emit<<<G(ctx, ni), 256, 0, st>>>(ni, rs, ikey, pairs, is_heavy, lrun_pos, lent_pos, d_litem, d_loff,
                                              d_lcentre, nlent, h_nlight);
     GK_LAUNCH(ctx);
@@ -440,12 +453,14 @@ geek_status assign_sets(geek_ctx *ctx, Scratch &scr, const int64_t *off, const u
     int32_t *clen, *counts;
     GK_TRY(scr.alloc(&cmask, k));
     GK_TRY(scr.alloc(&clen, k));
+    GK_COUNT();
     k_heavy_masks<<<G(ctx, k), 256, 0, st>>>(k, coff, citems, d_heavy, nheavy, cmask, clen);
     GK_LAUNCH(ctx);
     const int blocks = ctx->num_sms * 4;
     const int64_t nwarps = (int64_t)blocks * 8;
     GK_TRY(scr.alloc(&counts, (size_t)nwarps * k));
     GK_CUDA(ctx, cudaMemsetAsync(counts, 0, sizeof(int32_t) * nwarps * k, st));
+    GK_COUNT();
     k_assign_jaccard<<<blocks, 256, 0, st>>>(n, off, items, k, clen, cmask, d_heavy, nheavy, d_litem, d_loff,
                                              h_nlight, d_lcentre, counts, labels);
     GK_LAUNCH(ctx);

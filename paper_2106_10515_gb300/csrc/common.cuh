@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <cstdio>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -16,6 +17,38 @@ struct geek_ctx {
     int device = 0;
     int num_sms = 0;
     std::string last_error;
+    // CUDA-event timing of phases and kernels (off by default)
+    bool timing = false;
+    std::map<std::string, std::pair<double, long long>> times;
+};
+
+// Brackets work on a stream with CUDA events when ctx->timing is on; the
+// elapsed time is added to ctx->times[name] when the bracket ends (which
+// waits for the end event).
+struct EvTimer {
+    geek_ctx *ctx;
+    const char *name;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr, b = nullptr;
+    EvTimer(geek_ctx *c, const char *nm, cudaStream_t s) : ctx(c), name(nm), st(s) {
+        if (ctx && ctx->timing && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
+            cudaEventRecord(a, st);
+    }
+    void stop() {
+        if (!b) return;
+        cudaEventRecord(b, st);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, a, b) == cudaSuccess) {
+            auto &e = ctx->times[name];
+            e.first += ms;
+            e.second += 1;
+        }
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        a = b = nullptr;
+    }
+    ~EvTimer() { stop(); }
 };
 
 // Per-call error plumbing: every failure sets ctx->last_error and returns.
@@ -38,6 +71,11 @@ geek_status set_error(geek_ctx *ctx, geek_status st, const char *fmt, ...);
     } while (0)
 
 #define GK_LAUNCH(ctx) GK_CUDA(ctx, cudaGetLastError())
+
+// Number of kernels this library has launched (process-wide), read through
+// geek_launch_count() by callers that account for device work.
+extern unsigned long long g_geek_launches;
+#define GK_COUNT() (__atomic_fetch_add(&g_geek_launches, 1ull, __ATOMIC_RELAXED))
 
 // Stream-ordered scratch owned by one API call; freed (stream-ordered) when
 // the call returns.

@@ -401,8 +401,11 @@ geek_status project_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t l
     if (d > 100000) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "d > 100000");
     float *anorm;
     GK_TRY(scr.alloc(&anorm, F));
+    GK_COUNT();
     k_row_norms<<<(F + 127) / 128, 128, 0, st>>>(a, F, d, anorm);
+    GK_COUNT();
     k_fill_i32<<<(F + 255) / 256, 256, 0, st>>>(fmin, F, INT32_MAX);
+    GK_COUNT();
     k_fill_i32<<<(F + 255) / 256, 256, 0, st>>>(fmax, F, INT32_MIN);
     GK_LAUNCH(ctx);
     if (n == 0) {
@@ -437,8 +440,12 @@ geek_status project_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t l
         GK_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
         A.flags = flags; A.n_flags = cnt; A.flag_cap = cap;
         const int64_t blocks = ceil_div(n, TR);
-        k_project_fp32<<<(unsigned)blocks, threads, smem, st>>>(A);
-        GK_LAUNCH(ctx);
+        {
+            EvTimer tk(ctx, "kernel.project_fp32", st);
+            GK_COUNT();
+            k_project_fp32<<<(unsigned)blocks, threads, smem, st>>>(A);
+            GK_LAUNCH(ctx);
+        }
         unsigned long long h_cnt = 0;
         GK_CUDA(ctx, cudaMemcpyAsync(&h_cnt, cnt, sizeof h_cnt, cudaMemcpyDeviceToHost, st));
         GK_CUDA(ctx, cudaStreamSynchronize(st));
@@ -448,6 +455,8 @@ geek_status project_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t l
         }
         *n_flagged = (int64_t)h_cnt;
         if (h_cnt) {
+            EvTimer tk(ctx, "kernel.recheck_fp64", st);
+            GK_COUNT();
             k_recheck_fp64<<<grid_for((int64_t)h_cnt, 128, ctx->num_sms), 128, 0, st>>>(
                 x, ldx, d, a, b, w, srp, F, flags, cnt, cap, codes, fmin, fmax, status);
             GK_LAUNCH(ctx);
@@ -471,6 +480,7 @@ geek_status minhash_rows(geek_ctx *ctx, int64_t n, const int64_t *off, int row_l
     const bool fixed = off == nullptr;
 #define MH_LAUNCH(FPL)                                                                             \
     do {                                                                                          \
+        GK_COUNT();                                                                               \
         if (fixed)                                                                                \
             k_minhash<FPL, true><<<blocks, threads, 0, st>>>(n, off, row_len, items, F, A, B, out, F); \
         else                                                                                      \
@@ -491,6 +501,7 @@ geek_status key_layout(geek_ctx *ctx, Scratch &scr, const int *fmin, const int *
     GK_TRY(scr.alloc(&tb, L));
     GK_TRY(scr.alloc(&status, 1));
     GK_CUDA(ctx, cudaMemsetAsync(status, 0, sizeof(int), st));
+    GK_COUNT();
     k_key_layout<<<1, 256, 0, st>>>(fmin, fmax, L, K1, K2, bits_dev, tb, status);
     GK_LAUNCH(ctx);
     tbits.assign(L, 0);
@@ -506,6 +517,7 @@ geek_status pack_keys(geek_ctx *ctx, int64_t n, int L, const int32_t *codes, int
                       const int *fmin, const int *bits, const uint32_t *mh, int F2, int K2,
                       uint64_t *klo, uint64_t *khi, cudaStream_t st) {
     if (n == 0) return GEEK_OK;
+    GK_COUNT();
     k_pack_keys<<<grid_for(n * L, 256, ctx->num_sms), 256, 0, st>>>(n, L, codes, F1, K1, fmin, bits, mh, F2, K2, klo, khi);
     GK_LAUNCH(ctx);
     return GEEK_OK;
@@ -517,7 +529,10 @@ geek_status group_tables(geek_ctx *ctx, Scratch &scr, int64_t n, int L, uint64_t
                          cudaStream_t st) {
     launch_iota_u32(ids, n * L, n, st);
     GK_LAUNCH(ctx);
-    GK_TRY(radix_sort_segments(ctx, scr, L, n, &klo, khi ? &khi : nullptr, &ids, nbits, st));
+    {
+        EvTimer tk(ctx, "hash.sort", st);
+        GK_TRY(radix_sort_segments(ctx, scr, L, n, &klo, khi ? &khi : nullptr, &ids, nbits, st));
+    }
     int32_t *rank;
     int64_t *run_start, *runs;
     GK_TRY(scr.alloc(&rank, (size_t)n * L));
@@ -525,6 +540,7 @@ geek_status group_tables(geek_ctx *ctx, Scratch &scr, int64_t n, int L, uint64_t
     GK_TRY(scr.alloc(&runs, L));
     GK_TRY(segment_runs(ctx, scr, L, n, klo, nbits > 64 ? khi : nullptr, rank, run_start, runs, st));
     if (n)
+        GK_COUNT();
         k_scatter_rank<<<grid_for(n * L, 256, ctx->num_sms), 256, 0, st>>>(n, L, ids, rank, obj_bucket);
     GK_LAUNCH(ctx);
     nb.assign(L, 0);
@@ -544,6 +560,7 @@ geek_status group_tables(geek_ctx *ctx, Scratch &scr, int64_t n, int L, uint64_t
     if (e != cudaSuccess) return set_error(ctx, GEEK_ERR_NOMEM, "bucket offsets: %s", cudaGetErrorString(e));
     int64_t maxnb = 1;
     for (auto v : nb) maxnb = std::max(maxnb, v);
+    GK_COUNT();
     k_bucket_off<<<dim3((unsigned)std::min<int64_t>(ceil_div(maxnb, 256), 4096), L), 256, 0, st>>>(
         n, L, run_start, d_base, runs, boff, NB);
     GK_LAUNCH(ctx);

@@ -246,6 +246,7 @@ geek_status make_bins(geek_ctx *ctx, Scratch &scr, int64_t nsets, const int64_t 
     GK_TRY(scr.alloc(&klo, nsets));
     if (Ks > 2) GK_TRY(scr.alloc(&khi, nsets));
     GK_TRY(scr.alloc(perm, nsets));
+    GK_COUNT();
     k_set_sig<<<G(ctx, nsets), 256, 0, st>>>(nsets, soff, sids, Ks, A, B, klo, khi, *perm);
     GK_LAUNCH(ctx);
     GK_TRY(radix_sort_segments(ctx, scr, 1, nsets, &klo, khi ? &khi : nullptr, perm, 32 * Ks, st));
@@ -268,6 +269,7 @@ geek_status vote_bins(geek_ctx *ctx, Scratch &scr, int64_t m, const uint32_t *pe
     GK_TRY(scr.alloc(&w, m));
     GK_TRY(scr.alloc(&woff, m));
     GK_TRY(scr.alloc(&T_dev, 1));
+    GK_COUNT();
     k_vote_weights<<<G(ctx, m), 256, 0, st>>>(m, rank, rs, perm, soff, w);
     GK_LAUNCH(ctx);
     GK_TRY(exclusive_scan_i64(ctx, scr, w, woff, m, T_dev, st));
@@ -287,6 +289,7 @@ geek_status vote_bins(geek_ctx *ctx, Scratch &scr, int64_t m, const uint32_t *pe
     }
     uint64_t *pairs;
     GK_TRY(scr.alloc(&pairs, T));
+    GK_COUNT();
     k_vote_expand<<<G(ctx, m), 256, 0, st>>>(m, rank, perm, woff, w, soff, sids, pairs);
     GK_LAUNCH(ctx);
     const int nbits = 32 + bit_length_u64((uint64_t)nbins);
@@ -305,8 +308,11 @@ geek_status vote_bins(geek_ctx *ctx, Scratch &scr, int64_t m, const uint32_t *pe
     GK_TRY(scr.alloc(&boffs, nbins));
     GK_TRY(scr.alloc(&set_idx, nbins));
     GK_TRY(scr.alloc(&nsets, 1));
+    GK_COUNT();
     k_vote_keep<<<G(ctx, NR), 256, 0, st>>>(nruns, prs, pairs, rs, keep, cnt);
+    GK_COUNT();
     k_bin_ok<<<G(ctx, nbins), 256, 0, st>>>(nbins, rs, cnt, delta, ok, len);
+    GK_COUNT();
     k_vote_sel<<<G(ctx, NR), 256, 0, st>>>(nruns, prs, pairs, keep, ok, sel);
     GK_LAUNCH(ctx);
     GK_TRY(exclusive_scan_i64(ctx, scr, sel, pos, NR, total, st));
@@ -319,7 +325,9 @@ geek_status vote_bins(geek_ctx *ctx, Scratch &scr, int64_t m, const uint32_t *pe
     out->nids = h_total;
     GK_TRY(scr.alloc(&out->off, h_nsets + 1));
     GK_TRY(scr.alloc(&out->ids, std::max<int64_t>(1, h_total)));
+    GK_COUNT();
     k_vote_emit<<<G(ctx, NR), 256, 0, st>>>(nruns, prs, pairs, sel, pos, out->ids);
+    GK_COUNT();
     k_compact_offsets<<<G(ctx, nbins), 256, 0, st>>>(nbins, ok, set_idx, boffs, out->off, nsets, total);
     GK_LAUNCH(ctx);
     return GEEK_OK;
@@ -333,12 +341,14 @@ geek_status gather_sets(geek_ctx *ctx, Scratch &scr, int64_t cnt, const int64_t 
     GK_TRY(scr.alloc(&len, std::max<int64_t>(cnt, 1)));
     GK_TRY(scr.alloc(&out->off, cnt + 1));
     GK_TRY(scr.alloc(&tot, 1));
+    GK_COUNT();
     k_gather_len<<<G(ctx, cnt), 256, 0, st>>>(cnt, idx, soff, len);
     GK_LAUNCH(ctx);
     GK_TRY(exclusive_scan_i64(ctx, scr, len, out->off, cnt, tot, st));
     GK_CUDA(ctx, cudaMemcpyAsync(out->off + cnt, tot, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
     GK_TRY(d2h_i64(ctx, tot, &out->nids, st));
     GK_TRY(scr.alloc(&out->ids, std::max<int64_t>(1, out->nids)));
+    GK_COUNT();
     k_gather_ids<<<G(ctx, cnt), 256, 0, st>>>(cnt, idx, soff, sids, out->off, out->ids);
     GK_LAUNCH(ctx);
     return GEEK_OK;
@@ -431,6 +441,7 @@ geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p,
         GK_TRY(scr.alloc(&has, nbins));
         GK_TRY(scr.alloc(&pos, nbins));
         GK_TRY(scr.alloc(&npick, 1));
+        GK_COUNT();
         k_dedup_pick<<<G(ctx, nbins), 256, 0, st>>>(nbins, rs, perm, ok, C.off, C.ids, pick, has);
         GK_LAUNCH(ctx);
         GK_TRY(exclusive_scan_i64(ctx, scr, has, pos, nbins, npick, st));
@@ -439,6 +450,7 @@ geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p,
         if (hp) {
             int64_t *idx;
             GK_TRY(scr.alloc(&idx, hp));
+            GK_COUNT();
             k_compact_idx<<<G(ctx, nbins), 256, 0, st>>>(nbins, has, pos, pick, idx);
             GK_LAUNCH(ctx);
             Csr P;
@@ -462,6 +474,7 @@ geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p,
     uint32_t *perm;
     GK_TRY(scr.alloc(&key, D.n));
     GK_TRY(scr.alloc(&perm, D.n));
+    GK_COUNT();
     k_prefix_key<<<G(ctx, D.n), 256, 0, st>>>(D.n, D.off, D.ids, key, perm);
     GK_LAUNCH(ctx);
     GK_TRY(radix_sort_segments(ctx, scr, 1, D.n, &key, nullptr, &perm, 64, st));
@@ -475,7 +488,9 @@ geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p,
     GK_TRY(scr.alloc(&keep, D.n));
     GK_TRY(scr.alloc(&kpos, D.n));
     GK_TRY(scr.alloc(&kt, 1));
+    GK_COUNT();
     k_prefix_fix<<<G(ctx, D.n), 256, 0, st>>>(D.n, rank, rs, perm, D.off, D.ids, order);
+    GK_COUNT();
     k_dup_flags<<<G(ctx, D.n), 256, 0, st>>>(D.n, order, D.off, D.ids, keep);
     GK_LAUNCH(ctx);
     GK_TRY(exclusive_scan_i64(ctx, scr, keep, kpos, D.n, kt, st));
@@ -483,6 +498,7 @@ geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p,
     GK_TRY(d2h_i64(ctx, kt, &k, st));
     int64_t *sel;
     GK_TRY(scr.alloc(&sel, k));
+    GK_COUNT();
     k_compact_idx<<<G(ctx, D.n), 256, 0, st>>>(D.n, keep, kpos, order, sel);
     GK_LAUNCH(ctx);
     Csr E;

@@ -290,6 +290,7 @@ geek_status set_error(geek_ctx *ctx, geek_status st, const char *fmt, ...) {
 void launch_iota_u32(uint32_t *v, int64_t n, int64_t period, cudaStream_t st) {
     if (n <= 0) return;
     int blocks = (int)std::min<int64_t>(ceil_div(n, 256), 1 << 16);
+    GK_COUNT();
     k_iota_u32<<<blocks, 256, 0, st>>>(v, n, period);
 }
 
@@ -316,8 +317,12 @@ geek_status radix_sort_segments(geek_ctx *ctx, Scratch &scr, int S, int64_t m, u
     const dim3 grid(tiles, S);
     for (int sh = 0; sh < nbits; sh += 8, passes++) {
         const int dsel = sh >= 64, s = sh & 63;
+        GK_COUNT();
         k_rs_hist<<<grid, RS_THREADS, 0, st>>>(dsel ? ahi : alo, s, m, tiles, counts);
+        GK_COUNT();
         k_seg_scan_u32<<<S, 1024, 0, st>>>(counts, (int64_t)256 * tiles, nullptr);
+        EvTimer tk(ctx, "kernel.rs_scatter", st);
+        GK_COUNT();
         if (hi && hv)
             k_rs_scatter<true, true><<<grid, RS_THREADS, 0, st>>>(alo, ahi, av, blo, bhi, bv, m, tiles, dsel, s, counts);
         else if (hi)
@@ -352,8 +357,11 @@ geek_status segment_runs(geek_ctx *ctx, Scratch &scr, int S, int64_t m, const ui
     uint32_t *tile_cnt;
     GK_TRY(scr.alloc(&tile_cnt, (size_t)S * tiles));
     const dim3 grid(tiles, S);
+    GK_COUNT();
     k_runs_count<<<grid, RS_THREADS, 0, st>>>(key_lo, key_hi, m, tiles, tile_cnt);
+    GK_COUNT();
     k_seg_scan_u32<<<S, 1024, 0, st>>>(tile_cnt, tiles, runs);
+    GK_COUNT();
     k_runs_emit<<<grid, RS_THREADS, 0, st>>>(key_lo, key_hi, m, tiles, tile_cnt, runs, rank, run_start);
     GK_LAUNCH(ctx);
     return GEEK_OK;
@@ -368,8 +376,11 @@ geek_status exclusive_scan_i64(geek_ctx *ctx, Scratch &scr, const int64_t *in, i
     const int64_t tiles = ceil_div(n, RS_TILE);
     int64_t *sums;
     GK_TRY(scr.alloc(&sums, tiles));
+    GK_COUNT();
     k_i64_tile_sum<<<(unsigned)tiles, RS_THREADS, 0, st>>>(in, n, sums);
+    GK_COUNT();
     k_i64_scan_small<<<1, 1024, 0, st>>>(sums, tiles, total_dev);
+    GK_COUNT();
     k_i64_tile_apply<<<(unsigned)tiles, RS_THREADS, 0, st>>>(in, out, n, sums);
     GK_LAUNCH(ctx);
     return GEEK_OK;

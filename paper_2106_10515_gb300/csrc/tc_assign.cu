@@ -441,7 +441,9 @@ geek_status assign_tc_bf16(geek_ctx *ctx, Scratch &scr, const float *x, int64_t 
     GK_TRY(scr.alloc(&xnorm, n));
     GK_TRY(scr.alloc(&cb, (size_t)kpad * Kp));
     GK_TRY(scr.alloc(&cn, kpad));
+    GK_COUNT();
     k_x_to_bf16<<<grid_for(n * 32, 256, ctx->num_sms), 256, 0, st>>>(x, ldx, n, d, Kp, xb, xnorm);
+    GK_COUNT();
     k_c_to_bf16<<<grid_for(kpad, 128, ctx->num_sms), 128, 0, st>>>(centres, k, kpad, d, Kp, cb, cn);
     GK_LAUNCH(ctx);
     // max |c| over the centres (upper bound)
@@ -476,8 +478,12 @@ geek_status assign_tc_bf16(geek_ctx *ctx, Scratch &scr, const float *x, int64_t 
     const size_t smem = 1024 + 2 * (size_t)TC_M * Kp * 2 + 2 * (size_t)TC_N * Kp * 2 + 16 * 8 + 128 * 3 * 4 + 64;
     GK_CUDA(ctx, cudaFuncSetAttribute(k_assign_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = (int)std::min<int64_t>(A.ntiles_r, ctx->num_sms);
-    k_assign_tc<<<grid, TC_THREADS, smem, st>>>(A);
-    GK_LAUNCH(ctx);
+    {
+        EvTimer tk(ctx, "kernel.assign_tc", st);
+        GK_COUNT();
+        k_assign_tc<<<grid, TC_THREADS, smem, st>>>(A);
+        GK_LAUNCH(ctx);
+    }
     int h_err = 0;
     GK_CUDA(ctx, cudaMemcpyAsync(&h_err, err, sizeof h_err, cudaMemcpyDeviceToHost, st));
     GK_CUDA(ctx, cudaStreamSynchronize(st));

@@ -65,7 +65,8 @@ class geek_assign_stats(C.Structure):
 EXPORTS = ["geek_ctx_create", "geek_ctx_destroy", "geek_last_error", "geek_version", "geek_hash",
            "geek_buckets_info_get", "geek_buckets_copy_out", "geek_buckets_free", "silk_seed",
            "silk_seeds_info", "silk_seeds_copy_out", "silk_seeds_free", "geek_assign",
-           "geek_assign_centers"]
+           "geek_assign_centers", "geek_timing_enable", "geek_timing_reset", "geek_timing_get",
+           "geek_launch_count"]
 
 _lib = None
 
@@ -96,9 +97,13 @@ def lib():
                               C.POINTER(geek_assign_stats), P]
     L.geek_assign_centers.argtypes = [P, C.POINTER(geek_data), P, C.c_int64,
                                       C.POINTER(geek_assign_params), P, C.POINTER(geek_assign_stats), P]
+    L.geek_timing_enable.argtypes = [P, C.c_int]
+    L.geek_timing_reset.argtypes = [P]
+    L.geek_timing_get.argtypes = [P, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+    L.geek_launch_count.restype = C.c_ulonglong
     for name in EXPORTS:
         f = getattr(L, name)
-        if name not in ("geek_last_error", "geek_version", "geek_ctx_destroy"):
+        if name not in ("geek_last_error", "geek_version", "geek_ctx_destroy", "geek_launch_count"):
             f.restype = st
     _lib = L
     return L
@@ -106,6 +111,10 @@ def lib():
 
 def version() -> str:
     return lib().geek_version().decode()
+
+
+def launch_count() -> int:
+    return int(lib().geek_launch_count())
 
 
 def _ptr(t):
@@ -227,6 +236,17 @@ class Context:
             raise GeekError(st, f"geek_ctx_create(device={device}) failed")
         self.h = h
         self._keep = []
+
+    def timing(self, on=True):
+        self._chk(lib().geek_timing_enable(self.h, 1 if on else 0))
+
+    def timing_reset(self):
+        self._chk(lib().geek_timing_reset(self.h))
+
+    def timing_get(self, name):
+        ms, cnt = C.c_double(), C.c_int64()
+        self._chk(lib().geek_timing_get(self.h, name.encode(), C.byref(ms), C.byref(cnt)))
+        return ms.value, cnt.value
 
     def _chk(self, st):
         if st != OK:
