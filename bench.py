@@ -30,6 +30,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+TIMED = ["hash", "silk", "assign", "hash.sort", "kernel.project_fp32", "kernel.recheck_fp64",
+         "kernel.rs_scatter", "kernel.assign_tc", "kernel.assign_fp32", "kernel.assign_recheck"]
 METRIC = "points/sec hash+assign (n=10M,d=128) mixed vs plain FP32; TC util/HBM GB/s"
 UNIT = "points/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -198,9 +200,7 @@ def run_ours(args):
         ms = e0.elapsed_time(e1) / steps
         ctx.timing(False)
         launches = geek.launch_count() - l0
-        tm = {name: ctx.timing_get(name) for name in
-              ["hash", "silk", "assign", "hash.sort", "kernel.project_fp32", "kernel.recheck_fp64",
-               "kernel.rs_scatter", "kernel.assign_tc", "kernel.assign_fp32", "kernel.assign_recheck"]}
+        tm = {name: ctx.timing_get(name) for name in TIMED}
         if world > 1:
             t = torch.tensor([ms], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -295,6 +295,8 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (x is 5.1 GB)", "parallelism": f"replicas x{world}",
                    "precision": args.precision},
         "phases_ms": {ph: tm[ph][0] / max(1, tm[ph][1]) for ph in ["hash", "silk", "assign", "hash.sort"]},
+        "kernels_ms_per_step": {kk: v[0] / args.steps for kk, v in tm.items() if kk.startswith("kernel.") and v[1]},
+        "kernel_launches_per_step": {kk: v[1] / args.steps for kk, v in tm.items() if kk.startswith("kernel.") and v[1]},
         "hash_assign_points_per_s": cfg.n * world / ((tm["hash"][0] / max(1, tm["hash"][1]) +
                                                      tm["assign"][0] / max(1, tm["assign"][1])) / 1e3),
         "recheck": {"hash_flagged_elems": main_info["n_flagged"], "assign_recheck_rows": main_info["n_recheck_rows"]},

@@ -221,6 +221,140 @@ __global__ void k_dup_flags(int64_t ns, const int64_t *__restrict__ order, const
         keep[p] = p == 0 || set_cmp(sids, soff, order[p - 1], order[p]) != 0;
 }
 
+// ---- virtual buckets ---------------------------------------------------------
+// Identical buckets always share a bin and contribute identically to its
+// vote, so the main pass works on distinct "virtual buckets" with a
+// multiplicity: every object whose bucket is a singleton in m >= 1 tables
+// gives one virtual bucket {i} of weight m; every bucket of two or more
+// objects is its own virtual bucket of weight 1.  A bin's size |Bin| is the
+// total weight of its virtual buckets and an object's count the total weight
+// of those containing it, exactly as in Alg. 4 over the original buckets.
+__global__ void k_vb_count(int64_t NB, const int64_t *__restrict__ boff, const uint32_t *__restrict__ mem,
+                           int32_t *__restrict__ mult, int64_t *__restrict__ ns_flag) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < NB; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t sz = boff[g + 1] - boff[g];
+        if (sz == 1) atomicAdd(&mult[mem[boff[g]]], 1);
+        ns_flag[g] = sz >= 2;
+    }
+}
+
+__global__ void k_pos_flag(int64_t n, const int32_t *__restrict__ mult, int64_t *__restrict__ f) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        f[i] = mult[i] > 0;
+}
+
+__global__ void k_vb_fill_s(int64_t n, const int32_t *__restrict__ mult, const int64_t *__restrict__ pos,
+                            int64_t *__restrict__ vsz, int32_t *__restrict__ vw, int64_t *__restrict__ vsrc) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (mult[i] > 0) {
+            const int64_t v = pos[i];
+            vsz[v] = 1;
+            vw[v] = mult[i];
+            vsrc[v] = i;
+        }
+}
+
+__global__ void k_vb_fill_n(int64_t NB, const int64_t *__restrict__ boff, const int64_t *__restrict__ ns_flag,
+                            const int64_t *__restrict__ pos, int64_t base, int64_t *__restrict__ vsz,
+                            int32_t *__restrict__ vw, int64_t *__restrict__ vsrc) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < NB; g += (int64_t)gridDim.x * blockDim.x)
+        if (ns_flag[g]) {
+            const int64_t v = base + pos[g];
+            vsz[v] = boff[g + 1] - boff[g];
+            vw[v] = 1;
+            vsrc[v] = g;
+        }
+}
+
+__global__ void k_vb_members(int64_t NV, int64_t NS1, const int64_t *__restrict__ vsrc,
+                             const int64_t *__restrict__ voff, const int64_t *__restrict__ boff,
+                             const uint32_t *__restrict__ mem, uint32_t *__restrict__ vmem) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < NV; v += (int64_t)gridDim.x * blockDim.x) {
+        if (v < NS1) {
+            vmem[voff[v]] = (uint32_t)vsrc[v];
+        } else {
+            const int64_t g = vsrc[v];
+            int64_t o = voff[v];
+            for (int64_t q = boff[g]; q < boff[g + 1]; q++) vmem[o++] = mem[q];
+        }
+    }
+}
+
+// per bin: number of virtual buckets and total weight |Bin|
+__global__ void k_bin_weight(int64_t nbins, const int64_t *__restrict__ rs, const uint32_t *__restrict__ perm,
+                             const int32_t *__restrict__ vw, int64_t *__restrict__ bw) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nbins; r += (int64_t)gridDim.x * blockDim.x) {
+        int64_t s = 0;
+        for (int64_t p = rs[r]; p < rs[r + 1]; p++) s += vw[perm[p]];
+        bw[r] = s;
+    }
+}
+
+// bins of exactly one virtual bucket with |Bin| >= 2: every member occurs in
+// all |Bin| copies, so C_shared is the whole bucket
+__global__ void k_single_bins(int64_t nbins, const int64_t *__restrict__ rs, const uint32_t *__restrict__ perm,
+                              const int64_t *__restrict__ bw, const int64_t *__restrict__ voff, int delta,
+                              int64_t *__restrict__ has, int64_t *__restrict__ pick) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nbins; r += (int64_t)gridDim.x * blockDim.x) {
+        const bool one = rs[r + 1] - rs[r] == 1;
+        const int64_t v = perm[rs[r]];
+        const bool h = one && bw[r] >= 2 && voff[v + 1] - voff[v] >= delta;
+        has[r] = h;
+        pick[r] = v;
+    }
+}
+
+// weighted vote over bins of >= 2 virtual buckets
+__global__ void k_wvote_weights(int64_t m, const int32_t *__restrict__ rank, const int64_t *__restrict__ rs,
+                                const uint32_t *__restrict__ perm, const int64_t *__restrict__ voff,
+                                int64_t *__restrict__ w) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = rank[p];
+        const uint32_t v = perm[p];
+        w[p] = bin_size(rs, r) >= 2 ? voff[v + 1] - voff[v] : 0;
+    }
+}
+
+__global__ void k_wvote_expand(int64_t m, const int32_t *__restrict__ rank, const uint32_t *__restrict__ perm,
+                               const int64_t *__restrict__ woff, const int64_t *__restrict__ w,
+                               const int64_t *__restrict__ voff, const uint32_t *__restrict__ vmem,
+                               const int32_t *__restrict__ vw, uint64_t *__restrict__ pairs,
+                               uint32_t *__restrict__ pw) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
+        if (w[p] == 0) continue;
+        const uint64_t r = (uint64_t)rank[p];
+        const uint32_t v = perm[p];
+        int64_t o = woff[p];
+        for (int64_t q = voff[v]; q < voff[v + 1]; q++) {
+            pw[o] = (uint32_t)vw[v];
+            pairs[o++] = (r << 32) | vmem[q];
+        }
+    }
+}
+
+__global__ void k_wvote_keep(const int64_t *__restrict__ nruns_dev, const int64_t *__restrict__ prs,
+                             const uint64_t *__restrict__ pairs, const uint32_t *__restrict__ pw,
+                             const int64_t *__restrict__ bw, int64_t *__restrict__ keep, int64_t *__restrict__ cnt) {
+    const int64_t nr = *nruns_dev;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += (int64_t)gridDim.x * blockDim.x) {
+        int64_t c = 0;
+        for (int64_t q = prs[r]; q < prs[r + 1]; q++) c += pw[q];
+        const int64_t bin = (int64_t)(pairs[prs[r]] >> 32);
+        const bool k = 2 * c > bw[bin];
+        keep[r] = k;
+        if (k) atomicAdd((unsigned long long *)&cnt[bin], 1ull);
+    }
+}
+
+__global__ void k_wbin_ok(int64_t nbins, const int64_t *__restrict__ rs, const int64_t *__restrict__ cnt, int delta,
+                          int64_t *__restrict__ ok, int64_t *__restrict__ len) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nbins; b += (int64_t)gridDim.x * blockDim.x) {
+        const bool o = bin_size(rs, b) >= 2 && cnt[b] >= delta;
+        ok[b] = o;
+        len[b] = o ? cnt[b] : 0;
+    }
+}
+
 struct Csr {
     int64_t n = 0;        // sets
     int64_t nids = 0;     // members
@@ -333,6 +467,75 @@ geek_status vote_bins(geek_ctx *ctx, Scratch &scr, int64_t m, const uint32_t *pe
     return GEEK_OK;
 }
 
+// Weighted majority vote of every bin holding >= 2 virtual buckets; emits
+// C_shared of the bins whose vote has at least delta objects.
+geek_status wvote_bins(geek_ctx *ctx, Scratch &scr, int64_t m, const uint32_t *perm, const int32_t *rank,
+                       const int64_t *rs, int64_t nbins, const int64_t *voff, const uint32_t *vmem,
+                       const int32_t *vw, const int64_t *bw, int delta, Csr *out, cudaStream_t st) {
+    int64_t *w, *woff, *T_dev;
+    GK_TRY(scr.alloc(&w, m));
+    GK_TRY(scr.alloc(&woff, m));
+    GK_TRY(scr.alloc(&T_dev, 1));
+    GK_COUNT();
+    k_wvote_weights<<<G(ctx, m), 256, 0, st>>>(m, rank, rs, perm, voff, w);
+    GK_LAUNCH(ctx);
+    GK_TRY(exclusive_scan_i64(ctx, scr, w, woff, m, T_dev, st));
+    int64_t T = 0;
+    GK_TRY(d2h_i64(ctx, T_dev, &T, st));
+    out->n = 0;
+    out->nids = 0;
+    if (T == 0) return GEEK_OK;
+    uint64_t *pairs;
+    uint32_t *pw;
+    GK_TRY(scr.alloc(&pairs, T));
+    GK_TRY(scr.alloc(&pw, T));
+    GK_COUNT();
+    k_wvote_expand<<<G(ctx, m), 256, 0, st>>>(m, rank, perm, woff, w, voff, vmem, vw, pairs, pw);
+    GK_LAUNCH(ctx);
+    GK_TRY(radix_sort_segments(ctx, scr, 1, T, &pairs, nullptr, &pw, 32 + bit_length_u64((uint64_t)nbins), st));
+    int64_t *prs, *nruns;
+    GK_TRY(scr.alloc(&prs, T + 1));
+    GK_TRY(scr.alloc(&nruns, 1));
+    GK_TRY(segment_runs(ctx, scr, 1, T, pairs, nullptr, nullptr, prs, nruns, st));
+    int64_t NR = 0;
+    GK_TRY(d2h_i64(ctx, nruns, &NR, st));
+    int64_t *keep, *sel, *pos, *total, *boffs, *set_idx, *nsets, *cnt, *ok, *len;
+    GK_TRY(scr.alloc(&keep, NR));
+    GK_TRY(scr.alloc(&sel, NR));
+    GK_TRY(scr.alloc(&pos, NR));
+    GK_TRY(scr.alloc(&total, 1));
+    GK_TRY(scr.alloc(&boffs, nbins));
+    GK_TRY(scr.alloc(&set_idx, nbins));
+    GK_TRY(scr.alloc(&nsets, 1));
+    GK_TRY(scr.alloc(&cnt, nbins));
+    GK_TRY(scr.alloc(&ok, nbins));
+    GK_TRY(scr.alloc(&len, nbins));
+    GK_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(int64_t) * nbins, st));
+    GK_COUNT();
+    k_wvote_keep<<<G(ctx, NR), 256, 0, st>>>(nruns, prs, pairs, pw, bw, keep, cnt);
+    GK_COUNT();
+    k_wbin_ok<<<G(ctx, nbins), 256, 0, st>>>(nbins, rs, cnt, delta, ok, len);
+    GK_COUNT();
+    k_vote_sel<<<G(ctx, NR), 256, 0, st>>>(nruns, prs, pairs, keep, ok, sel);
+    GK_LAUNCH(ctx);
+    GK_TRY(exclusive_scan_i64(ctx, scr, sel, pos, NR, total, st));
+    GK_TRY(exclusive_scan_i64(ctx, scr, len, boffs, nbins, nullptr, st));
+    GK_TRY(exclusive_scan_i64(ctx, scr, ok, set_idx, nbins, nsets, st));
+    int64_t h_total = 0, h_nsets = 0;
+    GK_TRY(d2h_i64(ctx, total, &h_total, st));
+    GK_TRY(d2h_i64(ctx, nsets, &h_nsets, st));
+    out->n = h_nsets;
+    out->nids = h_total;
+    GK_TRY(scr.alloc(&out->off, h_nsets + 1));
+    GK_TRY(scr.alloc(&out->ids, std::max<int64_t>(1, h_total)));
+    GK_COUNT();
+    k_vote_emit<<<G(ctx, NR), 256, 0, st>>>(nruns, prs, pairs, sel, pos, out->ids);
+    GK_COUNT();
+    k_compact_offsets<<<G(ctx, nbins), 256, 0, st>>>(nbins, ok, set_idx, boffs, out->off, nsets, total);
+    GK_LAUNCH(ctx);
+    return GEEK_OK;
+}
+
 // gathers the listed sets (device index list) into a new CSR
 geek_status gather_sets(geek_ctx *ctx, Scratch &scr, int64_t cnt, const int64_t *idx,
                         const int64_t *soff, const uint32_t *sids, Csr *out, cudaStream_t st) {
@@ -396,18 +599,88 @@ geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p,
     const int Ks = p->Ks, Ls = p->Ls, delta = p->delta;
     const int64_t NB = b->NB;
     std::vector<Csr> parts;
-    // ---- Alg. 4: Ls SILK tables over all buckets -------------------------
-    for (int t = 0; t < Ls && NB > 0; t++) {
+    // ---- virtual buckets (see k_vb_count) -------------------------------------
+    const int64_t n = b->n;
+    int32_t *mult;
+    int64_t *ns_flag, *s_flag, *s_pos, *n_pos, *d_ns1, *d_ns2;
+    GK_TRY(scr.alloc(&mult, std::max<int64_t>(n, 1)));
+    GK_TRY(scr.alloc(&ns_flag, std::max<int64_t>(NB, 1)));
+    GK_TRY(scr.alloc(&s_flag, std::max<int64_t>(n, 1)));
+    GK_TRY(scr.alloc(&s_pos, std::max<int64_t>(n, 1)));
+    GK_TRY(scr.alloc(&n_pos, std::max<int64_t>(NB, 1)));
+    GK_TRY(scr.alloc(&d_ns1, 1));
+    GK_TRY(scr.alloc(&d_ns2, 1));
+    GK_CUDA(ctx, cudaMemsetAsync(mult, 0, sizeof(int32_t) * std::max<int64_t>(n, 1), st));
+    GK_COUNT();
+    k_vb_count<<<G(ctx, NB), 256, 0, st>>>(NB, b->boff, b->members, mult, ns_flag);
+    GK_COUNT();
+    k_pos_flag<<<G(ctx, n), 256, 0, st>>>(n, mult, s_flag);
+    GK_LAUNCH(ctx);
+    GK_TRY(exclusive_scan_i64(ctx, scr, s_flag, s_pos, n, d_ns1, st));
+    GK_TRY(exclusive_scan_i64(ctx, scr, ns_flag, n_pos, NB, d_ns2, st));
+    int64_t NS1 = 0, NS2 = 0;
+    GK_TRY(d2h_i64(ctx, d_ns1, &NS1, st));
+    GK_TRY(d2h_i64(ctx, d_ns2, &NS2, st));
+    const int64_t NV = NS1 + NS2;
+    int64_t *vsz, *vsrc, *voff, *d_vtot;
+    int32_t *vw;
+    uint32_t *vmem;
+    GK_TRY(scr.alloc(&vsz, std::max<int64_t>(NV, 1)));
+    GK_TRY(scr.alloc(&vsrc, std::max<int64_t>(NV, 1)));
+    GK_TRY(scr.alloc(&vw, std::max<int64_t>(NV, 1)));
+    GK_TRY(scr.alloc(&voff, NV + 1));
+    GK_TRY(scr.alloc(&d_vtot, 1));
+    GK_COUNT();
+    k_vb_fill_s<<<G(ctx, n), 256, 0, st>>>(n, mult, s_pos, vsz, vw, vsrc);
+    GK_COUNT();
+    k_vb_fill_n<<<G(ctx, NB), 256, 0, st>>>(NB, b->boff, ns_flag, n_pos, NS1, vsz, vw, vsrc);
+    GK_LAUNCH(ctx);
+    GK_TRY(exclusive_scan_i64(ctx, scr, vsz, voff, NV, d_vtot, st));
+    GK_CUDA(ctx, cudaMemcpyAsync(voff + NV, d_vtot, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+    int64_t VT = 0;
+    GK_TRY(d2h_i64(ctx, d_vtot, &VT, st));
+    GK_TRY(scr.alloc(&vmem, std::max<int64_t>(VT, 1)));
+    GK_COUNT();
+    k_vb_members<<<G(ctx, NV), 256, 0, st>>>(NV, NS1, vsrc, voff, b->boff, b->members, vmem);
+    GK_LAUNCH(ctx);
+
+    // ---- Alg. 4: Ls SILK tables over the (virtual) buckets ------------------
+    for (int t = 0; t < Ls && NV > 0; t++) {
         Scratch tscr(ctx, st);  // per-table temporaries
         uint32_t *perm;
         int32_t *rank;
         int64_t *rs, nbins = 0;
-        GK_TRY(make_bins(ctx, tscr, NB, b->boff, b->members, Ks, p->mh_a + (int64_t)t * Ks,
-                         p->mh_b + (int64_t)t * Ks, &perm, &rank, &rs, &nbins, st));
-        Csr c;
-        int64_t *ok;
-        GK_TRY(vote_bins(ctx, tscr, NB, perm, rank, rs, nbins, b->boff, b->members, delta, &c, &ok, st));
-        if (c.n) {
+        GK_TRY(make_bins(ctx, tscr, NV, voff, vmem, Ks, p->mh_a + (int64_t)t * Ks, p->mh_b + (int64_t)t * Ks,
+                         &perm, &rank, &rs, &nbins, st));
+        int64_t *bw, *has, *pick, *hpos, *d_nh;
+        GK_TRY(tscr.alloc(&bw, nbins));
+        GK_TRY(tscr.alloc(&has, nbins));
+        GK_TRY(tscr.alloc(&pick, nbins));
+        GK_TRY(tscr.alloc(&hpos, nbins));
+        GK_TRY(tscr.alloc(&d_nh, 1));
+        GK_COUNT();
+        k_bin_weight<<<G(ctx, nbins), 256, 0, st>>>(nbins, rs, perm, vw, bw);
+        GK_COUNT();
+        k_single_bins<<<G(ctx, nbins), 256, 0, st>>>(nbins, rs, perm, bw, voff, delta, has, pick);
+        GK_LAUNCH(ctx);
+        GK_TRY(exclusive_scan_i64(ctx, tscr, has, hpos, nbins, d_nh, st));
+        int64_t nh = 0;
+        GK_TRY(d2h_i64(ctx, d_nh, &nh, st));
+        std::vector<Csr> tparts;
+        if (nh) {
+            int64_t *idx;
+            GK_TRY(tscr.alloc(&idx, nh));
+            GK_COUNT();
+            k_compact_idx<<<G(ctx, nbins), 256, 0, st>>>(nbins, has, hpos, pick, idx);
+            GK_LAUNCH(ctx);
+            Csr c1;
+            GK_TRY(gather_sets(ctx, tscr, nh, idx, voff, vmem, &c1, st));
+            tparts.push_back(c1);
+        }
+        Csr c2;
+        GK_TRY(wvote_bins(ctx, tscr, NV, perm, rank, rs, nbins, voff, vmem, vw, bw, delta, &c2, st));
+        if (c2.n) tparts.push_back(c2);
+        for (auto &c : tparts) {
             // move the table's C_shared sets into the outer scratch
             Csr keep;
             keep.n = c.n;
