@@ -225,6 +225,40 @@ geek_status geek_assign_centers(geek_ctx *ctx, const geek_data *data, const doub
                                 int64_t k, const geek_assign_params *p, int32_t *labels,
                                 geek_assign_stats *stats, geek_stream stream);
 
+/* ---- allocation-free dense assignment ------------------------------------ */
+
+/* The paper has no counterpart of this entry point: it serves callers that
+ * cannot allocate device memory during the call, for example a serving loop
+ * whose memory is fully reserved up front by another allocator (a framework's
+ * caching pool holding all free memory, where cudaMalloc would fail), or code
+ * that must not pay the device-wide synchronisation an allocation or free
+ * can imply.
+ *
+ * geek_assign_centers_noalloc computes exactly what geek_assign_centers
+ * computes with GEEK_PREC_FP32 (same labels: the FP64 argmin of Eq. 1, ties to
+ * the smallest index) but allocates nothing: no cudaMalloc, cudaFree or
+ * allocating library routine.  Its scratch (the FP32 centres and their norms)
+ * is one fixed device array of GEEK_NOALLOC_SCRATCH_BYTES that every GPU which
+ * loads this library holds until the process exits.  Arguments are device
+ * pointers on the current device: x (n x d float32, row stride ldx), centers
+ * (k x d float64), labels (n int32, also used to mark undecided rows while the
+ * call runs).  No context is needed; the call is stream-ordered on `stream`.
+ *  - The first call on a device does a one-time set-up with that device
+ *    current (it looks up the scratch array's device address); make that
+ *    first call before any stream capture.
+ *  - Every call shares the one scratch array and leaves the last call's
+ *    contents in it: calls that overlap on the GPU (different streams or
+ *    threads without ordering) race and give wrong results.
+ *  - Returns GEEK_ERR_INVALID for bad arguments and GEEK_ERR_UNSUPPORTED when
+ *    d > 256, k > GEEK_NOALLOC_MAX_K or k*d > GEEK_NOALLOC_MAX_KD (the
+ *    scratch limit); GEEK_ERR_CUDA if a CUDA call fails. */
+#define GEEK_NOALLOC_MAX_K 65536
+#define GEEK_NOALLOC_MAX_KD 1048576
+#define GEEK_NOALLOC_SCRATCH_BYTES (4 * GEEK_NOALLOC_MAX_KD + 4 * GEEK_NOALLOC_MAX_K + 256)
+geek_status geek_assign_centers_noalloc(const float *x, int64_t n, int32_t d, int64_t ldx,
+                                        const double *centers, int64_t k, int32_t *labels,
+                                        geek_stream stream);
+
 /* ---- tracing -------------------------------------------------------------- */
 
 /* When on, every phase (names "hash", "silk", "assign") and the main kernels

@@ -66,7 +66,7 @@ EXPORTS = ["geek_ctx_create", "geek_ctx_destroy", "geek_last_error", "geek_versi
            "geek_buckets_info_get", "geek_buckets_copy_out", "geek_buckets_free", "silk_seed",
            "silk_seeds_info", "silk_seeds_copy_out", "silk_seeds_free", "geek_assign",
            "geek_assign_centers", "geek_timing_enable", "geek_timing_reset", "geek_timing_get",
-           "geek_launch_count"]
+           "geek_launch_count", "geek_assign_centers_noalloc"]
 
 _lib = None
 
@@ -101,6 +101,7 @@ def lib():
     L.geek_timing_reset.argtypes = [P]
     L.geek_timing_get.argtypes = [P, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
     L.geek_launch_count.restype = C.c_ulonglong
+    L.geek_assign_centers_noalloc.argtypes = [P, C.c_int64, C.c_int32, C.c_int64, P, C.c_int64, P, P]
     for name in EXPORTS:
         f = getattr(L, name)
         if name not in ("geek_last_error", "geek_version", "geek_ctx_destroy", "geek_launch_count"):
