@@ -38,6 +38,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 # FP32 SIMT peak: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (nominal)
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP32_NOTE = "derived FP32 SIMT nominal (152 SM x 128 lanes x 2 flop x 2.07 GHz)"
 
 
 def peaks():
@@ -107,6 +108,8 @@ class Clocks:
 def workload(args):
     import synth
     over = {} if args.n is None else dict(n=args.n, n_comp=max(50, min(20000, args.n // 500)))
+    if args.comps is not None:
+        over["n_comp"] = args.comps
     cfg = synth.config(args.workload, **over)
     t0 = time.time()
     wl = synth.make(cfg)
@@ -124,20 +127,6 @@ def traffic_for(kernel):
     if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["source_sha256"]:
         return None
     return rec["dram_bytes_per_launch_full_size"]
-
-
-def kernel_work(name, cfg, k, nb_total):
-    """Algorithmic work of one launch: (bound, amount, unit)."""
-    n, d, F, L = cfg.n, cfg.d, cfg.K * cfg.L, cfg.L
-    if name == "kernel.assign_tc":
-        return "tensor", 2.0 * n * k * d, "flop"
-    if name == "kernel.assign_fp32":
-        return "alu", 2.0 * n * k * d, "flop"
-    if name == "kernel.project_fp32":
-        return "alu", 2.0 * n * F * d, "flop"
-    if name == "kernel.rs_scatter":
-        return "hbm", None, "byte"  # per-launch bytes depend on the sort; filled by caller
-    return None, None, None
 
 
 def run_ours(args):
@@ -242,32 +231,25 @@ def run_ours(args):
                "d2h_bytes_per_step": int(lh.numel() * 4), "ms_per_step": e2e_s * 1e3}
 
     pk, pk_kind = peaks()
-    # dominant kernel of the timed step
-    kern = {kname: v for kname, v in tm.items() if kname.startswith("kernel.") and v[1] > 0}
-    dom = max(kern, key=lambda kk: kern[kk][0]) if kern else None
-    roof = None
-    if dom:
-        tot_ms, cnt = kern[dom]
-        avg_s = tot_ms / cnt / 1e3
-        bound, work, unit = kernel_work(dom, cfg, k, main_info["n_buckets"])
-        if bound == "tensor":
-            peak = pk["bf16_tflops_sustained"]
-            roof = {"kernel": dom, "bound": "tensor", "achieved": work / avg_s / 1e12, "peak": peak,
-                    "unit": "TFLOP/s", "peak_source": f"{pk_kind} bf16_tflops_sustained"}
-        elif bound == "alu":
-            roof = {"kernel": dom, "bound": "alu", "achieved": work / avg_s / 1e12, "peak": FP32_SIMT_TFLOPS,
-                    "unit": "TFLOP/s", "peak_source": "derived FP32 SIMT nominal (152 SM x 128 x 2 x 2.07 GHz)"}
-        elif bound == "hbm":
-            # one scatter pass moves keys (8 B, +8 B above 64 bits) and a 4-byte id in and out
-            kw = 16 if main_info["key_bits"] > 64 else 8
-            work = 2.0 * (kw + 4) * cfg.n * cfg.L
-            roof = {"kernel": dom, "bound": "hbm", "achieved": work / avg_s / 1e9, "peak": pk["hbm_gbs"],
-                    "unit": "GB/s", "peak_source": f"{pk_kind} hbm_gbs"}
-        if roof:
-            roof["frac"] = roof["achieved"] / roof["peak"]
-            roof["avg_launch_ms"] = avg_s * 1e3
-            roof["launches_timed"] = cnt
-            roof["traffic"] = traffic_for(dom)
+    # roofline of every timed kernel from the work the library recorded for
+    # it; the dominant one (largest share of the step) is the headline
+    bounds = {"kernel.assign_tc": ("tensor", 1e12, "TFLOP/s", pk["bf16_tflops_sustained"],
+                                   f"{pk_kind} bf16_tflops_sustained"),
+              "kernel.assign_fp32": ("alu", 1e12, "TFLOP/s", FP32_SIMT_TFLOPS, FP32_NOTE),
+              "kernel.project_fp32": ("alu", 1e12, "TFLOP/s", FP32_SIMT_TFLOPS, FP32_NOTE),
+              "kernel.rs_scatter": ("hbm", 1e9, "GB/s", pk["hbm_gbs"], f"{pk_kind} hbm_gbs")}
+    roofs = {}
+    for kname, (tot_ms, cnt, work) in tm.items():
+        if kname not in bounds or cnt == 0 or work <= 0:
+            continue
+        bound, scale, unit, peak, src = bounds[kname]
+        ach = work / (tot_ms / 1e3) / scale  # work-weighted: total work over total time
+        roofs[kname] = {"kernel": kname, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
+                        "frac": ach / peak, "peak_source": src, "avg_launch_ms": tot_ms / cnt,
+                        "launches_timed": cnt, "share_of_step": tot_ms / args.steps / ms,
+                        "traffic": traffic_for(kname)}
+    dom = max(roofs, key=lambda kk: tm[kk][0]) if roofs else None
+    roof = roofs.get(dom)
 
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
@@ -303,6 +285,7 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": cl,
         "roofline": roof,
+        "roofline_all": roofs,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "generate_s": t_gen,
@@ -311,6 +294,8 @@ def run_ours(args):
         line[f"{other}_assign_variant"] = {
             "value": cfg.n * world / (ms_other / 1e3), "ms_per_step": ms_other,
             "assign_ms": tm_other["assign"][0] / max(1, tm_other["assign"][1]),
+            "assign_kernel_tflops": {kk: v[2] / (v[0] / 1e3) / 1e12 for kk, v in tm_other.items()
+                                     if kk in ("kernel.assign_fp32", "kernel.assign_tc") and v[1] and v[0] > 0},
             "hash_assign_points_per_s": cfg.n * world / ((tm_other["hash"][0] / max(1, tm_other["hash"][1]) +
                                                           tm_other["assign"][0] / max(1, tm_other["assign"][1])) / 1e3)}
     if rank == 0:
@@ -370,6 +355,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--n", type=int, default=None, help="override n (smaller runs)")
+    ap.add_argument("--comps", type=int, default=None, help="override the number of mixture components")
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--cpu-rows", type=int, default=4096)
     ap.add_argument("--skip-other", action="store_true")

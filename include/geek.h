@@ -262,15 +262,19 @@ geek_status geek_assign_centers_noalloc(const float *x, int64_t n, int32_t d, in
 /* ---- tracing -------------------------------------------------------------- */
 
 /* When on, every phase (names "hash", "silk", "assign") and the main kernels
- * ("kernel.project_fp32", "kernel.recheck_fp64", "kernel.rs_scatter",
- * "kernel.assign_fp32", "kernel.assign_tc", "kernel.assign_recheck", and the
- * sort phase "hash.sort") are bracketed by CUDA events on the call's stream;
- * each bracket waits for its end event, so timing adds synchronisation.
- * Off by default. */
+ * are bracketed by CUDA events on the call's stream; each bracket waits for
+ * its end event, so timing adds synchronisation.  Off by default.  Kernel
+ * brackets also record their algorithmic work: "kernel.project_fp32" and
+ * "kernel.assign_fp32" / "kernel.assign_tc" in flops (2 d per output element),
+ * "kernel.recheck_fp64" in FP64 flops (2 d per rechecked element),
+ * "kernel.rs_scatter" in bytes (each key word, and the value, read once and
+ * written once); "hash.sort" and "kernel.assign_recheck" record time only. */
 geek_status geek_timing_enable(geek_ctx *ctx, int on);
 geek_status geek_timing_reset(geek_ctx *ctx);
-/* Total milliseconds and bracket count recorded under `name` (0 if none). */
-geek_status geek_timing_get(const geek_ctx *ctx, const char *name, double *total_ms, int64_t *count);
+/* Total milliseconds, bracket count and recorded work under `name` (0 if
+ * none).  Any output pointer may be NULL. */
+geek_status geek_timing_get(const geek_ctx *ctx, const char *name, double *total_ms, int64_t *count,
+                            double *total_work);
 /* Kernels launched by this library in this process so far. */
 unsigned long long geek_launch_count(void);
 

@@ -192,11 +192,14 @@ geek_status geek_timing_reset(geek_ctx *ctx) {
     return GEEK_OK;
 }
 
-geek_status geek_timing_get(const geek_ctx *ctx, const char *name, double *total_ms, int64_t *count) {
+geek_status geek_timing_get(const geek_ctx *ctx, const char *name, double *total_ms, int64_t *count,
+                            double *total_work) {
     if (!ctx || !name) return GEEK_ERR_INVALID;
     auto it = ctx->times.find(name);
-    if (total_ms) *total_ms = it == ctx->times.end() ? 0.0 : it->second.first;
-    if (count) *count = it == ctx->times.end() ? 0 : it->second.second;
+    const bool f = it != ctx->times.end();
+    if (total_ms) *total_ms = f ? it->second.ms : 0.0;
+    if (count) *count = f ? it->second.count : 0;
+    if (total_work) *total_work = f ? it->second.work : 0.0;
     return GEEK_OK;
 }
 

@@ -373,6 +373,7 @@ geek_status assign_dense_centres(geek_ctx *ctx, Scratch &scr, const float *x, in
         const size_t smem = (size_t)d * AS_TR * sizeof(float) + (size_t)AS_KC * AS_TC * sizeof(float);
         GK_CUDA(ctx, cudaFuncSetAttribute(k_assign_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         EvTimer tk(ctx, "kernel.assign_fp32", st);
+        tk.work = 2.0 * (double)n * (double)k * (double)d;
         GK_COUNT();
         k_assign_fp32<<<(unsigned)ceil_div(n, AS_TR), 256, smem, st>>>(x, ldx, n, d, c32, cn, k, cmax, labels,
                                                                          flag_rows, n_flag);

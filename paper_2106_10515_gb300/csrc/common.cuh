@@ -19,7 +19,12 @@ struct geek_ctx {
     std::string last_error;
     // CUDA-event timing of phases and kernels (off by default)
     bool timing = false;
-    std::map<std::string, std::pair<double, long long>> times;
+    struct Timed {
+        double ms = 0.0;
+        long long count = 0;
+        double work = 0.0;  // algorithmic bytes or flops of the bracketed work
+    };
+    std::map<std::string, Timed> times;
 };
 
 // Brackets work on a stream with CUDA events when ctx->timing is on; the
@@ -30,6 +35,7 @@ struct EvTimer {
     const char *name;
     cudaStream_t st;
     cudaEvent_t a = nullptr, b = nullptr;
+    double work = 0.0;
     EvTimer(geek_ctx *c, const char *nm, cudaStream_t s) : ctx(c), name(nm), st(s) {
         if (ctx && ctx->timing && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
             cudaEventRecord(a, st);
@@ -41,8 +47,9 @@ struct EvTimer {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, a, b) == cudaSuccess) {
             auto &e = ctx->times[name];
-            e.first += ms;
-            e.second += 1;
+            e.ms += ms;
+            e.count += 1;
+            e.work += work;
         }
         cudaEventDestroy(a);
         cudaEventDestroy(b);

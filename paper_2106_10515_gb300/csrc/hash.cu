@@ -442,6 +442,7 @@ geek_status project_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t l
         const int64_t blocks = ceil_div(n, TR);
         {
             EvTimer tk(ctx, "kernel.project_fp32", st);
+            tk.work = 2.0 * (double)n * (double)F * (double)d;
             GK_COUNT();
             k_project_fp32<<<(unsigned)blocks, threads, smem, st>>>(A);
             GK_LAUNCH(ctx);
@@ -456,6 +457,7 @@ geek_status project_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t l
         *n_flagged = (int64_t)h_cnt;
         if (h_cnt) {
             EvTimer tk(ctx, "kernel.recheck_fp64", st);
+            tk.work = 2.0 * (double)h_cnt * (double)d;
             GK_COUNT();
             k_recheck_fp64<<<grid_for((int64_t)h_cnt, 128, ctx->num_sms), 128, 0, st>>>(
                 x, ldx, d, a, b, w, srp, F, flags, cnt, cap, codes, fmin, fmax, status);

@@ -89,54 +89,117 @@ __global__ void __launch_bounds__(1024) k_seg_scan_u32(uint32_t *__restrict__ c,
     if (totals && threadIdx.x == 0) totals[blockIdx.x] = carry;
 }
 
+// Digit offsets of one radix pass.  counts is [S][256][tiles]; one block per
+// (segment, digit) turns its tile counts into an exclusive scan and records
+// the digit total; k_digit_base then scans the 256 totals of each segment.
+__global__ void __launch_bounds__(1024) k_digit_tile_scan(uint32_t *__restrict__ counts, int tiles,
+                                                          uint32_t *__restrict__ dtot) {
+    __shared__ uint32_t wsum[32];
+    const int seg = blockIdx.y, dg = blockIdx.x;
+    uint32_t *a = counts + ((int64_t)seg * 256 + dg) * tiles;
+    uint32_t carry = 0;
+    for (int base = 0; base < tiles; base += 1024) {
+        const int p = base + threadIdx.x;
+        const uint32_t v = p < tiles ? a[p] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_excl_scan<1024>(v, &tot, wsum) + carry;
+        if (p < tiles) a[p] = ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) dtot[seg * 256 + dg] = carry;
+}
+
+__global__ void __launch_bounds__(256) k_digit_base(uint32_t *__restrict__ dtot) {
+    __shared__ uint32_t wsum[32];
+    uint32_t *a = dtot + blockIdx.x * 256;
+    const uint32_t v = a[threadIdx.x];
+    uint32_t tot;
+    const uint32_t ex = block_excl_scan<256>(v, &tot, wsum);
+    a[threadIdx.x] = ex;
+}
+
 // ---- stable scatter of one digit ------------------------------------------
+// A tile of 4096 elements is split into 8 warp slices of 512; warp w reads
+// its slice striped (item i of lane l is element w*512 + i*32 + l), so the
+// order (warp, item, lane) is the input order.  Each warp ranks its elements
+// per digit with match-any (a running per-warp digit count in shared memory),
+// the block turns the per-warp counts into tile offsets, the tile is staged
+// in shared memory in (digit, input order), and written out contiguously per
+// digit: coalesced stores, stable order, three block barriers per tile.
 template <bool HI, bool VALS>
 __global__ void __launch_bounds__(RS_THREADS)
     k_rs_scatter(const uint64_t *__restrict__ lo_in, const uint64_t *__restrict__ hi_in,
                  const uint32_t *__restrict__ v_in, uint64_t *__restrict__ lo_out,
                  uint64_t *__restrict__ hi_out, uint32_t *__restrict__ v_out, int64_t m, int tiles,
-                 int dsel, int sh, const uint32_t *__restrict__ offs) {
-    __shared__ uint32_t base[256];
-    __shared__ uint32_t wc[NWARP][256];
+                 int dsel, int sh, const uint32_t *__restrict__ offs, const uint32_t *__restrict__ dbase) {
+    __shared__ uint32_t whist[NWARP][256];
+    __shared__ uint32_t tstart[256];
+    __shared__ uint32_t gbase[256];
+    __shared__ uint32_t wsum[32];
+    extern __shared__ uint64_t stage[];
+    uint64_t *st_lo = stage;
+    uint64_t *st_hi = stage + RS_TILE;
+    uint32_t *st_v = (uint32_t *)(stage + (HI ? 2 : 1) * RS_TILE);
     const int seg = blockIdx.y, tile = blockIdx.x, t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int64_t so = (int64_t)seg * m;
+    const int64_t t0 = (int64_t)tile * RS_TILE;
     const uint32_t lt = (1u << lane) - 1;
-    base[t] = offs[((int64_t)seg * 256 + t) * tiles + tile];
-    for (int c = 0; c < RS_ITEMS; c++) {
-        const int64_t p = (int64_t)tile * RS_TILE + (int64_t)c * RS_THREADS + t;
-        const bool valid = p < m;
-        uint64_t klo = 0, khi = 0;
-        uint32_t v = 0, dg = 256;
-        if (valid) {
-            klo = lo_in[so + p];
-            if (HI) khi = hi_in[so + p];
-            if (VALS) v = v_in[so + p];
-            dg = (uint32_t)(((dsel ? khi : klo) >> sh) & 0xFFu);
-        }
-        for (int i = lane; i < 256; i += 32) wc[warp][i] = 0;
-        __syncwarp();
-        const uint32_t peers = __match_any_sync(0xffffffffu, dg);
-        const uint32_t rank = __popc(peers & lt);
-        if (valid && rank == 0) wc[warp][dg] = __popc(peers);
-        __syncthreads();
-        {
-            uint32_t run = base[t];
 #pragma unroll
-            for (int w = 0; w < NWARP; w++) {
-                uint32_t x = wc[w][t];
-                wc[w][t] = run;
-                run += x;
-            }
-            base[t] = run;
+    for (int w = 0; w < NWARP; w++) whist[w][t] = 0;
+    gbase[t] = offs[((int64_t)seg * 256 + t) * tiles + tile] + dbase[seg * 256 + t];
+    __syncthreads();
+    constexpr int IT = RS_TILE / RS_THREADS;  // 16 items per lane
+    uint64_t klo[IT], khi[IT];
+    uint32_t vv[IT], dr[IT];  // dr = digit | rank-in-warp << 9
+#pragma unroll
+    for (int i = 0; i < IT; i++) {
+        const int64_t p = t0 + warp * (IT * 32) + i * 32 + lane;
+        const bool valid = p < m;
+        klo[i] = valid ? lo_in[so + p] : 0;
+        khi[i] = (HI && valid) ? hi_in[so + p] : 0;
+        vv[i] = (VALS && valid) ? v_in[so + p] : 0;
+        const uint32_t d = valid ? (uint32_t)(((dsel ? khi[i] : klo[i]) >> sh) & 0xFFu) : 256u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const int leader = __ffs(peers) - 1;
+        uint32_t old = 0;
+        if (lane == leader && d < 256) {
+            old = whist[warp][d];
+            whist[warp][d] = old + __popc(peers);
         }
-        __syncthreads();
-        if (valid) {
-            const int64_t dst = so + wc[warp][dg] + rank;
-            lo_out[dst] = klo;
-            if (HI) hi_out[dst] = khi;
-            if (VALS) v_out[dst] = v;
+        old = __shfl_sync(0xffffffffu, old, leader);
+        dr[i] = d | ((old + __popc(peers & lt)) << 9);
+    }
+    __syncthreads();
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < NWARP; w++) {
+        const uint32_t c = whist[w][t];
+        whist[w][t] = run;
+        run += c;
+    }
+    uint32_t tot;
+    tstart[t] = block_excl_scan<RS_THREADS>(run, &tot, wsum);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < IT; i++) {
+        const uint32_t d = dr[i] & 511u;
+        if (d < 256) {
+            const uint32_t lp = tstart[d] + whist[warp][d] + (dr[i] >> 9);
+            st_lo[lp] = klo[i];
+            if (HI) st_hi[lp] = khi[i];
+            if (VALS) st_v[lp] = vv[i];
         }
-        __syncthreads();
+    }
+    __syncthreads();
+    const int cnt = (int)min((int64_t)RS_TILE, m - t0);
+    for (int q = t; q < cnt; q += RS_THREADS) {
+        const uint64_t kl = st_lo[q];
+        const uint64_t kh = HI ? st_hi[q] : 0;
+        const uint32_t d = (uint32_t)(((dsel ? kh : kl) >> sh) & 0xFFu);
+        const int64_t dst = so + gbase[d] + (q - tstart[d]);
+        lo_out[dst] = kl;
+        if (HI) hi_out[dst] = kh;
+        if (VALS) v_out[dst] = st_v[q];
     }
 }
 
@@ -304,8 +367,9 @@ geek_status radix_sort_segments(geek_ctx *ctx, Scratch &scr, int S, int64_t m, u
     const bool hv = vals && *vals;
     const int tiles = (int)ceil_div(m, RS_TILE);
     const int64_t total = (int64_t)S * m;
-    uint32_t *counts;
+    uint32_t *counts, *dtot;
     GK_TRY(scr.alloc(&counts, (size_t)S * 256 * tiles));
+    GK_TRY(scr.alloc(&dtot, (size_t)S * 256));
     uint64_t *lo2 = nullptr, *hi2 = nullptr;
     uint32_t *v2 = nullptr;
     GK_TRY(scr.alloc(&lo2, total));
@@ -315,22 +379,35 @@ geek_status radix_sort_segments(geek_ctx *ctx, Scratch &scr, int S, int64_t m, u
     uint32_t *av = hv ? *vals : nullptr, *bv = v2;
     int passes = 0;
     const dim3 grid(tiles, S);
+    const size_t stage = (size_t)RS_TILE * ((hi ? 16 : 8) + (hv ? 4 : 0));
+    static bool attr_done = false;
+    if (!attr_done) {
+        const int mx = RS_TILE * 20;
+        GK_CUDA(ctx, cudaFuncSetAttribute(k_rs_scatter<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        GK_CUDA(ctx, cudaFuncSetAttribute(k_rs_scatter<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        GK_CUDA(ctx, cudaFuncSetAttribute(k_rs_scatter<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        GK_CUDA(ctx, cudaFuncSetAttribute(k_rs_scatter<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        attr_done = true;
+    }
     for (int sh = 0; sh < nbits; sh += 8, passes++) {
         const int dsel = sh >= 64, s = sh & 63;
         GK_COUNT();
         k_rs_hist<<<grid, RS_THREADS, 0, st>>>(dsel ? ahi : alo, s, m, tiles, counts);
         GK_COUNT();
-        k_seg_scan_u32<<<S, 1024, 0, st>>>(counts, (int64_t)256 * tiles, nullptr);
+        k_digit_tile_scan<<<dim3(256, S), 1024, 0, st>>>(counts, tiles, dtot);
+        GK_COUNT();
+        k_digit_base<<<S, 256, 0, st>>>(dtot);
         EvTimer tk(ctx, "kernel.rs_scatter", st);
+        tk.work = 2.0 * (double)total * ((hi ? 16 : 8) + (hv ? 4 : 0));
         GK_COUNT();
         if (hi && hv)
-            k_rs_scatter<true, true><<<grid, RS_THREADS, 0, st>>>(alo, ahi, av, blo, bhi, bv, m, tiles, dsel, s, counts);
+            k_rs_scatter<true, true><<<grid, RS_THREADS, stage, st>>>(alo, ahi, av, blo, bhi, bv, m, tiles, dsel, s, counts, dtot);
         else if (hi)
-            k_rs_scatter<true, false><<<grid, RS_THREADS, 0, st>>>(alo, ahi, av, blo, bhi, bv, m, tiles, dsel, s, counts);
+            k_rs_scatter<true, false><<<grid, RS_THREADS, stage, st>>>(alo, ahi, av, blo, bhi, bv, m, tiles, dsel, s, counts, dtot);
         else if (hv)
-            k_rs_scatter<false, true><<<grid, RS_THREADS, 0, st>>>(alo, ahi, av, blo, bhi, bv, m, tiles, dsel, s, counts);
+            k_rs_scatter<false, true><<<grid, RS_THREADS, stage, st>>>(alo, ahi, av, blo, bhi, bv, m, tiles, dsel, s, counts, dtot);
         else
-            k_rs_scatter<false, false><<<grid, RS_THREADS, 0, st>>>(alo, ahi, av, blo, bhi, bv, m, tiles, dsel, s, counts);
+            k_rs_scatter<false, false><<<grid, RS_THREADS, stage, st>>>(alo, ahi, av, blo, bhi, bv, m, tiles, dsel, s, counts, dtot);
         GK_LAUNCH(ctx);
         std::swap(alo, blo);
         std::swap(ahi, bhi);

@@ -100,6 +100,26 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *tm,
         : "memory");
 }
 
+// untiled bulk copy global -> shared (16-byte aligned addresses and size)
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"((uint64_t)src), "r"(bytes), "r"(su32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -166,8 +186,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
     uint64_t *bars = (uint64_t *)(base + 2 * a_bytes + 2 * b_bytes);
     uint64_t *full_a = bars, *empty_a = bars + 2, *full_b = bars + 4, *empty_b = bars + 6;
     uint64_t *full_acc = bars + 8, *empty_acc = bars + 10, *done_bar = bars + 12;
-    uint32_t *tmem_slot = (uint32_t *)(bars + 14);
-    float *mrg = (float *)(bars + 16);  // [128][3] second-half results
+    uint64_t *full_cn = bars + 13;  // 4 slots
+    uint32_t *tmem_slot = (uint32_t *)(bars + 17);
+    float *mrg = (float *)(bars + 18);         // [128][3] second-half results
+    float *cn_s = (float *)(base + 2 * a_bytes + 2 * b_bytes + 2048);  // [4][256] |c|^2 ring
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nkb = A.Kp / TC_KB;
@@ -181,6 +203,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
             mbar_init(&empty_acc[i], TC_EPI_WARPS);
         }
         mbar_init(done_bar, 1);
+        for (int i = 0; i < 4; i++) mbar_init(&full_cn[i], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -199,7 +222,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
             uint64_t ct = 0;
-            uint32_t issued_b[2] = {0, 0};
+            uint32_t issued_b[2] = {0, 0}, issued_cn[4] = {0, 0, 0, 0};
             bool ok = true;
             int64_t it = 0;
             for (int64_t rt = blockIdx.x; rt < A.ntiles_r && ok; rt += gridDim.x, it++) {
@@ -219,11 +242,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
                         tma_load_2d(su32(sB0 + s * b_bytes + kb * TC_N * 128), &A.tmB, kb * TC_KB, c * TC_N,
                                     &full_b[s]);
                     issued_b[s] = u + 1;
+                    // |c|^2 of this centre tile into ring slot ct % 4.  The
+                    // epilogue of tile ct - 4, the last reader of the slot,
+                    // finished before the MMA of tile ct - 2 started, which
+                    // finished before empty_b let this tile in.
+                    const int cs = (int)(ct & 3);
+                    mbar_expect_tx(&full_cn[cs], TC_N * 4);
+                    bulk_load(su32(cn_s + cs * TC_N), A.cn + (int64_t)c * TC_N, TC_N * 4, &full_cn[cs]);
+                    issued_cn[cs] = (uint32_t)(ct >> 2) + 1;
                 }
             }
             // drain: every centre-tile copy this thread issued has landed
             for (int s = 0; s < 2; s++)
                 if (issued_b[s]) mbar_wait(&full_b[s], (issued_b[s] - 1) & 1, A.err, true);
+            for (int s = 0; s < 4; s++)
+                if (issued_cn[s]) mbar_wait(&full_cn[s], (issued_cn[s] - 1) & 1, A.err, true);
         }
         __syncwarp();
     } else if (warp == 1) {
@@ -279,24 +312,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
             for (int c = 0; c < A.ntiles_c; c++, ct++) {
                 const int s = (int)(ct & 1);
                 const uint32_t u = (uint32_t)(ct >> 1);
+                const int cs = (int)(ct & 3);
                 int w_ok = 0;
-                if (lane == 0 && ok) w_ok = mbar_wait(&full_acc[s], u & 1, A.err);
+                if (lane == 0 && ok)
+                    w_ok = mbar_wait(&full_acc[s], u & 1, A.err) &&
+                           mbar_wait(&full_cn[cs], (uint32_t)(ct >> 2) & 1, A.err);
                 w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
                 ok = ok && w_ok;
                 if (ok) {
                     fence_after();
-#pragma unroll 1
+                    // four 32-column chunks; the TMEM load of chunk ch + 1 is in
+                    // flight while chunk ch is reduced
+                    const uint32_t tbase = tmem + (uint32_t)(s * TC_N + h * 128) + ((uint32_t)(32 * q) << 16);
+                    const float *cnt = cn_s + cs * TC_N + h * 128;
+                    uint32_t ra[32], rb[32];
+                    tmem_ld32_async(tbase, ra);
+                    tmem_wait_ld();
+#pragma unroll
                     for (int ch = 0; ch < 4; ch++) {
-                        const int col = h * 128 + ch * 32;
-                        uint32_t r[32];
-                        tmem_ld32(tmem + (uint32_t)(s * TC_N + col) + ((uint32_t)(32 * q) << 16), r);
-                        const int64_t j0 = (int64_t)c * TC_N + col;
-                        const float4 *cn4 = reinterpret_cast<const float4 *>(A.cn + j0);
+                        if (ch < 3) {
+                            if (ch & 1) tmem_ld32_async(tbase + (ch + 1) * 32, ra);
+                            else tmem_ld32_async(tbase + (ch + 1) * 32, rb);
+                        }
+                        const uint32_t *r = (ch & 1) ? rb : ra;
+                        const int64_t j0 = (int64_t)c * TC_N + h * 128 + ch * 32;
+                        const float4 *cn4 = reinterpret_cast<const float4 *>(cnt + ch * 32);
                         float v[32];
                         float tm = FLT_MAX;
 #pragma unroll
                         for (int i = 0; i < 8; i++) {
-                            const float4 cc = __ldg(cn4 + i);
+                            const float4 cc = cn4[i];
                             v[4 * i + 0] = fmaf(-2.f, __uint_as_float(r[4 * i + 0]), cc.x);
                             v[4 * i + 1] = fmaf(-2.f, __uint_as_float(r[4 * i + 1]), cc.y);
                             v[4 * i + 2] = fmaf(-2.f, __uint_as_float(r[4 * i + 2]), cc.z);
@@ -318,6 +363,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
                                 }
                             }
                         }
+                        if (ch < 3) tmem_wait_ld();
                     }
                     fence_before();
                 }
@@ -475,11 +521,13 @@ geek_status assign_tc_bf16(geek_ctx *ctx, Scratch &scr, const float *x, int64_t 
     A.flag_rows = flag_rows;
     A.n_flag = n_flag;
     A.err = err;
-    const size_t smem = 1024 + 2 * (size_t)TC_M * Kp * 2 + 2 * (size_t)TC_N * Kp * 2 + 16 * 8 + 128 * 3 * 4 + 64;
+    // tiles + 2 KB (barriers, TMEM slot, merge buffer) + 4 KB |c|^2 ring + alignment
+    const size_t smem = 1024 + 2 * (size_t)TC_M * Kp * 2 + 2 * (size_t)TC_N * Kp * 2 + 2048 + 4 * TC_N * 4;
     GK_CUDA(ctx, cudaFuncSetAttribute(k_assign_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = (int)std::min<int64_t>(A.ntiles_r, ctx->num_sms);
     {
         EvTimer tk(ctx, "kernel.assign_tc", st);
+        tk.work = 2.0 * (double)n * (double)k * (double)d;
         GK_COUNT();
         k_assign_tc<<<grid, TC_THREADS, smem, st>>>(A);
         GK_LAUNCH(ctx);

@@ -99,7 +99,8 @@ def lib():
                                       C.POINTER(geek_assign_params), P, C.POINTER(geek_assign_stats), P]
     L.geek_timing_enable.argtypes = [P, C.c_int]
     L.geek_timing_reset.argtypes = [P]
-    L.geek_timing_get.argtypes = [P, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+    L.geek_timing_get.argtypes = [P, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64),
+                                  C.POINTER(C.c_double)]
     L.geek_launch_count.restype = C.c_ulonglong
     L.geek_assign_centers_noalloc.argtypes = [P, C.c_int64, C.c_int32, C.c_int64, P, C.c_int64, P, P]
     for name in EXPORTS:
@@ -245,9 +246,10 @@ class Context:
         self._chk(lib().geek_timing_reset(self.h))
 
     def timing_get(self, name):
-        ms, cnt = C.c_double(), C.c_int64()
-        self._chk(lib().geek_timing_get(self.h, name.encode(), C.byref(ms), C.byref(cnt)))
-        return ms.value, cnt.value
+        """(total ms, brackets, total algorithmic work) recorded under name."""
+        ms, cnt, work = C.c_double(), C.c_int64(), C.c_double()
+        self._chk(lib().geek_timing_get(self.h, name.encode(), C.byref(ms), C.byref(cnt), C.byref(work)))
+        return ms.value, cnt.value, work.value
 
     def _chk(self, st):
         if st != OK:
