@@ -30,7 +30,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-TIMED = ["hash", "silk", "assign", "hash.sort", "kernel.project_fp32", "kernel.recheck_fp64",
+TIMED = ["hash", "silk", "assign", "hash.sort", "silk.vbuckets", "silk.bins", "silk.vote", "silk.dedup",
+         "kernel.project_fp32", "kernel.recheck_dot2", "kernel.recheck_fp64",
          "kernel.rs_scatter", "kernel.assign_tc", "kernel.assign_fp32", "kernel.assign_recheck"]
 METRIC = "points/sec hash+assign (n=10M,d=128) mixed vs plain FP32; TC util/HBM GB/s"
 UNIT = "points/s"
@@ -163,7 +164,7 @@ def run_ours(args):
         seeds = ctx.silk(bk, **silk)
         st = ctx.assign_centers(data, centres, labels, precision=p)
         info.update(k_star=seeds.k, n_multiset=seeds.n_multiset, n_buckets=bk.n_buckets,
-                    n_flagged=bk.n_flagged, n_recheck_rows=st.n_recheck_rows, sse=st.sse,
+                    n_flagged=bk.n_flagged, n_flagged_fp64=bk.n_flagged_fp64, n_recheck_rows=st.n_recheck_rows, sse=st.sse,
                     key_bits=bk.key_bits_max)
         del bk, seeds
 
@@ -276,12 +277,13 @@ def run_ours(args):
                    "n": cfg.n, "d": cfg.d, "k_assign": k, "k_star_silk": main_info["k_star"],
                    "l2": "inputs larger than L2 (x is 5.1 GB)", "parallelism": f"replicas x{world}",
                    "precision": args.precision},
-        "phases_ms": {ph: tm[ph][0] / max(1, tm[ph][1]) for ph in ["hash", "silk", "assign", "hash.sort"]},
+        "phases_ms_per_step": {ph: tm[ph][0] / args.steps for ph in ["hash", "silk", "assign", "hash.sort",
+                                                                   "silk.vbuckets", "silk.bins", "silk.vote", "silk.dedup"]},
         "kernels_ms_per_step": {kk: v[0] / args.steps for kk, v in tm.items() if kk.startswith("kernel.") and v[1]},
         "kernel_launches_per_step": {kk: v[1] / args.steps for kk, v in tm.items() if kk.startswith("kernel.") and v[1]},
         "hash_assign_points_per_s": cfg.n * world / ((tm["hash"][0] / max(1, tm["hash"][1]) +
                                                      tm["assign"][0] / max(1, tm["assign"][1])) / 1e3),
-        "recheck": {"hash_flagged_elems": main_info["n_flagged"], "assign_recheck_rows": main_info["n_recheck_rows"]},
+        "recheck": {"hash_flagged_elems": main_info["n_flagged"], "hash_fp64_elems": main_info["n_flagged_fp64"], "assign_recheck_rows": main_info["n_recheck_rows"]},
         "gpu_launches": int(launches),
         "clocks": cl,
         "roofline": roof,

@@ -106,7 +106,8 @@ typedef struct geek_buckets_info {
     int32_t L;               /* tables */
     int32_t key_bits_max;    /* widest packed table key, bits */
     int64_t n_buckets;       /* buckets over all tables */
-    int64_t n_flagged;       /* fast-path elements recomputed in FP64 */
+    int64_t n_flagged;       /* elements outside the FP32 window (rechecked) */
+    int64_t n_flagged_fp64;  /* of those, elements decided by the FP64 reference */
 } geek_buckets_info;
 
 /* SILK parameters (Alg. 4): Ls tables of Ks MinHash functions over object

@@ -115,7 +115,8 @@ geek_status hash_impl(geek_ctx *ctx, const geek_data *data, const geek_hash_para
         const float *x;
         GK_TRY(stage(ctx, scr, data->x, (size_t)n * data->ldx, host, &x, st));
         GK_TRY(project_dense(ctx, scr, x, data->ldx, n, data->d, p->a, p->b, F1, p->w,
-                             p->proj == GEEK_PROJ_SRP, b->codes, fmin, fmax, &b->n_flagged, st));
+                             p->proj == GEEK_PROJ_SRP, b->codes, fmin, fmax, &b->n_flagged,
+                             &b->n_flagged_fp64, st));
     }
     if (kind == GEEK_SETS) {
         const int64_t *off;
@@ -258,6 +259,7 @@ geek_status geek_buckets_info_get(const geek_buckets *b, geek_buckets_info *info
     info->key_bits_max = b->key_bits_max;
     info->n_buckets = b->NB;
     info->n_flagged = b->n_flagged;
+    info->n_flagged_fp64 = b->n_flagged_fp64;
     return GEEK_OK;
 }
 

@@ -246,45 +246,61 @@ __global__ void k_centre_prep(const double *__restrict__ c64, int64_t k, int d, 
     }
 }
 
-// per-object distance to its centre in double-float form: diff = (x - c_hi)
-// - c_lo with c = c_hi + c_lo, squares accumulated in FP32; partial sums
-// per block (deterministic final reduction on one block)
+// double-float split of the FP64 centres: c = hi + lo with hi = (float)c
+__global__ void k_centre_split(const double *__restrict__ c64, int64_t kd, float *__restrict__ hi,
+                               float *__restrict__ lo) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < kd; e += (int64_t)gridDim.x * blockDim.x) {
+        const double c = c64[e];
+        const float h = (float)c;
+        hi[e] = h;
+        lo[e] = (float)(c - (double)h);
+    }
+}
+
+// per-object distance to its centre, warp per object, lanes over
+// coordinates: diff = (x - c_hi) - c_lo, squares accumulated in FP32; block
+// partial sums (FP64) and maxima, reduced on one block in a fixed order
 __global__ void __launch_bounds__(256) k_assign_stats(const float *__restrict__ x, int64_t ldx, int64_t n, int d,
-                                                      const double *__restrict__ c64, int64_t k,
-                                                      const int32_t *__restrict__ labels,
+                                                      const float *__restrict__ chi, const float *__restrict__ clo,
+                                                      int64_t k, const int32_t *__restrict__ labels,
                                                       double *__restrict__ part_sum, float *__restrict__ part_max) {
-    __shared__ double ss[256];
-    __shared__ float sm_[256];
+    __shared__ double ss[8];
+    __shared__ float sm_[8];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double s = 0.0;
     float mx = 0.f;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = warp; i < n; i += nw) {
         const int j = labels[i];
-        if (j < 0 || j >= k) continue;
+        if (j < 0 || j >= k) continue;  // uniform across the warp
+        const float *xr = x + i * ldx;
+        const float *h = chi + (int64_t)j * d;
+        const float *l = clo + (int64_t)j * d;
         float D = 0.f;
-        for (int t = 0; t < d; t++) {
-            const double c = c64[(int64_t)j * d + t];
-            const float ch = (float)c;
-            const float cl = (float)(c - (double)ch);
-            const float e = (x[i * ldx + t] - ch) - cl;
+        for (int t = lane; t < d; t += 32) {
+            const float e = (xr[t] - h[t]) - l[t];
             D = fmaf(e, e, D);
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) D += __shfl_xor_sync(0xffffffffu, D, o);
         s += (double)D;
         mx = fmaxf(mx, D);
     }
-    ss[threadIdx.x] = s;
-    sm_[threadIdx.x] = mx;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) {
-            ss[threadIdx.x] += ss[threadIdx.x + o];
-            sm_[threadIdx.x] = fmaxf(sm_[threadIdx.x], sm_[threadIdx.x + o]);
-        }
-        __syncthreads();
+    if (lane == 0) {
+        ss[wib] = s;
+        sm_[wib] = mx;
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        part_sum[blockIdx.x] = ss[0];
-        part_max[blockIdx.x] = sm_[0];
+        double a = 0.0;
+        float m = 0.f;
+        for (int w = 0; w < 8; w++) {
+            a += ss[w];
+            m = fmaxf(m, sm_[w]);
+        }
+        part_sum[blockIdx.x] = a;
+        part_max[blockIdx.x] = m;
     }
 }
 
@@ -397,8 +413,13 @@ geek_status assign_dense_centres(geek_ctx *ctx, Scratch &scr, const float *x, in
         GK_TRY(scr.alloc(&ps, nb));
         GK_TRY(scr.alloc(&pm, nb));
         GK_TRY(scr.alloc(&out, 2));
+        float *chi, *clo;
+        GK_TRY(scr.alloc(&chi, (size_t)k * d));
+        GK_TRY(scr.alloc(&clo, (size_t)k * d));
         GK_COUNT();
-        k_assign_stats<<<nb, 256, 0, st>>>(x, ldx, n, d, centres, k, labels, ps, pm);
+        k_centre_split<<<grid_for(k * d, 256, ctx->num_sms), 256, 0, st>>>(centres, k * d, chi, clo);
+        GK_COUNT();
+        k_assign_stats<<<nb, 256, 0, st>>>(x, ldx, n, d, chi, clo, k, labels, ps, pm);
         GK_COUNT();
         k_stats_final<<<1, 32, 0, st>>>(ps, pm, nb, out);
         GK_LAUNCH(ctx);

@@ -218,6 +218,104 @@ __global__ void k_row_norms(const float *__restrict__ a, int F, int d, float *__
     out[f] = sqrtf(s) * 1.0001f;
 }
 
+// Second stage for flagged elements: the dot product again in compensated
+// FP32 (TwoProduct by FMA, TwoSum, error terms summed separately, after Ogita,
+// Rump and Oishi's Dot2).  With the FP64 reference's own error this gives an
+// interval of width ~1e-6 |a||x| around s64; if the monotone reference map
+// sends both ends to one code the element is settled here, otherwise it goes
+// on to the FP64 list (about one element in 10^7 at d = 128).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float z = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+// A warp takes 32 flagged elements at a time.  For each, all lanes
+// accumulate strided terms with TwoProduct / TwoSum (coalesced loads) and a
+// TwoSum tree combines the 32 partial (sum, error) pairs; lane k keeps
+// element k's result, and the 32 interval tests then run in parallel.  The
+// exact value equals the final sum plus all error terms; only the float
+// summation of those error terms is inexact, by at most
+// gamma_2d * (d + 1) u sum|a_j x_j| <= 2.2 (2d)(d+1) u^2 |a||x|.
+__global__ void __launch_bounds__(256) k_recheck_dot2(
+    const float *__restrict__ x, int64_t ldx, int d, const float *__restrict__ a, const float *__restrict__ b,
+    double w, int srp, int F, const float *__restrict__ anorm, const uint64_t *__restrict__ flags,
+    const unsigned long long *__restrict__ n_flags, int64_t cap, int32_t *__restrict__ codes, int *__restrict__ fmin,
+    int *__restrict__ fmax, uint64_t *__restrict__ flags2, unsigned long long *__restrict__ n_flags2) {
+    const int64_t nf = min((int64_t)*n_flags, cap);
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const double u = 5.9604644775390625e-08;  // 2^-24
+    const double cfac = 2.2 * (2.0 * d) * (d + 1.0) * u * u + (double)d * 2.220446049250313e-16;
+    for (int64_t base = warp * 32; base < nf; base += nw * 32) {
+        const int cnt = (int)min((int64_t)32, nf - base);
+        const uint64_t mine = lane < cnt ? flags[base + lane] : 0;
+        float my_sh = 0.f, my_sc = 0.f, my_xx = 0.f;
+        for (int kk = 0; kk < cnt; kk++) {
+            const uint64_t e = __shfl_sync(0xffffffffu, mine, kk);
+            const int64_t row = (int64_t)(e >> 16);
+            const int f = (int)(e & 0xFFFF);
+            const float *xr = x + row * ldx;
+            const float *ar = a + (int64_t)f * d;
+            float sh = 0.f, sc = 0.f, xx = 0.f;
+            for (int j = lane; j < d; j += 32) {
+                const float av = ar[j], xv = xr[j];
+                const float p = __fmul_rn(av, xv);
+                const float h = fmaf(av, xv, -p);  // exact product error
+                float t, er;
+                two_sum(sh, p, t, er);
+                sh = t;
+                sc = __fadd_rn(sc, __fadd_rn(er, h));
+                xx = fmaf(xv, xv, xx);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float os = __shfl_xor_sync(0xffffffffu, sh, o);
+                const float oc = __shfl_xor_sync(0xffffffffu, sc, o);
+                xx += __shfl_xor_sync(0xffffffffu, xx, o);
+                float t, er;
+                two_sum(sh, os, t, er);
+                sh = t;
+                sc = __fadd_rn(__fadd_rn(sc, oc), er);
+            }
+            if (lane == kk) {
+                my_sh = sh;
+                my_sc = sc;
+                my_xx = xx;
+            }
+        }
+        if (lane >= cnt) continue;
+        const uint64_t e = mine;
+        const int64_t row = (int64_t)(e >> 16);
+        const int f = (int)(e & 0xFFFF);
+        const double S = (double)my_sh + (double)my_sc;
+        const double an = (double)anorm[f], xn = (double)(sqrtf(my_xx) * (1.0f + 1.0e-3f));
+        const double E = cfac * an * xn + fabs(S) * 8.881784197001252e-16 + (double)d * 1e-40 + 1e-300;
+        const double lo = S - E, hi = S + E;
+        bool sure;
+        int code;
+        if (srp) {
+            sure = lo >= 0.0 || hi < 0.0;
+            code = lo >= 0.0 ? 1 : 0;
+        } else {
+            const double bb = (double)b[f];
+            const double tl = floor(__ddiv_rn(__dadd_rn(lo, bb), w));
+            const double th = floor(__ddiv_rn(__dadd_rn(hi, bb), w));
+            sure = tl == th && tl >= -2147483648.0 && tl <= 2147483647.0;
+            code = sure ? (int)tl : 0;
+        }
+        if (sure) {
+            codes[row * F + f] = code;
+            atomicMin(&fmin[f], code);
+            atomicMax(&fmax[f], code);
+        } else {
+            const unsigned long long slot = atomicAdd(n_flags2, 1ull);
+            flags2[slot] = e;  // slot < nf <= cap
+        }
+    }
+}
+
 // FP64 recheck of flagged elements with the reference sequence: products of
 // the float inputs (exact in FP64), summed in j order, then (s + b) / w,
 // each step rounded to nearest; no fused multiply-add.
@@ -334,24 +432,25 @@ __device__ __forceinline__ void shl_or(uint64_t &hi, uint64_t &lo, int b, uint64
 
 // key of table l for object i: fields codes[l*K1+k] - min (bits[f] wide),
 // then K2 MinHash values (32 bits each), the first field most significant.
+// One thread per object walks all L tables, so each code row is read once.
 __global__ void k_pack_keys(int64_t n, int L, const int32_t *__restrict__ codes, int F1, int K1,
                             const int *__restrict__ fmin, const int *__restrict__ bits,
                             const uint32_t *__restrict__ mh, int F2, int K2,
                             uint64_t *__restrict__ klo, uint64_t *__restrict__ khi) {
-    const int64_t total = n * L;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e % n;
-        const int l = (int)(e / n);
-        uint64_t hi = 0, lo = 0;
-        for (int k = 0; k < K1; k++) {
-            const int f = l * K1 + k;
-            const uint32_t v = (uint32_t)((int64_t)codes[i * F1 + f] - (int64_t)fmin[f]);
-            shl_or(hi, lo, bits[f], v);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t *cr = codes + i * F1;
+        const uint32_t *mr = mh ? mh + i * F2 : nullptr;
+        for (int l = 0; l < L; l++) {
+            uint64_t hi = 0, lo = 0;
+            for (int k = 0; k < K1; k++) {
+                const int f = l * K1 + k;
+                const uint32_t v = (uint32_t)((int64_t)cr[f] - (int64_t)fmin[f]);
+                shl_or(hi, lo, bits[f], v);
+            }
+            for (int k = 0; k < K2; k++) shl_or(hi, lo, 32, mr[l * K2 + k]);
+            klo[(int64_t)l * n + i] = lo;
+            if (khi) khi[(int64_t)l * n + i] = hi;
         }
-        for (int k = 0; k < K2; k++) shl_or(hi, lo, 32, mh[i * F2 + l * K2 + k]);
-        klo[e] = lo;
-        if (khi) khi[e] = hi;
     }
 }
 
@@ -396,7 +495,8 @@ int grid_for(int64_t work, int threads, int num_sms) {
 geek_status project_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ldx, int64_t n,
                           int d, const float *a, const float *b, int F, double w, int srp,
                           int32_t *codes, int *fmin, int *fmax, int64_t *n_flagged,
-                          cudaStream_t st) {
+                          int64_t *n_flagged_fp64, cudaStream_t st) {
+    *n_flagged_fp64 = 0;
     if (F > 512) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "more than 512 projections");
     if (d > 100000) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "d > 100000");
     float *anorm;
@@ -456,12 +556,28 @@ geek_status project_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t l
         }
         *n_flagged = (int64_t)h_cnt;
         if (h_cnt) {
+            uint64_t *flags2;
+            unsigned long long *cnt2;
+            GK_TRY(scr.alloc(&flags2, (size_t)h_cnt));
+            GK_TRY(scr.alloc(&cnt2, 1));
+            GK_CUDA(ctx, cudaMemsetAsync(cnt2, 0, sizeof(unsigned long long), st));
+            {
+                EvTimer tk(ctx, "kernel.recheck_dot2", st);
+                GK_COUNT();
+                k_recheck_dot2<<<grid_for((int64_t)h_cnt, 256, ctx->num_sms), 256, 0, st>>>(
+                    x, ldx, d, a, b, w, srp, F, anorm, flags, cnt, cap, codes, fmin, fmax, flags2, cnt2);
+                GK_LAUNCH(ctx);
+            }
             EvTimer tk(ctx, "kernel.recheck_fp64", st);
-            tk.work = 2.0 * (double)h_cnt * (double)d;
             GK_COUNT();
             k_recheck_fp64<<<grid_for((int64_t)h_cnt, 128, ctx->num_sms), 128, 0, st>>>(
-                x, ldx, d, a, b, w, srp, F, flags, cnt, cap, codes, fmin, fmax, status);
+                x, ldx, d, a, b, w, srp, F, flags2, cnt2, (int64_t)h_cnt, codes, fmin, fmax, status);
             GK_LAUNCH(ctx);
+            unsigned long long h2 = 0;
+            GK_CUDA(ctx, cudaMemcpyAsync(&h2, cnt2, sizeof h2, cudaMemcpyDeviceToHost, st));
+            GK_CUDA(ctx, cudaStreamSynchronize(st));
+            tk.work = 2.0 * (double)h2 * (double)d;
+            *n_flagged_fp64 = (int64_t)h2;
         }
         int h_status = 0;
         GK_CUDA(ctx, cudaMemcpyAsync(&h_status, status, sizeof h_status, cudaMemcpyDeviceToHost, st));
@@ -520,7 +636,7 @@ geek_status pack_keys(geek_ctx *ctx, int64_t n, int L, const int32_t *codes, int
                       uint64_t *klo, uint64_t *khi, cudaStream_t st) {
     if (n == 0) return GEEK_OK;
     GK_COUNT();
-    k_pack_keys<<<grid_for(n * L, 256, ctx->num_sms), 256, 0, st>>>(n, L, codes, F1, K1, fmin, bits, mh, F2, K2, klo, khi);
+    k_pack_keys<<<grid_for(n, 256, ctx->num_sms), 256, 0, st>>>(n, L, codes, F1, K1, fmin, bits, mh, F2, K2, klo, khi);
     GK_LAUNCH(ctx);
     return GEEK_OK;
 }

@@ -8,7 +8,7 @@
 geek_status project_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ldx, int64_t n,
                           int d, const float *a, const float *b, int F, double w, int srp,
                           int32_t *codes, int *fmin, int *fmax, int64_t *n_flagged,
-                          cudaStream_t st);
+                          int64_t *n_flagged_fp64, cudaStream_t st);
 geek_status minhash_rows(geek_ctx *ctx, int64_t n, const int64_t *off, int row_len,
                          const uint32_t *items, int F, const uint64_t *A, const uint64_t *B,
                          uint32_t *out, cudaStream_t st);
@@ -31,7 +31,8 @@ struct geek_buckets {
     int L = 0, K = 0, Kc = 0, F = 0;
     int key_bits_max = 0;
     int64_t NB = 0;
-    int64_t n_flagged = 0;
+    int64_t n_flagged = 0;       // elements outside the FP32 certainty window
+    int64_t n_flagged_fp64 = 0;  // of those, elements decided by the FP64 reference
     std::vector<int64_t> nb;       // buckets per table
     int32_t *obj_bucket = nullptr; // L x n
     int64_t *boff = nullptr;       // NB + 1

@@ -16,14 +16,17 @@ __global__ void k_set_sig(int64_t nsets, const int64_t *__restrict__ soff,
                           const uint32_t *__restrict__ sids, int Ks, const uint64_t *__restrict__ A,
                           const uint64_t *__restrict__ B, uint64_t *__restrict__ klo,
                           uint64_t *__restrict__ khi, uint32_t *__restrict__ vals) {
+    // blockIdx.y = SILK table of this segment (functions t*Ks .. t*Ks+Ks-1)
+    const int t = blockIdx.y;
+    const int64_t so = (int64_t)t * nsets;
+    uint64_t a[4], b[4];
+    for (int k = 0; k < Ks; k++) {
+        a[k] = A[t * Ks + k];
+        b[k] = B[t * Ks + k];
+    }
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nsets;
          g += (int64_t)gridDim.x * blockDim.x) {
         uint32_t m[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
-        uint64_t a[4], b[4];
-        for (int k = 0; k < Ks; k++) {
-            a[k] = A[k];
-            b[k] = B[k];
-        }
         for (int64_t p = soff[g]; p < soff[g + 1]; p++) {
             const uint32_t id = sids[p];
             for (int k = 0; k < Ks; k++) m[k] = min(m[k], mh_hash32(a[k], b[k], id));
@@ -33,10 +36,82 @@ __global__ void k_set_sig(int64_t nsets, const int64_t *__restrict__ soff,
             hi = (hi << 32) | (lo >> 32);
             lo = (lo << 32) | m[k];
         }
-        klo[g] = lo;
-        if (khi) khi[g] = hi;
-        vals[g] = (uint32_t)g;
+        klo[so + g] = lo;
+        if (khi) khi[so + g] = hi;
+        vals[so + g] = (uint32_t)g;
     }
+}
+
+// first signature component (the most significant 32 bits of the packed key)
+__global__ void k_first_component(int64_t n, const uint64_t *__restrict__ klo, const uint64_t *__restrict__ khi,
+                                  int Ks, uint64_t *__restrict__ k0) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t v;
+        if (Ks == 1) v = klo[g];
+        else if (Ks == 2) v = klo[g] >> 32;
+        else if (Ks == 3) v = khi[g];
+        else v = khi[g] >> 32;
+        k0[g] = v & 0xFFFFFFFFull;
+    }
+}
+
+__device__ __forceinline__ bool sig_less(const uint64_t *klo, const uint64_t *khi, uint32_t a, uint32_t b) {
+    const uint64_t ha = khi ? khi[a] : 0, hb = khi ? khi[b] : 0;
+    if (ha != hb) return ha < hb;
+    if (klo[a] != klo[b]) return klo[a] < klo[b];
+    return a < b;
+}
+
+// insertion sort of each run of equal first components by (signature, index);
+// blockIdx.y = segment
+__global__ void k_fix_runs(int64_t m, const int64_t *__restrict__ runs, const int64_t *__restrict__ rs_all,
+                           const uint64_t *__restrict__ klo_all, const uint64_t *__restrict__ khi_all,
+                           uint32_t *__restrict__ perm_all) {
+    const int t = blockIdx.y;
+    const int64_t *rs = rs_all + (int64_t)t * (m + 1);
+    const uint64_t *klo = klo_all + (int64_t)t * m;
+    const uint64_t *khi = khi_all ? khi_all + (int64_t)t * m : nullptr;
+    uint32_t *perm = perm_all + (int64_t)t * m;
+    const int64_t nr = runs[t];
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = rs[r], e = rs[r + 1];
+        for (int64_t i = s + 1; i < e; i++) {
+            const uint32_t v = perm[i];
+            int64_t j = i - 1;
+            while (j >= s && sig_less(klo, khi, v, perm[j])) {
+                perm[j + 1] = perm[j];
+                j--;
+            }
+            perm[j + 1] = v;
+        }
+    }
+}
+
+__global__ void k_gather_sig(int64_t m, int S, const uint32_t *__restrict__ perm, const uint64_t *__restrict__ klo,
+                             const uint64_t *__restrict__ khi, uint64_t *__restrict__ slo, uint64_t *__restrict__ shi) {
+    const int64_t tot = m * S;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < tot; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t so = (p / m) * m;
+        const uint32_t g = perm[p];
+        slo[p] = klo[so + g];
+        if (shi) shi[p] = khi[so + g];
+    }
+}
+
+// per-segment bin numbering -> one global numbering over all segments
+__global__ void k_globalize_rank(int64_t m, int S, const int64_t *__restrict__ base, int32_t *__restrict__ rank) {
+    const int64_t tot = m * S;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < tot; p += (int64_t)gridDim.x * blockDim.x)
+        rank[p] += (int32_t)base[p / m];
+}
+
+__global__ void k_globalize_rs(int64_t m, const int64_t *__restrict__ runs, const int64_t *__restrict__ base,
+                               const int64_t *__restrict__ rs_seg, int64_t *__restrict__ rs_g, int S) {
+    const int t = blockIdx.y;
+    const int64_t nr = runs[t];
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += (int64_t)gridDim.x * blockDim.x)
+        rs_g[base[t] + r] = (int64_t)t * m + rs_seg[(int64_t)t * (m + 1) + r];
+    if (t == S - 1 && blockIdx.x == 0 && threadIdx.x == 0) rs_g[base[t] + nr] = (int64_t)S * m;
 }
 
 __device__ __forceinline__ int64_t bin_size(const int64_t *rs, int64_t r) { return rs[r + 1] - rs[r]; }
@@ -373,23 +448,68 @@ geek_status d2h_i64(geek_ctx *ctx, const int64_t *dev, int64_t *host, cudaStream
 // Group nsets sets into bins by their Ks-function MinHash signature.
 // Returns perm (set index per sorted position), rank (bin per position),
 // rs (bin starts, nbins + 1) and nbins.
-geek_status make_bins(geek_ctx *ctx, Scratch &scr, int64_t nsets, const int64_t *soff,
+// Groups nsets sets into bins by their Ks-function MinHash signature, for S
+// SILK tables at once (segment t uses functions A/B[t*Ks ..]).  Returns, over
+// all S*nsets positions: perm (set index), rank (global bin id), rs (global
+// bin starts, nbins + 1) and nbins; bins of table t precede those of t + 1.
+geek_status make_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const int64_t *soff,
                       const uint32_t *sids, int Ks, const uint64_t *A, const uint64_t *B,
                       uint32_t **perm, int32_t **rank, int64_t **rs, int64_t *nbins, cudaStream_t st) {
-    uint64_t *klo, *khi = nullptr;
-    GK_TRY(scr.alloc(&klo, nsets));
-    if (Ks > 2) GK_TRY(scr.alloc(&khi, nsets));
-    GK_TRY(scr.alloc(perm, nsets));
+    const int64_t tot = (int64_t)S * nsets;
+    uint64_t *klo, *khi = nullptr, *k0, *slo, *shi = nullptr;
+    GK_TRY(scr.alloc(&klo, tot));
+    if (Ks > 2) GK_TRY(scr.alloc(&khi, tot));
+    GK_TRY(scr.alloc(&k0, tot));
+    GK_TRY(scr.alloc(&slo, tot));
+    if (Ks > 2) GK_TRY(scr.alloc(&shi, tot));
+    GK_TRY(scr.alloc(perm, tot));
+    const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nsets, 256), (int64_t)ctx->num_sms * 8));
     GK_COUNT();
-    k_set_sig<<<G(ctx, nsets), 256, 0, st>>>(nsets, soff, sids, Ks, A, B, klo, khi, *perm);
+    k_set_sig<<<dim3(gx, S), 256, 0, st>>>(nsets, soff, sids, Ks, A, B, klo, khi, *perm);
+    GK_COUNT();
+    k_first_component<<<G(ctx, tot), 256, 0, st>>>(tot, klo, khi, Ks, k0);
     GK_LAUNCH(ctx);
-    GK_TRY(radix_sort_segments(ctx, scr, 1, nsets, &klo, khi ? &khi : nullptr, perm, 32 * Ks, st));
-    int64_t *runs;
-    GK_TRY(scr.alloc(rank, nsets));
-    GK_TRY(scr.alloc(rs, nsets + 1));
-    GK_TRY(scr.alloc(&runs, 1));
-    GK_TRY(segment_runs(ctx, scr, 1, nsets, klo, khi, *rank, *rs, runs, st));
-    GK_TRY(d2h_i64(ctx, runs, nbins, st));
+    // stable sort by the first component (32 bits), then order every run of
+    // equal first components by the whole signature (runs are short: sets
+    // sharing a first component share that component's argmin object, which
+    // lies in at most one bucket per table, unless 32-bit values collide)
+    GK_TRY(radix_sort_segments(ctx, scr, S, nsets, &k0, nullptr, perm, 32, st));
+    int64_t *runs0, *rs0;
+    GK_TRY(scr.alloc(&runs0, S));
+    GK_TRY(scr.alloc(&rs0, (size_t)S * (nsets + 1)));
+    GK_TRY(segment_runs(ctx, scr, S, nsets, k0, nullptr, nullptr, rs0, runs0, st));
+    if (Ks > 1) {
+        GK_COUNT();
+        k_fix_runs<<<dim3(gx, S), 256, 0, st>>>(nsets, runs0, rs0, klo, khi, *perm);
+    }
+    GK_COUNT();
+    k_gather_sig<<<G(ctx, tot), 256, 0, st>>>(nsets, S, *perm, klo, khi, slo, shi);
+    GK_LAUNCH(ctx);
+    int64_t *runs, *rs_seg, *d_base;
+    GK_TRY(scr.alloc(rank, tot));
+    GK_TRY(scr.alloc(&rs_seg, (size_t)S * (nsets + 1)));
+    GK_TRY(scr.alloc(&runs, S));
+    GK_TRY(scr.alloc(&d_base, S));
+    GK_TRY(segment_runs(ctx, scr, S, nsets, slo, shi, *rank, rs_seg, runs, st));
+    std::vector<int64_t> h_runs(S), h_base(S);
+    GK_CUDA(ctx, cudaMemcpyAsync(h_runs.data(), runs, sizeof(int64_t) * S, cudaMemcpyDeviceToHost, st));
+    GK_CUDA(ctx, cudaStreamSynchronize(st));
+    int64_t total = 0, maxr = 1;
+    for (int t = 0; t < S; t++) {
+        h_base[t] = total;
+        total += h_runs[t];
+        maxr = std::max(maxr, h_runs[t]);
+    }
+    if (total > 0x7FFFFFFFLL) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "more than 2^31 SILK bins in one pass");
+    GK_CUDA(ctx, cudaMemcpyAsync(d_base, h_base.data(), sizeof(int64_t) * S, cudaMemcpyHostToDevice, st));
+    GK_TRY(scr.alloc(rs, total + 1));
+    GK_COUNT();
+    k_globalize_rank<<<G(ctx, tot), 256, 0, st>>>(nsets, S, d_base, *rank);
+    GK_COUNT();
+    k_globalize_rs<<<dim3((unsigned)std::min<int64_t>(ceil_div(maxr, 256), 4096), S), 256, 0, st>>>(
+        nsets, runs, d_base, rs_seg, *rs, S);
+    GK_LAUNCH(ctx);
+    *nbins = total;
     return GEEK_OK;
 }
 
@@ -600,6 +720,7 @@ geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p,
     const int64_t NB = b->NB;
     std::vector<Csr> parts;
     // ---- virtual buckets (see k_vb_count) -------------------------------------
+    EvTimer t_vb(ctx, "silk.vbuckets", st);
     const int64_t n = b->n;
     int32_t *mult;
     int64_t *ns_flag, *s_flag, *s_pos, *n_pos, *d_ns1, *d_ns2;
@@ -644,14 +765,25 @@ geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p,
     k_vb_members<<<G(ctx, NV), 256, 0, st>>>(NV, NS1, vsrc, voff, b->boff, b->members, vmem);
     GK_LAUNCH(ctx);
 
+    t_vb.stop();
     // ---- Alg. 4: Ls SILK tables over the (virtual) buckets ------------------
-    for (int t = 0; t < Ls && NV > 0; t++) {
-        Scratch tscr(ctx, st);  // per-table temporaries
+    // SILK tables are processed in chunks of S (all at once when they fit the
+    // position budget); bins of a chunk are numbered globally
+    const int64_t budget = (int64_t)1 << 27;
+    const int TS = (int)std::max<int64_t>(1, std::min<int64_t>(Ls, NV > 0 ? budget / NV : Ls));
+    for (int t = 0; t < Ls && NV > 0; t += TS) {
+        const int S = std::min(TS, Ls - t);
+        const int64_t M = (int64_t)S * NV;
+        Scratch tscr(ctx, st);  // per-chunk temporaries
         uint32_t *perm;
         int32_t *rank;
         int64_t *rs, nbins = 0;
-        GK_TRY(make_bins(ctx, tscr, NV, voff, vmem, Ks, p->mh_a + (int64_t)t * Ks, p->mh_b + (int64_t)t * Ks,
-                         &perm, &rank, &rs, &nbins, st));
+        {
+            EvTimer tb(ctx, "silk.bins", st);
+            GK_TRY(make_bins(ctx, tscr, S, NV, voff, vmem, Ks, p->mh_a + (int64_t)t * Ks, p->mh_b + (int64_t)t * Ks,
+                             &perm, &rank, &rs, &nbins, st));
+        }
+        EvTimer tv(ctx, "silk.vote", st);
         int64_t *bw, *has, *pick, *hpos, *d_nh;
         GK_TRY(tscr.alloc(&bw, nbins));
         GK_TRY(tscr.alloc(&has, nbins));
@@ -678,7 +810,7 @@ geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p,
             tparts.push_back(c1);
         }
         Csr c2;
-        GK_TRY(wvote_bins(ctx, tscr, NV, perm, rank, rs, nbins, voff, vmem, vw, bw, delta, &c2, st));
+        GK_TRY(wvote_bins(ctx, tscr, M, perm, rank, rs, nbins, voff, vmem, vw, bw, delta, &c2, st));
         if (c2.n) tparts.push_back(c2);
         for (auto &c : tparts) {
             // move the table's C_shared sets into the outer scratch
@@ -699,12 +831,13 @@ geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p,
     out->n_multiset = C.n;
 
     // ---- near-duplicate removal: one more table over C --------------------
+    EvTimer t_dd(ctx, "silk.dedup", st);
     std::vector<Csr> dparts;
     if (C.n > 0) {
         uint32_t *perm;
         int32_t *rank;
         int64_t *rs, nbins = 0;
-        GK_TRY(make_bins(ctx, scr, C.n, C.off, C.ids, Ks, p->dd_a, p->dd_b, &perm, &rank, &rs, &nbins, st));
+        GK_TRY(make_bins(ctx, scr, 1, C.n, C.off, C.ids, Ks, p->dd_a, p->dd_b, &perm, &rank, &rs, &nbins, st));
         Csr V;
         int64_t *ok;
         GK_TRY(vote_bins(ctx, scr, C.n, perm, rank, rs, nbins, C.off, C.ids, delta, &V, &ok, st));

@@ -7,7 +7,8 @@
 //
 // Persistent kernel, one CTA per SM, 10 warps:
 //   warp 0     TMA producer: X row tiles (double buffered) and centre tiles
-//              (2-stage ring), 128-byte swizzled, K-major
+//              (2-stage ring), 128-byte swizzled, K-major, plus |c|^2 of
+//              each centre tile by bulk copy
 //   warp 1     MMA issuer: tcgen05.mma.cta_group::1.kind::f16, M=128, N=256,
 //              into one of two TMEM accumulators (2 x 256 columns)
 //   warps 2-9  epilogue: tcgen05.ld of the accumulator, d' = |c|^2 - 2 s,
@@ -161,6 +162,26 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// d = -2 a + c on two lanes at once (fma.rn.f32x2: the same per-lane
+// rounding as fmaf(-2.f, a, c))
+__device__ __forceinline__ void ffma2_m2(float a0, float a1, float c0, float c1, float &d0, float &d1) {
+    asm("{ .reg .b64 ra, rc, rm, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rc, {%4, %5};\n\t"
+        "mov.b64 rm, {%6, %6};\n\t"
+        "fma.rn.f32x2 rd, rm, ra, rc;\n\t"
+        "mov.b64 {%0, %1}, rd; }"
+        : "=f"(d0), "=f"(d1)
+        : "f"(a0), "f"(a1), "f"(c0), "f"(c1), "f"(-2.f));
+}
+
+// three-input minimum
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
 // Rigorous half-window of the BF16 path for one object:
 //   inputs rounded to bf16 (u_b = 2^-8):    2 (2 u_b + u_b^2) |x| cmax
 //   FP32 accumulation in the tensor core:   2 (d + 16) 2^-21 |x| cmax
@@ -188,7 +209,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
     uint64_t *full_acc = bars + 8, *empty_acc = bars + 10, *done_bar = bars + 12;
     uint64_t *full_cn = bars + 13;  // 4 slots
     uint32_t *tmem_slot = (uint32_t *)(bars + 17);
-    float *mrg = (float *)(bars + 18);         // [128][3] second-half results
+    float *mrg = (float *)(bars + 18);  // [128][3] second-half results
     float *cn_s = (float *)(base + 2 * a_bytes + 2 * b_bytes + 2048);  // [4][256] |c|^2 ring
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -338,30 +359,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
                         const int64_t j0 = (int64_t)c * TC_N + h * 128 + ch * 32;
                         const float4 *cn4 = reinterpret_cast<const float4 *>(cnt + ch * 32);
                         float v[32];
-                        float tm = FLT_MAX;
 #pragma unroll
                         for (int i = 0; i < 8; i++) {
                             const float4 cc = cn4[i];
-                            v[4 * i + 0] = fmaf(-2.f, __uint_as_float(r[4 * i + 0]), cc.x);
-                            v[4 * i + 1] = fmaf(-2.f, __uint_as_float(r[4 * i + 1]), cc.y);
-                            v[4 * i + 2] = fmaf(-2.f, __uint_as_float(r[4 * i + 2]), cc.z);
-                            v[4 * i + 3] = fmaf(-2.f, __uint_as_float(r[4 * i + 3]), cc.w);
-                            tm = fminf(tm, fminf(fminf(v[4 * i], v[4 * i + 1]), fminf(v[4 * i + 2], v[4 * i + 3])));
+                            ffma2_m2(__uint_as_float(r[4 * i + 0]), __uint_as_float(r[4 * i + 1]), cc.x, cc.y,
+                                     v[4 * i + 0], v[4 * i + 1]);
+                            ffma2_m2(__uint_as_float(r[4 * i + 2]), __uint_as_float(r[4 * i + 3]), cc.z, cc.w,
+                                     v[4 * i + 2], v[4 * i + 3]);
                         }
-                        // all 32 values beyond the window of the current best:
-                        // none can be the argmin or spoil its certainty
-                        if (!(tm - b1 > Wc)) {
+                        float t11[11];
 #pragma unroll
-                            for (int i = 0; i < 32; i++) {
-                                const float x = v[i];
-                                if (x < b1) {
-                                    b2 = b1;
-                                    b1 = x;
-                                    i1 = (int)(j0 + i);
-                                } else {
-                                    b2 = fminf(b2, x);
-                                }
-                            }
+                        for (int i = 0; i < 10; i++) t11[i] = min3f(v[3 * i], v[3 * i + 1], v[3 * i + 2]);
+                        t11[10] = fminf(v[30], v[31]);
+                        const float tm = fminf(min3f(min3f(t11[0], t11[1], t11[2]), min3f(t11[3], t11[4], t11[5]),
+                                                     min3f(t11[6], t11[7], t11[8])),
+                                               fminf(t11[9], t11[10]));
+                        if (tm < b1) {
+                            // a new best in this chunk: its first position and
+                            // the chunk's second smallest value
+                            int idx = 31;
+#pragma unroll
+                            for (int i = 31; i >= 0; i--)
+                                if (v[i] == tm) idx = i;
+                            float m2 = FLT_MAX;
+#pragma unroll
+                            for (int i = 0; i < 32; i++) m2 = fminf(m2, i == idx ? FLT_MAX : v[i]);
+                            b2 = fminf(b1, m2);
+                            b1 = tm;
+                            i1 = (int)(j0 + idx);
+                        } else {
+                            // the best is unchanged; only the runner-up can move
+                            b2 = fminf(b2, tm);
                         }
                         if (ch < 3) tmem_wait_ld();
                     }

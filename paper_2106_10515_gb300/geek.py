@@ -44,7 +44,7 @@ class geek_hash_params(C.Structure):
 
 class geek_buckets_info(C.Structure):
     _fields_ = [("n", C.c_int64), ("L", C.c_int32), ("key_bits_max", C.c_int32),
-                ("n_buckets", C.c_int64), ("n_flagged", C.c_int64)]
+                ("n_buckets", C.c_int64), ("n_flagged", C.c_int64), ("n_flagged_fp64", C.c_int64)]
 
 
 class silk_params(C.Structure):
@@ -185,6 +185,7 @@ class Buckets:
         ctx._chk(lib().geek_buckets_info_get(self.h, C.byref(info)))
         self.n, self.L = info.n, info.L
         self.key_bits_max, self.n_buckets, self.n_flagged = info.key_bits_max, info.n_buckets, info.n_flagged
+        self.n_flagged_fp64 = info.n_flagged_fp64
 
     def copy_out(self):
         n, L = self.n, self.L

@@ -77,6 +77,7 @@ def test_dense_c2_shape_hash_and_assign(G, ctx):
     codes, ref = oracle.hash_dense(wl["x"], wl["a"], wl["b"], wl["w"], cfg.K, cfg.L)
     check_buckets(bk.copy_out(), ref, codes)
     assert bk.n_flagged > 0  # the window does flag elements at this scale
+    assert 0 <= bk.n_flagged_fp64 <= bk.n_flagged
     c = wl["centres"].astype(np.float64)
     lab_ref, dist_ref = oracle.assign_dense(wl["x"], c)
     for prec in (G.PREC_FP32, G.PREC_BF16):
