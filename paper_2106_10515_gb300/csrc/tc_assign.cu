@@ -14,6 +14,8 @@
 //   warps 2-9  epilogue: tcgen05.ld of the accumulator, d' = |c|^2 - 2 s,
 //              per-row best / second-best over the centres; each warp reads
 //              its TMEM lane quarter (warp % 4) and one half of the columns
+//              (each column group is an independent running minimum per
+//              row, so fewer groups mean fewer new-best rescans)
 // Every mbarrier wait is bounded: on expiry the kernel records
 // GEEK_ERR_TIMEOUT, stops issuing work, drains its own copies and MMAs, frees
 // its tensor memory and returns.
@@ -29,7 +31,11 @@ namespace {
 constexpr int TC_M = 128;
 constexpr int TC_N = 256;
 constexpr int TC_KB = 64;  // bf16 elements per 128-byte swizzle row
-constexpr int TC_EPI_WARPS = 8;
+constexpr int TC_EPI_WARPS = 8;                   // 2 per TMEM lane quarter
+constexpr int TC_EPI_GROUPS = TC_EPI_WARPS / 4;     // column groups per tile
+constexpr int TC_EPI_COLS = TC_N / TC_EPI_GROUPS;   // columns per warp
+constexpr int TC_EPI_CH = TC_EPI_COLS / 32;         // 32-column chunks per warp
+constexpr int TC_MISC = 2048;                       // barriers, TMEM slot, merge buffer
 constexpr int TC_THREADS = 32 * (2 + TC_EPI_WARPS);
 constexpr uint32_t TC_TMEM_COLS = 512;
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s per wait
@@ -209,8 +215,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
     uint64_t *full_acc = bars + 8, *empty_acc = bars + 10, *done_bar = bars + 12;
     uint64_t *full_cn = bars + 13;  // 4 slots
     uint32_t *tmem_slot = (uint32_t *)(bars + 17);
-    float *mrg = (float *)(bars + 18);  // [128][3] second-half results
-    float *cn_s = (float *)(base + 2 * a_bytes + 2 * b_bytes + 2048);  // [4][256] |c|^2 ring
+    float *mrg = (float *)(bars + 32);  // [groups-1][128][3] results of column groups 1..
+    float *cn_s = (float *)(base + 2 * a_bytes + 2 * b_bytes + TC_MISC);  // [4][256] |c|^2 ring
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nkb = A.Kp / TC_KB;
@@ -319,7 +325,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
         // ------------------------------------------------ epilogue
         const int ew = warp - 2;
         const int q = warp & 3;     // TMEM lane quarter this warp may access
-        const int h = ew >> 2;      // column half
+        const int h = ew >> 2;      // column group
         const int rloc = 32 * q + lane;
         uint64_t ct = 0;
         bool ok = true;
@@ -344,19 +350,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
                     fence_after();
                     // four 32-column chunks; the TMEM load of chunk ch + 1 is in
                     // flight while chunk ch is reduced
-                    const uint32_t tbase = tmem + (uint32_t)(s * TC_N + h * 128) + ((uint32_t)(32 * q) << 16);
-                    const float *cnt = cn_s + cs * TC_N + h * 128;
+                    const uint32_t tbase =
+                        tmem + (uint32_t)(s * TC_N + h * TC_EPI_COLS) + ((uint32_t)(32 * q) << 16);
+                    const float *cnt = cn_s + cs * TC_N + h * TC_EPI_COLS;
                     uint32_t ra[32], rb[32];
                     tmem_ld32_async(tbase, ra);
                     tmem_wait_ld();
 #pragma unroll
-                    for (int ch = 0; ch < 4; ch++) {
-                        if (ch < 3) {
+                    for (int ch = 0; ch < TC_EPI_CH; ch++) {
+                        if (ch < TC_EPI_CH - 1) {
                             if (ch & 1) tmem_ld32_async(tbase + (ch + 1) * 32, ra);
                             else tmem_ld32_async(tbase + (ch + 1) * 32, rb);
                         }
                         const uint32_t *r = (ch & 1) ? rb : ra;
-                        const int64_t j0 = (int64_t)c * TC_N + h * 128 + ch * 32;
+                        const int64_t j0 = (int64_t)c * TC_N + h * TC_EPI_COLS + ch * 32;
                         const float4 *cn4 = reinterpret_cast<const float4 *>(cnt + ch * 32);
                         float v[32];
 #pragma unroll
@@ -391,35 +398,40 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
                             // the best is unchanged; only the runner-up can move
                             b2 = fminf(b2, tm);
                         }
-                        if (ch < 3) tmem_wait_ld();
+                        if (ch < TC_EPI_CH - 1) tmem_wait_ld();
                     }
                     fence_before();
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty_acc[s]);
             }
-            // merge the two column halves of each row
+            // merge the column groups of each row
             asm volatile("bar.sync 1, %0;" ::"r"(32 * TC_EPI_WARPS) : "memory");
-            if (h == 1) {
-                mrg[rloc * 3 + 0] = b1;
-                mrg[rloc * 3 + 1] = b2;
-                mrg[rloc * 3 + 2] = __int_as_float(i1);
+            if (h > 0) {
+                float *m = mrg + ((h - 1) * TC_M + rloc) * 3;
+                m[0] = b1;
+                m[1] = b2;
+                m[2] = __int_as_float(i1);
             }
             asm volatile("bar.sync 1, %0;" ::"r"(32 * TC_EPI_WARPS) : "memory");
             if (h == 0 && row < A.n && ok) {
-                const float ob1 = mrg[rloc * 3 + 0], ob2 = mrg[rloc * 3 + 1];
-                const int oi1 = __float_as_int(mrg[rloc * 3 + 2]);
-                // equal best values leave b2 == b1: the row is then flagged
-                // and decided in FP64, so the provisional index is moot
-                float nb2;
-                if (ob1 < b1) {
-                    nb2 = fminf(b1, fminf(b2, ob2));
-                    b1 = ob1;
-                    i1 = oi1;
-                } else {
-                    nb2 = fminf(ob1, fminf(b2, ob2));
+#pragma unroll
+                for (int g = 1; g < TC_EPI_GROUPS; g++) {
+                    const float *m = mrg + ((g - 1) * TC_M + rloc) * 3;
+                    const float ob1 = m[0], ob2 = m[1];
+                    const int oi1 = __float_as_int(m[2]);
+                    // equal best values leave b2 == b1: the row is then
+                    // flagged and decided in FP64, so the index is moot
+                    float nb2;
+                    if (ob1 < b1) {
+                        nb2 = fminf(b1, fminf(b2, ob2));
+                        b1 = ob1;
+                        i1 = oi1;
+                    } else {
+                        nb2 = fminf(ob1, fminf(b2, ob2));
+                    }
+                    b2 = nb2;
                 }
-                b2 = nb2;
                 const bool valid = i1 != 0x7FFFFFFF;
                 A.labels[row] = valid ? i1 : -1;
                 const bool sure = valid && (A.k == 1 || b2 - b1 > Wc);
@@ -549,8 +561,9 @@ geek_status assign_tc_bf16(geek_ctx *ctx, Scratch &scr, const float *x, int64_t 
     A.flag_rows = flag_rows;
     A.n_flag = n_flag;
     A.err = err;
-    // tiles + 2 KB (barriers, TMEM slot, merge buffer) + 4 KB |c|^2 ring + alignment
-    const size_t smem = 1024 + 2 * (size_t)TC_M * Kp * 2 + 2 * (size_t)TC_N * Kp * 2 + 2048 + 4 * TC_N * 4;
+    // tiles + barriers / TMEM slot / merge buffer + 4 KB |c|^2 ring + alignment
+    static_assert(32 * 8 + (TC_EPI_GROUPS - 1) * TC_M * 3 * 4 <= TC_MISC, "misc region too small");
+    const size_t smem = 1024 + 2 * (size_t)TC_M * Kp * 2 + 2 * (size_t)TC_N * Kp * 2 + TC_MISC + 4 * TC_N * 4;
     GK_CUDA(ctx, cudaFuncSetAttribute(k_assign_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = (int)std::min<int64_t>(A.ntiles_r, ctx->num_sms);
     {
