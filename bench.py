@@ -117,17 +117,27 @@ def workload(args):
     return wl, time.time() - t0
 
 
+TRAFFIC_PROFILES = {"kernel.assign_tc": "k_assign_tc_dense_n1M_d128_k20000.md"}
+
+
 def traffic_for(kernel):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the kernel source as it is now (else None)."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}.traffic.json")
-    if not os.path.exists(path):
+    """DRAM bytes per full-size launch from the committed ncu summary of the
+    kernel, if it was taken on the kernel source as it is now (else None)."""
+    name = TRAFFIC_PROFILES.get(kernel)
+    path = os.path.join(ROOT, "profiles", name) if name else None
+    if not path or not os.path.exists(path):
         return None
-    rec = json.load(open(path))
-    src = os.path.join(ROOT, rec["source"])
-    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["source_sha256"]:
+    rec = {}
+    for line in open(path):
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            rec[k.strip()] = v.strip()
+    try:
+        src = os.path.join(ROOT, rec["source"])
+        ok = hashlib.sha256(open(src, "rb").read()).hexdigest() == rec["source_sha256"]
+        return float(rec["dram_bytes_per_launch_full_size"]) if ok else None
+    except (KeyError, OSError, ValueError):
         return None
-    return rec["dram_bytes_per_launch_full_size"]
 
 
 def run_ours(args):
