@@ -260,6 +260,103 @@ geek_status geek_assign_centers_noalloc(const float *x, int64_t n, int32_t d, in
                                         const double *centers, int64_t k, int32_t *labels,
                                         geek_stream stream);
 
+/* ---- batched instances ------------------------------------------------------ */
+
+/* Many independent dense clustering problems of uneven n, d and seed count run
+ * as one batch: the whole pipeline above (E2LSH / SRP hashing, bucket grouping,
+ * SILK seeding, centroids and the one-pass assignment, Sects. 3.1-3.3) for every
+ * instance, with each step launched once for all instances.  The hashing pass
+ * runs every instance's row blocks in one launch and the BF16 tcgen05 assignment
+ * runs all (instance, row tile) units in one persistent launch; both phases are
+ * captured in CUDA graphs on the first run and replayed by later runs.  The
+ * centre-tile width of the assignment (64, 128 or 256 columns) is chosen per
+ * instance by an autotuner that times the candidates on the batch's own data
+ * the first time a (d, seed count) class is seen on a context.
+ * Results are, instance by instance, exactly those of geek_hash + silk_seed +
+ * geek_assign (GEEK_PREC_BF16) on that instance alone. */
+typedef struct geek_batch geek_batch;
+
+/* One dense instance: x (n x d float32, row stride ldx, n >= 0, 1 <= d <= 128),
+ * its K*L projections a (K*L x d float32) and offsets b (K*L float32), bucket
+ * width w (E2LSH), and its SILK coefficients mh_a/mh_b (Ls*Ks pairs) and
+ * dd_a/dd_b (Ks pairs) as in silk_params.  Device arrays; they must stay
+ * valid, at the same addresses, for the life of the batch (their contents
+ * may change between runs). */
+typedef struct geek_instance {
+    int64_t n;
+    int32_t d;
+    int64_t ldx;
+    const float *x;
+    const float *a;
+    const float *b;
+    double w;
+    const uint64_t *mh_a, *mh_b;
+    const uint64_t *dd_a, *dd_b;
+} geek_instance;
+
+/* Shared by every instance: projection family, K functions per table, L
+ * tables, SILK Ks / Ls / delta, and tile_n: 0 = autotuned, or 64 / 128 / 256
+ * to force the assignment's centre-tile width. */
+typedef struct geek_batch_params {
+    int32_t proj;
+    int32_t K, L;
+    int32_t Ks, Ls, delta;
+    int32_t tile_n;
+} geek_batch_params;
+
+typedef struct geek_batch_info {
+    int32_t count;            /* instances */
+    int64_t n_total;          /* objects over all instances */
+    int64_t k_total;          /* seeds over all instances (last run) */
+    int64_t n_buckets;        /* buckets over all instances and tables */
+    int64_t n_flagged;        /* projection elements rechecked */
+    int64_t n_flagged_fp64;   /* of those, decided by the FP64 reference */
+    int64_t n_recheck_rows;   /* objects whose argmin was decided in FP64 */
+    int32_t key_bits;         /* composite sort key width (instance id + key) */
+    int32_t graph_launches;   /* CUDA graph replays so far (hash + assignment) */
+    int32_t graph_captures;   /* graphs captured so far */
+    int32_t tuned_classes;    /* (d, k) classes this batch timed for tile_n */
+} geek_batch_info;
+
+/* Creates a batch of `count` (1..65535) instances; validates the parameters
+ * and sets up the hashing phase (nothing runs yet).  Instances are numbered
+ * 0..count-1 and their objects concatenated in that order (global row
+ * r = sum of earlier n + local row).  Errors: INVALID, UNSUPPORTED (d > 128,
+ * more than 2^31 - 1 objects, K*L > 512), NOMEM, CUDA. */
+geek_status geek_batch_create(geek_ctx *ctx, const geek_instance *inst, int32_t count,
+                              const geek_batch_params *p, geek_batch **out);
+
+/* Runs the whole pipeline for every instance on `stream`.  labels: n_total
+ * int32 (device), instance i's labels at its global rows, as seed indices
+ * local to the instance (0..k_i-1, or -1 when the instance has no seed).
+ * Returns after the run has finished on the device (the seed counts it
+ * needs are read back mid-way).  Calls on one batch must not overlap. */
+geek_status geek_batch_run(geek_batch *b, int32_t *labels, geek_stream stream);
+
+geek_status geek_batch_info_get(const geek_batch *b, geek_batch_info *info);
+
+/* Per-instance results of the last run, HOST arrays of `count` entries (each
+ * pointer may be NULL): seed count k, SSE and largest distance to the
+ * assigned centre (Sect. 4.1), and the assignment's centre-tile width. */
+geek_status geek_batch_instance_stats(const geek_batch *b, int64_t *k, double *sse, double *radius_max,
+                                      int32_t *tile_n);
+
+/* Device copies of the last run's intermediate results (each pointer may be
+ * NULL):
+ *  codes       n_total x (K*L) int32 per-function codes
+ *  obj_bucket  L x n_total int32: per instance, the canonical bucket id of
+ *              geek_hash on that instance alone (ranks restart at 0)
+ *  seed_off    k_total + 1 int64 and seed_ids (int32, local ids): the seeds
+ *              of all instances in instance order, each instance's in its
+ *              canonical order
+ *  centres     sum_i k_i * d_i float64: instance i's k_i x d_i centroids,
+ *              instances in order */
+geek_status geek_batch_copy_out(const geek_batch *b, int32_t *codes, int32_t *obj_bucket, int64_t *seed_off,
+                                int32_t *seed_ids, double *centres, geek_stream stream);
+/* Seed id count of the last run (the size of seed_ids). */
+geek_status geek_batch_seed_ids_count(const geek_batch *b, int64_t *n_ids);
+geek_status geek_batch_destroy(geek_batch *b);
+
 /* ---- tracing -------------------------------------------------------------- */
 
 /* When on, every phase (names "hash", "silk", "assign") and the main kernels

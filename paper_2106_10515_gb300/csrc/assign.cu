@@ -162,13 +162,12 @@ __global__ void __launch_bounds__(256) k_assign_fp32(const float *__restrict__ x
 }
 
 // Exact decision for one flagged object: FP32 filter over all centres, then
-// the FP64 reference distance for every centre inside the window.
-__global__ void __launch_bounds__(256) k_assign_recheck(const float *__restrict__ x, int64_t ldx, int d,
-                                                        const float *__restrict__ c32, const float *__restrict__ cn,
-                                                        const double *__restrict__ c64, int64_t k, float cmax,
+// the FP64 reference distance for every centre inside the window.  Flag
+// entries are global rows; instance i owns rows [row_off[i], row_off[i+1]).
+__global__ void __launch_bounds__(256) k_assign_recheck(const RInst *__restrict__ R,
+                                                        const int64_t *__restrict__ row_off, int count,
                                                         const int32_t *__restrict__ flag_rows,
-                                                        const unsigned long long *__restrict__ n_flag,
-                                                        int32_t *__restrict__ labels) {
+                                                        const unsigned long long *__restrict__ n_flag) {
     extern __shared__ float xr[];  // d floats
     __shared__ float red_f[256];
     __shared__ double red_d[256];
@@ -176,9 +175,15 @@ __global__ void __launch_bounds__(256) k_assign_recheck(const float *__restrict_
     const int t = threadIdx.x;
     const int64_t nf = (int64_t)*n_flag;
     for (int64_t q = blockIdx.x; q < nf; q += gridDim.x) {
-        const int64_t row = flag_rows[q];
+        const int64_t grow = flag_rows[q];
+        const RInst &I = R[find_inst(row_off, count, grow)];
+        const int64_t row = grow - I.row_base;
+        const int d = I.d;
+        const int64_t k = I.k;
+        const float *c32 = I.c32, *cn = I.cn;
+        const float cmax = __uint_as_float(*I.cmax_bits);
         __syncthreads();
-        for (int kk = t; kk < d; kk += 256) xr[kk] = x[row * ldx + kk];
+        for (int kk = t; kk < d; kk += 256) xr[kk] = I.x[row * I.ldx + kk];
         __syncthreads();
         float xs2 = 0.f;
         for (int kk = 0; kk < d; kk++) xs2 = fmaf(xr[kk], xr[kk], xs2);
@@ -202,7 +207,7 @@ __global__ void __launch_bounds__(256) k_assign_recheck(const float *__restrict_
             float dot = 0.f;
             for (int kk = 0; kk < d; kk++) dot = fmaf(xr[kk], c32[j * d + kk], dot);
             if (fmaf(-2.f, dot, cn[j]) <= lim) {
-                const double D = ref_dist(xr, c64 + j * d, d);
+                const double D = ref_dist(xr, I.c64 + j * d, d);
                 if (D < bD || (D == bD && (int)j < bj)) {
                     bD = D;
                     bj = (int)j;
@@ -225,24 +230,28 @@ __global__ void __launch_bounds__(256) k_assign_recheck(const float *__restrict_
         }
         // no candidate with a distance below +inf (non-finite input): -1,
         // as the reference argmin that never improves on +inf
-        if (t == 0) labels[row] = red_i[0] == 0x7FFFFFFF ? -1 : red_i[0];
+        if (t == 0) I.labels[row] = red_i[0] == 0x7FFFFFFF ? -1 : red_i[0];
     }
 }
 
-// centre preparation: FP32 copy, |c|^2 (FP64 then rounded), max |c|
-__global__ void k_centre_prep(const double *__restrict__ c64, int64_t k, int d, float *__restrict__ c32,
-                              float *__restrict__ cn, unsigned *__restrict__ cmax_bits) {
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k;
-         j += (int64_t)gridDim.x * blockDim.x) {
+// centre preparation: FP32 copy, |c|^2 (FP64 then rounded), max |c|;
+// thread per global centre e of instance find_inst(k_off, e)
+__global__ void k_centre_prep(const CInst *__restrict__ C, const int64_t *__restrict__ k_off, int count,
+                              int64_t ktot) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ktot;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const CInst &I = C[find_inst(k_off, count, e)];
+        const int64_t j = e - I.k_base;
+        const int d = I.d;
         double s = 0.0;
         for (int t = 0; t < d; t++) {
-            const double v = c64[j * d + t];
-            c32[j * d + t] = (float)v;
+            const double v = I.c64[j * d + t];
+            I.c32[j * d + t] = (float)v;
             s += v * v;
         }
-        cn[j] = (float)s;
+        I.cn[j] = (float)s;
         const float nrm = (float)sqrt(s) * (1.f + 1e-6f);
-        atomicMax(cmax_bits, __float_as_uint(nrm));  // non-negative floats order as uints
+        atomicMax(I.cmax_bits, __float_as_uint(nrm));  // non-negative floats order as uints
     }
 }
 
@@ -318,8 +327,17 @@ __global__ void k_stats_final(const double *__restrict__ ps, const float *__rest
     }
 }
 
-// centroid of each seed: FP64 sum over members in ascending id, one IEEE
-// division by the count; one thread per (seed, coordinate)
+// centroid coordinate t of the seed with members sids[s0 .. s1) (ascending
+// ids, rows x + (id - row_base) * ldx): FP64 sum in member order, one IEEE
+// division by the count
+__device__ __forceinline__ double centroid_coord(const float *__restrict__ x, int64_t ldx, int64_t row_base,
+                                                 const int32_t *__restrict__ sids, int64_t s0, int64_t s1, int t) {
+    double s = 0.0;
+    for (int64_t p = s0; p < s1; p++) s = __dadd_rn(s, (double)x[((int64_t)sids[p] - row_base) * ldx + t]);
+    return __ddiv_rn(s, (double)(s1 - s0));
+}
+
+// centroid of each seed; one thread per (seed, coordinate)
 __global__ void k_centroids(const float *__restrict__ x, int64_t ldx, int d, int64_t k,
                             const int64_t *__restrict__ soff, const int32_t *__restrict__ sids,
                             double *__restrict__ c) {
@@ -328,9 +346,89 @@ __global__ void k_centroids(const float *__restrict__ x, int64_t ldx, int d, int
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j = e / d;
         const int t = (int)(e % d);
+        c[e] = centroid_coord(x, ldx, 0, sids, soff[j], soff[j + 1], t);
+    }
+}
+
+// batched: thread per (global seed, coordinate < dmax); instance i owns
+// seeds [seed_inst_off[i], seed_inst_off[i + 1])
+__global__ void k_centroids_batch(const CenInst *__restrict__ C, const int64_t *__restrict__ seed_inst_off,
+                                  int count, int64_t ktot, int dmax, const int64_t *__restrict__ soff,
+                                  const int32_t *__restrict__ sids) {
+    const int64_t total = ktot * dmax;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = e / dmax;
+        const int t = (int)(e % dmax);
+        const CenInst &I = C[find_inst(seed_inst_off, count, s)];
+        if (t >= I.d) continue;
+        I.c[(s - I.seed_base) * I.d + t] = centroid_coord(I.x, I.ldx, I.row_base, sids, soff[s], soff[s + 1], t);
+    }
+}
+
+// batched SSE / radius partials: block per 128-row unit (instance, tile),
+// warp per row, squares of (x - c_hi) - c_lo accumulated in FP32
+__global__ void __launch_bounds__(256) k_assign_stats_batch(const SInst *__restrict__ S, const int2 *__restrict__ units,
+                                                            int64_t nunits, double *__restrict__ part_sum,
+                                                            float *__restrict__ part_max) {
+    __shared__ double ss[8];
+    __shared__ float sm_[8];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+        const int2 un = units[u];
+        const SInst &I = S[un.x];
         double s = 0.0;
-        for (int64_t p = soff[j]; p < soff[j + 1]; p++) s = __dadd_rn(s, (double)x[(int64_t)sids[p] * ldx + t]);
-        c[e] = __ddiv_rn(s, (double)(soff[j + 1] - soff[j]));
+        float mx = 0.f;
+        for (int r = wib; r < 128; r += 8) {
+            const int64_t i = (int64_t)un.y * 128 + r;
+            if (i >= I.n) break;
+            const int j = I.labels[i];
+            if (j < 0 || j >= I.k) continue;  // uniform across the warp
+            const float *xr = I.x + i * I.ldx;
+            const float *h = I.chi + (int64_t)j * I.d;
+            const float *l = I.clo + (int64_t)j * I.d;
+            float D = 0.f;
+            for (int t = lane; t < I.d; t += 32) {
+                const float e = (xr[t] - h[t]) - l[t];
+                D = fmaf(e, e, D);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) D += __shfl_xor_sync(0xffffffffu, D, o);
+            s += (double)D;
+            mx = fmaxf(mx, D);
+        }
+        __syncthreads();
+        if (lane == 0) {
+            ss[wib] = s;
+            sm_[wib] = mx;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0.0;
+            float m = 0.f;
+            for (int w = 0; w < 8; w++) {
+                a += ss[w];
+                m = fmaxf(m, sm_[w]);
+            }
+            part_sum[u] = a;
+            part_max[u] = m;
+        }
+    }
+}
+
+// per instance: its units' partials in unit order (deterministic)
+__global__ void k_stats_final_batch(const double *__restrict__ ps, const float *__restrict__ pm,
+                                    const int64_t *__restrict__ unit_off, int count, double *__restrict__ sse,
+                                    double *__restrict__ rmax) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        float m = 0.f;
+        for (int64_t u = unit_off[i]; u < unit_off[i + 1]; u++) {
+            s += ps[u];
+            m = fmaxf(m, pm[u]);
+        }
+        sse[i] = s;
+        rmax[i] = sqrt((double)m);
     }
 }
 
@@ -370,8 +468,25 @@ geek_status assign_dense_centres(geek_ctx *ctx, Scratch &scr, const float *x, in
     GK_TRY(scr.alloc(&cn, k));
     GK_TRY(scr.alloc(&cmax_bits, 1));
     GK_CUDA(ctx, cudaMemsetAsync(cmax_bits, 0, sizeof(unsigned), st));
+    // one-instance tables for the instance-driven kernels
+    CInst *ci;
+    RInst *ri;
+    int64_t *koff, *roff;
+    GK_TRY(scr.alloc(&ci, 1));
+    GK_TRY(scr.alloc(&ri, 1));
+    GK_TRY(scr.alloc(&koff, 2));
+    GK_TRY(scr.alloc(&roff, 2));
+    {
+        const CInst hc{centres, c32, cn, cmax_bits, d, 0};
+        const RInst hr{x, ldx, d, c32, cn, centres, k, cmax_bits, labels, 0};
+        const int64_t hk[2] = {0, k}, hn[2] = {0, n};
+        GK_CUDA(ctx, cudaMemcpyAsync(ci, &hc, sizeof hc, cudaMemcpyHostToDevice, st));
+        GK_CUDA(ctx, cudaMemcpyAsync(ri, &hr, sizeof hr, cudaMemcpyHostToDevice, st));
+        GK_CUDA(ctx, cudaMemcpyAsync(koff, hk, sizeof hk, cudaMemcpyHostToDevice, st));
+        GK_CUDA(ctx, cudaMemcpyAsync(roff, hn, sizeof hn, cudaMemcpyHostToDevice, st));
+    }
     GK_COUNT();
-    k_centre_prep<<<grid_for(k, 128, ctx->num_sms), 128, 0, st>>>(centres, k, d, c32, cn, cmax_bits);
+    k_centre_prep<<<grid_for(k, 128, ctx->num_sms), 128, 0, st>>>(ci, koff, 1, k);
     GK_LAUNCH(ctx);
     unsigned h_bits = 0;
     GK_CUDA(ctx, cudaMemcpyAsync(&h_bits, cmax_bits, sizeof h_bits, cudaMemcpyDeviceToHost, st));
@@ -402,8 +517,7 @@ geek_status assign_dense_centres(geek_ctx *ctx, Scratch &scr, const float *x, in
         const int blocks = (int)std::min<unsigned long long>(h_flag, (unsigned long long)ctx->num_sms * 8);
         EvTimer tk(ctx, "kernel.assign_recheck", st);
         GK_COUNT();
-        k_assign_recheck<<<blocks, 256, d * sizeof(float), st>>>(x, ldx, d, c32, cn, centres, k, cmax, flag_rows,
-                                                                  n_flag, labels);
+        k_assign_recheck<<<blocks, 256, d * sizeof(float), st>>>(ri, roff, 1, flag_rows, n_flag);
         GK_LAUNCH(ctx);
     }
     if (stats) {
@@ -434,3 +548,59 @@ geek_status assign_dense_centres(geek_ctx *ctx, Scratch &scr, const float *x, in
     return GEEK_OK;
 }
 
+geek_status centroids_batch(geek_ctx *ctx, const CenInst *C, const int64_t *seed_inst_off, int count, int64_t ktot,
+                            int dmax, const int64_t *soff, const int32_t *sids, cudaStream_t st) {
+    if (ktot == 0) return GEEK_OK;
+    GK_COUNT();
+    k_centroids_batch<<<grid_for(ktot * dmax, 256, ctx->num_sms), 256, 0, st>>>(C, seed_inst_off, count, ktot, dmax,
+                                                                              soff, sids);
+    GK_LAUNCH(ctx);
+    return GEEK_OK;
+}
+
+geek_status centre_prep_batch(geek_ctx *ctx, const CInst *C, const int64_t *k_off, int count, int64_t ktot,
+                              cudaStream_t st) {
+    if (ktot == 0) return GEEK_OK;
+    GK_COUNT();
+    k_centre_prep<<<grid_for(ktot, 128, ctx->num_sms), 128, 0, st>>>(C, k_off, count, ktot);
+    GK_LAUNCH(ctx);
+    return GEEK_OK;
+}
+
+geek_status recheck_batch(geek_ctx *ctx, const RInst *R, const int64_t *row_off, int count, int dmax,
+                          const int32_t *flag_rows, const unsigned long long *n_flag, cudaStream_t st) {
+    EvTimer tk(ctx, "kernel.assign_recheck", st);
+    GK_COUNT();
+    k_assign_recheck<<<ctx->num_sms * 8, 256, dmax * sizeof(float), st>>>(R, row_off, count, flag_rows, n_flag);
+    GK_LAUNCH(ctx);
+    return GEEK_OK;
+}
+
+geek_status centre_split(geek_ctx *ctx, const double *c64, int64_t total, float *chi, float *clo, cudaStream_t st) {
+    if (total == 0) return GEEK_OK;
+    GK_COUNT();
+    k_centre_split<<<grid_for(total, 256, ctx->num_sms), 256, 0, st>>>(c64, total, chi, clo);
+    GK_LAUNCH(ctx);
+    return GEEK_OK;
+}
+
+geek_status stats_batch(geek_ctx *ctx, const SInst *S, const int2 *units, int64_t nunits, const int64_t *unit_off,
+                        int count, double *part_sum, float *part_max, double *sse, double *rmax, cudaStream_t st) {
+    if (nunits > 0) {
+        GK_COUNT();
+        k_assign_stats_batch<<<(int)std::min<int64_t>(nunits, (int64_t)ctx->num_sms * 16), 256, 0, st>>>(
+            S, units, nunits, part_sum, part_max);
+    }
+    GK_COUNT();
+    k_stats_final_batch<<<(count + 127) / 128, 128, 0, st>>>(part_sum, part_max, unit_off, count, sse, rmax);
+    GK_LAUNCH(ctx);
+    return GEEK_OK;
+}
+
+geek_status fill_labels(geek_ctx *ctx, int32_t *labels, int64_t n, int32_t v, cudaStream_t st) {
+    if (n == 0) return GEEK_OK;
+    GK_COUNT();
+    k_fill_labels<<<grid_for(n, 256, ctx->num_sms), 256, 0, st>>>(labels, n, v);
+    GK_LAUNCH(ctx);
+    return GEEK_OK;
+}

@@ -19,12 +19,16 @@ struct geek_ctx {
     std::string last_error;
     // CUDA-event timing of phases and kernels (off by default)
     bool timing = false;
+    bool capturing = false;  // a stream capture is open: no event brackets
     struct Timed {
         double ms = 0.0;
         long long count = 0;
         double work = 0.0;  // algorithmic bytes or flops of the bracketed work
     };
     std::map<std::string, Timed> times;
+    // centre-tile width chosen by the batch autotuner per (padded d << 8 |
+    // seed-count class)
+    std::map<int, int> tile_cache;
 };
 
 // Brackets work on a stream with CUDA events when ctx->timing is on; the
@@ -37,7 +41,8 @@ struct EvTimer {
     cudaEvent_t a = nullptr, b = nullptr;
     double work = 0.0;
     EvTimer(geek_ctx *c, const char *nm, cudaStream_t s) : ctx(c), name(nm), st(s) {
-        if (ctx && ctx->timing && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
+        if (ctx && ctx->timing && !ctx->capturing && cudaEventCreate(&a) == cudaSuccess &&
+            cudaEventCreate(&b) == cudaSuccess)
             cudaEventRecord(a, st);
     }
     void stop() {
@@ -147,6 +152,19 @@ __device__ __forceinline__ uint32_t mh_hash32(uint64_t A, uint64_t B, uint32_t x
     return hi;
 }
 
+// Largest i < count with off[i] <= v: the instance (or block range) holding
+// global index v, for ascending offsets off[0..count] (empty ranges are
+// skipped because a later equal offset wins).
+static __device__ __forceinline__ int find_inst(const int64_t *__restrict__ off, int count, int64_t v) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= v) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // ---------------------------------------------------------------------------
 // Internal building blocks (implemented in the .cu files)
 // ---------------------------------------------------------------------------
@@ -169,6 +187,11 @@ geek_status radix_sort_segments(geek_ctx *ctx, Scratch &scr, int S, int64_t m, u
 geek_status segment_runs(geek_ctx *ctx, Scratch &scr, int S, int64_t m, const uint64_t *key_lo,
                          const uint64_t *key_hi, int32_t *rank, int64_t *run_start, int64_t *runs,
                          cudaStream_t st);
+// As segment_runs, with an optional tag per position (S x m, may be null):
+// a run also starts where the tag changes.
+geek_status segment_runs_tagged(geek_ctx *ctx, Scratch &scr, int S, int64_t m, const uint64_t *key_lo,
+                                const uint64_t *key_hi, const uint32_t *tag, int32_t *rank, int64_t *run_start,
+                                int64_t *runs, cudaStream_t st);
 
 // Exclusive prefix sum of n int64 values (in place allowed); total -> *total_dev.
 geek_status exclusive_scan_i64(geek_ctx *ctx, Scratch &scr, const int64_t *in, int64_t *out,

@@ -25,25 +25,9 @@ constexpr int PJ_FPT = 8;       // functions per thread
 constexpr int PJ_RPT = 8;       // rows per thread
 constexpr int PJ_MAXT = 256;    // threads per block (upper bound)
 
-struct ProjArgs {
-    const float *x;
-    int64_t ldx;
-    int64_t n;
-    int d;
-    int F, FPAD, FG, RG;  // functions, padded to 8, function groups, row groups
-    const float *a;       // F x d
-    const float *b;       // F
-    const float *anorm;   // F
-    float w, inv_w;
-    int srp;
-    int32_t *codes;       // n x F
-    uint64_t *flags;      // (row << 16 | f)
-    unsigned long long *n_flags;
-    int64_t flag_cap;
-    int *fmin, *fmax;     // F
-};
 
-__global__ void __launch_bounds__(PJ_MAXT) k_project_fp32(ProjArgs A) {
+// One block: rows [tile * TR, tile * TR + TR) of instance A.
+__device__ __forceinline__ void project_block(const ProjArgs &A, int64_t tile) {
     extern __shared__ float sm[];
     const int TR = A.RG * PJ_RPT;
     float *xs = sm;                       // [PJ_KC][TR]
@@ -53,7 +37,7 @@ __global__ void __launch_bounds__(PJ_MAXT) k_project_fp32(ProjArgs A) {
     const int nthr = A.FG * A.RG;
     const int fg = t % A.FG, rg = t / A.FG;
     const bool active = t < nthr;
-    const int64_t row0 = (int64_t)blockIdx.x * TR;
+    const int64_t row0 = tile * TR;
     for (int f = t; f < A.F; f += blockDim.x) {
         smin[f] = INT32_MAX;
         smax[f] = INT32_MIN;
@@ -197,7 +181,7 @@ __global__ void __launch_bounds__(PJ_MAXT) k_project_fp32(ProjArgs A) {
             flagmask &= flagmask - 1;
             const int64_t row = row0 + rg * PJ_RPT + bit / PJ_FPT;
             const int f = fg * PJ_FPT + bit % PJ_FPT;
-            if ((int64_t)pos < A.flag_cap) A.flags[pos] = ((uint64_t)row << 16) | (uint64_t)f;
+            if ((int64_t)pos < A.flag_cap) A.flags[pos] = ((uint64_t)(A.row_base + row) << 16) | (uint64_t)f;
             pos++;
         }
     }
@@ -208,6 +192,25 @@ __global__ void __launch_bounds__(PJ_MAXT) k_project_fp32(ProjArgs A) {
             atomicMax(&A.fmax[f], smax[f]);
         }
     }
+}
+
+__global__ void __launch_bounds__(PJ_MAXT) k_project_fp32(const __grid_constant__ ProjArgs A) {
+    project_block(A, blockIdx.x);
+}
+
+// Batched form: the blocks of all instances in one launch; block b works on
+// instance i with tile_off[i] <= b < tile_off[i + 1].
+__global__ void __launch_bounds__(PJ_MAXT) k_project_fp32_batch(const ProjArgs *__restrict__ P,
+                                                                const int64_t *__restrict__ tile_off, int count) {
+    __shared__ ProjArgs sA;
+    __shared__ int64_t s_tile;
+    if (threadIdx.x == 0) {
+        const int i = find_inst(tile_off, count, blockIdx.x);
+        sA = P[i];
+        s_tile = (int64_t)blockIdx.x - tile_off[i];
+    }
+    __syncthreads();
+    project_block(sA, s_tile);
 }
 
 __global__ void k_row_norms(const float *__restrict__ a, int F, int d, float *__restrict__ out) {
@@ -237,27 +240,31 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
 // exact value equals the final sum plus all error terms; only the float
 // summation of those error terms is inexact, by at most
 // gamma_2d * (d + 1) u sum|a_j x_j| <= 2.2 (2d)(d+1) u^2 |a||x|.
+// Flag entries carry global rows (row_base + local row); instance i holds
+// global rows [row_off[i], row_off[i + 1]).
 __global__ void __launch_bounds__(256) k_recheck_dot2(
-    const float *__restrict__ x, int64_t ldx, int d, const float *__restrict__ a, const float *__restrict__ b,
-    double w, int srp, int F, const float *__restrict__ anorm, const uint64_t *__restrict__ flags,
-    const unsigned long long *__restrict__ n_flags, int64_t cap, int32_t *__restrict__ codes, int *__restrict__ fmin,
-    int *__restrict__ fmax, uint64_t *__restrict__ flags2, unsigned long long *__restrict__ n_flags2) {
+    const ProjArgs *__restrict__ P, const int64_t *__restrict__ row_off, int count, int srp, int F,
+    const uint64_t *__restrict__ flags, const unsigned long long *__restrict__ n_flags, int64_t cap,
+    uint64_t *__restrict__ flags2, unsigned long long *__restrict__ n_flags2) {
     const int64_t nf = min((int64_t)*n_flags, cap);
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const double u = 5.9604644775390625e-08;  // 2^-24
-    const double cfac = 2.2 * (2.0 * d) * (d + 1.0) * u * u + (double)d * 2.220446049250313e-16;
     for (int64_t base = warp * 32; base < nf; base += nw * 32) {
         const int cnt = (int)min((int64_t)32, nf - base);
         const uint64_t mine = lane < cnt ? flags[base + lane] : 0;
+        const int my_inst = lane < cnt ? find_inst(row_off, count, (int64_t)(mine >> 16)) : 0;
         float my_sh = 0.f, my_sc = 0.f, my_xx = 0.f;
         for (int kk = 0; kk < cnt; kk++) {
             const uint64_t e = __shfl_sync(0xffffffffu, mine, kk);
-            const int64_t row = (int64_t)(e >> 16);
+            const int ii = __shfl_sync(0xffffffffu, my_inst, kk);
+            const ProjArgs &A = P[ii];
+            const int d = A.d;
+            const int64_t row = (int64_t)(e >> 16) - A.row_base;
             const int f = (int)(e & 0xFFFF);
-            const float *xr = x + row * ldx;
-            const float *ar = a + (int64_t)f * d;
+            const float *xr = A.x + row * A.ldx;
+            const float *ar = A.a + (int64_t)f * d;
             float sh = 0.f, sc = 0.f, xx = 0.f;
             for (int j = lane; j < d; j += 32) {
                 const float av = ar[j], xv = xr[j];
@@ -287,10 +294,14 @@ __global__ void __launch_bounds__(256) k_recheck_dot2(
         }
         if (lane >= cnt) continue;
         const uint64_t e = mine;
-        const int64_t row = (int64_t)(e >> 16);
+        const ProjArgs &A = P[my_inst];
+        const int d = A.d;
+        const double w = A.wd;
+        const double cfac = 2.2 * (2.0 * d) * (d + 1.0) * u * u + (double)d * 2.220446049250313e-16;
+        const int64_t row = (int64_t)(e >> 16) - A.row_base;
         const int f = (int)(e & 0xFFFF);
         const double S = (double)my_sh + (double)my_sc;
-        const double an = (double)anorm[f], xn = (double)(sqrtf(my_xx) * (1.0f + 1.0e-3f));
+        const double an = (double)A.anorm[f], xn = (double)(sqrtf(my_xx) * (1.0f + 1.0e-3f));
         const double E = cfac * an * xn + fabs(S) * 8.881784197001252e-16 + (double)d * 1e-40 + 1e-300;
         const double lo = S - E, hi = S + E;
         bool sure;
@@ -299,16 +310,16 @@ __global__ void __launch_bounds__(256) k_recheck_dot2(
             sure = lo >= 0.0 || hi < 0.0;
             code = lo >= 0.0 ? 1 : 0;
         } else {
-            const double bb = (double)b[f];
+            const double bb = (double)A.b[f];
             const double tl = floor(__ddiv_rn(__dadd_rn(lo, bb), w));
             const double th = floor(__ddiv_rn(__dadd_rn(hi, bb), w));
             sure = tl == th && tl >= -2147483648.0 && tl <= 2147483647.0;
             code = sure ? (int)tl : 0;
         }
         if (sure) {
-            codes[row * F + f] = code;
-            atomicMin(&fmin[f], code);
-            atomicMax(&fmax[f], code);
+            A.codes[row * F + f] = code;
+            atomicMin(&A.fmin[f], code);
+            atomicMax(&A.fmax[f], code);
         } else {
             const unsigned long long slot = atomicAdd(n_flags2, 1ull);
             flags2[slot] = e;  // slot < nf <= cap
@@ -319,27 +330,27 @@ __global__ void __launch_bounds__(256) k_recheck_dot2(
 // FP64 recheck of flagged elements with the reference sequence: products of
 // the float inputs (exact in FP64), summed in j order, then (s + b) / w,
 // each step rounded to nearest; no fused multiply-add.
-__global__ void k_recheck_fp64(const float *__restrict__ x, int64_t ldx, int d,
-                               const float *__restrict__ a, const float *__restrict__ b, double w,
+__global__ void k_recheck_fp64(const ProjArgs *__restrict__ P, const int64_t *__restrict__ row_off, int count,
                                int srp, int F, const uint64_t *__restrict__ flags,
                                const unsigned long long *__restrict__ n_flags, int64_t cap,
-                               int32_t *__restrict__ codes, int *__restrict__ fmin,
-                               int *__restrict__ fmax, int *__restrict__ status) {
+                               int *__restrict__ status) {
     const int64_t nf = min((int64_t)*n_flags, cap);
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nf;
          q += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t e = flags[q];
-        const int64_t row = (int64_t)(e >> 16);
+        const ProjArgs &A = P[find_inst(row_off, count, (int64_t)(e >> 16))];
+        const int d = A.d;
+        const int64_t row = (int64_t)(e >> 16) - A.row_base;
         const int f = (int)(e & 0xFFFF);
-        const float *xr = x + row * ldx;
-        const float *ar = a + (int64_t)f * d;
+        const float *xr = A.x + row * A.ldx;
+        const float *ar = A.a + (int64_t)f * d;
         double s = 0.0;
         for (int j = 0; j < d; j++) s = __dadd_rn(s, __dmul_rn((double)ar[j], (double)xr[j]));
         int code;
         if (srp) {
             code = s >= 0.0 ? 1 : 0;
         } else {
-            const double t = __ddiv_rn(__dadd_rn(s, (double)b[f]), w);
+            const double t = __ddiv_rn(__dadd_rn(s, (double)A.b[f]), A.wd);
             const double fl = floor(t);
             if (!(fl >= -2147483648.0 && fl <= 2147483647.0)) {
                 atomicExch(status, (int)GEEK_ERR_OVERFLOW);
@@ -347,9 +358,9 @@ __global__ void k_recheck_fp64(const float *__restrict__ x, int64_t ldx, int d,
             }
             code = (int)fl;
         }
-        codes[row * F + f] = code;
-        atomicMin(&fmin[f], code);
-        atomicMax(&fmax[f], code);
+        A.codes[row * F + f] = code;
+        atomicMin(&A.fmin[f], code);
+        atomicMax(&A.fmax[f], code);
     }
 }
 
@@ -405,10 +416,16 @@ __global__ void __launch_bounds__(256) k_minhash(int64_t n, const int64_t *__res
 // ---------------------------------------------------------------------------
 // Key layout and packing.
 // ---------------------------------------------------------------------------
-// One block: per function bit width of (max - min); per table total; status.
+// One block per instance (blockIdx.x; its F = L*K1 functions and L tables
+// at offsets blockIdx.x * F and blockIdx.x * L): per function bit width of
+// (max - min); per table total; status.
 __global__ void k_key_layout(const int *__restrict__ fmin, const int *__restrict__ fmax, int L,
                              int K1, int K2, int *__restrict__ bits, int *__restrict__ tbits,
                              int *__restrict__ status) {
+    fmin += (int64_t)blockIdx.x * L * K1;
+    fmax += (int64_t)blockIdx.x * L * K1;
+    bits += (int64_t)blockIdx.x * L * K1;
+    tbits += (int64_t)blockIdx.x * L;
     for (int l = threadIdx.x; l < L; l += blockDim.x) {
         int tot = 0;
         for (int k = 0; k < K1; k++) {
@@ -454,6 +471,52 @@ __global__ void k_pack_keys(int64_t n, int L, const int32_t *__restrict__ codes,
     }
 }
 
+// Batched form over the concatenated rows of `count` instances: table l's
+// key of global row r (instance i) is i in the bits above `B` followed by
+// the instance's own packed K-tuple, so that one sort per table groups every
+// instance separately and keeps each instance's lexicographic order.
+__global__ void k_pack_keys_batch(int64_t N, int L, const int32_t *__restrict__ codes, int F1, int K1,
+                                  const int64_t *__restrict__ row_off, int count, const int *__restrict__ fmin,
+                                  const int *__restrict__ bits, int B, uint64_t *__restrict__ klo,
+                                  uint64_t *__restrict__ khi) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < N; r += (int64_t)gridDim.x * blockDim.x) {
+        const int i = find_inst(row_off, count, r);
+        const int32_t *cr = codes + r * F1;
+        const int *fm = fmin + (int64_t)i * F1;
+        const int *bt = bits + (int64_t)i * F1;
+        for (int l = 0; l < L; l++) {
+            uint64_t hi = 0, lo = 0;
+            for (int k = 0; k < K1; k++) {
+                const int f = l * K1 + k;
+                shl_or(hi, lo, bt[f], (uint32_t)((int64_t)cr[f] - (int64_t)fm[f]));
+            }
+            const uint64_t iv = (uint64_t)i;
+            if (B >= 64) {
+                hi |= iv << (B - 64);
+            } else if (B > 0) {
+                lo |= iv << B;
+                hi |= iv >> (64 - B);
+            } else {
+                lo = iv;
+            }
+            klo[(int64_t)l * N + r] = lo;
+            if (khi) khi[(int64_t)l * N + r] = hi;
+        }
+    }
+}
+
+// E2LSH / SRP row norms of every instance's projections: thread per
+// (instance, function)
+__global__ void k_row_norms_batch(const ProjArgs *__restrict__ P, int count, int F, float *__restrict__ out) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)count * F) return;
+    const ProjArgs &A = P[e / F];
+    const int f = (int)(e % F);
+    float s = 0.f;
+    for (int j = 0; j < A.d; j++) s = fmaf(A.a[(int64_t)f * A.d + j], A.a[(int64_t)f * A.d + j], s);
+    out[e] = sqrtf(s) * 1.0001f;
+}
+
 __global__ void k_scatter_rank(int64_t n, int L, const uint32_t *__restrict__ ids,
                                const int32_t *__restrict__ rank, int32_t *__restrict__ obj_bucket) {
     const int64_t total = n * L;
@@ -492,6 +555,17 @@ int grid_for(int64_t work, int threads, int num_sms) {
 // Host side
 // ---------------------------------------------------------------------------
 
+// Thread layout of the projection kernel for F functions.
+static void proj_layout(ProjArgs &A, int F) {
+    A.F = F;
+    A.FPAD = (int)ceil_div(F, PJ_FPT) * PJ_FPT;
+    A.FG = A.FPAD / PJ_FPT;
+    A.RG = std::max(1, PJ_MAXT / A.FG);
+}
+static int proj_rows(const ProjArgs &A) { return A.RG * PJ_RPT; }
+static int proj_threads(const ProjArgs &A) { return (int)ceil_div(A.FG * A.RG, 32) * 32; }  // whole warps
+static size_t proj_smem(const ProjArgs &A) { return (size_t)PJ_KC * (proj_rows(A) + A.FPAD) * sizeof(float); }
+
 geek_status project_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ldx, int64_t n,
                           int d, const float *a, const float *b, int F, double w, int srp,
                           int32_t *codes, int *fmin, int *fmax, int64_t *n_flagged,
@@ -513,19 +587,18 @@ geek_status project_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t l
         return GEEK_OK;
     }
     ProjArgs A{};
-    A.x = x; A.ldx = ldx; A.n = n; A.d = d; A.F = F;
-    A.FPAD = (int)ceil_div(F, PJ_FPT) * PJ_FPT;
-    A.FG = A.FPAD / PJ_FPT;
-    A.RG = std::max(1, PJ_MAXT / A.FG);
+    A.x = x; A.ldx = ldx; A.n = n; A.d = d;
+    proj_layout(A, F);
     A.a = a; A.b = b; A.anorm = anorm;
-    A.w = (float)w; A.inv_w = (float)(1.0 / w);
+    A.w = (float)w; A.inv_w = (float)(1.0 / w); A.wd = w;
     // 1/w must be exact for the FP32 cell test's error model to hold as
     // written; otherwise widen it by one more rounding.
     A.srp = srp; A.codes = codes;
     A.fmin = fmin; A.fmax = fmax;
-    const int TR = A.RG * PJ_RPT;
-    const int threads = (int)ceil_div(A.FG * A.RG, 32) * 32;  // whole warps
-    const size_t smem = (size_t)PJ_KC * (TR + A.FPAD) * sizeof(float);
+    A.row_base = 0;
+    const int TR = proj_rows(A);
+    const int threads = proj_threads(A);
+    const size_t smem = proj_smem(A);
     if (smem > 200 * 1024) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "projection tile too large");
     GK_CUDA(ctx, cudaFuncSetAttribute(k_project_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     unsigned long long *cnt;
@@ -533,12 +606,19 @@ geek_status project_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t l
     int *status;
     GK_TRY(scr.alloc(&status, 1));
     GK_CUDA(ctx, cudaMemsetAsync(status, 0, sizeof(int), st));
+    int64_t *row_off;
+    ProjArgs *P;
+    GK_TRY(scr.alloc(&row_off, 2));
+    GK_TRY(scr.alloc(&P, 1));
+    const int64_t h_off[2] = {0, n};
+    GK_CUDA(ctx, cudaMemcpyAsync(row_off, h_off, sizeof h_off, cudaMemcpyHostToDevice, st));
     int64_t cap = std::max<int64_t>(1 << 20, n * F / 16);
     for (int attempt = 0; attempt < 2; attempt++) {
         uint64_t *flags;
         GK_TRY(scr.alloc(&flags, cap));
         GK_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
         A.flags = flags; A.n_flags = cnt; A.flag_cap = cap;
+        GK_CUDA(ctx, cudaMemcpyAsync(P, &A, sizeof A, cudaMemcpyHostToDevice, st));
         const int64_t blocks = ceil_div(n, TR);
         {
             EvTimer tk(ctx, "kernel.project_fp32", st);
@@ -565,13 +645,13 @@ geek_status project_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t l
                 EvTimer tk(ctx, "kernel.recheck_dot2", st);
                 GK_COUNT();
                 k_recheck_dot2<<<grid_for((int64_t)h_cnt, 256, ctx->num_sms), 256, 0, st>>>(
-                    x, ldx, d, a, b, w, srp, F, anorm, flags, cnt, cap, codes, fmin, fmax, flags2, cnt2);
+                    P, row_off, 1, srp, F, flags, cnt, cap, flags2, cnt2);
                 GK_LAUNCH(ctx);
             }
             EvTimer tk(ctx, "kernel.recheck_fp64", st);
             GK_COUNT();
             k_recheck_fp64<<<grid_for((int64_t)h_cnt, 128, ctx->num_sms), 128, 0, st>>>(
-                x, ldx, d, a, b, w, srp, F, flags2, cnt2, (int64_t)h_cnt, codes, fmin, fmax, status);
+                P, row_off, 1, srp, F, flags2, cnt2, (int64_t)h_cnt, status);
             GK_LAUNCH(ctx);
             unsigned long long h2 = 0;
             GK_CUDA(ctx, cudaMemcpyAsync(&h2, cnt2, sizeof h2, cudaMemcpyDeviceToHost, st));
@@ -586,6 +666,78 @@ geek_status project_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t l
         return GEEK_OK;
     }
     return set_error(ctx, GEEK_ERR_CUDA, "projection flag list did not converge");
+}
+
+geek_status proj_batch_setup(geek_ctx *ctx, std::vector<ProjArgs> &P, const std::vector<DenseInst> &inst, int F,
+                             int srp, int32_t *codes, const int64_t *row_off_host, ProjBatchBufs &B) {
+    if (F > 512) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "more than 512 projections");
+    const int count = (int)inst.size();
+    P.assign(count, ProjArgs{});
+    std::vector<int64_t> toff(count + 1, 0);
+    for (int i = 0; i < count; i++) {
+        ProjArgs &A = P[i];
+        const DenseInst &I = inst[i];
+        A.x = I.x; A.ldx = I.ldx; A.n = I.n; A.d = I.d;
+        proj_layout(A, F);
+        A.a = I.a; A.b = I.b; A.anorm = B.anorm + (int64_t)i * F;
+        A.w = (float)I.w; A.inv_w = (float)(1.0 / I.w); A.wd = I.w;
+        A.srp = srp;
+        A.codes = codes + row_off_host[i] * F;
+        A.fmin = B.fmin + (int64_t)i * F;
+        A.fmax = B.fmax + (int64_t)i * F;
+        A.flags = B.flags; A.n_flags = B.cnt; A.flag_cap = B.cap;
+        A.row_base = row_off_host[i];
+        toff[i + 1] = toff[i] + ceil_div(I.n, proj_rows(A));
+    }
+    B.total_tiles = toff[count];
+    if (B.total_tiles > 0x7FFFFFFFLL) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "batch too large for one launch");
+    const size_t smem = proj_smem(P[0]);
+    if (smem > 200 * 1024) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "projection tile too large");
+    GK_CUDA(ctx, cudaFuncSetAttribute(k_project_fp32_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GK_CUDA(ctx, cudaMemcpy(B.P, P.data(), sizeof(ProjArgs) * count, cudaMemcpyHostToDevice));
+    GK_CUDA(ctx, cudaMemcpy(B.tile_off, toff.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice));
+    return GEEK_OK;
+}
+
+geek_status proj_batch_enqueue(geek_ctx *ctx, const ProjArgs &P0, int count, int F, int L, int K, int srp,
+                               const ProjBatchBufs &B, cudaStream_t st) {
+    GK_CUDA(ctx, cudaMemsetAsync(B.cnt, 0, sizeof(unsigned long long), st));
+    GK_CUDA(ctx, cudaMemsetAsync(B.cnt2, 0, sizeof(unsigned long long), st));
+    GK_CUDA(ctx, cudaMemsetAsync(B.status, 0, sizeof(int), st));
+    const int CF = count * F;
+    GK_COUNT();
+    k_fill_i32<<<(CF + 255) / 256, 256, 0, st>>>(B.fmin, CF, INT32_MAX);
+    GK_COUNT();
+    k_fill_i32<<<(CF + 255) / 256, 256, 0, st>>>(B.fmax, CF, INT32_MIN);
+    GK_COUNT();
+    k_row_norms_batch<<<(CF + 127) / 128, 128, 0, st>>>(B.P, count, F, B.anorm);
+    GK_LAUNCH(ctx);
+    if (B.total_tiles > 0) {
+        GK_COUNT();
+        k_project_fp32_batch<<<(unsigned)B.total_tiles, proj_threads(P0), proj_smem(P0), st>>>(B.P, B.tile_off, count);
+        GK_COUNT();
+        k_recheck_dot2<<<ctx->num_sms * 4, 256, 0, st>>>(B.P, B.row_off, count, srp, F, B.flags, B.cnt, B.cap,
+                                                        B.flags2, B.cnt2);
+        GK_COUNT();
+        k_recheck_fp64<<<ctx->num_sms * 4, 128, 0, st>>>(B.P, B.row_off, count, srp, F, B.flags2, B.cnt2, B.cap,
+                                                        B.status);
+        GK_LAUNCH(ctx);
+    }
+    GK_COUNT();
+    k_key_layout<<<count, 256, 0, st>>>(B.fmin, B.fmax, L, K, 0, B.bits, B.tbits, B.status);
+    GK_LAUNCH(ctx);
+    return GEEK_OK;
+}
+
+geek_status pack_keys_batch(geek_ctx *ctx, int64_t N, int L, const int32_t *codes, int K, const int64_t *row_off,
+                            int count, const int *fmin, const int *bits, int B, uint64_t *klo, uint64_t *khi,
+                            cudaStream_t st) {
+    if (N == 0) return GEEK_OK;
+    GK_COUNT();
+    k_pack_keys_batch<<<grid_for(N, 256, ctx->num_sms), 256, 0, st>>>(N, L, codes, K * L, K, row_off, count, fmin,
+                                                                      bits, B, klo, khi);
+    GK_LAUNCH(ctx);
+    return GEEK_OK;
 }
 
 geek_status minhash_rows(geek_ctx *ctx, int64_t n, const int64_t *off, int row_len,

@@ -4,6 +4,64 @@
 
 #include "common.cuh"
 
+
+// ---- dense projection (hash.cu) -------------------------------------------
+// Per-instance arguments of the FP32 projection kernel and its recheck
+// stages (device copies are read by the batched kernels).
+struct ProjArgs {
+    const float *x;
+    int64_t ldx;
+    int64_t n;
+    int d;
+    int F, FPAD, FG, RG;  // functions, padded to 8, function groups, row groups
+    const float *a;       // F x d
+    const float *b;       // F
+    const float *anorm;   // F
+    float w, inv_w;
+    int srp;
+    int32_t *codes;       // n x F
+    uint64_t *flags;      // (row << 16 | f)
+    unsigned long long *n_flags;
+    int64_t flag_cap;
+    int *fmin, *fmax;     // F
+    double wd;            // w as given (the reference divides by it in FP64)
+    int64_t row_base;     // global row of local row 0 (flag list entries)
+};
+
+// One dense instance of a batch (device pointers).
+struct DenseInst {
+    const float *x;
+    int64_t ldx, n;
+    int d;
+    const float *a, *b;
+    double w;
+};
+
+// Device buffers of the batched hash phase (owned by the batch plan).
+struct ProjBatchBufs {
+    ProjArgs *P = nullptr;         // count
+    int64_t *tile_off = nullptr;   // count + 1: projection blocks per instance
+    int64_t *row_off = nullptr;    // count + 1: global rows per instance
+    float *anorm = nullptr;        // count * F
+    int *fmin = nullptr, *fmax = nullptr, *bits = nullptr;  // count * F
+    int *tbits = nullptr;          // count * L
+    uint64_t *flags = nullptr, *flags2 = nullptr;           // cap
+    unsigned long long *cnt = nullptr, *cnt2 = nullptr;
+    int *status = nullptr;
+    int64_t cap = 0;
+    int64_t total_tiles = 0;
+};
+
+geek_status proj_batch_setup(geek_ctx *ctx, std::vector<ProjArgs> &P, const std::vector<DenseInst> &inst, int F,
+                             int srp, int32_t *codes, const int64_t *row_off_host, ProjBatchBufs &B);
+// Enqueues the whole batched hash phase up to the key layouts; no host
+// synchronisation and no allocation, so it can be captured in a CUDA graph.
+geek_status proj_batch_enqueue(geek_ctx *ctx, const ProjArgs &P0, int count, int F, int L, int K, int srp,
+                               const ProjBatchBufs &B, cudaStream_t st);
+geek_status pack_keys_batch(geek_ctx *ctx, int64_t N, int L, const int32_t *codes, int K, const int64_t *row_off,
+                            int count, const int *fmin, const int *bits, int B, uint64_t *klo, uint64_t *khi,
+                            cudaStream_t st);
+
 // hash.cu
 geek_status project_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ldx, int64_t n,
                           int d, const float *a, const float *b, int F, double w, int srp,
@@ -51,15 +109,125 @@ struct silk_seeds {
 };
 
 // silk.cu
+// Batched instances: object ids are global rows, instance i owning
+// [row_off[i], row_off[i + 1]) (device, count + 1).  SILK then runs on every
+// instance at once with bins never spanning instances and each instance's
+// own coefficients (instance-major: Ls*Ks SILK pairs, Ks dedup pairs each)
+// applied to its local ids, which gives each instance's own seeds.
+struct SilkBatch {
+    const int64_t *row_off = nullptr;
+    int count = 1;
+};
 geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p, silk_seeds *out,
-                     cudaStream_t st);
+                     cudaStream_t st, const SilkBatch *bt = nullptr);
 
 // tc_assign.cu
+// One instance of a (batched) BF16 tcgen05 assignment: rows x (n x d,
+// stride ldx) against k FP64 centres, labels written at labels[0..n), flag
+// list entries are row_base + local row; N = centre-tile width (64/128/256).
+struct TcPlanInst {
+    const float *x;
+    int64_t ldx, n;
+    int d;
+    const double *centres;
+    int64_t k;
+    int32_t *labels;
+    int64_t row_base;
+    int N;
+};
+struct TcInst;
+struct TcXPrep;
+struct TcCPrep;
+// Buffers, descriptors and the unit list (instance, row tile) of one
+// persistent tcgen05 launch over a set of instances.
+struct TcPlan {
+    struct Impl;
+    Impl *impl = nullptr;
+    std::vector<TcPlanInst> desc;
+    int count = 0;
+    int64_t N_total = 0, kpad_total = 0, nunits = 0;
+    TcInst *inst = nullptr;
+    TcXPrep *xprep = nullptr;
+    TcCPrep *cprep = nullptr;
+    int2 *units = nullptr;
+    int64_t *row_off = nullptr, *kpad_off_dev = nullptr;
+    float *xnorm = nullptr;
+    unsigned *cmax_bits = nullptr;
+    int *err = nullptr;
+    std::vector<void *> owned;
+};
+// scr == nullptr: buffers are cudaMalloc'd and owned by the plan
+geek_status tc_plan_build(geek_ctx *ctx, Scratch *scr, const std::vector<TcPlanInst> &desc, TcPlan *P,
+                          cudaStream_t st);
+// conversions of X and the centres (BF16, norms, max |c|^2)
+geek_status tc_plan_convert(geek_ctx *ctx, const TcPlan &P, cudaStream_t st);
+// the persistent tcgen05 pass (after tc_plan_convert); n_flag zeroed by the caller
+geek_status tc_plan_launch(geek_ctx *ctx, const TcPlan &P, int32_t *flag_rows, unsigned long long *n_flag,
+                           cudaStream_t st);
+geek_status tc_plan_enqueue(geek_ctx *ctx, const TcPlan &P, int32_t *flag_rows, unsigned long long *n_flag,
+                            cudaStream_t st);
+geek_status tc_plan_set_tiles(geek_ctx *ctx, TcPlan *P, const std::vector<int> &N, cudaStream_t st);
+geek_status tc_plan_time(geek_ctx *ctx, TcPlan *P, const std::vector<int> &which, int N, int32_t *flag_rows,
+                         unsigned long long *n_flag, int reps, float *ms_out, cudaStream_t st);
+geek_status tc_plan_check(geek_ctx *ctx, const TcPlan &P, cudaStream_t st);
+void tc_plan_free(TcPlan *P);
+int tc_tile_candidates(const int **tiles);
 geek_status assign_tc_bf16(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ldx, int64_t n, int d,
                            const double *centres, int64_t k, int32_t *labels, int32_t *flag_rows,
                            unsigned long long *n_flag, cudaStream_t st);
 
 // assign.cu
+// Centre preparation of one instance (device copies): FP32 copy and |c|^2
+// of centres k_base.. (global index) and the max of |c| (FP32 bits).
+struct CInst {
+    const double *c64;
+    float *c32;
+    float *cn;
+    unsigned *cmax_bits;
+    int d;
+    int64_t k_base;
+};
+// FP64 argmin decision of one instance's flagged rows (device copies).
+struct RInst {
+    const float *x;
+    int64_t ldx;
+    int d;
+    const float *c32, *cn;
+    const double *c64;
+    int64_t k;
+    const unsigned *cmax_bits;
+    int32_t *labels;
+    int64_t row_base;
+};
+// Centroids of one instance's seeds (device copies): seeds seed_base ..
+// seed_base + k - 1 of the global seed list, member ids global rows.
+struct CenInst {
+    const float *x;
+    int64_t ldx;
+    int d;
+    int64_t row_base, seed_base;
+    double *c;
+};
+// SSE / radius of one instance (device copies).
+struct SInst {
+    const float *x;
+    int64_t ldx, n;
+    int d;
+    const float *chi, *clo;
+    int64_t k;
+    const int32_t *labels;
+};
+// Enqueue-only batched steps (no host synchronisation, no allocation).
+geek_status centroids_batch(geek_ctx *ctx, const CenInst *C, const int64_t *seed_inst_off, int count, int64_t ktot,
+                            int dmax, const int64_t *soff, const int32_t *sids, cudaStream_t st);
+geek_status centre_prep_batch(geek_ctx *ctx, const CInst *C, const int64_t *k_off, int count, int64_t ktot,
+                              cudaStream_t st);
+geek_status recheck_batch(geek_ctx *ctx, const RInst *R, const int64_t *row_off, int count, int dmax,
+                          const int32_t *flag_rows, const unsigned long long *n_flag, cudaStream_t st);
+geek_status centre_split(geek_ctx *ctx, const double *c64, int64_t total, float *chi, float *clo, cudaStream_t st);
+geek_status stats_batch(geek_ctx *ctx, const SInst *S, const int2 *units, int64_t nunits, const int64_t *unit_off,
+                        int count, double *part_sum, float *part_max, double *sse, double *rmax, cudaStream_t st);
+geek_status fill_labels(geek_ctx *ctx, int32_t *labels, int64_t n, int32_t v, cudaStream_t st);
 geek_status assign_dense_centres(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ldx,
                                  int64_t n, int d, const double *centres, int64_t k, int precision,
                                  int32_t *labels, geek_assign_stats *stats, cudaStream_t st);

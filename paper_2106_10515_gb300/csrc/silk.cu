@@ -11,11 +11,15 @@
 namespace {
 
 // signature key of set g under Ks functions (first function most
-// significant): Ks <= 2 fits the low word, Ks 3..4 use the high word too
+// significant): Ks <= 2 fits the low word, Ks 3..4 use the high word too.
+// Batched instances (count > 1): ids are global rows, instance i owning
+// [row_off[i], row_off[i + 1]); a set lies inside one instance, whose
+// coefficients (A/B + i * coef_stride) hash its local ids, and tag[g] = i.
 __global__ void k_set_sig(int64_t nsets, const int64_t *__restrict__ soff,
                           const uint32_t *__restrict__ sids, int Ks, const uint64_t *__restrict__ A,
-                          const uint64_t *__restrict__ B, uint64_t *__restrict__ klo,
-                          uint64_t *__restrict__ khi, uint32_t *__restrict__ vals) {
+                          const uint64_t *__restrict__ B, const int64_t *__restrict__ row_off, int count,
+                          int64_t coef_stride, uint64_t *__restrict__ klo, uint64_t *__restrict__ khi,
+                          uint32_t *__restrict__ vals, uint32_t *__restrict__ tag) {
     // blockIdx.y = SILK table of this segment (functions t*Ks .. t*Ks+Ks-1)
     const int t = blockIdx.y;
     const int64_t so = (int64_t)t * nsets;
@@ -26,9 +30,20 @@ __global__ void k_set_sig(int64_t nsets, const int64_t *__restrict__ soff,
     }
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nsets;
          g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s0 = soff[g], s1 = soff[g + 1];
+        int inst = 0;
+        uint32_t base = 0;
+        if (count > 1 && s1 > s0) {
+            inst = find_inst(row_off, count, (int64_t)sids[s0]);
+            base = (uint32_t)row_off[inst];
+            for (int k = 0; k < Ks; k++) {
+                a[k] = A[inst * coef_stride + t * Ks + k];
+                b[k] = B[inst * coef_stride + t * Ks + k];
+            }
+        }
         uint32_t m[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
-        for (int64_t p = soff[g]; p < soff[g + 1]; p++) {
-            const uint32_t id = sids[p];
+        for (int64_t p = s0; p < s1; p++) {
+            const uint32_t id = sids[p] - base;
             for (int k = 0; k < Ks; k++) m[k] = min(m[k], mh_hash32(a[k], b[k], id));
         }
         uint64_t hi = 0, lo = 0;
@@ -39,19 +54,21 @@ __global__ void k_set_sig(int64_t nsets, const int64_t *__restrict__ soff,
         klo[so + g] = lo;
         if (khi) khi[so + g] = hi;
         vals[so + g] = (uint32_t)g;
+        if (tag) tag[so + g] = (uint32_t)inst;
     }
 }
 
-// first signature component (the most significant 32 bits of the packed key)
+// first signature component (the most significant 32 bits of the packed
+// key), with the instance tag (if any) above it
 __global__ void k_first_component(int64_t n, const uint64_t *__restrict__ klo, const uint64_t *__restrict__ khi,
-                                  int Ks, uint64_t *__restrict__ k0) {
+                                  const uint32_t *__restrict__ tag, int Ks, uint64_t *__restrict__ k0) {
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
         uint64_t v;
         if (Ks == 1) v = klo[g];
         else if (Ks == 2) v = klo[g] >> 32;
         else if (Ks == 3) v = khi[g];
         else v = khi[g] >> 32;
-        k0[g] = v & 0xFFFFFFFFull;
+        k0[g] = (v & 0xFFFFFFFFull) | (tag ? (uint64_t)tag[g] << 32 : 0ull);
     }
 }
 
@@ -88,13 +105,15 @@ __global__ void k_fix_runs(int64_t m, const int64_t *__restrict__ runs, const in
 }
 
 __global__ void k_gather_sig(int64_t m, int S, const uint32_t *__restrict__ perm, const uint64_t *__restrict__ klo,
-                             const uint64_t *__restrict__ khi, uint64_t *__restrict__ slo, uint64_t *__restrict__ shi) {
+                             const uint64_t *__restrict__ khi, const uint32_t *__restrict__ tag,
+                             uint64_t *__restrict__ slo, uint64_t *__restrict__ shi, uint32_t *__restrict__ stag) {
     const int64_t tot = m * S;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < tot; p += (int64_t)gridDim.x * blockDim.x) {
         const int64_t so = (p / m) * m;
         const uint32_t g = perm[p];
         slo[p] = klo[so + g];
         if (shi) shi[p] = khi[so + g];
+        if (stag) stag[p] = tag[so + g];
     }
 }
 
@@ -453,27 +472,36 @@ geek_status d2h_i64(geek_ctx *ctx, const int64_t *dev, int64_t *host, cudaStream
 // all S*nsets positions: perm (set index), rank (global bin id), rs (global
 // bin starts, nbins + 1) and nbins; bins of table t precede those of t + 1.
 geek_status make_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const int64_t *soff,
-                      const uint32_t *sids, int Ks, const uint64_t *A, const uint64_t *B,
-                      uint32_t **perm, int32_t **rank, int64_t **rs, int64_t *nbins, cudaStream_t st) {
+                      const uint32_t *sids, int Ks, const uint64_t *A, const uint64_t *B, const SilkBatch *bt,
+                      int64_t coef_stride, uint32_t **perm, int32_t **rank, int64_t **rs, int64_t *nbins,
+                      cudaStream_t st) {
     const int64_t tot = (int64_t)S * nsets;
+    const bool tagged = bt && bt->count > 1;
     uint64_t *klo, *khi = nullptr, *k0, *slo, *shi = nullptr;
+    uint32_t *tag = nullptr, *stag = nullptr;
     GK_TRY(scr.alloc(&klo, tot));
     if (Ks > 2) GK_TRY(scr.alloc(&khi, tot));
     GK_TRY(scr.alloc(&k0, tot));
     GK_TRY(scr.alloc(&slo, tot));
     if (Ks > 2) GK_TRY(scr.alloc(&shi, tot));
+    if (tagged) {
+        GK_TRY(scr.alloc(&tag, tot));
+        GK_TRY(scr.alloc(&stag, tot));
+    }
     GK_TRY(scr.alloc(perm, tot));
     const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nsets, 256), (int64_t)ctx->num_sms * 8));
     GK_COUNT();
-    k_set_sig<<<dim3(gx, S), 256, 0, st>>>(nsets, soff, sids, Ks, A, B, klo, khi, *perm);
+    k_set_sig<<<dim3(gx, S), 256, 0, st>>>(nsets, soff, sids, Ks, A, B, tagged ? bt->row_off : nullptr,
+                                           tagged ? bt->count : 1, coef_stride, klo, khi, *perm, tag);
     GK_COUNT();
-    k_first_component<<<G(ctx, tot), 256, 0, st>>>(tot, klo, khi, Ks, k0);
+    k_first_component<<<G(ctx, tot), 256, 0, st>>>(tot, klo, khi, tag, Ks, k0);
     GK_LAUNCH(ctx);
-    // stable sort by the first component (32 bits), then order every run of
+    // stable sort by (instance, first component), then order every run of
     // equal first components by the whole signature (runs are short: sets
     // sharing a first component share that component's argmin object, which
     // lies in at most one bucket per table, unless 32-bit values collide)
-    GK_TRY(radix_sort_segments(ctx, scr, S, nsets, &k0, nullptr, perm, 32, st));
+    const int k0bits = 32 + (tagged ? bit_length_u64((uint64_t)(bt->count - 1)) : 0);
+    GK_TRY(radix_sort_segments(ctx, scr, S, nsets, &k0, nullptr, perm, k0bits, st));
     int64_t *runs0, *rs0;
     GK_TRY(scr.alloc(&runs0, S));
     GK_TRY(scr.alloc(&rs0, (size_t)S * (nsets + 1)));
@@ -483,14 +511,14 @@ geek_status make_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const i
         k_fix_runs<<<dim3(gx, S), 256, 0, st>>>(nsets, runs0, rs0, klo, khi, *perm);
     }
     GK_COUNT();
-    k_gather_sig<<<G(ctx, tot), 256, 0, st>>>(nsets, S, *perm, klo, khi, slo, shi);
+    k_gather_sig<<<G(ctx, tot), 256, 0, st>>>(nsets, S, *perm, klo, khi, tag, slo, shi, stag);
     GK_LAUNCH(ctx);
     int64_t *runs, *rs_seg, *d_base;
     GK_TRY(scr.alloc(rank, tot));
     GK_TRY(scr.alloc(&rs_seg, (size_t)S * (nsets + 1)));
     GK_TRY(scr.alloc(&runs, S));
     GK_TRY(scr.alloc(&d_base, S));
-    GK_TRY(segment_runs(ctx, scr, S, nsets, slo, shi, *rank, rs_seg, runs, st));
+    GK_TRY(segment_runs_tagged(ctx, scr, S, nsets, slo, shi, stag, *rank, rs_seg, runs, st));
     std::vector<int64_t> h_runs(S), h_base(S);
     GK_CUDA(ctx, cudaMemcpyAsync(h_runs.data(), runs, sizeof(int64_t) * S, cudaMemcpyDeviceToHost, st));
     GK_CUDA(ctx, cudaStreamSynchronize(st));
@@ -714,7 +742,7 @@ geek_status concat_sets(geek_ctx *ctx, Scratch &scr, const std::vector<Csr> &par
 }  // namespace
 
 geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p, silk_seeds *out,
-                     cudaStream_t st) {
+                     cudaStream_t st, const SilkBatch *bt) {
     Scratch scr(ctx, st);
     const int Ks = p->Ks, Ls = p->Ls, delta = p->delta;
     const int64_t NB = b->NB;
@@ -781,7 +809,7 @@ geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p,
         {
             EvTimer tb(ctx, "silk.bins", st);
             GK_TRY(make_bins(ctx, tscr, S, NV, voff, vmem, Ks, p->mh_a + (int64_t)t * Ks, p->mh_b + (int64_t)t * Ks,
-                             &perm, &rank, &rs, &nbins, st));
+                             bt, (int64_t)Ls * Ks, &perm, &rank, &rs, &nbins, st));
         }
         EvTimer tv(ctx, "silk.vote", st);
         int64_t *bw, *has, *pick, *hpos, *d_nh;
@@ -837,7 +865,8 @@ geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p,
         uint32_t *perm;
         int32_t *rank;
         int64_t *rs, nbins = 0;
-        GK_TRY(make_bins(ctx, scr, 1, C.n, C.off, C.ids, Ks, p->dd_a, p->dd_b, &perm, &rank, &rs, &nbins, st));
+        GK_TRY(make_bins(ctx, scr, 1, C.n, C.off, C.ids, Ks, p->dd_a, p->dd_b, bt, Ks, &perm, &rank, &rs, &nbins,
+                         st));
         Csr V;
         int64_t *ok;
         GK_TRY(vote_bins(ctx, scr, C.n, perm, rank, rs, nbins, C.off, C.ids, delta, &V, &ok, st));

@@ -204,25 +204,29 @@ __global__ void __launch_bounds__(RS_THREADS)
 }
 
 // ---- run detection ---------------------------------------------------------
-__device__ __forceinline__ bool run_start_at(const uint64_t *lo, const uint64_t *hi, int64_t p) {
+// a run starts where the key (lo, hi) or the optional tag changes
+__device__ __forceinline__ bool run_start_at(const uint64_t *lo, const uint64_t *hi, const uint32_t *tag, int64_t p) {
     if (p == 0) return true;
     if (lo[p] != lo[p - 1]) return true;
+    if (tag != nullptr && tag[p] != tag[p - 1]) return true;
     return hi != nullptr && hi[p] != hi[p - 1];
 }
 
 __global__ void __launch_bounds__(RS_THREADS) k_runs_count(const uint64_t *__restrict__ lo,
                                                            const uint64_t *__restrict__ hi,
+                                                           const uint32_t *__restrict__ tag,
                                                            int64_t m, int tiles,
                                                            uint32_t *__restrict__ tile_cnt) {
     __shared__ uint32_t wsum[32];
     const int seg = blockIdx.y, tile = blockIdx.x;
     const uint64_t *l = lo + (int64_t)seg * m;
     const uint64_t *h = hi ? hi + (int64_t)seg * m : nullptr;
+    const uint32_t *g = tag ? tag + (int64_t)seg * m : nullptr;
     const int64_t p0 = (int64_t)tile * RS_TILE + (int64_t)threadIdx.x * RS_ITEMS;
     uint32_t c = 0;
     for (int i = 0; i < RS_ITEMS; i++) {
         int64_t p = p0 + i;
-        if (p < m && run_start_at(l, h, p)) c++;
+        if (p < m && run_start_at(l, h, g, p)) c++;
     }
     uint32_t tot;
     block_excl_scan<RS_THREADS>(c, &tot, wsum);
@@ -230,19 +234,20 @@ __global__ void __launch_bounds__(RS_THREADS) k_runs_count(const uint64_t *__res
 }
 
 __global__ void __launch_bounds__(RS_THREADS)
-    k_runs_emit(const uint64_t *__restrict__ lo, const uint64_t *__restrict__ hi, int64_t m,
-                int tiles, const uint32_t *__restrict__ tile_off, const int64_t *__restrict__ runs,
+    k_runs_emit(const uint64_t *__restrict__ lo, const uint64_t *__restrict__ hi, const uint32_t *__restrict__ tag,
+                int64_t m, int tiles, const uint32_t *__restrict__ tile_off, const int64_t *__restrict__ runs,
                 int32_t *__restrict__ rank, int64_t *__restrict__ run_start) {
     __shared__ uint32_t wsum[32];
     const int seg = blockIdx.y, tile = blockIdx.x;
     const uint64_t *l = lo + (int64_t)seg * m;
     const uint64_t *h = hi ? hi + (int64_t)seg * m : nullptr;
+    const uint32_t *g = tag ? tag + (int64_t)seg * m : nullptr;
     int64_t *rs = run_start + (int64_t)seg * (m + 1);
     const int64_t p0 = (int64_t)tile * RS_TILE + (int64_t)threadIdx.x * RS_ITEMS;
     uint32_t flags = 0, c = 0;
     for (int i = 0; i < RS_ITEMS; i++) {
         int64_t p = p0 + i;
-        if (p < m && run_start_at(l, h, p)) {
+        if (p < m && run_start_at(l, h, g, p)) {
             flags |= 1u << i;
             c++;
         }
@@ -424,6 +429,12 @@ geek_status radix_sort_segments(geek_ctx *ctx, Scratch &scr, int S, int64_t m, u
 geek_status segment_runs(geek_ctx *ctx, Scratch &scr, int S, int64_t m, const uint64_t *key_lo,
                          const uint64_t *key_hi, int32_t *rank, int64_t *run_start, int64_t *runs,
                          cudaStream_t st) {
+    return segment_runs_tagged(ctx, scr, S, m, key_lo, key_hi, nullptr, rank, run_start, runs, st);
+}
+
+geek_status segment_runs_tagged(geek_ctx *ctx, Scratch &scr, int S, int64_t m, const uint64_t *key_lo,
+                                const uint64_t *key_hi, const uint32_t *tag, int32_t *rank, int64_t *run_start,
+                                int64_t *runs, cudaStream_t st) {
     if (S <= 0) return GEEK_OK;
     if (m == 0) {
         GK_CUDA(ctx, cudaMemsetAsync(runs, 0, sizeof(int64_t) * S, st));
@@ -435,11 +446,11 @@ geek_status segment_runs(geek_ctx *ctx, Scratch &scr, int S, int64_t m, const ui
     GK_TRY(scr.alloc(&tile_cnt, (size_t)S * tiles));
     const dim3 grid(tiles, S);
     GK_COUNT();
-    k_runs_count<<<grid, RS_THREADS, 0, st>>>(key_lo, key_hi, m, tiles, tile_cnt);
+    k_runs_count<<<grid, RS_THREADS, 0, st>>>(key_lo, key_hi, tag, m, tiles, tile_cnt);
     GK_COUNT();
     k_seg_scan_u32<<<S, 1024, 0, st>>>(tile_cnt, tiles, runs);
     GK_COUNT();
-    k_runs_emit<<<grid, RS_THREADS, 0, st>>>(key_lo, key_hi, m, tiles, tile_cnt, runs, rank, run_start);
+    k_runs_emit<<<grid, RS_THREADS, 0, st>>>(key_lo, key_hi, tag, m, tiles, tile_cnt, runs, rank, run_start);
     GK_LAUNCH(ctx);
     return GEEK_OK;
 }

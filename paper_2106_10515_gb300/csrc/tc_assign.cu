@@ -22,9 +22,40 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cfloat>
 
 #include "internal.cuh"
+
+// One instance of the (batched) assignment.  Device copies are read by the
+// kernel; CUtensorMap's 64-byte alignment keeps every array element aligned.
+struct TcInst {
+    CUtensorMap tmA;             // Xb: {Kp, n} bf16, box {64, 128}
+    CUtensorMap tmB;             // Cb: {Kp, kpad} bf16, box {64, N}
+    const float *cn;             // kpad: |c|^2 (+inf for padding)
+    const float *xnorm;          // n: upper bound of |x|
+    const unsigned *cmax_bits;   // max over real centres of |c|^2 (FP32 bits)
+    int32_t *labels;             // n
+    int64_t n, k;
+    int64_t row_base;            // global row of local row 0 (flag list entries)
+    int ntiles_c, Kp, d, N;      // centre tiles of N columns, padded d, d, tile N
+};
+
+// Per-instance conversion arguments (device copies).
+struct TcXPrep {
+    const float *x;
+    int64_t ldx;
+    int d, Kp;
+    __nv_bfloat16 *xb;  // n x Kp
+};
+struct TcCPrep {
+    const double *c;    // k x d
+    int64_t k, kpad;
+    int d, Kp;
+    __nv_bfloat16 *cb;  // kpad x Kp
+    float *cn;          // kpad
+    unsigned *cmax_bits;
+};
 
 namespace {
 
@@ -37,21 +68,17 @@ constexpr int TC_EPI_COLS = TC_N / TC_EPI_GROUPS;   // columns per warp
 constexpr int TC_EPI_CH = TC_EPI_COLS / 32;         // 32-column chunks per warp
 constexpr int TC_MISC = 2048;                       // barriers, TMEM slot, merge buffer
 constexpr int TC_THREADS = 32 * (2 + TC_EPI_WARPS);
+constexpr int TC_KP_MAX = 128;                      // d <= 128
+constexpr int TC_A_STAGE = TC_M * TC_KP_MAX * 2;    // bytes of one X tile stage
+constexpr int TC_B_STAGE = TC_N * TC_KP_MAX * 2;    // bytes of one centre tile stage
 constexpr uint32_t TC_TMEM_COLS = 512;
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s per wait
 
 struct TcArgs {
-    CUtensorMap tmA;  // Xb: {Kp, n} bf16, box {64, 128}
-    CUtensorMap tmB;  // Cb: {Kp, kpad} bf16, box {64, 256}
-    const float *cn;  // kpad: |c|^2 (+inf for padding)
-    const float *xnorm;
-    int64_t n, k;
-    int64_t ntiles_r;
-    int ntiles_c;
-    int Kp, d;
-    float cmax;
-    int32_t *labels;
-    int32_t *flag_rows;
+    const TcInst *inst;
+    const int2 *units;           // (instance, row tile); null: instance 0, unit = row tile
+    int64_t nunits;
+    int32_t *flag_rows;          // global rows whose argmin needs the FP64 decision
     unsigned long long *n_flag;
     int *err;
 };
@@ -207,19 +234,16 @@ __device__ __forceinline__ float window_bf16(float xn, float cmax, int d) {
 __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_constant__ TcArgs A) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const uint32_t a_bytes = (uint32_t)TC_M * A.Kp * 2;
-    const uint32_t b_bytes = (uint32_t)TC_N * A.Kp * 2;
-    uint8_t *sA0 = base, *sB0 = base + 2 * a_bytes;
-    uint64_t *bars = (uint64_t *)(base + 2 * a_bytes + 2 * b_bytes);
+    uint8_t *sA0 = base, *sB0 = base + 2 * TC_A_STAGE;
+    uint64_t *bars = (uint64_t *)(base + 2 * TC_A_STAGE + 2 * TC_B_STAGE);
     uint64_t *full_a = bars, *empty_a = bars + 2, *full_b = bars + 4, *empty_b = bars + 6;
     uint64_t *full_acc = bars + 8, *empty_acc = bars + 10, *done_bar = bars + 12;
     uint64_t *full_cn = bars + 13;  // 4 slots
     uint32_t *tmem_slot = (uint32_t *)(bars + 17);
     float *mrg = (float *)(bars + 32);  // [groups-1][128][3] results of column groups 1..
-    float *cn_s = (float *)(base + 2 * a_bytes + 2 * b_bytes + TC_MISC);  // [4][256] |c|^2 ring
+    float *cn_s = (float *)(base + 2 * TC_A_STAGE + 2 * TC_B_STAGE + TC_MISC);  // [4][256] |c|^2 ring
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nkb = A.Kp / TC_KB;
     if (threadIdx.x == 0) {
         for (int i = 0; i < 2; i++) {
             mbar_init(&full_a[i], 1);
@@ -245,6 +269,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
     fence_after();
     const uint32_t tmem = *tmem_slot;
 
+    // Every role walks the same unit sequence (unit u = blockIdx.x + j *
+    // gridDim.x); an instance's Kp, N and centre-tile count fix the per-unit
+    // copy sizes, MMA shape and epilogue width.
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
@@ -252,30 +279,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
             uint32_t issued_b[2] = {0, 0}, issued_cn[4] = {0, 0, 0, 0};
             bool ok = true;
             int64_t it = 0;
-            for (int64_t rt = blockIdx.x; rt < A.ntiles_r && ok; rt += gridDim.x, it++) {
+            for (int64_t u = blockIdx.x; u < A.nunits && ok; u += gridDim.x, it++) {
+                const int2 un = A.units ? A.units[u] : make_int2(0, (int)u);
+                const TcInst &I = A.inst[un.x];
+                const int nkb = I.Kp / TC_KB, N = I.N;
+                const uint32_t a_bytes = (uint32_t)TC_M * I.Kp * 2, b_bytes = (uint32_t)N * I.Kp * 2;
                 const int ab = (int)(it & 1);
                 const uint32_t ua = (uint32_t)(it >> 1);
                 if (!(ok = mbar_wait(&empty_a[ab], (ua & 1) ^ 1, A.err))) break;
                 mbar_expect_tx(&full_a[ab], a_bytes);
                 for (int kb = 0; kb < nkb; kb++)
-                    tma_load_2d(su32(sA0 + ab * a_bytes + kb * TC_M * 128), &A.tmA, kb * TC_KB, (int)(rt * TC_M),
+                    tma_load_2d(su32(sA0 + ab * TC_A_STAGE + kb * TC_M * 128), &I.tmA, kb * TC_KB, un.y * TC_M,
                                 &full_a[ab]);
-                for (int c = 0; c < A.ntiles_c; c++, ct++) {
+                for (int c = 0; c < I.ntiles_c; c++, ct++) {
                     const int s = (int)(ct & 1);
-                    const uint32_t u = (uint32_t)(ct >> 1);
-                    if (!(ok = mbar_wait(&empty_b[s], (u & 1) ^ 1, A.err))) break;
+                    const uint32_t uu = (uint32_t)(ct >> 1);
+                    if (!(ok = mbar_wait(&empty_b[s], (uu & 1) ^ 1, A.err))) break;
                     mbar_expect_tx(&full_b[s], b_bytes);
                     for (int kb = 0; kb < nkb; kb++)
-                        tma_load_2d(su32(sB0 + s * b_bytes + kb * TC_N * 128), &A.tmB, kb * TC_KB, c * TC_N,
-                                    &full_b[s]);
-                    issued_b[s] = u + 1;
+                        tma_load_2d(su32(sB0 + s * TC_B_STAGE + kb * N * 128), &I.tmB, kb * TC_KB, c * N, &full_b[s]);
+                    issued_b[s] = uu + 1;
                     // |c|^2 of this centre tile into ring slot ct % 4.  The
                     // epilogue of tile ct - 4, the last reader of the slot,
                     // finished before the MMA of tile ct - 2 started, which
                     // finished before empty_b let this tile in.
                     const int cs = (int)(ct & 3);
-                    mbar_expect_tx(&full_cn[cs], TC_N * 4);
-                    bulk_load(su32(cn_s + cs * TC_N), A.cn + (int64_t)c * TC_N, TC_N * 4, &full_cn[cs]);
+                    mbar_expect_tx(&full_cn[cs], N * 4);
+                    bulk_load(su32(cn_s + cs * TC_N), I.cn + (int64_t)c * N, N * 4, &full_cn[cs]);
                     issued_cn[cs] = (uint32_t)(ct >> 2) + 1;
                 }
             }
@@ -289,28 +319,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16(TC_M, TC_N);
             uint64_t ct = 0;
             bool ok = true;
             int64_t it = 0;
-            for (int64_t rt = blockIdx.x; rt < A.ntiles_r && ok; rt += gridDim.x, it++) {
+            for (int64_t u = blockIdx.x; u < A.nunits && ok; u += gridDim.x, it++) {
+                const int2 un = A.units ? A.units[u] : make_int2(0, (int)u);
+                const TcInst &I = A.inst[un.x];
+                const int nkb = I.Kp / TC_KB, N = I.N;
+                const uint32_t idesc = idesc_bf16(TC_M, N);
                 const int ab = (int)(it & 1);
                 const uint32_t ua = (uint32_t)(it >> 1);
                 if (!(ok = mbar_wait(&full_a[ab], ua & 1, A.err))) break;
-                const uint32_t a_base = su32(sA0 + ab * a_bytes);
-                for (int c = 0; c < A.ntiles_c; c++, ct++) {
+                const uint32_t a_base = su32(sA0 + ab * TC_A_STAGE);
+                for (int c = 0; c < I.ntiles_c; c++, ct++) {
                     const int s = (int)(ct & 1);
-                    const uint32_t u = (uint32_t)(ct >> 1);
-                    if (!(ok = mbar_wait(&full_b[s], u & 1, A.err))) break;
-                    if (!(ok = mbar_wait(&empty_acc[s], (u & 1) ^ 1, A.err))) break;
+                    const uint32_t uu = (uint32_t)(ct >> 1);
+                    if (!(ok = mbar_wait(&full_b[s], uu & 1, A.err))) break;
+                    if (!(ok = mbar_wait(&empty_acc[s], (uu & 1) ^ 1, A.err))) break;
                     fence_after();
-                    const uint32_t b_base = su32(sB0 + s * b_bytes);
+                    const uint32_t b_base = su32(sB0 + s * TC_B_STAGE);
                     const uint32_t dtm = tmem + (uint32_t)(s * TC_N);
                     for (int kb = 0; kb < nkb; kb++)
 #pragma unroll
                         for (int ks = 0; ks < TC_KB / 16; ks++)
                             mma_bf16(dtm, sdesc(a_base + kb * TC_M * 128 + ks * 32),
-                                     sdesc(b_base + kb * TC_N * 128 + ks * 32), idesc, (kb | ks) != 0);
+                                     sdesc(b_base + kb * N * 128 + ks * 32), idesc, (kb | ks) != 0);
                     mma_commit(&empty_b[s]);
                     mma_commit(&full_acc[s]);
                 }
@@ -329,76 +362,84 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
         const int rloc = 32 * q + lane;
         uint64_t ct = 0;
         bool ok = true;
-        for (int64_t rt = blockIdx.x; rt < A.ntiles_r; rt += gridDim.x) {
-            const int64_t row = rt * TC_M + rloc;
-            const float xn = row < A.n ? A.xnorm[row] : 0.f;
-            const float W = 2.f * window_bf16(xn, A.cmax, A.d);
+        for (int64_t u = blockIdx.x; u < A.nunits; u += gridDim.x) {
+            const int2 un = A.units ? A.units[u] : make_int2(0, (int)u);
+            const TcInst &I = A.inst[un.x];
+            const int N = I.N;
+            const int gcols = N / TC_EPI_GROUPS;  // columns of this warp's group
+            const int nch = gcols / 32;           // 32-column chunks (1, 2 or 4)
+            const int64_t row = (int64_t)un.y * TC_M + rloc;
+            const float xn = row < I.n ? I.xnorm[row] : 0.f;
+            const float cmax = sqrtf(__uint_as_float(*I.cmax_bits)) * (1.f + 1e-5f);
+            const float W = 2.f * window_bf16(xn, cmax, I.d);
             const float Wc = W * (1.f + 1e-6f);
             float b1 = FLT_MAX, b2 = FLT_MAX;
             int i1 = 0x7FFFFFFF;
-            for (int c = 0; c < A.ntiles_c; c++, ct++) {
+            for (int c = 0; c < I.ntiles_c; c++, ct++) {
                 const int s = (int)(ct & 1);
-                const uint32_t u = (uint32_t)(ct >> 1);
+                const uint32_t uu = (uint32_t)(ct >> 1);
                 const int cs = (int)(ct & 3);
                 int w_ok = 0;
                 if (lane == 0 && ok)
-                    w_ok = mbar_wait(&full_acc[s], u & 1, A.err) &&
+                    w_ok = mbar_wait(&full_acc[s], uu & 1, A.err) &&
                            mbar_wait(&full_cn[cs], (uint32_t)(ct >> 2) & 1, A.err);
                 w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
                 ok = ok && w_ok;
                 if (ok) {
                     fence_after();
-                    // four 32-column chunks; the TMEM load of chunk ch + 1 is in
-                    // flight while chunk ch is reduced
-                    const uint32_t tbase =
-                        tmem + (uint32_t)(s * TC_N + h * TC_EPI_COLS) + ((uint32_t)(32 * q) << 16);
-                    const float *cnt = cn_s + cs * TC_N + h * TC_EPI_COLS;
+                    // up to four 32-column chunks; the TMEM load of chunk
+                    // ch + 1 is in flight while chunk ch is reduced
+                    const uint32_t tbase = tmem + (uint32_t)(s * TC_N + h * gcols) + ((uint32_t)(32 * q) << 16);
+                    const float *cnt = cn_s + cs * TC_N + h * gcols;
                     uint32_t ra[32], rb[32];
                     tmem_ld32_async(tbase, ra);
                     tmem_wait_ld();
 #pragma unroll
                     for (int ch = 0; ch < TC_EPI_CH; ch++) {
-                        if (ch < TC_EPI_CH - 1) {
-                            if (ch & 1) tmem_ld32_async(tbase + (ch + 1) * 32, ra);
-                            else tmem_ld32_async(tbase + (ch + 1) * 32, rb);
+                        if (ch < nch) {
+                            if (ch + 1 < nch) {
+                                if (ch & 1) tmem_ld32_async(tbase + (ch + 1) * 32, ra);
+                                else tmem_ld32_async(tbase + (ch + 1) * 32, rb);
+                            }
+                            const uint32_t *r = (ch & 1) ? rb : ra;
+                            const int64_t j0 = (int64_t)c * N + h * gcols + ch * 32;
+                            const float4 *cn4 = reinterpret_cast<const float4 *>(cnt + ch * 32);
+                            float v[32];
+#pragma unroll
+                            for (int i = 0; i < 8; i++) {
+                                const float4 cc = cn4[i];
+                                ffma2_m2(__uint_as_float(r[4 * i + 0]), __uint_as_float(r[4 * i + 1]), cc.x, cc.y,
+                                         v[4 * i + 0], v[4 * i + 1]);
+                                ffma2_m2(__uint_as_float(r[4 * i + 2]), __uint_as_float(r[4 * i + 3]), cc.z, cc.w,
+                                         v[4 * i + 2], v[4 * i + 3]);
+                            }
+                            float t11[11];
+#pragma unroll
+                            for (int i = 0; i < 10; i++) t11[i] = min3f(v[3 * i], v[3 * i + 1], v[3 * i + 2]);
+                            t11[10] = fminf(v[30], v[31]);
+                            const float tm =
+                                fminf(min3f(min3f(t11[0], t11[1], t11[2]), min3f(t11[3], t11[4], t11[5]),
+                                            min3f(t11[6], t11[7], t11[8])),
+                                      fminf(t11[9], t11[10]));
+                            if (tm < b1) {
+                                // a new best in this chunk: its first position and
+                                // the chunk's second smallest value
+                                int idx = 31;
+#pragma unroll
+                                for (int i = 31; i >= 0; i--)
+                                    if (v[i] == tm) idx = i;
+                                float m2 = FLT_MAX;
+#pragma unroll
+                                for (int i = 0; i < 32; i++) m2 = fminf(m2, i == idx ? FLT_MAX : v[i]);
+                                b2 = fminf(b1, m2);
+                                b1 = tm;
+                                i1 = (int)(j0 + idx);
+                            } else {
+                                // the best is unchanged; only the runner-up can move
+                                b2 = fminf(b2, tm);
+                            }
+                            if (ch + 1 < nch) tmem_wait_ld();
                         }
-                        const uint32_t *r = (ch & 1) ? rb : ra;
-                        const int64_t j0 = (int64_t)c * TC_N + h * TC_EPI_COLS + ch * 32;
-                        const float4 *cn4 = reinterpret_cast<const float4 *>(cnt + ch * 32);
-                        float v[32];
-#pragma unroll
-                        for (int i = 0; i < 8; i++) {
-                            const float4 cc = cn4[i];
-                            ffma2_m2(__uint_as_float(r[4 * i + 0]), __uint_as_float(r[4 * i + 1]), cc.x, cc.y,
-                                     v[4 * i + 0], v[4 * i + 1]);
-                            ffma2_m2(__uint_as_float(r[4 * i + 2]), __uint_as_float(r[4 * i + 3]), cc.z, cc.w,
-                                     v[4 * i + 2], v[4 * i + 3]);
-                        }
-                        float t11[11];
-#pragma unroll
-                        for (int i = 0; i < 10; i++) t11[i] = min3f(v[3 * i], v[3 * i + 1], v[3 * i + 2]);
-                        t11[10] = fminf(v[30], v[31]);
-                        const float tm = fminf(min3f(min3f(t11[0], t11[1], t11[2]), min3f(t11[3], t11[4], t11[5]),
-                                                     min3f(t11[6], t11[7], t11[8])),
-                                               fminf(t11[9], t11[10]));
-                        if (tm < b1) {
-                            // a new best in this chunk: its first position and
-                            // the chunk's second smallest value
-                            int idx = 31;
-#pragma unroll
-                            for (int i = 31; i >= 0; i--)
-                                if (v[i] == tm) idx = i;
-                            float m2 = FLT_MAX;
-#pragma unroll
-                            for (int i = 0; i < 32; i++) m2 = fminf(m2, i == idx ? FLT_MAX : v[i]);
-                            b2 = fminf(b1, m2);
-                            b1 = tm;
-                            i1 = (int)(j0 + idx);
-                        } else {
-                            // the best is unchanged; only the runner-up can move
-                            b2 = fminf(b2, tm);
-                        }
-                        if (ch < TC_EPI_CH - 1) tmem_wait_ld();
                     }
                     fence_before();
                 }
@@ -414,7 +455,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
                 m[2] = __int_as_float(i1);
             }
             asm volatile("bar.sync 1, %0;" ::"r"(32 * TC_EPI_WARPS) : "memory");
-            if (h == 0 && row < A.n && ok) {
+            if (h == 0 && row < I.n && ok) {
 #pragma unroll
                 for (int g = 1; g < TC_EPI_GROUPS; g++) {
                     const float *m = mrg + ((g - 1) * TC_M + rloc) * 3;
@@ -433,11 +474,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
                     b2 = nb2;
                 }
                 const bool valid = i1 != 0x7FFFFFFF;
-                A.labels[row] = valid ? i1 : -1;
-                const bool sure = valid && (A.k == 1 || b2 - b1 > Wc);
+                I.labels[row] = valid ? i1 : -1;
+                const bool sure = valid && (I.k == 1 || b2 - b1 > Wc);
                 if (!sure) {
                     const unsigned long long qq = atomicAdd(A.n_flag, 1ull);
-                    A.flag_rows[qq] = (int32_t)row;
+                    A.flag_rows[qq] = (int32_t)(I.row_base + row);
                 }
             }
             asm volatile("bar.sync 1, %0;" ::"r"(32 * TC_EPI_WARPS) : "memory");
@@ -451,36 +492,48 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
     }
 }
 
-// X -> BF16 K-major [n][Kp] (zero padded) and an upper bound of |x| per row
-__global__ void k_x_to_bf16(const float *__restrict__ x, int64_t ldx, int64_t n, int d, int Kp,
-                            __nv_bfloat16 *__restrict__ xb, float *__restrict__ xnorm) {
+// X -> BF16 K-major [n][Kp] (zero padded) and an upper bound of |x| per row;
+// warp per global row r of instance find_inst(row_off, r); xnorm is global
+__global__ void k_x_to_bf16(const TcXPrep *__restrict__ X, const int64_t *__restrict__ row_off, int count, int64_t N,
+                            float *__restrict__ xnorm) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = warp; i < n; i += nw) {
+    for (int64_t r = warp; r < N; r += nw) {
+        const int ii = find_inst(row_off, count, r);
+        const TcXPrep &P = X[ii];
+        const int64_t i = r - row_off[ii];
         float s = 0.f;
-        for (int t = lane; t < Kp; t += 32) {
-            const float v = t < d ? x[i * ldx + t] : 0.f;
-            xb[i * Kp + t] = __float2bfloat16_rn(v);
+        for (int t = lane; t < P.Kp; t += 32) {
+            const float v = t < P.d ? P.x[i * P.ldx + t] : 0.f;
+            P.xb[i * P.Kp + t] = __float2bfloat16_rn(v);
             s = fmaf(v, v, s);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) xnorm[i] = sqrtf(s) * (1.f + 1.0e-3f);
+        if (lane == 0) xnorm[r] = sqrtf(s) * (1.f + 1.0e-3f);
     }
 }
 
-__global__ void k_c_to_bf16(const double *__restrict__ c, int64_t k, int64_t kpad, int d, int Kp,
-                            __nv_bfloat16 *__restrict__ cb, float *__restrict__ cn) {
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < kpad;
-         j += (int64_t)gridDim.x * blockDim.x) {
+// centres -> BF16 [kpad][Kp], |c|^2 (+inf for padding) and the max of |c|^2
+// over real centres; thread per global padded centre e of instance
+// find_inst(kpad_off, e)
+__global__ void k_c_to_bf16(const TcCPrep *__restrict__ C, const int64_t *__restrict__ kpad_off, int count,
+                            int64_t total) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int ii = find_inst(kpad_off, count, e);
+        const TcCPrep &P = C[ii];
+        const int64_t j = e - kpad_off[ii];
         double s = 0.0;
-        for (int t = 0; t < Kp; t++) {
-            const double v = (j < k && t < d) ? c[j * d + t] : 0.0;
-            cb[j * Kp + t] = __double2bfloat16(v);
+        for (int t = 0; t < P.Kp; t++) {
+            const double v = (j < P.k && t < P.d) ? P.c[j * P.d + t] : 0.0;
+            P.cb[j * P.Kp + t] = __double2bfloat16(v);
             s += v * v;
         }
-        cn[j] = j < k ? (float)s : __int_as_float(0x7f800000);  // +inf: padding never wins
+        const float f = (float)s;
+        P.cn[j] = j < P.k ? f : __int_as_float(0x7f800000);  // +inf: padding never wins
+        if (j < P.k) atomicMax(P.cmax_bits, __float_as_uint(f));  // non-negative floats order as uints
     }
 }
 
@@ -511,71 +564,320 @@ geek_status encode_bf16_2d(geek_ctx *ctx, CUtensorMap *tm, void *ptr, uint64_t i
     return GEEK_OK;
 }
 
+
+constexpr int TC_TILES[3] = {64, 128, 256};
+
 }  // namespace
 
-// BF16 tcgen05 pass: labels for every object, flagged rows appended to
-// flag_rows / n_flag for the FP64 decision.  d <= 128.
+struct TcPlan::Impl {
+    std::vector<TcInst> inst;      // host copy (tensor maps for the chosen N)
+    std::vector<TcXPrep> xp;
+    std::vector<TcCPrep> cp;
+    std::vector<int64_t> kpad_off;
+};
+
+namespace {
+
+template <class T>
+geek_status plan_alloc(geek_ctx *ctx, Scratch *scr, std::vector<void *> &owned, T **p, size_t count) {
+    if (scr) return scr->alloc(p, count);
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count * sizeof(T), 16));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ctx, GEEK_ERR_NOMEM, "device allocation of %zu bytes failed", count * sizeof(T));
+    }
+    owned.push_back(q);
+    *p = (T *)q;
+    return GEEK_OK;
+}
+
+// TcInst of instance i for tile width N (tensor maps re-encoded)
+geek_status make_inst(geek_ctx *ctx, const TcPlan &P, int i, int N, TcInst *out) {
+    const TcPlanInst &I = P.desc[i];
+    const int Kp = I.d <= 64 ? 64 : 128;
+    TcInst T;
+    memset(&T, 0, sizeof T);
+    const TcXPrep &xp = P.impl->xp[i];
+    const TcCPrep &cp = P.impl->cp[i];
+    if (I.n > 0) GK_TRY(encode_bf16_2d(ctx, &T.tmA, xp.xb, Kp, I.n, TC_KB, TC_M));
+    if (I.k > 0) GK_TRY(encode_bf16_2d(ctx, &T.tmB, cp.cb, Kp, cp.kpad, TC_KB, N));
+    T.cn = cp.cn;
+    T.xnorm = P.xnorm + I.row_base;
+    T.cmax_bits = cp.cmax_bits;
+    T.labels = I.labels;
+    T.n = I.n;
+    T.k = I.k;
+    T.row_base = I.row_base;
+    T.ntiles_c = (int)ceil_div(I.k, N);
+    T.Kp = Kp;
+    T.d = I.d;
+    T.N = N;
+    *out = T;
+    return GEEK_OK;
+}
+
+// units of the listed instances, longest first (LPT order over the CTAs)
+void make_units(const TcPlan &P, const std::vector<int> &which, std::vector<int2> &units) {
+    std::vector<std::pair<int64_t, int>> cost;
+    for (int i : which) {
+        const TcInst &T = P.impl->inst[i];
+        if (T.n <= 0 || T.k <= 0) continue;
+        cost.push_back({(int64_t)T.ntiles_c * T.N * T.Kp + 2048, i});
+    }
+    std::stable_sort(cost.begin(), cost.end(), [](const std::pair<int64_t, int> &a, const std::pair<int64_t, int> &b) {
+        return a.first > b.first;
+    });
+    units.clear();
+    for (auto &c : cost) {
+        const int64_t nt = ceil_div(P.impl->inst[c.second].n, TC_M);
+        for (int64_t r = 0; r < nt; r++) units.push_back(make_int2(c.second, (int)r));
+    }
+}
+
+size_t tc_smem() {
+    static_assert(32 * 8 + (TC_EPI_GROUPS - 1) * TC_M * 3 * 4 <= TC_MISC, "misc region too small");
+    // tile stages + barriers / TMEM slot / merge buffer + |c|^2 ring + alignment
+    return 1024 + 2 * (size_t)TC_A_STAGE + 2 * (size_t)TC_B_STAGE + TC_MISC + 4 * TC_N * 4;
+}
+
+}  // namespace
+
+int tc_tile_candidates(const int **tiles) {
+    *tiles = TC_TILES;
+    return 3;
+}
+
+geek_status tc_plan_build(geek_ctx *ctx, Scratch *scr, const std::vector<TcPlanInst> &desc, TcPlan *P,
+                          cudaStream_t st) {
+    P->impl = new TcPlan::Impl();
+    P->desc = desc;
+    const int count = (int)desc.size();
+    P->count = count;
+    auto &im = *P->impl;
+    std::vector<int64_t> row_off(count + 1, 0);
+    im.kpad_off.assign(count + 1, 0);
+    int64_t xb_total = 0, cb_total = 0;
+    for (int i = 0; i < count; i++) {
+        const TcPlanInst &I = desc[i];
+        if (I.d > TC_KP_MAX || I.d <= 0)
+            return set_error(ctx, GEEK_ERR_UNSUPPORTED, "BF16 tensor-core assignment supports 1 <= d <= 128");
+        if (I.N != 64 && I.N != 128 && I.N != 256) return set_error(ctx, GEEK_ERR_INVALID, "tile N must be 64/128/256");
+        const int Kp = I.d <= 64 ? 64 : 128;
+        row_off[i + 1] = row_off[i] + I.n;
+        // padding to a multiple of 256 serves every tile width
+        im.kpad_off[i + 1] = im.kpad_off[i] + ceil_div(I.k, TC_N) * TC_N;
+        xb_total += I.n * Kp;
+        cb_total += ceil_div(I.k, TC_N) * TC_N * Kp;
+    }
+    P->N_total = row_off[count];
+    P->kpad_total = im.kpad_off[count];
+    auto &own = P->owned;
+    __nv_bfloat16 *xb, *cb;
+    float *cn;
+    unsigned *cmax_bits;
+    GK_TRY(plan_alloc(ctx, scr, own, &xb, (size_t)xb_total));
+    GK_TRY(plan_alloc(ctx, scr, own, &cb, (size_t)std::max<int64_t>(cb_total, 1)));
+    GK_TRY(plan_alloc(ctx, scr, own, &P->xnorm, (size_t)std::max<int64_t>(P->N_total, 1)));
+    GK_TRY(plan_alloc(ctx, scr, own, &cn, (size_t)std::max<int64_t>(P->kpad_total, 1)));
+    GK_TRY(plan_alloc(ctx, scr, own, &cmax_bits, (size_t)count));
+    GK_TRY(plan_alloc(ctx, scr, own, &P->row_off, (size_t)count + 1));
+    GK_TRY(plan_alloc(ctx, scr, own, &P->kpad_off_dev, (size_t)count + 1));
+    GK_TRY(plan_alloc(ctx, scr, own, &P->xprep, (size_t)count));
+    GK_TRY(plan_alloc(ctx, scr, own, &P->cprep, (size_t)count));
+    GK_TRY(plan_alloc(ctx, scr, own, &P->inst, (size_t)count));
+    GK_TRY(plan_alloc(ctx, scr, own, &P->err, 1));
+    P->cmax_bits = cmax_bits;
+    im.xp.resize(count);
+    im.cp.resize(count);
+    int64_t xo = 0, co = 0;
+    for (int i = 0; i < count; i++) {
+        const TcPlanInst &I = desc[i];
+        const int Kp = I.d <= 64 ? 64 : 128;
+        im.xp[i] = TcXPrep{I.x, I.ldx, I.d, Kp, xb + xo};
+        const int64_t kpad = im.kpad_off[i + 1] - im.kpad_off[i];
+        im.cp[i] = TcCPrep{I.centres, I.k, kpad, I.d, Kp, cb + co, cn + im.kpad_off[i], cmax_bits + i};
+        xo += I.n * Kp;
+        co += kpad * Kp;
+    }
+    im.inst.resize(count);
+    for (int i = 0; i < count; i++) GK_TRY(make_inst(ctx, *P, i, desc[i].N, &im.inst[i]));
+    std::vector<int> all(count);
+    for (int i = 0; i < count; i++) all[i] = i;
+    std::vector<int2> units;
+    make_units(*P, all, units);
+    P->nunits = (int64_t)units.size();
+    GK_TRY(plan_alloc(ctx, scr, own, &P->units, (size_t)std::max<int64_t>(P->nunits, 1)));
+    GK_CUDA(ctx, cudaMemcpyAsync(P->row_off, row_off.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, st));
+    GK_CUDA(ctx, cudaMemcpyAsync(P->kpad_off_dev, im.kpad_off.data(), sizeof(int64_t) * (count + 1),
+                                 cudaMemcpyHostToDevice, st));
+    GK_CUDA(ctx, cudaMemcpyAsync(P->xprep, im.xp.data(), sizeof(TcXPrep) * count, cudaMemcpyHostToDevice, st));
+    GK_CUDA(ctx, cudaMemcpyAsync(P->cprep, im.cp.data(), sizeof(TcCPrep) * count, cudaMemcpyHostToDevice, st));
+    GK_CUDA(ctx, cudaMemcpyAsync(P->inst, im.inst.data(), sizeof(TcInst) * count, cudaMemcpyHostToDevice, st));
+    if (P->nunits)
+        GK_CUDA(ctx, cudaMemcpyAsync(P->units, units.data(), sizeof(int2) * P->nunits, cudaMemcpyHostToDevice, st));
+    // the host vectors above are pageable: the copies have read them on return
+    GK_CUDA(ctx, cudaFuncSetAttribute(k_assign_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem()));
+    return GEEK_OK;
+}
+
+// Conversions of X and the centres; then the persistent tcgen05 pass over
+// every unit.  flag_rows / n_flag receive the rows left to the FP64 decision
+// (n_flag must be zeroed by the caller).  No host synchronisation.
+geek_status tc_plan_convert(geek_ctx *ctx, const TcPlan &P, cudaStream_t st) {
+    const int count = P.count;
+    GK_CUDA(ctx, cudaMemsetAsync(P.err, 0, sizeof(int), st));
+    GK_CUDA(ctx, cudaMemsetAsync(P.cmax_bits, 0, sizeof(unsigned) * count, st));
+    if (P.N_total > 0) {
+        GK_COUNT();
+        k_x_to_bf16<<<grid_for(P.N_total * 32, 256, ctx->num_sms), 256, 0, st>>>(P.xprep, P.row_off, count,
+                                                                                 P.N_total, P.xnorm);
+    }
+    if (P.kpad_total > 0) {
+        GK_COUNT();
+        k_c_to_bf16<<<grid_for(P.kpad_total, 128, ctx->num_sms), 128, 0, st>>>(P.cprep, P.kpad_off_dev, count,
+                                                                               P.kpad_total);
+    }
+    GK_LAUNCH(ctx);
+    return GEEK_OK;
+}
+
+geek_status tc_plan_launch(geek_ctx *ctx, const TcPlan &P, int32_t *flag_rows, unsigned long long *n_flag,
+                           cudaStream_t st) {
+    if (P.nunits == 0) return GEEK_OK;
+    TcArgs A;
+    A.inst = P.inst;
+    A.units = P.units;
+    A.nunits = P.nunits;
+    A.flag_rows = flag_rows;
+    A.n_flag = n_flag;
+    A.err = P.err;
+    const int grid = (int)std::min<int64_t>(P.nunits, ctx->num_sms);
+    EvTimer tk(ctx, "kernel.assign_tc", st);
+    for (const TcPlanInst &I : P.desc) tk.work += 2.0 * (double)I.n * (double)I.k * (double)I.d;
+    GK_COUNT();
+    k_assign_tc<<<grid, TC_THREADS, tc_smem(), st>>>(A);
+    GK_LAUNCH(ctx);
+    return GEEK_OK;
+}
+
+geek_status tc_plan_enqueue(geek_ctx *ctx, const TcPlan &P, int32_t *flag_rows, unsigned long long *n_flag,
+                            cudaStream_t st) {
+    GK_TRY(tc_plan_convert(ctx, P, st));
+    return tc_plan_launch(ctx, P, flag_rows, n_flag, st);
+}
+
+geek_status tc_plan_set_tiles(geek_ctx *ctx, TcPlan *P, const std::vector<int> &N, cudaStream_t st) {
+    const int count = P->count;
+    for (int i = 0; i < count; i++) {
+        P->desc[i].N = N[i];
+        GK_TRY(make_inst(ctx, *P, i, N[i], &P->impl->inst[i]));
+    }
+    std::vector<int> all(count);
+    for (int i = 0; i < count; i++) all[i] = i;
+    std::vector<int2> units;
+    make_units(*P, all, units);
+    GK_CUDA(ctx, cudaMemcpyAsync(P->inst, P->impl->inst.data(), sizeof(TcInst) * count, cudaMemcpyHostToDevice, st));
+    if (!units.empty())
+        GK_CUDA(ctx, cudaMemcpyAsync(P->units, units.data(), sizeof(int2) * units.size(), cudaMemcpyHostToDevice, st));
+    P->nunits = (int64_t)units.size();
+    return GEEK_OK;
+}
+
+// Times the tcgen05 pass over the units of `which` with tile width N for
+// those instances (the conversions of tc_plan_enqueue must have run).
+// Writes labels and flags of those rows as a side effect.
+geek_status tc_plan_time(geek_ctx *ctx, TcPlan *P, const std::vector<int> &which, int N, int32_t *flag_rows,
+                         unsigned long long *n_flag, int reps, float *ms_out, cudaStream_t st) {
+    auto &im = *P->impl;
+    std::vector<TcInst> saved = im.inst;
+    for (int i : which) GK_TRY(make_inst(ctx, *P, i, N, &im.inst[i]));
+    std::vector<int2> units;
+    make_units(*P, which, units);
+    TcInst *dinst = nullptr;
+    int2 *dunits = nullptr;
+    geek_status rc = GEEK_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float best = 1e30f;
+    if (units.empty()) {
+        *ms_out = 0.f;
+        im.inst = saved;
+        return GEEK_OK;
+    }
+    if (cudaMalloc((void **)&dinst, sizeof(TcInst) * P->count) != cudaSuccess ||
+        cudaMalloc((void **)&dunits, sizeof(int2) * units.size()) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        rc = set_error(ctx, GEEK_ERR_NOMEM, "autotune set-up failed");
+    }
+    if (rc == GEEK_OK &&
+        (cudaMemcpyAsync(dinst, im.inst.data(), sizeof(TcInst) * P->count, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+         cudaMemcpyAsync(dunits, units.data(), sizeof(int2) * units.size(), cudaMemcpyHostToDevice, st) != cudaSuccess))
+        rc = set_error(ctx, GEEK_ERR_CUDA, "autotune upload failed");
+    for (int r = 0; r < reps && rc == GEEK_OK; r++) {
+        TcArgs A;
+        A.inst = dinst;
+        A.units = dunits;
+        A.nunits = (int64_t)units.size();
+        A.flag_rows = flag_rows;
+        A.n_flag = n_flag;
+        A.err = P->err;
+        cudaMemsetAsync(n_flag, 0, sizeof(unsigned long long), st);
+        cudaEventRecord(e0, st);
+        GK_COUNT();
+        k_assign_tc<<<(int)std::min<int64_t>(A.nunits, ctx->num_sms), TC_THREADS, tc_smem(), st>>>(A);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = set_error(ctx, GEEK_ERR_CUDA, "autotune launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        best = std::min(best, ms);
+    }
+    int h_err = 0;
+    if (rc == GEEK_OK) {
+        cudaMemcpy(&h_err, P->err, sizeof h_err, cudaMemcpyDeviceToHost);
+        if (h_err) rc = set_error(ctx, (geek_status)h_err, "tensor-core assignment: a pipeline wait timed out");
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(dinst);
+    cudaFree(dunits);
+    im.inst = saved;
+    *ms_out = best;
+    return rc;
+}
+
+geek_status tc_plan_check(geek_ctx *ctx, const TcPlan &P, cudaStream_t st) {
+    int h_err = 0;
+    GK_CUDA(ctx, cudaMemcpyAsync(&h_err, P.err, sizeof h_err, cudaMemcpyDeviceToHost, st));
+    GK_CUDA(ctx, cudaStreamSynchronize(st));
+    if (h_err) return set_error(ctx, (geek_status)h_err, "tensor-core assignment: a pipeline wait timed out");
+    return GEEK_OK;
+}
+
+void tc_plan_free(TcPlan *P) {
+    for (void *p : P->owned) cudaFree(p);
+    P->owned.clear();
+    delete P->impl;
+    P->impl = nullptr;
+}
+
+// BF16 tcgen05 pass of one data set: labels for every object, flagged rows
+// appended to flag_rows / n_flag for the FP64 decision.  d <= 128.
 geek_status assign_tc_bf16(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ldx, int64_t n, int d,
                            const double *centres, int64_t k, int32_t *labels, int32_t *flag_rows,
                            unsigned long long *n_flag, cudaStream_t st) {
     if (d > 128) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "BF16 tensor-core assignment supports d <= 128");
-    const int Kp = d <= 64 ? 64 : 128;
-    const int64_t kpad = ceil_div(k, TC_N) * TC_N;
-    __nv_bfloat16 *xb, *cb;
-    float *xnorm, *cn;
-    GK_TRY(scr.alloc(&xb, (size_t)n * Kp));
-    GK_TRY(scr.alloc(&xnorm, n));
-    GK_TRY(scr.alloc(&cb, (size_t)kpad * Kp));
-    GK_TRY(scr.alloc(&cn, kpad));
-    GK_COUNT();
-    k_x_to_bf16<<<grid_for(n * 32, 256, ctx->num_sms), 256, 0, st>>>(x, ldx, n, d, Kp, xb, xnorm);
-    GK_COUNT();
-    k_c_to_bf16<<<grid_for(kpad, 128, ctx->num_sms), 128, 0, st>>>(centres, k, kpad, d, Kp, cb, cn);
-    GK_LAUNCH(ctx);
-    // max |c| over the centres (upper bound)
-    float cmax = 0.f;
-    {
-        std::vector<float> h(kpad);
-        GK_CUDA(ctx, cudaMemcpyAsync(h.data(), cn, sizeof(float) * kpad, cudaMemcpyDeviceToHost, st));
-        GK_CUDA(ctx, cudaStreamSynchronize(st));
-        for (int64_t j = 0; j < k; j++) cmax = std::max(cmax, h[j]);
-        cmax = sqrtf(cmax) * (1.f + 1e-5f);
-    }
-    TcArgs A;
-    memset(&A, 0, sizeof A);
-    GK_TRY(encode_bf16_2d(ctx, &A.tmA, xb, Kp, n, TC_KB, TC_M));
-    GK_TRY(encode_bf16_2d(ctx, &A.tmB, cb, Kp, kpad, TC_KB, TC_N));
-    int *err;
-    GK_TRY(scr.alloc(&err, 1));
-    GK_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(int), st));
-    A.cn = cn;
-    A.xnorm = xnorm;
-    A.n = n;
-    A.k = k;
-    A.ntiles_r = ceil_div(n, TC_M);
-    A.ntiles_c = (int)(kpad / TC_N);
-    A.Kp = Kp;
-    A.d = d;
-    A.cmax = cmax;
-    A.labels = labels;
-    A.flag_rows = flag_rows;
-    A.n_flag = n_flag;
-    A.err = err;
-    // tiles + barriers / TMEM slot / merge buffer + 4 KB |c|^2 ring + alignment
-    static_assert(32 * 8 + (TC_EPI_GROUPS - 1) * TC_M * 3 * 4 <= TC_MISC, "misc region too small");
-    const size_t smem = 1024 + 2 * (size_t)TC_M * Kp * 2 + 2 * (size_t)TC_N * Kp * 2 + TC_MISC + 4 * TC_N * 4;
-    GK_CUDA(ctx, cudaFuncSetAttribute(k_assign_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int grid = (int)std::min<int64_t>(A.ntiles_r, ctx->num_sms);
-    {
-        EvTimer tk(ctx, "kernel.assign_tc", st);
-        tk.work = 2.0 * (double)n * (double)k * (double)d;
-        GK_COUNT();
-        k_assign_tc<<<grid, TC_THREADS, smem, st>>>(A);
-        GK_LAUNCH(ctx);
-    }
-    int h_err = 0;
-    GK_CUDA(ctx, cudaMemcpyAsync(&h_err, err, sizeof h_err, cudaMemcpyDeviceToHost, st));
-    GK_CUDA(ctx, cudaStreamSynchronize(st));
-    if (h_err) return set_error(ctx, (geek_status)h_err, "tensor-core assignment: a pipeline wait timed out");
-    return GEEK_OK;
+    TcPlan P;
+    std::vector<TcPlanInst> one(1);
+    one[0] = TcPlanInst{x, ldx, n, d, centres, k, labels, 0, TC_N};
+    struct Free {
+        TcPlan *p;
+        ~Free() { tc_plan_free(p); }
+    } fr{&P};
+    GK_TRY(tc_plan_build(ctx, &scr, one, &P, st));
+    GK_TRY(tc_plan_enqueue(ctx, P, flag_rows, n_flag, st));
+    return tc_plan_check(ctx, P, st);
 }

@@ -61,12 +61,32 @@ class geek_assign_stats(C.Structure):
                 ("n_recheck_rows", C.c_int64)]
 
 
+class geek_instance(C.Structure):
+    _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("ldx", C.c_int64), ("x", C.c_void_p), ("a", C.c_void_p),
+                ("b", C.c_void_p), ("w", C.c_double), ("mh_a", C.c_void_p), ("mh_b", C.c_void_p),
+                ("dd_a", C.c_void_p), ("dd_b", C.c_void_p)]
+
+
+class geek_batch_params(C.Structure):
+    _fields_ = [("proj", C.c_int32), ("K", C.c_int32), ("L", C.c_int32), ("Ks", C.c_int32), ("Ls", C.c_int32),
+                ("delta", C.c_int32), ("tile_n", C.c_int32)]
+
+
+class geek_batch_info(C.Structure):
+    _fields_ = [("count", C.c_int32), ("n_total", C.c_int64), ("k_total", C.c_int64), ("n_buckets", C.c_int64),
+                ("n_flagged", C.c_int64), ("n_flagged_fp64", C.c_int64), ("n_recheck_rows", C.c_int64),
+                ("key_bits", C.c_int32), ("graph_launches", C.c_int32), ("graph_captures", C.c_int32),
+                ("tuned_classes", C.c_int32)]
+
+
 # every symbol declared in include/geek.h
 EXPORTS = ["geek_ctx_create", "geek_ctx_destroy", "geek_last_error", "geek_version", "geek_hash",
            "geek_buckets_info_get", "geek_buckets_copy_out", "geek_buckets_free", "silk_seed",
            "silk_seeds_info", "silk_seeds_copy_out", "silk_seeds_free", "geek_assign",
            "geek_assign_centers", "geek_timing_enable", "geek_timing_reset", "geek_timing_get",
-           "geek_launch_count", "geek_assign_centers_noalloc"]
+           "geek_launch_count", "geek_assign_centers_noalloc", "geek_batch_create", "geek_batch_run",
+           "geek_batch_info_get", "geek_batch_instance_stats", "geek_batch_copy_out", "geek_batch_seed_ids_count",
+           "geek_batch_destroy"]
 
 _lib = None
 
@@ -103,6 +123,14 @@ def lib():
                                   C.POINTER(C.c_double)]
     L.geek_launch_count.restype = C.c_ulonglong
     L.geek_assign_centers_noalloc.argtypes = [P, C.c_int64, C.c_int32, C.c_int64, P, C.c_int64, P, P]
+    L.geek_batch_create.argtypes = [P, C.POINTER(geek_instance), C.c_int32, C.POINTER(geek_batch_params),
+                                    C.POINTER(P)]
+    L.geek_batch_run.argtypes = [P, P, P]
+    L.geek_batch_info_get.argtypes = [P, C.POINTER(geek_batch_info)]
+    L.geek_batch_instance_stats.argtypes = [P, P, P, P, P]
+    L.geek_batch_copy_out.argtypes = [P, P, P, P, P, P, P]
+    L.geek_batch_seed_ids_count.argtypes = [P, C.POINTER(C.c_int64)]
+    L.geek_batch_destroy.argtypes = [P]
     for name in EXPORTS:
         f = getattr(L, name)
         if name not in ("geek_last_error", "geek_version", "geek_ctx_destroy", "geek_launch_count"):
@@ -316,3 +344,82 @@ def silk_args(sp):
     """Device copies of a SILK parameter dict (from synth.silk_params)."""
     return dict(Ks=sp["Ks"], Ls=sp["Ls"], delta=sp["delta"], mh_a=_dev(sp["mh_a"]), mh_b=_dev(sp["mh_b"]),
                 dd_a=_dev(sp["dd_a"]), dd_b=_dev(sp["dd_b"]))
+
+
+class Batch:
+    """A batch of dense instances (geek_batch): one plan, runs replayed.
+
+    ``instances`` is a list of dicts with device tensors x (n x d float32),
+    a (K*L x d float32), b (K*L float32), mh_a / mh_b (Ls*Ks int64 bits of
+    uint64), dd_a / dd_b (Ks), and w.  The tensors are kept alive here."""
+
+    def __init__(self, ctx: Context, instances, K, L, Ks, Ls, delta, proj=PROJ_E2LSH, tile_n=0):
+        self.ctx = ctx
+        self._refs = instances
+        arr = (geek_instance * len(instances))()
+        for c, I in zip(arr, instances):
+            x = I["x"]
+            c.n, c.d, c.ldx = x.shape[0], x.shape[1], x.shape[1]
+            c.x, c.a, c.b, c.w = _ptr(x), _ptr(I["a"]), _ptr(I["b"]), float(I["w"])
+            c.mh_a, c.mh_b, c.dd_a, c.dd_b = _ptr(I["mh_a"]), _ptr(I["mh_b"]), _ptr(I["dd_a"]), _ptr(I["dd_b"])
+        p = geek_batch_params()
+        p.proj, p.K, p.L, p.Ks, p.Ls, p.delta, p.tile_n = proj, K, L, Ks, Ls, delta, tile_n
+        h = C.c_void_p()
+        ctx._chk(lib().geek_batch_create(ctx.h, arr, len(instances), C.byref(p), C.byref(h)))
+        self.h = h
+        self.count = len(instances)
+        self.K, self.L = K, L
+        self.ns = [I["x"].shape[0] for I in instances]
+        self.ds = [I["x"].shape[1] for I in instances]
+        self.row_off = np.concatenate([[0], np.cumsum(self.ns)]).astype(np.int64)
+
+    def run(self, labels):
+        self.ctx._chk(lib().geek_batch_run(self.h, _ptr(labels), _stream()))
+
+    def info(self):
+        i = geek_batch_info()
+        self.ctx._chk(lib().geek_batch_info_get(self.h, C.byref(i)))
+        return {f: getattr(i, f) for f, _ in geek_batch_info._fields_}
+
+    def instance_stats(self):
+        n = self.count
+        k, sse, rmax = np.zeros(n, np.int64), np.zeros(n, np.float64), np.zeros(n, np.float64)
+        tile = np.zeros(n, np.int32)
+        self.ctx._chk(lib().geek_batch_instance_stats(self.h, k.ctypes.data, sse.ctypes.data, rmax.ctypes.data,
+                                                      tile.ctypes.data))
+        return dict(k=k, sse=sse, radius_max=rmax, tile_n=tile)
+
+    def copy_out(self):
+        """Per-instance results of the last run (host numpy)."""
+        st = self.instance_stats()
+        N = int(self.row_off[-1])
+        kt = int(st["k"].sum())
+        nid = C.c_int64()
+        self.ctx._chk(lib().geek_batch_seed_ids_count(self.h, C.byref(nid)))
+        codes = torch.empty((N, self.K * self.L), dtype=torch.int32, device="cuda")
+        ob = torch.empty((self.L, N), dtype=torch.int32, device="cuda")
+        soff = torch.empty(kt + 1, dtype=torch.int64, device="cuda")
+        sids = torch.empty(max(nid.value, 1), dtype=torch.int32, device="cuda")
+        kd = int(sum(int(k) * d for k, d in zip(st["k"], self.ds)))
+        cen = torch.empty(max(kd, 1), dtype=torch.float64, device="cuda")
+        self.ctx._chk(lib().geek_batch_copy_out(self.h, _ptr(codes), _ptr(ob), _ptr(soff), _ptr(sids), _ptr(cen),
+                                                _stream()))
+        codes, ob, soff = codes.cpu().numpy(), ob.cpu().numpy(), soff.cpu().numpy()
+        sids, cen = sids.cpu().numpy()[: nid.value], cen.cpu().numpy()
+        out = []
+        sb = np.concatenate([[0], np.cumsum(st["k"])])
+        co = np.concatenate([[0], np.cumsum(st["k"] * np.array(self.ds))])
+        for i in range(self.count):
+            r0, r1 = self.row_off[i], self.row_off[i + 1]
+            s0, s1 = sb[i], sb[i + 1]
+            seeds = [tuple(sids[soff[j]:soff[j + 1]].tolist()) for j in range(s0, s1)]
+            out.append(dict(codes=codes[r0:r1], obj_bucket=ob[:, r0:r1], seeds=seeds,
+                            centres=cen[co[i]:co[i + 1]].reshape(int(st["k"][i]), self.ds[i]),
+                            k=int(st["k"][i]), sse=float(st["sse"][i]), radius_max=float(st["radius_max"][i]),
+                            tile_n=int(st["tile_n"][i])))
+        return out
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().geek_batch_destroy(self.h)
+            self.h = None

@@ -270,25 +270,33 @@ def make(cfg: Config):
 # Batched workload: many uneven dense instances (one persistent launch).
 # ---------------------------------------------------------------------------
 def batch_instances(count: int = 256, n_range=(10_000, 500_000), d_choices=(32, 64, 128),
-                    comp_range=(10, 2000), seed: int = ROOT_SEED + 5, n_scale: float = 1.0):
+                    comp_range=(10, 2000), seed: int = ROOT_SEED + 5, n_scale: float = 1.0,
+                    threads: int = 1):
     """``count`` dense instances, n = floor(exp(U[ln 1e4, ln 5e5])) (times
     ``n_scale`` for parity cases), d uniform over {32, 64, 128}, components
     U{10..2000}, centres U[-10,10]^d, sigma = 1, equal weights, E2LSH K=4,
-    L=8, w=4 and SILK thresholds as for the small dense workload."""
+    L=8, w=4 and SILK thresholds as for the small dense workload.  Every
+    instance draws from its own stream, so ``threads`` (parallel generation)
+    does not change the values."""
     rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence(seed)))
     lo, hi = n_range
     ns = np.floor(np.exp(rng.uniform(math.log(lo), math.log(hi), count))).astype(np.int64)
     ns = np.maximum((ns * n_scale).astype(np.int64), 1)
     ds = rng.choice(np.array(d_choices), size=count)
     cs = rng.integers(comp_range[0], comp_range[1] + 1, size=count)
-    out = []
-    for i in range(count):
+
+    def one(i):
         cfg = Config("c5", "dense", n=int(ns[i]), d=int(ds[i]), n_comp=int(cs[i]),
                      centre_range=10.0, sigma=(1.0, 1.0), weights="equal",
                      K=4, L=8, w=4.0, silk=dict(SILK_DEFAULTS["c5"]), seed=seed)
         rdata, rhash, rsilk = _streams(seed, (i,))
         x, lab, centres = dense_points(cfg, rdata)
         a, b = projection_params(cfg, rhash)
-        out.append(dict(cfg=cfg, x=x, labels=lab, centres=centres, a=a, b=b,
-                        w=float(cfg.w), silk=silk_params(cfg, rsilk)))
-    return out
+        return dict(cfg=cfg, x=x, labels=lab, centres=centres, a=a, b=b,
+                    w=float(cfg.w), silk=silk_params(cfg, rsilk))
+
+    if threads <= 1:
+        return [one(i) for i in range(count)]
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(threads) as ex:
+        return list(ex.map(one, range(count)))
