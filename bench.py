@@ -360,7 +360,8 @@ def bench_batched(args, geek, ctx, pk, pk_kind):
     ctx.timing(False)
     launches = (geek.launch_count() - l0) / args.steps
     phases = {ph: ctx.timing_get(ph)[0] / args.steps
-              for ph in ["batch.hash_graph", "batch.group", "batch.silk", "batch.assign_graph"]}
+              for ph in ["batch.hash_graph", "batch.group", "batch.silk", "batch.assign_graph", "hash.sort",
+                         "silk.vbuckets", "silk.bins", "silk.vote", "silk.dedup"]}
     st = b.instance_stats()
     info = b.info()
     lab_b = labels.cpu().numpy()

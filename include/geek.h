@@ -54,8 +54,12 @@ enum { GEEK_DENSE = 0, GEEK_SETS = 1, GEEK_HETERO = 2 };
 enum { GEEK_MEM_DEVICE = 0, GEEK_MEM_HOST = 1 };
 /* dense projection family */
 enum { GEEK_PROJ_E2LSH = 0, GEEK_PROJ_SRP = 1 };
-/* arithmetic of the fast path (FP64 rechecks keep every result exact) */
-enum { GEEK_PREC_FP32 = 0, GEEK_PREC_BF16 = 1 };
+/* arithmetic of the fast path (FP64 rechecks keep every result exact):
+ * FP32 SIMT; BF16 tcgen05 (one product per term, error window ~2^-7 |x||c|);
+ * split-BF16 tcgen05 (x = x_h + x_l, c = c_h + c_l in BF16 pairs, three
+ * products x_h.c_h + x_l.c_h + x_h.c_l, window ~2^-14 |x||c|: far fewer
+ * near-tie rechecks for three times the tensor work) */
+enum { GEEK_PREC_FP32 = 0, GEEK_PREC_BF16 = 1, GEEK_PREC_BF16X3 = 2 };
 
 /* One data set.
  *  DENSE : x is n x d float32, row-major with row stride ldx (elements).
@@ -121,7 +125,7 @@ typedef struct silk_params {
 } silk_params;
 
 typedef struct geek_assign_params {
-    int32_t precision; /* GEEK_PREC_FP32 (SIMT) or GEEK_PREC_BF16 (tcgen05) */
+    int32_t precision; /* GEEK_PREC_FP32 (SIMT), GEEK_PREC_BF16 or GEEK_PREC_BF16X3 (tcgen05) */
 } geek_assign_params;
 
 typedef struct geek_assign_stats {
@@ -269,11 +273,13 @@ geek_status geek_assign_centers_noalloc(const float *x, int64_t n, int32_t d, in
  * runs every instance's row blocks in one launch and the BF16 tcgen05 assignment
  * runs all (instance, row tile) units in one persistent launch; both phases are
  * captured in CUDA graphs on the first run and replayed by later runs.  The
- * centre-tile width of the assignment (64, 128 or 256 columns) is chosen per
- * instance by an autotuner that times the candidates on the batch's own data
- * the first time a (d, seed count) class is seen on a context.
+ * assignment's arithmetic (BF16 or split-BF16) and centre-tile width (64, 128
+ * or 256 columns) are chosen per instance by an autotuner that times the
+ * candidates, FP64 near-tie decisions included, on the batch's own data the
+ * first time a (d, seed count) class is seen on a context.
  * Results are, instance by instance, exactly those of geek_hash + silk_seed +
- * geek_assign (GEEK_PREC_BF16) on that instance alone. */
+ * geek_assign on that instance alone (every precision gives the same,
+ * exact labels). */
 typedef struct geek_batch geek_batch;
 
 /* One dense instance: x (n x d float32, row stride ldx, n >= 0, 1 <= d <= 128),
@@ -295,12 +301,18 @@ typedef struct geek_instance {
 } geek_instance;
 
 /* Shared by every instance: projection family, K functions per table, L
- * tables, SILK Ks / Ls / delta, and tile_n: 0 = autotuned, or 64 / 128 / 256
- * to force the assignment's centre-tile width. */
+ * tables, SILK Ks / Ls / delta; the assignment's arithmetic, precision =
+ * GEEK_PREC_BF16, GEEK_PREC_BF16X3 or GEEK_PREC_AUTO (the autotuner picks one
+ * per class of instances: the fewer tensor products of BF16 against the
+ * fewer FP64 near-tie decisions of split-BF16); tile_n: 0 = autotuned, or
+ * 64 / 128 / 256 to force the centre-tile width (split-BF16 caps it at 128
+ * for d <= 64 and 64 for d <= 128). */
+#define GEEK_PREC_AUTO (-1)
 typedef struct geek_batch_params {
     int32_t proj;
     int32_t K, L;
     int32_t Ks, Ls, delta;
+    int32_t precision;
     int32_t tile_n;
 } geek_batch_params;
 
@@ -337,9 +349,10 @@ geek_status geek_batch_info_get(const geek_batch *b, geek_batch_info *info);
 
 /* Per-instance results of the last run, HOST arrays of `count` entries (each
  * pointer may be NULL): seed count k, SSE and largest distance to the
- * assigned centre (Sect. 4.1), and the assignment's centre-tile width. */
+ * assigned centre (Sect. 4.1), and the assignment's centre-tile width and
+ * precision (GEEK_PREC_BF16 or GEEK_PREC_BF16X3). */
 geek_status geek_batch_instance_stats(const geek_batch *b, int64_t *k, double *sse, double *radius_max,
-                                      int32_t *tile_n);
+                                      int32_t *tile_n, int32_t *precision);
 
 /* Device copies of the last run's intermediate results (each pointer may be
  * NULL):

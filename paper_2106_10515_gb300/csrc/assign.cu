@@ -8,6 +8,7 @@
 // order, each operation rounded to nearest, no fused multiply-add; ties go
 // to the smallest centre index.
 #include <cfloat>
+#include <type_traits>
 
 #include "internal.cuh"
 
@@ -68,169 +69,309 @@ __device__ __forceinline__ Best best_merge(Best a, Best b) {
 
 // FP32 SIMT assignment: block = 128 rows, all centres streamed in tiles of
 // 64; 256 threads = 16 row groups (8 rows) x 16 centre groups (4 centres).
-__global__ void __launch_bounds__(256) k_assign_fp32(const float *__restrict__ x, int64_t ldx, int64_t n,
-                                                     int d, const float *__restrict__ c32,
-                                                     const float *__restrict__ cn, int64_t k, float cmax,
-                                                     int32_t *__restrict__ labels,
-                                                     int32_t *__restrict__ flag_rows,
-                                                     unsigned long long *__restrict__ n_flag) {
+// GATHER = false: blocks walk the row tiles of the one data set A.
+// GATHER = true: blocks walk units of up to 128 flagged rows of one instance
+// (unit u: instance unit_inst[u], global rows grows[unit_start[u] ..
+// + unit_cnt[u]]); the instance's data replace A's, uncertain rows are
+// appended (as global rows) to A.flag_rows.
+struct FArgs {
+    const float *x;
+    int64_t ldx, n;
+    int d;
+    const float *c32, *cn;
+    int64_t k;
+    float cmax;
+    int32_t *labels;
+    int32_t *flag_rows;
+    unsigned long long *n_flag;
+    int64_t ntiles;
+};
+struct GatherUnits {
+    const RInst *R;
+    const int32_t *grows;
+    const int *unit_inst;
+    const int64_t *unit_start;
+    const int *unit_cnt;
+    const int *n_units;
+};
+
+template <bool GATHER>
+__global__ void __launch_bounds__(256) k_assign_fp32(FArgs A, GatherUnits U) {
     extern __shared__ float sm[];
-    float *xs = sm;                         // [d][AS_TR]
-    float *cs = sm + (size_t)d * AS_TR;     // [AS_KC][AS_TC]
     __shared__ float cns[AS_TC];
+    __shared__ int64_t s_rows[AS_TR];
     const int t = threadIdx.x, cg = t & 15, rg = t >> 4;
-    const int64_t row0 = (int64_t)blockIdx.x * AS_TR;
-    for (int e = t; e < AS_TR * d; e += 256) {
-        const int r = e / d, kk = e % d;
-        const int64_t row = row0 + r;
-        xs[kk * AS_TR + r] = row < n ? x[row * ldx + kk] : 0.f;
-    }
-    Best B[AS_RPT];
-#pragma unroll
-    for (int r = 0; r < AS_RPT; r++) B[r] = Best{FLT_MAX, FLT_MAX, 0x7FFFFFFF};
-    for (int64_t j0 = 0; j0 < k; j0 += AS_TC) {
-        float acc[AS_RPT][AS_CPT];
-#pragma unroll
-        for (int r = 0; r < AS_RPT; r++)
-#pragma unroll
-            for (int c = 0; c < AS_CPT; c++) acc[r][c] = 0.f;
-        for (int k0 = 0; k0 < d; k0 += AS_KC) {
+    const int64_t nunits = GATHER ? (int64_t)*U.n_units : A.ntiles;
+    for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+        int64_t row0 = u * AS_TR;
+        int nrows = (int)min((int64_t)AS_TR, A.n - row0);
+        int64_t rbase = 0;
+        if (GATHER) {
+            const RInst &I = U.R[U.unit_inst[u]];
+            A.x = I.x;
+            A.ldx = I.ldx;
+            A.d = I.d;
+            A.c32 = I.c32;
+            A.cn = I.cn;
+            A.k = I.k;
+            A.cmax = __uint_as_float(*I.cmax_bits);
+            A.labels = I.labels;
+            rbase = I.row_base;
+            nrows = U.unit_cnt[u];
+            __syncthreads();  // s_rows of the previous unit fully used
+            if (t < nrows) s_rows[t] = (int64_t)U.grows[U.unit_start[u] + t] - rbase;
             __syncthreads();
-            for (int e = t; e < AS_TC * AS_KC; e += 256) {
-                const int c = e / AS_KC, kk = e % AS_KC;
-                const int64_t j = j0 + c;
-                cs[kk * AS_TC + c] = (j < k && k0 + kk < d) ? c32[j * d + k0 + kk] : 0.f;
+        }
+        const int d = A.d;
+        const int64_t k = A.k;
+        float *xs = sm;                         // [d][AS_TR]
+        float *cs = sm + (size_t)d * AS_TR;     // [AS_KC][AS_TC]
+        __syncthreads();
+        for (int e = t; e < AS_TR * d; e += 256) {
+            const int r = e / d, kk = e % d;
+            float v = 0.f;
+            if (r < nrows) v = A.x[(GATHER ? s_rows[r] : row0 + r) * A.ldx + kk];
+            xs[kk * AS_TR + r] = v;
+        }
+        Best B[AS_RPT];
+#pragma unroll
+        for (int r = 0; r < AS_RPT; r++) B[r] = Best{FLT_MAX, FLT_MAX, 0x7FFFFFFF};
+        for (int64_t j0 = 0; j0 < k; j0 += AS_TC) {
+            float acc[AS_RPT][AS_CPT];
+#pragma unroll
+            for (int r = 0; r < AS_RPT; r++)
+#pragma unroll
+                for (int c = 0; c < AS_CPT; c++) acc[r][c] = 0.f;
+            for (int k0 = 0; k0 < d; k0 += AS_KC) {
+                __syncthreads();
+                for (int e = t; e < AS_TC * AS_KC; e += 256) {
+                    const int c = e / AS_KC, kk = e % AS_KC;
+                    const int64_t j = j0 + c;
+                    cs[kk * AS_TC + c] = (j < k && k0 + kk < d) ? A.c32[j * d + k0 + kk] : 0.f;
+                }
+                if (k0 == 0 && t < AS_TC) cns[t] = j0 + t < k ? A.cn[j0 + t] : FLT_MAX;
+                __syncthreads();
+                const int kmax = min(AS_KC, d - k0);
+                for (int kk = 0; kk < kmax; kk++) {
+                    const float4 x0 = *reinterpret_cast<const float4 *>(&xs[(k0 + kk) * AS_TR + rg * AS_RPT]);
+                    const float4 x1 = *reinterpret_cast<const float4 *>(&xs[(k0 + kk) * AS_TR + rg * AS_RPT + 4]);
+                    const float4 cv = *reinterpret_cast<const float4 *>(&cs[kk * AS_TC + cg * AS_CPT]);
+                    const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+                    const float cc[4] = {cv.x, cv.y, cv.z, cv.w};
+#pragma unroll
+                    for (int r = 0; r < AS_RPT; r++)
+#pragma unroll
+                        for (int c = 0; c < AS_CPT; c++) acc[r][c] = fmaf(xv[r], cc[c], acc[r][c]);
+                }
             }
-            if (k0 == 0 && t < AS_TC) cns[t] = j0 + t < k ? cn[j0 + t] : FLT_MAX;
-            __syncthreads();
-            const int kmax = min(AS_KC, d - k0);
-            for (int kk = 0; kk < kmax; kk++) {
-                const float4 x0 = *reinterpret_cast<const float4 *>(&xs[(k0 + kk) * AS_TR + rg * AS_RPT]);
-                const float4 x1 = *reinterpret_cast<const float4 *>(&xs[(k0 + kk) * AS_TR + rg * AS_RPT + 4]);
-                const float4 cv = *reinterpret_cast<const float4 *>(&cs[kk * AS_TC + cg * AS_CPT]);
-                const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-                const float cc[4] = {cv.x, cv.y, cv.z, cv.w};
 #pragma unroll
-                for (int r = 0; r < AS_RPT; r++)
+            for (int c = 0; c < AS_CPT; c++) {
+                const int64_t j = j0 + cg * AS_CPT + c;
+                if (j >= k) continue;
+                const float cnj = cns[cg * AS_CPT + c];
 #pragma unroll
-                    for (int c = 0; c < AS_CPT; c++) acc[r][c] = fmaf(xv[r], cc[c], acc[r][c]);
+                for (int r = 0; r < AS_RPT; r++) best_push(B[r], fmaf(-2.f, acc[r][c], cnj), (int)j);
             }
         }
-#pragma unroll
-        for (int c = 0; c < AS_CPT; c++) {
-            const int64_t j = j0 + cg * AS_CPT + c;
-            if (j >= k) continue;
-            const float cnj = cns[cg * AS_CPT + c];
-#pragma unroll
-            for (int r = 0; r < AS_RPT; r++) best_push(B[r], fmaf(-2.f, acc[r][c], cnj), (int)j);
-        }
-    }
-    // merge the 16 centre groups of each row group (lanes of one half-warp)
-#pragma unroll
-    for (int r = 0; r < AS_RPT; r++) {
-#pragma unroll
-        for (int o = 1; o < 16; o <<= 1) {
-            Best o_;
-            o_.b1 = __shfl_xor_sync(0xffffffffu, B[r].b1, o);
-            o_.b2 = __shfl_xor_sync(0xffffffffu, B[r].b2, o);
-            o_.i1 = __shfl_xor_sync(0xffffffffu, B[r].i1, o);
-            B[r] = best_merge(B[r], o_);
-        }
-    }
-    if (cg == 0) {
+        // merge the 16 centre groups of each row group (lanes of one half-warp)
 #pragma unroll
         for (int r = 0; r < AS_RPT; r++) {
-            const int64_t row = row0 + rg * AS_RPT + r;
-            if (row >= n) continue;
-            float xs2 = 0.f;
-            for (int kk = 0; kk < d; kk++) {
-                const float v = xs[kk * AS_TR + rg * AS_RPT + r];
-                xs2 = fmaf(v, v, xs2);
+#pragma unroll
+            for (int o = 1; o < 16; o <<= 1) {
+                Best o_;
+                o_.b1 = __shfl_xor_sync(0xffffffffu, B[r].b1, o);
+                o_.b2 = __shfl_xor_sync(0xffffffffu, B[r].b2, o);
+                o_.i1 = __shfl_xor_sync(0xffffffffu, B[r].i1, o);
+                B[r] = best_merge(B[r], o_);
             }
-            const float xn = sqrtf(xs2) * (1.f + 1.0e-3f);
-            const float W = 2.f * window_fp32(xn, cmax, d);
-            // no finite value (non-finite input): undecided here, FP64 decides
-            const bool valid = B[r].i1 != 0x7FFFFFFF;
-            labels[row] = valid ? B[r].i1 : -1;
-            const bool sure = valid && (k == 1 || (B[r].b2 - B[r].b1 > W * (1.f + 1e-6f)));
-            if (!sure) {
-                const unsigned long long q = atomicAdd(n_flag, 1ull);
-                flag_rows[q] = (int32_t)row;
+        }
+        if (cg == 0) {
+#pragma unroll
+            for (int r = 0; r < AS_RPT; r++) {
+                const int rr = rg * AS_RPT + r;
+                if (rr >= nrows) continue;
+                const int64_t row = GATHER ? s_rows[rr] : row0 + rr;
+                float xs2 = 0.f;
+                for (int kk = 0; kk < d; kk++) {
+                    const float v = xs[kk * AS_TR + rr];
+                    xs2 = fmaf(v, v, xs2);
+                }
+                const float xn = sqrtf(xs2) * (1.f + 1.0e-3f);
+                const float W = 2.f * window_fp32(xn, A.cmax, d);
+                // no finite value (non-finite input): undecided here, FP64 decides
+                const bool valid = B[r].i1 != 0x7FFFFFFF;
+                A.labels[row] = valid ? B[r].i1 : -1;
+                const bool sure = valid && (k == 1 || (B[r].b2 - B[r].b1 > W * (1.f + 1e-6f)));
+                if (!sure) {
+                    const unsigned long long q = atomicAdd(A.n_flag, 1ull);
+                    A.flag_rows[q] = (int32_t)(rbase + row);
+                }
             }
         }
     }
 }
 
-// Exact decision for one flagged object: FP32 filter over all centres, then
-// the FP64 reference distance for every centre inside the window.  Flag
-// entries are global rows; instance i owns rows [row_off[i], row_off[i+1]).
+// ---- grouping a flag list by instance (device-side, graph friendly) --------
+__global__ void k_flag_count(const int32_t *__restrict__ flags, const unsigned long long *__restrict__ n_flag,
+                             const int64_t *__restrict__ row_off, int count, int *__restrict__ cnt) {
+    const int64_t nf = (int64_t)*n_flag;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nf; q += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[find_inst(row_off, count, flags[q])], 1);
+}
+
+// one block: segment offsets and 128-row units per instance; cursor[i] =
+// segment start for the scatter
+__global__ void __launch_bounds__(1024) k_flag_units(const int *__restrict__ cnt, int count, int64_t *__restrict__ cursor,
+                                                     int *__restrict__ unit_inst, int64_t *__restrict__ unit_start,
+                                                     int *__restrict__ unit_cnt, int *__restrict__ n_units) {
+    __shared__ int64_t seg_carry, unit_carry;
+    __shared__ int64_t s_seg[1024], s_unit[1024];
+    if (threadIdx.x == 0) seg_carry = unit_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < count; base += 1024) {
+        const int i = base + threadIdx.x;
+        const int64_t c = i < count ? cnt[i] : 0;
+        const int64_t nu = (c + AS_TR - 1) / AS_TR;
+        s_seg[threadIdx.x] = c;
+        s_unit[threadIdx.x] = nu;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {  // inclusive scans
+            const int64_t a = threadIdx.x >= o ? s_seg[threadIdx.x - o] : 0;
+            const int64_t b = threadIdx.x >= o ? s_unit[threadIdx.x - o] : 0;
+            __syncthreads();
+            s_seg[threadIdx.x] += a;
+            s_unit[threadIdx.x] += b;
+            __syncthreads();
+        }
+        const int64_t so = seg_carry + s_seg[threadIdx.x] - c, uo = unit_carry + s_unit[threadIdx.x] - nu;
+        if (i < count) {
+            cursor[i] = so;
+            for (int64_t q = 0; q < nu; q++) {
+                unit_inst[uo + q] = i;
+                unit_start[uo + q] = so + q * AS_TR;
+                unit_cnt[uo + q] = (int)min((int64_t)AS_TR, c - q * AS_TR);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 1023) {
+            seg_carry += s_seg[1023];
+            unit_carry += s_unit[1023];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *n_units = (int)unit_carry;
+}
+
+__global__ void k_flag_scatter(const int32_t *__restrict__ flags, const unsigned long long *__restrict__ n_flag,
+                               const int64_t *__restrict__ row_off, int count, int64_t *__restrict__ cursor,
+                               int32_t *__restrict__ grows) {
+    const int64_t nf = (int64_t)*n_flag;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nf; q += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = flags[q];
+        grows[atomicAdd((unsigned long long *)&cursor[find_inst(row_off, count, r)], 1ull)] = r;
+    }
+}
+
+// Exact decision for flagged objects, one warp per object: an FP32 pass over
+// all centres (lanes over coordinates, coalesced centre reads, the row held
+// in registers) finds the smallest fast value m; a second pass takes every
+// centre whose fast value is within the FP32 window of m and decides among
+// them with the FP64 reference distance, one candidate per lane, ties to the
+// smaller index.  Flag entries are global rows; instance i owns rows
+// [row_off[i], row_off[i + 1]).  d <= 256.
+constexpr int RC_MAXD = 256;
 __global__ void __launch_bounds__(256) k_assign_recheck(const RInst *__restrict__ R,
                                                         const int64_t *__restrict__ row_off, int count,
                                                         const int32_t *__restrict__ flag_rows,
                                                         const unsigned long long *__restrict__ n_flag) {
-    extern __shared__ float xr[];  // d floats
-    __shared__ float red_f[256];
-    __shared__ double red_d[256];
-    __shared__ int red_i[256];
-    const int t = threadIdx.x;
+    __shared__ float xs[8][RC_MAXD];  // the warp's row, for the FP64 candidates
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nf = (int64_t)*n_flag;
-    for (int64_t q = blockIdx.x; q < nf; q += gridDim.x) {
+    for (int64_t q = warp; q < nf; q += nw) {
         const int64_t grow = flag_rows[q];
         const RInst &I = R[find_inst(row_off, count, grow)];
         const int64_t row = grow - I.row_base;
         const int d = I.d;
         const int64_t k = I.k;
-        const float *c32 = I.c32, *cn = I.cn;
-        const float cmax = __uint_as_float(*I.cmax_bits);
-        __syncthreads();
-        for (int kk = t; kk < d; kk += 256) xr[kk] = I.x[row * I.ldx + kk];
-        __syncthreads();
+        const float *xr = I.x + row * I.ldx;
+        float xv[RC_MAXD / 32];
         float xs2 = 0.f;
-        for (int kk = 0; kk < d; kk++) xs2 = fmaf(xr[kk], xr[kk], xs2);
+#pragma unroll
+        for (int u = 0; u < RC_MAXD / 32; u++) {
+            const int t = lane + 32 * u;
+            xv[u] = t < d ? xr[t] : 0.f;
+            if (t < d) xs[wib][t] = xv[u];
+            xs2 = fmaf(xv[u], xv[u], xs2);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) xs2 += __shfl_xor_sync(0xffffffffu, xs2, o);
+        __syncwarp();
         const float xn = sqrtf(xs2) * (1.f + 1.0e-3f);
-        float m = FLT_MAX;
-        for (int64_t j = t; j < k; j += 256) {
+        const float cmax = __uint_as_float(*I.cmax_bits);
+        const int nu = (d + 31) / 32;
+        // fast value of centre j (warp-uniform result)
+        auto fast = [&](int64_t j) {
+            const float *cr = I.c32 + j * d;
             float dot = 0.f;
-            for (int kk = 0; kk < d; kk++) dot = fmaf(xr[kk], c32[j * d + kk], dot);
-            m = fminf(m, fmaf(-2.f, dot, cn[j]));
-        }
-        red_f[t] = m;
-        __syncthreads();
-        for (int o = 128; o > 0; o >>= 1) {
-            if (t < o) red_f[t] = fminf(red_f[t], red_f[t + o]);
-            __syncthreads();
-        }
-        const float lim = red_f[0] + 2.f * window_fp32(xn, cmax, d) * (1.f + 1e-6f);
+#pragma unroll
+            for (int u = 0; u < RC_MAXD / 32; u++)
+                if (u < nu) {
+                    const int t = lane + 32 * u;
+                    if (t < d) dot = fmaf(xv[u], cr[t], dot);
+                }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+            return fmaf(-2.f, dot, I.cn[j]);
+        };
+        float m = FLT_MAX;
+        for (int64_t j = 0; j < k; j++) m = fminf(m, fast(j));
+        const float lim = m + 2.f * window_fp32(xn, cmax, d) * (1.f + 1e-6f);
         double bD = DBL_MAX;
         int bj = 0x7FFFFFFF;
-        for (int64_t j = t; j < k; j += 256) {
-            float dot = 0.f;
-            for (int kk = 0; kk < d; kk++) dot = fmaf(xr[kk], c32[j * d + kk], dot);
-            if (fmaf(-2.f, dot, cn[j]) <= lim) {
-                const double D = ref_dist(xr, I.c64 + j * d, d);
-                if (D < bD || (D == bD && (int)j < bj)) {
-                    bD = D;
-                    bj = (int)j;
+        int64_t cand = -1;  // this lane's pending candidate
+        int nc = 0;
+        for (int64_t j = 0; j < k; j++) {
+            if (fast(j) <= lim) {  // warp-uniform
+                if (lane == nc) cand = j;
+                if (++nc == 32 || j == k - 1) {
+                    if (cand >= 0) {
+                        const double D = ref_dist(xs[wib], I.c64 + cand * d, d);
+                        if (D < bD || (D == bD && (int)cand < bj)) {
+                            bD = D;
+                            bj = (int)cand;
+                        }
+                    }
+                    cand = -1;
+                    nc = 0;
                 }
+            } else if (j == k - 1 && nc > 0) {
+                if (cand >= 0) {
+                    const double D = ref_dist(xs[wib], I.c64 + cand * d, d);
+                    if (D < bD || (D == bD && (int)cand < bj)) {
+                        bD = D;
+                        bj = (int)cand;
+                    }
+                }
+                cand = -1;
+                nc = 0;
             }
         }
-        red_d[t] = bD;
-        red_i[t] = bj;
-        __syncthreads();
-        for (int o = 128; o > 0; o >>= 1) {
-            if (t < o) {
-                const double D2 = red_d[t + o];
-                const int j2 = red_i[t + o];
-                if (D2 < red_d[t] || (D2 == red_d[t] && j2 < red_i[t])) {
-                    red_d[t] = D2;
-                    red_i[t] = j2;
-                }
+        // warp argmin, ties to the smaller index
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double D2 = __shfl_xor_sync(0xffffffffu, bD, o);
+            const int j2 = __shfl_xor_sync(0xffffffffu, bj, o);
+            if (D2 < bD || (D2 == bD && j2 < bj)) {
+                bD = D2;
+                bj = j2;
             }
-            __syncthreads();
         }
         // no candidate with a distance below +inf (non-finite input): -1,
         // as the reference argmin that never improves on +inf
-        if (t == 0) I.labels[row] = red_i[0] == 0x7FFFFFFF ? -1 : red_i[0];
+        if (lane == 0) I.labels[row] = bj == 0x7FFFFFFF ? -1 : bj;
+        __syncwarp();
     }
 }
 
@@ -460,7 +601,7 @@ geek_status assign_dense_centres(geek_ctx *ctx, Scratch &scr, const float *x, in
         return GEEK_OK;
     }
     if (d > AS_MAXD) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "dense assignment supports d <= %d", AS_MAXD);
-    if (precision != GEEK_PREC_FP32 && precision != GEEK_PREC_BF16)
+    if (precision != GEEK_PREC_FP32 && precision != GEEK_PREC_BF16 && precision != GEEK_PREC_BF16X3)
         return set_error(ctx, GEEK_ERR_INVALID, "bad precision");
     float *c32, *cn;
     unsigned *cmax_bits;
@@ -498,27 +639,35 @@ geek_status assign_dense_centres(geek_ctx *ctx, Scratch &scr, const float *x, in
     GK_TRY(scr.alloc(&flag_rows, n));
     GK_TRY(scr.alloc(&n_flag, 1));
     GK_CUDA(ctx, cudaMemsetAsync(n_flag, 0, sizeof(unsigned long long), st));
-    if (precision == GEEK_PREC_BF16) {
-        GK_TRY(assign_tc_bf16(ctx, scr, x, ldx, n, d, centres, k, labels, flag_rows, n_flag, st));
+    if (precision == GEEK_PREC_BF16 || precision == GEEK_PREC_BF16X3) {
+        GK_TRY(assign_tc_bf16(ctx, scr, x, ldx, n, d, centres, k, precision == GEEK_PREC_BF16X3, labels, flag_rows,
+                              n_flag, st));
     } else {
         const size_t smem = (size_t)d * AS_TR * sizeof(float) + (size_t)AS_KC * AS_TC * sizeof(float);
-        GK_CUDA(ctx, cudaFuncSetAttribute(k_assign_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        GK_CUDA(ctx, cudaFuncSetAttribute(k_assign_fp32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         EvTimer tk(ctx, "kernel.assign_fp32", st);
         tk.work = 2.0 * (double)n * (double)k * (double)d;
+        FArgs A{x, ldx, n, d, c32, cn, k, cmax, labels, flag_rows, n_flag, ceil_div(n, AS_TR)};
         GK_COUNT();
-        k_assign_fp32<<<(unsigned)ceil_div(n, AS_TR), 256, smem, st>>>(x, ldx, n, d, c32, cn, k, cmax, labels,
-                                                                         flag_rows, n_flag);
+        k_assign_fp32<false><<<(unsigned)A.ntiles, 256, smem, st>>>(A, GatherUnits{});
         GK_LAUNCH(ctx);
     }
     unsigned long long h_flag = 0;
     GK_CUDA(ctx, cudaMemcpyAsync(&h_flag, n_flag, sizeof h_flag, cudaMemcpyDeviceToHost, st));
     GK_CUDA(ctx, cudaStreamSynchronize(st));
     if (h_flag) {
-        const int blocks = (int)std::min<unsigned long long>(h_flag, (unsigned long long)ctx->num_sms * 8);
-        EvTimer tk(ctx, "kernel.assign_recheck", st);
-        GK_COUNT();
-        k_assign_recheck<<<blocks, 256, d * sizeof(float), st>>>(ri, roff, 1, flag_rows, n_flag);
-        GK_LAUNCH(ctx);
+        DecideBufs db;
+        GK_TRY(decide_bufs_alloc(ctx, &scr, 1, n, db));
+        if (precision == GEEK_PREC_FP32) {
+            // the FP32 pass already applied the FP32 window: straight to FP64
+            const int blocks = (int)std::min<unsigned long long>(ceil_div((int64_t)h_flag, 8), (unsigned long long)ctx->num_sms * 8);
+            EvTimer tk(ctx, "kernel.assign_recheck", st);
+            GK_COUNT();
+            k_assign_recheck<<<blocks, 256, 0, st>>>(ri, roff, 1, flag_rows, n_flag);
+            GK_LAUNCH(ctx);
+        } else {
+            GK_TRY(decide_flags(ctx, ri, roff, 1, d, flag_rows, n_flag, db, st));
+        }
     }
     if (stats) {
         const int nb = grid_for(n, 256, ctx->num_sms);
@@ -567,14 +716,6 @@ geek_status centre_prep_batch(geek_ctx *ctx, const CInst *C, const int64_t *k_of
     return GEEK_OK;
 }
 
-geek_status recheck_batch(geek_ctx *ctx, const RInst *R, const int64_t *row_off, int count, int dmax,
-                          const int32_t *flag_rows, const unsigned long long *n_flag, cudaStream_t st) {
-    EvTimer tk(ctx, "kernel.assign_recheck", st);
-    GK_COUNT();
-    k_assign_recheck<<<ctx->num_sms * 8, 256, dmax * sizeof(float), st>>>(R, row_off, count, flag_rows, n_flag);
-    GK_LAUNCH(ctx);
-    return GEEK_OK;
-}
 
 geek_status centre_split(geek_ctx *ctx, const double *c64, int64_t total, float *chi, float *clo, cudaStream_t st) {
     if (total == 0) return GEEK_OK;
@@ -601,6 +742,72 @@ geek_status fill_labels(geek_ctx *ctx, int32_t *labels, int64_t n, int32_t v, cu
     if (n == 0) return GEEK_OK;
     GK_COUNT();
     k_fill_labels<<<grid_for(n, 256, ctx->num_sms), 256, 0, st>>>(labels, n, v);
+    GK_LAUNCH(ctx);
+    return GEEK_OK;
+}
+
+geek_status decide_bufs_alloc(geek_ctx *ctx, Scratch *scr, int count, int64_t n_total, DecideBufs &B) {
+    const int64_t nu = ceil_div(n_total, AS_TR) + count;
+    auto al = [&](auto **p, size_t c) -> geek_status {
+        if (scr) return scr->alloc(p, c);
+        void *q = nullptr;
+        if (cudaMalloc(&q, std::max<size_t>(c * sizeof(**p), 16)) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(ctx, GEEK_ERR_NOMEM, "decision buffers");
+        }
+        B.owned.push_back(q);
+        *p = (std::remove_reference_t<decltype(*p)>)q;
+        return GEEK_OK;
+    };
+    GK_TRY(al(&B.cnt, count));
+    GK_TRY(al(&B.cursor, count));
+    GK_TRY(al(&B.unit_inst, nu));
+    GK_TRY(al(&B.unit_start, nu));
+    GK_TRY(al(&B.unit_cnt, nu));
+    GK_TRY(al(&B.n_units, 1));
+    GK_TRY(al(&B.grows, std::max<int64_t>(n_total, 1)));
+    GK_TRY(al(&B.flags2, std::max<int64_t>(n_total, 1)));
+    GK_TRY(al(&B.n_flag2, 1));
+    return GEEK_OK;
+}
+
+void decide_bufs_free(DecideBufs &B) {
+    for (void *p : B.owned) cudaFree(p);
+    B.owned.clear();
+}
+
+// Decides the flagged rows of a fast pass exactly: rows grouped by
+// instance, a tiled FP32 pass (narrow FP32 window) over each group, then the
+// FP64 reference for the rows still uncertain.  No host synchronisation.
+geek_status decide_flags(geek_ctx *ctx, const RInst *R, const int64_t *row_off, int count, int dmax,
+                         const int32_t *flags, const unsigned long long *n_flag, const DecideBufs &B,
+                         cudaStream_t st) {
+    EvTimer tk(ctx, "kernel.assign_recheck", st);
+    const int g = ctx->num_sms * 4;
+    GK_CUDA(ctx, cudaMemsetAsync(B.cnt, 0, sizeof(int) * count, st));
+    GK_CUDA(ctx, cudaMemsetAsync(B.n_flag2, 0, sizeof(unsigned long long), st));
+    GK_COUNT();
+    k_flag_count<<<g, 256, 0, st>>>(flags, n_flag, row_off, count, B.cnt);
+    GK_COUNT();
+    k_flag_units<<<1, 1024, 0, st>>>(B.cnt, count, B.cursor, B.unit_inst, B.unit_start, B.unit_cnt, B.n_units);
+    GK_COUNT();
+    k_flag_scatter<<<g, 256, 0, st>>>(flags, n_flag, row_off, count, B.cursor, B.grows);
+    GK_LAUNCH(ctx);
+    const size_t smem = (size_t)dmax * AS_TR * sizeof(float) + (size_t)AS_KC * AS_TC * sizeof(float);
+    static bool attr = false;
+    if (!attr) {
+        const size_t mx = (size_t)AS_MAXD * AS_TR * sizeof(float) + (size_t)AS_KC * AS_TC * sizeof(float);
+        GK_CUDA(ctx, cudaFuncSetAttribute(k_assign_fp32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
+        attr = true;
+    }
+    FArgs A{};
+    A.flag_rows = B.flags2;
+    A.n_flag = B.n_flag2;
+    GatherUnits U{R, B.grows, B.unit_inst, B.unit_start, B.unit_cnt, B.n_units};
+    GK_COUNT();
+    k_assign_fp32<true><<<ctx->num_sms * 2, 256, smem, st>>>(A, U);
+    GK_COUNT();
+    k_assign_recheck<<<ctx->num_sms * 8, 256, 0, st>>>(R, row_off, count, B.flags2, B.n_flag2);
     GK_LAUNCH(ctx);
     return GEEK_OK;
 }

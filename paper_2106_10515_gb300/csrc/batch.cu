@@ -88,8 +88,16 @@ int k_class(int64_t k) {
 }
 
 // default centre-tile width before (or without) tuning: the narrowest
-// candidate that holds all centres, else the widest
-int tile_default(int64_t k) { return k <= 64 ? 64 : (k <= 128 ? 128 : 256); }
+// candidate that holds all centres, else the widest the mode allows
+// (split-BF16 tiles need N * Kp <= 8192)
+int tile_max(int d, int split) { return split ? (d <= 64 ? 128 : 64) : 256; }
+int tile_default(int64_t k, int d, int split) {
+    return std::min(tile_max(d, split), k <= 64 ? 64 : (k <= 128 ? 128 : 256));
+}
+// tuning-cache key: (padded d, seed-count class) under one precision setting
+int class_key(int precision, int d, int64_t k) {
+    return ((precision + 2) << 16) | ((d <= 64 ? 64 : 128) << 8) | k_class(k);
+}
 
 }  // namespace
 
@@ -125,7 +133,7 @@ struct geek_batch {
     std::vector<int64_t> a_k;        // seed counts the phase was built for
     int32_t *a_labels = nullptr;     // labels pointer it was captured with
     TcPlan tc;
-    std::vector<int> tile;
+    std::vector<int> tile, split;    // per instance: centre-tile width, split-BF16 mode
     int64_t ktot = 0, ids_cap = 0, kd_tot = 0;
     int64_t *s_off = nullptr;        // seeds copied into plan-owned buffers
     int32_t *s_ids = nullptr;
@@ -144,6 +152,7 @@ struct geek_batch {
     float *part_max = nullptr;
     int32_t *flag_rows = nullptr;
     unsigned long long *n_flag = nullptr;
+    DecideBufs dec;                  // grouping and FP32 / FP64 decision of flagged rows
     cudaGraphExec_t g_assign = nullptr;
     int g_assign_kernels = 0;
     std::vector<int64_t> cen_off;    // count + 1 (doubles)
@@ -175,6 +184,7 @@ struct geek_batch {
         dfree(part_max);
         dfree(sse_d);
         dfree(rmax_d);
+        decide_bufs_free(dec);
         a_ready = false;
     }
     ~geek_batch() {
@@ -220,6 +230,8 @@ geek_status batch_create(geek_ctx *ctx, const geek_instance *inst, int count, co
     if (p->Ks < 1 || p->Ks > 4 || p->Ls < 1 || p->delta < 1) return set_error(ctx, GEEK_ERR_INVALID, "bad SILK parameters");
     if (p->tile_n != 0 && p->tile_n != 64 && p->tile_n != 128 && p->tile_n != 256)
         return set_error(ctx, GEEK_ERR_INVALID, "tile_n must be 0, 64, 128 or 256");
+    if (p->precision != GEEK_PREC_AUTO && p->precision != GEEK_PREC_BF16 && p->precision != GEEK_PREC_BF16X3)
+        return set_error(ctx, GEEK_ERR_INVALID, "batch precision must be GEEK_PREC_AUTO, BF16 or BF16X3");
     b->ctx = ctx;
     b->count = count;
     b->p = *p;
@@ -275,6 +287,7 @@ geek_status batch_create(geek_ctx *ctx, const geek_instance *inst, int count, co
     b->sse.assign(count, 0.0);
     b->rmax.assign(count, 0.0);
     b->tile.assign(count, 256);
+    b->split.assign(count, 0);
     return GEEK_OK;
 }
 
@@ -492,13 +505,18 @@ geek_status build_assign(geek_batch *b, int32_t *labels, cudaStream_t st) {
         si[i] = SInst{I.x, I.ldx, I.n, I.d, b->chi + b->cen_off[i], b->clo + b->cen_off[i], b->k[i], labels + r0};
         for (int64_t r = 0; r < ceil_div(I.n, 128); r++) su.push_back(make_int2(i, (int)r));
         suoff[i + 1] = (int64_t)su.size();
-        int N = b->p.tile_n ? b->p.tile_n : tile_default(b->k[i]);
-        if (!b->p.tile_n) {
-            auto it = ctx->tile_cache.find(((I.d <= 64 ? 64 : 128) << 8) | k_class(b->k[i]));
-            if (it != ctx->tile_cache.end()) N = it->second;
+        // mode and tile: forced, tuned earlier on this context, or defaults
+        int split = b->p.precision == GEEK_PREC_BF16X3 || b->p.precision == GEEK_PREC_AUTO;
+        int N = tile_default(b->k[i], I.d, split);
+        auto it = ctx->tile_cache.find(class_key(b->p.precision, I.d, b->k[i]));
+        if (it != ctx->tile_cache.end() && !b->p.tile_n) {
+            N = it->second & 0xFFFF;
+            split = it->second >> 16;
         }
+        if (b->p.tile_n) N = std::min(b->p.tile_n, tile_max(I.d, split));
         b->tile[i] = N;
-        tp[i] = TcPlanInst{I.x, I.ldx, I.n, I.d, c, b->k[i], labels + r0, r0, N};
+        b->split[i] = split;
+        tp[i] = TcPlanInst{I.x, I.ldx, I.n, I.d, c, b->k[i], labels + r0, r0, N, split};
     }
     b->n_st_units = (int64_t)su.size();
     GK_TRY(dalloc(ctx, &b->st_units, std::max<int64_t>(b->n_st_units, 1)));
@@ -511,7 +529,9 @@ geek_status build_assign(geek_batch *b, int32_t *labels, cudaStream_t st) {
     GK_CUDA(ctx, cudaMemcpy(b->sinst, si.data(), sizeof(SInst) * count, cudaMemcpyHostToDevice));
     GK_CUDA(ctx, cudaMemcpy(b->st_uoff, suoff.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice));
     if (!su.empty()) GK_CUDA(ctx, cudaMemcpy(b->st_units, su.data(), sizeof(int2) * su.size(), cudaMemcpyHostToDevice));
+    b->tc.allow_split = b->p.precision == GEEK_PREC_AUTO;
     GK_TRY(tc_plan_build(ctx, nullptr, tp, &b->tc, st));
+    GK_TRY(decide_bufs_alloc(ctx, nullptr, count, b->N, b->dec));
     GK_CUDA(ctx, cudaStreamSynchronize(st));
     b->a_k = b->k;
     b->a_labels = labels;
@@ -536,54 +556,100 @@ geek_status enqueue_assign(geek_batch *b, int32_t *labels, cudaStream_t s) {
     GK_TRY(fill_labels(ctx, labels, b->N, -1, s));
     GK_TRY(enqueue_centres(b, s));
     GK_TRY(tc_plan_launch(ctx, b->tc, b->flag_rows, b->n_flag, s));
-    GK_TRY(recheck_batch(ctx, b->rinst, b->hb.row_off, b->count, b->dmax, b->flag_rows, b->n_flag, s));
+    GK_TRY(decide_flags(ctx, b->rinst, b->hb.row_off, b->count, b->dmax, b->flag_rows, b->n_flag, b->dec, s));
     GK_TRY(centre_split(ctx, b->c64, b->kd_tot, b->chi, b->clo, s));
     GK_TRY(stats_batch(ctx, b->sinst, b->st_units, b->n_st_units, b->st_uoff, b->count, b->part_sum, b->part_max,
                        b->sse_d, b->rmax_d, s));
     return GEEK_OK;
 }
 
-// Times the candidate tile widths for every (padded d, seed class) of the
-// batch that the context has not tuned yet; records the fastest.
+// Chooses, for every (padded d, seed-count class) of the batch that the
+// context has not tuned yet, the assignment mode (BF16 or split-BF16) and the
+// centre-tile width by timing each candidate on that class's own instances:
+// the tcgen05 pass plus the FP64 decision of the rows it leaves uncertain
+// (a wide BF16 window trades tensor work for rechecks).  The choice is
+// recorded on the context.
 geek_status autotune(geek_batch *b, cudaStream_t st) {
     geek_ctx *ctx = b->ctx;
     std::map<int, std::vector<int>> classes;
     for (int i = 0; i < b->count; i++) {
         if (b->inst[i].n == 0 || b->k[i] == 0) continue;
-        const int key = ((b->inst[i].d <= 64 ? 64 : 128) << 8) | k_class(b->k[i]);
+        const int key = class_key(b->p.precision, b->inst[i].d, b->k[i]);
         if (!ctx->tile_cache.count(key)) classes[key].push_back(i);
     }
     if (classes.empty()) return GEEK_OK;
     EvTimer tk(ctx, "batch.autotune", st);
-    GK_TRY(enqueue_centres(b, st));
+    GK_TRY(enqueue_centres(b, st));  // centroids, centre preparation and conversions
+    std::vector<int> modes;
+    if (b->p.precision != GEEK_PREC_BF16X3) modes.push_back(0);
+    if (b->p.precision != GEEK_PREC_BF16) modes.push_back(1);
     const int *cand;
     const int nc = tc_tile_candidates(&cand);
-    std::vector<int> tiles = b->tile;
-    for (auto &c : classes) {
-        // at most ~8 units per SM of this class's instances
-        std::vector<int> which;
-        int64_t units = 0;
-        for (int i : c.second) {
-            if (units > (int64_t)ctx->num_sms * 8) break;
-            which.push_back(i);
-            units += ceil_div(b->inst[i].n, 128);
-        }
-        int best = tiles[c.second[0]];
-        float best_ms = 1e30f;
-        for (int q = 0; q < nc; q++) {
-            float ms = 0.f;
-            GK_TRY(tc_plan_time(ctx, &b->tc, which, cand[q], b->flag_rows, b->n_flag, 2, &ms, st));
-            if (ms < best_ms) {
-                best_ms = ms;
-                best = cand[q];
+    std::map<int, std::pair<float, int>> best;  // class -> (ms, N | split << 16)
+    cudaEvent_t e0, e1;
+    GK_CUDA(ctx, cudaEventCreate(&e0));
+    GK_CUDA(ctx, cudaEventCreate(&e1));
+    geek_status rc = GEEK_OK;
+    std::vector<int> N = b->tile, split = b->split;
+    for (int mode : modes) {
+        for (auto &c : classes)
+            for (int i : c.second) {
+                split[i] = mode;
+                N[i] = tile_default(b->k[i], b->inst[i].d, mode);
+            }
+        rc = tc_plan_set_modes(ctx, &b->tc, N, split, st);
+        if (rc == GEEK_OK) rc = tc_plan_convert(ctx, b->tc, st);
+        for (auto c = classes.begin(); c != classes.end() && rc == GEEK_OK; ++c) {
+            // at most ~8 units per SM of this class's instances
+            std::vector<int> which;
+            int64_t units = 0;
+            for (int i : c->second) {
+                if (units > (int64_t)ctx->num_sms * 8) break;
+                which.push_back(i);
+                units += ceil_div(b->inst[i].n, 128);
+            }
+            const int dcls = b->inst[c->second[0]].d;
+            for (int q = 0; q < nc && rc == GEEK_OK; q++) {
+                if (cand[q] > tile_max(dcls, mode) || (b->p.tile_n && cand[q] != std::min(b->p.tile_n, tile_max(dcls, mode))))
+                    continue;
+                for (int i : c->second) N[i] = cand[q];
+                rc = tc_plan_set_modes(ctx, &b->tc, N, split, st);
+                float ms = 1e30f;
+                for (int rep = 0; rep < 2 && rc == GEEK_OK; rep++) {
+                    cudaMemsetAsync(b->n_flag, 0, sizeof(unsigned long long), st);
+                    cudaEventRecord(e0, st);
+                    rc = tc_plan_launch_subset(ctx, &b->tc, which, b->flag_rows, b->n_flag, st);
+                    if (rc == GEEK_OK)
+                        rc = decide_flags(ctx, b->rinst, b->hb.row_off, b->count, b->dmax, b->flag_rows, b->n_flag,
+                                          b->dec, st);
+                    cudaEventRecord(e1, st);
+                    if (cudaEventSynchronize(e1) != cudaSuccess && rc == GEEK_OK)
+                        rc = set_error(ctx, GEEK_ERR_CUDA, "autotune run failed: %s", cudaGetErrorString(cudaGetLastError()));
+                    float t = 0.f;
+                    cudaEventElapsedTime(&t, e0, e1);
+                    ms = std::min(ms, t);
+                }
+                if (rc == GEEK_OK) rc = tc_plan_check(ctx, b->tc, st);
+                auto &bb = best[c->first];
+                if (rc == GEEK_OK && (bb.second == 0 || ms < bb.first)) bb = {ms, cand[q] | (mode << 16)};
             }
         }
-        ctx->tile_cache[c.first] = best;
-        for (int i : c.second) tiles[i] = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    GK_TRY(rc);
+    for (auto &c : classes) {
+        const int v = best[c.first].second;
+        ctx->tile_cache[c.first] = v;
+        for (int i : c.second) {
+            N[i] = v & 0xFFFF;
+            split[i] = v >> 16;
+        }
         b->tuned++;
     }
-    b->tile = tiles;
-    GK_TRY(tc_plan_set_tiles(ctx, &b->tc, tiles, st));
+    b->tile = N;
+    b->split = split;
+    GK_TRY(tc_plan_set_modes(ctx, &b->tc, N, split, st));
     GK_CUDA(ctx, cudaStreamSynchronize(st));
     return GEEK_OK;
 }
@@ -597,7 +663,7 @@ geek_status run_assign(geek_batch *b, int32_t *labels, cudaStream_t st) {
     GK_CUDA(ctx, cudaMemcpyAsync(b->s_off, b->seeds.off, sizeof(int64_t) * (b->ktot + 1), cudaMemcpyDeviceToDevice, st));
     if (b->seeds.n_ids)
         GK_CUDA(ctx, cudaMemcpyAsync(b->s_ids, b->seeds.ids, sizeof(int32_t) * b->seeds.n_ids, cudaMemcpyDeviceToDevice, st));
-    if (rebuild && !b->p.tile_n) GK_TRY(autotune(b, st));
+    if (rebuild && (!b->p.tile_n || b->p.precision == GEEK_PREC_AUTO)) GK_TRY(autotune(b, st));
     if (!b->g_assign)
         GK_TRY(capture(b, &b->g_assign, &b->g_assign_kernels, [&](cudaStream_t s) { return enqueue_assign(b, labels, s); }));
     {
@@ -683,13 +749,14 @@ geek_status geek_batch_info_get(const geek_batch *b, geek_batch_info *info) {
 }
 
 geek_status geek_batch_instance_stats(const geek_batch *b, int64_t *k, double *sse, double *radius_max,
-                                      int32_t *tile_n) {
+                                      int32_t *tile_n, int32_t *precision) {
     if (!b) return GEEK_ERR_INVALID;
     for (int i = 0; i < b->count; i++) {
         if (k) k[i] = b->k[i];
         if (sse) sse[i] = b->sse[i];
         if (radius_max) radius_max[i] = b->rmax[i];
         if (tile_n) tile_n[i] = b->tile[i];
+        if (precision) precision[i] = b->split[i] ? GEEK_PREC_BF16X3 : GEEK_PREC_BF16;
     }
     return GEEK_OK;
 }

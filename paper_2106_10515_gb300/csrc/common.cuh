@@ -26,8 +26,8 @@ struct geek_ctx {
         double work = 0.0;  // algorithmic bytes or flops of the bracketed work
     };
     std::map<std::string, Timed> times;
-    // centre-tile width chosen by the batch autotuner per (padded d << 8 |
-    // seed-count class)
+    // (centre-tile width | split-BF16 << 16) chosen by the batch autotuner per
+    // (precision setting, padded d, seed-count class)
     std::map<int, int> tile_cache;
 };
 

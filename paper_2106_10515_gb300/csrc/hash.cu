@@ -26,8 +26,36 @@ constexpr int PJ_RPT = 8;       // rows per thread
 constexpr int PJ_MAXT = 256;    // threads per block (upper bound)
 
 
-// One block: rows [tile * TR, tile * TR + TR) of instance A.
-__device__ __forceinline__ void project_block(const ProjArgs &A, int64_t tile) {
+// One block: rows [tile * TR, tile * TR + TR) of one instance.  BATCH = false:
+// A describes the only instance (read from the parameter space, which the
+// inner loops use as operands directly).  BATCH = true: block b belongs to
+// instance i with tile_off[i] <= b < tile_off[i + 1], whose pointers and
+// sizes P[i] replace A's; the thread layout (F, FPAD, FG, RG) and the flag
+// list are common to the batch and stay A's.
+template <bool BATCH>
+__global__ void __launch_bounds__(PJ_MAXT) k_project_fp32(ProjArgs A, const ProjArgs *__restrict__ P,
+                                                          const int64_t *__restrict__ tile_off, int count) {
+    int64_t tile = blockIdx.x;
+    if (BATCH) {
+        __shared__ int s_i;
+        if (threadIdx.x == 0) s_i = find_inst(tile_off, count, blockIdx.x);
+        __syncthreads();
+        const ProjArgs &Q = P[s_i];
+        tile = (int64_t)blockIdx.x - tile_off[s_i];
+        A.x = Q.x;
+        A.ldx = Q.ldx;
+        A.n = Q.n;
+        A.d = Q.d;
+        A.a = Q.a;
+        A.b = Q.b;
+        A.anorm = Q.anorm;
+        A.w = Q.w;
+        A.inv_w = Q.inv_w;
+        A.codes = Q.codes;
+        A.fmin = Q.fmin;
+        A.fmax = Q.fmax;
+        A.row_base = Q.row_base;
+    }
     extern __shared__ float sm[];
     const int TR = A.RG * PJ_RPT;
     float *xs = sm;                       // [PJ_KC][TR]
@@ -194,24 +222,6 @@ __device__ __forceinline__ void project_block(const ProjArgs &A, int64_t tile) {
     }
 }
 
-__global__ void __launch_bounds__(PJ_MAXT) k_project_fp32(const __grid_constant__ ProjArgs A) {
-    project_block(A, blockIdx.x);
-}
-
-// Batched form: the blocks of all instances in one launch; block b works on
-// instance i with tile_off[i] <= b < tile_off[i + 1].
-__global__ void __launch_bounds__(PJ_MAXT) k_project_fp32_batch(const ProjArgs *__restrict__ P,
-                                                                const int64_t *__restrict__ tile_off, int count) {
-    __shared__ ProjArgs sA;
-    __shared__ int64_t s_tile;
-    if (threadIdx.x == 0) {
-        const int i = find_inst(tile_off, count, blockIdx.x);
-        sA = P[i];
-        s_tile = (int64_t)blockIdx.x - tile_off[i];
-    }
-    __syncthreads();
-    project_block(sA, s_tile);
-}
 
 __global__ void k_row_norms(const float *__restrict__ a, int F, int d, float *__restrict__ out) {
     int f = blockIdx.x * blockDim.x + threadIdx.x;
@@ -600,7 +610,7 @@ geek_status project_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t l
     const int threads = proj_threads(A);
     const size_t smem = proj_smem(A);
     if (smem > 200 * 1024) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "projection tile too large");
-    GK_CUDA(ctx, cudaFuncSetAttribute(k_project_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GK_CUDA(ctx, cudaFuncSetAttribute(k_project_fp32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     unsigned long long *cnt;
     GK_TRY(scr.alloc(&cnt, 1));
     int *status;
@@ -624,7 +634,7 @@ geek_status project_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t l
             EvTimer tk(ctx, "kernel.project_fp32", st);
             tk.work = 2.0 * (double)n * (double)F * (double)d;
             GK_COUNT();
-            k_project_fp32<<<(unsigned)blocks, threads, smem, st>>>(A);
+            k_project_fp32<false><<<(unsigned)blocks, threads, smem, st>>>(A, nullptr, nullptr, 1);
             GK_LAUNCH(ctx);
         }
         unsigned long long h_cnt = 0;
@@ -693,7 +703,7 @@ geek_status proj_batch_setup(geek_ctx *ctx, std::vector<ProjArgs> &P, const std:
     if (B.total_tiles > 0x7FFFFFFFLL) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "batch too large for one launch");
     const size_t smem = proj_smem(P[0]);
     if (smem > 200 * 1024) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "projection tile too large");
-    GK_CUDA(ctx, cudaFuncSetAttribute(k_project_fp32_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GK_CUDA(ctx, cudaFuncSetAttribute(k_project_fp32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     GK_CUDA(ctx, cudaMemcpy(B.P, P.data(), sizeof(ProjArgs) * count, cudaMemcpyHostToDevice));
     GK_CUDA(ctx, cudaMemcpy(B.tile_off, toff.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice));
     return GEEK_OK;
@@ -714,7 +724,8 @@ geek_status proj_batch_enqueue(geek_ctx *ctx, const ProjArgs &P0, int count, int
     GK_LAUNCH(ctx);
     if (B.total_tiles > 0) {
         GK_COUNT();
-        k_project_fp32_batch<<<(unsigned)B.total_tiles, proj_threads(P0), proj_smem(P0), st>>>(B.P, B.tile_off, count);
+        k_project_fp32<true><<<(unsigned)B.total_tiles, proj_threads(P0), proj_smem(P0), st>>>(P0, B.P, B.tile_off,
+                                                                                              count);
         GK_COUNT();
         k_recheck_dot2<<<ctx->num_sms * 4, 256, 0, st>>>(B.P, B.row_off, count, srp, F, B.flags, B.cnt, B.cap,
                                                         B.flags2, B.cnt2);

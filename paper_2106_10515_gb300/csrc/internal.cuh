@@ -134,6 +134,7 @@ struct TcPlanInst {
     int32_t *labels;
     int64_t row_base;
     int N;
+    int split;  // 1: split-BF16 (three products, narrow window); needs N * Kp <= 8192
 };
 struct TcInst;
 struct TcXPrep;
@@ -145,7 +146,10 @@ struct TcPlan {
     Impl *impl = nullptr;
     std::vector<TcPlanInst> desc;
     int count = 0;
-    int64_t N_total = 0, kpad_total = 0, nunits = 0;
+    int64_t N_total = 0, kpad_total = 0, nunits = 0, nunits_x3 = 0;
+    bool allow_split = false;    // buffers sized for the split layout of every instance
+    int2 *tune_units = nullptr;  // scratch unit list of tc_plan_launch_subset
+    int64_t tune_cap = 0;
     TcInst *inst = nullptr;
     TcXPrep *xprep = nullptr;
     TcCPrep *cprep = nullptr;
@@ -166,14 +170,16 @@ geek_status tc_plan_launch(geek_ctx *ctx, const TcPlan &P, int32_t *flag_rows, u
                            cudaStream_t st);
 geek_status tc_plan_enqueue(geek_ctx *ctx, const TcPlan &P, int32_t *flag_rows, unsigned long long *n_flag,
                             cudaStream_t st);
-geek_status tc_plan_set_tiles(geek_ctx *ctx, TcPlan *P, const std::vector<int> &N, cudaStream_t st);
-geek_status tc_plan_time(geek_ctx *ctx, TcPlan *P, const std::vector<int> &which, int N, int32_t *flag_rows,
-                         unsigned long long *n_flag, int reps, float *ms_out, cudaStream_t st);
+geek_status tc_plan_upload(geek_ctx *ctx, TcPlan *P, cudaStream_t st);
+geek_status tc_plan_set_modes(geek_ctx *ctx, TcPlan *P, const std::vector<int> &N, const std::vector<int> &split,
+                              cudaStream_t st);
+geek_status tc_plan_launch_subset(geek_ctx *ctx, TcPlan *P, const std::vector<int> &which, int32_t *flag_rows,
+                                  unsigned long long *n_flag, cudaStream_t st);
 geek_status tc_plan_check(geek_ctx *ctx, const TcPlan &P, cudaStream_t st);
 void tc_plan_free(TcPlan *P);
 int tc_tile_candidates(const int **tiles);
 geek_status assign_tc_bf16(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ldx, int64_t n, int d,
-                           const double *centres, int64_t k, int32_t *labels, int32_t *flag_rows,
+                           const double *centres, int64_t k, int split, int32_t *labels, int32_t *flag_rows,
                            unsigned long long *n_flag, cudaStream_t st);
 
 // assign.cu
@@ -222,12 +228,28 @@ geek_status centroids_batch(geek_ctx *ctx, const CenInst *C, const int64_t *seed
                             int dmax, const int64_t *soff, const int32_t *sids, cudaStream_t st);
 geek_status centre_prep_batch(geek_ctx *ctx, const CInst *C, const int64_t *k_off, int count, int64_t ktot,
                               cudaStream_t st);
-geek_status recheck_batch(geek_ctx *ctx, const RInst *R, const int64_t *row_off, int count, int dmax,
-                          const int32_t *flag_rows, const unsigned long long *n_flag, cudaStream_t st);
 geek_status centre_split(geek_ctx *ctx, const double *c64, int64_t total, float *chi, float *clo, cudaStream_t st);
 geek_status stats_batch(geek_ctx *ctx, const SInst *S, const int2 *units, int64_t nunits, const int64_t *unit_off,
                         int count, double *part_sum, float *part_max, double *sse, double *rmax, cudaStream_t st);
 geek_status fill_labels(geek_ctx *ctx, int32_t *labels, int64_t n, int32_t v, cudaStream_t st);
+// Buffers of decide_flags (scratch-owned when allocated from a Scratch).
+struct DecideBufs {
+    int *cnt = nullptr;            // count: flagged rows per instance
+    int64_t *cursor = nullptr;     // count
+    int *unit_inst = nullptr;      // units of up to 128 flagged rows
+    int64_t *unit_start = nullptr;
+    int *unit_cnt = nullptr;
+    int *n_units = nullptr;
+    int32_t *grows = nullptr;      // flagged rows grouped by instance
+    int32_t *flags2 = nullptr;     // rows left to the FP64 reference
+    unsigned long long *n_flag2 = nullptr;
+    std::vector<void *> owned;
+};
+geek_status decide_bufs_alloc(geek_ctx *ctx, Scratch *scr, int count, int64_t n_total, DecideBufs &B);
+void decide_bufs_free(DecideBufs &B);
+geek_status decide_flags(geek_ctx *ctx, const RInst *R, const int64_t *row_off, int count, int dmax,
+                         const int32_t *flags, const unsigned long long *n_flag, const DecideBufs &B,
+                         cudaStream_t st);
 geek_status assign_dense_centres(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ldx,
                                  int64_t n, int d, const double *centres, int64_t k, int precision,
                                  int32_t *labels, geek_assign_stats *stats, cudaStream_t st);

@@ -46,13 +46,15 @@ struct TcXPrep {
     const float *x;
     int64_t ldx;
     int d, Kp;
-    __nv_bfloat16 *xb;  // n x Kp
+    int split;          // 1: rows hold [bf16(x) | bf16(x - bf16(x))]
+    __nv_bfloat16 *xb;  // n x Kp (x 2 when split)
 };
 struct TcCPrep {
     const double *c;    // k x d
     int64_t k, kpad;
     int d, Kp;
-    __nv_bfloat16 *cb;  // kpad x Kp
+    int split;
+    __nv_bfloat16 *cb;  // kpad x Kp (x 2 when split)
     float *cn;          // kpad
     unsigned *cmax_bits;
 };
@@ -64,13 +66,16 @@ constexpr int TC_N = 256;
 constexpr int TC_KB = 64;  // bf16 elements per 128-byte swizzle row
 constexpr int TC_EPI_WARPS = 8;                   // 2 per TMEM lane quarter
 constexpr int TC_EPI_GROUPS = TC_EPI_WARPS / 4;     // column groups per tile
-constexpr int TC_EPI_COLS = TC_N / TC_EPI_GROUPS;   // columns per warp
-constexpr int TC_EPI_CH = TC_EPI_COLS / 32;         // 32-column chunks per warp
 constexpr int TC_MISC = 2048;                       // barriers, TMEM slot, merge buffer
 constexpr int TC_THREADS = 32 * (2 + TC_EPI_WARPS);
 constexpr int TC_KP_MAX = 128;                      // d <= 128
 constexpr int TC_A_STAGE = TC_M * TC_KP_MAX * 2;    // bytes of one X tile stage
 constexpr int TC_B_STAGE = TC_N * TC_KP_MAX * 2;    // bytes of one centre tile stage
+// split-BF16 mode: tiles hold [hi | lo] (2 Kp columns); the same 192 KB is
+// cut into larger X stages and smaller centre stages (N * Kp <= 8192)
+constexpr int TC_A_STAGE_X3 = 2 * TC_A_STAGE;
+constexpr int TC_B_STAGE_X3 = TC_B_STAGE / 2;
+static_assert(TC_A_STAGE_X3 + TC_B_STAGE_X3 == TC_A_STAGE + TC_B_STAGE, "both modes share one layout size");
 constexpr uint32_t TC_TMEM_COLS = 512;
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s per wait
 
@@ -183,18 +188,6 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
 // d = -2 a + c on two lanes at once (fma.rn.f32x2: the same per-lane
 // rounding as fmaf(-2.f, a, c))
 __device__ __forceinline__ void ffma2_m2(float a0, float a1, float c0, float c1, float &d0, float &d1) {
@@ -231,10 +224,108 @@ __device__ __forceinline__ float window_bf16(float xn, float cmax, int d) {
     return 1.01f * (e + e64) + 1e-30f;
 }
 
+// Rigorous half-window of the split-BF16 path.  With x_h = bf16(x), x_l =
+// bf16(x - x_h) (and the same for c), x.c - (x_h.c_h + x_l.c_h + x_h.c_l) =
+// -(x - x_h - x_l).c_h - x_h.(c - c_h - c_l) + (x - x_h).(c - c_h), each
+// term bounded by u_b^2 (1 + u_b) |x| |c|: input term 2 * 3 u_b^2 (1 + u_b)
+// |x| cmax; the tensor core's accumulation over 3d products
+// 2 (3d + 16) 2^-21 (1 + 4 u_b) |x| cmax; the |c|^2, FMA and FP64 reference
+// terms as in window_bf16; times 1.01.
+__device__ __forceinline__ float window_bf16x3(float xn, float cmax, int d) {
+    const float ub = 0.00390625f, u = 5.9604645e-8f;
+    const float xc = xn * cmax;
+    const float e = 6.f * ub * ub * (1.f + ub) * xc +
+                    2.f * (float)(3 * d + 16) * 4.76837158e-7f * (1.f + 4.f * ub) * xc + u * cmax * cmax +
+                    u * (2.f * xc * (1.f + 2.f * ub) + cmax * cmax);
+    const float s = xn + cmax;
+    const float e64 = (float)(d + 3) * 1.1102230e-16f * s * s;
+    return 1.01f * (e + e64) + 1e-30f;
+}
+
+// Running minimum of one warp's rows over NCH 32-column chunks of one
+// accumulator tile (columns jb .. jb + 32 NCH - 1); the TMEM load of chunk
+// ch + 1 is in flight while chunk ch is reduced.  Per row:
+//   b1     the smallest value so far, found in the chunk saved in sv / sj
+//   b2o    the smallest value outside that chunk
+// A chunk with a new minimum is copied to sv (its index and second-smallest
+// value are resolved once per row tile, see epi_resolve); any other chunk
+// only lowers b2o.  So min(b2o, second smallest of sv) is exactly the
+// runner-up over all columns.
+template <int NCH>
+__device__ __forceinline__ void epi_tile(uint32_t tbase, const float *cnt, int64_t jb, float &b1, float &b2o,
+                                         float (&sv)[32], int64_t &sj) {
+    uint32_t ra[32], rb[32];
+    tmem_ld32_async(tbase, ra);
+    tmem_wait_ld();
+#pragma unroll
+    for (int ch = 0; ch < NCH; ch++) {
+        if (ch + 1 < NCH) {
+            if (ch & 1) tmem_ld32_async(tbase + (ch + 1) * 32, ra);
+            else tmem_ld32_async(tbase + (ch + 1) * 32, rb);
+        }
+        const uint32_t *r = (ch & 1) ? rb : ra;
+        const float4 *cn4 = reinterpret_cast<const float4 *>(cnt + ch * 32);
+        float v[32];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const float4 cc = cn4[i];
+            ffma2_m2(__uint_as_float(r[4 * i + 0]), __uint_as_float(r[4 * i + 1]), cc.x, cc.y, v[4 * i + 0],
+                     v[4 * i + 1]);
+            ffma2_m2(__uint_as_float(r[4 * i + 2]), __uint_as_float(r[4 * i + 3]), cc.z, cc.w, v[4 * i + 2],
+                     v[4 * i + 3]);
+        }
+        float t11[11];
+#pragma unroll
+        for (int i = 0; i < 10; i++) t11[i] = min3f(v[3 * i], v[3 * i + 1], v[3 * i + 2]);
+        t11[10] = fminf(v[30], v[31]);
+        const float tm = fminf(min3f(min3f(t11[0], t11[1], t11[2]), min3f(t11[3], t11[4], t11[5]),
+                                     min3f(t11[6], t11[7], t11[8])),
+                               fminf(t11[9], t11[10]));
+        if (tm < b1) {
+            b2o = fminf(b2o, b1);  // the old best chunk is now "outside"
+            b1 = tm;
+#pragma unroll
+            for (int i = 0; i < 32; i++) sv[i] = v[i];
+            sj = jb + ch * 32;
+        } else {
+            b2o = fminf(b2o, tm);
+        }
+        if (ch + 1 < NCH) tmem_wait_ld();
+    }
+}
+
+// Index (first position) of the minimum in the saved chunk and the exact
+// runner-up over all columns.
+__device__ __forceinline__ void epi_resolve(float b1, float b2o, const float (&sv)[32], int64_t sj, float &b2,
+                                            int &i1) {
+    if (sj < 0) {  // no finite value at all
+        b2 = b2o;
+        i1 = 0x7FFFFFFF;
+        return;
+    }
+    int idx = 31;
+#pragma unroll
+    for (int i = 31; i >= 0; i--)
+        if (sv[i] == b1) idx = i;
+    float m2 = FLT_MAX;
+#pragma unroll
+    for (int i = 0; i < 32; i++) m2 = fminf(m2, i == idx ? FLT_MAX : sv[i]);
+    b2 = fminf(b2o, m2);
+    i1 = (int)(sj + idx);
+}
+
+// SPLIT = false: S = x_h . c_h, one BF16 product per element (window_bf16).
+// SPLIT = true: x = x_h + x_l and c = c_h + c_l in BF16 pairs, S = x_h . c_h +
+// x_l . c_h + x_h . c_l: three MMAs per k-step into the same accumulator
+// (window_bf16x3, ~100x narrower).
+template <bool SPLIT>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_constant__ TcArgs A) {
+    constexpr int A_ST = SPLIT ? TC_A_STAGE_X3 : TC_A_STAGE;
+    constexpr int B_ST = SPLIT ? TC_B_STAGE_X3 : TC_B_STAGE;
+    constexpr int KW = SPLIT ? 2 : 1;  // stored column blocks per k-block
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t *sA0 = base, *sB0 = base + 2 * TC_A_STAGE;
+    uint8_t *sA0 = base, *sB0 = base + 2 * A_ST;
     uint64_t *bars = (uint64_t *)(base + 2 * TC_A_STAGE + 2 * TC_B_STAGE);
     uint64_t *full_a = bars, *empty_a = bars + 2, *full_b = bars + 4, *empty_b = bars + 6;
     uint64_t *full_acc = bars + 8, *empty_acc = bars + 10, *done_bar = bars + 12;
@@ -282,14 +373,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
             for (int64_t u = blockIdx.x; u < A.nunits && ok; u += gridDim.x, it++) {
                 const int2 un = A.units ? A.units[u] : make_int2(0, (int)u);
                 const TcInst &I = A.inst[un.x];
-                const int nkb = I.Kp / TC_KB, N = I.N;
-                const uint32_t a_bytes = (uint32_t)TC_M * I.Kp * 2, b_bytes = (uint32_t)N * I.Kp * 2;
+                const int nkb = KW * I.Kp / TC_KB, N = I.N;  // stored k-blocks
+                const uint32_t a_bytes = (uint32_t)TC_M * KW * I.Kp * 2, b_bytes = (uint32_t)N * KW * I.Kp * 2;
                 const int ab = (int)(it & 1);
                 const uint32_t ua = (uint32_t)(it >> 1);
                 if (!(ok = mbar_wait(&empty_a[ab], (ua & 1) ^ 1, A.err))) break;
                 mbar_expect_tx(&full_a[ab], a_bytes);
                 for (int kb = 0; kb < nkb; kb++)
-                    tma_load_2d(su32(sA0 + ab * TC_A_STAGE + kb * TC_M * 128), &I.tmA, kb * TC_KB, un.y * TC_M,
+                    tma_load_2d(su32(sA0 + ab * A_ST + kb * TC_M * 128), &I.tmA, kb * TC_KB, un.y * TC_M,
                                 &full_a[ab]);
                 for (int c = 0; c < I.ntiles_c; c++, ct++) {
                     const int s = (int)(ct & 1);
@@ -297,7 +388,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
                     if (!(ok = mbar_wait(&empty_b[s], (uu & 1) ^ 1, A.err))) break;
                     mbar_expect_tx(&full_b[s], b_bytes);
                     for (int kb = 0; kb < nkb; kb++)
-                        tma_load_2d(su32(sB0 + s * TC_B_STAGE + kb * N * 128), &I.tmB, kb * TC_KB, c * N, &full_b[s]);
+                        tma_load_2d(su32(sB0 + s * B_ST + kb * N * 128), &I.tmB, kb * TC_KB, c * N, &full_b[s]);
                     issued_b[s] = uu + 1;
                     // |c|^2 of this centre tile into ring slot ct % 4.  The
                     // epilogue of tile ct - 4, the last reader of the slot,
@@ -325,25 +416,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
             for (int64_t u = blockIdx.x; u < A.nunits && ok; u += gridDim.x, it++) {
                 const int2 un = A.units ? A.units[u] : make_int2(0, (int)u);
                 const TcInst &I = A.inst[un.x];
-                const int nkb = I.Kp / TC_KB, N = I.N;
+                const int nkb = I.Kp / TC_KB, N = I.N;  // logical k-blocks
                 const uint32_t idesc = idesc_bf16(TC_M, N);
                 const int ab = (int)(it & 1);
                 const uint32_t ua = (uint32_t)(it >> 1);
                 if (!(ok = mbar_wait(&full_a[ab], ua & 1, A.err))) break;
-                const uint32_t a_base = su32(sA0 + ab * TC_A_STAGE);
+                const uint32_t a_base = su32(sA0 + ab * A_ST);
                 for (int c = 0; c < I.ntiles_c; c++, ct++) {
                     const int s = (int)(ct & 1);
                     const uint32_t uu = (uint32_t)(ct >> 1);
                     if (!(ok = mbar_wait(&full_b[s], uu & 1, A.err))) break;
                     if (!(ok = mbar_wait(&empty_acc[s], (uu & 1) ^ 1, A.err))) break;
                     fence_after();
-                    const uint32_t b_base = su32(sB0 + s * TC_B_STAGE);
+                    const uint32_t b_base = su32(sB0 + s * B_ST);
                     const uint32_t dtm = tmem + (uint32_t)(s * TC_N);
                     for (int kb = 0; kb < nkb; kb++)
 #pragma unroll
-                        for (int ks = 0; ks < TC_KB / 16; ks++)
-                            mma_bf16(dtm, sdesc(a_base + kb * TC_M * 128 + ks * 32),
-                                     sdesc(b_base + kb * N * 128 + ks * 32), idesc, (kb | ks) != 0);
+                        for (int ks = 0; ks < TC_KB / 16; ks++) {
+                            const uint32_t ao = kb * TC_M * 128 + ks * 32, bo = kb * N * 128 + ks * 32;
+                            mma_bf16(dtm, sdesc(a_base + ao), sdesc(b_base + bo), idesc, (kb | ks) != 0);
+                            if (SPLIT) {
+                                // x_l . c_h and x_h . c_l: the lo halves sit nkb k-blocks on
+                                mma_bf16(dtm, sdesc(a_base + ao + nkb * TC_M * 128), sdesc(b_base + bo), idesc, 1);
+                                mma_bf16(dtm, sdesc(a_base + ao), sdesc(b_base + bo + nkb * N * 128), idesc, 1);
+                            }
+                        }
                     mma_commit(&empty_b[s]);
                     mma_commit(&full_acc[s]);
                 }
@@ -371,10 +468,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
             const int64_t row = (int64_t)un.y * TC_M + rloc;
             const float xn = row < I.n ? I.xnorm[row] : 0.f;
             const float cmax = sqrtf(__uint_as_float(*I.cmax_bits)) * (1.f + 1e-5f);
-            const float W = 2.f * window_bf16(xn, cmax, I.d);
+            const float W = 2.f * (SPLIT ? window_bf16x3(xn, cmax, I.d) : window_bf16(xn, cmax, I.d));
             const float Wc = W * (1.f + 1e-6f);
-            float b1 = FLT_MAX, b2 = FLT_MAX;
-            int i1 = 0x7FFFFFFF;
+            float b1 = FLT_MAX, b2o = FLT_MAX, sv[32];
+            int64_t sj = -1;
             for (int c = 0; c < I.ntiles_c; c++, ct++) {
                 const int s = (int)(ct & 1);
                 const uint32_t uu = (uint32_t)(ct >> 1);
@@ -387,65 +484,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
                 ok = ok && w_ok;
                 if (ok) {
                     fence_after();
-                    // up to four 32-column chunks; the TMEM load of chunk
-                    // ch + 1 is in flight while chunk ch is reduced
                     const uint32_t tbase = tmem + (uint32_t)(s * TC_N + h * gcols) + ((uint32_t)(32 * q) << 16);
                     const float *cnt = cn_s + cs * TC_N + h * gcols;
-                    uint32_t ra[32], rb[32];
-                    tmem_ld32_async(tbase, ra);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int ch = 0; ch < TC_EPI_CH; ch++) {
-                        if (ch < nch) {
-                            if (ch + 1 < nch) {
-                                if (ch & 1) tmem_ld32_async(tbase + (ch + 1) * 32, ra);
-                                else tmem_ld32_async(tbase + (ch + 1) * 32, rb);
-                            }
-                            const uint32_t *r = (ch & 1) ? rb : ra;
-                            const int64_t j0 = (int64_t)c * N + h * gcols + ch * 32;
-                            const float4 *cn4 = reinterpret_cast<const float4 *>(cnt + ch * 32);
-                            float v[32];
-#pragma unroll
-                            for (int i = 0; i < 8; i++) {
-                                const float4 cc = cn4[i];
-                                ffma2_m2(__uint_as_float(r[4 * i + 0]), __uint_as_float(r[4 * i + 1]), cc.x, cc.y,
-                                         v[4 * i + 0], v[4 * i + 1]);
-                                ffma2_m2(__uint_as_float(r[4 * i + 2]), __uint_as_float(r[4 * i + 3]), cc.z, cc.w,
-                                         v[4 * i + 2], v[4 * i + 3]);
-                            }
-                            float t11[11];
-#pragma unroll
-                            for (int i = 0; i < 10; i++) t11[i] = min3f(v[3 * i], v[3 * i + 1], v[3 * i + 2]);
-                            t11[10] = fminf(v[30], v[31]);
-                            const float tm =
-                                fminf(min3f(min3f(t11[0], t11[1], t11[2]), min3f(t11[3], t11[4], t11[5]),
-                                            min3f(t11[6], t11[7], t11[8])),
-                                      fminf(t11[9], t11[10]));
-                            if (tm < b1) {
-                                // a new best in this chunk: its first position and
-                                // the chunk's second smallest value
-                                int idx = 31;
-#pragma unroll
-                                for (int i = 31; i >= 0; i--)
-                                    if (v[i] == tm) idx = i;
-                                float m2 = FLT_MAX;
-#pragma unroll
-                                for (int i = 0; i < 32; i++) m2 = fminf(m2, i == idx ? FLT_MAX : v[i]);
-                                b2 = fminf(b1, m2);
-                                b1 = tm;
-                                i1 = (int)(j0 + idx);
-                            } else {
-                                // the best is unchanged; only the runner-up can move
-                                b2 = fminf(b2, tm);
-                            }
-                            if (ch + 1 < nch) tmem_wait_ld();
-                        }
-                    }
+                    const int64_t jb = (int64_t)c * N + h * gcols;
+                    if (nch == 4) epi_tile<4>(tbase, cnt, jb, b1, b2o, sv, sj);
+                    else if (nch == 2) epi_tile<2>(tbase, cnt, jb, b1, b2o, sv, sj);
+                    else epi_tile<1>(tbase, cnt, jb, b1, b2o, sv, sj);
                     fence_before();
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty_acc[s]);
             }
+            float b2;
+            int i1;
+            epi_resolve(b1, b2o, sv, sj, b2, i1);
             // merge the column groups of each row
             asm volatile("bar.sync 1, %0;" ::"r"(32 * TC_EPI_WARPS) : "memory");
             if (h > 0) {
@@ -503,10 +555,13 @@ __global__ void k_x_to_bf16(const TcXPrep *__restrict__ X, const int64_t *__rest
         const int ii = find_inst(row_off, count, r);
         const TcXPrep &P = X[ii];
         const int64_t i = r - row_off[ii];
+        const int W = P.split ? 2 * P.Kp : P.Kp;
         float s = 0.f;
         for (int t = lane; t < P.Kp; t += 32) {
             const float v = t < P.d ? P.x[i * P.ldx + t] : 0.f;
-            P.xb[i * P.Kp + t] = __float2bfloat16_rn(v);
+            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+            P.xb[i * W + t] = h;
+            if (P.split) P.xb[i * W + P.Kp + t] = __float2bfloat16_rn(v - __bfloat162float(h));  // v - h exact
             s = fmaf(v, v, s);
         }
 #pragma unroll
@@ -525,10 +580,13 @@ __global__ void k_c_to_bf16(const TcCPrep *__restrict__ C, const int64_t *__rest
         const int ii = find_inst(kpad_off, count, e);
         const TcCPrep &P = C[ii];
         const int64_t j = e - kpad_off[ii];
+        const int W = P.split ? 2 * P.Kp : P.Kp;
         double s = 0.0;
         for (int t = 0; t < P.Kp; t++) {
             const double v = (j < P.k && t < P.d) ? P.c[j * P.d + t] : 0.0;
-            P.cb[j * P.Kp + t] = __double2bfloat16(v);
+            const __nv_bfloat16 h = __double2bfloat16(v);
+            P.cb[j * W + t] = h;
+            if (P.split) P.cb[j * W + P.Kp + t] = __double2bfloat16(v - (double)__bfloat162float(h));  // exact
             s += v * v;
         }
         const float f = (float)s;
@@ -600,8 +658,11 @@ geek_status make_inst(geek_ctx *ctx, const TcPlan &P, int i, int N, TcInst *out)
     memset(&T, 0, sizeof T);
     const TcXPrep &xp = P.impl->xp[i];
     const TcCPrep &cp = P.impl->cp[i];
-    if (I.n > 0) GK_TRY(encode_bf16_2d(ctx, &T.tmA, xp.xb, Kp, I.n, TC_KB, TC_M));
-    if (I.k > 0) GK_TRY(encode_bf16_2d(ctx, &T.tmB, cp.cb, Kp, cp.kpad, TC_KB, N));
+    const int Kst = I.split ? 2 * Kp : Kp;  // stored columns
+    if (I.split && N * Kp > 8192)
+        return set_error(ctx, GEEK_ERR_INVALID, "split-BF16 tiles need N * Kp <= 8192 (N %d, Kp %d)", N, Kp);
+    if (I.n > 0) GK_TRY(encode_bf16_2d(ctx, &T.tmA, xp.xb, Kst, I.n, TC_KB, TC_M));
+    if (I.k > 0) GK_TRY(encode_bf16_2d(ctx, &T.tmB, cp.cb, Kst, cp.kpad, TC_KB, N));
     T.cn = cp.cn;
     T.xnorm = P.xnorm + I.row_base;
     T.cmax_bits = cp.cmax_bits;
@@ -617,13 +678,14 @@ geek_status make_inst(geek_ctx *ctx, const TcPlan &P, int i, int N, TcInst *out)
     return GEEK_OK;
 }
 
-// units of the listed instances, longest first (LPT order over the CTAs)
-void make_units(const TcPlan &P, const std::vector<int> &which, std::vector<int2> &units) {
+// units of the listed instances in one mode (split or not), longest first
+// (LPT order over the CTAs)
+void make_units(const TcPlan &P, const std::vector<int> &which, int split, std::vector<int2> &units) {
     std::vector<std::pair<int64_t, int>> cost;
     for (int i : which) {
         const TcInst &T = P.impl->inst[i];
-        if (T.n <= 0 || T.k <= 0) continue;
-        cost.push_back({(int64_t)T.ntiles_c * T.N * T.Kp + 2048, i});
+        if (T.n <= 0 || T.k <= 0 || P.desc[i].split != split) continue;
+        cost.push_back({(int64_t)T.ntiles_c * T.N * T.Kp * (split ? 3 : 1) + 2048, i});
     }
     std::stable_sort(cost.begin(), cost.end(), [](const std::pair<int64_t, int> &a, const std::pair<int64_t, int> &b) {
         return a.first > b.first;
@@ -664,11 +726,13 @@ geek_status tc_plan_build(geek_ctx *ctx, Scratch *scr, const std::vector<TcPlanI
             return set_error(ctx, GEEK_ERR_UNSUPPORTED, "BF16 tensor-core assignment supports 1 <= d <= 128");
         if (I.N != 64 && I.N != 128 && I.N != 256) return set_error(ctx, GEEK_ERR_INVALID, "tile N must be 64/128/256");
         const int Kp = I.d <= 64 ? 64 : 128;
+        // room for the split layout whenever a plan may switch modes
+        const int Kst = (I.split || P->allow_split) ? 2 * Kp : Kp;
         row_off[i + 1] = row_off[i] + I.n;
         // padding to a multiple of 256 serves every tile width
         im.kpad_off[i + 1] = im.kpad_off[i] + ceil_div(I.k, TC_N) * TC_N;
-        xb_total += I.n * Kp;
-        cb_total += ceil_div(I.k, TC_N) * TC_N * Kp;
+        xb_total += I.n * Kst;
+        cb_total += ceil_div(I.k, TC_N) * TC_N * Kst;
     }
     P->N_total = row_off[count];
     P->kpad_total = im.kpad_off[count];
@@ -676,7 +740,7 @@ geek_status tc_plan_build(geek_ctx *ctx, Scratch *scr, const std::vector<TcPlanI
     __nv_bfloat16 *xb, *cb;
     float *cn;
     unsigned *cmax_bits;
-    GK_TRY(plan_alloc(ctx, scr, own, &xb, (size_t)xb_total));
+    GK_TRY(plan_alloc(ctx, scr, own, &xb, (size_t)std::max<int64_t>(xb_total, 1)));
     GK_TRY(plan_alloc(ctx, scr, own, &cb, (size_t)std::max<int64_t>(cb_total, 1)));
     GK_TRY(plan_alloc(ctx, scr, own, &P->xnorm, (size_t)std::max<int64_t>(P->N_total, 1)));
     GK_TRY(plan_alloc(ctx, scr, own, &cn, (size_t)std::max<int64_t>(P->kpad_total, 1)));
@@ -694,36 +758,54 @@ geek_status tc_plan_build(geek_ctx *ctx, Scratch *scr, const std::vector<TcPlanI
     for (int i = 0; i < count; i++) {
         const TcPlanInst &I = desc[i];
         const int Kp = I.d <= 64 ? 64 : 128;
-        im.xp[i] = TcXPrep{I.x, I.ldx, I.d, Kp, xb + xo};
+        const int Kst = (I.split || P->allow_split) ? 2 * Kp : Kp;
+        im.xp[i] = TcXPrep{I.x, I.ldx, I.d, Kp, I.split, xb + xo};
         const int64_t kpad = im.kpad_off[i + 1] - im.kpad_off[i];
-        im.cp[i] = TcCPrep{I.centres, I.k, kpad, I.d, Kp, cb + co, cn + im.kpad_off[i], cmax_bits + i};
-        xo += I.n * Kp;
-        co += kpad * Kp;
+        im.cp[i] = TcCPrep{I.centres, I.k, kpad, I.d, Kp, I.split, cb + co, cn + im.kpad_off[i], cmax_bits + i};
+        xo += I.n * Kst;
+        co += kpad * Kst;
     }
     im.inst.resize(count);
     for (int i = 0; i < count; i++) GK_TRY(make_inst(ctx, *P, i, desc[i].N, &im.inst[i]));
-    std::vector<int> all(count);
-    for (int i = 0; i < count; i++) all[i] = i;
-    std::vector<int2> units;
-    make_units(*P, all, units);
-    P->nunits = (int64_t)units.size();
-    GK_TRY(plan_alloc(ctx, scr, own, &P->units, (size_t)std::max<int64_t>(P->nunits, 1)));
+    GK_TRY(plan_alloc(ctx, scr, own, &P->units, (size_t)std::max<int64_t>(ceil_div(P->N_total, TC_M) + count, 1)));
     GK_CUDA(ctx, cudaMemcpyAsync(P->row_off, row_off.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, st));
     GK_CUDA(ctx, cudaMemcpyAsync(P->kpad_off_dev, im.kpad_off.data(), sizeof(int64_t) * (count + 1),
                                  cudaMemcpyHostToDevice, st));
-    GK_CUDA(ctx, cudaMemcpyAsync(P->xprep, im.xp.data(), sizeof(TcXPrep) * count, cudaMemcpyHostToDevice, st));
-    GK_CUDA(ctx, cudaMemcpyAsync(P->cprep, im.cp.data(), sizeof(TcCPrep) * count, cudaMemcpyHostToDevice, st));
-    GK_CUDA(ctx, cudaMemcpyAsync(P->inst, im.inst.data(), sizeof(TcInst) * count, cudaMemcpyHostToDevice, st));
-    if (P->nunits)
-        GK_CUDA(ctx, cudaMemcpyAsync(P->units, units.data(), sizeof(int2) * P->nunits, cudaMemcpyHostToDevice, st));
-    // the host vectors above are pageable: the copies have read them on return
-    GK_CUDA(ctx, cudaFuncSetAttribute(k_assign_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem()));
+    GK_TRY(tc_plan_upload(ctx, P, st));
+    GK_CUDA(ctx, cudaFuncSetAttribute(k_assign_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem()));
+    GK_CUDA(ctx, cudaFuncSetAttribute(k_assign_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem()));
     return GEEK_OK;
 }
 
-// Conversions of X and the centres; then the persistent tcgen05 pass over
-// every unit.  flag_rows / n_flag receive the rows left to the FP64 decision
-// (n_flag must be zeroed by the caller).  No host synchronisation.
+// Uploads the descriptors and unit lists of the current modes and tiles:
+// units[0, nunits) run in BF16, units[nunits, nunits + nunits_x3) in
+// split-BF16.
+geek_status tc_plan_upload(geek_ctx *ctx, TcPlan *P, cudaStream_t st) {
+    auto &im = *P->impl;
+    const int count = P->count;
+    for (int i = 0; i < count; i++) {
+        im.xp[i].split = P->desc[i].split;
+        im.cp[i].split = P->desc[i].split;
+    }
+    std::vector<int> all(count);
+    for (int i = 0; i < count; i++) all[i] = i;
+    std::vector<int2> u0, u1;
+    make_units(*P, all, 0, u0);
+    make_units(*P, all, 1, u1);
+    P->nunits = (int64_t)u0.size();
+    P->nunits_x3 = (int64_t)u1.size();
+    u0.insert(u0.end(), u1.begin(), u1.end());
+    GK_CUDA(ctx, cudaMemcpyAsync(P->xprep, im.xp.data(), sizeof(TcXPrep) * count, cudaMemcpyHostToDevice, st));
+    GK_CUDA(ctx, cudaMemcpyAsync(P->cprep, im.cp.data(), sizeof(TcCPrep) * count, cudaMemcpyHostToDevice, st));
+    GK_CUDA(ctx, cudaMemcpyAsync(P->inst, im.inst.data(), sizeof(TcInst) * count, cudaMemcpyHostToDevice, st));
+    if (!u0.empty())
+        GK_CUDA(ctx, cudaMemcpyAsync(P->units, u0.data(), sizeof(int2) * u0.size(), cudaMemcpyHostToDevice, st));
+    // the host vectors are pageable: the copies have read them on return
+    return GEEK_OK;
+}
+
+// Conversions of X and the centres (BF16 or split-BF16 pairs, norms, the
+// max of |c|^2).  No host synchronisation.
 geek_status tc_plan_convert(geek_ctx *ctx, const TcPlan &P, cudaStream_t st) {
     const int count = P.count;
     GK_CUDA(ctx, cudaMemsetAsync(P.err, 0, sizeof(int), st));
@@ -742,23 +824,43 @@ geek_status tc_plan_convert(geek_ctx *ctx, const TcPlan &P, cudaStream_t st) {
     return GEEK_OK;
 }
 
-geek_status tc_plan_launch(geek_ctx *ctx, const TcPlan &P, int32_t *flag_rows, unsigned long long *n_flag,
-                           cudaStream_t st) {
-    if (P.nunits == 0) return GEEK_OK;
+namespace {
+
+geek_status launch_units(geek_ctx *ctx, const TcInst *inst, const int2 *units, int64_t n0, int64_t n1,
+                         int32_t *flag_rows, unsigned long long *n_flag, int *err, double work, cudaStream_t st) {
     TcArgs A;
-    A.inst = P.inst;
-    A.units = P.units;
-    A.nunits = P.nunits;
+    A.inst = inst;
     A.flag_rows = flag_rows;
     A.n_flag = n_flag;
-    A.err = P.err;
-    const int grid = (int)std::min<int64_t>(P.nunits, ctx->num_sms);
+    A.err = err;
     EvTimer tk(ctx, "kernel.assign_tc", st);
-    for (const TcPlanInst &I : P.desc) tk.work += 2.0 * (double)I.n * (double)I.k * (double)I.d;
-    GK_COUNT();
-    k_assign_tc<<<grid, TC_THREADS, tc_smem(), st>>>(A);
+    tk.work = work;
+    if (n0 > 0) {
+        A.units = units;
+        A.nunits = n0;
+        GK_COUNT();
+        k_assign_tc<false><<<(int)std::min<int64_t>(n0, ctx->num_sms), TC_THREADS, tc_smem(), st>>>(A);
+    }
+    if (n1 > 0) {
+        A.units = units + n0;
+        A.nunits = n1;
+        GK_COUNT();
+        k_assign_tc<true><<<(int)std::min<int64_t>(n1, ctx->num_sms), TC_THREADS, tc_smem(), st>>>(A);
+    }
     GK_LAUNCH(ctx);
     return GEEK_OK;
+}
+
+}  // namespace
+
+// The persistent tcgen05 passes (BF16 units, then split-BF16 units) after
+// tc_plan_convert; flagged rows are appended to flag_rows / n_flag (zeroed
+// by the caller).
+geek_status tc_plan_launch(geek_ctx *ctx, const TcPlan &P, int32_t *flag_rows, unsigned long long *n_flag,
+                           cudaStream_t st) {
+    double work = 0.0;
+    for (const TcPlanInst &I : P.desc) work += 2.0 * (double)I.n * (double)I.k * (double)I.d;
+    return launch_units(ctx, P.inst, P.units, P.nunits, P.nunits_x3, flag_rows, n_flag, P.err, work, st);
 }
 
 geek_status tc_plan_enqueue(geek_ctx *ctx, const TcPlan &P, int32_t *flag_rows, unsigned long long *n_flag,
@@ -767,86 +869,47 @@ geek_status tc_plan_enqueue(geek_ctx *ctx, const TcPlan &P, int32_t *flag_rows, 
     return tc_plan_launch(ctx, P, flag_rows, n_flag, st);
 }
 
-geek_status tc_plan_set_tiles(geek_ctx *ctx, TcPlan *P, const std::vector<int> &N, cudaStream_t st) {
-    const int count = P->count;
-    for (int i = 0; i < count; i++) {
+// Sets every instance's tile width and mode (descriptors re-encoded, units
+// rebuilt).  The next tc_plan_convert writes the matching layouts.
+geek_status tc_plan_set_modes(geek_ctx *ctx, TcPlan *P, const std::vector<int> &N, const std::vector<int> &split,
+                              cudaStream_t st) {
+    for (int i = 0; i < P->count; i++) {
+        if (split[i] && !P->allow_split && !P->desc[i].split)
+            return set_error(ctx, GEEK_ERR_INVALID, "plan was built without room for split-BF16");
         P->desc[i].N = N[i];
+        P->desc[i].split = split[i];
         GK_TRY(make_inst(ctx, *P, i, N[i], &P->impl->inst[i]));
     }
-    std::vector<int> all(count);
-    for (int i = 0; i < count; i++) all[i] = i;
-    std::vector<int2> units;
-    make_units(*P, all, units);
-    GK_CUDA(ctx, cudaMemcpyAsync(P->inst, P->impl->inst.data(), sizeof(TcInst) * count, cudaMemcpyHostToDevice, st));
-    if (!units.empty())
-        GK_CUDA(ctx, cudaMemcpyAsync(P->units, units.data(), sizeof(int2) * units.size(), cudaMemcpyHostToDevice, st));
-    P->nunits = (int64_t)units.size();
-    return GEEK_OK;
+    return tc_plan_upload(ctx, P, st);
 }
 
-// Times the tcgen05 pass over the units of `which` with tile width N for
-// those instances (the conversions of tc_plan_enqueue must have run).
-// Writes labels and flags of those rows as a side effect.
-geek_status tc_plan_time(geek_ctx *ctx, TcPlan *P, const std::vector<int> &which, int N, int32_t *flag_rows,
-                         unsigned long long *n_flag, int reps, float *ms_out, cudaStream_t st) {
+// Launches the tcgen05 pass over the units of `which` only, with tile width
+// N and mode `split` for those instances (their layouts must match: run
+// tc_plan_convert after tc_plan_set_modes).  Uses the plan's scratch
+// descriptor table; writes labels and flags of those rows.  No host sync.
+geek_status tc_plan_launch_subset(geek_ctx *ctx, TcPlan *P, const std::vector<int> &which, int32_t *flag_rows,
+                                  unsigned long long *n_flag, cudaStream_t st) {
     auto &im = *P->impl;
-    std::vector<TcInst> saved = im.inst;
-    for (int i : which) GK_TRY(make_inst(ctx, *P, i, N, &im.inst[i]));
-    std::vector<int2> units;
-    make_units(*P, which, units);
-    TcInst *dinst = nullptr;
-    int2 *dunits = nullptr;
-    geek_status rc = GEEK_OK;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    float best = 1e30f;
-    if (units.empty()) {
-        *ms_out = 0.f;
-        im.inst = saved;
-        return GEEK_OK;
-    }
-    if (cudaMalloc((void **)&dinst, sizeof(TcInst) * P->count) != cudaSuccess ||
-        cudaMalloc((void **)&dunits, sizeof(int2) * units.size()) != cudaSuccess ||
-        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
-        cudaGetLastError();
-        rc = set_error(ctx, GEEK_ERR_NOMEM, "autotune set-up failed");
-    }
-    if (rc == GEEK_OK &&
-        (cudaMemcpyAsync(dinst, im.inst.data(), sizeof(TcInst) * P->count, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-         cudaMemcpyAsync(dunits, units.data(), sizeof(int2) * units.size(), cudaMemcpyHostToDevice, st) != cudaSuccess))
-        rc = set_error(ctx, GEEK_ERR_CUDA, "autotune upload failed");
-    for (int r = 0; r < reps && rc == GEEK_OK; r++) {
-        TcArgs A;
-        A.inst = dinst;
-        A.units = dunits;
-        A.nunits = (int64_t)units.size();
-        A.flag_rows = flag_rows;
-        A.n_flag = n_flag;
-        A.err = P->err;
-        cudaMemsetAsync(n_flag, 0, sizeof(unsigned long long), st);
-        cudaEventRecord(e0, st);
-        GK_COUNT();
-        k_assign_tc<<<(int)std::min<int64_t>(A.nunits, ctx->num_sms), TC_THREADS, tc_smem(), st>>>(A);
-        cudaEventRecord(e1, st);
-        if (cudaEventSynchronize(e1) != cudaSuccess) {
-            rc = set_error(ctx, GEEK_ERR_CUDA, "autotune launch failed: %s", cudaGetErrorString(cudaGetLastError()));
-            break;
+    std::vector<int2> u0, u1;
+    make_units(*P, which, 0, u0);
+    make_units(*P, which, 1, u1);
+    const int64_t n0 = (int64_t)u0.size(), n1 = (int64_t)u1.size();
+    u0.insert(u0.end(), u1.begin(), u1.end());
+    if (u0.empty()) return GEEK_OK;
+    if (!P->tune_units || P->tune_cap < (int64_t)u0.size()) {
+        if (P->tune_units) cudaFree(P->tune_units);
+        P->tune_units = nullptr;
+        P->tune_cap = 0;
+        if (cudaMalloc((void **)&P->tune_units, sizeof(int2) * u0.size()) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(ctx, GEEK_ERR_NOMEM, "autotune unit list");
         }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        best = std::min(best, ms);
+        P->tune_cap = (int64_t)u0.size();
     }
-    int h_err = 0;
-    if (rc == GEEK_OK) {
-        cudaMemcpy(&h_err, P->err, sizeof h_err, cudaMemcpyDeviceToHost);
-        if (h_err) rc = set_error(ctx, (geek_status)h_err, "tensor-core assignment: a pipeline wait timed out");
-    }
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    cudaFree(dinst);
-    cudaFree(dunits);
-    im.inst = saved;
-    *ms_out = best;
-    return rc;
+    GK_CUDA(ctx, cudaMemcpyAsync(P->tune_units, u0.data(), sizeof(int2) * u0.size(), cudaMemcpyHostToDevice, st));
+    GK_CUDA(ctx, cudaStreamSynchronize(st));  // u0 is pageable and about to go out of scope
+    (void)im;
+    return launch_units(ctx, P->inst, P->tune_units, n0, n1, flag_rows, n_flag, P->err, 0.0, st);
 }
 
 geek_status tc_plan_check(geek_ctx *ctx, const TcPlan &P, cudaStream_t st) {
@@ -860,19 +923,24 @@ geek_status tc_plan_check(geek_ctx *ctx, const TcPlan &P, cudaStream_t st) {
 void tc_plan_free(TcPlan *P) {
     for (void *p : P->owned) cudaFree(p);
     P->owned.clear();
+    if (P->tune_units) cudaFree(P->tune_units);
+    P->tune_units = nullptr;
+    P->tune_cap = 0;
     delete P->impl;
     P->impl = nullptr;
 }
 
-// BF16 tcgen05 pass of one data set: labels for every object, flagged rows
-// appended to flag_rows / n_flag for the FP64 decision.  d <= 128.
+// BF16 (split = 0) or split-BF16 (split = 1) tcgen05 pass of one data set:
+// labels for every object, flagged rows appended to flag_rows / n_flag for
+// the FP64 decision.  d <= 128.
 geek_status assign_tc_bf16(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ldx, int64_t n, int d,
-                           const double *centres, int64_t k, int32_t *labels, int32_t *flag_rows,
+                           const double *centres, int64_t k, int split, int32_t *labels, int32_t *flag_rows,
                            unsigned long long *n_flag, cudaStream_t st) {
     if (d > 128) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "BF16 tensor-core assignment supports d <= 128");
     TcPlan P;
     std::vector<TcPlanInst> one(1);
-    one[0] = TcPlanInst{x, ldx, n, d, centres, k, labels, 0, TC_N};
+    const int N = split ? (d <= 64 ? 128 : 64) : TC_N;
+    one[0] = TcPlanInst{x, ldx, n, d, centres, k, labels, 0, N, split};
     struct Free {
         TcPlan *p;
         ~Free() { tc_plan_free(p); }

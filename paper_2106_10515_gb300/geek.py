@@ -19,7 +19,8 @@ OK, ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_OVERFLOW, ERR_UNSUPPORTED
 DENSE, SETS, HETERO = 0, 1, 2
 MEM_DEVICE, MEM_HOST = 0, 1
 PROJ_E2LSH, PROJ_SRP = 0, 1
-PREC_FP32, PREC_BF16 = 0, 1
+PREC_FP32, PREC_BF16, PREC_BF16X3 = 0, 1, 2
+PREC_AUTO = -1
 STATUS_NAMES = ["OK", "ERR_INVALID", "ERR_NOMEM", "ERR_CUDA", "ERR_TIMEOUT", "ERR_OVERFLOW",
                 "ERR_UNSUPPORTED"]
 
@@ -69,7 +70,7 @@ class geek_instance(C.Structure):
 
 class geek_batch_params(C.Structure):
     _fields_ = [("proj", C.c_int32), ("K", C.c_int32), ("L", C.c_int32), ("Ks", C.c_int32), ("Ls", C.c_int32),
-                ("delta", C.c_int32), ("tile_n", C.c_int32)]
+                ("delta", C.c_int32), ("precision", C.c_int32), ("tile_n", C.c_int32)]
 
 
 class geek_batch_info(C.Structure):
@@ -127,7 +128,7 @@ def lib():
                                     C.POINTER(P)]
     L.geek_batch_run.argtypes = [P, P, P]
     L.geek_batch_info_get.argtypes = [P, C.POINTER(geek_batch_info)]
-    L.geek_batch_instance_stats.argtypes = [P, P, P, P, P]
+    L.geek_batch_instance_stats.argtypes = [P, P, P, P, P, P]
     L.geek_batch_copy_out.argtypes = [P, P, P, P, P, P, P]
     L.geek_batch_seed_ids_count.argtypes = [P, C.POINTER(C.c_int64)]
     L.geek_batch_destroy.argtypes = [P]
@@ -353,7 +354,7 @@ class Batch:
     a (K*L x d float32), b (K*L float32), mh_a / mh_b (Ls*Ks int64 bits of
     uint64), dd_a / dd_b (Ks), and w.  The tensors are kept alive here."""
 
-    def __init__(self, ctx: Context, instances, K, L, Ks, Ls, delta, proj=PROJ_E2LSH, tile_n=0):
+    def __init__(self, ctx: Context, instances, K, L, Ks, Ls, delta, proj=PROJ_E2LSH, tile_n=0, precision=PREC_AUTO):
         self.ctx = ctx
         self._refs = instances
         arr = (geek_instance * len(instances))()
@@ -364,6 +365,7 @@ class Batch:
             c.mh_a, c.mh_b, c.dd_a, c.dd_b = _ptr(I["mh_a"]), _ptr(I["mh_b"]), _ptr(I["dd_a"]), _ptr(I["dd_b"])
         p = geek_batch_params()
         p.proj, p.K, p.L, p.Ks, p.Ls, p.delta, p.tile_n = proj, K, L, Ks, Ls, delta, tile_n
+        p.precision = precision
         h = C.c_void_p()
         ctx._chk(lib().geek_batch_create(ctx.h, arr, len(instances), C.byref(p), C.byref(h)))
         self.h = h
@@ -384,10 +386,10 @@ class Batch:
     def instance_stats(self):
         n = self.count
         k, sse, rmax = np.zeros(n, np.int64), np.zeros(n, np.float64), np.zeros(n, np.float64)
-        tile = np.zeros(n, np.int32)
+        tile, prec = np.zeros(n, np.int32), np.zeros(n, np.int32)
         self.ctx._chk(lib().geek_batch_instance_stats(self.h, k.ctypes.data, sse.ctypes.data, rmax.ctypes.data,
-                                                      tile.ctypes.data))
-        return dict(k=k, sse=sse, radius_max=rmax, tile_n=tile)
+                                                      tile.ctypes.data, prec.ctypes.data))
+        return dict(k=k, sse=sse, radius_max=rmax, tile_n=tile, precision=prec)
 
     def copy_out(self):
         """Per-instance results of the last run (host numpy)."""

@@ -38,11 +38,12 @@ def dev_instance(G, I):
                 mh_b=G._dev(sp["mh_b"]), dd_a=G._dev(sp["dd_a"]), dd_b=G._dev(sp["dd_b"]))
 
 
-def make_batch(G, ctx, insts, tile_n=0):
+def make_batch(G, ctx, insts, tile_n=0, precision=None):
     cfg = insts[0]["cfg"]
     s = insts[0]["silk"]
     dev = [dev_instance(G, I) for I in insts]
-    return G.Batch(ctx, dev, cfg.K, cfg.L, s["Ks"], s["Ls"], s["delta"], tile_n=tile_n), dev
+    prec = G.PREC_AUTO if precision is None else precision
+    return G.Batch(ctx, dev, cfg.K, cfg.L, s["Ks"], s["Ls"], s["delta"], tile_n=tile_n, precision=prec), dev
 
 
 def run_batch(b):
@@ -102,11 +103,21 @@ def test_batch_tiles_replay_and_sequential_agree(G, ctx):
     assert np.array_equal(lab, lab2)
     assert info2["graph_captures"] == info1["graph_captures"]
     assert info2["graph_launches"] == info1["graph_launches"] + 2
-    # every forced tile width gives the same labels
-    for tn in (64, 128, 256):
-        bt, _ = make_batch(G, ctx, insts, tile_n=tn)
-        assert np.array_equal(run_batch(bt), lab), tn
-        assert set(bt.instance_stats()["tile_n"].tolist()) == {tn}
+    assert set(st["precision"].tolist()) <= {G.PREC_BF16, G.PREC_BF16X3}
+    # every forced tile width and precision gives the same labels
+    rows = {}
+    for prec, tn in ((G.PREC_BF16, 64), (G.PREC_BF16, 128), (G.PREC_BF16, 256), (G.PREC_BF16X3, 64),
+                     (G.PREC_BF16X3, 128)):
+        bt, _ = make_batch(G, ctx, insts, tile_n=tn, precision=prec)
+        assert np.array_equal(run_batch(bt), lab), (prec, tn)
+        s2 = bt.instance_stats()
+        assert set(s2["precision"].tolist()) == {prec}
+        ds = np.array([I["x"].shape[1] for I in insts])
+        cap = np.where(ds <= 64, 128, 64) if prec == G.PREC_BF16X3 else 256
+        assert (s2["tile_n"] == np.minimum(tn, cap)).all(), (prec, tn)
+        rows[prec] = bt.info()["n_recheck_rows"]
+    # the split-BF16 window is ~100x narrower: fewer rows need the FP64 decision
+    assert rows[G.PREC_BF16X3] <= rows[G.PREC_BF16]
     # the single-instance C ABI, instance by instance
     got = b.copy_out()
     for i, (I, D) in enumerate(zip(insts, dev)):

@@ -80,7 +80,7 @@ def test_dense_c2_shape_hash_and_assign(G, ctx):
     assert 0 <= bk.n_flagged_fp64 <= bk.n_flagged
     c = wl["centres"].astype(np.float64)
     lab_ref, dist_ref = oracle.assign_dense(wl["x"], c)
-    for prec in (G.PREC_FP32, G.PREC_BF16):
+    for prec in (G.PREC_FP32, G.PREC_BF16, G.PREC_BF16X3):
         labels = torch.empty(cfg.n, dtype=torch.int32, device="cuda")
         st = ctx.assign_centers(ctx.dense(x), G._dev(c), labels, precision=prec)
         torch.cuda.synchronize()
@@ -105,7 +105,7 @@ def test_assign_near_ties_are_exact(G, ctx):
     c[150:] = c[:150]                      # exact duplicates
     c[100:150] += 1e-9                     # near duplicates
     lab_ref, _ = oracle.assign_dense(x, c)
-    for prec in (0, 1):
+    for prec in (G.PREC_FP32, G.PREC_BF16, G.PREC_BF16X3):
         labels = torch.empty(5000, dtype=torch.int32, device="cuda")
         st = ctx.assign_centers(ctx.dense(G._dev(x)), G._dev(c), labels, precision=prec)
         torch.cuda.synchronize()
