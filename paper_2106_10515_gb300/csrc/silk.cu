@@ -53,7 +53,7 @@ __global__ void k_set_sig(int64_t nsets, const int64_t *__restrict__ soff,
         }
         klo[so + g] = lo;
         if (khi) khi[so + g] = hi;
-        vals[so + g] = (uint32_t)g;
+        if (vals) vals[so + g] = (uint32_t)g;
         if (tag) tag[so + g] = (uint32_t)inst;
     }
 }
@@ -384,20 +384,6 @@ __global__ void k_bin_weight(int64_t nbins, const int64_t *__restrict__ rs, cons
     }
 }
 
-// bins of exactly one virtual bucket with |Bin| >= 2: every member occurs in
-// all |Bin| copies, so C_shared is the whole bucket
-__global__ void k_single_bins(int64_t nbins, const int64_t *__restrict__ rs, const uint32_t *__restrict__ perm,
-                              const int64_t *__restrict__ bw, const int64_t *__restrict__ voff, int delta,
-                              int64_t *__restrict__ has, int64_t *__restrict__ pick) {
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nbins; r += (int64_t)gridDim.x * blockDim.x) {
-        const bool one = rs[r + 1] - rs[r] == 1;
-        const int64_t v = perm[rs[r]];
-        const bool h = one && bw[r] >= 2 && voff[v + 1] - voff[v] >= delta;
-        has[r] = h;
-        pick[r] = v;
-    }
-}
-
 // weighted vote over bins of >= 2 virtual buckets
 __global__ void k_wvote_weights(int64_t m, const int32_t *__restrict__ rank, const int64_t *__restrict__ rs,
                                 const uint32_t *__restrict__ perm, const int64_t *__restrict__ voff,
@@ -446,6 +432,74 @@ __global__ void k_wbin_ok(int64_t nbins, const int64_t *__restrict__ rs, const i
         const bool o = bin_size(rs, b) >= 2 && cnt[b] >= delta;
         ok[b] = o;
         len[b] = o ? cnt[b] : 0;
+    }
+}
+
+// ---- exact grouping of equal signatures by hashing ---------------------------
+// Segment t (a SILK table) has a table of C slots (C a power of two >= 2 NV,
+// so probing always ends); a slot holds the index g of the first set that
+// claimed it, and sets whose full signature (and instance tag) equals that
+// set's join its group.  Returns, per position, the slot of its group; cnt
+// counts each group's sets.
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    // SplitMix64 finalizer (Steele, Lea and Flood, 2014)
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_group_insert(int64_t NV, int64_t C, const uint64_t *__restrict__ klo,
+                               const uint64_t *__restrict__ khi, const uint32_t *__restrict__ tag,
+                               uint32_t *__restrict__ slot, uint32_t *__restrict__ cnt, uint32_t *__restrict__ grp) {
+    const int t = blockIdx.y;
+    const int64_t so = (int64_t)t * NV;
+    uint32_t *sl = slot + (int64_t)t * C;
+    uint32_t *ct = cnt + (int64_t)t * C;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < NV; g += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t lo = klo[so + g], hi = khi ? khi[so + g] : 0;
+        const uint32_t tg = tag ? tag[so + g] : 0;
+        uint64_t h = mix64(lo ^ mix64(hi + 0x9e3779b97f4a7c15ull * (uint64_t)(tg + 1))) & (uint64_t)(C - 1);
+        for (int64_t probe = 0; probe < C; probe++) {
+            uint32_t cur = sl[h];
+            if (cur == 0xFFFFFFFFu) {
+                const uint32_t prev = atomicCAS(&sl[h], 0xFFFFFFFFu, (uint32_t)g);
+                if (prev == 0xFFFFFFFFu) {
+                    grp[so + g] = (uint32_t)h;
+                    atomicAdd(&ct[h], 1u);
+                    break;
+                }
+                cur = prev;
+            }
+            if (klo[so + cur] == lo && (!khi || khi[so + cur] == hi) && (!tag || tag[so + cur] == tg)) {
+                grp[so + g] = (uint32_t)h;
+                atomicAdd(&ct[h], 1u);
+                break;
+            }
+            h = (h + 1) & (uint64_t)(C - 1);
+        }
+    }
+}
+
+// Positions of groups of >= 2 sets go to the multi list (key = segment * C +
+// slot, value = set); a set alone in its group with weight >= 2 and at least
+// delta members is a bin of one virtual bucket that keeps the whole bucket.
+__global__ void k_group_lists(int64_t NV, int S, int64_t C, const uint32_t *__restrict__ grp,
+                              const uint32_t *__restrict__ cnt, const int32_t *__restrict__ vw,
+                              const int64_t *__restrict__ voff, int delta, uint64_t *__restrict__ mkey,
+                              uint32_t *__restrict__ mval, unsigned long long *__restrict__ n_multi,
+                              int64_t *__restrict__ singles, unsigned long long *__restrict__ n_single) {
+    const int64_t tot = NV * S;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < tot; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = p / NV, g = p - t * NV;
+        const uint64_t key = (uint64_t)t * (uint64_t)C + grp[p];
+        const uint32_t c = cnt[key];
+        if (c >= 2) {
+            const unsigned long long q = atomicAdd(n_multi, 1ull);
+            mkey[q] = key;
+            mval[q] = (uint32_t)g;
+        } else if (vw[g] >= 2 && voff[g + 1] - voff[g] >= delta) {
+            singles[atomicAdd(n_single, 1ull)] = g;
+        }
     }
 }
 
@@ -538,6 +592,72 @@ geek_status make_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const i
         nsets, runs, d_base, rs_seg, *rs, S);
     GK_LAUNCH(ctx);
     *nbins = total;
+    return GEEK_OK;
+}
+
+// Bins of the main SILK pass for S tables at once, by exact hashing of the
+// signatures (no sort of all S * nsets signatures): only bins of >= 2 virtual
+// buckets take part in the vote, and single-bucket bins matter only when
+// their weight is >= 2 and the bucket has >= delta objects.  Returns the
+// vote's bins (perm: virtual bucket per position, rank: bin per position, rs:
+// bin starts, nbins; positions grouped by bin, bins in arbitrary order -- the
+// seeds do not depend on bin order) and the single-bin buckets (singles).
+geek_status group_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const int64_t *soff, const uint32_t *sids,
+                       const int32_t *vw, int delta, int Ks, const uint64_t *A, const uint64_t *B, const SilkBatch *bt,
+                       int64_t coef_stride, uint32_t **perm, int32_t **rank, int64_t **rs, int64_t *npos,
+                       int64_t *nbins, int64_t **singles, int64_t *n_singles, cudaStream_t st) {
+    const int64_t tot = (int64_t)S * nsets;
+    const bool tagged = bt && bt->count > 1;
+    int64_t C = 64;
+    while (C < 2 * nsets) C <<= 1;
+    uint64_t *klo, *khi = nullptr;
+    uint32_t *tag = nullptr, *slot, *cnt, *grp;
+    GK_TRY(scr.alloc(&klo, tot));
+    if (Ks > 2) GK_TRY(scr.alloc(&khi, tot));
+    if (tagged) GK_TRY(scr.alloc(&tag, tot));
+    GK_TRY(scr.alloc(&slot, (size_t)S * C));
+    GK_TRY(scr.alloc(&cnt, (size_t)S * C));
+    GK_TRY(scr.alloc(&grp, tot));
+    GK_CUDA(ctx, cudaMemsetAsync(slot, 0xFF, sizeof(uint32_t) * S * C, st));
+    GK_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * S * C, st));
+    const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nsets, 256), (int64_t)ctx->num_sms * 8));
+    GK_COUNT();
+    k_set_sig<<<dim3(gx, S), 256, 0, st>>>(nsets, soff, sids, Ks, A, B, tagged ? bt->row_off : nullptr,
+                                           tagged ? bt->count : 1, coef_stride, klo, khi, nullptr, tag);
+    GK_COUNT();
+    k_group_insert<<<dim3(gx, S), 256, 0, st>>>(nsets, C, klo, khi, tag, slot, cnt, grp);
+    GK_LAUNCH(ctx);
+    uint64_t *mkey;
+    uint32_t *mval;
+    unsigned long long *counts;
+    GK_TRY(scr.alloc(&mkey, tot));
+    GK_TRY(scr.alloc(&mval, tot));
+    GK_TRY(scr.alloc(singles, tot));
+    GK_TRY(scr.alloc(&counts, 2));
+    GK_CUDA(ctx, cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), st));
+    GK_COUNT();
+    k_group_lists<<<G(ctx, tot), 256, 0, st>>>(nsets, S, C, grp, cnt, vw, soff, delta, mkey, mval, counts, *singles,
+                                               counts + 1);
+    GK_LAUNCH(ctx);
+    unsigned long long h[2];
+    GK_CUDA(ctx, cudaMemcpyAsync(h, counts, sizeof h, cudaMemcpyDeviceToHost, st));
+    GK_CUDA(ctx, cudaStreamSynchronize(st));
+    const int64_t m = (int64_t)h[0];
+    *npos = m;
+    *n_singles = (int64_t)h[1];
+    // the vote's positions grouped by bin: sort the multi list by group key
+    GK_TRY(radix_sort_segments(ctx, scr, 1, m, &mkey, nullptr, &mval, bit_length_u64((uint64_t)(S * C)), st));
+    int64_t *runs;
+    GK_TRY(scr.alloc(rank, std::max<int64_t>(m, 1)));
+    GK_TRY(scr.alloc(rs, m + 1));
+    GK_TRY(scr.alloc(&runs, 1));
+    if (m > 0) {
+        GK_TRY(segment_runs(ctx, scr, 1, m, mkey, nullptr, *rank, *rs, runs, st));
+        GK_TRY(d2h_i64(ctx, runs, nbins, st));
+    } else {
+        *nbins = 0;
+    }
+    *perm = mval;
     return GEEK_OK;
 }
 
@@ -801,44 +921,32 @@ geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p,
     const int TS = (int)std::max<int64_t>(1, std::min<int64_t>(Ls, NV > 0 ? budget / NV : Ls));
     for (int t = 0; t < Ls && NV > 0; t += TS) {
         const int S = std::min(TS, Ls - t);
-        const int64_t M = (int64_t)S * NV;
         Scratch tscr(ctx, st);  // per-chunk temporaries
         uint32_t *perm;
         int32_t *rank;
-        int64_t *rs, nbins = 0;
+        int64_t *rs, nbins = 0, *singles, nh = 0, npos = 0;
         {
             EvTimer tb(ctx, "silk.bins", st);
-            GK_TRY(make_bins(ctx, tscr, S, NV, voff, vmem, Ks, p->mh_a + (int64_t)t * Ks, p->mh_b + (int64_t)t * Ks,
-                             bt, (int64_t)Ls * Ks, &perm, &rank, &rs, &nbins, st));
+            GK_TRY(group_bins(ctx, tscr, S, NV, voff, vmem, vw, delta, Ks, p->mh_a + (int64_t)t * Ks,
+                              p->mh_b + (int64_t)t * Ks, bt, (int64_t)Ls * Ks, &perm, &rank, &rs, &npos, &nbins,
+                              &singles, &nh, st));
         }
         EvTimer tv(ctx, "silk.vote", st);
-        int64_t *bw, *has, *pick, *hpos, *d_nh;
-        GK_TRY(tscr.alloc(&bw, nbins));
-        GK_TRY(tscr.alloc(&has, nbins));
-        GK_TRY(tscr.alloc(&pick, nbins));
-        GK_TRY(tscr.alloc(&hpos, nbins));
-        GK_TRY(tscr.alloc(&d_nh, 1));
-        GK_COUNT();
-        k_bin_weight<<<G(ctx, nbins), 256, 0, st>>>(nbins, rs, perm, vw, bw);
-        GK_COUNT();
-        k_single_bins<<<G(ctx, nbins), 256, 0, st>>>(nbins, rs, perm, bw, voff, delta, has, pick);
-        GK_LAUNCH(ctx);
-        GK_TRY(exclusive_scan_i64(ctx, tscr, has, hpos, nbins, d_nh, st));
-        int64_t nh = 0;
-        GK_TRY(d2h_i64(ctx, d_nh, &nh, st));
+        int64_t *bw;
+        GK_TRY(tscr.alloc(&bw, std::max<int64_t>(nbins, 1)));
+        if (nbins) {
+            GK_COUNT();
+            k_bin_weight<<<G(ctx, nbins), 256, 0, st>>>(nbins, rs, perm, vw, bw);
+            GK_LAUNCH(ctx);
+        }
         std::vector<Csr> tparts;
         if (nh) {
-            int64_t *idx;
-            GK_TRY(tscr.alloc(&idx, nh));
-            GK_COUNT();
-            k_compact_idx<<<G(ctx, nbins), 256, 0, st>>>(nbins, has, hpos, pick, idx);
-            GK_LAUNCH(ctx);
             Csr c1;
-            GK_TRY(gather_sets(ctx, tscr, nh, idx, voff, vmem, &c1, st));
+            GK_TRY(gather_sets(ctx, tscr, nh, singles, voff, vmem, &c1, st));
             tparts.push_back(c1);
         }
         Csr c2;
-        GK_TRY(wvote_bins(ctx, tscr, M, perm, rank, rs, nbins, voff, vmem, vw, bw, delta, &c2, st));
+        if (nbins) GK_TRY(wvote_bins(ctx, tscr, npos, perm, rank, rs, nbins, voff, vmem, vw, bw, delta, &c2, st));
         if (c2.n) tparts.push_back(c2);
         for (auto &c : tparts) {
             // move the table's C_shared sets into the outer scratch
