@@ -117,6 +117,9 @@ struct silk_seeds {
 struct SilkBatch {
     const int64_t *row_off = nullptr;
     int count = 1;
+    // set inside silk_run: per-instance slot regions of the grouping tables
+    const int64_t *slot_off = nullptr, *slot_cap = nullptr;
+    int64_t slots = 0;
 };
 geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p, silk_seeds *out,
                      cudaStream_t st, const SilkBatch *bt = nullptr);

@@ -437,10 +437,10 @@ __global__ void k_wbin_ok(int64_t nbins, const int64_t *__restrict__ rs, const i
 
 // ---- exact grouping of equal signatures by hashing ---------------------------
 // Segment t (a SILK table) has a table of C slots (C a power of two >= 2 NV,
-// so probing always ends); a slot holds the index g of the first set that
-// claimed it, and sets whose full signature (and instance tag) equals that
-// set's join its group.  Returns, per position, the slot of its group; cnt
-// counts each group's sets.
+// so probing always ends).  A slot holds, in its low 31 bits, the index g of
+// the first set that claimed it; sets whose full signature (and instance tag)
+// equals that set's join its group, and the first joiner sets bit 31 (the
+// group has >= 2 sets).  grp[p] = the slot of position p's group.
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     // SplitMix64 finalizer (Steele, Lea and Flood, 2014)
     z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
@@ -448,58 +448,100 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     return z ^ (z >> 31);
 }
 
+constexpr uint32_t SLOT_EMPTY = 0xFFFFFFFFu, SLOT_MULTI = 0x80000000u;
+
+// Batched instances: instance i owns the slot region [roff[i], roff[i] +
+// rcap[i]) (rcap a power of two >= 2x its sets), so a block, whose sets mostly
+// belong to one instance, probes one small region.
 __global__ void k_group_insert(int64_t NV, int64_t C, const uint64_t *__restrict__ klo,
                                const uint64_t *__restrict__ khi, const uint32_t *__restrict__ tag,
-                               uint32_t *__restrict__ slot, uint32_t *__restrict__ cnt, uint32_t *__restrict__ grp) {
+                               const int64_t *__restrict__ roff, const int64_t *__restrict__ rcap,
+                               uint32_t *__restrict__ slot, uint32_t *__restrict__ grp) {
     const int t = blockIdx.y;
     const int64_t so = (int64_t)t * NV;
     uint32_t *sl = slot + (int64_t)t * C;
-    uint32_t *ct = cnt + (int64_t)t * C;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < NV; g += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t lo = klo[so + g], hi = khi ? khi[so + g] : 0;
         const uint32_t tg = tag ? tag[so + g] : 0;
-        uint64_t h = mix64(lo ^ mix64(hi + 0x9e3779b97f4a7c15ull * (uint64_t)(tg + 1))) & (uint64_t)(C - 1);
-        for (int64_t probe = 0; probe < C; probe++) {
-            uint32_t cur = sl[h];
-            if (cur == 0xFFFFFFFFu) {
-                const uint32_t prev = atomicCAS(&sl[h], 0xFFFFFFFFu, (uint32_t)g);
-                if (prev == 0xFFFFFFFFu) {
-                    grp[so + g] = (uint32_t)h;
-                    atomicAdd(&ct[h], 1u);
+        const int64_t base = tag ? roff[tg] : 0;
+        const uint64_t mask = (uint64_t)(tag ? rcap[tg] : C) - 1;
+        uint64_t h = mix64(lo ^ mix64(hi + 0x9e3779b97f4a7c15ull * (uint64_t)(tg + 1))) & mask;
+        for (uint64_t probe = 0; probe <= mask; probe++) {
+            uint32_t cur = sl[base + h];
+            if (cur == SLOT_EMPTY) {
+                const uint32_t prev = atomicCAS(&sl[base + h], SLOT_EMPTY, (uint32_t)g);
+                if (prev == SLOT_EMPTY) {
+                    grp[so + g] = (uint32_t)(base + h);
                     break;
                 }
                 cur = prev;
             }
-            if (klo[so + cur] == lo && (!khi || khi[so + cur] == hi) && (!tag || tag[so + cur] == tg)) {
-                grp[so + g] = (uint32_t)h;
-                atomicAdd(&ct[h], 1u);
+            const uint32_t r = cur & ~SLOT_MULTI;
+            if (klo[so + r] == lo && (!khi || khi[so + r] == hi) && (!tag || tag[so + r] == tg)) {
+                if (!(cur & SLOT_MULTI)) atomicOr(&sl[base + h], SLOT_MULTI);
+                grp[so + g] = (uint32_t)(base + h);
                 break;
             }
-            h = (h + 1) & (uint64_t)(C - 1);
+            h = (h + 1) & mask;
         }
     }
+}
+
+// sets per instance (the instance of a set is that of its first member);
+// lanes of a warp with the same instance add once
+__global__ void k_sets_per_inst(int64_t nsets, const int64_t *__restrict__ soff, const uint32_t *__restrict__ sids,
+                                const int64_t *__restrict__ row_off, int count, unsigned long long *__restrict__ cnt) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nsets; base += stride) {
+        const int64_t g = base + threadIdx.x;
+        const int i = g < nsets ? find_inst(row_off, count, (int64_t)sids[soff[g]]) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, i);
+        if (i >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[i], (unsigned long long)__popc(peers));
+    }
+}
+
+// warp-aggregated append: one atomic per warp and list
+__device__ __forceinline__ unsigned long long warp_append(bool want, unsigned long long *counter) {
+    const unsigned mask = __ballot_sync(0xffffffffu, want);
+    if (!mask) return 0;
+    const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    return base + __popc(mask & ((1u << lane) - 1));
 }
 
 // Positions of groups of >= 2 sets go to the multi list (key = segment * C +
 // slot, value = set); a set alone in its group with weight >= 2 and at least
 // delta members is a bin of one virtual bucket that keeps the whole bucket.
 __global__ void k_group_lists(int64_t NV, int S, int64_t C, const uint32_t *__restrict__ grp,
-                              const uint32_t *__restrict__ cnt, const int32_t *__restrict__ vw,
+                              const uint32_t *__restrict__ slot, const int32_t *__restrict__ vw,
                               const int64_t *__restrict__ voff, int delta, uint64_t *__restrict__ mkey,
                               uint32_t *__restrict__ mval, unsigned long long *__restrict__ n_multi,
                               int64_t *__restrict__ singles, unsigned long long *__restrict__ n_single) {
     const int64_t tot = NV * S;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < tot; p += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t t = p / NV, g = p - t * NV;
-        const uint64_t key = (uint64_t)t * (uint64_t)C + grp[p];
-        const uint32_t c = cnt[key];
-        if (c >= 2) {
-            const unsigned long long q = atomicAdd(n_multi, 1ull);
-            mkey[q] = key;
-            mval[q] = (uint32_t)g;
-        } else if (vw[g] >= 2 && voff[g + 1] - voff[g] >= delta) {
-            singles[atomicAdd(n_single, 1ull)] = g;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // whole warps iterate together (the appends are warp collectives)
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < tot; base += stride) {
+        const int64_t p = base + threadIdx.x;
+        bool multi = false, single = false;
+        uint64_t key = 0;
+        int64_t g = 0;
+        if (p < tot) {
+            const int64_t t = p / NV;
+            g = p - t * NV;
+            key = (uint64_t)t * (uint64_t)C + grp[p];
+            multi = (slot[key] & SLOT_MULTI) != 0;
+            single = !multi && vw[g] >= 2 && voff[g + 1] - voff[g] >= delta;
         }
+        const unsigned long long qm = warp_append(multi, n_multi);
+        if (multi) {
+            mkey[qm] = key;
+            mval[qm] = (uint32_t)g;
+        }
+        const unsigned long long qs = warp_append(single, n_single);
+        if (single) singles[qs] = g;
     }
 }
 
@@ -610,22 +652,28 @@ geek_status group_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const 
     const bool tagged = bt && bt->count > 1;
     int64_t C = 64;
     while (C < 2 * nsets) C <<= 1;
+    const int64_t *roff = nullptr, *rcap = nullptr;
+    if (tagged) {
+        if (!bt->slot_off || !bt->slot_cap) return set_error(ctx, GEEK_ERR_INVALID, "slot regions missing");
+        roff = bt->slot_off;
+        rcap = bt->slot_cap;
+        C = bt->slots;
+    }
     uint64_t *klo, *khi = nullptr;
-    uint32_t *tag = nullptr, *slot, *cnt, *grp;
+    if (nsets >= (int64_t)SLOT_MULTI) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "more than 2^31 SILK sets");
+    uint32_t *tag = nullptr, *slot, *grp;
     GK_TRY(scr.alloc(&klo, tot));
     if (Ks > 2) GK_TRY(scr.alloc(&khi, tot));
     if (tagged) GK_TRY(scr.alloc(&tag, tot));
     GK_TRY(scr.alloc(&slot, (size_t)S * C));
-    GK_TRY(scr.alloc(&cnt, (size_t)S * C));
     GK_TRY(scr.alloc(&grp, tot));
     GK_CUDA(ctx, cudaMemsetAsync(slot, 0xFF, sizeof(uint32_t) * S * C, st));
-    GK_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * S * C, st));
     const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nsets, 256), (int64_t)ctx->num_sms * 8));
     GK_COUNT();
     k_set_sig<<<dim3(gx, S), 256, 0, st>>>(nsets, soff, sids, Ks, A, B, tagged ? bt->row_off : nullptr,
                                            tagged ? bt->count : 1, coef_stride, klo, khi, nullptr, tag);
     GK_COUNT();
-    k_group_insert<<<dim3(gx, S), 256, 0, st>>>(nsets, C, klo, khi, tag, slot, cnt, grp);
+    k_group_insert<<<dim3(gx, S), 256, 0, st>>>(nsets, C, klo, khi, tag, roff, rcap, slot, grp);
     GK_LAUNCH(ctx);
     uint64_t *mkey;
     uint32_t *mval;
@@ -636,7 +684,7 @@ geek_status group_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const 
     GK_TRY(scr.alloc(&counts, 2));
     GK_CUDA(ctx, cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), st));
     GK_COUNT();
-    k_group_lists<<<G(ctx, tot), 256, 0, st>>>(nsets, S, C, grp, cnt, vw, soff, delta, mkey, mval, counts, *singles,
+    k_group_lists<<<G(ctx, tot), 256, 0, st>>>(nsets, S, C, grp, slot, vw, soff, delta, mkey, mval, counts, *singles,
                                                counts + 1);
     GK_LAUNCH(ctx);
     unsigned long long h[2];
@@ -658,6 +706,42 @@ geek_status group_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const 
         *nbins = 0;
     }
     *perm = mval;
+    return GEEK_OK;
+}
+
+// One slot region per instance for group_bins: a power of two >= 2x the
+// instance's sets (device arrays from scr, total in bt->slots).
+geek_status slot_regions(geek_ctx *ctx, Scratch &scr, int64_t nsets, const int64_t *soff, const uint32_t *sids,
+                         SilkBatch *bt, cudaStream_t st) {
+    const int count = bt->count;
+    unsigned long long *cnt;
+    GK_TRY(scr.alloc(&cnt, count));
+    GK_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * count, st));
+    if (nsets) {
+        GK_COUNT();
+        k_sets_per_inst<<<G(ctx, nsets), 256, 0, st>>>(nsets, soff, sids, bt->row_off, count, cnt);
+        GK_LAUNCH(ctx);
+    }
+    std::vector<unsigned long long> hc(count);
+    GK_CUDA(ctx, cudaMemcpyAsync(hc.data(), cnt, sizeof(unsigned long long) * count, cudaMemcpyDeviceToHost, st));
+    GK_CUDA(ctx, cudaStreamSynchronize(st));
+    std::vector<int64_t> ho(count), hp(count);
+    int64_t C = 0;
+    for (int i = 0; i < count; i++) {
+        int64_t c = 32;
+        while (c < 2 * (int64_t)hc[i]) c <<= 1;
+        ho[i] = C;
+        hp[i] = c;
+        C += c;
+    }
+    int64_t *roff, *rcap;
+    GK_TRY(scr.alloc(&roff, count));
+    GK_TRY(scr.alloc(&rcap, count));
+    GK_CUDA(ctx, cudaMemcpyAsync(roff, ho.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice, st));
+    GK_CUDA(ctx, cudaMemcpyAsync(rcap, hp.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice, st));
+    bt->slot_off = roff;
+    bt->slot_cap = rcap;
+    bt->slots = C;
     return GEEK_OK;
 }
 
@@ -914,6 +998,12 @@ geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p,
     GK_LAUNCH(ctx);
 
     t_vb.stop();
+    SilkBatch btl;  // batched: per-instance slot regions of the grouping tables
+    if (bt && bt->count > 1) {
+        btl = *bt;
+        GK_TRY(slot_regions(ctx, scr, NV, voff, vmem, &btl, st));
+        bt = &btl;
+    }
     // ---- Alg. 4: Ls SILK tables over the (virtual) buckets ------------------
     // SILK tables are processed in chunks of S (all at once when they fit the
     // position budget); bins of a chunk are numbered globally
