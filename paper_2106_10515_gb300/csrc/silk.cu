@@ -450,40 +450,91 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
 
 constexpr uint32_t SLOT_EMPTY = 0xFFFFFFFFu, SLOT_MULTI = 0x80000000u;
 
+// warp-aggregated append: one atomic per warp and list
+__device__ __forceinline__ unsigned long long warp_append(bool want, unsigned long long *counter) {
+    const unsigned mask = __ballot_sync(0xffffffffu, want);
+    if (!mask) return 0;
+    const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    return base + __popc(mask & ((1u << lane) - 1));
+}
+
 // Batched instances: instance i owns the slot region [roff[i], roff[i] +
 // rcap[i]) (rcap a power of two >= 2x its sets), so a block, whose sets mostly
-// belong to one instance, probes one small region.
+// belong to one instance, probes one small region.  A set that joins an
+// existing group appends itself to the multi list (key = segment * C + slot);
+// the groups' first sets are added by k_group_reps.
 __global__ void k_group_insert(int64_t NV, int64_t C, const uint64_t *__restrict__ klo,
                                const uint64_t *__restrict__ khi, const uint32_t *__restrict__ tag,
                                const int64_t *__restrict__ roff, const int64_t *__restrict__ rcap,
-                               uint32_t *__restrict__ slot, uint32_t *__restrict__ grp) {
+                               uint32_t *__restrict__ slot, uint64_t *__restrict__ mkey, uint32_t *__restrict__ mval,
+                               unsigned long long *__restrict__ n_multi) {
     const int t = blockIdx.y;
     const int64_t so = (int64_t)t * NV;
     uint32_t *sl = slot + (int64_t)t * C;
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < NV; g += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t lo = klo[so + g], hi = khi ? khi[so + g] : 0;
-        const uint32_t tg = tag ? tag[so + g] : 0;
-        const int64_t base = tag ? roff[tg] : 0;
-        const uint64_t mask = (uint64_t)(tag ? rcap[tg] : C) - 1;
-        uint64_t h = mix64(lo ^ mix64(hi + 0x9e3779b97f4a7c15ull * (uint64_t)(tg + 1))) & mask;
-        for (uint64_t probe = 0; probe <= mask; probe++) {
-            uint32_t cur = sl[base + h];
-            if (cur == SLOT_EMPTY) {
-                const uint32_t prev = atomicCAS(&sl[base + h], SLOT_EMPTY, (uint32_t)g);
-                if (prev == SLOT_EMPTY) {
-                    grp[so + g] = (uint32_t)(base + h);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // whole warps iterate together (the append is a warp collective)
+    for (int64_t gb = (int64_t)blockIdx.x * blockDim.x; gb < NV; gb += stride) {
+        const int64_t g = gb + threadIdx.x;
+        bool joined = false;
+        uint64_t key = 0;
+        if (g < NV) {
+            const uint64_t lo = klo[so + g], hi = khi ? khi[so + g] : 0;
+            const uint32_t tg = tag ? tag[so + g] : 0;
+            const int64_t base = tag ? roff[tg] : 0;
+            const uint64_t mask = (uint64_t)(tag ? rcap[tg] : C) - 1;
+            uint64_t h = mix64(lo ^ mix64(hi + 0x9e3779b97f4a7c15ull * (uint64_t)(tg + 1))) & mask;
+            for (uint64_t probe = 0; probe <= mask; probe++) {
+                uint32_t cur = sl[base + h];
+                if (cur == SLOT_EMPTY) {
+                    const uint32_t prev = atomicCAS(&sl[base + h], SLOT_EMPTY, (uint32_t)g);
+                    if (prev == SLOT_EMPTY) break;  // first set of a new group
+                    cur = prev;
+                }
+                const uint32_t r = cur & ~SLOT_MULTI;
+                if (klo[so + r] == lo && (!khi || khi[so + r] == hi) && (!tag || tag[so + r] == tg)) {
+                    if (!(cur & SLOT_MULTI)) atomicOr(&sl[base + h], SLOT_MULTI);
+                    joined = true;
+                    key = (uint64_t)t * (uint64_t)C + (uint64_t)(base + h);
                     break;
                 }
-                cur = prev;
+                h = (h + 1) & mask;
             }
-            const uint32_t r = cur & ~SLOT_MULTI;
-            if (klo[so + r] == lo && (!khi || khi[so + r] == hi) && (!tag || tag[so + r] == tg)) {
-                if (!(cur & SLOT_MULTI)) atomicOr(&sl[base + h], SLOT_MULTI);
-                grp[so + g] = (uint32_t)(base + h);
-                break;
-            }
-            h = (h + 1) & mask;
         }
+        const unsigned long long q = warp_append(joined, n_multi);
+        if (joined) {
+            mkey[q] = key;
+            mval[q] = (uint32_t)g;
+        }
+    }
+}
+
+// One pass over the slots: the first set of every group of >= 2 sets joins
+// the multi list; with delta <= 1 a set alone in its group with weight >= 2
+// is a bin of one virtual bucket that keeps the whole bucket (with delta >= 2
+// that rule cannot fire: weight >= 2 only for one-object buckets).
+__global__ void k_group_reps(int64_t C, int S, const uint32_t *__restrict__ slot, const int32_t *__restrict__ vw,
+                             const int64_t *__restrict__ voff, int delta, uint64_t *__restrict__ mkey,
+                             uint32_t *__restrict__ mval, unsigned long long *__restrict__ n_multi,
+                             int64_t *__restrict__ singles, unsigned long long *__restrict__ n_single) {
+    const int64_t tot = C * S;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < tot; b += stride) {
+        const int64_t e = b + threadIdx.x;
+        const uint32_t v = e < tot ? slot[e] : SLOT_EMPTY;
+        const bool used = v != SLOT_EMPTY;
+        const bool multi = used && (v & SLOT_MULTI);
+        const uint32_t g = v & ~SLOT_MULTI;
+        const bool single = used && !multi && delta <= 1 && vw[g] >= 2 && voff[g + 1] - voff[g] >= delta;
+        const unsigned long long qm = warp_append(multi, n_multi);
+        if (multi) {
+            mkey[qm] = (uint64_t)e;  // segment * C + slot
+            mval[qm] = g;
+        }
+        const unsigned long long qs = warp_append(single, n_single);
+        if (single) singles[qs] = g;
     }
 }
 
@@ -501,49 +552,6 @@ __global__ void k_sets_per_inst(int64_t nsets, const int64_t *__restrict__ soff,
     }
 }
 
-// warp-aggregated append: one atomic per warp and list
-__device__ __forceinline__ unsigned long long warp_append(bool want, unsigned long long *counter) {
-    const unsigned mask = __ballot_sync(0xffffffffu, want);
-    if (!mask) return 0;
-    const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
-    unsigned long long base = 0;
-    if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(mask));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    return base + __popc(mask & ((1u << lane) - 1));
-}
-
-// Positions of groups of >= 2 sets go to the multi list (key = segment * C +
-// slot, value = set); a set alone in its group with weight >= 2 and at least
-// delta members is a bin of one virtual bucket that keeps the whole bucket.
-__global__ void k_group_lists(int64_t NV, int S, int64_t C, const uint32_t *__restrict__ grp,
-                              const uint32_t *__restrict__ slot, const int32_t *__restrict__ vw,
-                              const int64_t *__restrict__ voff, int delta, uint64_t *__restrict__ mkey,
-                              uint32_t *__restrict__ mval, unsigned long long *__restrict__ n_multi,
-                              int64_t *__restrict__ singles, unsigned long long *__restrict__ n_single) {
-    const int64_t tot = NV * S;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // whole warps iterate together (the appends are warp collectives)
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < tot; base += stride) {
-        const int64_t p = base + threadIdx.x;
-        bool multi = false, single = false;
-        uint64_t key = 0;
-        int64_t g = 0;
-        if (p < tot) {
-            const int64_t t = p / NV;
-            g = p - t * NV;
-            key = (uint64_t)t * (uint64_t)C + grp[p];
-            multi = (slot[key] & SLOT_MULTI) != 0;
-            single = !multi && vw[g] >= 2 && voff[g + 1] - voff[g] >= delta;
-        }
-        const unsigned long long qm = warp_append(multi, n_multi);
-        if (multi) {
-            mkey[qm] = key;
-            mval[qm] = (uint32_t)g;
-        }
-        const unsigned long long qs = warp_append(single, n_single);
-        if (single) singles[qs] = g;
-    }
-}
 
 struct Csr {
     int64_t n = 0;        // sets
@@ -661,20 +669,12 @@ geek_status group_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const 
     }
     uint64_t *klo, *khi = nullptr;
     if (nsets >= (int64_t)SLOT_MULTI) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "more than 2^31 SILK sets");
-    uint32_t *tag = nullptr, *slot, *grp;
+    uint32_t *tag = nullptr, *slot;
     GK_TRY(scr.alloc(&klo, tot));
     if (Ks > 2) GK_TRY(scr.alloc(&khi, tot));
     if (tagged) GK_TRY(scr.alloc(&tag, tot));
     GK_TRY(scr.alloc(&slot, (size_t)S * C));
-    GK_TRY(scr.alloc(&grp, tot));
     GK_CUDA(ctx, cudaMemsetAsync(slot, 0xFF, sizeof(uint32_t) * S * C, st));
-    const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nsets, 256), (int64_t)ctx->num_sms * 8));
-    GK_COUNT();
-    k_set_sig<<<dim3(gx, S), 256, 0, st>>>(nsets, soff, sids, Ks, A, B, tagged ? bt->row_off : nullptr,
-                                           tagged ? bt->count : 1, coef_stride, klo, khi, nullptr, tag);
-    GK_COUNT();
-    k_group_insert<<<dim3(gx, S), 256, 0, st>>>(nsets, C, klo, khi, tag, roff, rcap, slot, grp);
-    GK_LAUNCH(ctx);
     uint64_t *mkey;
     uint32_t *mval;
     unsigned long long *counts;
@@ -683,9 +683,14 @@ geek_status group_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const 
     GK_TRY(scr.alloc(singles, tot));
     GK_TRY(scr.alloc(&counts, 2));
     GK_CUDA(ctx, cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), st));
+    const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nsets, 256), (int64_t)ctx->num_sms * 8));
     GK_COUNT();
-    k_group_lists<<<G(ctx, tot), 256, 0, st>>>(nsets, S, C, grp, slot, vw, soff, delta, mkey, mval, counts, *singles,
-                                               counts + 1);
+    k_set_sig<<<dim3(gx, S), 256, 0, st>>>(nsets, soff, sids, Ks, A, B, tagged ? bt->row_off : nullptr,
+                                           tagged ? bt->count : 1, coef_stride, klo, khi, nullptr, tag);
+    GK_COUNT();
+    k_group_insert<<<dim3(gx, S), 256, 0, st>>>(nsets, C, klo, khi, tag, roff, rcap, slot, mkey, mval, counts);
+    GK_COUNT();
+    k_group_reps<<<G(ctx, S * C), 256, 0, st>>>(C, S, slot, vw, soff, delta, mkey, mval, counts, *singles, counts + 1);
     GK_LAUNCH(ctx);
     unsigned long long h[2];
     GK_CUDA(ctx, cudaMemcpyAsync(h, counts, sizeof h, cudaMemcpyDeviceToHost, st));
