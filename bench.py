@@ -155,6 +155,17 @@ def run_ours(args):
         dist.barrier()
     from paper_2106_10515_gb300 import geek
 
+    if args.batch_only:
+        # the batched form alone (profiling runs); not the headline line
+        ctx = geek.Context(local)
+        pk, pk_kind = peaks()
+        b = bench_batched(args, geek, ctx, pk, pk_kind)
+        if rank == 0:
+            print(json.dumps({"metric": "points/sec, 256 batched dense instances (hash + SILK + assign)",
+                              "value": b["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                              "warmup": args.warmup, "batched": b}), flush=True)
+        return
+
     wl, t_gen = workload(args)
     cfg = wl["cfg"]
     ctx = geek.Context(local)
@@ -475,6 +486,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batch", action="store_true", help="skip the 256-instance batched measurement")
     ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--batch-only", action="store_true", help="run only the batched measurement (profiling)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours" and args.n is None:
         args.warmup = 3
