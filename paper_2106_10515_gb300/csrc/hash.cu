@@ -25,6 +25,9 @@ constexpr int PJ_FPT = 8;       // functions per thread
 constexpr int PJ_RPT = 8;       // rows per thread
 constexpr int PJ_MAXT = 256;    // threads per block (upper bound)
 
+// smallest stride >= v (a multiple of 4) with stride = 4 (mod 32)
+__host__ __device__ __forceinline__ int pj_stride(int v) { return v + ((36 - (v & 31)) & 31); }
+
 
 // One block: rows [tile * TR, tile * TR + TR) of one instance.  BATCH = false:
 // A describes the only instance (read from the parameter space, which the
@@ -58,8 +61,11 @@ __global__ void __launch_bounds__(PJ_MAXT) k_project_fp32(ProjArgs A, const Proj
     }
     extern __shared__ float sm[];
     const int TR = A.RG * PJ_RPT;
-    float *xs = sm;                       // [PJ_KC][TR]
-    float *as = sm + PJ_KC * TR;          // [PJ_KC][FPAD]
+    // k-major stages; row strides padded to 4 (mod 32) floats so that the
+    // float4 stores of 8 consecutive k (a quarter warp) hit distinct banks
+    const int TRS = pj_stride(TR), FPS = pj_stride(A.FPAD);
+    float *xs = sm;                       // [PJ_KC][TRS]
+    float *as = sm + PJ_KC * TRS;         // [PJ_KC][FPS]
     __shared__ int smin[512], smax[512];  // F <= 512 checked on the host
     const int t = threadIdx.x;
     const int nthr = A.FG * A.RG;
@@ -80,28 +86,38 @@ __global__ void __launch_bounds__(PJ_MAXT) k_project_fp32(ProjArgs A, const Proj
     }
     for (int k0 = 0; k0 < A.d; k0 += PJ_KC) {
         __syncthreads();
-        // stage X chunk transposed: xs[kk][r]
-        for (int e = t; e < TR * PJ_KC; e += blockDim.x) {
-            int r = e / PJ_KC, kk = e % PJ_KC;
-            int64_t row = row0 + r;
-            float v = 0.f;
-            if (row < A.n && k0 + kk < A.d) v = A.x[row * A.ldx + k0 + kk];
-            xs[kk * TR + r] = v;
+        // stage X and A chunks transposed: xs[kk][r], as[kk][f]; a thread
+        // loads 4 consecutive rows (functions) of one column (lanes run
+        // along k: coalesced) and stores them as one float4
+        for (int e = t; e < (TR / 4) * PJ_KC; e += blockDim.x) {
+            const int r4 = (e / PJ_KC) * 4, kk = e % PJ_KC;
+            const bool kin = k0 + kk < A.d;
+            float4 v;
+            float *vp = reinterpret_cast<float *>(&v);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int64_t row = row0 + r4 + q;
+                vp[q] = (row < A.n && kin) ? A.x[row * A.ldx + k0 + kk] : 0.f;
+            }
+            *reinterpret_cast<float4 *>(&xs[kk * TRS + r4]) = v;
         }
-        for (int e = t; e < A.FPAD * PJ_KC; e += blockDim.x) {
-            int f = e / PJ_KC, kk = e % PJ_KC;
-            float v = 0.f;
-            if (f < A.F && k0 + kk < A.d) v = A.a[(int64_t)f * A.d + k0 + kk];
-            as[kk * A.FPAD + f] = v;
+        for (int e = t; e < (A.FPAD / 4) * PJ_KC; e += blockDim.x) {
+            const int f4 = (e / PJ_KC) * 4, kk = e % PJ_KC;
+            const bool kin = k0 + kk < A.d;
+            float4 v;
+            float *vp = reinterpret_cast<float *>(&v);
+#pragma unroll
+            for (int q = 0; q < 4; q++) vp[q] = (f4 + q < A.F && kin) ? A.a[(int64_t)(f4 + q) * A.d + k0 + kk] : 0.f;
+            *reinterpret_cast<float4 *>(&as[kk * FPS + f4]) = v;
         }
         __syncthreads();
         if (active) {
             const int kmax = min(PJ_KC, A.d - k0);
             for (int kk = 0; kk < kmax; kk++) {
-                const float4 x0 = *reinterpret_cast<const float4 *>(&xs[kk * TR + rg * PJ_RPT]);
-                const float4 x1 = *reinterpret_cast<const float4 *>(&xs[kk * TR + rg * PJ_RPT + 4]);
-                const float4 a0 = *reinterpret_cast<const float4 *>(&as[kk * A.FPAD + fg * PJ_FPT]);
-                const float4 a1 = *reinterpret_cast<const float4 *>(&as[kk * A.FPAD + fg * PJ_FPT + 4]);
+                const float4 x0 = *reinterpret_cast<const float4 *>(&xs[kk * TRS + rg * PJ_RPT]);
+                const float4 x1 = *reinterpret_cast<const float4 *>(&xs[kk * TRS + rg * PJ_RPT + 4]);
+                const float4 a0 = *reinterpret_cast<const float4 *>(&as[kk * FPS + fg * PJ_FPT]);
+                const float4 a1 = *reinterpret_cast<const float4 *>(&as[kk * FPS + fg * PJ_FPT + 4]);
                 const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
                 const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
 #pragma unroll
@@ -574,7 +590,9 @@ static void proj_layout(ProjArgs &A, int F) {
 }
 static int proj_rows(const ProjArgs &A) { return A.RG * PJ_RPT; }
 static int proj_threads(const ProjArgs &A) { return (int)ceil_div(A.FG * A.RG, 32) * 32; }  // whole warps
-static size_t proj_smem(const ProjArgs &A) { return (size_t)PJ_KC * (proj_rows(A) + A.FPAD) * sizeof(float); }
+static size_t proj_smem(const ProjArgs &A) {
+    return (size_t)PJ_KC * (pj_stride(proj_rows(A)) + pj_stride(A.FPAD)) * sizeof(float);
+}
 
 geek_status project_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ldx, int64_t n,
                           int d, const float *a, const float *b, int F, double w, int srp,
