@@ -126,8 +126,10 @@ __global__ void __launch_bounds__(256) k_digit_base(uint32_t *__restrict__ dtot)
 // the block turns the per-warp counts into tile offsets, the tile is staged
 // in shared memory in (digit, input order), and written out contiguously per
 // digit: coalesced stores, stable order, three block barriers per tile.
+// (3 blocks per SM: the scatter is latency bound, and occupancy is worth
+// the few registers spilled)
 template <bool HI, bool VALS>
-__global__ void __launch_bounds__(RS_THREADS)
+__global__ void __launch_bounds__(RS_THREADS, 3)
     k_rs_scatter(const uint64_t *__restrict__ lo_in, const uint64_t *__restrict__ hi_in,
                  const uint32_t *__restrict__ v_in, uint64_t *__restrict__ lo_out,
                  uint64_t *__restrict__ hi_out, uint32_t *__restrict__ v_out, int64_t m, int tiles,
