@@ -31,8 +31,8 @@
 // kernel; CUtensorMap's 64-byte alignment keeps every array element aligned.
 struct TcInst {
     CUtensorMap tmA;             // Xb: {Kp, n} bf16, box {64, 128}
-    CUtensorMap tmB;             // Cb: {Kp, kpad} bf16, box {64, N}
-    const float *cn;             // kpad: |c|^2 (+inf for padding)
+    CUtensorMap tmB;             // Cb = -2 c: {Kp, kpad} bf16, box {64, N}
+    CUtensorMap tmX;             // |c|^2 columns: {16, kpad} bf16, box {16, N}, 32-byte swizzle
     const float *xnorm;          // n: upper bound of |x|
     const unsigned *cmax_bits;   // max over real centres of |c|^2 (FP32 bits)
     int32_t *labels;             // n
@@ -54,8 +54,9 @@ struct TcCPrep {
     int64_t k, kpad;
     int d, Kp;
     int split;
-    __nv_bfloat16 *cb;  // kpad x Kp (x 2 when split)
-    float *cn;          // kpad
+    __nv_bfloat16 *cb;  // kpad x Kp (x 2 when split): -2 c
+    __nv_bfloat16 *cbx; // kpad x 16: |c|^2 as bf16 hi, mid, lo, then zeros
+    float *cn;          // kpad: |c|^2 in FP32 (for max |c|)
     unsigned *cmax_bits;
 };
 
@@ -139,13 +140,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *tm,
         : "memory");
 }
 
-// untiled bulk copy global -> shared (16-byte aligned addresses and size)
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"((uint64_t)src), "r"(bytes), "r"(su32(bar))
-                 : "memory");
-}
-
 __device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
@@ -172,6 +166,17 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     return d;
 }
 
+// K-major operand of one 16-element k-step, 32-byte swizzle: rows of 32 B,
+// 8-row atoms of 256 B.
+__device__ __forceinline__ uint64_t sdesc32(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;            // leading byte offset (unused: K fits the swizzle width)
+    d |= (uint64_t)(256 >> 4) << 32;   // stride byte offset: 8 rows x 32 B
+    d |= (uint64_t)1 << 46;            // descriptor version for tcgen05
+    d |= (uint64_t)6 << 61;            // 32-byte swizzle
+    return d;
+}
+
 // instruction descriptor: kind::f16, A = B = BF16, D = F32, both K-major
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
@@ -188,19 +193,6 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                  : "memory");
 }
 
-// d = -2 a + c on two lanes at once (fma.rn.f32x2: the same per-lane
-// rounding as fmaf(-2.f, a, c))
-__device__ __forceinline__ void ffma2_m2(float a0, float a1, float c0, float c1, float &d0, float &d1) {
-    asm("{ .reg .b64 ra, rc, rm, rd;\n\t"
-        "mov.b64 ra, {%2, %3};\n\t"
-        "mov.b64 rc, {%4, %5};\n\t"
-        "mov.b64 rm, {%6, %6};\n\t"
-        "fma.rn.f32x2 rd, rm, ra, rc;\n\t"
-        "mov.b64 {%0, %1}, rd; }"
-        : "=f"(d0), "=f"(d1)
-        : "f"(a0), "f"(a1), "f"(c0), "f"(c1), "f"(-2.f));
-}
-
 // three-input minimum
 __device__ __forceinline__ float min3f(float a, float b, float c) {
     float d;
@@ -208,17 +200,21 @@ __device__ __forceinline__ float min3f(float a, float b, float c) {
     return d;
 }
 
-// Rigorous half-window of the BF16 path for one object:
-//   inputs rounded to bf16 (u_b = 2^-8):    2 (2 u_b + u_b^2) |x| cmax
-//   FP32 accumulation in the tensor core:   2 (d + 16) 2^-21 |x| cmax
-//   |c|^2 rounded to FP32 and the final FMA: u cmax^2 + u (2 |x| cmax (1 + 2 u_b) + cmax^2)
-//   the FP64 reference's own error:         (d + 3) 2^-53 (|x| + cmax)^2
+// Rigorous half-window of the BF16 path for one object.  The accumulator
+// holds |c|^2 - 2 x_h.c_h summed by the tensor core: -2 c is exact in BF16,
+// and |c|^2 enters as hi + mid + lo BF16 terms (within 2^-24 |c|^2) times one.
+//   inputs rounded to bf16 (u_b = 2^-8):     2 (2 u_b + u_b^2) |x| cmax
+//   |c|^2 split:                             2^-24 cmax^2
+//   the tensor core's accumulation of the d + 3 products, bounded loosely
+//   by (d + 19) 2^-21 of the sum of their magnitudes:
+//                                            (d + 19) 2^-21 (2 |x| cmax + cmax^2)(1 + 2 u_b)
+//   the FP64 reference's own error:          (d + 3) 2^-53 (|x| + cmax)^2
 // times 1.01 for second-order terms.
 __device__ __forceinline__ float window_bf16(float xn, float cmax, int d) {
-    const float ub = 0.00390625f, u = 5.9604645e-8f;
-    const float xc = xn * cmax;
-    const float e = 2.f * (2.f * ub + ub * ub) * xc + 2.f * (float)(d + 16) * 4.76837158e-7f * xc +
-                    u * cmax * cmax + u * (2.f * xc * (1.f + 2.f * ub) + cmax * cmax);
+    const float ub = 0.00390625f;
+    const float xc = xn * cmax, c2 = cmax * cmax;
+    const float e = 2.f * (2.f * ub + ub * ub) * xc + 5.9604645e-8f * c2 +
+                    (float)(d + 19) * 4.76837158e-7f * (2.f * xc + c2) * (1.f + 2.f * ub);
     const float s = xn + cmax;
     const float e64 = (float)(d + 3) * 1.1102230e-16f * s * s;
     return 1.01f * (e + e64) + 1e-30f;
@@ -228,15 +224,14 @@ __device__ __forceinline__ float window_bf16(float xn, float cmax, int d) {
 // bf16(x - x_h) (and the same for c), x.c - (x_h.c_h + x_l.c_h + x_h.c_l) =
 // -(x - x_h - x_l).c_h - x_h.(c - c_h - c_l) + (x - x_h).(c - c_h), each
 // term bounded by u_b^2 (1 + u_b) |x| |c|: input term 2 * 3 u_b^2 (1 + u_b)
-// |x| cmax; the tensor core's accumulation over 3d products
-// 2 (3d + 16) 2^-21 (1 + 4 u_b) |x| cmax; the |c|^2, FMA and FP64 reference
-// terms as in window_bf16; times 1.01.
+// |x| cmax; the |c|^2 split 2^-24 cmax^2; the accumulation of 3d + 3
+// products (3d + 19) 2^-21 (2 |x| cmax (1 + 4 u_b) + cmax^2 (1 + 2 u_b)); the
+// FP64 reference term as in window_bf16; times 1.01.
 __device__ __forceinline__ float window_bf16x3(float xn, float cmax, int d) {
-    const float ub = 0.00390625f, u = 5.9604645e-8f;
-    const float xc = xn * cmax;
-    const float e = 6.f * ub * ub * (1.f + ub) * xc +
-                    2.f * (float)(3 * d + 16) * 4.76837158e-7f * (1.f + 4.f * ub) * xc + u * cmax * cmax +
-                    u * (2.f * xc * (1.f + 2.f * ub) + cmax * cmax);
+    const float ub = 0.00390625f;
+    const float xc = xn * cmax, c2 = cmax * cmax;
+    const float e = 6.f * ub * ub * (1.f + ub) * xc + 5.9604645e-8f * c2 +
+                    (float)(3 * d + 19) * 4.76837158e-7f * (2.f * xc * (1.f + 4.f * ub) + c2 * (1.f + 2.f * ub));
     const float s = xn + cmax;
     const float e64 = (float)(d + 3) * 1.1102230e-16f * s * s;
     return 1.01f * (e + e64) + 1e-30f;
@@ -252,8 +247,8 @@ __device__ __forceinline__ float window_bf16x3(float xn, float cmax, int d) {
 // only lowers b2o.  So min(b2o, second smallest of sv) is exactly the
 // runner-up over all columns.
 template <int NCH>
-__device__ __forceinline__ void epi_tile(uint32_t tbase, const float *cnt, int64_t jb, float &b1, float &b2o,
-                                         float (&sv)[32], int64_t &sj) {
+__device__ __forceinline__ void epi_tile(uint32_t tbase, int64_t jb, float &b1, float &b2o, float (&sv)[32],
+                                         int64_t &sj) {
     uint32_t ra[32], rb[32];
     tmem_ld32_async(tbase, ra);
     tmem_wait_ld();
@@ -264,16 +259,9 @@ __device__ __forceinline__ void epi_tile(uint32_t tbase, const float *cnt, int64
             else tmem_ld32_async(tbase + (ch + 1) * 32, rb);
         }
         const uint32_t *r = (ch & 1) ? rb : ra;
-        const float4 *cn4 = reinterpret_cast<const float4 *>(cnt + ch * 32);
-        float v[32];
+        float v[32];  // d' = |c|^2 - 2 x.c, straight from the accumulator
 #pragma unroll
-        for (int i = 0; i < 8; i++) {
-            const float4 cc = cn4[i];
-            ffma2_m2(__uint_as_float(r[4 * i + 0]), __uint_as_float(r[4 * i + 1]), cc.x, cc.y, v[4 * i + 0],
-                     v[4 * i + 1]);
-            ffma2_m2(__uint_as_float(r[4 * i + 2]), __uint_as_float(r[4 * i + 3]), cc.z, cc.w, v[4 * i + 2],
-                     v[4 * i + 3]);
-        }
+        for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
         float t11[11];
 #pragma unroll
         for (int i = 0; i < 10; i++) t11[i] = min3f(v[3 * i], v[3 * i + 1], v[3 * i + 2]);
@@ -329,10 +317,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
     uint64_t *bars = (uint64_t *)(base + 2 * TC_A_STAGE + 2 * TC_B_STAGE);
     uint64_t *full_a = bars, *empty_a = bars + 2, *full_b = bars + 4, *empty_b = bars + 6;
     uint64_t *full_acc = bars + 8, *empty_acc = bars + 10, *done_bar = bars + 12;
-    uint64_t *full_cn = bars + 13;  // 4 slots
     uint32_t *tmem_slot = (uint32_t *)(bars + 17);
     float *mrg = (float *)(bars + 32);  // [groups-1][128][3] results of column groups 1..
-    float *cn_s = (float *)(base + 2 * TC_A_STAGE + 2 * TC_B_STAGE + TC_MISC);  // [4][256] |c|^2 ring
+    // |c|^2 columns: an all-ones X block (128 x 16) and per stage the centres'
+    // (hi, mid, lo, 0...) rows (N x 16), 32-byte swizzled; one extra K = 16
+    // step adds |c|^2 to every accumulator column
+    uint8_t *sOnes = base + 2 * TC_A_STAGE + 2 * TC_B_STAGE + TC_MISC;  // 4 KB
+    uint8_t *sX0 = sOnes + TC_M * 32;                                   // [2][TC_N * 32]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -345,10 +336,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
             mbar_init(&empty_acc[i], TC_EPI_WARPS);
         }
         mbar_init(done_bar, 1);
-        for (int i = 0; i < 4; i++) mbar_init(&full_cn[i], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
+    // the all-ones block (1.0 in BF16 everywhere, so its swizzle is moot)
+    for (int e = threadIdx.x; e < TC_M * 32 / 4; e += blockDim.x)
+        reinterpret_cast<uint32_t *>(sOnes)[e] = 0x3F803F80u;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
                      "r"(TC_TMEM_COLS)
@@ -367,7 +360,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
             uint64_t ct = 0;
-            uint32_t issued_b[2] = {0, 0}, issued_cn[4] = {0, 0, 0, 0};
+            uint32_t issued_b[2] = {0, 0};
             bool ok = true;
             int64_t it = 0;
             for (int64_t u = blockIdx.x; u < A.nunits && ok; u += gridDim.x, it++) {
@@ -386,25 +379,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
                     const int s = (int)(ct & 1);
                     const uint32_t uu = (uint32_t)(ct >> 1);
                     if (!(ok = mbar_wait(&empty_b[s], (uu & 1) ^ 1, A.err))) break;
-                    mbar_expect_tx(&full_b[s], b_bytes);
+                    mbar_expect_tx(&full_b[s], b_bytes + (uint32_t)N * 32);
                     for (int kb = 0; kb < nkb; kb++)
                         tma_load_2d(su32(sB0 + s * B_ST + kb * N * 128), &I.tmB, kb * TC_KB, c * N, &full_b[s]);
+                    tma_load_2d(su32(sX0 + s * TC_N * 32), &I.tmX, 0, c * N, &full_b[s]);
                     issued_b[s] = uu + 1;
-                    // |c|^2 of this centre tile into ring slot ct % 4.  The
-                    // epilogue of tile ct - 4, the last reader of the slot,
-                    // finished before the MMA of tile ct - 2 started, which
-                    // finished before empty_b let this tile in.
-                    const int cs = (int)(ct & 3);
-                    mbar_expect_tx(&full_cn[cs], N * 4);
-                    bulk_load(su32(cn_s + cs * TC_N), I.cn + (int64_t)c * N, N * 4, &full_cn[cs]);
-                    issued_cn[cs] = (uint32_t)(ct >> 2) + 1;
                 }
             }
             // drain: every centre-tile copy this thread issued has landed
             for (int s = 0; s < 2; s++)
                 if (issued_b[s]) mbar_wait(&full_b[s], (issued_b[s] - 1) & 1, A.err, true);
-            for (int s = 0; s < 4; s++)
-                if (issued_cn[s]) mbar_wait(&full_cn[s], (issued_cn[s] - 1) & 1, A.err, true);
         }
         __syncwarp();
     } else if (warp == 1) {
@@ -441,6 +425,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
                                 mma_bf16(dtm, sdesc(a_base + ao), sdesc(b_base + bo + nkb * N * 128), idesc, 1);
                             }
                         }
+                    // + |c|^2: ones (128 x 16) times the centres' (hi, mid, lo, 0...)
+                    mma_bf16(dtm, sdesc32(su32(sOnes)), sdesc32(su32(sX0 + s * TC_N * 32)), idesc, 1);
                     mma_commit(&empty_b[s]);
                     mma_commit(&full_acc[s]);
                 }
@@ -475,21 +461,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
             for (int c = 0; c < I.ntiles_c; c++, ct++) {
                 const int s = (int)(ct & 1);
                 const uint32_t uu = (uint32_t)(ct >> 1);
-                const int cs = (int)(ct & 3);
                 int w_ok = 0;
-                if (lane == 0 && ok)
-                    w_ok = mbar_wait(&full_acc[s], uu & 1, A.err) &&
-                           mbar_wait(&full_cn[cs], (uint32_t)(ct >> 2) & 1, A.err);
+                if (lane == 0 && ok) w_ok = mbar_wait(&full_acc[s], uu & 1, A.err);
                 w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
                 ok = ok && w_ok;
                 if (ok) {
                     fence_after();
                     const uint32_t tbase = tmem + (uint32_t)(s * TC_N + h * gcols) + ((uint32_t)(32 * q) << 16);
-                    const float *cnt = cn_s + cs * TC_N + h * gcols;
                     const int64_t jb = (int64_t)c * N + h * gcols;
-                    if (nch == 4) epi_tile<4>(tbase, cnt, jb, b1, b2o, sv, sj);
-                    else if (nch == 2) epi_tile<2>(tbase, cnt, jb, b1, b2o, sv, sj);
-                    else epi_tile<1>(tbase, cnt, jb, b1, b2o, sv, sj);
+                    if (nch == 4) epi_tile<4>(tbase, jb, b1, b2o, sv, sj);
+                    else if (nch == 2) epi_tile<2>(tbase, jb, b1, b2o, sv, sj);
+                    else epi_tile<1>(tbase, jb, b1, b2o, sv, sj);
                     fence_before();
                 }
                 __syncwarp();
@@ -583,14 +565,32 @@ __global__ void k_c_to_bf16(const TcCPrep *__restrict__ C, const int64_t *__rest
         const int W = P.split ? 2 * P.Kp : P.Kp;
         double s = 0.0;
         for (int t = 0; t < P.Kp; t++) {
+            // -2 c: scaling by a power of two is exact in BF16
             const double v = (j < P.k && t < P.d) ? P.c[j * P.d + t] : 0.0;
-            const __nv_bfloat16 h = __double2bfloat16(v);
+            const __nv_bfloat16 h = __double2bfloat16(-2.0 * v);
             P.cb[j * W + t] = h;
-            if (P.split) P.cb[j * W + P.Kp + t] = __double2bfloat16(v - (double)__bfloat162float(h));  // exact
+            if (P.split) P.cb[j * W + P.Kp + t] = __double2bfloat16(-2.0 * v - (double)__bfloat162float(h));  // exact
             s += v * v;
         }
+        // |c|^2 = hi + mid + lo in BF16 (within 2^-24 |c|^2); padding: +inf,
+        // which never wins
+        __nv_bfloat16 *xr = P.cbx + j * 16;
+        if (j < P.k) {
+            const __nv_bfloat16 h = __double2bfloat16(s);
+            const double r1 = s - (double)__bfloat162float(h);
+            const __nv_bfloat16 m = __double2bfloat16(r1);
+            const double r2 = r1 - (double)__bfloat162float(m);
+            xr[0] = h;
+            xr[1] = m;
+            xr[2] = __double2bfloat16(r2);
+        } else {
+            xr[0] = __ushort_as_bfloat16((unsigned short)0x7F80);
+            xr[1] = __ushort_as_bfloat16((unsigned short)0);
+            xr[2] = __ushort_as_bfloat16((unsigned short)0);
+        }
+        for (int t = 3; t < 16; t++) xr[t] = __ushort_as_bfloat16((unsigned short)0);
         const float f = (float)s;
-        P.cn[j] = j < P.k ? f : __int_as_float(0x7f800000);  // +inf: padding never wins
+        P.cn[j] = j < P.k ? f : __int_as_float(0x7f800000);
         if (j < P.k) atomicMax(P.cmax_bits, __float_as_uint(f));  // non-negative floats order as uints
     }
 }
@@ -600,7 +600,8 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 geek_status encode_bf16_2d(geek_ctx *ctx, CUtensorMap *tm, void *ptr, uint64_t inner, uint64_t outer,
-                           uint32_t box_inner, uint32_t box_outer) {
+                           uint32_t box_inner, uint32_t box_outer,
+                           CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {
     static EncodeTiledFn fn = nullptr;
     if (!fn) {
         cudaDriverEntryPointQueryResult q;
@@ -616,7 +617,7 @@ geek_status encode_bf16_2d(geek_ctx *ctx, CUtensorMap *tm, void *ptr, uint64_t i
     const cuuint32_t box[2] = {box_inner, box_outer};
     const cuuint32_t es[2] = {1, 1};
     CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, es,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(ctx, GEEK_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return GEEK_OK;
@@ -663,7 +664,7 @@ geek_status make_inst(geek_ctx *ctx, const TcPlan &P, int i, int N, TcInst *out)
         return set_error(ctx, GEEK_ERR_INVALID, "split-BF16 tiles need N * Kp <= 8192 (N %d, Kp %d)", N, Kp);
     if (I.n > 0) GK_TRY(encode_bf16_2d(ctx, &T.tmA, xp.xb, Kst, I.n, TC_KB, TC_M));
     if (I.k > 0) GK_TRY(encode_bf16_2d(ctx, &T.tmB, cp.cb, Kst, cp.kpad, TC_KB, N));
-    T.cn = cp.cn;
+    if (I.k > 0) GK_TRY(encode_bf16_2d(ctx, &T.tmX, cp.cbx, 16, cp.kpad, 16, N, CU_TENSOR_MAP_SWIZZLE_32B));
     T.xnorm = P.xnorm + I.row_base;
     T.cmax_bits = cp.cmax_bits;
     T.labels = I.labels;
@@ -700,7 +701,9 @@ void make_units(const TcPlan &P, const std::vector<int> &which, int split, std::
 size_t tc_smem() {
     static_assert(32 * 8 + (TC_EPI_GROUPS - 1) * TC_M * 3 * 4 <= TC_MISC, "misc region too small");
     // tile stages + barriers / TMEM slot / merge buffer + |c|^2 ring + alignment
-    return 1024 + 2 * (size_t)TC_A_STAGE + 2 * (size_t)TC_B_STAGE + TC_MISC + 4 * TC_N * 4;
+    // tile stages + barriers / TMEM slot / merge buffer + ones block + two
+    // |c|^2 stages + alignment
+    return 1024 + 2 * (size_t)TC_A_STAGE + 2 * (size_t)TC_B_STAGE + TC_MISC + TC_M * 32 + 2 * TC_N * 32;
 }
 
 }  // namespace
@@ -737,11 +740,12 @@ geek_status tc_plan_build(geek_ctx *ctx, Scratch *scr, const std::vector<TcPlanI
     P->N_total = row_off[count];
     P->kpad_total = im.kpad_off[count];
     auto &own = P->owned;
-    __nv_bfloat16 *xb, *cb;
+    __nv_bfloat16 *xb, *cb, *cbx;
     float *cn;
     unsigned *cmax_bits;
     GK_TRY(plan_alloc(ctx, scr, own, &xb, (size_t)std::max<int64_t>(xb_total, 1)));
     GK_TRY(plan_alloc(ctx, scr, own, &cb, (size_t)std::max<int64_t>(cb_total, 1)));
+    GK_TRY(plan_alloc(ctx, scr, own, &cbx, (size_t)std::max<int64_t>(im.kpad_off[count] * 16, 1)));
     GK_TRY(plan_alloc(ctx, scr, own, &P->xnorm, (size_t)std::max<int64_t>(P->N_total, 1)));
     GK_TRY(plan_alloc(ctx, scr, own, &cn, (size_t)std::max<int64_t>(P->kpad_total, 1)));
     GK_TRY(plan_alloc(ctx, scr, own, &cmax_bits, (size_t)count));
@@ -761,7 +765,8 @@ geek_status tc_plan_build(geek_ctx *ctx, Scratch *scr, const std::vector<TcPlanI
         const int Kst = (I.split || P->allow_split) ? 2 * Kp : Kp;
         im.xp[i] = TcXPrep{I.x, I.ldx, I.d, Kp, I.split, xb + xo};
         const int64_t kpad = im.kpad_off[i + 1] - im.kpad_off[i];
-        im.cp[i] = TcCPrep{I.centres, I.k, kpad, I.d, Kp, I.split, cb + co, cn + im.kpad_off[i], cmax_bits + i};
+        im.cp[i] = TcCPrep{I.centres, I.k, kpad, I.d, Kp, I.split, cb + co, cbx + im.kpad_off[i] * 16,
+                           cn + im.kpad_off[i], cmax_bits + i};
         xo += I.n * Kst;
         co += kpad * Kst;
     }
