@@ -25,8 +25,6 @@ constexpr int PJ_FPT = 8;       // functions per thread
 constexpr int PJ_RPT = 8;       // rows per thread
 constexpr int PJ_MAXT = 256;    // threads per block (upper bound)
 
-// smallest stride >= v (a multiple of 4) with stride = 4 (mod 32)
-__host__ __device__ __forceinline__ int pj_stride(int v) { return v + ((36 - (v & 31)) & 31); }
 
 
 // One block: rows [tile * TR, tile * TR + TR) of one instance.  BATCH = false:
@@ -36,7 +34,7 @@ __host__ __device__ __forceinline__ int pj_stride(int v) { return v + ((36 - (v 
 // sizes P[i] replace A's; the thread layout (F, FPAD, FG, RG) and the flag
 // list are common to the batch and stay A's.
 template <bool BATCH>
-__global__ void __launch_bounds__(PJ_MAXT) k_project_fp32(ProjArgs A, const ProjArgs *__restrict__ P,
+__global__ void __launch_bounds__(PJ_MAXT, 2) k_project_fp32(ProjArgs A, const ProjArgs *__restrict__ P,
                                                           const int64_t *__restrict__ tile_off, int count) {
     int64_t tile = blockIdx.x;
     if (BATCH) {
@@ -61,11 +59,13 @@ __global__ void __launch_bounds__(PJ_MAXT) k_project_fp32(ProjArgs A, const Proj
     }
     extern __shared__ float sm[];
     const int TR = A.RG * PJ_RPT;
-    // k-major stages; row strides padded to 4 (mod 32) floats so that the
-    // float4 stores of 8 consecutive k (a quarter warp) hit distinct banks
-    const int TRS = pj_stride(TR), FPS = pj_stride(A.FPAD);
-    float *xs = sm;                       // [PJ_KC][TRS]
-    float *as = sm + PJ_KC * TRS;         // [PJ_KC][FPS]
+    // Two stages of row-major chunks, 32 k-values (128 B) per row: xs [TR][32]
+    // and as [FPAD][32].  The 16-byte piece j of row r sits at position
+    // j ^ ((r >> 3) & 7), so the float4 reads of a quarter warp (rows 8
+    // apart) fall in different banks.  With 16-byte aligned rows the stages
+    // are filled by cp.async one chunk ahead of the arithmetic.
+    const int SR = TR + A.FPAD;  // rows per stage
+    float *st0 = sm, *st1 = sm + (size_t)SR * PJ_KC;
     __shared__ int smin[512], smax[512];  // F <= 512 checked on the host
     const int t = threadIdx.x;
     const int nthr = A.FG * A.RG;
@@ -84,50 +84,79 @@ __global__ void __launch_bounds__(PJ_MAXT) k_project_fp32(ProjArgs A, const Proj
 #pragma unroll
         for (int c = 0; c < PJ_FPT; c++) acc[r][c] = 0.f;
     }
-    for (int k0 = 0; k0 < A.d; k0 += PJ_KC) {
-        __syncthreads();
-        // stage X and A chunks transposed: xs[kk][r], as[kk][f]; a thread
-        // loads 4 consecutive rows (functions) of one column (lanes run
-        // along k: coalesced) and stores them as one float4
-        for (int e = t; e < (TR / 4) * PJ_KC; e += blockDim.x) {
-            const int r4 = (e / PJ_KC) * 4, kk = e % PJ_KC;
-            const bool kin = k0 + kk < A.d;
-            float4 v;
-            float *vp = reinterpret_cast<float *>(&v);
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const int64_t row = row0 + r4 + q;
-                vp[q] = (row < A.n && kin) ? A.x[row * A.ldx + k0 + kk] : 0.f;
+    const bool vec = ((A.ldx & 3) == 0) && ((A.d & 3) == 0) && (((uintptr_t)A.x & 15) == 0) &&
+                     (((uintptr_t)A.a & 15) == 0);
+    // fills stage `buf` with the chunk at k0: rows 0..TR-1 from X, then FPAD
+    // rows from A (zeros outside the data)
+    auto stage = [&](float *buf, int k0) {
+        for (int e = t; e < SR * 8; e += blockDim.x) {
+            const int r = e >> 3, j = e & 7;
+            const int k = k0 + 4 * j;
+            const float *src = nullptr;
+            bool in = false;
+            int sw;  // row index within its own matrix (the swizzle key)
+            if (r < TR) {
+                const int64_t row = row0 + r;
+                in = row < A.n;
+                src = A.x + row * A.ldx + k;
+                sw = r;
+            } else {
+                const int f = r - TR;
+                in = f < A.F;
+                src = A.a + (int64_t)f * A.d + k;
+                sw = f;
             }
-            *reinterpret_cast<float4 *>(&xs[kk * TRS + r4]) = v;
-        }
-        for (int e = t; e < (A.FPAD / 4) * PJ_KC; e += blockDim.x) {
-            const int f4 = (e / PJ_KC) * 4, kk = e % PJ_KC;
-            const bool kin = k0 + kk < A.d;
-            float4 v;
-            float *vp = reinterpret_cast<float *>(&v);
+            float *dst = buf + r * PJ_KC + 4 * (j ^ ((sw >> 3) & 7));
+            const int nv = in ? max(0, min(4, A.d - k)) : 0;
+            if (vec) {
+                const uint32_t sa = (uint32_t)__cvta_generic_to_shared(dst);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(nv ? src : A.x),
+                             "r"(nv * 4)
+                             : "memory");
+            } else {
 #pragma unroll
-            for (int q = 0; q < 4; q++) vp[q] = (f4 + q < A.F && kin) ? A.a[(int64_t)(f4 + q) * A.d + k0 + kk] : 0.f;
-            *reinterpret_cast<float4 *>(&as[kk * FPS + f4]) = v;
+                for (int q = 0; q < 4; q++) dst[q] = q < nv ? src[q] : 0.f;
+            }
+        }
+        if (vec) asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    const int nchunks = (A.d + PJ_KC - 1) / PJ_KC;
+    stage(st0, 0);
+    for (int ci = 0; ci < nchunks; ci++) {
+        float *cur = (ci & 1) ? st1 : st0;
+        if (ci + 1 < nchunks) {
+            stage((ci & 1) ? st0 : st1, (ci + 1) * PJ_KC);
+            if (vec) asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else if (vec) {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
         __syncthreads();
         if (active) {
-            const int kmax = min(PJ_KC, A.d - k0);
-            for (int kk = 0; kk < kmax; kk++) {
-                const float4 x0 = *reinterpret_cast<const float4 *>(&xs[kk * TRS + rg * PJ_RPT]);
-                const float4 x1 = *reinterpret_cast<const float4 *>(&xs[kk * TRS + rg * PJ_RPT + 4]);
-                const float4 a0 = *reinterpret_cast<const float4 *>(&as[kk * FPS + fg * PJ_FPT]);
-                const float4 a1 = *reinterpret_cast<const float4 *>(&as[kk * FPS + fg * PJ_FPT + 4]);
-                const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-                const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float *xb = cur, *ab = cur + (size_t)TR * PJ_KC;
+            const int kmax = min(PJ_KC, A.d - ci * PJ_KC);
+            for (int jb = 0; jb < (kmax + 3) / 4; jb++) {
+                float4 xv[PJ_RPT];
 #pragma unroll
-                for (int r = 0; r < PJ_RPT; r++) {
+                for (int q = 0; q < PJ_RPT; q++) {
+                    const int r = rg * PJ_RPT + q;
+                    xv[q] = *reinterpret_cast<const float4 *>(xb + r * PJ_KC + 4 * (jb ^ ((r >> 3) & 7)));
+                    xsq[q] = fmaf(xv[q].x, xv[q].x, fmaf(xv[q].y, xv[q].y, fmaf(xv[q].z, xv[q].z, fmaf(xv[q].w, xv[q].w, xsq[q]))));
+                }
 #pragma unroll
-                    for (int c = 0; c < PJ_FPT; c++) acc[r][c] = fmaf(xv[r], av[c], acc[r][c]);
-                    xsq[r] = fmaf(xv[r], xv[r], xsq[r]);
+                for (int c = 0; c < PJ_FPT; c++) {
+                    const int f = fg * PJ_FPT + c;
+                    const float4 av = *reinterpret_cast<const float4 *>(ab + f * PJ_KC + 4 * (jb ^ ((f >> 3) & 7)));
+#pragma unroll
+                    for (int q = 0; q < PJ_RPT; q++) {
+                        acc[q][c] = fmaf(xv[q].x, av.x, acc[q][c]);
+                        acc[q][c] = fmaf(xv[q].y, av.y, acc[q][c]);
+                        acc[q][c] = fmaf(xv[q].z, av.z, acc[q][c]);
+                        acc[q][c] = fmaf(xv[q].w, av.w, acc[q][c]);
+                    }
                 }
             }
         }
+        __syncthreads();  // the next stage() overwrites this buffer
     }
     __syncthreads();
     unsigned nfl = 0;
@@ -475,13 +504,29 @@ __device__ __forceinline__ void shl_or(uint64_t &hi, uint64_t &lo, int b, uint64
 
 // key of table l for object i: fields codes[l*K1+k] - min (bits[f] wide),
 // then K2 MinHash values (32 bits each), the first field most significant.
-// One thread per object walks all L tables, so each code row is read once.
-__global__ void k_pack_keys(int64_t n, int L, const int32_t *__restrict__ codes, int F1, int K1,
-                            const int *__restrict__ fmin, const int *__restrict__ bits,
-                            const uint32_t *__restrict__ mh, int F2, int K2,
-                            uint64_t *__restrict__ klo, uint64_t *__restrict__ khi) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t *cr = codes + i * F1;
+// One thread per object walks all L tables, so each code row is read once;
+// a block first copies its objects' code rows to shared memory with
+// coalesced loads (row stride F1 | 1 words: conflict-free row reads), when
+// they fit (PK_STAGE_MAX codes per row).
+constexpr int PK_THREADS = 128, PK_STAGE_MAX = 128;
+__global__ void __launch_bounds__(PK_THREADS) k_pack_keys(int64_t n, int L, const int32_t *__restrict__ codes,
+                                                          int F1, int K1, const int *__restrict__ fmin,
+                                                          const int *__restrict__ bits,
+                                                          const uint32_t *__restrict__ mh, int F2, int K2,
+                                                          uint64_t *__restrict__ klo, uint64_t *__restrict__ khi) {
+    extern __shared__ int32_t cs[];
+    const bool staged = F1 > 0 && F1 <= PK_STAGE_MAX;
+    const int rs = F1 | 1;
+    for (int64_t i0 = (int64_t)blockIdx.x * PK_THREADS; i0 < n; i0 += (int64_t)gridDim.x * PK_THREADS) {
+        const int64_t i = i0 + threadIdx.x;
+        if (staged) {
+            const int rows = (int)min((int64_t)PK_THREADS, n - i0);
+            __syncthreads();
+            for (int e = threadIdx.x; e < rows * F1; e += PK_THREADS) cs[(e / F1) * rs + e % F1] = codes[i0 * F1 + e];
+            __syncthreads();
+        }
+        if (i >= n) continue;
+        const int32_t *cr = staged ? cs + threadIdx.x * rs : codes + i * F1;
         const uint32_t *mr = mh ? mh + i * F2 : nullptr;
         for (int l = 0; l < L; l++) {
             uint64_t hi = 0, lo = 0;
@@ -501,13 +546,27 @@ __global__ void k_pack_keys(int64_t n, int L, const int32_t *__restrict__ codes,
 // key of global row r (instance i) is i in the bits above `B` followed by
 // the instance's own packed K-tuple, so that one sort per table groups every
 // instance separately and keeps each instance's lexicographic order.
-__global__ void k_pack_keys_batch(int64_t N, int L, const int32_t *__restrict__ codes, int F1, int K1,
-                                  const int64_t *__restrict__ row_off, int count, const int *__restrict__ fmin,
-                                  const int *__restrict__ bits, int B, uint64_t *__restrict__ klo,
-                                  uint64_t *__restrict__ khi) {
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < N; r += (int64_t)gridDim.x * blockDim.x) {
+// (code rows staged through shared memory as in k_pack_keys)
+__global__ void __launch_bounds__(PK_THREADS) k_pack_keys_batch(int64_t N, int L, const int32_t *__restrict__ codes,
+                                                                int F1, int K1, const int64_t *__restrict__ row_off,
+                                                                int count, const int *__restrict__ fmin,
+                                                                const int *__restrict__ bits, int B,
+                                                                uint64_t *__restrict__ klo,
+                                                                uint64_t *__restrict__ khi) {
+    extern __shared__ int32_t cs[];
+    const bool staged = F1 <= PK_STAGE_MAX;
+    const int rs = F1 | 1;
+    for (int64_t r0 = (int64_t)blockIdx.x * PK_THREADS; r0 < N; r0 += (int64_t)gridDim.x * PK_THREADS) {
+        const int64_t r = r0 + threadIdx.x;
+        if (staged) {
+            const int rows = (int)min((int64_t)PK_THREADS, N - r0);
+            __syncthreads();
+            for (int e = threadIdx.x; e < rows * F1; e += PK_THREADS) cs[(e / F1) * rs + e % F1] = codes[r0 * F1 + e];
+            __syncthreads();
+        }
+        if (r >= N) continue;
         const int i = find_inst(row_off, count, r);
-        const int32_t *cr = codes + r * F1;
+        const int32_t *cr = staged ? cs + threadIdx.x * rs : codes + r * F1;
         const int *fm = fmin + (int64_t)i * F1;
         const int *bt = bits + (int64_t)i * F1;
         for (int l = 0; l < L; l++) {
@@ -586,13 +645,11 @@ static void proj_layout(ProjArgs &A, int F) {
     A.F = F;
     A.FPAD = (int)ceil_div(F, PJ_FPT) * PJ_FPT;
     A.FG = A.FPAD / PJ_FPT;
-    A.RG = std::max(1, PJ_MAXT / A.FG);
+    A.RG = std::max(1, std::min(64, PJ_MAXT / A.FG));  // at most 512 rows per block
 }
 static int proj_rows(const ProjArgs &A) { return A.RG * PJ_RPT; }
 static int proj_threads(const ProjArgs &A) { return (int)ceil_div(A.FG * A.RG, 32) * 32; }  // whole warps
-static size_t proj_smem(const ProjArgs &A) {
-    return (size_t)PJ_KC * (pj_stride(proj_rows(A)) + pj_stride(A.FPAD)) * sizeof(float);
-}
+static size_t proj_smem(const ProjArgs &A) { return 2 * (size_t)PJ_KC * (proj_rows(A) + A.FPAD) * sizeof(float); }
 
 geek_status project_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ldx, int64_t n,
                           int d, const float *a, const float *b, int F, double w, int srp,
@@ -763,8 +820,12 @@ geek_status pack_keys_batch(geek_ctx *ctx, int64_t N, int L, const int32_t *code
                             cudaStream_t st) {
     if (N == 0) return GEEK_OK;
     GK_COUNT();
-    k_pack_keys_batch<<<grid_for(N, 256, ctx->num_sms), 256, 0, st>>>(N, L, codes, K * L, K, row_off, count, fmin,
-                                                                      bits, B, klo, khi);
+    const int F1 = K * L;
+    const size_t smem = F1 <= PK_STAGE_MAX ? (size_t)PK_THREADS * (F1 | 1) * sizeof(int32_t) : 0;
+    GK_CUDA(ctx, cudaFuncSetAttribute(k_pack_keys_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(PK_THREADS * (PK_STAGE_MAX | 1) * sizeof(int32_t))));
+    k_pack_keys_batch<<<grid_for(N, PK_THREADS, ctx->num_sms), PK_THREADS, smem, st>>>(N, L, codes, F1, K, row_off,
+                                                                                       count, fmin, bits, B, klo, khi);
     GK_LAUNCH(ctx);
     return GEEK_OK;
 }
@@ -817,7 +878,11 @@ geek_status pack_keys(geek_ctx *ctx, int64_t n, int L, const int32_t *codes, int
                       uint64_t *klo, uint64_t *khi, cudaStream_t st) {
     if (n == 0) return GEEK_OK;
     GK_COUNT();
-    k_pack_keys<<<grid_for(n, 256, ctx->num_sms), 256, 0, st>>>(n, L, codes, F1, K1, fmin, bits, mh, F2, K2, klo, khi);
+    const size_t smem = (F1 > 0 && F1 <= PK_STAGE_MAX) ? (size_t)PK_THREADS * (F1 | 1) * sizeof(int32_t) : 0;
+    GK_CUDA(ctx, cudaFuncSetAttribute(k_pack_keys, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(PK_THREADS * (PK_STAGE_MAX | 1) * sizeof(int32_t))));
+    k_pack_keys<<<grid_for(n, PK_THREADS, ctx->num_sms), PK_THREADS, smem, st>>>(n, L, codes, F1, K1, fmin, bits, mh,
+                                                                                 F2, K2, klo, khi);
     GK_LAUNCH(ctx);
     return GEEK_OK;
 }

@@ -96,6 +96,24 @@ def test_srp_codes_and_buckets(G, ctx):
     check_buckets(bk.copy_out(), ref, bits)
 
 
+@pytest.mark.parametrize("d", [33, 7])
+def test_odd_dimension_codes_and_buckets(G, ctx, d):
+    """d not a multiple of 4: the projection stages rows without 16-byte
+    copies; codes, buckets and the tcgen05 assignment stay exact."""
+    wl = synth.make(synth.config("c1", n=6001, d=d))
+    cfg = wl["cfg"]
+    x, bk = run_dense(G, ctx, wl)
+    codes, ref = oracle.hash_dense(wl["x"], wl["a"], wl["b"], wl["w"], cfg.K, cfg.L)
+    check_buckets(bk.copy_out(), ref, codes)
+    c = wl["centres"].astype(np.float64)
+    lab_ref, _ = oracle.assign_dense(wl["x"], c)
+    for prec in (G.PREC_BF16, G.PREC_BF16X3):
+        labels = torch.empty(cfg.n, dtype=torch.int32, device="cuda")
+        ctx.assign_centers(ctx.dense(x), G._dev(c), labels, precision=prec)
+        torch.cuda.synchronize()
+        assert np.array_equal(labels.cpu().numpy(), lab_ref), prec
+
+
 def test_assign_near_ties_are_exact(G, ctx):
     """Duplicated and nearly duplicated centres force the FP64 decision:
     exact ties must go to the smaller index."""
