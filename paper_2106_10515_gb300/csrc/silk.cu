@@ -450,15 +450,30 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
 
 constexpr uint32_t SLOT_EMPTY = 0xFFFFFFFFu, SLOT_MULTI = 0x80000000u;
 
-// warp-aggregated append: one atomic per warp and list
-__device__ __forceinline__ unsigned long long warp_append(bool want, unsigned long long *counter) {
+// Block-aggregated append (256 threads, block-uniform call): one atomic per
+// block and list, so that a list filled by every block does not serialise
+// on one counter.  Returns this thread's slot (meaningful when want).
+constexpr int AP_THREADS = 256;
+__device__ __forceinline__ unsigned long long block_append(bool want, unsigned long long *counter,
+                                                           unsigned *wcnt /* [AP_THREADS / 32] shared */,
+                                                           unsigned long long *base /* shared */) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned mask = __ballot_sync(0xffffffffu, want);
-    if (!mask) return 0;
-    const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
-    unsigned long long base = 0;
-    if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(mask));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    return base + __popc(mask & ((1u << lane) - 1));
+    if (lane == 0) wcnt[warp] = __popc(mask);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned run = 0;
+        for (int w = 0; w < AP_THREADS / 32; w++) {
+            const unsigned c = wcnt[w];
+            wcnt[w] = run;
+            run += c;
+        }
+        *base = run ? atomicAdd(counter, (unsigned long long)run) : 0ull;
+    }
+    __syncthreads();
+    const unsigned long long q = *base + wcnt[warp] + __popc(mask & ((1u << lane) - 1));
+    __syncthreads();  // wcnt / base reused by the next call
+    return q;
 }
 
 // Batched instances: instance i owns the slot region [roff[i], roff[i] +
@@ -475,7 +490,9 @@ __global__ void k_group_insert(int64_t NV, int64_t C, const uint64_t *__restrict
     const int64_t so = (int64_t)t * NV;
     uint32_t *sl = slot + (int64_t)t * C;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // whole warps iterate together (the append is a warp collective)
+    __shared__ unsigned s_wc[AP_THREADS / 32];
+    __shared__ unsigned long long s_base;
+    // the whole block iterates together (the append is a block collective)
     for (int64_t gb = (int64_t)blockIdx.x * blockDim.x; gb < NV; gb += stride) {
         const int64_t g = gb + threadIdx.x;
         bool joined = false;
@@ -503,7 +520,7 @@ __global__ void k_group_insert(int64_t NV, int64_t C, const uint64_t *__restrict
                 h = (h + 1) & mask;
             }
         }
-        const unsigned long long q = warp_append(joined, n_multi);
+        const unsigned long long q = block_append(joined, n_multi, s_wc, &s_base);
         if (joined) {
             mkey[q] = key;
             mval[q] = (uint32_t)g;
@@ -521,6 +538,8 @@ __global__ void k_group_reps(int64_t C, int S, const uint32_t *__restrict__ slot
                              int64_t *__restrict__ singles, unsigned long long *__restrict__ n_single) {
     const int64_t tot = C * S;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    __shared__ unsigned s_wc[AP_THREADS / 32];
+    __shared__ unsigned long long s_base;
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < tot; b += stride) {
         const int64_t e = b + threadIdx.x;
         const uint32_t v = e < tot ? slot[e] : SLOT_EMPTY;
@@ -528,13 +547,15 @@ __global__ void k_group_reps(int64_t C, int S, const uint32_t *__restrict__ slot
         const bool multi = used && (v & SLOT_MULTI);
         const uint32_t g = v & ~SLOT_MULTI;
         const bool single = used && !multi && delta <= 1 && vw[g] >= 2 && voff[g + 1] - voff[g] >= delta;
-        const unsigned long long qm = warp_append(multi, n_multi);
+        const unsigned long long qm = block_append(multi, n_multi, s_wc, &s_base);
         if (multi) {
             mkey[qm] = (uint64_t)e;  // segment * C + slot
             mval[qm] = g;
         }
-        const unsigned long long qs = warp_append(single, n_single);
-        if (single) singles[qs] = g;
+        if (__syncthreads_or(single)) {  // (block-uniform: single-bin sets are rare)
+            const unsigned long long qs = block_append(single, n_single, s_wc, &s_base);
+            if (single) singles[qs] = g;
+        }
     }
 }
 
