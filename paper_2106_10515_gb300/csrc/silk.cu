@@ -385,13 +385,31 @@ __global__ void k_bin_weight(int64_t nbins, const int64_t *__restrict__ rs, cons
 }
 
 // weighted vote over bins of >= 2 virtual buckets
+// A bin in which one single-object virtual bucket {a} holds at least half
+// of the weight |Bin| keeps at most a: any other object is counted at most
+// |Bin| - m_a <= |Bin| / 2 times.  With delta >= 2 such a bin yields nothing
+// and skips the vote (pruned[bin] = 1).
+__global__ void k_bin_prune(int64_t nbins, const int64_t *__restrict__ rs, const uint32_t *__restrict__ perm,
+                            const int32_t *__restrict__ vw, const int64_t *__restrict__ voff,
+                            const int64_t *__restrict__ bw, int delta, uint8_t *__restrict__ pruned) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nbins; r += (int64_t)gridDim.x * blockDim.x) {
+        bool pr = false;
+        if (delta >= 2)
+            for (int64_t q = rs[r]; q < rs[r + 1] && !pr; q++) {
+                const uint32_t v = perm[q];
+                pr = voff[v + 1] - voff[v] == 1 && 2 * (int64_t)vw[v] >= bw[r];
+            }
+        pruned[r] = pr;
+    }
+}
+
 __global__ void k_wvote_weights(int64_t m, const int32_t *__restrict__ rank, const int64_t *__restrict__ rs,
                                 const uint32_t *__restrict__ perm, const int64_t *__restrict__ voff,
-                                int64_t *__restrict__ w) {
+                                const uint8_t *__restrict__ pruned, int64_t *__restrict__ w) {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = rank[p];
         const uint32_t v = perm[p];
-        w[p] = bin_size(rs, r) >= 2 ? voff[v + 1] - voff[v] : 0;
+        w[p] = (bin_size(rs, r) >= 2 && !(pruned && pruned[r])) ? voff[v + 1] - voff[v] : 0;
     }
 }
 
@@ -851,11 +869,15 @@ geek_status wvote_bins(geek_ctx *ctx, Scratch &scr, int64_t m, const uint32_t *p
                        const int64_t *rs, int64_t nbins, const int64_t *voff, const uint32_t *vmem,
                        const int32_t *vw, const int64_t *bw, int delta, Csr *out, cudaStream_t st) {
     int64_t *w, *woff, *T_dev;
+    uint8_t *pruned;
     GK_TRY(scr.alloc(&w, m));
     GK_TRY(scr.alloc(&woff, m));
     GK_TRY(scr.alloc(&T_dev, 1));
+    GK_TRY(scr.alloc(&pruned, nbins));
     GK_COUNT();
-    k_wvote_weights<<<G(ctx, m), 256, 0, st>>>(m, rank, rs, perm, voff, w);
+    k_bin_prune<<<G(ctx, nbins), 256, 0, st>>>(nbins, rs, perm, vw, voff, bw, delta, pruned);
+    GK_COUNT();
+    k_wvote_weights<<<G(ctx, m), 256, 0, st>>>(m, rank, rs, perm, voff, pruned, w);
     GK_LAUNCH(ctx);
     GK_TRY(exclusive_scan_i64(ctx, scr, w, woff, m, T_dev, st));
     int64_t T = 0;
