@@ -120,6 +120,7 @@ struct SilkBatch {
     // set inside silk_run: per-instance slot regions of the grouping tables
     const int64_t *slot_off = nullptr, *slot_cap = nullptr;
     int64_t slots = 0;
+    const uint32_t *set_inst = nullptr;  // instance of every virtual bucket
 };
 geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p, silk_seeds *out,
                      cudaStream_t st, const SilkBatch *bt = nullptr);

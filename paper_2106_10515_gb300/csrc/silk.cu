@@ -15,11 +15,12 @@ namespace {
 // Batched instances (count > 1): ids are global rows, instance i owning
 // [row_off[i], row_off[i + 1]); a set lies inside one instance, whose
 // coefficients (A/B + i * coef_stride) hash its local ids, and tag[g] = i.
+// (set_inst, when given, holds every set's instance: no search per set)
 __global__ void k_set_sig(int64_t nsets, const int64_t *__restrict__ soff,
                           const uint32_t *__restrict__ sids, int Ks, const uint64_t *__restrict__ A,
                           const uint64_t *__restrict__ B, const int64_t *__restrict__ row_off, int count,
-                          int64_t coef_stride, uint64_t *__restrict__ klo, uint64_t *__restrict__ khi,
-                          uint32_t *__restrict__ vals, uint32_t *__restrict__ tag) {
+                          const uint32_t *__restrict__ set_inst, int64_t coef_stride, uint64_t *__restrict__ klo,
+                          uint64_t *__restrict__ khi, uint32_t *__restrict__ vals, uint32_t *__restrict__ tag) {
     // blockIdx.y = SILK table of this segment (functions t*Ks .. t*Ks+Ks-1)
     const int t = blockIdx.y;
     const int64_t so = (int64_t)t * nsets;
@@ -28,17 +29,21 @@ __global__ void k_set_sig(int64_t nsets, const int64_t *__restrict__ soff,
         a[k] = A[t * Ks + k];
         b[k] = B[t * Ks + k];
     }
+    int have = count > 1 ? -1 : 0;  // instance whose coefficients are in a / b
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nsets;
          g += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s0 = soff[g], s1 = soff[g + 1];
         int inst = 0;
         uint32_t base = 0;
         if (count > 1 && s1 > s0) {
-            inst = find_inst(row_off, count, (int64_t)sids[s0]);
+            inst = set_inst ? (int)set_inst[g] : find_inst(row_off, count, (int64_t)sids[s0]);
             base = (uint32_t)row_off[inst];
-            for (int k = 0; k < Ks; k++) {
-                a[k] = A[inst * coef_stride + t * Ks + k];
-                b[k] = B[inst * coef_stride + t * Ks + k];
+            if (inst != have) {
+                for (int k = 0; k < Ks; k++) {
+                    a[k] = A[inst * coef_stride + t * Ks + k];
+                    b[k] = B[inst * coef_stride + t * Ks + k];
+                }
+                have = inst;
             }
         }
         uint32_t m[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
@@ -580,12 +585,14 @@ __global__ void k_group_reps(int64_t C, int S, const uint32_t *__restrict__ slot
 // sets per instance (the instance of a set is that of its first member);
 // lanes of a warp with the same instance add once
 __global__ void k_sets_per_inst(int64_t nsets, const int64_t *__restrict__ soff, const uint32_t *__restrict__ sids,
-                                const int64_t *__restrict__ row_off, int count, unsigned long long *__restrict__ cnt) {
+                                const int64_t *__restrict__ row_off, int count, unsigned long long *__restrict__ cnt,
+                                uint32_t *__restrict__ set_inst) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nsets; base += stride) {
         const int64_t g = base + threadIdx.x;
         const int i = g < nsets ? find_inst(row_off, count, (int64_t)sids[soff[g]]) : -1;
+        if (g < nsets) set_inst[g] = (uint32_t)i;
         const unsigned peers = __match_any_sync(0xffffffffu, i);
         if (i >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[i], (unsigned long long)__popc(peers));
     }
@@ -635,7 +642,7 @@ geek_status make_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const i
     const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nsets, 256), (int64_t)ctx->num_sms * 8));
     GK_COUNT();
     k_set_sig<<<dim3(gx, S), 256, 0, st>>>(nsets, soff, sids, Ks, A, B, tagged ? bt->row_off : nullptr,
-                                           tagged ? bt->count : 1, coef_stride, klo, khi, *perm, tag);
+                                           tagged ? bt->count : 1, nullptr, coef_stride, klo, khi, *perm, tag);
     GK_COUNT();
     k_first_component<<<G(ctx, tot), 256, 0, st>>>(tot, klo, khi, tag, Ks, k0);
     GK_LAUNCH(ctx);
@@ -725,7 +732,8 @@ geek_status group_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const 
     const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nsets, 256), (int64_t)ctx->num_sms * 8));
     GK_COUNT();
     k_set_sig<<<dim3(gx, S), 256, 0, st>>>(nsets, soff, sids, Ks, A, B, tagged ? bt->row_off : nullptr,
-                                           tagged ? bt->count : 1, coef_stride, klo, khi, nullptr, tag);
+                                           tagged ? bt->count : 1, tagged ? bt->set_inst : nullptr, coef_stride,
+                                           klo, khi, nullptr, tag);
     GK_COUNT();
     k_group_insert<<<dim3(gx, S), 256, 0, st>>>(nsets, C, klo, khi, tag, roff, rcap, slot, mkey, mval, counts);
     GK_COUNT();
@@ -759,13 +767,16 @@ geek_status slot_regions(geek_ctx *ctx, Scratch &scr, int64_t nsets, const int64
                          SilkBatch *bt, cudaStream_t st) {
     const int count = bt->count;
     unsigned long long *cnt;
+    uint32_t *set_inst;
     GK_TRY(scr.alloc(&cnt, count));
+    GK_TRY(scr.alloc(&set_inst, std::max<int64_t>(nsets, 1)));
     GK_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * count, st));
     if (nsets) {
         GK_COUNT();
-        k_sets_per_inst<<<G(ctx, nsets), 256, 0, st>>>(nsets, soff, sids, bt->row_off, count, cnt);
+        k_sets_per_inst<<<G(ctx, nsets), 256, 0, st>>>(nsets, soff, sids, bt->row_off, count, cnt, set_inst);
         GK_LAUNCH(ctx);
     }
+    bt->set_inst = set_inst;
     std::vector<unsigned long long> hc(count);
     GK_CUDA(ctx, cudaMemcpyAsync(hc.data(), cnt, sizeof(unsigned long long) * count, cudaMemcpyDeviceToHost, st));
     GK_CUDA(ctx, cudaStreamSynchronize(st));
