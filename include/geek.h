@@ -146,6 +146,26 @@ const char *geek_last_error(const geek_ctx *ctx);
 /* Library version string (static storage). */
 const char *geek_version(void);
 
+/* ---- resident data ------------------------------------------------------ */
+
+/* A device copy of a host data set, owned by the library, that several calls
+ * share (hash, SILK and assignment all read x: staging a host data set once
+ * instead of once per call).
+ * geek_data_upload copies `host` (mem = GEEK_MEM_HOST: x n*ldx floats,
+ * set_off n+1 and set_items set_off[n] entries, cat n*n_cat tokens) into the
+ * device buffers of *res, creating the handle when *res is NULL and growing
+ * its buffers when they are too small, all in stream order on `stream`;
+ * *view then describes the copy (mem = GEEK_MEM_DEVICE, same kind, n, d,
+ * ldx and n_cat) and stays valid until the next upload into, or the free of,
+ * the same handle.  The host arrays must stay unchanged until the copies
+ * have completed (synchronise `stream`).
+ * Errors: INVALID (NULL arguments, data not on the host, bad shapes), NOMEM,
+ * CUDA.  On error *res keeps its previous buffers. */
+typedef struct geek_resident geek_resident;
+geek_status geek_data_upload(geek_ctx *ctx, const geek_data *host, geek_resident **res, geek_data *view,
+                             geek_stream stream);
+geek_status geek_resident_free(geek_resident *r);
+
 /* ---- data transformation (Sect. 3.1) ------------------------------------ */
 
 /* geek_hash: converts every object into one bucket per table.

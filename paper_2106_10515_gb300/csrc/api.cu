@@ -337,6 +337,85 @@ geek_status silk_seeds_free(silk_seeds *s) {
     return GEEK_OK;
 }
 
+struct geek_resident {
+    void *buf[3] = {nullptr, nullptr, nullptr};  // x, set_off, set_items or cat
+    size_t cap[3] = {0, 0, 0};                   // bytes
+};
+
+geek_status geek_resident_free(geek_resident *r) {
+    if (!r) return GEEK_OK;
+    for (void *p : r->buf) cudaFree(p);
+    delete r;
+    return GEEK_OK;
+}
+
+geek_status geek_data_upload(geek_ctx *ctx, const geek_data *host, geek_resident **res, geek_data *view,
+                             geek_stream stream) {
+    if (!ctx) return GEEK_ERR_INVALID;
+    try {
+        if (!res || !view) return set_error(ctx, GEEK_ERR_INVALID, "NULL argument");
+        GK_TRY(check_data(ctx, host));
+        if (host->mem != GEEK_MEM_HOST) return set_error(ctx, GEEK_ERR_INVALID, "upload needs host data");
+        const int64_t n = host->n;
+        size_t bytes[3] = {0, 0, 0};
+        const void *src[3] = {nullptr, nullptr, nullptr};
+        if (host->kind == GEEK_DENSE || host->kind == GEEK_HETERO) {
+            bytes[0] = (size_t)n * host->ldx * sizeof(float);
+            src[0] = host->x;
+        }
+        if (host->kind == GEEK_HETERO) {
+            bytes[1] = (size_t)n * host->n_cat * sizeof(uint32_t);
+            src[1] = host->cat;
+        }
+        if (host->kind == GEEK_SETS) {
+            if (host->set_off[0] != 0 || host->set_off[n] < 0)
+                return set_error(ctx, GEEK_ERR_INVALID, "set_off must start at 0 and ascend");
+            bytes[1] = (size_t)(n + 1) * sizeof(int64_t);
+            src[1] = host->set_off;
+            bytes[2] = (size_t)host->set_off[n] * sizeof(uint32_t);
+            src[2] = host->set_items;
+        }
+        geek_resident *r = *res ? *res : new (std::nothrow) geek_resident;
+        if (!r) return set_error(ctx, GEEK_ERR_NOMEM, "host allocation");
+        cudaStream_t st = S(stream);
+        for (int j = 0; j < 3; ++j) {
+            if (bytes[j] <= r->cap[j]) continue;
+            void *p = nullptr;
+            geek_status e = own_alloc(ctx, &p, bytes[j]);
+            if (e != GEEK_OK) {
+                if (!*res) geek_resident_free(r);
+                return e;
+            }
+            // the old buffer may still be read by work queued on `st`
+            if (r->buf[j]) {
+                cudaStreamSynchronize(st);
+                cudaFree(r->buf[j]);
+            }
+            r->buf[j] = p;
+            r->cap[j] = bytes[j];
+        }
+        for (int j = 0; j < 3; ++j)
+            if (bytes[j]) {
+                cudaError_t e = cudaMemcpyAsync(r->buf[j], src[j], bytes[j], cudaMemcpyHostToDevice, st);
+                if (e != cudaSuccess) {
+                    if (!*res) geek_resident_free(r);
+                    cudaGetLastError();
+                    return set_error(ctx, GEEK_ERR_CUDA, "upload copy: %s", cudaGetErrorString(e));
+                }
+            }
+        *view = *host;
+        view->mem = GEEK_MEM_DEVICE;
+        view->x = host->kind == GEEK_SETS ? nullptr : (const float *)r->buf[0];
+        view->cat = host->kind == GEEK_HETERO ? (const uint32_t *)r->buf[1] : nullptr;
+        view->set_off = host->kind == GEEK_SETS ? (const int64_t *)r->buf[1] : nullptr;
+        view->set_items = host->kind == GEEK_SETS ? (const uint32_t *)r->buf[2] : nullptr;
+        *res = r;
+        return GEEK_OK;
+    } catch (...) {
+        return set_error(ctx, GEEK_ERR_NOMEM, "host exception in geek_data_upload");
+    }
+}
+
 geek_status geek_assign_centers(geek_ctx *ctx, const geek_data *data, const double *centers,
                                 int64_t k, const geek_assign_params *p, int32_t *labels,
                                 geek_assign_stats *stats, geek_stream stream) {

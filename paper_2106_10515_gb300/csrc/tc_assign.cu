@@ -527,7 +527,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
 }
 
 // X -> BF16 K-major [n][Kp] (zero padded) and an upper bound of |x| per row;
-// warp per global row r of instance find_inst(row_off, r); xnorm is global
+// warp per global row r of instance find_inst(row_off, r); xnorm is global.
+// A lane converts 4 consecutive columns at a time (float4 loads, 8-byte
+// stores) when the row is 16-byte aligned.
 __global__ void k_x_to_bf16(const TcXPrep *__restrict__ X, const int64_t *__restrict__ row_off, int count, int64_t N,
                             float *__restrict__ xnorm) {
     const int lane = threadIdx.x & 31;
@@ -538,13 +540,36 @@ __global__ void k_x_to_bf16(const TcXPrep *__restrict__ X, const int64_t *__rest
         const TcXPrep &P = X[ii];
         const int64_t i = r - row_off[ii];
         const int W = P.split ? 2 * P.Kp : P.Kp;
+        const float *xr = P.x + i * P.ldx;
+        __nv_bfloat16 *hb = P.xb + i * W;
         float s = 0.f;
-        for (int t = lane; t < P.Kp; t += 32) {
-            const float v = t < P.d ? P.x[i * P.ldx + t] : 0.f;
-            const __nv_bfloat16 h = __float2bfloat16_rn(v);
-            P.xb[i * W + t] = h;
-            if (P.split) P.xb[i * W + P.Kp + t] = __float2bfloat16_rn(v - __bfloat162float(h));  // v - h exact
-            s = fmaf(v, v, s);
+        if (((P.ldx & 3) == 0) && ((P.d & 3) == 0) && (((uintptr_t)P.x & 15) == 0)) {
+            for (int t = 4 * lane; t < P.Kp; t += 128) {
+                const float4 v = t < P.d ? *reinterpret_cast<const float4 *>(xr + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
+                uint2 hv;
+                hv.x = *reinterpret_cast<const uint32_t *>(&h01);
+                hv.y = *reinterpret_cast<const uint32_t *>(&h23);
+                *reinterpret_cast<uint2 *>(hb + t) = hv;
+                if (P.split) {
+                    const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+                    const __nv_bfloat162 l01 = __floats2bfloat162_rn(v.x - f01.x, v.y - f01.y);  // differences exact
+                    const __nv_bfloat162 l23 = __floats2bfloat162_rn(v.z - f23.x, v.w - f23.y);
+                    uint2 lv;
+                    lv.x = *reinterpret_cast<const uint32_t *>(&l01);
+                    lv.y = *reinterpret_cast<const uint32_t *>(&l23);
+                    *reinterpret_cast<uint2 *>(hb + P.Kp + t) = lv;
+                }
+                s = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, s))));
+            }
+        } else {
+            for (int t = lane; t < P.Kp; t += 32) {
+                const float v = t < P.d ? xr[t] : 0.f;
+                const __nv_bfloat16 h = __float2bfloat16_rn(v);
+                hb[t] = h;
+                if (P.split) hb[P.Kp + t] = __float2bfloat16_rn(v - __bfloat162float(h));  // v - h exact
+                s = fmaf(v, v, s);
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);

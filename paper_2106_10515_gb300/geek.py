@@ -87,7 +87,7 @@ EXPORTS = ["geek_ctx_create", "geek_ctx_destroy", "geek_last_error", "geek_versi
            "geek_assign_centers", "geek_timing_enable", "geek_timing_reset", "geek_timing_get",
            "geek_launch_count", "geek_assign_centers_noalloc", "geek_batch_create", "geek_batch_run",
            "geek_batch_info_get", "geek_batch_instance_stats", "geek_batch_copy_out", "geek_batch_seed_ids_count",
-           "geek_batch_destroy"]
+           "geek_batch_destroy", "geek_data_upload", "geek_resident_free"]
 
 _lib = None
 
@@ -132,6 +132,8 @@ def lib():
     L.geek_batch_copy_out.argtypes = [P, P, P, P, P, P, P]
     L.geek_batch_seed_ids_count.argtypes = [P, C.POINTER(C.c_int64)]
     L.geek_batch_destroy.argtypes = [P]
+    L.geek_data_upload.argtypes = [P, C.POINTER(geek_data), C.POINTER(P), C.POINTER(geek_data), P]
+    L.geek_resident_free.argtypes = [P]
     for name in EXPORTS:
         f = getattr(L, name)
         if name not in ("geek_last_error", "geek_version", "geek_ctx_destroy", "geek_launch_count"):
@@ -203,6 +205,29 @@ class Data:
         self.c.cat = _ptr(tokens)
         self.refs.append(tokens)
         return self
+
+
+class Resident:
+    """Library-owned device copy of a host data set (geek_data_upload); the
+    buffers are reused by the next upload into the same handle."""
+
+    def __init__(self, ctx):
+        self.ctx, self.h = ctx, C.c_void_p()
+        self.data = None
+
+    def upload(self, host: Data) -> Data:
+        """Copies `host` (a Data with host=True) in stream order; returns the
+        device view, valid until the next upload or the handle's release."""
+        v = Data(host.c.kind, False, host.c.n, [self, host])
+        self.ctx._chk(lib().geek_data_upload(self.ctx.h, C.byref(host.c), C.byref(self.h), C.byref(v.c),
+                                             _stream()))
+        self.data = v
+        return v
+
+    def __del__(self):
+        if self.h:
+            lib().geek_resident_free(self.h)
+            self.h = C.c_void_p()
 
 
 class Buckets:
@@ -291,6 +316,9 @@ class Context:
             self.h = None
 
     # ---------------------------------------------------------------- data --
+    def resident(self) -> "Resident":
+        return Resident(self)
+
     @staticmethod
     def dense(x, host=False):
         return Data.dense(x, host)

@@ -142,6 +142,36 @@ def test_host_memory_path(G, ctx):
     assert np.array_equal(labels, lab_ref)
 
 
+def test_resident_upload_shared_by_hash_and_assign(G, ctx):
+    """geek_data_upload: one device copy of host data serves hash, SILK and
+    the assignment; the handle is reused by smaller and larger uploads."""
+    res = ctx.resident()
+    for n in (5000, 1200, 9000):
+        wl = synth.make(synth.config("c1", n=n))
+        cfg = wl["cfg"]
+        xh = np.ascontiguousarray(wl["x"])
+        dv = res.upload(ctx.dense(xh, host=True))
+        assert dv.c.mem == G.MEM_DEVICE and dv.c.n == n and dv.c.d == cfg.d
+        bk = ctx.hash(dv, cfg.K, cfg.L, a=G._dev(wl["a"]), b=G._dev(wl["b"]), w=wl["w"])
+        ref = oracle.run_workload(wl)
+        check_buckets(bk.copy_out(), ref["buckets"], ref["codes"].astype(np.int32))
+        seeds = ctx.silk(bk, **G.silk_args(wl["silk"]))
+        assert seeds.sets() == ref["seeds"].sets()
+        labels = torch.empty(n, dtype=torch.int32, device="cuda")
+        ctx.assign(dv, bk, seeds, labels, precision=G.PREC_BF16)
+        torch.cuda.synchronize()
+        assert np.array_equal(labels.cpu().numpy(), ref["labels"])
+    wl = synth.make(synth.config("c3", n=3001, n_base=50))
+    cfg = wl["cfg"]
+    dv = res.upload(ctx.sets(wl["set_off"], wl["set_items"].astype(np.uint32), host=True))
+    bk = ctx.hash(dv, cfg.K, cfg.L, mh_a=G._dev(wl["mh_a"]), mh_b=G._dev(wl["mh_b"]))
+    ref = oracle.run_workload(wl)
+    check_buckets(bk.copy_out(), ref["buckets"], ref["codes"].view(np.int32))
+    with pytest.raises(G.GeekError) as e:
+        res.upload(ctx.dense(G._dev(np.zeros((4, 4), np.float32))))  # device data: nothing to upload
+    assert e.value.status == G.ERR_INVALID
+
+
 def test_invalid_arguments_are_reported(G, ctx):
     wl = synth.make(synth.config("c1", n=100))
     x = G._dev(wl["x"])
