@@ -327,7 +327,7 @@ geek_status majority_per_group(geek_ctx *ctx, Scratch &scr, int64_t ng, const in
         GK_LAUNCH(ctx);
         GK_TRY(exclusive_scan_i64(ctx, scr, keep, pos, NR, ktot, st));
         GK_CUDA(ctx, cudaMemcpyAsync(&total, ktot, 8, cudaMemcpyDeviceToHost, st));
-        GK_CUDA(ctx, cudaStreamSynchronize(st));
+        GK_TRY(sort_err_check(ctx, st));  // synchronises st
         GK_TRY(scr.alloc(out_ids, std::max<int64_t>(1, total)));
         GK_COUNT();
         k_group_emit<<<G(ctx, NR), 256, 0, st>>>(nr, prs, pairs, keep, pos, *out_ids);
@@ -464,6 +464,5 @@ geek_status assign_sets(geek_ctx *ctx, Scratch &scr, const int64_t *off, const u
     k_assign_jaccard<<<blocks, 256, 0, st>>>(n, off, items, k, clen, cmask, d_heavy, nheavy, d_litem, d_loff,
                                              h_nlight, d_lcentre, counts, labels);
     GK_LAUNCH(ctx);
-    GK_CUDA(ctx, cudaStreamSynchronize(st));
-    return GEEK_OK;
+    return sort_err_check(ctx, st);  // synchronises st
 }

@@ -29,6 +29,11 @@ struct geek_ctx {
     // (centre-tile width | split-BF16 << 16) chosen by the batch autotuner per
     // (precision setting, padded d, seed-count class)
     std::map<int, int> tile_cache;
+    // device word a bounded wait of the radix sort sets on timeout (lazy)
+    int *sort_err = nullptr;
+    ~geek_ctx() {
+        if (sort_err) cudaFree(sort_err);
+    }
 };
 
 // Brackets work on a stream with CUDA events when ctx->timing is on; the
@@ -169,7 +174,18 @@ static __device__ __forceinline__ int find_inst(const int64_t *__restrict__ off,
 // Internal building blocks (implemented in the .cu files)
 // ---------------------------------------------------------------------------
 
-// Stable LSD radix sort of S segments of m elements each.  Keys are up to
+// Allocates ctx->sort_err (zeroed) on first use.
+geek_status sort_err_word(geek_ctx *ctx);
+// Synchronises `st`, then reads and clears ctx->sort_err (no-op while
+// capturing):
+// TIMEOUT when a radix pass gave up waiting on a predecessor tile.
+geek_status sort_err_check(geek_ctx *ctx, cudaStream_t st);
+// The same in two halves around a synchronisation the caller makes anyway:
+// fetch enqueues the copy into *h, eval (after the sync) clears and reports.
+geek_status sort_err_fetch(geek_ctx *ctx, int *h, cudaStream_t st);
+geek_status sort_err_eval(geek_ctx *ctx, const int *h, cudaStream_t st);
+
+// Stable LSD radix sort of S segments of m elements each (m < 2^30).  Keys are up to
 // 128 bits: key_lo holds bits 0..63, key_hi (may be null when nbits <= 64)
 // bits 64..127.  vals (may be null) moves with the keys.  Only bits
 // [0, nbits) are examined.  On return the sorted data is in the buffers

@@ -288,13 +288,13 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
 }
 
-// A warp takes 32 flagged elements at a time.  For each, all lanes
-// accumulate strided terms with TwoProduct / TwoSum (coalesced loads) and a
-// TwoSum tree combines the 32 partial (sum, error) pairs; lane k keeps
-// element k's result, and the 32 interval tests then run in parallel.  The
-// exact value equals the final sum plus all error terms; only the float
-// summation of those error terms is inexact, by at most
-// gamma_2d * (d + 1) u sum|a_j x_j| <= 2.2 (2d)(d+1) u^2 |a||x|.
+// A thread takes one flagged element and runs Dot2 over j = 0..d-1 in
+// order: TwoProduct p + h = a_j x_j, TwoSum sh + er = sh + p, and the error
+// terms er + h accumulated in sc.  sh + sc equals the exact dot product up
+// to the float summation of the 2d error terms, at most
+// gamma_d^2 sum|a_j x_j| <= 2.2 (2d)(d+1) u^2 |a||x| (Ogita, Rump and Oishi).
+// Rows are read with 16-byte loads when aligned; neighbouring flags mostly
+// share a row, so the re-reads hit L1.
 // Flag entries carry global rows (row_base + local row); instance i holds
 // global rows [row_off[i], row_off[i + 1]).
 __global__ void __launch_bounds__(256) k_recheck_dot2(
@@ -302,61 +302,42 @@ __global__ void __launch_bounds__(256) k_recheck_dot2(
     const uint64_t *__restrict__ flags, const unsigned long long *__restrict__ n_flags, int64_t cap,
     uint64_t *__restrict__ flags2, unsigned long long *__restrict__ n_flags2) {
     const int64_t nf = min((int64_t)*n_flags, cap);
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const double u = 5.9604644775390625e-08;  // 2^-24
-    for (int64_t base = warp * 32; base < nf; base += nw * 32) {
-        const int cnt = (int)min((int64_t)32, nf - base);
-        const uint64_t mine = lane < cnt ? flags[base + lane] : 0;
-        const int my_inst = lane < cnt ? find_inst(row_off, count, (int64_t)(mine >> 16)) : 0;
-        float my_sh = 0.f, my_sc = 0.f, my_xx = 0.f;
-        for (int kk = 0; kk < cnt; kk++) {
-            const uint64_t e = __shfl_sync(0xffffffffu, mine, kk);
-            const int ii = __shfl_sync(0xffffffffu, my_inst, kk);
-            const ProjArgs &A = P[ii];
-            const int d = A.d;
-            const int64_t row = (int64_t)(e >> 16) - A.row_base;
-            const int f = (int)(e & 0xFFFF);
-            const float *xr = A.x + row * A.ldx;
-            const float *ar = A.a + (int64_t)f * d;
-            float sh = 0.f, sc = 0.f, xx = 0.f;
-            for (int j = lane; j < d; j += 32) {
-                const float av = ar[j], xv = xr[j];
-                const float p = __fmul_rn(av, xv);
-                const float h = fmaf(av, xv, -p);  // exact product error
-                float t, er;
-                two_sum(sh, p, t, er);
-                sh = t;
-                sc = __fadd_rn(sc, __fadd_rn(er, h));
-                xx = fmaf(xv, xv, xx);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float os = __shfl_xor_sync(0xffffffffu, sh, o);
-                const float oc = __shfl_xor_sync(0xffffffffu, sc, o);
-                xx += __shfl_xor_sync(0xffffffffu, xx, o);
-                float t, er;
-                two_sum(sh, os, t, er);
-                sh = t;
-                sc = __fadd_rn(__fadd_rn(sc, oc), er);
-            }
-            if (lane == kk) {
-                my_sh = sh;
-                my_sc = sc;
-                my_xx = xx;
-            }
-        }
-        if (lane >= cnt) continue;
-        const uint64_t e = mine;
-        const ProjArgs &A = P[my_inst];
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nf;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t e = flags[q];
+        const ProjArgs &A = P[find_inst(row_off, count, (int64_t)(e >> 16))];
         const int d = A.d;
-        const double w = A.wd;
-        const double cfac = 2.2 * (2.0 * d) * (d + 1.0) * u * u + (double)d * 2.220446049250313e-16;
         const int64_t row = (int64_t)(e >> 16) - A.row_base;
         const int f = (int)(e & 0xFFFF);
-        const double S = (double)my_sh + (double)my_sc;
-        const double an = (double)A.anorm[f], xn = (double)(sqrtf(my_xx) * (1.0f + 1.0e-3f));
+        const float *xr = A.x + row * A.ldx;
+        const float *ar = A.a + (int64_t)f * d;
+        float sh = 0.f, sc = 0.f, xx = 0.f;
+        auto term = [&](float av, float xv) {
+            const float p = __fmul_rn(av, xv);
+            const float h = fmaf(av, xv, -p);  // exact product error
+            float t, er;
+            two_sum(sh, p, t, er);
+            sh = t;
+            sc = __fadd_rn(sc, __fadd_rn(er, h));
+            xx = fmaf(xv, xv, xx);
+        };
+        if (((d & 3) == 0) && ((((uintptr_t)xr) | ((uintptr_t)ar)) & 15) == 0) {
+            for (int j = 0; j < d; j += 4) {
+                const float4 av = *reinterpret_cast<const float4 *>(ar + j);
+                const float4 xv = *reinterpret_cast<const float4 *>(xr + j);
+                term(av.x, xv.x);
+                term(av.y, xv.y);
+                term(av.z, xv.z);
+                term(av.w, xv.w);
+            }
+        } else {
+            for (int j = 0; j < d; j++) term(ar[j], xr[j]);
+        }
+        const double w = A.wd;
+        const double cfac = 2.2 * (2.0 * d) * (d + 1.0) * u * u + (double)d * 2.220446049250313e-16;
+        const double S = (double)sh + (double)sc;
+        const double an = (double)A.anorm[f], xn = (double)(sqrtf(xx) * (1.0f + 1.0e-3f));
         const double E = cfac * an * xn + fabs(S) * 8.881784197001252e-16 + (double)d * 1e-40 + 1e-300;
         const double lo = S - E, hi = S + E;
         bool sure;
@@ -373,8 +354,10 @@ __global__ void __launch_bounds__(256) k_recheck_dot2(
         }
         if (sure) {
             A.codes[row * F + f] = code;
-            atomicMin(&A.fmin[f], code);
-            atomicMax(&A.fmax[f], code);
+            // the bounds only move outwards: a code inside a value read
+            // earlier is inside the final one, and needs no atomic
+            if (code < *(volatile int *)&A.fmin[f]) atomicMin(&A.fmin[f], code);
+            if (code > *(volatile int *)&A.fmax[f]) atomicMax(&A.fmax[f], code);
         } else {
             const unsigned long long slot = atomicAdd(n_flags2, 1ull);
             flags2[slot] = e;  // slot < nf <= cap
@@ -802,7 +785,7 @@ geek_status proj_batch_enqueue(geek_ctx *ctx, const ProjArgs &P0, int count, int
         k_project_fp32<true><<<(unsigned)B.total_tiles, proj_threads(P0), proj_smem(P0), st>>>(P0, B.P, B.tile_off,
                                                                                               count);
         GK_COUNT();
-        k_recheck_dot2<<<ctx->num_sms * 4, 256, 0, st>>>(B.P, B.row_off, count, srp, F, B.flags, B.cnt, B.cap,
+        k_recheck_dot2<<<ctx->num_sms * 8, 256, 0, st>>>(B.P, B.row_off, count, srp, F, B.flags, B.cnt, B.cap,
                                                         B.flags2, B.cnt2);
         GK_COUNT();
         k_recheck_fp64<<<ctx->num_sms * 4, 128, 0, st>>>(B.P, B.row_off, count, srp, F, B.flags2, B.cnt2, B.cap,
@@ -908,8 +891,11 @@ geek_status group_tables(geek_ctx *ctx, Scratch &scr, int64_t n, int L, uint64_t
         k_scatter_rank<<<grid_for(n * L, 256, ctx->num_sms), 256, 0, st>>>(n, L, ids, rank, obj_bucket);
     GK_LAUNCH(ctx);
     nb.assign(L, 0);
+    int sort_err = 0;
     GK_CUDA(ctx, cudaMemcpyAsync(nb.data(), runs, sizeof(int64_t) * L, cudaMemcpyDeviceToHost, st));
+    GK_TRY(sort_err_fetch(ctx, &sort_err, st));
     GK_CUDA(ctx, cudaStreamSynchronize(st));
+    GK_TRY(sort_err_eval(ctx, &sort_err, st));
     std::vector<int64_t> base(L, 0);
     int64_t NB = 0;
     for (int l = 0; l < L; l++) {

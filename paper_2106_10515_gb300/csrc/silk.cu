@@ -1201,7 +1201,10 @@ geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p,
     GK_CUDA(ctx, cudaMemcpyAsync(out->off, E.off, sizeof(int64_t) * (k + 1), cudaMemcpyDeviceToDevice, st));
     if (E.nids)
         GK_CUDA(ctx, cudaMemcpyAsync(out->ids, E.ids, sizeof(uint32_t) * E.nids, cudaMemcpyDeviceToDevice, st));
+    int sort_err = 0;
+    GK_TRY(sort_err_fetch(ctx, &sort_err, st));
     GK_CUDA(ctx, cudaStreamSynchronize(st));
+    GK_TRY(sort_err_eval(ctx, &sort_err, st));
     out->k = k;
     out->n_ids = E.nids;
     return GEEK_OK;

@@ -2,7 +2,8 @@
 // behind bucket formation (T[G(x)].push(j) in Algs. 2-3), SILK bins (Alg. 4)
 // and majority voting.  Sorting is a stable LSD radix sort with 8-bit digits
 // over S equal-length segments at once (one segment per hash table), so the
-// L tables of a transform share every launch.
+// L tables of a transform share every launch; each pass is one kernel whose
+// tiles find their output offsets by decoupled look-back.
 #include <cstdarg>
 
 #include "common.cuh"
@@ -10,30 +11,9 @@
 namespace {
 
 constexpr int RS_THREADS = 256;
-constexpr int RS_ITEMS = 16;
-constexpr int RS_TILE = RS_THREADS * RS_ITEMS;  // 4096 elements per tile
+constexpr int RS_ITEMS = 10;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;  // 2560 elements per tile
 constexpr int NWARP = RS_THREADS / 32;
-
-// ---- histogram of one digit per (segment, tile) ---------------------------
-__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t *__restrict__ word, int sh,
-                                                        int64_t m, int tiles,
-                                                        uint32_t *__restrict__ counts) {
-    __shared__ uint32_t h[256];
-    const int seg = blockIdx.y, tile = blockIdx.x, t = threadIdx.x;
-    const uint32_t lane = t & 31;
-    h[t] = 0;
-    __syncthreads();
-    const uint64_t *w = word + (int64_t)seg * m;
-    const int64_t base = (int64_t)tile * RS_TILE;
-    for (int i = 0; i < RS_ITEMS; i++) {
-        int64_t p = base + (int64_t)i * RS_THREADS + t;
-        uint32_t dg = p < m ? (uint32_t)(w[p] >> sh) & 0xFFu : 256u;
-        uint32_t peers = __match_any_sync(0xffffffffu, dg);
-        if (dg < 256 && (peers & ((1u << lane) - 1)) == 0) atomicAdd(&h[dg], (uint32_t)__popc(peers));
-    }
-    __syncthreads();
-    counts[((int64_t)seg * 256 + t) * tiles + tile] = h[t];
-}
 
 // ---- block-wide exclusive scan helper (uint32, 1024 threads max) ----------
 template <int NT>
@@ -89,70 +69,102 @@ __global__ void __launch_bounds__(1024) k_seg_scan_u32(uint32_t *__restrict__ c,
     if (totals && threadIdx.x == 0) totals[blockIdx.x] = carry;
 }
 
-// Digit offsets of one radix pass.  counts is [S][256][tiles]; one block per
-// (segment, digit) turns its tile counts into an exclusive scan and records
-// the digit total; k_digit_base then scans the 256 totals of each segment.
-__global__ void __launch_bounds__(1024) k_digit_tile_scan(uint32_t *__restrict__ counts, int tiles,
-                                                          uint32_t *__restrict__ dtot) {
-    __shared__ uint32_t wsum[32];
-    const int seg = blockIdx.y, dg = blockIdx.x;
-    uint32_t *a = counts + ((int64_t)seg * 256 + dg) * tiles;
-    uint32_t carry = 0;
-    for (int base = 0; base < tiles; base += 1024) {
-        const int p = base + threadIdx.x;
-        const uint32_t v = p < tiles ? a[p] : 0u;
-        uint32_t tot;
-        const uint32_t ex = block_excl_scan<1024>(v, &tot, wsum) + carry;
-        if (p < tiles) a[p] = ex;
-        carry += tot;
-    }
-    if (threadIdx.x == 0) dtot[seg * 256 + dg] = carry;
+// ---- one-sweep passes (decoupled look-back) --------------------------------
+// Digit totals do not change from one LSD pass to the next (a pass only
+// permutes a segment), so one read of the keys gives every pass its global
+// digit offsets.  Each pass is then a single kernel: a block takes the next
+// tile of its segment in launch order (a global ticket), publishes the
+// tile's per-digit count, and adds up its predecessors' counts by looking
+// back through their published words until one carries an inclusive prefix.
+// Word layout: bits 31..30 = state (0 empty, 1 tile count, 2 inclusive
+// prefix), bits 29..0 = count; segments are limited to 2^30 - 1 elements.
+constexpr uint32_t LB_AGG = 1u << 30, LB_PREFIX = 2u << 30, LB_MASK = (1u << 30) - 1;
+constexpr unsigned long long LB_WAIT_NS = 2000000000ull;  // 2 s per look-back wait
+constexpr int HIST_BLOCKS_PER_SEG = 96;
+
+__device__ __forceinline__ unsigned long long sort_gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
 }
 
-__global__ void __launch_bounds__(256) k_digit_base(uint32_t *__restrict__ dtot) {
+// counts[seg][pass][256] += digit counts of every pass (counts zeroed first).
+// Shared histograms per warp pair keep same-address atomics rare when a
+// high digit takes few values.
+__global__ void __launch_bounds__(256) k_rs_hist_all(const uint64_t *__restrict__ lo, const uint64_t *__restrict__ hi,
+                                                     int64_t m, int npass, uint32_t *__restrict__ counts) {
+    extern __shared__ uint32_t hs[];  // [4][npass][256]
+    const int seg = blockIdx.y, t = threadIdx.x, sub = (t >> 6);
+    for (int i = t; i < 4 * npass * 256; i += 256) hs[i] = 0;
+    __syncthreads();
+    const uint64_t *l = lo + (int64_t)seg * m;
+    const uint64_t *h = hi ? hi + (int64_t)seg * m : nullptr;
+    uint32_t *my = hs + sub * npass * 256;
+    for (int64_t p = (int64_t)blockIdx.x * 256 + t; p < m; p += (int64_t)gridDim.x * 256) {
+        const uint64_t kl = l[p];
+        const uint64_t kh = h ? h[p] : 0;
+        for (int q = 0; q < npass; q++) {
+            const int sh = q * 8;
+            const uint32_t d = (uint32_t)(((sh >= 64 ? kh : kl) >> (sh & 63)) & 0xFFu);
+            atomicAdd(&my[q * 256 + d], 1u);
+        }
+    }
+    __syncthreads();
+    for (int i = t; i < npass * 256; i += 256) {
+        const uint32_t c = hs[i] + hs[npass * 256 + i] + hs[2 * npass * 256 + i] + hs[3 * npass * 256 + i];
+        if (c) atomicAdd(&counts[(int64_t)seg * npass * 256 + i], c);
+    }
+}
+
+// exclusive scan of every (segment, pass) row of 256 digit counts, in place
+__global__ void __launch_bounds__(256) k_rs_base_all(uint32_t *__restrict__ counts) {
     __shared__ uint32_t wsum[32];
-    uint32_t *a = dtot + blockIdx.x * 256;
+    uint32_t *a = counts + (int64_t)blockIdx.x * 256;
     const uint32_t v = a[threadIdx.x];
     uint32_t tot;
-    const uint32_t ex = block_excl_scan<256>(v, &tot, wsum);
-    a[threadIdx.x] = ex;
+    a[threadIdx.x] = block_excl_scan<256>(v, &tot, wsum);
 }
 
-// ---- stable scatter of one digit ------------------------------------------
-// A tile of 4096 elements is split into 8 warp slices of 512; warp w reads
-// its slice striped (item i of lane l is element w*512 + i*32 + l), so the
-// order (warp, item, lane) is the input order.  Each warp ranks its elements
-// per digit with match-any (a running per-warp digit count in shared memory),
-// the block turns the per-warp counts into tile offsets, the tile is staged
-// in shared memory in (digit, input order), and written out contiguously per
-// digit: coalesced stores, stable order, three block barriers per tile.
-// (3 blocks per SM: the scatter is latency bound, and occupancy is worth
-// the few registers spilled)
+// One pass.  A tile of RS_TILE elements is split into 8 warp slices; warp w
+// reads its slice striped (item i of lane l is element w*IT*32 + i*32 + l),
+// so (warp, item, lane) is input order.  Each warp ranks its elements per
+// digit with match-any, the block turns per-warp counts into tile offsets,
+// stages the tile in shared memory in (digit, input order) and writes it out
+// contiguously per digit: coalesced, stable.  Small tiles and 4 blocks per
+// SM: the pass is latency bound, and occupancy pays more than long tiles.
 template <bool HI, bool VALS>
-__global__ void __launch_bounds__(RS_THREADS, 3)
-    k_rs_scatter(const uint64_t *__restrict__ lo_in, const uint64_t *__restrict__ hi_in,
-                 const uint32_t *__restrict__ v_in, uint64_t *__restrict__ lo_out,
-                 uint64_t *__restrict__ hi_out, uint32_t *__restrict__ v_out, int64_t m, int tiles,
-                 int dsel, int sh, const uint32_t *__restrict__ offs, const uint32_t *__restrict__ dbase) {
+__global__ void __launch_bounds__(RS_THREADS, 4)
+    k_rs_onesweep(const uint64_t *__restrict__ lo_in, const uint64_t *__restrict__ hi_in,
+                  const uint32_t *__restrict__ v_in, uint64_t *__restrict__ lo_out,
+                  uint64_t *__restrict__ hi_out, uint32_t *__restrict__ v_out, int64_t m, int tiles,
+                  int dsel, int sh, const uint32_t *__restrict__ dbase, int dstride, uint32_t *__restrict__ look,
+                  uint32_t *__restrict__ ticket, int *__restrict__ err) {
     __shared__ uint32_t whist[NWARP][256];
     __shared__ uint32_t tstart[256];
     __shared__ uint32_t gbase[256];
     __shared__ uint32_t wsum[32];
+    __shared__ uint32_t s_idx;
     extern __shared__ uint64_t stage[];
     uint64_t *st_lo = stage;
     uint64_t *st_hi = stage + RS_TILE;
     uint32_t *st_v = (uint32_t *)(stage + (HI ? 2 : 1) * RS_TILE);
-    const int seg = blockIdx.y, tile = blockIdx.x, t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    if (t == 0) s_idx = atomicAdd(ticket, 1u);
+#pragma unroll
+    for (int w = 0; w < NWARP; w++) whist[w][t] = 0;
+    __syncthreads();
+    const uint32_t idx = s_idx;
+    // tickets interleave the segments: a tile's predecessor in its own
+    // segment took its ticket S tickets earlier
+    const int S = (int)(gridDim.x / (uint32_t)tiles);
+    const int seg = (int)(idx % (uint32_t)S), tile = (int)(idx / (uint32_t)S);
     const int64_t so = (int64_t)seg * m;
     const int64_t t0 = (int64_t)tile * RS_TILE;
     const uint32_t lt = (1u << lane) - 1;
-#pragma unroll
-    for (int w = 0; w < NWARP; w++) whist[w][t] = 0;
-    gbase[t] = offs[((int64_t)seg * 256 + t) * tiles + tile] + dbase[seg * 256 + t];
-    __syncthreads();
-    constexpr int IT = RS_TILE / RS_THREADS;  // 16 items per lane
+    constexpr int IT = RS_TILE / RS_THREADS;
     uint64_t klo[IT], khi[IT];
-    uint32_t vv[IT], dr[IT];  // dr = digit | rank-in-warp << 9
+    uint32_t vv[IT], dr[IT];
+    // every load of the tile in flight before the first (synchronising) rank step
 #pragma unroll
     for (int i = 0; i < IT; i++) {
         const int64_t p = t0 + warp * (IT * 32) + i * 32 + lane;
@@ -160,6 +172,10 @@ __global__ void __launch_bounds__(RS_THREADS, 3)
         klo[i] = valid ? lo_in[so + p] : 0;
         khi[i] = (HI && valid) ? hi_in[so + p] : 0;
         vv[i] = (VALS && valid) ? v_in[so + p] : 0;
+    }
+#pragma unroll
+    for (int i = 0; i < IT; i++) {
+        const bool valid = t0 + warp * (IT * 32) + i * 32 + lane < m;
         const uint32_t d = valid ? (uint32_t)(((dsel ? khi[i] : klo[i]) >> sh) & 0xFFu) : 256u;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         const int leader = __ffs(peers) - 1;
@@ -179,6 +195,11 @@ __global__ void __launch_bounds__(RS_THREADS, 3)
         whist[w][t] = run;
         run += c;
     }
+    // publish this tile's count of digit t; the look-back comes after the
+    // tile is staged, so that predecessors have had time to finish theirs
+    uint32_t *lk = look + (int64_t)seg * tiles * 256;
+    volatile uint32_t *vlk = lk;
+    vlk[(int64_t)tile * 256 + t] = (tile == 0 ? LB_PREFIX : LB_AGG) | run;
     uint32_t tot;
     tstart[t] = block_excl_scan<RS_THREADS>(run, &tot, wsum);
     __syncthreads();
@@ -192,13 +213,49 @@ __global__ void __launch_bounds__(RS_THREADS, 3)
             if (VALS) st_v[lp] = vv[i];
         }
     }
+    // look back over the predecessors of this segment, four words per read
+    uint32_t excl = 0;
+    if (tile > 0) {
+        int j = tile - 1;
+        unsigned long long w0 = 0;
+        for (uint32_t it = 0;; it++) {
+            uint32_t w[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) w[k] = j - k >= 0 ? vlk[(int64_t)(j - k) * 256 + t] : 0u;
+            int k = 0;
+            bool done = false;
+            for (; k < 4; k++) {
+                const uint32_t stt = w[k] & ~LB_MASK;
+                if (stt == 0) break;  // not published yet: poll again from here
+                excl += w[k] & LB_MASK;
+                if (stt == LB_PREFIX) {
+                    done = true;
+                    break;
+                }
+            }
+            if (done) break;
+            j -= k;  // tile 0 always publishes a prefix, so j stays >= 0
+            if (k == 0 && (it & 63) == 63) {
+                const unsigned long long tn = sort_gtimer();
+                if (w0 == 0) {
+                    w0 = tn;
+                } else if (tn - w0 > LB_WAIT_NS) {
+                    atomicExch(err, (int)GEEK_ERR_TIMEOUT);  // partial prefix: wrong but in bounds
+                    break;
+                }
+            }
+        }
+        vlk[(int64_t)tile * 256 + t] = LB_PREFIX | ((excl + run) & LB_MASK);
+    }
+    // output position of staged element q of digit d: goff[d] + q
+    gbase[t] = dbase[(int64_t)seg * dstride + t] + excl - tstart[t];
     __syncthreads();
     const int cnt = (int)min((int64_t)RS_TILE, m - t0);
     for (int q = t; q < cnt; q += RS_THREADS) {
         const uint64_t kl = st_lo[q];
         const uint64_t kh = HI ? st_hi[q] : 0;
         const uint32_t d = (uint32_t)(((dsel ? kh : kl) >> sh) & 0xFFu);
-        const int64_t dst = so + gbase[d] + (q - tstart[d]);
+        const int64_t dst = so + (uint32_t)(gbase[d] + (uint32_t)q);
         lo_out[dst] = kl;
         if (HI) hi_out[dst] = kh;
         if (VALS) v_out[dst] = st_v[q];
@@ -357,6 +414,34 @@ geek_status set_error(geek_ctx *ctx, geek_status st, const char *fmt, ...) {
     return st;
 }
 
+geek_status sort_err_word(geek_ctx *ctx) {
+    if (ctx->sort_err) return GEEK_OK;
+    GK_CUDA(ctx, cudaMalloc((void **)&ctx->sort_err, sizeof(int)));
+    GK_CUDA(ctx, cudaMemset(ctx->sort_err, 0, sizeof(int)));
+    return GEEK_OK;
+}
+
+geek_status sort_err_fetch(geek_ctx *ctx, int *h, cudaStream_t st) {
+    *h = 0;
+    if (!ctx->sort_err || ctx->capturing) return GEEK_OK;
+    GK_CUDA(ctx, cudaMemcpyAsync(h, ctx->sort_err, sizeof *h, cudaMemcpyDeviceToHost, st));
+    return GEEK_OK;
+}
+
+geek_status sort_err_eval(geek_ctx *ctx, const int *h, cudaStream_t st) {
+    if (!*h) return GEEK_OK;
+    GK_CUDA(ctx, cudaMemsetAsync(ctx->sort_err, 0, sizeof(int), st));
+    return set_error(ctx, (geek_status)*h, "radix sort: a look-back wait timed out");
+}
+
+geek_status sort_err_check(geek_ctx *ctx, cudaStream_t st) {
+    if (ctx->capturing) return GEEK_OK;
+    int h = 0;
+    GK_TRY(sort_err_fetch(ctx, &h, st));
+    GK_CUDA(ctx, cudaStreamSynchronize(st));
+    return sort_err_eval(ctx, &h, st);
+}
+
 void launch_iota_u32(uint32_t *v, int64_t n, int64_t period, cudaStream_t st) {
     if (n <= 0) return;
     int blocks = (int)std::min<int64_t>(ceil_div(n, 256), 1 << 16);
@@ -368,15 +453,14 @@ geek_status radix_sort_segments(geek_ctx *ctx, Scratch &scr, int S, int64_t m, u
                                 uint64_t **key_hi, uint32_t **vals, int nbits, cudaStream_t st) {
     if (S <= 0 || m <= 1 || nbits <= 0) return GEEK_OK;
     if (S > 65535) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "radix sort: %d segments", S);
-    if (m > 0xFFFFFFFFLL) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "radix sort: segment too long");
+    if (m > (int64_t)LB_MASK) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "radix sort: segment too long");
+    if ((int64_t)S * ceil_div(m, RS_TILE) > 0xFFFFFFFFLL)
+        return set_error(ctx, GEEK_ERR_UNSUPPORTED, "radix sort: too many tiles");
     const bool hi = nbits > 64;
     if (hi && !(key_hi && *key_hi)) return set_error(ctx, GEEK_ERR_INVALID, "radix sort: missing hi word");
     const bool hv = vals && *vals;
     const int tiles = (int)ceil_div(m, RS_TILE);
     const int64_t total = (int64_t)S * m;
-    uint32_t *counts, *dtot;
-    GK_TRY(scr.alloc(&counts, (size_t)S * 256 * tiles));
-    GK_TRY(scr.alloc(&dtot, (size_t)S * 256));
     uint64_t *lo2 = nullptr, *hi2 = nullptr;
     uint32_t *v2 = nullptr;
     GK_TRY(scr.alloc(&lo2, total));
@@ -385,36 +469,51 @@ geek_status radix_sort_segments(geek_ctx *ctx, Scratch &scr, int S, int64_t m, u
     uint64_t *alo = *key_lo, *ahi = hi ? *key_hi : nullptr, *blo = lo2, *bhi = hi2;
     uint32_t *av = hv ? *vals : nullptr, *bv = v2;
     int passes = 0;
-    const dim3 grid(tiles, S);
     const size_t stage = (size_t)RS_TILE * ((hi ? 16 : 8) + (hv ? 4 : 0));
     static bool attr_done = false;
     if (!attr_done) {
         const int mx = RS_TILE * 20;
-        GK_CUDA(ctx, cudaFuncSetAttribute(k_rs_scatter<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-        GK_CUDA(ctx, cudaFuncSetAttribute(k_rs_scatter<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-        GK_CUDA(ctx, cudaFuncSetAttribute(k_rs_scatter<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-        GK_CUDA(ctx, cudaFuncSetAttribute(k_rs_scatter<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        GK_CUDA(ctx, cudaFuncSetAttribute(k_rs_onesweep<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        GK_CUDA(ctx, cudaFuncSetAttribute(k_rs_onesweep<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        GK_CUDA(ctx, cudaFuncSetAttribute(k_rs_onesweep<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        GK_CUDA(ctx, cudaFuncSetAttribute(k_rs_onesweep<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        GK_CUDA(ctx, cudaFuncSetAttribute(k_rs_hist_all, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 16 * 256 * 4));
         attr_done = true;
     }
-    for (int sh = 0; sh < nbits; sh += 8, passes++) {
-        const int dsel = sh >= 64, s = sh & 63;
+    const int npass = (nbits + 7) / 8;
+    // all digit offsets from one read of the keys
+    uint32_t *dbase_all, *look, *ticket;
+    GK_TRY(scr.alloc(&dbase_all, (size_t)S * npass * 256));
+    GK_TRY(scr.alloc(&look, (size_t)S * tiles * 256 + 32));
+    ticket = look + (size_t)S * tiles * 256;
+    GK_TRY(sort_err_word(ctx));
+    GK_CUDA(ctx, cudaMemsetAsync(dbase_all, 0, sizeof(uint32_t) * S * npass * 256, st));
+    {
+        const int hb = (int)std::min<int64_t>(HIST_BLOCKS_PER_SEG, ceil_div(m, 256 * 16));
         GK_COUNT();
-        k_rs_hist<<<grid, RS_THREADS, 0, st>>>(dsel ? ahi : alo, s, m, tiles, counts);
+        k_rs_hist_all<<<dim3(std::max(hb, 1), S), 256, (size_t)4 * npass * 256 * 4, st>>>(alo, hi ? ahi : nullptr, m, npass,
+                                                                                        dbase_all);
+        GK_LAUNCH(ctx);
         GK_COUNT();
-        k_digit_tile_scan<<<dim3(256, S), 1024, 0, st>>>(counts, tiles, dtot);
-        GK_COUNT();
-        k_digit_base<<<S, 256, 0, st>>>(dtot);
+        k_rs_base_all<<<S * npass, 256, 0, st>>>(dbase_all);
+        GK_LAUNCH(ctx);
+    }
+    const int64_t nblocks = (int64_t)S * tiles;
+    for (int q = 0; q < npass; q++, passes++) {
+        const int sh = q * 8, dsel = sh >= 64, sv = sh & 63;
+        GK_CUDA(ctx, cudaMemsetAsync(look, 0, sizeof(uint32_t) * ((size_t)S * tiles * 256 + 32), st));
         EvTimer tk(ctx, "kernel.rs_scatter", st);
         tk.work = 2.0 * (double)total * ((hi ? 16 : 8) + (hv ? 4 : 0));
         GK_COUNT();
-        if (hi && hv)
-            k_rs_scatter<true, true><<<grid, RS_THREADS, stage, st>>>(alo, ahi, av, blo, bhi, bv, m, tiles, dsel, s, counts, dtot);
-        else if (hi)
-            k_rs_scatter<true, false><<<grid, RS_THREADS, stage, st>>>(alo, ahi, av, blo, bhi, bv, m, tiles, dsel, s, counts, dtot);
-        else if (hv)
-            k_rs_scatter<false, true><<<grid, RS_THREADS, stage, st>>>(alo, ahi, av, blo, bhi, bv, m, tiles, dsel, s, counts, dtot);
-        else
-            k_rs_scatter<false, false><<<grid, RS_THREADS, stage, st>>>(alo, ahi, av, blo, bhi, bv, m, tiles, dsel, s, counts, dtot);
+#define RS_OS(H, V)                                                                                              \
+    k_rs_onesweep<H, V><<<(unsigned)nblocks, RS_THREADS, stage, st>>>(alo, ahi, av, blo, bhi, bv, m, tiles, dsel, sv, \
+                                                                      dbase_all + (size_t)q * 256, npass * 256, look, \
+                                                                      ticket, ctx->sort_err)
+        if (hi && hv) RS_OS(true, true);
+        else if (hi) RS_OS(true, false);
+        else if (hv) RS_OS(false, true);
+        else RS_OS(false, false);
+#undef RS_OS
         GK_LAUNCH(ctx);
         std::swap(alo, blo);
         std::swap(ahi, bhi);
