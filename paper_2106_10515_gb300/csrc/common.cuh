@@ -194,6 +194,17 @@ geek_status sort_err_eval(geek_ctx *ctx, const int *h, cudaStream_t st);
 geek_status radix_sort_segments(geek_ctx *ctx, Scratch &scr, int S, int64_t m, uint64_t **key_lo,
                                 uint64_t **key_hi, uint32_t **vals, int nbits, cudaStream_t st);
 
+// Buckets of S key-sorted segments of m elements (ids: object id at each
+// sorted position): obj_bucket[seg][id] = rank of the id's key among the
+// segment's distinct keys; *boff_out (stream-ordered allocation, NB + 1
+// entries) holds the global start seg * m + p of every run, tables in order,
+// then S * m; nb[seg] = runs of segment seg, *NB_out their sum.  Synchronises
+// `st` once (the run counts size the offsets) and reports a radix-sort
+// timeout recorded before it.
+geek_status segment_buckets(geek_ctx *ctx, Scratch &scr, int S, int64_t m, const uint64_t *key_lo,
+                            const uint64_t *key_hi, const uint32_t *ids, int32_t *obj_bucket, int64_t **boff_out,
+                            std::vector<int64_t> &nb, int64_t *NB_out, cudaStream_t st);
+
 // Run detection over S segments of m sorted keys: starts flagged where the
 // key differs from its predecessor in the segment.  Produces
 //   rank[p]         (may be null)  run index of position p within its segment

@@ -585,27 +585,6 @@ __global__ void k_row_norms_batch(const ProjArgs *__restrict__ P, int count, int
     out[e] = sqrtf(s) * 1.0001f;
 }
 
-__global__ void k_scatter_rank(int64_t n, int L, const uint32_t *__restrict__ ids,
-                               const int32_t *__restrict__ rank, int32_t *__restrict__ obj_bucket) {
-    const int64_t total = n * L;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t l = e / n;
-        obj_bucket[l * n + ids[e]] = rank[e];
-    }
-}
-
-// global bucket offsets: boff[base[l] + r] = l*n + run_start[l][r]
-__global__ void k_bucket_off(int64_t n, int L, const int64_t *__restrict__ run_start,
-                             const int64_t *__restrict__ table_base, const int64_t *__restrict__ nb,
-                             int64_t *__restrict__ boff, int64_t NB) {
-    const int l = blockIdx.y;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nb[l];
-         r += (int64_t)gridDim.x * blockDim.x)
-        boff[table_base[l] + r] = (int64_t)l * n + run_start[(int64_t)l * (n + 1) + r];
-    if (l == 0 && blockIdx.x == 0 && threadIdx.x == 0) boff[NB] = (int64_t)L * n;
-}
-
 __global__ void k_fill_i32(int *p, int n, int v) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) p[i] = v;
@@ -880,41 +859,6 @@ geek_status group_tables(geek_ctx *ctx, Scratch &scr, int64_t n, int L, uint64_t
         EvTimer tk(ctx, "hash.sort", st);
         GK_TRY(radix_sort_segments(ctx, scr, L, n, &klo, khi ? &khi : nullptr, &ids, nbits, st));
     }
-    int32_t *rank;
-    int64_t *run_start, *runs;
-    GK_TRY(scr.alloc(&rank, (size_t)n * L));
-    GK_TRY(scr.alloc(&run_start, (size_t)(n + 1) * L));
-    GK_TRY(scr.alloc(&runs, L));
-    GK_TRY(segment_runs(ctx, scr, L, n, klo, nbits > 64 ? khi : nullptr, rank, run_start, runs, st));
-    if (n)
-        GK_COUNT();
-        k_scatter_rank<<<grid_for(n * L, 256, ctx->num_sms), 256, 0, st>>>(n, L, ids, rank, obj_bucket);
-    GK_LAUNCH(ctx);
-    nb.assign(L, 0);
-    int sort_err = 0;
-    GK_CUDA(ctx, cudaMemcpyAsync(nb.data(), runs, sizeof(int64_t) * L, cudaMemcpyDeviceToHost, st));
-    GK_TRY(sort_err_fetch(ctx, &sort_err, st));
-    GK_CUDA(ctx, cudaStreamSynchronize(st));
-    GK_TRY(sort_err_eval(ctx, &sort_err, st));
-    std::vector<int64_t> base(L, 0);
-    int64_t NB = 0;
-    for (int l = 0; l < L; l++) {
-        base[l] = NB;
-        NB += nb[l];
-    }
-    int64_t *d_base;
-    GK_TRY(scr.alloc(&d_base, L));
-    GK_CUDA(ctx, cudaMemcpyAsync(d_base, base.data(), sizeof(int64_t) * L, cudaMemcpyHostToDevice, st));
-    int64_t *boff;
-    cudaError_t e = cudaMallocAsync((void **)&boff, sizeof(int64_t) * (NB + 1), st);
-    if (e != cudaSuccess) return set_error(ctx, GEEK_ERR_NOMEM, "bucket offsets: %s", cudaGetErrorString(e));
-    int64_t maxnb = 1;
-    for (auto v : nb) maxnb = std::max(maxnb, v);
-    GK_COUNT();
-    k_bucket_off<<<dim3((unsigned)std::min<int64_t>(ceil_div(maxnb, 256), 4096), L), 256, 0, st>>>(
-        n, L, run_start, d_base, runs, boff, NB);
-    GK_LAUNCH(ctx);
-    *boff_out = boff;
-    *NB_out = NB;
-    return GEEK_OK;
+    return segment_buckets(ctx, scr, L, n, klo, nbits > 64 ? khi : nullptr, ids, obj_bucket, boff_out, nb, NB_out,
+                           st);
 }

@@ -327,6 +327,46 @@ __global__ void __launch_bounds__(RS_THREADS)
     if (tile == 0 && threadIdx.x == 0) rs[runs[seg]] = m;
 }
 
+// Bucket formation from sorted segments in one pass: position p of segment
+// seg (key-sorted, ids[] the object ids in that order) belongs to run r;
+// the object's bucket id in its table is r, and a run start records the
+// run's global offset.  Writes obj_bucket[seg][ids[p]] = r and, at starts,
+// boff[base[seg] + r] = seg * m + p; boff[NB] = S * m closes the list.
+__global__ void __launch_bounds__(RS_THREADS)
+    k_runs_buckets(const uint64_t *__restrict__ lo, const uint64_t *__restrict__ hi, int64_t m, int tiles,
+                   const uint32_t *__restrict__ tile_off, const uint32_t *__restrict__ ids,
+                   const int64_t *__restrict__ base, int32_t *__restrict__ obj_bucket,
+                   int64_t *__restrict__ boff, int64_t NB) {
+    __shared__ uint32_t wsum[32];
+    const int seg = blockIdx.y, tile = blockIdx.x;
+    const int64_t so = (int64_t)seg * m;
+    const uint64_t *l = lo + so;
+    const uint64_t *h = hi ? hi + so : nullptr;
+    const int64_t p0 = (int64_t)tile * RS_TILE + (int64_t)threadIdx.x * RS_ITEMS;
+    uint32_t flags = 0, c = 0;
+    for (int i = 0; i < RS_ITEMS; i++) {
+        const int64_t p = p0 + i;
+        if (p < m && run_start_at(l, h, nullptr, p)) {
+            flags |= 1u << i;
+            c++;
+        }
+    }
+    uint32_t tot;
+    const uint32_t ex = block_excl_scan<RS_THREADS>(c, &tot, wsum) + tile_off[(int64_t)seg * tiles + tile];
+    int64_t r = (int64_t)ex - 1;
+    const int64_t bb = base[seg];
+    for (int i = 0; i < RS_ITEMS; i++) {
+        const int64_t p = p0 + i;
+        if (p >= m) break;
+        if (flags >> i & 1u) {
+            r++;
+            boff[bb + r] = so + p;
+        }
+        obj_bucket[so + ids[so + p]] = (int32_t)r;
+    }
+    if (seg == 0 && tile == 0 && threadIdx.x == 0) boff[NB] = (int64_t)gridDim.y * m;
+}
+
 // ---- generic int64 exclusive scan -----------------------------------------
 __global__ void __launch_bounds__(RS_THREADS) k_i64_tile_sum(const int64_t *__restrict__ in,
                                                              int64_t n, int64_t *__restrict__ sums) {
@@ -553,6 +593,57 @@ geek_status segment_runs_tagged(geek_ctx *ctx, Scratch &scr, int S, int64_t m, c
     GK_COUNT();
     k_runs_emit<<<grid, RS_THREADS, 0, st>>>(key_lo, key_hi, tag, m, tiles, tile_cnt, runs, rank, run_start);
     GK_LAUNCH(ctx);
+    return GEEK_OK;
+}
+
+geek_status segment_buckets(geek_ctx *ctx, Scratch &scr, int S, int64_t m, const uint64_t *key_lo,
+                            const uint64_t *key_hi, const uint32_t *ids, int32_t *obj_bucket, int64_t **boff_out,
+                            std::vector<int64_t> &nb, int64_t *NB_out, cudaStream_t st) {
+    nb.assign(S, 0);
+    int64_t *runs;
+    GK_TRY(scr.alloc(&runs, std::max(S, 1)));
+    const int tiles = (int)std::max<int64_t>(1, ceil_div(m, RS_TILE));
+    uint32_t *tile_cnt = nullptr;
+    if (S > 0 && m > 0) {
+        GK_TRY(scr.alloc(&tile_cnt, (size_t)S * tiles));
+        GK_COUNT();
+        k_runs_count<<<dim3(tiles, S), RS_THREADS, 0, st>>>(key_lo, key_hi, nullptr, m, tiles, tile_cnt);
+        GK_COUNT();
+        k_seg_scan_u32<<<S, 1024, 0, st>>>(tile_cnt, tiles, runs);
+        GK_LAUNCH(ctx);
+        GK_CUDA(ctx, cudaMemcpyAsync(nb.data(), runs, sizeof(int64_t) * S, cudaMemcpyDeviceToHost, st));
+    }
+    int sort_err = 0;
+    GK_TRY(sort_err_fetch(ctx, &sort_err, st));
+    GK_CUDA(ctx, cudaStreamSynchronize(st));
+    GK_TRY(sort_err_eval(ctx, &sort_err, st));
+    std::vector<int64_t> base(std::max(S, 1), 0);
+    int64_t NB = 0;
+    for (int l = 0; l < S; l++) {
+        base[l] = NB;
+        NB += nb[l];
+    }
+    int64_t *boff;
+    cudaError_t e = cudaMallocAsync((void **)&boff, sizeof(int64_t) * (NB + 1), st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ctx, GEEK_ERR_NOMEM, "bucket offsets: %s", cudaGetErrorString(e));
+    }
+    if (S == 0 || m == 0) {
+        const int64_t sentinel = (int64_t)S * m;  // = 0
+        GK_CUDA(ctx, cudaMemcpyAsync(boff + NB, &sentinel, sizeof sentinel, cudaMemcpyHostToDevice, st));
+        GK_CUDA(ctx, cudaStreamSynchronize(st));
+    } else {
+        int64_t *d_base;
+        GK_TRY(scr.alloc(&d_base, S));
+        GK_CUDA(ctx, cudaMemcpyAsync(d_base, base.data(), sizeof(int64_t) * S, cudaMemcpyHostToDevice, st));
+        GK_COUNT();
+        k_runs_buckets<<<dim3(tiles, S), RS_THREADS, 0, st>>>(key_lo, key_hi, m, tiles, tile_cnt, ids, d_base,
+                                                             obj_bucket, boff, NB);
+        GK_LAUNCH(ctx);
+    }
+    *boff_out = boff;
+    *NB_out = NB;
     return GEEK_OK;
 }
 
