@@ -83,6 +83,7 @@ struct FArgs {
     float cmax;
     int32_t *labels;
     int32_t *flag_rows;
+    float *flag_m;  // may be null: the row's smallest fast value, beside flag_rows
     unsigned long long *n_flag;
     int64_t ntiles;
 };
@@ -205,6 +206,7 @@ __global__ void __launch_bounds__(256) k_assign_fp32(FArgs A, GatherUnits U) {
                 if (!sure) {
                     const unsigned long long q = atomicAdd(A.n_flag, 1ull);
                     A.flag_rows[q] = (int32_t)(rbase + row);
+                    if (A.flag_m) A.flag_m[q] = valid ? B[r].b1 : __int_as_float(0x7fc00000);
                 }
             }
         }
@@ -279,10 +281,16 @@ __global__ void k_flag_scatter(const int32_t *__restrict__ flags, const unsigned
 // them with the FP64 reference distance, one candidate per lane, ties to the
 // smaller index.  Flag entries are global rows; instance i owns rows
 // [row_off[i], row_off[i + 1]).  d <= 256.
+// With flag_m, entry q brings the smallest fast value of its row from the
+// tiled FP32 pass and the first pass is skipped.  Any fast value f' of any
+// centre j' serves as m: the winner j* has fast(j*) <= D(j*) + W <= D(j') + W
+// <= f' + 2W, W the rigorous FP32 window (both passes are within W of the
+// exact distance whatever their summation order).  NaN: no finite value.
 constexpr int RC_MAXD = 256;
 __global__ void __launch_bounds__(256) k_assign_recheck(const RInst *__restrict__ R,
                                                         const int64_t *__restrict__ row_off, int count,
                                                         const int32_t *__restrict__ flag_rows,
+                                                        const float *__restrict__ flag_m,
                                                         const unsigned long long *__restrict__ n_flag) {
     __shared__ float xs[8][RC_MAXD];  // the warp's row, for the FP64 candidates
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -325,8 +333,11 @@ __global__ void __launch_bounds__(256) k_assign_recheck(const RInst *__restrict_
             for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
             return fmaf(-2.f, dot, I.cn[j]);
         };
-        float m = FLT_MAX;
-        for (int64_t j = 0; j < k; j++) m = fminf(m, fast(j));
+        float m = flag_m ? flag_m[q] : __int_as_float(0x7fc00000);
+        if (m != m) {
+            m = FLT_MAX;
+            for (int64_t j = 0; j < k; j++) m = fminf(m, fast(j));
+        }
         const float lim = m + 2.f * window_fp32(xn, cmax, d) * (1.f + 1e-6f);
         double bD = DBL_MAX;
         int bj = 0x7FFFFFFF;
@@ -635,8 +646,10 @@ geek_status assign_dense_centres(geek_ctx *ctx, Scratch &scr, const float *x, in
     float cmax;
     memcpy(&cmax, &h_bits, sizeof cmax);
     int32_t *flag_rows;
+    float *flag_m = nullptr;  // the FP32 pass's smallest value per flagged row
     unsigned long long *n_flag;
     GK_TRY(scr.alloc(&flag_rows, n));
+    if (precision == GEEK_PREC_FP32) GK_TRY(scr.alloc(&flag_m, n));
     GK_TRY(scr.alloc(&n_flag, 1));
     GK_CUDA(ctx, cudaMemsetAsync(n_flag, 0, sizeof(unsigned long long), st));
     if (precision == GEEK_PREC_BF16 || precision == GEEK_PREC_BF16X3) {
@@ -647,7 +660,7 @@ geek_status assign_dense_centres(geek_ctx *ctx, Scratch &scr, const float *x, in
         GK_CUDA(ctx, cudaFuncSetAttribute(k_assign_fp32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         EvTimer tk(ctx, "kernel.assign_fp32", st);
         tk.work = 2.0 * (double)n * (double)k * (double)d;
-        FArgs A{x, ldx, n, d, c32, cn, k, cmax, labels, flag_rows, n_flag, ceil_div(n, AS_TR)};
+        FArgs A{x, ldx, n, d, c32, cn, k, cmax, labels, flag_rows, flag_m, n_flag, ceil_div(n, AS_TR)};
         GK_COUNT();
         k_assign_fp32<false><<<(unsigned)A.ntiles, 256, smem, st>>>(A, GatherUnits{});
         GK_LAUNCH(ctx);
@@ -663,7 +676,7 @@ geek_status assign_dense_centres(geek_ctx *ctx, Scratch &scr, const float *x, in
             const int blocks = (int)std::min<unsigned long long>(ceil_div((int64_t)h_flag, 8), (unsigned long long)ctx->num_sms * 8);
             EvTimer tk(ctx, "kernel.assign_recheck", st);
             GK_COUNT();
-            k_assign_recheck<<<blocks, 256, 0, st>>>(ri, roff, 1, flag_rows, n_flag);
+            k_assign_recheck<<<blocks, 256, 0, st>>>(ri, roff, 1, flag_rows, flag_m, n_flag);
             GK_LAUNCH(ctx);
         } else {
             GK_TRY(decide_flags(ctx, ri, roff, 1, d, flag_rows, n_flag, db, st));
@@ -767,6 +780,7 @@ geek_status decide_bufs_alloc(geek_ctx *ctx, Scratch *scr, int count, int64_t n_
     GK_TRY(al(&B.n_units, 1));
     GK_TRY(al(&B.grows, std::max<int64_t>(n_total, 1)));
     GK_TRY(al(&B.flags2, std::max<int64_t>(n_total, 1)));
+    GK_TRY(al(&B.flags2_m, std::max<int64_t>(n_total, 1)));
     GK_TRY(al(&B.n_flag2, 1));
     return GEEK_OK;
 }
@@ -802,12 +816,13 @@ geek_status decide_flags(geek_ctx *ctx, const RInst *R, const int64_t *row_off, 
     }
     FArgs A{};
     A.flag_rows = B.flags2;
+    A.flag_m = B.flags2_m;
     A.n_flag = B.n_flag2;
     GatherUnits U{R, B.grows, B.unit_inst, B.unit_start, B.unit_cnt, B.n_units};
     GK_COUNT();
     k_assign_fp32<true><<<ctx->num_sms * 2, 256, smem, st>>>(A, U);
     GK_COUNT();
-    k_assign_recheck<<<ctx->num_sms * 8, 256, 0, st>>>(R, row_off, count, B.flags2, B.n_flag2);
+    k_assign_recheck<<<ctx->num_sms * 8, 256, 0, st>>>(R, row_off, count, B.flags2, B.flags2_m, B.n_flag2);
     GK_LAUNCH(ctx);
     return GEEK_OK;
 }

@@ -471,110 +471,133 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     return z ^ (z >> 31);
 }
 
-constexpr uint32_t SLOT_EMPTY = 0xFFFFFFFFu, SLOT_MULTI = 0x80000000u;
+// A slot is 64 bits: a 32-bit fingerprint of the signature (high word) and
+// the group's first set g | SLOT_MULTI (low word; g < 2^31 - 1, so a used
+// slot never equals SLOT_EMPTY).  Probes compare fingerprints first and read
+// the first set's signature only on a fingerprint match.
+constexpr uint64_t SLOT_EMPTY = ~0ull;
+constexpr uint32_t SLOT_MULTI = 0x80000000u;
 
 // Block-aggregated append (256 threads, block-uniform call): one atomic per
 // block and list, so that a list filled by every block does not serialise
-// on one counter.  Returns this thread's slot (meaningful when want).
+// on one counter.  Thread t appends c entries (c >= 0); returns the first of
+// its positions.
 constexpr int AP_THREADS = 256;
-__device__ __forceinline__ unsigned long long block_append(bool want, unsigned long long *counter,
-                                                           unsigned *wcnt /* [AP_THREADS / 32] shared */,
-                                                           unsigned long long *base /* shared */) {
+__device__ __forceinline__ unsigned long long block_append_n(unsigned c, unsigned long long *counter,
+                                                             unsigned *wcnt /* [AP_THREADS / 32] shared */,
+                                                             unsigned long long *base /* shared */) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned mask = __ballot_sync(0xffffffffu, want);
-    if (lane == 0) wcnt[warp] = __popc(mask);
+    unsigned x = c;  // inclusive scan over the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wcnt[warp] = x;
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned run = 0;
         for (int w = 0; w < AP_THREADS / 32; w++) {
-            const unsigned c = wcnt[w];
+            const unsigned v = wcnt[w];
             wcnt[w] = run;
-            run += c;
+            run += v;
         }
         *base = run ? atomicAdd(counter, (unsigned long long)run) : 0ull;
     }
     __syncthreads();
-    const unsigned long long q = *base + wcnt[warp] + __popc(mask & ((1u << lane) - 1));
+    const unsigned long long q = *base + wcnt[warp] + (x - c);
     __syncthreads();  // wcnt / base reused by the next call
     return q;
+}
+__device__ __forceinline__ unsigned long long block_append(bool want, unsigned long long *counter, unsigned *wcnt,
+                                                           unsigned long long *base) {
+    return block_append_n(want ? 1u : 0u, counter, wcnt, base);
 }
 
 // Batched instances: instance i owns the slot region [roff[i], roff[i] +
 // rcap[i]) (rcap a power of two >= 2x its sets), so a block, whose sets mostly
 // belong to one instance, probes one small region.  A set that joins an
 // existing group appends itself to the multi list (key = segment * C + slot);
-// the groups' first sets are added by k_group_reps.
+// the one joiner that sets the group's SLOT_MULTI bit also appends the
+// group's first set, so every group of >= 2 sets is listed whole.
 __global__ void k_group_insert(int64_t NV, int64_t C, const uint64_t *__restrict__ klo,
                                const uint64_t *__restrict__ khi, const uint32_t *__restrict__ tag,
                                const int64_t *__restrict__ roff, const int64_t *__restrict__ rcap,
-                               uint32_t *__restrict__ slot, uint64_t *__restrict__ mkey, uint32_t *__restrict__ mval,
+                               uint64_t *__restrict__ slot, uint64_t *__restrict__ mkey, uint32_t *__restrict__ mval,
                                unsigned long long *__restrict__ n_multi) {
     const int t = blockIdx.y;
     const int64_t so = (int64_t)t * NV;
-    uint32_t *sl = slot + (int64_t)t * C;
+    uint64_t *sl = slot + (int64_t)t * C;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     __shared__ unsigned s_wc[AP_THREADS / 32];
     __shared__ unsigned long long s_base;
     // the whole block iterates together (the append is a block collective)
     for (int64_t gb = (int64_t)blockIdx.x * blockDim.x; gb < NV; gb += stride) {
         const int64_t g = gb + threadIdx.x;
-        bool joined = false;
+        bool joined = false, first = false;
+        uint32_t rep = 0;
         uint64_t key = 0;
         if (g < NV) {
             const uint64_t lo = klo[so + g], hi = khi ? khi[so + g] : 0;
             const uint32_t tg = tag ? tag[so + g] : 0;
             const int64_t base = tag ? roff[tg] : 0;
             const uint64_t mask = (uint64_t)(tag ? rcap[tg] : C) - 1;
-            uint64_t h = mix64(lo ^ mix64(hi + 0x9e3779b97f4a7c15ull * (uint64_t)(tg + 1))) & mask;
+            const uint64_t hf = mix64(lo ^ mix64(hi + 0x9e3779b97f4a7c15ull * (uint64_t)(tg + 1)));
+            const uint32_t fp = (uint32_t)(hf >> 32);
+            const uint64_t mine = ((uint64_t)fp << 32) | (uint64_t)g;
+            uint64_t h = hf & mask;
             for (uint64_t probe = 0; probe <= mask; probe++) {
-                uint32_t cur = sl[base + h];
+                unsigned long long *ps = (unsigned long long *)&sl[base + h];
+                uint64_t cur = *ps;
                 if (cur == SLOT_EMPTY) {
-                    const uint32_t prev = atomicCAS(&sl[base + h], SLOT_EMPTY, (uint32_t)g);
+                    const uint64_t prev = atomicCAS(ps, (unsigned long long)SLOT_EMPTY, (unsigned long long)mine);
                     if (prev == SLOT_EMPTY) break;  // first set of a new group
                     cur = prev;
                 }
-                const uint32_t r = cur & ~SLOT_MULTI;
-                if (klo[so + r] == lo && (!khi || khi[so + r] == hi) && (!tag || tag[so + r] == tg)) {
-                    if (!(cur & SLOT_MULTI)) atomicOr(&sl[base + h], SLOT_MULTI);
-                    joined = true;
-                    key = (uint64_t)t * (uint64_t)C + (uint64_t)(base + h);
-                    break;
+                if ((uint32_t)(cur >> 32) == fp) {
+                    const uint32_t r = (uint32_t)cur & ~SLOT_MULTI;
+                    if (klo[so + r] == lo && (!khi || khi[so + r] == hi) && (!tag || tag[so + r] == tg)) {
+                        if (!(cur & SLOT_MULTI))
+                            first = !(atomicOr(ps, (unsigned long long)SLOT_MULTI) & SLOT_MULTI);
+                        rep = r;
+                        joined = true;
+                        key = (uint64_t)t * (uint64_t)C + (uint64_t)(base + h);
+                        break;
+                    }
                 }
                 h = (h + 1) & mask;
             }
         }
-        const unsigned long long q = block_append(joined, n_multi, s_wc, &s_base);
+        const unsigned long long q = block_append_n((joined ? 1u : 0u) + (first ? 1u : 0u), n_multi, s_wc, &s_base);
         if (joined) {
             mkey[q] = key;
             mval[q] = (uint32_t)g;
         }
+        if (first) {
+            mkey[q + 1] = key;
+            mval[q + 1] = rep;
+        }
     }
 }
 
-// One pass over the slots: the first set of every group of >= 2 sets joins
-// the multi list; with delta <= 1 a set alone in its group with weight >= 2
-// is a bin of one virtual bucket that keeps the whole bucket (with delta >= 2
-// that rule cannot fire: weight >= 2 only for one-object buckets).
-__global__ void k_group_reps(int64_t C, int S, const uint32_t *__restrict__ slot, const int32_t *__restrict__ vw,
-                             const int64_t *__restrict__ voff, int delta, uint64_t *__restrict__ mkey,
-                             uint32_t *__restrict__ mval, unsigned long long *__restrict__ n_multi,
-                             int64_t *__restrict__ singles, unsigned long long *__restrict__ n_single) {
+// With delta <= 1, one pass over the slots: a set alone in its group with
+// weight >= 2 is a bin of one virtual bucket that keeps the whole bucket
+// (with delta >= 2 that rule cannot fire: weight >= 2 only for one-object
+// buckets, and the pass is skipped).
+__global__ void k_group_singles(int64_t C, int S, const uint64_t *__restrict__ slot, const int32_t *__restrict__ vw,
+                                const int64_t *__restrict__ voff, int delta, int64_t *__restrict__ singles,
+                                unsigned long long *__restrict__ n_single) {
     const int64_t tot = C * S;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     __shared__ unsigned s_wc[AP_THREADS / 32];
     __shared__ unsigned long long s_base;
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < tot; b += stride) {
         const int64_t e = b + threadIdx.x;
-        const uint32_t v = e < tot ? slot[e] : SLOT_EMPTY;
+        const uint64_t v = e < tot ? slot[e] : SLOT_EMPTY;
         const bool used = v != SLOT_EMPTY;
-        const bool multi = used && (v & SLOT_MULTI);
-        const uint32_t g = v & ~SLOT_MULTI;
-        const bool single = used && !multi && delta <= 1 && vw[g] >= 2 && voff[g + 1] - voff[g] >= delta;
-        const unsigned long long qm = block_append(multi, n_multi, s_wc, &s_base);
-        if (multi) {
-            mkey[qm] = (uint64_t)e;  // segment * C + slot
-            mval[qm] = g;
-        }
+        const bool multi = used && ((uint32_t)v & SLOT_MULTI);
+        const uint32_t g = (uint32_t)v & ~SLOT_MULTI;
+        const bool single = used && !multi && vw[g] >= 2 && voff[g + 1] - voff[g] >= delta;
         if (__syncthreads_or(single)) {  // (block-uniform: single-bin sets are rare)
             const unsigned long long qs = block_append(single, n_single, s_wc, &s_base);
             if (single) singles[qs] = g;
@@ -714,13 +737,14 @@ geek_status group_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const 
         C = bt->slots;
     }
     uint64_t *klo, *khi = nullptr;
-    if (nsets >= (int64_t)SLOT_MULTI) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "more than 2^31 SILK sets");
-    uint32_t *tag = nullptr, *slot;
+    if (nsets >= (int64_t)SLOT_MULTI - 1) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "more than 2^31 SILK sets");
+    uint32_t *tag = nullptr;
+    uint64_t *slot;
     GK_TRY(scr.alloc(&klo, tot));
     if (Ks > 2) GK_TRY(scr.alloc(&khi, tot));
     if (tagged) GK_TRY(scr.alloc(&tag, tot));
     GK_TRY(scr.alloc(&slot, (size_t)S * C));
-    GK_CUDA(ctx, cudaMemsetAsync(slot, 0xFF, sizeof(uint32_t) * S * C, st));
+    GK_CUDA(ctx, cudaMemsetAsync(slot, 0xFF, sizeof(uint64_t) * S * C, st));
     uint64_t *mkey;
     uint32_t *mval;
     unsigned long long *counts;
@@ -736,8 +760,10 @@ geek_status group_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const 
                                            klo, khi, nullptr, tag);
     GK_COUNT();
     k_group_insert<<<dim3(gx, S), 256, 0, st>>>(nsets, C, klo, khi, tag, roff, rcap, slot, mkey, mval, counts);
-    GK_COUNT();
-    k_group_reps<<<G(ctx, S * C), 256, 0, st>>>(C, S, slot, vw, soff, delta, mkey, mval, counts, *singles, counts + 1);
+    if (delta <= 1) {
+        GK_COUNT();
+        k_group_singles<<<G(ctx, S * C), 256, 0, st>>>(C, S, slot, vw, soff, delta, *singles, counts + 1);
+    }
     GK_LAUNCH(ctx);
     unsigned long long h[2];
     GK_CUDA(ctx, cudaMemcpyAsync(h, counts, sizeof h, cudaMemcpyDeviceToHost, st));
