@@ -10,6 +10,29 @@
 
 namespace {
 
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    // SplitMix64 finalizer (Steele, Lea and Flood, 2014)
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+// 64-bit hash of a signature (lo, hi) of instance tg: slot index (low
+// bits) and fingerprint (high word) of the grouping tables
+__device__ __forceinline__ uint64_t sig_hash(uint64_t lo, uint64_t hi, uint32_t tg) {
+    return mix64(lo ^ mix64(hi + 0x9e3779b97f4a7c15ull * (uint64_t)(tg + 1)));
+}
+
+// Sets seen once / twice: two bitmaps with a part of seen_mask + 1 bits per
+// table (part t at t * (seen_mask + 1)), indexed by a hash of the signature
+// hash.  A set whose bit in the second map is clear has no other set with
+// its signature in its table: its bin holds it alone, and it skips the
+// grouping table.  Blocks run roughly table by table, so the part in use
+// stays in L2.
+__device__ __forceinline__ uint64_t seen_pos(uint64_t hf, int t, uint64_t seen_mask) {
+    return (uint64_t)t * (seen_mask + 1) + (mix64(hf ^ 0xd1b54a32d192ed03ull) & seen_mask);
+}
+
 // signature key of set g under Ks functions (first function most
 // significant): Ks <= 2 fits the low word, Ks 3..4 use the high word too.
 // Batched instances (count > 1): ids are global rows, instance i owning
@@ -20,7 +43,9 @@ __global__ void k_set_sig(int64_t nsets, const int64_t *__restrict__ soff,
                           const uint32_t *__restrict__ sids, int Ks, const uint64_t *__restrict__ A,
                           const uint64_t *__restrict__ B, const int64_t *__restrict__ row_off, int count,
                           const uint32_t *__restrict__ set_inst, int64_t coef_stride, uint64_t *__restrict__ klo,
-                          uint64_t *__restrict__ khi, uint32_t *__restrict__ vals, uint32_t *__restrict__ tag) {
+                          uint64_t *__restrict__ khi, uint32_t *__restrict__ vals, uint32_t *__restrict__ tag,
+                          uint32_t *__restrict__ seen1 = nullptr, uint32_t *__restrict__ seen2 = nullptr,
+                          uint64_t seen_mask = 0) {
     // blockIdx.y = SILK table of this segment (functions t*Ks .. t*Ks+Ks-1)
     const int t = blockIdx.y;
     const int64_t so = (int64_t)t * nsets;
@@ -60,6 +85,11 @@ __global__ void k_set_sig(int64_t nsets, const int64_t *__restrict__ soff,
         if (khi) khi[so + g] = hi;
         if (vals) vals[so + g] = (uint32_t)g;
         if (tag) tag[so + g] = (uint32_t)inst;
+        if (seen1) {
+            const uint64_t pos = seen_pos(sig_hash(lo, hi, (uint32_t)inst), t, seen_mask);
+            const uint32_t bit = 1u << (pos & 31);
+            if (atomicOr(&seen1[pos >> 5], bit) & bit) atomicOr(&seen2[pos >> 5], bit);
+        }
     }
 }
 
@@ -464,13 +494,6 @@ __global__ void k_wbin_ok(int64_t nbins, const int64_t *__restrict__ rs, const i
 // the first set that claimed it; sets whose full signature (and instance tag)
 // equals that set's join its group, and the first joiner sets bit 31 (the
 // group has >= 2 sets).  grp[p] = the slot of position p's group.
-__device__ __forceinline__ uint64_t mix64(uint64_t z) {
-    // SplitMix64 finalizer (Steele, Lea and Flood, 2014)
-    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
-    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
-    return z ^ (z >> 31);
-}
-
 // A slot is 64 bits: a 32-bit fingerprint of the signature (high word) and
 // the group's first set g | SLOT_MULTI (low word; g < 2^31 - 1, so a used
 // slot never equals SLOT_EMPTY).  Probes compare fingerprints first and read
@@ -524,7 +547,9 @@ __global__ void k_group_insert(int64_t NV, int64_t C, const uint64_t *__restrict
                                const uint64_t *__restrict__ khi, const uint32_t *__restrict__ tag,
                                const int64_t *__restrict__ roff, const int64_t *__restrict__ rcap,
                                uint64_t *__restrict__ slot, uint64_t *__restrict__ mkey, uint32_t *__restrict__ mval,
-                               unsigned long long *__restrict__ n_multi) {
+                               unsigned long long *__restrict__ n_multi, const uint32_t *__restrict__ seen2,
+                               uint64_t seen_mask, const int32_t *__restrict__ vw, const int64_t *__restrict__ voff,
+                               int delta, int64_t *__restrict__ singles, unsigned long long *__restrict__ n_single) {
     const int t = blockIdx.y;
     const int64_t so = (int64_t)t * NV;
     uint64_t *sl = slot + (int64_t)t * C;
@@ -534,15 +559,28 @@ __global__ void k_group_insert(int64_t NV, int64_t C, const uint64_t *__restrict
     // the whole block iterates together (the append is a block collective)
     for (int64_t gb = (int64_t)blockIdx.x * blockDim.x; gb < NV; gb += stride) {
         const int64_t g = gb + threadIdx.x;
-        bool joined = false, first = false;
+        bool joined = false, first = false, single = false;
         uint32_t rep = 0;
         uint64_t key = 0;
-        if (g < NV) {
-            const uint64_t lo = klo[so + g], hi = khi ? khi[so + g] : 0;
-            const uint32_t tg = tag ? tag[so + g] : 0;
+        bool go = g < NV;
+        uint64_t lo = 0, hi = 0, hf = 0;
+        uint32_t tg = 0;
+        if (go) {
+            lo = klo[so + g];
+            hi = khi ? khi[so + g] : 0;
+            tg = tag ? tag[so + g] : 0;
+            hf = sig_hash(lo, hi, tg);
+            if (seen2) {
+                const uint64_t pos = seen_pos(hf, t, seen_mask);
+                if (!((seen2[pos >> 5] >> (pos & 31)) & 1u)) {
+                    go = false;  // alone in its bin
+                    single = delta <= 1 && vw[g] >= 2 && voff[g + 1] - voff[g] >= delta;
+                }
+            }
+        }
+        if (go) {
             const int64_t base = tag ? roff[tg] : 0;
             const uint64_t mask = (uint64_t)(tag ? rcap[tg] : C) - 1;
-            const uint64_t hf = mix64(lo ^ mix64(hi + 0x9e3779b97f4a7c15ull * (uint64_t)(tg + 1)));
             const uint32_t fp = (uint32_t)(hf >> 32);
             const uint64_t mine = ((uint64_t)fp << 32) | (uint64_t)g;
             uint64_t h = hf & mask;
@@ -576,6 +614,10 @@ __global__ void k_group_insert(int64_t NV, int64_t C, const uint64_t *__restrict
         if (first) {
             mkey[q + 1] = key;
             mval[q + 1] = rep;
+        }
+        if (delta <= 1 && __syncthreads_or(single)) {  // (block-uniform)
+            const unsigned long long qs = block_append(single, n_single, s_wc, &s_base);
+            if (single) singles[qs] = g;
         }
     }
 }
@@ -754,12 +796,22 @@ geek_status group_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const 
     GK_TRY(scr.alloc(&counts, 2));
     GK_CUDA(ctx, cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), st));
     const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nsets, 256), (int64_t)ctx->num_sms * 8));
+    // seen-once / seen-twice maps: per table about four bits per set, at
+    // most 2^28 bits (two parts of at most 32 MB)
+    int64_t Mt = 1 << 10;
+    while (Mt < 4 * nsets && Mt < ((int64_t)1 << 28)) Mt <<= 1;
+    const int64_t M = Mt * S;
+    uint32_t *seen;
+    GK_TRY(scr.alloc(&seen, (size_t)(M / 32) * 2));
+    GK_CUDA(ctx, cudaMemsetAsync(seen, 0, sizeof(uint32_t) * (size_t)(M / 32) * 2, st));
+    uint32_t *seen1 = seen, *seen2 = seen + M / 32;
     GK_COUNT();
     k_set_sig<<<dim3(gx, S), 256, 0, st>>>(nsets, soff, sids, Ks, A, B, tagged ? bt->row_off : nullptr,
                                            tagged ? bt->count : 1, tagged ? bt->set_inst : nullptr, coef_stride,
-                                           klo, khi, nullptr, tag);
+                                           klo, khi, nullptr, tag, seen1, seen2, (uint64_t)(Mt - 1));
     GK_COUNT();
-    k_group_insert<<<dim3(gx, S), 256, 0, st>>>(nsets, C, klo, khi, tag, roff, rcap, slot, mkey, mval, counts);
+    k_group_insert<<<dim3(gx, S), 256, 0, st>>>(nsets, C, klo, khi, tag, roff, rcap, slot, mkey, mval, counts, seen2,
+                                                (uint64_t)(Mt - 1), vw, soff, delta, *singles, counts + 1);
     if (delta <= 1) {
         GK_COUNT();
         k_group_singles<<<G(ctx, S * C), 256, 0, st>>>(C, S, slot, vw, soff, delta, *singles, counts + 1);
