@@ -185,7 +185,7 @@ def run_ours(args):
         seeds = ctx.silk(bk, **silk)
         st = ctx.assign_centers(data, centres, labels, precision=p)
         info.update(k_star=seeds.k, n_multiset=seeds.n_multiset, n_buckets=bk.n_buckets,
-                    n_flagged=bk.n_flagged, n_flagged_fp64=bk.n_flagged_fp64, n_recheck_rows=st.n_recheck_rows, sse=st.sse,
+                    n_flagged=bk.n_flagged, n_flagged_fp64=bk.n_flagged_fp64, n_recheck_rows=st.n_recheck_rows, n_fp64_rows=st.n_fp64_rows, sse=st.sse,
                     key_bits=bk.key_bits_max)
         del bk, seeds
 
@@ -317,7 +317,7 @@ def run_ours(args):
         "kernel_launches_per_step": {kk: v[1] / args.steps for kk, v in tm.items() if kk.startswith("kernel.") and v[1]},
         "hash_assign_points_per_s": cfg.n * world / ((tm["hash"][0] / max(1, tm["hash"][1]) +
                                                      tm["assign"][0] / max(1, tm["assign"][1])) / 1e3),
-        "recheck": {"hash_flagged_elems": main_info["n_flagged"], "hash_fp64_elems": main_info["n_flagged_fp64"], "assign_recheck_rows": main_info["n_recheck_rows"]},
+        "recheck": {"hash_flagged_elems": main_info["n_flagged"], "hash_fp64_elems": main_info["n_flagged_fp64"], "assign_recheck_rows": main_info["n_recheck_rows"], "assign_fp64_rows": main_info["n_fp64_rows"]},
         "gpu_launches": int(launches),
         "clocks": cl,
         "roofline": roof,
@@ -430,7 +430,7 @@ def bench_batched(args, geek, ctx, pk, pk_kind):
         "gpu_launches_per_run": launches,
         "graph_launches": info["graph_launches"], "graph_captures": info["graph_captures"],
         "first_run_s": first_s, "tuned_classes": info["tuned_classes"], "tile_n_histogram": tiles,
-        "k_total": int(st["k"].sum()), "n_flagged": info["n_flagged"], "n_recheck_rows": info["n_recheck_rows"],
+        "k_total": int(st["k"].sum()), "n_flagged": info["n_flagged"], "n_recheck_rows": info["n_recheck_rows"], "n_fp64_rows": info["n_fp64_rows"],
         "key_bits": info["key_bits"],
         "assign_phase": {"bound": "tensor", "achieved": assign_tf, "peak": pk["bf16_tflops_sustained"],
                          "unit": "TFLOP/s", "frac": (assign_tf / pk["bf16_tflops_sustained"]) if assign_tf else None,

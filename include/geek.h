@@ -132,7 +132,8 @@ typedef struct geek_assign_stats {
     double sse;              /* sum over objects of the distance to its centre */
     double radius_max;       /* max over objects of that distance (Sect. 4.1) */
     int64_t k;               /* number of centres used */
-    int64_t n_recheck_rows;  /* objects whose argmin was decided in FP64 */
+    int64_t n_recheck_rows;  /* objects the fast pass left undecided (then decided exactly) */
+    int64_t n_fp64_rows;     /* of those, objects decided by the FP64 reference distance */
 } geek_assign_stats;
 
 /* ---- context ------------------------------------------------------------ */
@@ -343,11 +344,12 @@ typedef struct geek_batch_info {
     int64_t n_buckets;        /* buckets over all instances and tables */
     int64_t n_flagged;        /* projection elements rechecked */
     int64_t n_flagged_fp64;   /* of those, decided by the FP64 reference */
-    int64_t n_recheck_rows;   /* objects whose argmin was decided in FP64 */
+    int64_t n_recheck_rows;   /* objects the fast assignment pass left undecided */
     int32_t key_bits;         /* composite sort key width (instance id + key) */
     int32_t graph_launches;   /* CUDA graph replays so far (hash + assignment) */
     int32_t graph_captures;   /* graphs captured so far */
     int32_t tuned_classes;    /* (d, k) classes this batch timed for tile_n */
+    int64_t n_fp64_rows;      /* of the undecided objects, those decided by the FP64 reference */
 } geek_batch_info;
 
 /* Creates a batch of `count` (1..65535) instances; validates the parameters

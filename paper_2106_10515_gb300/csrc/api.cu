@@ -425,6 +425,7 @@ geek_status geek_assign_centers(geek_ctx *ctx, const geek_data *data, const doub
         if (data->kind != GEEK_DENSE) return set_error(ctx, GEEK_ERR_INVALID, "dense data only");
         if (!p || !labels || (k > 0 && !centers) || k < 0 || k > 0x7FFFFFFFLL)
             return set_error(ctx, GEEK_ERR_INVALID, "bad assignment arguments");
+        if (stats) *stats = geek_assign_stats{};
         cudaStream_t st = S(stream);
         EvTimer tm(ctx, "assign", st);
         Scratch scr(ctx, st);
@@ -458,6 +459,7 @@ geek_status geek_assign(geek_ctx *ctx, const geek_data *data, const geek_buckets
     try {
         GK_TRY(check_data(ctx, data));
         if (!s || !p || !labels) return set_error(ctx, GEEK_ERR_INVALID, "NULL argument");
+        if (stats) *stats = geek_assign_stats{};
         cudaStream_t st = S(stream);
         EvTimer tm(ctx, "assign", st);
         Scratch scr(ctx, st);

@@ -274,12 +274,11 @@ __global__ void k_flag_scatter(const int32_t *__restrict__ flags, const unsigned
     }
 }
 
-// Exact decision for flagged objects, one warp per object: an FP32 pass over
-// all centres (lanes over coordinates, coalesced centre reads, the row held
-// in registers) finds the smallest fast value m; a second pass takes every
-// centre whose fast value is within the FP32 window of m and decides among
-// them with the FP64 reference distance, one candidate per lane, ties to the
-// smaller index.  Flag entries are global rows; instance i owns rows
+// Exact decision for flagged objects, one warp per object, one centre per
+// lane (the row in shared memory): an FP32 pass over all centres finds the
+// smallest fast value m; a second pass takes every centre whose fast value
+// is within the FP32 window of m and decides among them with the FP64
+// reference distance, ties to the smaller index.  Flag entries are global rows; instance i owns rows
 // [row_off[i], row_off[i + 1]).  d <= 256.
 // With flag_m, entry q brings the smallest fast value of its row from the
 // tiled FP32 pass and the first pass is skipped.  Any fast value f' of any
@@ -292,7 +291,7 @@ __global__ void __launch_bounds__(256) k_assign_recheck(const RInst *__restrict_
                                                         const int32_t *__restrict__ flag_rows,
                                                         const float *__restrict__ flag_m,
                                                         const unsigned long long *__restrict__ n_flag) {
-    __shared__ float xs[8][RC_MAXD];  // the warp's row, for the FP64 candidates
+    __shared__ __align__(16) float xs[8][RC_MAXD];  // the warp's row
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -318,55 +317,50 @@ __global__ void __launch_bounds__(256) k_assign_recheck(const RInst *__restrict_
         __syncwarp();
         const float xn = sqrtf(xs2) * (1.f + 1.0e-3f);
         const float cmax = __uint_as_float(*I.cmax_bits);
-        const int nu = (d + 31) / 32;
-        // fast value of centre j (warp-uniform result)
+        // fast value of centre j, one centre per lane: the row is read from
+        // shared memory (a broadcast), the centre from its own row
+        const float *xw = xs[wib];
+        const bool v4 = (d & 3) == 0 && (((uintptr_t)I.c32) & 15) == 0;
         auto fast = [&](int64_t j) {
             const float *cr = I.c32 + j * d;
             float dot = 0.f;
-#pragma unroll
-            for (int u = 0; u < RC_MAXD / 32; u++)
-                if (u < nu) {
-                    const int t = lane + 32 * u;
-                    if (t < d) dot = fmaf(xv[u], cr[t], dot);
+            if (v4) {
+                for (int t = 0; t < d; t += 4) {
+                    const float4 c4 = *reinterpret_cast<const float4 *>(cr + t);
+                    const float4 x4 = *reinterpret_cast<const float4 *>(xw + t);
+                    dot = fmaf(x4.x, c4.x, dot);
+                    dot = fmaf(x4.y, c4.y, dot);
+                    dot = fmaf(x4.z, c4.z, dot);
+                    dot = fmaf(x4.w, c4.w, dot);
                 }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+            } else {
+                for (int t = 0; t < d; t++) dot = fmaf(xw[t], cr[t], dot);
+            }
             return fmaf(-2.f, dot, I.cn[j]);
         };
         float m = flag_m ? flag_m[q] : __int_as_float(0x7fc00000);
         if (m != m) {
             m = FLT_MAX;
-            for (int64_t j = 0; j < k; j++) m = fminf(m, fast(j));
+            for (int64_t j0 = 0; j0 < k; j0 += 32) {
+                const int64_t j = j0 + lane;
+                if (j < k) m = fminf(m, fast(j));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
         }
         const float lim = m + 2.f * window_fp32(xn, cmax, d) * (1.f + 1e-6f);
         double bD = DBL_MAX;
         int bj = 0x7FFFFFFF;
-        int64_t cand = -1;  // this lane's pending candidate
-        int nc = 0;
-        for (int64_t j = 0; j < k; j++) {
-            if (fast(j) <= lim) {  // warp-uniform
-                if (lane == nc) cand = j;
-                if (++nc == 32 || j == k - 1) {
-                    if (cand >= 0) {
-                        const double D = ref_dist(xs[wib], I.c64 + cand * d, d);
-                        if (D < bD || (D == bD && (int)cand < bj)) {
-                            bD = D;
-                            bj = (int)cand;
-                        }
-                    }
-                    cand = -1;
-                    nc = 0;
+        for (int64_t j0 = 0; j0 < k; j0 += 32) {
+            const int64_t j = j0 + lane;
+            // candidates: fast value within the window of m; the FP64
+            // reference decides among them, each lane its own
+            if (j < k && fast(j) <= lim) {
+                const double D = ref_dist(xw, I.c64 + j * d, d);
+                if (D < bD || (D == bD && (int)j < bj)) {
+                    bD = D;
+                    bj = (int)j;
                 }
-            } else if (j == k - 1 && nc > 0) {
-                if (cand >= 0) {
-                    const double D = ref_dist(xs[wib], I.c64 + cand * d, d);
-                    if (D < bD || (D == bD && (int)cand < bj)) {
-                        bD = D;
-                        bj = (int)cand;
-                    }
-                }
-                cand = -1;
-                nc = 0;
             }
         }
         // warp argmin, ties to the smaller index
@@ -665,11 +659,11 @@ geek_status assign_dense_centres(geek_ctx *ctx, Scratch &scr, const float *x, in
         k_assign_fp32<false><<<(unsigned)A.ntiles, 256, smem, st>>>(A, GatherUnits{});
         GK_LAUNCH(ctx);
     }
-    unsigned long long h_flag = 0;
+    unsigned long long h_flag = 0, h_fp64 = 0;
     GK_CUDA(ctx, cudaMemcpyAsync(&h_flag, n_flag, sizeof h_flag, cudaMemcpyDeviceToHost, st));
     GK_CUDA(ctx, cudaStreamSynchronize(st));
+    DecideBufs db;
     if (h_flag) {
-        DecideBufs db;
         GK_TRY(decide_bufs_alloc(ctx, &scr, 1, n, db));
         if (precision == GEEK_PREC_FP32) {
             // the FP32 pass already applied the FP32 window: straight to FP64
@@ -678,6 +672,7 @@ geek_status assign_dense_centres(geek_ctx *ctx, Scratch &scr, const float *x, in
             GK_COUNT();
             k_assign_recheck<<<blocks, 256, 0, st>>>(ri, roff, 1, flag_rows, flag_m, n_flag);
             GK_LAUNCH(ctx);
+            h_fp64 = h_flag;
         } else {
             GK_TRY(decide_flags(ctx, ri, roff, 1, d, flag_rows, n_flag, db, st));
         }
@@ -701,11 +696,14 @@ geek_status assign_dense_centres(geek_ctx *ctx, Scratch &scr, const float *x, in
         GK_LAUNCH(ctx);
         double h[2];
         GK_CUDA(ctx, cudaMemcpyAsync(h, out, sizeof h, cudaMemcpyDeviceToHost, st));
+        if (h_flag && precision != GEEK_PREC_FP32)
+            GK_CUDA(ctx, cudaMemcpyAsync(&h_fp64, db.n_flag2, sizeof h_fp64, cudaMemcpyDeviceToHost, st));
         GK_CUDA(ctx, cudaStreamSynchronize(st));
         stats->sse = h[0];
         stats->radius_max = h[1];
         stats->k = k;
         stats->n_recheck_rows = (int64_t)h_flag;
+        stats->n_fp64_rows = (int64_t)h_fp64;
     }
     return GEEK_OK;
 }

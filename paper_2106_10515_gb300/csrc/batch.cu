@@ -159,6 +159,7 @@ struct geek_batch {
     // ---- results of the last run
     std::vector<double> sse, rmax;
     int64_t n_recheck_rows = 0;
+    int64_t n_fp64_rows = 0;
     int graph_launches = 0, graph_captures = 0, tuned = 0;
 
     void free_assign() {
@@ -670,12 +671,14 @@ geek_status run_assign(geek_batch *b, int32_t *labels, cudaStream_t st) {
         EvTimer tk(ctx, "batch.assign_graph", st);
         GK_TRY(launch(b, b->g_assign, b->g_assign_kernels, st));
     }
-    unsigned long long nf = 0;
+    unsigned long long nf = 0, nf64 = 0;
     GK_CUDA(ctx, cudaMemcpyAsync(&nf, b->n_flag, sizeof nf, cudaMemcpyDeviceToHost, st));
+    GK_CUDA(ctx, cudaMemcpyAsync(&nf64, b->dec.n_flag2, sizeof nf64, cudaMemcpyDeviceToHost, st));
     GK_CUDA(ctx, cudaMemcpyAsync(b->sse.data(), b->sse_d, sizeof(double) * count, cudaMemcpyDeviceToHost, st));
     GK_CUDA(ctx, cudaMemcpyAsync(b->rmax.data(), b->rmax_d, sizeof(double) * count, cudaMemcpyDeviceToHost, st));
     GK_TRY(tc_plan_check(ctx, b->tc, st));  // synchronises
     b->n_recheck_rows = (int64_t)nf;
+    b->n_fp64_rows = (int64_t)nf64;
     return GEEK_OK;
 }
 
@@ -741,6 +744,7 @@ geek_status geek_batch_info_get(const geek_batch *b, geek_batch_info *info) {
     info->n_flagged = b->n_flagged;
     info->n_flagged_fp64 = b->n_flagged_fp64;
     info->n_recheck_rows = b->n_recheck_rows;
+    info->n_fp64_rows = b->n_fp64_rows;
     info->key_bits = b->key_bits;
     info->graph_launches = b->graph_launches;
     info->graph_captures = b->graph_captures;

@@ -59,7 +59,7 @@ class geek_assign_params(C.Structure):
 
 class geek_assign_stats(C.Structure):
     _fields_ = [("sse", C.c_double), ("radius_max", C.c_double), ("k", C.c_int64),
-                ("n_recheck_rows", C.c_int64)]
+                ("n_recheck_rows", C.c_int64), ("n_fp64_rows", C.c_int64)]
 
 
 class geek_instance(C.Structure):
@@ -77,7 +77,7 @@ class geek_batch_info(C.Structure):
     _fields_ = [("count", C.c_int32), ("n_total", C.c_int64), ("k_total", C.c_int64), ("n_buckets", C.c_int64),
                 ("n_flagged", C.c_int64), ("n_flagged_fp64", C.c_int64), ("n_recheck_rows", C.c_int64),
                 ("key_bits", C.c_int32), ("graph_launches", C.c_int32), ("graph_captures", C.c_int32),
-                ("tuned_classes", C.c_int32)]
+                ("tuned_classes", C.c_int32), ("n_fp64_rows", C.c_int64)]
 
 
 # every symbol declared in include/geek.h

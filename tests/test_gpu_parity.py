@@ -129,6 +129,8 @@ def test_assign_near_ties_are_exact(G, ctx):
         torch.cuda.synchronize()
         assert np.array_equal(labels.cpu().numpy(), lab_ref)
         assert st.n_recheck_rows > 0
+        # exact ties cannot be settled by any window: they reach FP64
+        assert 0 < st.n_fp64_rows <= st.n_recheck_rows
 
 
 def test_host_memory_path(G, ctx):
