@@ -492,20 +492,48 @@ __device__ __forceinline__ void shl_or(uint64_t &hi, uint64_t &lo, int b, uint64
 // coalesced loads (row stride F1 | 1 words: conflict-free row reads), when
 // they fit (PK_STAGE_MAX codes per row).
 constexpr int PK_THREADS = 128, PK_STAGE_MAX = 128;
+
+// copies `rows` consecutive code rows (F1 codes each, from row r0) to shared
+// rows of stride F1 | 1; the (row, column) of element e advance by fixed
+// steps instead of a division per element
+__device__ __forceinline__ void pk_stage_rows(int32_t *cs, const int32_t *__restrict__ codes, int64_t r0, int rows,
+                                              int F1) {
+    const int rs = F1 | 1;
+    const int dr = PK_THREADS / F1, dc = PK_THREADS % F1;
+    int r = threadIdx.x / F1, c = threadIdx.x % F1;
+    const int32_t *src = codes + r0 * F1;
+    for (int e = threadIdx.x; e < rows * F1; e += PK_THREADS) {
+        cs[r * rs + c] = src[e];
+        r += dr;
+        c += dc;
+        if (c >= F1) {
+            c -= F1;
+            r++;
+        }
+    }
+}
 __global__ void __launch_bounds__(PK_THREADS) k_pack_keys(int64_t n, int L, const int32_t *__restrict__ codes,
                                                           int F1, int K1, const int *__restrict__ fmin,
                                                           const int *__restrict__ bits,
                                                           const uint32_t *__restrict__ mh, int F2, int K2,
                                                           uint64_t *__restrict__ klo, uint64_t *__restrict__ khi) {
     extern __shared__ int32_t cs[];
+    __shared__ int s_min[PK_STAGE_MAX], s_bits[PK_STAGE_MAX];
     const bool staged = F1 > 0 && F1 <= PK_STAGE_MAX;
     const int rs = F1 | 1;
+    if (staged) {
+        for (int f = threadIdx.x; f < F1; f += PK_THREADS) {
+            s_min[f] = fmin[f];
+            s_bits[f] = bits[f];
+        }
+    }
+    const int *fm = staged ? s_min : fmin;
+    const int *bt = staged ? s_bits : bits;
     for (int64_t i0 = (int64_t)blockIdx.x * PK_THREADS; i0 < n; i0 += (int64_t)gridDim.x * PK_THREADS) {
         const int64_t i = i0 + threadIdx.x;
         if (staged) {
-            const int rows = (int)min((int64_t)PK_THREADS, n - i0);
             __syncthreads();
-            for (int e = threadIdx.x; e < rows * F1; e += PK_THREADS) cs[(e / F1) * rs + e % F1] = codes[i0 * F1 + e];
+            pk_stage_rows(cs, codes, i0, (int)min((int64_t)PK_THREADS, n - i0), F1);
             __syncthreads();
         }
         if (i >= n) continue;
@@ -515,8 +543,8 @@ __global__ void __launch_bounds__(PK_THREADS) k_pack_keys(int64_t n, int L, cons
             uint64_t hi = 0, lo = 0;
             for (int k = 0; k < K1; k++) {
                 const int f = l * K1 + k;
-                const uint32_t v = (uint32_t)((int64_t)cr[f] - (int64_t)fmin[f]);
-                shl_or(hi, lo, bits[f], v);
+                const uint32_t v = (uint32_t)((int64_t)cr[f] - (int64_t)fm[f]);
+                shl_or(hi, lo, bt[f], v);
             }
             for (int k = 0; k < K2; k++) shl_or(hi, lo, 32, mr[l * K2 + k]);
             klo[(int64_t)l * n + i] = lo;
@@ -542,9 +570,8 @@ __global__ void __launch_bounds__(PK_THREADS) k_pack_keys_batch(int64_t N, int L
     for (int64_t r0 = (int64_t)blockIdx.x * PK_THREADS; r0 < N; r0 += (int64_t)gridDim.x * PK_THREADS) {
         const int64_t r = r0 + threadIdx.x;
         if (staged) {
-            const int rows = (int)min((int64_t)PK_THREADS, N - r0);
             __syncthreads();
-            for (int e = threadIdx.x; e < rows * F1; e += PK_THREADS) cs[(e / F1) * rs + e % F1] = codes[r0 * F1 + e];
+            pk_stage_rows(cs, codes, r0, (int)min((int64_t)PK_THREADS, N - r0), F1);
             __syncthreads();
         }
         if (r >= N) continue;
