@@ -229,7 +229,10 @@ def run_ours(args):
 
     # end to end with host buffers (pinned): every step uploads x once into a
     # library-owned resident copy (geek_data_upload) that hash, SILK and the
-    # assignment share, copies the centres in and reads the labels back
+    # assignment share, copies the centres in and reads the labels back, one
+    # step after the other (no overlap of one step's upload with another's
+    # compute: host-to-device copies issued concurrently from two streams
+    # were measured to stall each other on this machine)
     e2e = None
     if not args.skip_e2e:
         xh = torch.from_numpy(wl["x"]).pin_memory()
@@ -261,8 +264,8 @@ def run_ours(args):
         h2d = xh.numel() * 4 + ch.numel() * 8  # x once, centres once
         e2e = {"value": cfg.n * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(lh.numel() * 4), "ms_per_step": e2e_s * 1e3,
-               "path": "geek_data_upload (pinned x -> resident device copy), hash, SILK, assign_centers, "
-                       "labels D2H"}
+               "path": "per step: geek_data_upload of pinned x into a resident device copy, centres H2D, "
+                       "hash, SILK, assign_centers, labels D2H"}
         del res
 
     pk, pk_kind = peaks()

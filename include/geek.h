@@ -199,6 +199,10 @@ geek_status geek_buckets_info_get(const geek_buckets *b, geek_buckets_info *info
 geek_status geek_buckets_copy_out(const geek_buckets *b, int32_t *obj_bucket, int64_t *n_buckets,
                                   int64_t *bucket_off, int32_t *members, int32_t *codes,
                                   geek_stream stream);
+/* Releases b.  Its device memory was allocated, and is freed, in stream
+ * order on the stream geek_hash ran on (no device-wide synchronisation):
+ * that stream must still exist, and work reading b on other streams must
+ * be complete. */
 geek_status geek_buckets_free(geek_buckets *b);
 
 /* ---- initial seeding, SILK (Sect. 3.2, Alg. 4) -------------------------- */
@@ -220,6 +224,8 @@ geek_status silk_seed(geek_ctx *ctx, const geek_buckets *b, const silk_params *p
 geek_status silk_seeds_info(const silk_seeds *s, int64_t *k, int64_t *n_ids, int64_t *n_multiset);
 /* off: k+1 int64, ids: n_ids int32 (device buffers). */
 geek_status silk_seeds_copy_out(const silk_seeds *s, int64_t *off, int32_t *ids, geek_stream stream);
+/* Releases s, in stream order on the stream silk_seed ran on (the same
+ * conditions as geek_buckets_free). */
 geek_status silk_seeds_free(silk_seeds *s);
 
 /* ---- data assignment (Sect. 3.3, Eq. 1) --------------------------------- */

@@ -24,8 +24,10 @@ geek_status stage(geek_ctx *ctx, Scratch &scr, const T *src, size_t count, bool 
     return GEEK_OK;
 }
 
-geek_status own_alloc(geek_ctx *ctx, void **p, size_t bytes) {
-    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+// Result buffers are stream-ordered allocations on the call's stream (no
+// device-wide synchronisation, so copies on other streams keep running).
+geek_status own_alloc(geek_ctx *ctx, void **p, size_t bytes, cudaStream_t st) {
+    cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return set_error(ctx, GEEK_ERR_NOMEM, "device allocation of %zu bytes failed", bytes);
@@ -35,11 +37,9 @@ geek_status own_alloc(geek_ctx *ctx, void **p, size_t bytes) {
 
 void free_buckets(geek_buckets *b) {
     if (!b) return;
-    cudaFree(b->obj_bucket);
-    cudaFree(b->boff);
-    cudaFree(b->members);
-    cudaFree(b->codes);
-    cudaFree(b->num_key);
+    for (void *p : {(void *)b->obj_bucket, (void *)b->boff, (void *)b->members, (void *)b->codes,
+                    (void *)b->num_key})
+        if (p) cudaFreeAsync(p, b->st);
     delete b;
 }
 
@@ -91,6 +91,7 @@ geek_status hash_impl(geek_ctx *ctx, const geek_data *data, const geek_hash_para
         ~Guard() { free_buckets(b); }
     } guard{b};
     b->ctx = ctx;
+    b->st = st;
     b->kind = kind;
     b->n = n;
     b->L = L;
@@ -108,7 +109,7 @@ geek_status hash_impl(geek_ctx *ctx, const geek_data *data, const geek_hash_para
     GK_TRY(scr.alloc(&fmin, Fm));
     GK_TRY(scr.alloc(&fmax, Fm));
     GK_TRY(scr.alloc(&bits, Fm));
-    GK_TRY(own_alloc(ctx, (void **)&b->codes, sizeof(int32_t) * (size_t)n * std::max(1, b->F)));
+    GK_TRY(own_alloc(ctx, (void **)&b->codes, sizeof(int32_t) * (size_t)n * std::max(1, b->F), st));
 
     uint32_t *mh = nullptr;
     if (F1) {
@@ -156,12 +157,12 @@ geek_status hash_impl(geek_ctx *ctx, const geek_data *data, const geek_hash_para
         int nbn = 0;
         for (int l = 0; l < L; l++) nbn = std::max(nbn, tbits[l] - 32 * K2);
         if (nbn > 64) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "numeric key wider than 64 bits");
-        GK_TRY(own_alloc(ctx, (void **)&b->num_key, sizeof(uint64_t) * (size_t)n * L));
+        GK_TRY(own_alloc(ctx, (void **)&b->num_key, sizeof(uint64_t) * (size_t)n * L, st));
         GK_TRY(pack_keys(ctx, n, L, b->codes, F1, K1, fmin, bits, nullptr, 0, 0, b->num_key, nullptr, st));
     }
 
-    GK_TRY(own_alloc(ctx, (void **)&b->members, sizeof(uint32_t) * (size_t)n * L));
-    GK_TRY(own_alloc(ctx, (void **)&b->obj_bucket, sizeof(int32_t) * (size_t)n * L));
+    GK_TRY(own_alloc(ctx, (void **)&b->members, sizeof(uint32_t) * (size_t)n * L, st));
+    GK_TRY(own_alloc(ctx, (void **)&b->obj_bucket, sizeof(int32_t) * (size_t)n * L, st));
     int64_t *boff = nullptr;
     GK_TRY(group_tables(ctx, scr, n, L, klo, khi, nbits, b->members, b->obj_bucket, &boff, b->nb, &b->NB, st));
     b->boff = boff;
@@ -297,6 +298,7 @@ geek_status silk_seed(geek_ctx *ctx, const geek_buckets *b, const silk_params *p
     silk_seeds *s = new (std::nothrow) silk_seeds();
     if (!s) return set_error(ctx, GEEK_ERR_NOMEM, "host allocation");
     s->ctx = ctx;
+    s->st = S(stream);
     geek_status st;
     try {
         EvTimer tm(ctx, "silk", S(stream));
@@ -331,8 +333,8 @@ geek_status silk_seeds_copy_out(const silk_seeds *s, int64_t *off, int32_t *ids,
 
 geek_status silk_seeds_free(silk_seeds *s) {
     if (!s) return GEEK_OK;
-    cudaFree(s->off);
-    cudaFree(s->ids);
+    if (s->off) cudaFreeAsync(s->off, s->st);
+    if (s->ids) cudaFreeAsync(s->ids, s->st);
     delete s;
     return GEEK_OK;
 }
@@ -381,7 +383,7 @@ geek_status geek_data_upload(geek_ctx *ctx, const geek_data *host, geek_resident
         for (int j = 0; j < 3; ++j) {
             if (bytes[j] <= r->cap[j]) continue;
             void *p = nullptr;
-            geek_status e = own_alloc(ctx, &p, bytes[j]);
+            geek_status e = own_alloc(ctx, &p, bytes[j], st);
             if (e != GEEK_OK) {
                 if (!*res) geek_resident_free(r);
                 return e;

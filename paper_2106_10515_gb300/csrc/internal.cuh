@@ -84,6 +84,7 @@ int grid_for(int64_t work, int threads, int num_sms);
 // Library-owned result of geek_hash.
 struct geek_buckets {
     geek_ctx *ctx = nullptr;
+    cudaStream_t st = nullptr;     // stream of creation: allocations and frees are ordered on it
     int kind = 0;
     int64_t n = 0;
     int L = 0, K = 0, Kc = 0, F = 0;
@@ -103,6 +104,7 @@ struct geek_buckets {
 
 struct silk_seeds {
     geek_ctx *ctx = nullptr;
+    cudaStream_t st = nullptr;  // stream of creation (allocations and frees)
     int64_t k = 0, n_ids = 0, n_multiset = 0;
     int64_t *off = nullptr;  // k + 1
     int32_t *ids = nullptr;  // n_ids

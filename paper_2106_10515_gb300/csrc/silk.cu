@@ -1235,7 +1235,7 @@ geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p,
     out->k = 0;
     out->n_ids = 0;
     if (D.n == 0) {
-        GK_CUDA(ctx, cudaMalloc((void **)&out->off, sizeof(int64_t)));
+        GK_CUDA(ctx, cudaMallocAsync((void **)&out->off, sizeof(int64_t), st));
         GK_CUDA(ctx, cudaMemsetAsync(out->off, 0, sizeof(int64_t), st));
         GK_CUDA(ctx, cudaStreamSynchronize(st));
         return GEEK_OK;
@@ -1274,8 +1274,8 @@ geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p,
     Csr E;
     GK_TRY(gather_sets(ctx, scr, k, sel, D.off, D.ids, &E, st));
     // hand the final CSR to the handle (persistent allocations)
-    GK_CUDA(ctx, cudaMalloc((void **)&out->off, sizeof(int64_t) * (k + 1)));
-    GK_CUDA(ctx, cudaMalloc((void **)&out->ids, sizeof(int32_t) * std::max<int64_t>(1, E.nids)));
+    GK_CUDA(ctx, cudaMallocAsync((void **)&out->off, sizeof(int64_t) * (k + 1), st));
+    GK_CUDA(ctx, cudaMallocAsync((void **)&out->ids, sizeof(int32_t) * std::max<int64_t>(1, E.nids), st));
     GK_CUDA(ctx, cudaMemcpyAsync(out->off, E.off, sizeof(int64_t) * (k + 1), cudaMemcpyDeviceToDevice, st));
     if (E.nids)
         GK_CUDA(ctx, cudaMemcpyAsync(out->ids, E.ids, sizeof(uint32_t) * E.nids, cudaMemcpyDeviceToDevice, st));
