@@ -379,8 +379,12 @@ def bench_batched(args, geek, ctx, pk, pk_kind):
     l0 = geek.launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(args.steps):
+    for i in range(args.steps):
+        if args.profile_batch_run and i == 0:
+            torch.cuda.profiler.start()  # scopes ncu --profile-from-start off to one run
         b.run(labels)
+        if args.profile_batch_run and i == 0:
+            torch.cuda.profiler.stop()
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
@@ -503,6 +507,8 @@ def main():
     ap.add_argument("--skip-batch", action="store_true", help="skip the 256-instance batched measurement")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--batch-only", action="store_true", help="run only the batched measurement (profiling)")
+    ap.add_argument("--profile-batch-run", action="store_true",
+                    help="bracket the first timed batched run with cudaProfilerStart/Stop")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours" and args.n is None:
         args.warmup = 3
