@@ -426,21 +426,37 @@ __global__ void __launch_bounds__(256) k_assign_stats(const float *__restrict__ 
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double s = 0.0;
     float mx = 0.f;
-    for (int64_t i = warp; i < n; i += nw) {
-        const int j = labels[i];
-        if (j < 0 || j >= k) continue;  // uniform across the warp
-        const float *xr = x + i * ldx;
-        const float *h = chi + (int64_t)j * d;
-        const float *l = clo + (int64_t)j * d;
-        float D = 0.f;
-        for (int t = lane; t < d; t += 32) {
-            const float e = (xr[t] - h[t]) - l[t];
-            D = fmaf(e, e, D);
+    // four rows in flight per warp (independent loads and reductions)
+    for (int64_t i0 = warp; i0 < n; i0 += 4 * nw) {
+        float D[4];
+        bool ok[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int64_t i = i0 + q * nw;
+            const int j = i < n ? labels[i] : -1;
+            ok[q] = j >= 0 && j < k;  // uniform across the warp
+            D[q] = 0.f;
+            if (ok[q]) {
+                const float *xr = x + i * ldx;
+                const float *h = chi + (int64_t)j * d;
+                const float *l = clo + (int64_t)j * d;
+                for (int t = lane; t < d; t += 32) {
+                    const float e = (xr[t] - h[t]) - l[t];
+                    D[q] = fmaf(e, e, D[q]);
+                }
+            }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) D += __shfl_xor_sync(0xffffffffu, D, o);
-        s += (double)D;
-        mx = fmaxf(mx, D);
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int q = 0; q < 4; q++) D[q] += __shfl_xor_sync(0xffffffffu, D[q], o);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            if (ok[q]) {
+                s += (double)D[q];
+                mx = fmaxf(mx, D[q]);
+            }
     }
     if (lane == 0) {
         ss[wib] = s;
@@ -525,23 +541,37 @@ __global__ void __launch_bounds__(256) k_assign_stats_batch(const SInst *__restr
         const SInst &I = S[un.x];
         double s = 0.0;
         float mx = 0.f;
-        for (int r = wib; r < 128; r += 8) {
-            const int64_t i = (int64_t)un.y * 128 + r;
-            if (i >= I.n) break;
-            const int j = I.labels[i];
-            if (j < 0 || j >= I.k) continue;  // uniform across the warp
-            const float *xr = I.x + i * I.ldx;
-            const float *h = I.chi + (int64_t)j * I.d;
-            const float *l = I.clo + (int64_t)j * I.d;
-            float D = 0.f;
-            for (int t = lane; t < I.d; t += 32) {
-                const float e = (xr[t] - h[t]) - l[t];
-                D = fmaf(e, e, D);
+        // rows wib, wib + 8, ... of the unit, four in flight per warp
+        for (int r0 = wib; r0 < 128; r0 += 32) {
+            float D[4];
+            bool ok[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int64_t i = (int64_t)un.y * 128 + r0 + 8 * q;
+                const int j = i < I.n ? I.labels[i] : -1;
+                ok[q] = j >= 0 && j < I.k;  // uniform across the warp
+                D[q] = 0.f;
+                if (ok[q]) {
+                    const float *xr = I.x + i * I.ldx;
+                    const float *h = I.chi + (int64_t)j * I.d;
+                    const float *l = I.clo + (int64_t)j * I.d;
+                    for (int t = lane; t < I.d; t += 32) {
+                        const float e = (xr[t] - h[t]) - l[t];
+                        D[q] = fmaf(e, e, D[q]);
+                    }
+                }
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) D += __shfl_xor_sync(0xffffffffu, D, o);
-            s += (double)D;
-            mx = fmaxf(mx, D);
+            for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                for (int q = 0; q < 4; q++) D[q] += __shfl_xor_sync(0xffffffffu, D[q], o);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                if (ok[q]) {
+                    s += (double)D[q];
+                    mx = fmaxf(mx, D[q]);
+                }
         }
         __syncthreads();
         if (lane == 0) {

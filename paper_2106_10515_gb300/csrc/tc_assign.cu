@@ -535,8 +535,20 @@ __global__ void k_x_to_bf16(const TcXPrep *__restrict__ X, const int64_t *__rest
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r = warp; r < N; r += nw) {
-        const int ii = find_inst(row_off, count, r);
+    // one instance: rows strided over the warps; several: a contiguous range
+    // of rows per warp, the instance looked up again only when the range
+    // crosses into the next one
+    const bool one = count == 1;
+    const int64_t per = one ? 0 : (N + nw - 1) / nw;
+    const int64_t rbeg = one ? warp : warp * per, rend = one ? N : min(N, rbeg + per), rstep = one ? nw : 1;
+    int ii = 0;
+    int64_t ilo = 0, ihi = one ? N : -1;
+    for (int64_t r = rbeg; r < rend; r += rstep) {
+        if (r < ilo || r >= ihi) {
+            ii = find_inst(row_off, count, r);
+            ilo = row_off[ii];
+            ihi = row_off[ii + 1];
+        }
         const TcXPrep &P = X[ii];
         const int64_t i = r - row_off[ii];
         const int W = P.split ? 2 * P.Kp : P.Kp;
