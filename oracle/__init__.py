@@ -8,6 +8,8 @@ module marshals NumPy arrays and composes the steps in the paper's order:
 
 * dense data (Sect. 3.1): E2LSH codes floor((a.x+b)/w) (or sign bits), K per
   table concatenated over L tables (the static (K,L) framework, Sect. 2.2);
+* dense data, the paper's own transform (Alg. 1): m QALSH projections a.x,
+  each table sorted (ties by object id) and split evenly into t buckets;
 * sparse sets (Alg. 3, without DOPH): MinHash (Eq. 2), K per table, L tables;
 * heterogeneous rows (Alg. 2): E2LSH codes of the numeric part concatenated
   with MinHash of the categorical tokens, per table;
@@ -34,6 +36,8 @@ _lib = None
 PINS = {
     "e2lsh": "exact rational floor((a.x+b)/w) with fractions.Fraction (brute force)",
     "srp": "exact rational sign of a.x (brute force)",
+    "alg1": "exact rational projections sorted by (value, id) and split by floor(b n / t) (brute force); "
+            "bucket sizes, tie order and the t = 1 / t = n cases",
     "hash32": "Python big-integer (A*x+B) mod 2^64 >> 32",
     "minhash": "explicit set minima in Python; collision rate = Jaccard (Eq. 2)",
     "group": "Python dict of tuples, canonical rank by sorted distinct keys",
@@ -69,6 +73,7 @@ def lib():
         i64, i32, f64 = C.c_int64, C.c_int32, C.c_double
         L.orc_e2lsh.argtypes = [i64, i32, P, i64, i32, P, P, f64, P]
         L.orc_srp.argtypes = [i64, i32, P, i64, i32, P, P]
+        L.orc_qalsh.argtypes = [i64, i32, P, i64, i32, P, P]
         L.orc_hash32.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32]
         L.orc_hash32.restype = C.c_uint32
         L.orc_minhash_csr.argtypes = [i64, P, P, i32, P, P, P]
@@ -193,6 +198,48 @@ def table_keys(codes, L, K):
 def hash_dense(x, a, b, w, K, L, proj="e2lsh"):
     codes = e2lsh(x, a, b, w) if proj == "e2lsh" else srp(x, a).astype(np.int32)
     return codes, group(table_keys(codes, L, K))
+
+
+def qalsh(x, a):
+    """s[i, f] = a_f . x_i (pinned FP64 sequence), the QALSH value of Alg. 1."""
+    x = _c(x, np.float32); a = _c(a, np.float32)
+    n, d = x.shape
+    m = a.shape[0]
+    out = np.empty((n, m), dtype=np.float64)
+    _chk(lib().orc_qalsh(n, d, _p(x), d, m, _p(a), _p(out)), "qalsh")
+    return out
+
+
+def split_even(values, t):
+    """One table of Alg. 1: objects sorted by (value, id) ascending, the
+    sorted list cut into t parts; part b holds sorted positions
+    [floor(b n / t), floor((b + 1) n / t)).  Returns the bucket of every
+    object (ties between equal values go by ascending object id)."""
+    n = values.shape[0]
+    order = np.lexsort((np.arange(n), values))  # primary key: value, then id
+    bucket_at = (np.arange(1, n + 1) * t + n - 1) // n - 1  # largest b with floor(b n / t) <= p
+    ob = np.empty(n, dtype=np.int32)
+    ob[order] = bucket_at
+    return ob
+
+
+def transform_alg1(x, a, t):
+    """Alg. 1: m = rows of a QALSH functions, one table each, t buckets per
+    table.  Returns (s, Buckets) with canonical bucket id = part index."""
+    s = qalsh(x, a)
+    n, m = s.shape
+    if not 1 <= t <= max(n, 1):
+        raise ValueError("need 1 <= t <= n")
+    ob = np.empty((m, n), dtype=np.int32)
+    nb = np.full(m, t, dtype=np.int64)
+    mem = np.empty((m, n), dtype=np.int32)
+    bo = np.zeros((m, n + 1), dtype=np.int64)
+    cuts = (np.arange(t) * n) // t
+    for f in range(m):
+        ob[f] = split_even(s[:, f], t)
+        mem[f] = np.argsort(ob[f], kind="stable")  # by bucket, ascending id inside
+        bo[f, :t] = cuts
+    return s, Buckets(ob, nb, mem, bo)
 
 
 def hash_sets(off, items, A, B, K, L):

@@ -62,6 +62,29 @@ int orc_e2lsh(int64_t n, int32_t d, const float *x, int64_t ldx, int32_t F,
     return bad ? ORC_OVERFLOW : ORC_OK;
 }
 
+/* QALSH projection values of Alg. 1 (Sect. 3.1, homogeneous dense data):
+ * s[i*m + f] = a_f . x_i with the pinned FP64 dot product (products of the
+ * float inputs, summed in j order, no fused multiply-add). */
+int orc_qalsh(int64_t n, int32_t d, const float *x, int64_t ldx, int32_t m,
+              const float *a, double *s)
+{
+    if (n < 0 || d <= 0 || m <= 0 || ldx < d) return ORC_INVALID;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++) {
+        const float *xi = x + i * ldx;
+        for (int32_t f = 0; f < m; f++) {
+            const float *af = a + (int64_t)f * d;
+            double acc = 0.0;
+            for (int32_t j = 0; j < d; j++) {
+                double p = (double)af[j] * (double)xi[j];
+                acc = acc + p;
+            }
+            s[i * m + f] = acc;
+        }
+    }
+    return ORC_OK;
+}
+
 /* Sign random projection (SimHash, cited in Sect. 1): bit = [a.x >= 0],
  * with the same pinned dot product; -0.0 counts as >= 0. */
 int orc_srp(int64_t n, int32_t d, const float *x, int64_t ldx, int32_t F,

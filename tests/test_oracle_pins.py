@@ -95,6 +95,55 @@ def test_srp_matches_exact_sign(orc):
             assert got[i, f] == (1 if v >= 0 else 0)
 
 
+# ------------------------------------------------- Alg. 1 (QALSH split) --
+def exact_alg1(x, a, t):
+    """Alg. 1 by hand: exact rational projections, objects sorted by (value,
+    id), the sorted list cut at floor(b n / t)."""
+    n, d = x.shape
+    ob = np.empty((a.shape[0], n), dtype=np.int64)
+    for f in range(a.shape[0]):
+        v = [sum(Fraction(float(a[f, j])) * Fraction(float(x[i, j])) for j in range(d)) for i in range(n)]
+        order = sorted(range(n), key=lambda i: (v[i], i))
+        cuts = [(b * n) // t for b in range(t)] + [n]
+        for b in range(t):
+            for pos in range(cuts[b], cuts[b + 1]):
+                ob[f, order[pos]] = b
+    return ob
+
+
+@pytest.mark.parametrize("n,t", [(61, 7), (40, 1), (23, 23), (50, 3)])
+def test_alg1_matches_exact_rational_split(orc, n, t):
+    rng = np.random.default_rng(n * 31 + t)
+    x = rng.standard_normal((n, 5)).astype(np.float32)
+    a = rng.standard_normal((3, 5)).astype(np.float32)
+    x[7 % n] = x[3 % n]  # two identical objects: equal values, id order decides
+    s, B = orc.transform_alg1(x, a, t)
+    assert np.array_equal(B.obj_bucket, exact_alg1(x, a, t))
+    # every table is a partition into t parts of the even sizes
+    want = np.diff((np.arange(t + 1) * n) // t)
+    for f in range(3):
+        assert np.array_equal(np.bincount(B.obj_bucket[f], minlength=t), want)
+        # part b's values never exceed part b + 1's
+        for b in range(t - 1):
+            lo, hi = s[B.obj_bucket[f] == b, f], s[B.obj_bucket[f] == b + 1, f]
+            if lo.size and hi.size:
+                assert lo.max() <= hi.min()
+    assert B.NB == 3 * t
+    # members ascending inside each bucket, offsets at f * n + floor(b n / t)
+    for g in range(B.NB):
+        mem = B.bmem[B.boff[g]:B.boff[g + 1]]
+        assert np.all(np.diff(mem) > 0)
+    assert B.boff[1] == (n // t if t > 1 else n)
+
+
+def test_alg1_ties_follow_ids(orc):
+    # all objects equal: every projection ties, so the parts are id ranges
+    x = np.ones((10, 4), dtype=np.float32)
+    a = np.random.default_rng(2).standard_normal((2, 4)).astype(np.float32)
+    _, B = orc.transform_alg1(x, a, 3)
+    assert B.obj_bucket.tolist() == [[0, 0, 0, 1, 1, 1, 2, 2, 2, 2]] * 2
+
+
 # --------------------------------------------------------------- MinHash --
 def test_hash32_against_big_integers(orc):
     rng = random.Random(4)
