@@ -53,7 +53,7 @@ enum { GEEK_DENSE = 0, GEEK_SETS = 1, GEEK_HETERO = 2 };
 /* where the data arrays of a geek_data live */
 enum { GEEK_MEM_DEVICE = 0, GEEK_MEM_HOST = 1 };
 /* dense projection family */
-enum { GEEK_PROJ_E2LSH = 0, GEEK_PROJ_SRP = 1 };
+enum { GEEK_PROJ_E2LSH = 0, GEEK_PROJ_SRP = 1, GEEK_PROJ_QALSH = 2 };
 /* arithmetic of the fast path (FP64 rechecks keep every result exact):
  * FP32 SIMT; BF16 tcgen05 (one product per term, error window ~2^-7 |x||c|);
  * split-BF16 tcgen05 (x = x_h + x_l, c = c_h + c_l in BF16 pairs, three
@@ -93,7 +93,15 @@ typedef struct geek_data {
  *  Hetero: additionally Kc MinHash functions per table (Kc*L coefficient
  *    pairs) over each row's token set, appended to the table key.
  * Table l's key is the tuple of its K (+ Kc) values, compared
- * lexicographically (codes signed, MinHash values unsigned). */
+ * lexicographically (codes signed, MinHash values unsigned).
+ *  proj = QALSH (Alg. 1, the paper's own transform of dense data): K = 1 and
+ *    L = m tables, one per projection a_l (b and w unused); table l sorts
+ *    the objects by s = a_l.x (the pinned FP64 dot product defined for
+ *    E2LSH) with ties by ascending object id and cuts the sorted list into
+ *    t buckets: bucket j holds sorted positions [floor(j n / t),
+ *    floor((j + 1) n / t)), 1 <= t <= n.  codes then hold the FP32 bit
+ *    patterns of the projections (approximate; the buckets are exact).
+ *    DENSE data only; finite inputs. */
 typedef struct geek_hash_params {
     int32_t proj;
     int32_t precision;
@@ -103,6 +111,7 @@ typedef struct geek_hash_params {
     const float *b;
     const uint64_t *mh_a;
     const uint64_t *mh_b;
+    int32_t t;           /* QALSH: buckets per table (ignored otherwise) */
 } geek_hash_params;
 
 typedef struct geek_buckets_info {

@@ -74,8 +74,13 @@ geek_status hash_impl(geek_ctx *ctx, const geek_data *data, const geek_hash_para
     if (kind != GEEK_SETS) {
         if (!p->a || (p->proj == GEEK_PROJ_E2LSH && (!p->b || !(p->w > 0.0))))
             return set_error(ctx, GEEK_ERR_INVALID, "projection parameters missing");
-        if (p->proj != GEEK_PROJ_E2LSH && p->proj != GEEK_PROJ_SRP)
+        if (p->proj != GEEK_PROJ_E2LSH && p->proj != GEEK_PROJ_SRP && p->proj != GEEK_PROJ_QALSH)
             return set_error(ctx, GEEK_ERR_INVALID, "bad proj");
+    }
+    if (p->proj == GEEK_PROJ_QALSH && kind != GEEK_SETS) {
+        if (kind != GEEK_DENSE || K != 1)
+            return set_error(ctx, GEEK_ERR_INVALID, "QALSH (Alg. 1): dense data, K = 1, one table per projection");
+        if (n > 0 && (p->t < 1 || p->t > n)) return set_error(ctx, GEEK_ERR_INVALID, "QALSH: need 1 <= t <= n");
     }
     if ((kind == GEEK_SETS || kind == GEEK_HETERO) && (!p->mh_a || !p->mh_b))
         return set_error(ctx, GEEK_ERR_INVALID, "MinHash coefficients missing");
@@ -110,6 +115,18 @@ geek_status hash_impl(geek_ctx *ctx, const geek_data *data, const geek_hash_para
     GK_TRY(scr.alloc(&fmax, Fm));
     GK_TRY(scr.alloc(&bits, Fm));
     GK_TRY(own_alloc(ctx, (void **)&b->codes, sizeof(int32_t) * (size_t)n * std::max(1, b->F), st));
+
+    if (kind == GEEK_DENSE && p->proj == GEEK_PROJ_QALSH) {  // Alg. 1
+        const float *x;
+        GK_TRY(stage(ctx, scr, data->x, (size_t)n * data->ldx, host, &x, st));
+        GK_TRY(own_alloc(ctx, (void **)&b->members, sizeof(uint32_t) * (size_t)n * L, st));
+        GK_TRY(own_alloc(ctx, (void **)&b->obj_bucket, sizeof(int32_t) * (size_t)n * L, st));
+        GK_TRY(hash_qalsh(ctx, scr, x, data->ldx, n, data->d, p->a, L, p->t, b, st));
+        GK_CUDA(ctx, cudaStreamSynchronize(st));
+        guard.b = nullptr;
+        *out = b;
+        return GEEK_OK;
+    }
 
     uint32_t *mh = nullptr;
     if (F1) {

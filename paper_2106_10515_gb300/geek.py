@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libgeek.so")
 OK, ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_OVERFLOW, ERR_UNSUPPORTED = range(7)
 DENSE, SETS, HETERO = 0, 1, 2
 MEM_DEVICE, MEM_HOST = 0, 1
-PROJ_E2LSH, PROJ_SRP = 0, 1
+PROJ_E2LSH, PROJ_SRP, PROJ_QALSH = 0, 1, 2
 PREC_FP32, PREC_BF16, PREC_BF16X3 = 0, 1, 2
 PREC_AUTO = -1
 STATUS_NAMES = ["OK", "ERR_INVALID", "ERR_NOMEM", "ERR_CUDA", "ERR_TIMEOUT", "ERR_OVERFLOW",
@@ -40,7 +40,7 @@ class geek_data(C.Structure):
 class geek_hash_params(C.Structure):
     _fields_ = [("proj", C.c_int32), ("precision", C.c_int32), ("K", C.c_int32), ("L", C.c_int32),
                 ("Kc", C.c_int32), ("w", C.c_double), ("a", C.c_void_p), ("b", C.c_void_p),
-                ("mh_a", C.c_void_p), ("mh_b", C.c_void_p)]
+                ("mh_a", C.c_void_p), ("mh_b", C.c_void_p), ("t", C.c_int32)]
 
 
 class geek_buckets_info(C.Structure):
@@ -333,9 +333,9 @@ class Context:
 
     # ---------------------------------------------------------------- hash --
     def hash(self, data, K, L, a=None, b=None, w=4.0, mh_a=None, mh_b=None, Kc=0,
-             proj=PROJ_E2LSH, precision=PREC_FP32) -> Buckets:
+             proj=PROJ_E2LSH, precision=PREC_FP32, t=0) -> Buckets:
         p = geek_hash_params()
-        p.proj, p.precision, p.K, p.L, p.Kc, p.w = proj, precision, K, L, Kc, float(w)
+        p.proj, p.precision, p.K, p.L, p.Kc, p.w, p.t = proj, precision, K, L, Kc, float(w), t
         p.a, p.b, p.mh_a, p.mh_b = _ptr(a), _ptr(b), _ptr(mh_a), _ptr(mh_b)
         out = C.c_void_p()
         self._chk(lib().geek_hash(self.h, C.byref(data.c), C.byref(p), C.byref(out), _stream()))

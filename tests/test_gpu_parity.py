@@ -226,3 +226,74 @@ def test_hetero_c4_shape_pipeline(G, ctx, over):
     ctx.assign(data, bk, seeds, labels)
     torch.cuda.synchronize()
     assert np.array_equal(labels.cpu().numpy(), ref["labels"])
+
+
+# ------------------------------------------- Alg. 1 (QALSH, even split) --
+def qalsh_buckets(G, ctx, x, a, t):
+    m = a.shape[0]
+    bk = ctx.hash(ctx.dense(G._dev(x)), 1, m, a=G._dev(a), proj=G.PROJ_QALSH, t=t)
+    torch.cuda.synchronize()
+    return bk
+
+
+def check_alg1(got, ref):
+    assert np.array_equal(got["n_buckets"], ref.n_buckets)
+    assert np.array_equal(got["obj_bucket"].cpu().numpy(), ref.obj_bucket)
+    assert np.array_equal(got["bucket_off"].cpu().numpy(), ref.boff)
+    assert np.array_equal(got["members"].cpu().numpy(), ref.bmem)
+
+
+@pytest.mark.parametrize("n,m,t", [(20000, 8, 7), (20000, 8, 1), (6001, 5, 6001), (30001, 12, 300), (777, 3, 50)])
+def test_alg1_buckets_exact(G, ctx, n, m, t):
+    """Alg. 1: the FP32 order is fixed near every cut with FP64 values, so
+    the parts equal the oracle's exact split (sizes, members, ids)."""
+    wl = synth.make(synth.config("c1", n=n))
+    x, a = wl["x"], wl["a"][:m]
+    bk = qalsh_buckets(G, ctx, x, a, t)
+    _, ref = oracle.transform_alg1(x, a, t)
+    check_alg1(bk.copy_out(), ref)
+
+
+def test_alg1_ties_and_near_ties(G, ctx):
+    """Duplicated rows (exact ties, decided by id), rows a few ulps apart
+    across the cuts, and zero rows (+0 and -0 projections)."""
+    rng = np.random.default_rng(17)
+    n, d, m, t = 5000, 16, 6, 40
+    x = rng.standard_normal((n, d)).astype(np.float32)
+    x[1000:1400] = x[5]                      # 400 identical rows
+    x[2000:2300] = 0.0                       # projections exactly 0
+    x[2300:2310] = -0.0
+    base = x[300].copy()
+    for i in range(3000, 3600):              # rows within a few ulps of each other
+        x[i] = np.nextafter(base, np.float32(np.inf)) if i % 2 else base
+    a = rng.standard_normal((m, d)).astype(np.float32)
+    bk = qalsh_buckets(G, ctx, x, a, t)
+    _, ref = oracle.transform_alg1(x, a, t)
+    check_alg1(bk.copy_out(), ref)
+
+
+def test_alg1_feeds_silk_and_assignment(G, ctx):
+    """Alg. 1 buckets through SILK seeding and the one-pass assignment."""
+    wl = synth.make(synth.config("c1", n=12000))
+    x, a = wl["x"], wl["a"][:16]
+    bk = qalsh_buckets(G, ctx, x, a, 400)
+    _, ref_b = oracle.transform_alg1(x, a, 400)
+    seeds = ctx.silk(bk, **G.silk_args(wl["silk"]))
+    ref_s = oracle.silk_on(ref_b, wl["silk"])
+    assert seeds.sets() == ref_s.sets()
+    if seeds.k:
+        labels = torch.empty(x.shape[0], dtype=torch.int32, device="cuda")
+        ctx.assign(ctx.dense(G._dev(x)), bk, seeds, labels, precision=G.PREC_BF16)
+        torch.cuda.synchronize()
+        c = oracle.centroids(x, ref_s)
+        lab_ref, _ = oracle.assign_dense(x, c)
+        assert np.array_equal(labels.cpu().numpy(), lab_ref)
+
+
+def test_alg1_invalid(G, ctx):
+    wl = synth.make(synth.config("c1", n=100))
+    x = G._dev(wl["x"])
+    for K, t in ((2, 10), (1, 0), (1, 101)):
+        with pytest.raises(G.GeekError) as e:
+            ctx.hash(ctx.dense(x), K, 4, a=G._dev(wl["a"][:4 * K]), proj=G.PROJ_QALSH, t=t)
+        assert e.value.status == G.ERR_INVALID
