@@ -329,6 +329,8 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "generate_s": t_gen,
     }
+    if not args.skip_alg1:
+        line["alg1_transform"] = bench_alg1(args, geek, ctx, data, wl, world)
     if not args.skip_batch and world == 1:
         line["batched"] = bench_batched(args, geek, ctx, pk, pk_kind)
     if ms_other is not None:
@@ -343,6 +345,41 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def bench_alg1(args, geek, ctx, data, wl, world):
+    """The paper's own dense transform (Alg. 1) on the same resident points:
+    m QALSH projections, each table sorted and cut into t even buckets,
+    exact at every cut (FP64 re-sort of the objects near each cut)."""
+    import torch
+    cfg = wl["cfg"]
+    m, t = args.alg1_m, args.alg1_t
+    a = geek._dev(np.ascontiguousarray(wl["a"][:m]))
+
+    def run():
+        bk = ctx.hash(data, 1, m, a=a, proj=geek.PROJ_QALSH, t=t)
+        nb = bk.n_buckets
+        del bk
+        return nb
+
+    for _ in range(max(1, args.warmup)):
+        run()
+    torch.cuda.synchronize()
+    ctx.timing_reset()
+    ctx.timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        nb = run()
+    e1.record()
+    torch.cuda.synchronize()
+    ctx.timing(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    tm = {k: ctx.timing_get(k) for k in ("hash", "hash.sort", "kernel.project_dot2")}
+    return {"workload": f"Alg. 1 on the dense points above: n={cfg.n} d={cfg.d}, m={m} QALSH tables, t={t} "
+                        f"buckets each (paper grid m in {{20,40,60}}, t in [5k, 30k])",
+            "value": cfg.n * world / (ms / 1e3), "unit": UNIT, "ms_per_run": ms, "n_buckets": int(nb),
+            "phases_ms_per_run": {k: v[0] / args.steps for k, v in tm.items()}}
 
 
 def bench_batched(args, geek, ctx, pk, pk_kind):
@@ -506,6 +543,9 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batch", action="store_true", help="skip the 256-instance batched measurement")
     ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--skip-alg1", action="store_true", help="skip the Alg. 1 transform measurement")
+    ap.add_argument("--alg1-m", type=int, default=40, help="Alg. 1: QALSH tables")
+    ap.add_argument("--alg1-t", type=int, default=20000, help="Alg. 1: buckets per table")
     ap.add_argument("--batch-only", action="store_true", help="run only the batched measurement (profiling)")
     ap.add_argument("--profile-batch-run", action="store_true",
                     help="bracket the first timed batched run with cudaProfilerStart/Stop")

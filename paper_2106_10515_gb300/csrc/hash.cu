@@ -33,10 +33,7 @@ constexpr int PJ_MAXT = 256;    // threads per block (upper bound)
 // instance i with tile_off[i] <= b < tile_off[i + 1], whose pointers and
 // sizes P[i] replace A's; the thread layout (F, FPAD, FG, RG) and the flag
 // list are common to the batch and stay A's.
-// RAW (Alg. 1's QALSH values): the epilogue stores the bit patterns of the
-// FP32 dot products and raises *A.xmax_bits to the largest row-norm bound; no
-// codes, windows or flags.
-template <bool BATCH, bool RAW = false>
+template <bool BATCH>
 __global__ void __launch_bounds__(PJ_MAXT, 2) k_project_fp32(ProjArgs A, const ProjArgs *__restrict__ P,
                                                           const int64_t *__restrict__ tile_off, int count) {
     int64_t tile = blockIdx.x;
@@ -162,25 +159,6 @@ __global__ void __launch_bounds__(PJ_MAXT, 2) k_project_fp32(ProjArgs A, const P
         __syncthreads();  // the next stage() overwrites this buffer
     }
     __syncthreads();
-    if constexpr (RAW) {
-        float xm = 0.f;
-        if (active) {
-#pragma unroll
-            for (int r = 0; r < PJ_RPT; r++) {
-                const int64_t row = row0 + rg * PJ_RPT + r;
-                if (row >= A.n) continue;
-                xm = fmaxf(xm, sqrtf(xsq[r]) * 1.0001f);
-                int32_t *dst = A.codes + row * A.F + fg * PJ_FPT;
-#pragma unroll
-                for (int c = 0; c < PJ_FPT; c++)
-                    if (fg * PJ_FPT + c < A.F) dst[c] = __float_as_int(acc[r][c]);
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) xm = fmaxf(xm, __shfl_xor_sync(0xffffffffu, xm, o));
-        if ((t & 31) == 0 && xm > 0.f) atomicMax(A.xmax_bits, __float_as_uint(xm));  // positive: bits order
-        return;
-    }
     unsigned nfl = 0;
     uint64_t flagmask = 0;  // bit r*8 + c: element (row r, function c) is uncertain
     if (active) {
@@ -661,34 +639,6 @@ static void proj_layout(ProjArgs &A, int F) {
 static int proj_rows(const ProjArgs &A) { return A.RG * PJ_RPT; }
 static int proj_threads(const ProjArgs &A) { return (int)ceil_div(A.FG * A.RG, 32) * 32; }  // whole warps
 static size_t proj_smem(const ProjArgs &A) { return 2 * (size_t)PJ_KC * (proj_rows(A) + A.FPAD) * sizeof(float); }
-
-geek_status project_raw(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ldx, int64_t n, int d,
-                        const float *a, int F, float *vals, float *anorm, unsigned *xmax_bits, cudaStream_t st) {
-    if (F > 512) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "more than 512 projections");
-    if (d > 100000) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "d > 100000");
-    GK_COUNT();
-    k_row_norms<<<(F + 127) / 128, 128, 0, st>>>(a, F, d, anorm);
-    GK_LAUNCH(ctx);
-    GK_CUDA(ctx, cudaMemsetAsync(xmax_bits, 0, sizeof(unsigned), st));
-    if (n == 0) return GEEK_OK;
-    ProjArgs A{};
-    A.x = x; A.ldx = ldx; A.n = n; A.d = d;
-    proj_layout(A, F);
-    A.a = a; A.anorm = anorm;
-    A.codes = (int32_t *)vals;
-    A.xmax_bits = xmax_bits;
-    const int threads = proj_threads(A);
-    const size_t smem = proj_smem(A);
-    if (smem > 200 * 1024) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "projection tile too large");
-    GK_CUDA(ctx, cudaFuncSetAttribute(k_project_fp32<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-    EvTimer tk(ctx, "kernel.project_fp32", st);
-    tk.work = 2.0 * (double)n * (double)F * (double)d;
-    GK_COUNT();
-    k_project_fp32<false, true><<<(unsigned)ceil_div(n, proj_rows(A)), threads, smem, st>>>(A, nullptr, nullptr, 1);
-    GK_LAUNCH(ctx);
-    return GEEK_OK;
-}
 
 geek_status project_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ldx, int64_t n,
                           int d, const float *a, const float *b, int F, double w, int srp,

@@ -26,7 +26,6 @@ struct ProjArgs {
     int *fmin, *fmax;     // F
     double wd;            // w as given (the reference divides by it in FP64)
     int64_t row_base;     // global row of local row 0 (flag list entries)
-    unsigned *xmax_bits;  // raw projections only: max row-norm bound (float bits)
 };
 
 // One dense instance of a batch (device pointers).
@@ -76,10 +75,6 @@ geek_status key_layout(geek_ctx *ctx, Scratch &scr, const int *fmin, const int *
 geek_status pack_keys(geek_ctx *ctx, int64_t n, int L, const int32_t *codes, int F1, int K1,
                       const int *fmin, const int *bits, const uint32_t *mh, int F2, int K2,
                       uint64_t *klo, uint64_t *khi, cudaStream_t st);
-// FP32 projections a_f . x_i of every row (vals n x F, FP32 sums in k order), the norms |a_f| (times 1.0001) and, in *xmax_bits,
-// the float bits of the largest row-norm bound |x_i| (times 1.0001).
-geek_status project_raw(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ldx, int64_t n, int d,
-                        const float *a, int F, float *vals, float *anorm, unsigned *xmax_bits, cudaStream_t st);
 // Alg. 1 (qalsh.cu): m tables of t buckets from the m QALSH projections.
 geek_status hash_qalsh(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ldx, int64_t n, int d, const float *a,
                        int m, int t, geek_buckets *b, cudaStream_t st);

@@ -52,3 +52,30 @@ def test_c2_full_size():
     lab_ref, _ = oracle.assign_dense(wl["x"][rows], centres)
     for prec, lab in labs.items():
         assert np.array_equal(lab[rows], lab_ref), prec
+
+
+def test_alg1_full_size_sampled_tables():
+    """Alg. 1 at the bench's size and configuration (10M x 128, m = 40
+    QALSH tables, t = 20,000 buckets): every bucket id of 4 sampled tables
+    against the oracle's exact split, and the even bucket sizes of all 40."""
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2106_10515_gb300 import geek
+    wl = synth.make(synth.config("c2"))
+    n = wl["cfg"].n
+    m, t = 40, 20000
+    a = np.ascontiguousarray(wl["a"][:m])
+    ctx = geek.Context(0)
+    bk = ctx.hash(ctx.dense(geek._dev(wl["x"])), 1, m, a=geek._dev(a), proj=geek.PROJ_QALSH, t=t)
+    got = bk.copy_out()
+    ob = got["obj_bucket"].cpu().numpy()
+    boff = got["bucket_off"].cpu().numpy()
+    del got, bk
+    torch.cuda.empty_cache()
+    sizes = np.diff(boff)
+    want = np.diff((np.arange(t + 1) * n) // t)
+    assert np.array_equal(sizes, np.tile(want, m))
+    tables = np.random.default_rng(11).choice(m, 4, replace=False)
+    s = oracle.qalsh(wl["x"], a[tables])
+    for q, f in enumerate(tables):
+        assert np.array_equal(ob[f], oracle.split_even(s[:, q], t)), f
