@@ -14,7 +14,9 @@ module marshals NumPy arrays and composes the steps in the paper's order:
 * heterogeneous rows (Alg. 2): E2LSH codes of the numeric part concatenated
   with MinHash of the categorical tokens, per table;
 * SILK (Alg. 4) with majority voting and near-duplicate removal;
-* central vectors (Sect. 3.3) and one-pass assignment (Eq. 1).
+* central vectors (Sect. 3.3) and one-pass assignment (Eq. 1);
+* further passes of assignment (Sect. 5: several passes for more compact
+  clusters), each an update of the centres then a reassignment.
 
 Parity status of each function is listed in ``PINS`` below.
 """
@@ -45,6 +47,8 @@ PINS = {
     "silk": "Python brute-force re-statement on tiny inputs + invariants",
     "centroids": "exact rational mean within 1 ulp",
     "assign_dense": "exhaustive exact-rational nearest seed",
+    "refine_passes": "separated blobs: exact rational blob means after one pass; SSE non-increasing; "
+                     "fixed point; a centre without members keeps its value",
     "modes": "collections.Counter brute force",
     "assign_cat": "brute-force match counts",
     "sparse_centres": "Counter brute force",
@@ -365,6 +369,37 @@ def assign_dense(x, centres):
     dist = np.empty(n, dtype=np.float64)
     _chk(lib().orc_assign_dense(n, d, _p(x), d, k, _p(centres), _p(lab), _p(dist)), "assign")
     return lab, dist
+
+
+def update_centres(x, labels, centres):
+    """One update of a pass: centre j = FP64 mean of the objects labelled j
+    (summed in ascending object id, as for the seeds' centroids); a centre
+    with no object keeps its value."""
+    k = centres.shape[0]
+    n = labels.shape[0]
+    lab = np.asarray(labels, dtype=np.int64)
+    keep = lab >= 0
+    order = np.lexsort((np.arange(n), lab))  # by label, then id
+    order = order[keep[order]]
+    counts = np.bincount(lab[keep], minlength=k)
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    means = centroids(x, Seeds(off, order.astype(np.int32), 0)) if k else np.zeros((0, x.shape[1]))
+    out = np.array(centres, dtype=np.float64, copy=True)
+    out[counts > 0] = means[counts > 0]
+    return out
+
+
+def refine_passes(x, centres, labels, passes):
+    """Sect. 5's extra passes of assignment: update the centres from the
+    current labels, then reassign every object (Eq. 1), `passes` times.
+    Returns (labels, centres, dist) of the last pass."""
+    c = np.array(centres, dtype=np.float64, copy=True)
+    lab = np.asarray(labels, dtype=np.int32)
+    dist = None
+    for _ in range(passes):
+        c = update_centres(x, lab, c)
+        lab, dist = assign_dense(x, c)
+    return lab, c, dist
 
 
 def modes(attrs, seeds: Seeds):

@@ -363,6 +363,44 @@ def test_assign_dense_exhaustive_exact(orc):
     assert np.all(lab0 == -1)
 
 
+# ------------------------------------------ extra passes (Sect. 5) --
+def test_refine_blobs_reach_exact_means(orc):
+    """Three far-apart blobs and centres that start inside the wrong blobs'
+    neighbourhood: one pass moves every centre to the exact rational mean
+    of its blob (within 1 ulp), and the labels become the blobs."""
+    rng = np.random.default_rng(21)
+    blobs = [np.array([0.0, 0.0, 0.0]), np.array([100.0, 0.0, 0.0]), np.array([0.0, 100.0, 0.0])]
+    x = np.concatenate([(b + rng.standard_normal((40, 3))).astype(np.float32) for b in blobs])
+    truth = np.repeat(np.arange(3), 40)
+    c0 = np.array([[10.0, 0, 0], [80.0, 5, 0], [5.0, 90, 0]])
+    lab0, _ = orc.assign_dense(x, c0)
+    assert np.array_equal(lab0, truth)
+    lab, c, dist = orc.refine_passes(x, c0, lab0, 1)
+    assert np.array_equal(lab, truth)
+    for j in range(3):
+        pts = x[truth == j]
+        for t in range(3):
+            exact = sum(Fraction(float(v)) for v in pts[:, t]) / len(pts)
+            assert abs(c[j, t] - float(exact)) <= abs(np.spacing(float(exact)))
+    # a fixed point: another pass changes nothing
+    lab2, c2, _ = orc.refine_passes(x, c, lab, 1)
+    assert np.array_equal(lab2, lab) and np.array_equal(c2, c)
+
+
+def test_refine_sse_never_increases_and_empty_centres_stay(orc):
+    rng = np.random.default_rng(22)
+    x = (rng.standard_normal((400, 5)) * 3).astype(np.float32)
+    c = rng.standard_normal((12, 5)) * 3
+    c[11] = 1e6  # no object is nearest to it: it keeps its value
+    lab, dist = orc.assign_dense(x, c)
+    sse = float(dist.sum())
+    for _ in range(4):
+        lab, c_new, dist = orc.refine_passes(x, c, lab, 1)
+        assert np.array_equal(c_new[11], c[11])
+        assert float(dist.sum()) <= sse * (1 + 1e-12)
+        sse, c = float(dist.sum()), c_new
+
+
 def test_modes_and_categorical_assignment(orc):
     rng = np.random.default_rng(11)
     n, A = 80, 6
