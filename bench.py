@@ -331,6 +331,8 @@ def run_ours(args):
     }
     if not args.skip_alg1:
         line["alg1_transform"] = bench_alg1(args, geek, ctx, data, wl, world)
+    if not args.skip_refine:
+        line["refine_passes"] = bench_refine(args, geek, ctx, data, wl, world, prec)
     if not args.skip_batch and world == 1:
         line["batched"] = bench_batched(args, geek, ctx, pk, pk_kind)
     if ms_other is not None:
@@ -380,6 +382,38 @@ def bench_alg1(args, geek, ctx, data, wl, world):
                         f"buckets each (paper grid m in {{20,40,60}}, t in [5k, 30k])",
             "value": cfg.n * world / (ms / 1e3), "unit": UNIT, "ms_per_run": ms, "n_buckets": int(nb),
             "phases_ms_per_run": {k: v[0] / args.steps for k, v in tm.items()}}
+
+
+def bench_refine(args, geek, ctx, data, wl, world, prec):
+    """Sect. 5's extra passes of assignment on the same points: from the
+    planted centres and their one-pass labels, `--refine-passes` passes of
+    centre update (FP64 means) + exact reassignment."""
+    import torch
+    cfg = wl["cfg"]
+    c0 = geek._dev(wl["centres"].astype(np.float64))
+    labels0 = torch.empty(cfg.n, dtype=torch.int32, device="cuda")
+    ctx.assign_centers(data, c0, labels0, precision=prec)
+    P = args.refine_passes
+
+    def run():
+        c = c0.clone()
+        lab = labels0.clone()
+        return ctx.refine(data, c, lab, P, precision=prec)
+
+    for _ in range(max(1, args.warmup)):
+        run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        st = run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    return {"workload": f"{P} extra passes of assignment (centre update + exact reassignment) on the dense points "
+                        f"above, k={c0.shape[0]} planted centres",
+            "value": cfg.n * P * world / (ms / 1e3), "unit": "point-passes/s", "ms_per_run": ms,
+            "ms_per_pass": ms / P, "sse_after": st.sse, "fp64_rows_last_pass": st.n_fp64_rows}
 
 
 def bench_batched(args, geek, ctx, pk, pk_kind):
@@ -544,6 +578,8 @@ def main():
     ap.add_argument("--skip-batch", action="store_true", help="skip the 256-instance batched measurement")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--skip-alg1", action="store_true", help="skip the Alg. 1 transform measurement")
+    ap.add_argument("--skip-refine", action="store_true", help="skip the extra-passes measurement")
+    ap.add_argument("--refine-passes", type=int, default=2)
     ap.add_argument("--alg1-m", type=int, default=40, help="Alg. 1: QALSH tables")
     ap.add_argument("--alg1-t", type=int, default=20000, help="Alg. 1: buckets per table")
     ap.add_argument("--batch-only", action="store_true", help="run only the batched measurement (profiling)")

@@ -259,6 +259,23 @@ geek_status geek_assign(geek_ctx *ctx, const geek_data *data, const geek_buckets
                         const silk_seeds *s, const geek_assign_params *p, int32_t *labels,
                         double *centers, geek_assign_stats *stats, geek_stream stream);
 
+/* geek_refine: further passes of assignment for more compact clusters
+ * (Sect. 5: several passes of data assignment; each pass is Lloyd's update
+ * step then the assignment step, Sect. 2).  Dense data only.  On entry
+ * labels (n int32, device) hold an assignment of the objects to the k
+ * centres in centers (k x d float64, device), e.g. geek_assign's output.
+ * Each pass replaces centre j by the FP64 mean of the objects labelled j
+ * (summed in ascending object id, as the seeds' centroids; a centre with no
+ * object keeps its value) and then reassigns every object with the exact
+ * argmin of geek_assign_centers (precision p->precision).  centers and
+ * labels are updated in place; stats (nullable, HOST) describe the last
+ * assignment.  passes >= 0; labels must lie in [-1, k).
+ * Errors: INVALID (NULL arguments, data not DENSE, passes < 0, a label
+ * outside [-1, k)), NOMEM, CUDA. */
+geek_status geek_refine(geek_ctx *ctx, const geek_data *data, double *centers, int64_t k, int32_t passes,
+                        const geek_assign_params *p, int32_t *labels, geek_assign_stats *stats,
+                        geek_stream stream);
+
 /* geek_assign_centers: the dense assignment of geek_assign against k given
  * central vectors (k x d float64, device), with the same exact argmin
  * definition.  Useful when the centres come from elsewhere. */

@@ -471,6 +471,27 @@ geek_status geek_assign_centers(geek_ctx *ctx, const geek_data *data, const doub
     }
 }
 
+geek_status geek_refine(geek_ctx *ctx, const geek_data *data, double *centers, int64_t k, int32_t passes,
+                        const geek_assign_params *p, int32_t *labels, geek_assign_stats *stats,
+                        geek_stream stream) {
+    if (!ctx) return GEEK_ERR_INVALID;
+    try {
+        GK_TRY(check_data(ctx, data));
+        if (data->kind != GEEK_DENSE || data->mem != GEEK_MEM_DEVICE)
+            return set_error(ctx, GEEK_ERR_INVALID, "refine: dense device data only");
+        if (!p || !labels || passes < 0 || k < 0 || k > 0x7FFFFFFFLL || (k > 0 && !centers))
+            return set_error(ctx, GEEK_ERR_INVALID, "bad refine arguments");
+        if (stats) *stats = geek_assign_stats{};
+        cudaStream_t st = S(stream);
+        EvTimer tm(ctx, "refine", st);
+        Scratch scr(ctx, st);
+        return refine_dense(ctx, scr, data->x, data->ldx, data->n, data->d, centers, k, passes, p->precision, labels,
+                            stats, st);
+    } catch (...) {
+        return set_error(ctx, GEEK_ERR_NOMEM, "host exception in geek_refine");
+    }
+}
+
 geek_status geek_assign(geek_ctx *ctx, const geek_data *data, const geek_buckets *b,
                         const silk_seeds *s, const geek_assign_params *p, int32_t *labels,
                         double *centers, geek_assign_stats *stats, geek_stream stream) {

@@ -624,6 +624,97 @@ geek_status centroids_from_seeds(geek_ctx *ctx, const float *x, int64_t ldx, int
     return GEEK_OK;
 }
 
+// ---- extra passes of assignment (Sect. 5) --------------------------------
+// members grouped by label: key = label (k for -1), id; counts per label
+__global__ void k_label_keys(int64_t n, const int32_t *__restrict__ labels, int64_t k, uint64_t *__restrict__ key,
+                             uint32_t *__restrict__ ids, unsigned long long *__restrict__ cnt, int *__restrict__ bad) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t l = labels[i];
+        if (l < -1 || l >= k) {
+            atomicExch(bad, 1);
+            l = -1;
+        }
+        key[i] = l < 0 ? (uint64_t)k : (uint64_t)l;
+        ids[i] = (uint32_t)i;
+        if (l >= 0) atomicAdd(&cnt[l], 1ull);
+    }
+}
+
+// centre j <- mean of its members (ascending id, the seeds' centroid sum);
+// no member: unchanged.  Block per centre, thread per coordinate: member
+// ids staged 64 at a time in shared memory, each chunk's row values loaded
+// together (rows read coalesced across the coordinates), then added in
+// order -- the sum stays sequential in ascending id.
+constexpr int UC_T = 128, UC_CH = 64;
+__global__ void __launch_bounds__(UC_T) k_update_centres(const float *__restrict__ x, int64_t ldx, int d, int64_t k,
+                                                         const int64_t *__restrict__ off,
+                                                         const unsigned long long *__restrict__ cnt,
+                                                         const int32_t *__restrict__ ids, double *__restrict__ c) {
+    __shared__ int32_t sid[UC_CH];
+    for (int64_t j = blockIdx.x; j < k; j += gridDim.x) {
+        const int64_t cj = (int64_t)cnt[j];
+        if (cj == 0) continue;  // block-uniform
+        const int64_t s0 = off[j];
+        for (int t0 = 0; t0 < d; t0 += UC_T) {
+            const int t = t0 + threadIdx.x;
+            double s = 0.0;
+            for (int64_t p0 = 0; p0 < cj; p0 += UC_CH) {
+                const int len = (int)min((int64_t)UC_CH, cj - p0);
+                __syncthreads();
+                if (threadIdx.x < len) sid[threadIdx.x] = ids[s0 + p0 + threadIdx.x];
+                __syncthreads();
+                if (t < d) {
+                    for (int q0 = 0; q0 < len; q0 += 8) {
+                        float v[8];
+#pragma unroll
+                        for (int q = 0; q < 8; q++)
+                            v[q] = q0 + q < len ? x[(int64_t)sid[q0 + q] * ldx + t] : 0.f;
+#pragma unroll
+                        for (int q = 0; q < 8; q++)
+                            if (q0 + q < len) s = __dadd_rn(s, (double)v[q]);
+                    }
+                }
+            }
+            if (t < d) c[j * d + t] = __ddiv_rn(s, (double)cj);
+        }
+    }
+}
+
+geek_status refine_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ldx, int64_t n, int d, double *centres,
+                         int64_t k, int passes, int precision, int32_t *labels, geek_assign_stats *stats,
+                         cudaStream_t st) {
+    for (int pass = 0; pass < passes && n > 0 && k > 0; pass++) {
+        Scratch ps(ctx, st);
+        uint64_t *key;
+        uint32_t *ids;
+        unsigned long long *cnt;
+        int64_t *off;
+        int *bad;
+        GK_TRY(ps.alloc(&key, n));
+        GK_TRY(ps.alloc(&ids, n));
+        GK_TRY(ps.alloc(&cnt, k));
+        GK_TRY(ps.alloc(&off, k));
+        GK_TRY(ps.alloc(&bad, 1));
+        GK_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * k, st));
+        GK_CUDA(ctx, cudaMemsetAsync(bad, 0, sizeof(int), st));
+        GK_COUNT();
+        k_label_keys<<<grid_for(n, 256, ctx->num_sms), 256, 0, st>>>(n, labels, k, key, ids, cnt, bad);
+        GK_LAUNCH(ctx);
+        GK_TRY(radix_sort_segments(ctx, ps, 1, n, &key, nullptr, &ids, bit_length_u64((uint64_t)k), st));
+        GK_TRY(exclusive_scan_i64(ctx, ps, (const int64_t *)cnt, off, k, nullptr, st));
+        GK_COUNT();
+        k_update_centres<<<(unsigned)std::min<int64_t>(k, (int64_t)ctx->num_sms * 16), UC_T, 0, st>>>(
+            x, ldx, d, k, off, cnt, (const int32_t *)ids, centres);
+        GK_LAUNCH(ctx);
+        int h_bad = 0;
+        GK_CUDA(ctx, cudaMemcpyAsync(&h_bad, bad, sizeof h_bad, cudaMemcpyDeviceToHost, st));
+        GK_TRY(sort_err_check(ctx, st));  // synchronises st
+        if (h_bad) return set_error(ctx, GEEK_ERR_INVALID, "a label outside [-1, k)");
+        GK_TRY(assign_dense_centres(ctx, ps, x, ldx, n, d, centres, k, precision, labels, stats, st));
+    }
+    return GEEK_OK;
+}
+
 geek_status assign_dense_centres(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ldx, int64_t n, int d,
                                  const double *centres, int64_t k, int precision, int32_t *labels,
                                  geek_assign_stats *stats, cudaStream_t st) {

@@ -263,6 +263,11 @@ geek_status decide_flags(geek_ctx *ctx, const RInst *R, const int64_t *row_off, 
 geek_status assign_dense_centres(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ldx,
                                  int64_t n, int d, const double *centres, int64_t k, int precision,
                                  int32_t *labels, geek_assign_stats *stats, cudaStream_t st);
+// Sect. 5's extra passes: per pass, centre j <- FP64 mean of the objects
+// labelled j (unchanged without members), then the exact reassignment.
+geek_status refine_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ldx, int64_t n, int d, double *centres,
+                         int64_t k, int passes, int precision, int32_t *labels, geek_assign_stats *stats,
+                         cudaStream_t st);
 geek_status centroids_from_seeds(geek_ctx *ctx, const float *x, int64_t ldx, int d,
                                  const silk_seeds *s, double *centres, cudaStream_t st);
 geek_status assign_hetero(geek_ctx *ctx, Scratch &scr, const geek_buckets *b, const uint32_t *tok,

@@ -87,7 +87,7 @@ EXPORTS = ["geek_ctx_create", "geek_ctx_destroy", "geek_last_error", "geek_versi
            "geek_assign_centers", "geek_timing_enable", "geek_timing_reset", "geek_timing_get",
            "geek_launch_count", "geek_assign_centers_noalloc", "geek_batch_create", "geek_batch_run",
            "geek_batch_info_get", "geek_batch_instance_stats", "geek_batch_copy_out", "geek_batch_seed_ids_count",
-           "geek_batch_destroy", "geek_data_upload", "geek_resident_free"]
+           "geek_batch_destroy", "geek_data_upload", "geek_resident_free", "geek_refine"]
 
 _lib = None
 
@@ -134,6 +134,8 @@ def lib():
     L.geek_batch_destroy.argtypes = [P]
     L.geek_data_upload.argtypes = [P, C.POINTER(geek_data), C.POINTER(P), C.POINTER(geek_data), P]
     L.geek_resident_free.argtypes = [P]
+    L.geek_refine.argtypes = [P, C.POINTER(geek_data), P, C.c_int64, C.c_int32, C.POINTER(geek_assign_params), P,
+                              C.POINTER(geek_assign_stats), P]
     for name in EXPORTS:
         f = getattr(L, name)
         if name not in ("geek_last_error", "geek_version", "geek_ctx_destroy", "geek_launch_count"):
@@ -357,6 +359,16 @@ class Context:
         self._chk(lib().geek_assign(self.h, C.byref(data.c), buckets.h if buckets is not None else None,
                                     seeds.h, C.byref(p), _ptr(labels), _ptr(centers),
                                     C.byref(s) if stats else None, _stream()))
+        return s
+
+    def refine(self, data, centers, labels, passes, precision=PREC_FP32, stats=True):
+        """Sect. 5's extra passes of assignment: centers (k x d float64) and
+        labels (n int32) on the device, updated in place."""
+        p = geek_assign_params()
+        p.precision = precision
+        s = geek_assign_stats() if stats else None
+        self._chk(lib().geek_refine(self.h, C.byref(data.c), _ptr(centers), centers.shape[0], passes, C.byref(p),
+                                    _ptr(labels), C.byref(s) if s is not None else None, _stream()))
         return s
 
     def assign_centers(self, data, centers, labels, precision=PREC_FP32, stats=True):

@@ -297,3 +297,36 @@ def test_alg1_invalid(G, ctx):
         with pytest.raises(G.GeekError) as e:
             ctx.hash(ctx.dense(x), K, 4, a=G._dev(wl["a"][:4 * K]), proj=G.PROJ_QALSH, t=t)
         assert e.value.status == G.ERR_INVALID
+
+
+# ------------------------------------- extra passes of assignment (Sect. 5) --
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+def test_refine_passes_exact(G, ctx, prec):
+    """geek_refine: each pass's centres (FP64 means in ascending id) and
+    labels bit-exact against the oracle; a centre nobody is nearest to keeps
+    its value."""
+    P = G.PREC_BF16 if prec == "bf16" else G.PREC_FP32
+    wl = synth.make(synth.config("c1", n=9000))
+    x = wl["x"]
+    c0 = wl["centres"].astype(np.float64)
+    c0 = np.concatenate([c0, np.full((1, x.shape[1]), 1e5)])  # an empty cluster
+    lab0, _ = oracle.assign_dense(x, c0)
+    xd, cd = G._dev(x), G._dev(c0)
+    labels = G._dev(lab0.astype(np.int32))
+    st = ctx.refine(ctx.dense(xd), cd, labels, 3, precision=P)
+    torch.cuda.synchronize()
+    lab_ref, c_ref, dist = oracle.refine_passes(x, c0, lab0, 3)
+    assert np.array_equal(labels.cpu().numpy(), lab_ref)
+    assert np.array_equal(cd.cpu().numpy(), c_ref)
+    assert np.array_equal(c_ref[-1], c0[-1])
+    sse = float(dist.sum())
+    assert abs(st.sse - sse) <= 1e-6 * sse
+
+
+def test_refine_invalid_labels(G, ctx):
+    wl = synth.make(synth.config("c1", n=500))
+    c = G._dev(wl["centres"].astype(np.float64))
+    labels = torch.full((500,), c.shape[0], dtype=torch.int32, device="cuda")  # out of range
+    with pytest.raises(G.GeekError) as e:
+        ctx.refine(ctx.dense(G._dev(wl["x"])), c, labels, 1)
+    assert e.value.status == G.ERR_INVALID
