@@ -403,17 +403,23 @@ def bench_refine(args, geek, ctx, data, wl, world, prec):
     for _ in range(max(1, args.warmup)):
         run()
     torch.cuda.synchronize()
+    ctx.timing_reset()
+    ctx.timing(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
         st = run()
     e1.record()
     torch.cuda.synchronize()
+    ctx.timing(False)
     ms = e0.elapsed_time(e1) / args.steps
+    tm = {k: ctx.timing_get(k)[0] / args.steps for k in ("refine", "assign", "kernel.assign_tc", "kernel.assign_fp32",
+                                                        "kernel.assign_recheck")}
     return {"workload": f"{P} extra passes of assignment (centre update + exact reassignment) on the dense points "
                         f"above, k={c0.shape[0]} planted centres",
             "value": cfg.n * P * world / (ms / 1e3), "unit": "point-passes/s", "ms_per_run": ms,
-            "ms_per_pass": ms / P, "sse_after": st.sse, "fp64_rows_last_pass": st.n_fp64_rows}
+            "ms_per_pass": ms / P, "sse_after": st.sse, "undecided_rows_last_pass": st.n_recheck_rows,
+            "fp64_rows_last_pass": st.n_fp64_rows, "phases_ms_per_run": tm}
 
 
 def bench_batched(args, geek, ctx, pk, pk_kind):

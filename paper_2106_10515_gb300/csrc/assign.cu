@@ -642,10 +642,11 @@ __global__ void k_label_keys(int64_t n, const int32_t *__restrict__ labels, int6
 
 // centre j <- mean of its members (ascending id, the seeds' centroid sum);
 // no member: unchanged.  Block per centre, thread per coordinate: member
-// ids staged 64 at a time in shared memory, each chunk's row values loaded
-// together (rows read coalesced across the coordinates), then added in
-// order -- the sum stays sequential in ascending id.
-constexpr int UC_T = 128, UC_CH = 64;
+// ids staged 128 at a time in shared memory, 32 row values loaded together
+// (rows read coalesced across the coordinates), then added in order -- the
+// sum stays sequential in ascending id, so a centre's cost is a chain of
+// its member count (the largest cluster bounds the pass).
+constexpr int UC_T = 128, UC_CH = 128, UC_IN = 32;  // ids per chunk, loads in flight per thread
 __global__ void __launch_bounds__(UC_T) k_update_centres(const float *__restrict__ x, int64_t ldx, int d, int64_t k,
                                                          const int64_t *__restrict__ off,
                                                          const unsigned long long *__restrict__ cnt,
@@ -664,15 +665,15 @@ __global__ void __launch_bounds__(UC_T) k_update_centres(const float *__restrict
                 if (threadIdx.x < len) sid[threadIdx.x] = ids[s0 + p0 + threadIdx.x];
                 __syncthreads();
                 if (t < d) {
-                    for (int q0 = 0; q0 < len; q0 += 8) {
-                        float v[8];
+                    int q0 = 0;
+                    for (; q0 + UC_IN <= len; q0 += UC_IN) {  // full groups: every load issued first
+                        float v[UC_IN];
 #pragma unroll
-                        for (int q = 0; q < 8; q++)
-                            v[q] = q0 + q < len ? x[(int64_t)sid[q0 + q] * ldx + t] : 0.f;
+                        for (int q = 0; q < UC_IN; q++) v[q] = __ldg(x + (int64_t)sid[q0 + q] * ldx + t);
 #pragma unroll
-                        for (int q = 0; q < 8; q++)
-                            if (q0 + q < len) s = __dadd_rn(s, (double)v[q]);
+                        for (int q = 0; q < UC_IN; q++) s = __dadd_rn(s, (double)v[q]);
                     }
+                    for (; q0 < len; q0++) s = __dadd_rn(s, (double)__ldg(x + (int64_t)sid[q0] * ldx + t));
                 }
             }
             if (t < d) c[j * d + t] = __ddiv_rn(s, (double)cj);
