@@ -10,7 +10,8 @@ module marshals NumPy arrays and composes the steps in the paper's order:
   table concatenated over L tables (the static (K,L) framework, Sect. 2.2);
 * dense data, the paper's own transform (Alg. 1): m QALSH projections a.x,
   each table sorted (ties by object id) and split evenly into t buckets;
-* sparse sets (Alg. 3, without DOPH): MinHash (Eq. 2), K per table, L tables;
+* sparse sets (Alg. 3): MinHash (Eq. 2), K per table, L tables, on the sets
+  themselves or (transform_sparse_doph) on their DOPH reduction;
 * heterogeneous rows (Alg. 2): E2LSH codes of the numeric part concatenated
   with MinHash of the categorical tokens, per table;
 * SILK (Alg. 4) with majority voting and near-duplicate removal;
@@ -41,6 +42,8 @@ PINS = {
     "alg1": "exact rational projections sorted by (value, id) and split by floor(b n / t) (brute force); "
             "bucket sizes, tie order and the t = 1 / t = n cases",
     "hash32": "Python big-integer (A*x+B) mod 2^64 >> 32",
+    "doph": "hand-worked bins, borrowing and wrap-around with an affine pi; per-bin collision rate = Jaccard "
+            "(rotation densification); 64-bit-token MinHash against Python big integers",
     "minhash": "explicit set minima in Python; collision rate = Jaccard (Eq. 2)",
     "group": "Python dict of tuples, canonical rank by sorted distinct keys",
     "vote": "Example 2 with forced bins (Sect. 3.2)",
@@ -81,6 +84,8 @@ def lib():
         L.orc_hash32.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32]
         L.orc_hash32.restype = C.c_uint32
         L.orc_minhash_csr.argtypes = [i64, P, P, i32, P, P, P]
+        L.orc_doph.argtypes = [i64, P, P, i32, C.c_uint64, C.c_uint64, P]
+        L.orc_minhash_rows64.argtypes = [i64, i32, P, i32, P, P, P]
         L.orc_sort_rows.argtypes = [i64, i32, P, P]
         L.orc_group.argtypes = [i64, i32, i32, P, P, P, P, P]
         L.orc_bucket_sigs.argtypes = [i64, P, P, i32, P, P, P]
@@ -156,6 +161,31 @@ def minhash_rows(tokens, A, B):
     n, m = tokens.shape
     off = np.arange(n + 1, dtype=np.int64) * m
     return minhash_csr(off, tokens.reshape(-1), A, B)
+
+
+def doph(off, items, Dp, Ap, Bp):
+    """DOPH reduction (Alg. 3's first step): n x Dp 64-bit tokens."""
+    off = _c(off, np.int64); items = _c(items, np.uint32)
+    n = off.size - 1
+    out = np.empty((n, Dp), dtype=np.uint64)
+    _chk(lib().orc_doph(n, _p(off), _p(items), int(Dp), int(Ap), int(Bp), _p(out)), "doph")
+    return out
+
+
+def minhash_rows64(tokens, A, B):
+    tokens = _c(tokens, np.uint64); A = _c(A, np.uint64); B = _c(B, np.uint64)
+    n, m = tokens.shape
+    out = np.empty((n, A.size), dtype=np.uint32)
+    _chk(lib().orc_minhash_rows64(n, m, _p(tokens), A.size, _p(A), _p(B), _p(out)), "minhash64")
+    return out
+
+
+def transform_sparse_doph(off, items, Dp, Ap, Bp, A, B, K, L):
+    """Alg. 3 with its DOPH step: reduce every set to Dp tokens, then MinHash
+    (K, L) on the reduced sets and group per table."""
+    tok = doph(off, items, Dp, Ap, Bp)
+    mh = minhash_rows64(tok, A, B)
+    return tok, mh, group(table_keys(mh, L, K))
 
 
 # --------------------------------------------------------------- grouping --

@@ -136,6 +136,64 @@ int orc_minhash_csr(int64_t n, const int64_t *off, const uint32_t *items, int32_
     return ORC_OK;
 }
 
+/* DOPH reduction of the sparse transform (Alg. 3, first step; densified
+ * one permutation hashing with rotation).  One hash pi(v) = h(Ap, Bp, v)
+ * stands for the permutation; the hash range is cut into Dp equal bins:
+ * bin(v) = (pi(v) * Dp) >> 32, offset(v) = (pi(v) * Dp) mod 2^32.  Bin b
+ * keeps the smallest offset of its items; an empty bin b borrows the value
+ * of the first non-empty bin b + t (t >= 1, circular) and records t.  An
+ * empty set: t = Dp, value 2^32 - 1 everywhere.  Token of bin b:
+ * (b << 48) | (t << 32) | value, so the reduced object is a set of Dp
+ * distinct 64-bit tokens.  Dp <= 65535. */
+int orc_doph(int64_t n, const int64_t *off, const uint32_t *items, int32_t Dp, uint64_t Ap, uint64_t Bp,
+             uint64_t *tokens)
+{
+    if (n < 0 || Dp < 1 || Dp > 65535) return ORC_INVALID;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(| : bad)
+    for (int64_t i = 0; i < n; i++) {
+        uint64_t *m = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)Dp);
+        if (!m) { bad |= 1; continue; }
+        for (int32_t b = 0; b < Dp; b++) m[b] = UINT64_MAX; /* empty */
+        for (int64_t p = off[i]; p < off[i + 1]; p++) {
+            uint64_t scaled = (uint64_t)orc_hash32(Ap, Bp, items[p]) * (uint64_t)Dp;
+            int32_t b = (int32_t)(scaled >> 32);
+            uint64_t o = scaled & 0xFFFFFFFFull;
+            if (o < m[b]) m[b] = o;
+        }
+        for (int32_t b = 0; b < Dp; b++) {
+            uint64_t t = 0, v = m[b];
+            while (v == UINT64_MAX && t < (uint64_t)Dp) {
+                t++;
+                v = m[(b + t) % Dp];
+            }
+            if (v == UINT64_MAX) { t = (uint64_t)Dp; v = 0xFFFFFFFFull; }
+            tokens[i * Dp + b] = ((uint64_t)b << 48) | (t << 32) | v;
+        }
+        free(m);
+    }
+    return bad ? ORC_INVALID : ORC_OK;
+}
+
+/* MinHash of fixed-length rows of 64-bit tokens: h(A, B, x) =
+ * ((A x + B) mod 2^64) >> 32 with the full 64-bit token x. */
+int orc_minhash_rows64(int64_t n, int32_t m, const uint64_t *tokens, int32_t F, const uint64_t *A,
+                       const uint64_t *B, uint32_t *out)
+{
+    if (n < 0 || m < 0 || F <= 0) return ORC_INVALID;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++)
+        for (int32_t f = 0; f < F; f++) {
+            uint32_t best = 0xFFFFFFFFu;
+            for (int32_t j = 0; j < m; j++) {
+                uint32_t h = (uint32_t)((A[f] * tokens[i * m + j] + B[f]) >> 32);
+                if (h < best) best = h;
+            }
+            out[i * F + f] = best;
+        }
+    return ORC_OK;
+}
+
 /* ------------------------------------------------------------------------ */
 /* A stable sort of row indices by lexicographic int64 keys (a library-style */
 /* primitive: parallel merge sort; equal keys keep ascending index).         */

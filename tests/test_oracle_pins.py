@@ -95,6 +95,56 @@ def test_srp_matches_exact_sign(orc):
             assert got[i, f] == (1 if v >= 0 else 0)
 
 
+# --------------------------------------------------- DOPH (Alg. 3 step) --
+def test_doph_hand_worked_bins():
+    """pi(v) = v (A = 2^32, B = 0), 4 bins = the top two bits of v, offset =
+    the low 30 bits times 4.  Worked by hand from the definition."""
+    import oracle
+    S = [0x40000005, 0x40000003, 0xC0000001]
+    tok = oracle.doph(np.array([0, 3, 4], dtype=np.int64), np.array(S + [2], dtype=np.uint32), 4, 1 << 32, 0)
+    want0 = [(0 << 48) | (1 << 32) | 0xC,   # bin 0 empty: borrows bin 1 at distance 1
+             (1 << 48) | (0 << 32) | 0xC,   # min(0x14, 0xC)
+             (2 << 48) | (1 << 32) | 0x4,   # bin 2 empty: borrows bin 3
+             (3 << 48) | (0 << 32) | 0x4]
+    assert [int(v) for v in tok[0]] == want0
+    # one item in bin 0: bins 1..3 borrow it across the wrap-around
+    want1 = [(0 << 48) | 8, (1 << 48) | (3 << 32) | 8, (2 << 48) | (2 << 32) | 8, (3 << 48) | (1 << 32) | 8]
+    assert [int(v) for v in tok[1]] == want1
+
+
+def test_doph_collision_rate_is_jaccard():
+    """Rotation-densified OPH is an LSH for resemblance: for every bin,
+    Pr[token(S1) == token(S2)] = |S1 n S2| / |S1 u S2| over random pi."""
+    import oracle
+    rng = np.random.default_rng(44)
+    pool = rng.choice(1 << 31, size=100, replace=False).astype(np.uint32)
+    S1, S2 = pool[:80], pool[20:100]  # |n| = 60, |u| = 100
+    J = 0.6
+    off = np.array([0, 80, 160], dtype=np.int64)
+    items = np.concatenate([S1, S2])
+    trials, Dp = 1500, 6
+    hits = np.zeros(Dp)
+    for _ in range(trials):
+        A, B = int(rng.integers(1, 1 << 63)) * 2 + 1, int(rng.integers(0, 1 << 63))
+        t = oracle.doph(off, items, Dp, A, B)
+        hits += (t[0] == t[1])
+    rate = hits / trials
+    sd = math.sqrt(J * (1 - J) / trials)
+    assert np.all(np.abs(rate - J) < 4.5 * sd), rate
+
+
+def test_minhash_rows64_big_integers():
+    import oracle
+    rng = np.random.default_rng(45)
+    tok = rng.integers(0, 1 << 63, size=(7, 5), dtype=np.uint64) * 2 + 1
+    A = rng.integers(0, 1 << 63, size=4, dtype=np.uint64)
+    B = rng.integers(0, 1 << 63, size=4, dtype=np.uint64)
+    got = oracle.minhash_rows64(tok, A, B)
+    for i in range(7):
+        for f in range(4):
+            assert got[i, f] == min(((int(A[f]) * int(x) + int(B[f])) % M64) >> 32 for x in tok[i])
+
+
 # ------------------------------------------------- Alg. 1 (QALSH split) --
 def exact_alg1(x, a, t):
     """Alg. 1 by hand: exact rational projections, objects sorted by (value,
