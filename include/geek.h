@@ -101,7 +101,16 @@ typedef struct geek_data {
  *    t buckets: bucket j holds sorted positions [floor(j n / t),
  *    floor((j + 1) n / t)), 1 <= t <= n.  codes then hold the FP32 bit
  *    patterns of the projections (approximate; the buckets are exact).
- *    DENSE data only; finite inputs. */
+ *    DENSE data only; finite inputs.
+ *  Sets with doph_bins = D' > 0 (Alg. 3's DOPH step, 1 <= D' <= 1024):
+ *    pi(v) = ((doph_a*v + doph_b) mod 2^64) >> 32 cut into D' equal bins,
+ *    bin(v) = (pi(v)*D') >> 32, offset(v) = (pi(v)*D') mod 2^32; a bin keeps
+ *    its smallest offset; an empty bin takes the value of the first
+ *    non-empty bin to its right (circular) at distance t (rotation
+ *    densification); an empty set: t = D', value 2^32 - 1.  The set is
+ *    replaced by its D' tokens (b << 48) | (t << 32) | value and the K*L
+ *    MinHash functions hash the 64-bit tokens: ((mh_a*x + mh_b) mod 2^64)
+ *    >> 32. */
 typedef struct geek_hash_params {
     int32_t proj;
     int32_t precision;
@@ -112,6 +121,8 @@ typedef struct geek_hash_params {
     const uint64_t *mh_a;
     const uint64_t *mh_b;
     int32_t t;           /* QALSH: buckets per table (ignored otherwise) */
+    int32_t doph_bins;   /* SETS: > 0 reduces every set by DOPH to this many tokens first */
+    uint64_t doph_a, doph_b;  /* SETS with doph_bins: the permutation hash pair */
 } geek_hash_params;
 
 typedef struct geek_buckets_info {

@@ -84,6 +84,8 @@ geek_status hash_impl(geek_ctx *ctx, const geek_data *data, const geek_hash_para
     }
     if ((kind == GEEK_SETS || kind == GEEK_HETERO) && (!p->mh_a || !p->mh_b))
         return set_error(ctx, GEEK_ERR_INVALID, "MinHash coefficients missing");
+    if (p->doph_bins != 0 && (kind != GEEK_SETS || p->doph_bins < 0 || p->doph_bins > 1024))
+        return set_error(ctx, GEEK_ERR_INVALID, "DOPH: sets only, 1 <= bins <= 1024");
     if (p->precision != GEEK_PREC_FP32)
         return set_error(ctx, GEEK_ERR_UNSUPPORTED, "projection precision other than FP32");
     const bool host = data->mem == GEEK_MEM_HOST;
@@ -149,7 +151,14 @@ geek_status hash_impl(geek_ctx *ctx, const geek_data *data, const geek_hash_para
         const uint32_t *items;
         GK_TRY(stage(ctx, scr, data->set_items, (size_t)n_items, host, &items, st));
         mh = (uint32_t *)b->codes;
-        GK_TRY(minhash_rows(ctx, n, off, 0, items, F2, p->mh_a, p->mh_b, mh, st));
+        if (p->doph_bins > 0) {  // Alg. 3: DOPH reduction, then MinHash of the tokens
+            uint64_t *tok;
+            GK_TRY(scr.alloc(&tok, (size_t)n * p->doph_bins));
+            GK_TRY(doph_reduce(ctx, n, off, items, p->doph_bins, p->doph_a, p->doph_b, tok, st));
+            GK_TRY(minhash_rows64(ctx, n, p->doph_bins, tok, F2, p->mh_a, p->mh_b, mh, st));
+        } else {
+            GK_TRY(minhash_rows(ctx, n, off, 0, items, F2, p->mh_a, p->mh_b, mh, st));
+        }
     } else if (kind == GEEK_HETERO) {
         const uint32_t *tok;
         GK_TRY(stage(ctx, scr, data->cat, (size_t)n * data->n_cat, host, &tok, st));

@@ -406,9 +406,16 @@ __global__ void k_recheck_fp64(const ProjArgs *__restrict__ P, const int64_t *__
 // MinHash (Eq. 2): warp per set, lane over functions, items broadcast by
 // shuffles; every lane keeps FPL running minima.
 // ---------------------------------------------------------------------------
-template <int FPL, bool FIXED>
+// hash of one token: 32-bit items, or the 64-bit tokens of a DOPH reduction
+// (the same family, h = ((A x + B) mod 2^64) >> 32, over the whole token)
+__device__ __forceinline__ uint32_t mh_token(uint64_t A, uint64_t B, uint32_t x) { return mh_hash32(A, B, x); }
+__device__ __forceinline__ uint32_t mh_token(uint64_t A, uint64_t B, uint64_t x) {
+    return (uint32_t)((A * x + B) >> 32);
+}
+
+template <int FPL, bool FIXED, typename TOK = uint32_t>
 __global__ void __launch_bounds__(256) k_minhash(int64_t n, const int64_t *__restrict__ off,
-                                                 int row_len, const uint32_t *__restrict__ items,
+                                                 int row_len, const TOK *__restrict__ items,
                                                  int F, const uint64_t *__restrict__ A,
                                                  const uint64_t *__restrict__ B,
                                                  uint32_t *__restrict__ out, int out_ld) {
@@ -436,11 +443,11 @@ __global__ void __launch_bounds__(256) k_minhash(int64_t n, const int64_t *__res
         for (int q = 0; q < FPL; q++) m[q] = 0xFFFFFFFFu;
         for (int64_t base = s; base < e; base += 32) {
             const int cnt = (int)min((int64_t)32, e - base);
-            const uint32_t mine = lane < cnt ? items[base + lane] : 0u;
+            const TOK mine = lane < cnt ? items[base + lane] : (TOK)0;
             for (int j = 0; j < cnt; j++) {
-                const uint32_t v = __shfl_sync(0xffffffffu, mine, j);
+                const TOK v = __shfl_sync(0xffffffffu, mine, j);
 #pragma unroll
-                for (int q = 0; q < FPL; q++) m[q] = min(m[q], mh_hash32(ca[q], cb[q], v));
+                for (int q = 0; q < FPL; q++) m[q] = min(m[q], mh_token(ca[q], cb[q], v));
             }
         }
 #pragma unroll
@@ -834,6 +841,25 @@ geek_status minhash_rows(geek_ctx *ctx, int64_t n, const int64_t *off, int row_l
             k_minhash<FPL, true><<<blocks, threads, 0, st>>>(n, off, row_len, items, F, A, B, out, F); \
         else                                                                                      \
             k_minhash<FPL, false><<<blocks, threads, 0, st>>>(n, off, row_len, items, F, A, B, out, F); \
+    } while (0)
+    if (F <= 32) MH_LAUNCH(1);
+    else if (F <= 64) MH_LAUNCH(2);
+    else if (F <= 128) MH_LAUNCH(4);
+    else MH_LAUNCH(8);
+#undef MH_LAUNCH
+    GK_LAUNCH(ctx);
+    return GEEK_OK;
+}
+
+geek_status minhash_rows64(geek_ctx *ctx, int64_t n, int row_len, const uint64_t *tokens, int F, const uint64_t *A,
+                           const uint64_t *B, uint32_t *out, cudaStream_t st) {
+    if (n == 0) return GEEK_OK;
+    if (F > 256) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "more than 256 MinHash functions");
+    const int blocks = grid_for(n * 32, 256, ctx->num_sms);
+#define MH_LAUNCH(FPL)                                                                                             \
+    do {                                                                                                          \
+        GK_COUNT();                                                                                               \
+        k_minhash<FPL, true, uint64_t><<<blocks, 256, 0, st>>>(n, nullptr, row_len, tokens, F, A, B, out, F);    \
     } while (0)
     if (F <= 32) MH_LAUNCH(1);
     else if (F <= 64) MH_LAUNCH(2);

@@ -67,6 +67,12 @@ geek_status project_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t l
                           int d, const float *a, const float *b, int F, double w, int srp,
                           int32_t *codes, int *fmin, int *fmax, int64_t *n_flagged,
                           int64_t *n_flagged_fp64, cudaStream_t st);
+// MinHash of fixed rows of 64-bit tokens (a DOPH reduction): out n x F.
+geek_status minhash_rows64(geek_ctx *ctx, int64_t n, int row_len, const uint64_t *tokens, int F, const uint64_t *A,
+                           const uint64_t *B, uint32_t *out, cudaStream_t st);
+// DOPH reduction of CSR sets (doph.cu): tokens n x Dp, 1 <= Dp <= 1024.
+geek_status doph_reduce(geek_ctx *ctx, int64_t n, const int64_t *off, const uint32_t *items, int Dp, uint64_t Ap,
+                        uint64_t Bp, uint64_t *tokens, cudaStream_t st);
 geek_status minhash_rows(geek_ctx *ctx, int64_t n, const int64_t *off, int row_len,
                          const uint32_t *items, int F, const uint64_t *A, const uint64_t *B,
                          uint32_t *out, cudaStream_t st);

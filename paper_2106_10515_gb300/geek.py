@@ -40,7 +40,8 @@ class geek_data(C.Structure):
 class geek_hash_params(C.Structure):
     _fields_ = [("proj", C.c_int32), ("precision", C.c_int32), ("K", C.c_int32), ("L", C.c_int32),
                 ("Kc", C.c_int32), ("w", C.c_double), ("a", C.c_void_p), ("b", C.c_void_p),
-                ("mh_a", C.c_void_p), ("mh_b", C.c_void_p), ("t", C.c_int32)]
+                ("mh_a", C.c_void_p), ("mh_b", C.c_void_p), ("t", C.c_int32), ("doph_bins", C.c_int32),
+                ("doph_a", C.c_uint64), ("doph_b", C.c_uint64)]
 
 
 class geek_buckets_info(C.Structure):
@@ -335,9 +336,10 @@ class Context:
 
     # ---------------------------------------------------------------- hash --
     def hash(self, data, K, L, a=None, b=None, w=4.0, mh_a=None, mh_b=None, Kc=0,
-             proj=PROJ_E2LSH, precision=PREC_FP32, t=0) -> Buckets:
+             proj=PROJ_E2LSH, precision=PREC_FP32, t=0, doph_bins=0, doph_a=0, doph_b=0) -> Buckets:
         p = geek_hash_params()
         p.proj, p.precision, p.K, p.L, p.Kc, p.w, p.t = proj, precision, K, L, Kc, float(w), t
+        p.doph_bins, p.doph_a, p.doph_b = doph_bins, int(doph_a), int(doph_b)
         p.a, p.b, p.mh_a, p.mh_b = _ptr(a), _ptr(b), _ptr(mh_a), _ptr(mh_b)
         out = C.c_void_p()
         self._chk(lib().geek_hash(self.h, C.byref(data.c), C.byref(p), C.byref(out), _stream()))

@@ -330,3 +330,24 @@ def test_refine_invalid_labels(G, ctx):
     with pytest.raises(G.GeekError) as e:
         ctx.refine(ctx.dense(G._dev(wl["x"])), c, labels, 1)
     assert e.value.status == G.ERR_INVALID
+
+
+# -------------------------------------------- DOPH step of Alg. 3 (sets) --
+@pytest.mark.parametrize("Dp", [64, 400])
+def test_sets_doph_transform(G, ctx, Dp):
+    """Alg. 3 with DOPH: the reduced tokens' MinHash values and the buckets
+    bit-exact against the oracle (sets larger and smaller than Dp, an empty
+    set)."""
+    wl = synth.make(synth.config("c3", n=4000, n_base=80))
+    cfg = wl["cfg"]
+    off = np.concatenate([wl["set_off"], [wl["set_off"][-1]]]).astype(np.int64)  # + one empty set
+    items = wl["set_items"].astype(np.uint32)
+    rng = np.random.default_rng(Dp)
+    Ap, Bp = int(rng.integers(1, 1 << 62)) * 2 + 1, int(rng.integers(0, 1 << 62))
+    data = ctx.sets(G._dev(off), G._dev(items.astype(np.int32)))
+    bk = ctx.hash(data, cfg.K, cfg.L, mh_a=G._dev(wl["mh_a"]), mh_b=G._dev(wl["mh_b"]), doph_bins=Dp,
+                  doph_a=Ap, doph_b=Bp)
+    _, mh, ref = oracle.transform_sparse_doph(off, items, Dp, Ap, Bp, wl["mh_a"], wl["mh_b"], cfg.K, cfg.L)
+    got = bk.copy_out()
+    assert np.array_equal(got["codes"].cpu().numpy().view(np.uint32), mh)
+    check_buckets(got, ref)
