@@ -333,6 +333,8 @@ def run_ours(args):
         line["alg1_transform"] = bench_alg1(args, geek, ctx, data, wl, world)
     if not args.skip_refine:
         line["refine_passes"] = bench_refine(args, geek, ctx, data, wl, world, prec)
+    if not args.skip_doph:
+        line["doph_sets_transform"] = bench_doph(args, geek, ctx, world)
     if not args.skip_batch and world == 1:
         line["batched"] = bench_batched(args, geek, ctx, pk, pk_kind)
     if ms_other is not None:
@@ -420,6 +422,46 @@ def bench_refine(args, geek, ctx, data, wl, world, prec):
             "value": cfg.n * P * world / (ms / 1e3), "unit": "point-passes/s", "ms_per_run": ms,
             "ms_per_pass": ms / P, "sse_after": st.sse, "undecided_rows_last_pass": st.n_recheck_rows,
             "fp64_rows_last_pass": st.n_fp64_rows, "phases_ms_per_run": tm}
+
+
+def bench_doph(args, geek, ctx, world):
+    """Alg. 3 with its DOPH step on c3-shaped sparse sets: DOPH reduction to
+    `--doph-bins` tokens, K*L MinHash of the tokens, grouping per table."""
+    import torch
+    import synth
+    wl3 = synth.make(synth.config("c3", n=args.doph_n))
+    cfg = wl3["cfg"]
+    off = geek._dev(wl3["set_off"])
+    items = geek._dev(wl3["set_items"].astype(np.int32))
+    mh_a, mh_b = geek._dev(wl3["mh_a"]), geek._dev(wl3["mh_b"])
+    rng = np.random.default_rng(401)
+    Ap, Bp = int(rng.integers(1, 1 << 62)) * 2 + 1, int(rng.integers(0, 1 << 62))
+    data = ctx.sets(off, items)
+    D = args.doph_bins
+
+    def run():
+        bk = ctx.hash(data, cfg.K, cfg.L, mh_a=mh_a, mh_b=mh_b, doph_bins=D, doph_a=Ap, doph_b=Bp)
+        nb = bk.n_buckets
+        del bk
+        return nb
+
+    for _ in range(max(1, args.warmup)):
+        run()
+    torch.cuda.synchronize()
+    ctx.timing_reset()
+    ctx.timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        nb = run()
+    e1.record()
+    torch.cuda.synchronize()
+    ctx.timing(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    return {"workload": f"Alg. 3 with DOPH on c3-shaped sets: n={cfg.n} sets, {int(wl3['set_items'].size)} items, "
+                        f"DOPH to {D} tokens, MinHash K={cfg.K} L={cfg.L}",
+            "value": cfg.n * world / (ms / 1e3), "unit": "sets/s", "ms_per_run": ms, "n_buckets": int(nb),
+            "hash_sort_ms": ctx.timing_get("hash.sort")[0] / args.steps}
 
 
 def bench_batched(args, geek, ctx, pk, pk_kind):
@@ -585,6 +627,9 @@ def main():
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--skip-alg1", action="store_true", help="skip the Alg. 1 transform measurement")
     ap.add_argument("--skip-refine", action="store_true", help="skip the extra-passes measurement")
+    ap.add_argument("--skip-doph", action="store_true", help="skip the DOPH sets measurement")
+    ap.add_argument("--doph-n", type=int, default=500_000, help="DOPH measurement: c3-shaped sets")
+    ap.add_argument("--doph-bins", type=int, default=400)
     ap.add_argument("--refine-passes", type=int, default=2)
     ap.add_argument("--alg1-m", type=int, default=40, help="Alg. 1: QALSH tables")
     ap.add_argument("--alg1-t", type=int, default=20000, help="Alg. 1: buckets per table")
