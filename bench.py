@@ -56,6 +56,19 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x, world):
+    """The largest value of x (a float) over all ranks; x itself at world 1.
+    Replicas: the slowest rank sets the job's time."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -212,10 +225,7 @@ def run_ours(args):
         ctx.timing(False)
         launches = geek.launch_count() - l0
         tm = {name: ctx.timing_get(name) for name in TIMED}
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, world)
         return ms, launches, tm, cl
 
     clocks = Clocks(local)
