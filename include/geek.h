@@ -40,7 +40,7 @@ typedef enum geek_status {
     GEEK_ERR_CUDA = 3,        /* a CUDA runtime call or kernel failed */
     GEEK_ERR_TIMEOUT = 4,     /* a bounded device wait expired */
     GEEK_ERR_OVERFLOW = 5,    /* a code or key does not fit its field */
-    GEEK_ERR_UNSUPPORTED = 6  /* valid request this build does not implement */
+    GEEK_ERR_UNSUPPORTED = 6  /* valid request the library does not implement */
 } geek_status;
 
 typedef struct geek_ctx geek_ctx;
