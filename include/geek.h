@@ -304,8 +304,8 @@ geek_status geek_assign_centers(geek_ctx *ctx, const geek_data *data, const doub
  * can imply.
  *
  * geek_assign_centers_noalloc computes exactly what geek_assign_centers
- * computes with GEEK_PREC_FP32 (same labels: the FP64 argmin of Eq. 1, ties to
- * the smallest index) but allocates nothing: no cudaMalloc, cudaFree or
+ * computes with GEEK_PREC_FP32 (same labels: the FP64 nearest centre, ties
+ * to the smallest index) but allocates nothing: no cudaMalloc, cudaFree or
  * allocating library routine.  Its scratch (the FP32 centres and their norms)
  * is one fixed device array of GEEK_NOALLOC_SCRATCH_BYTES that every GPU which
  * loads this library holds until the process exits.  Arguments are device
@@ -320,7 +320,9 @@ geek_status geek_assign_centers(geek_ctx *ctx, const geek_data *data, const doub
  *    threads without ordering) race and give wrong results.
  *  - Returns GEEK_ERR_INVALID for bad arguments and GEEK_ERR_UNSUPPORTED when
  *    d > 256, k > GEEK_NOALLOC_MAX_K or k*d > GEEK_NOALLOC_MAX_KD (the
- *    scratch limit); GEEK_ERR_CUDA if a CUDA call fails. */
+ *    scratch limit); GEEK_ERR_CUDA if a CUDA call or launch fails, and also,
+ *    without launching anything, when an earlier CUDA error is still
+ *    pending on the calling thread (it is left pending for its owner). */
 #define GEEK_NOALLOC_MAX_K 65536
 #define GEEK_NOALLOC_MAX_KD 1048576
 #define GEEK_NOALLOC_SCRATCH_BYTES (4 * GEEK_NOALLOC_MAX_KD + 4 * GEEK_NOALLOC_MAX_K + 256)

@@ -52,6 +52,8 @@ PINS = {
     "assign_dense": "exhaustive exact-rational nearest seed",
     "refine_passes": "separated blobs: exact rational blob means after one pass; SSE non-increasing; "
                      "fixed point; a centre without members keeps its value",
+    "hash_hetero": "per-table key rebuilt from exact rational codes and big-integer MinHash, grouped with dicts",
+    "hetero_attrs": "per-table rank of the numeric tuple among sorted distinct tuples, then the raw values",
     "modes": "collections.Counter brute force",
     "assign_cat": "brute-force match counts",
     "sparse_centres": "Counter brute force",

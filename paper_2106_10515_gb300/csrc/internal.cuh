@@ -5,6 +5,33 @@
 #include "common.cuh"
 
 
+// ---- dense assignment arithmetic (assign.cu, noalloc.cu) -----------------
+// Both assignment entry points promise the same labels, so the reference
+// distance and the FP32 window they decide with are defined once, here.
+
+// FP64 reference distance of the pinned definition.
+static __device__ __forceinline__ double ref_dist(const float *__restrict__ x, const double *__restrict__ c, int d) {
+    double D = 0.0;
+    for (int t = 0; t < d; t++) {
+        const double e = __dsub_rn((double)x[t], c[t]);
+        D = __dadd_rn(D, __dmul_rn(e, e));
+    }
+    return D;
+}
+
+// Rigorous half-window of the FP32 path for one object (see the proof in
+// the file header): (2 gamma_d + 4u)|x| cmax + 2u cmax^2 for the fast value,
+// plus the FP64 reference's own error (d+3) 2^-53 (|x| + cmax)^2, times 1.01.
+static __device__ __forceinline__ float window_fp32(float xn, float cmax, int d) {
+    const float u = 5.9604645e-8f;
+    const float gam = (float)d * u / (1.f - (float)d * u);
+    const float e32 = (2.f * gam + 4.f * u) * xn * cmax + 2.f * u * cmax * cmax;
+    const float s = xn + cmax;
+    const float e64 = (float)(d + 3) * 1.1102230e-16f * s * s;
+    return 1.01f * (e32 + e64) + 1e-30f;
+}
+
+
 // ---- dense projection (hash.cu) -------------------------------------------
 // Per-instance arguments of the FP32 projection kernel and its recheck
 // stages (device copies are read by the batched kernels).

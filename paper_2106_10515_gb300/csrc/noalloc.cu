@@ -34,25 +34,6 @@ __host__ __device__ inline NaLayout na_layout(unsigned char *base) {
     return L;
 }
 
-__device__ __forceinline__ double na_ref_dist(const float *x, const double *c, int d) {
-    double D = 0.0;
-    for (int t = 0; t < d; t++) {
-        const double e = __dsub_rn((double)x[t], c[t]);
-        D = __dadd_rn(D, __dmul_rn(e, e));
-    }
-    return D;
-}
-
-// same rigorous half-window as the FP32 path of geek_assign_centers
-__device__ __forceinline__ float na_window(float xn, float cmax, int d) {
-    const float u = 5.9604645e-8f;
-    const float gam = (float)d * u / (1.f - (float)d * u);
-    const float e32 = (2.f * gam + 4.f * u) * xn * cmax + 2.f * u * cmax * cmax;
-    const float s = xn + cmax;
-    const float e64 = (float)(d + 3) * 1.1102230e-16f * s * s;
-    return 1.01f * (e32 + e64) + 1e-30f;
-}
-
 __global__ void k_na_clear(unsigned *cmax) { *cmax = 0u; }
 
 __global__ void k_na_prep(const double *__restrict__ c64, int64_t k, int d, NaLayout S) {
@@ -168,7 +149,7 @@ __global__ void __launch_bounds__(256) k_na_assign(const float *__restrict__ x, 
                 const float v = xs[kk * NA_TR + rg * NA_RPT + r];
                 xs2 = fmaf(v, v, xs2);
             }
-            const float W = 2.f * na_window(sqrtf(xs2) * (1.f + 1.0e-3f), cmax, d);
+            const float W = 2.f * window_fp32(sqrtf(xs2) * (1.f + 1.0e-3f), cmax, d);
             const bool valid = B[r].i1 != 0x7FFFFFFF;
             const bool sure = valid && (k == 1 || (B[r].b2 - B[r].b1 > W * (1.f + 1e-6f)));
             labels[row] = sure ? B[r].i1 : NA_UNDECIDED;
@@ -206,14 +187,14 @@ __global__ void __launch_bounds__(256) k_na_decide(const float *__restrict__ x, 
             if (t < o) red_f[t] = fminf(red_f[t], red_f[t + o]);
             __syncthreads();
         }
-        const float lim = red_f[0] + 2.f * na_window(xn, cmax, d) * (1.f + 1e-6f);
+        const float lim = red_f[0] + 2.f * window_fp32(xn, cmax, d) * (1.f + 1e-6f);
         double bD = DBL_MAX;
         int bj = 0x7FFFFFFF;
         for (int64_t j = t; j < k; j += 256) {
             float dot = 0.f;
             for (int kk = 0; kk < d; kk++) dot = fmaf(xr[kk], S.c32[j * d + kk], dot);
             if (fmaf(-2.f, dot, S.cn[j]) <= lim) {
-                const double D = na_ref_dist(xr, c64 + j * d, d);
+                const double D = ref_dist(xr, c64 + j * d, d);
                 if (D < bD || (D == bD && (int)j < bj)) {
                     bD = D;
                     bj = (int)j;
@@ -280,6 +261,9 @@ extern "C" geek_status geek_assign_centers_noalloc(const float *x, int64_t n, in
     if (n < 0 || d < 1 || ldx < d || k < 1 || (n > 0 && (!x || !labels)) || !centers) return GEEK_ERR_INVALID;
     if (d > 256 || k > GEEK_NOALLOC_MAX_K || k * (int64_t)d > GEEK_NOALLOC_MAX_KD || n > 0x7FFFFFFFLL)
         return GEEK_ERR_UNSUPPORTED;
+    // an error left by earlier work on this thread belongs to that work:
+    // report it without clearing it instead of launching behind it
+    if (cudaPeekAtLastError() != cudaSuccess) return GEEK_ERR_CUDA;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
@@ -291,13 +275,18 @@ extern "C" geek_status geek_assign_centers_noalloc(const float *x, int64_t n, in
     if (n == 0) return GEEK_OK;
     cudaStream_t st = (cudaStream_t)stream;
     const NaLayout S = na_layout(D->scratch);
+    // each launch is checked on its own, so an error this call reports is
+    // its own (an error pending from earlier work was refused on entry)
     GK_COUNT();
     k_na_clear<<<1, 1, 0, st>>>(S.cmax);
+    if (cudaGetLastError() != cudaSuccess) return GEEK_ERR_CUDA;
     GK_COUNT();
     k_na_prep<<<(int)std::min<int64_t>(ceil_div(k, 128), (int64_t)D->num_sms * 8), 128, 0, st>>>(centers, k, d, S);
+    if (cudaGetLastError() != cudaSuccess) return GEEK_ERR_CUDA;
     const size_t smem = (size_t)d * NA_TR * sizeof(float) + (size_t)NA_KC * NA_TC * sizeof(float);
     GK_COUNT();
     k_na_assign<<<(unsigned)ceil_div(n, NA_TR), 256, smem, st>>>(x, ldx, n, d, k, S, labels);
+    if (cudaGetLastError() != cudaSuccess) return GEEK_ERR_CUDA;
     GK_COUNT();
     k_na_decide<<<(int)std::min<int64_t>(n, (int64_t)D->num_sms * 8), 256, d * sizeof(float), st>>>(x, ldx, n, d,
                                                                                                    centers, k, S, labels);

@@ -190,7 +190,11 @@ class Data:
     def dense(cls, x, host=False):
         self = cls(DENSE, host, x.shape[0], [x])
         self.c.d = x.shape[1]
-        self.c.ldx = x.shape[1]
+        # a row-strided view (unit column stride) passes its row stride
+        if isinstance(x, torch.Tensor) and x.dim() == 2 and x.stride(1) == 1 and x.shape[0] > 1:
+            self.c.ldx = x.stride(0)
+        else:
+            self.c.ldx = x.shape[1]
         self.c.x = _ptr(x)
         return self
 

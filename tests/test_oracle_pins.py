@@ -494,3 +494,55 @@ def test_sparse_centres_and_jaccard(orc):
         J = [Fraction(len(set(s) & c), len(set(s) | c)) if (s or c) else Fraction(0) for c in cents]
         assert lab[i] == J.index(max(J))
         assert Fraction(int(inter[i]), int(uni[i])) == max(J)
+
+
+# ------------------------------------------------- heterogeneous rows (Alg. 2) --
+def test_hetero_keys_and_attrs_from_the_formula(orc):
+    """Alg. 2 reading: table l's key is (E2LSH codes of functions l*K .. l*K+K-1
+    on the numeric part) followed by (MinHash values of functions
+    l*Kc .. l*Kc+Kc-1 on the token set {offset_j + v_j}); the unified
+    attributes of Sect. 3.3 are, per table, the rank of the numeric-only tuple
+    among the table's distinct numeric tuples, then the raw categorical
+    values.  Rebuilt here with exact rationals, big integers and dicts; K != Kc
+    and L != n_cat so a swapped slice or attribute order cannot pass."""
+    rng = np.random.default_rng(21)
+    n, d, K, L, Kc, n_cat, w = 60, 3, 2, 3, 3, 4, 4.0
+    cards = [3, 5, 2, 7]
+    x = (rng.standard_normal((n, d)) * 3).astype(np.float32)
+    x[n // 2:] = x[: n - n // 2]                 # repeated numeric parts share buckets
+    a = rng.standard_normal((K * L, d)).astype(np.float32)
+    b = (rng.random(K * L) * 4).astype(np.float32)
+    cat = np.stack([rng.integers(0, c, size=n) for c in cards], axis=1).astype(np.int64)
+    offs = np.concatenate([[0], np.cumsum(cards)[:-1]])
+    tokens = (cat + offs[None, :]).astype(np.uint32)
+    A = rng.integers(0, 1 << 63, size=Kc * L, dtype=np.uint64) * np.uint64(2) + np.uint64(1)
+    B = rng.integers(0, 1 << 63, size=Kc * L, dtype=np.uint64)
+    codes, mh, bk, nbk = orc.hash_hetero(x, tokens, a, b, w, K, L, A, B, Kc)
+
+    want_codes, _ = exact_codes(x, a, b, w)
+    assert np.array_equal(codes, want_codes)
+    want_mh = np.array([[min(hbig(A[f], B[f], t) for t in tokens[i]) for f in range(Kc * L)] for i in range(n)])
+    assert np.array_equal(mh, want_mh)
+
+    attrs = orc.hetero_attrs(nbk, cat)
+    assert attrs.shape == (n, L + n_cat)
+    for l in range(L):
+        full = [tuple(int(v) for v in want_codes[i, l * K:(l + 1) * K]) +
+                tuple(int(v) for v in want_mh[i, l * Kc:(l + 1) * Kc]) for i in range(n)]
+        num = [tuple(int(v) for v in want_codes[i, l * K:(l + 1) * K]) for i in range(n)]
+        for keys, got in ((full, bk), (num, nbk)):
+            rank = {k: r for r, k in enumerate(sorted(set(keys)))}
+            assert got.n_buckets[l] == len(rank)
+            assert [int(v) for v in got.obj_bucket[l]] == [rank[k] for k in keys]
+            members = defaultdict(list)
+            for i, k in enumerate(keys):
+                members[rank[k]].append(i)
+            base = int(got.table_base[l])
+            for r in range(len(rank)):
+                lo, hi = got.boff[base + r], got.boff[base + r + 1]
+                assert got.bmem[lo:hi].tolist() == members[r]
+        num_rank = {k: r for r, k in enumerate(sorted(set(num)))}
+        assert [int(v) for v in attrs[:, l]] == [num_rank[k] for k in num]
+    assert np.array_equal(attrs[:, L:], cat)
+    # the split is a real concatenation: some numeric buckets are cut by MinHash
+    assert any(bk.n_buckets[l] > nbk.n_buckets[l] for l in range(L))
