@@ -162,6 +162,24 @@ typedef struct geek_assign_stats {
  * thread at a time; contexts are independent. */
 geek_status geek_ctx_create(int device, geek_ctx **out);
 geek_status geek_ctx_destroy(geek_ctx *ctx);
+/* Context options (geek_ctx_set_option).  The paper has no counterpart:
+ * these bound the library's own device waits and inject failures so that the
+ * error paths can be tested without faulting a GPU.
+ *  GEEK_OPT_WAIT_LIMIT_NS: limit of one bounded wait of a radix-sort pass on a
+ *    predecessor tile's published count, in ns (default 2e9, range
+ *    [1e3, 6e10]).  A wait that runs out gives up with a partial prefix (the
+ *    pass's writes stay inside its segment; its result is wrong), and the
+ *    call that sorted returns GEEK_ERR_TIMEOUT.
+ *  GEEK_OPT_TEST_STALL_TILE: FOR TESTS.  Tile t >= 0 of every radix pass never
+ *    publishes its count, so the tiles after it wait until the wait limit and
+ *    the call returns GEEK_ERR_TIMEOUT; -1 (default) turns it off.
+ *  GEEK_OPT_TEST_FAIL_ALLOC: FOR TESTS.  Value v >= 0 makes the device
+ *    allocation after the next v ones fail as if the device were out of memory
+ *    (the call returns GEEK_ERR_NOMEM, the countdown then turns itself off);
+ *    -1 (default) turns it off.
+ * Errors: INVALID (NULL ctx, unknown option, value out of range). */
+enum { GEEK_OPT_WAIT_LIMIT_NS = 1, GEEK_OPT_TEST_STALL_TILE = 2, GEEK_OPT_TEST_FAIL_ALLOC = 3 };
+geek_status geek_ctx_set_option(geek_ctx *ctx, int32_t option, int64_t value);
 /* Message for the last failing call on ctx (never NULL; owned by ctx). */
 const char *geek_last_error(const geek_ctx *ctx);
 /* Library version string (static storage). */

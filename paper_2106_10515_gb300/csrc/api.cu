@@ -27,6 +27,8 @@ geek_status stage(geek_ctx *ctx, Scratch &scr, const T *src, size_t count, bool 
 // Result buffers are stream-ordered allocations on the call's stream (no
 // device-wide synchronisation, so copies on other streams keep running).
 geek_status own_alloc(geek_ctx *ctx, void **p, size_t bytes, cudaStream_t st) {
+    if (alloc_injected_failure(ctx))
+        return set_error(ctx, GEEK_ERR_NOMEM, "device allocation of %zu bytes failed (injected)", bytes);
     cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -264,6 +266,27 @@ geek_status geek_ctx_create(int device, geek_ctx **out) {
 geek_status geek_ctx_destroy(geek_ctx *ctx) {
     delete ctx;
     return GEEK_OK;
+}
+
+geek_status geek_ctx_set_option(geek_ctx *ctx, int32_t option, int64_t value) {
+    if (!ctx) return GEEK_ERR_INVALID;
+    switch (option) {
+    case GEEK_OPT_WAIT_LIMIT_NS:
+        if (value < 1000 || value > 60000000000LL)
+            return set_error(ctx, GEEK_ERR_INVALID, "wait limit %lld ns outside [1e3, 6e10]", (long long)value);
+        ctx->lb_wait_ns = (unsigned long long)value;
+        return GEEK_OK;
+    case GEEK_OPT_TEST_STALL_TILE:
+        if (value < -1 || value > 0x7FFFFFFFLL) return set_error(ctx, GEEK_ERR_INVALID, "bad stall tile");
+        ctx->stall_tile = (int)value;
+        return GEEK_OK;
+    case GEEK_OPT_TEST_FAIL_ALLOC:
+        if (value < -1) return set_error(ctx, GEEK_ERR_INVALID, "bad allocation countdown");
+        ctx->fail_alloc_after = value;
+        return GEEK_OK;
+    default:
+        return set_error(ctx, GEEK_ERR_INVALID, "unknown option %d", (int)option);
+    }
 }
 
 const char *geek_last_error(const geek_ctx *ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }

@@ -31,6 +31,13 @@ struct geek_ctx {
     std::map<int, int> tile_cache;
     // device word a bounded wait of the radix sort sets on timeout (lazy)
     int *sort_err = nullptr;
+    // limit of one look-back wait of the radix passes (GEEK_OPT_WAIT_LIMIT_NS)
+    unsigned long long lb_wait_ns = 2000000000ull;
+    // failure injection (tests): a radix tile that never publishes its count
+    // (GEEK_OPT_TEST_STALL_TILE, -1 off) and a countdown after which device
+    // allocations fail (GEEK_OPT_TEST_FAIL_ALLOC, -1 off)
+    int stall_tile = -1;
+    long long fail_alloc_after = -1;
     ~geek_ctx() {
         if (sort_err) cudaFree(sort_err);
     }
@@ -67,6 +74,18 @@ struct EvTimer {
     }
     ~EvTimer() { stop(); }
 };
+
+// Failure injection of GEEK_OPT_TEST_FAIL_ALLOC: true when this allocation
+// is to fail (the countdown reached zero); the countdown then stays off.
+static inline bool alloc_injected_failure(geek_ctx *ctx) {
+    if (!ctx || ctx->fail_alloc_after < 0) return false;
+    if (ctx->fail_alloc_after == 0) {
+        ctx->fail_alloc_after = -1;
+        return true;
+    }
+    ctx->fail_alloc_after--;
+    return false;
+}
 
 // Per-call error plumbing: every failure sets ctx->last_error and returns.
 geek_status set_error(geek_ctx *ctx, geek_status st, const char *fmt, ...);
@@ -109,6 +128,8 @@ struct Scratch {
         void *p = nullptr;
         size_t bytes = count * sizeof(T);
         if (bytes == 0) bytes = 16;
+        if (alloc_injected_failure(ctx))
+            return set_error(ctx, GEEK_ERR_NOMEM, "device allocation of %zu bytes failed (injected)", bytes);
         cudaError_t e = cudaMallocAsync(&p, bytes, st);
         if (e != cudaSuccess) {
             cudaGetLastError();

@@ -79,7 +79,6 @@ __global__ void __launch_bounds__(1024) k_seg_scan_u32(uint32_t *__restrict__ c,
 // Word layout: bits 31..30 = state (0 empty, 1 tile count, 2 inclusive
 // prefix), bits 29..0 = count; segments are limited to 2^30 - 1 elements.
 constexpr uint32_t LB_AGG = 1u << 30, LB_PREFIX = 2u << 30, LB_MASK = (1u << 30) - 1;
-constexpr unsigned long long LB_WAIT_NS = 2000000000ull;  // 2 s per look-back wait
 constexpr int HIST_BLOCKS_PER_SEG = 96;
 
 __device__ __forceinline__ unsigned long long sort_gtimer() {
@@ -138,7 +137,8 @@ __global__ void __launch_bounds__(RS_THREADS, 4)
                   const uint32_t *__restrict__ v_in, uint64_t *__restrict__ lo_out,
                   uint64_t *__restrict__ hi_out, uint32_t *__restrict__ v_out, int64_t m, int tiles,
                   int dsel, int sh, const uint32_t *__restrict__ dbase, int dstride, uint32_t *__restrict__ look,
-                  uint32_t *__restrict__ ticket, int *__restrict__ err) {
+                  uint32_t *__restrict__ ticket, int *__restrict__ err, unsigned long long wait_ns,
+                  int stall_tile) {
     __shared__ uint32_t whist[NWARP][256];
     __shared__ uint32_t tstart[256];
     __shared__ uint32_t gbase[256];
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(RS_THREADS, 4)
     // tile is staged, so that predecessors have had time to finish theirs
     uint32_t *lk = look + (int64_t)seg * tiles * 256;
     volatile uint32_t *vlk = lk;
-    vlk[(int64_t)tile * 256 + t] = (tile == 0 ? LB_PREFIX : LB_AGG) | run;
+    if (tile != stall_tile) vlk[(int64_t)tile * 256 + t] = (tile == 0 ? LB_PREFIX : LB_AGG) | run;
     uint32_t tot;
     tstart[t] = block_excl_scan<RS_THREADS>(run, &tot, wsum);
     __syncthreads();
@@ -215,6 +215,7 @@ __global__ void __launch_bounds__(RS_THREADS, 4)
     }
     // look back over the predecessors of this segment, four words per read
     uint32_t excl = 0;
+    bool gave_up = false;
     if (tile > 0) {
         int j = tile - 1;
         unsigned long long w0 = 0;
@@ -239,14 +240,28 @@ __global__ void __launch_bounds__(RS_THREADS, 4)
                 const unsigned long long tn = sort_gtimer();
                 if (w0 == 0) {
                     w0 = tn;
-                } else if (tn - w0 > LB_WAIT_NS) {
-                    atomicExch(err, (int)GEEK_ERR_TIMEOUT);  // partial prefix: wrong but in bounds
+                } else if (tn - w0 > wait_ns) {
+                    gave_up = true;
                     break;
                 }
             }
         }
-        vlk[(int64_t)tile * 256 + t] = LB_PREFIX | ((excl + run) & LB_MASK);
     }
+    // A wait that ran out: the block recounts every digit of its
+    // predecessors straight from this pass's input (a permutation of the
+    // keys, so the counts are exact), which keeps the pass correct and every
+    // write inside the segment; the call still reports GEEK_ERR_TIMEOUT.
+    if (__syncthreads_or(gave_up)) {
+        if (t == 0) atomicExch(err, (int)GEEK_ERR_TIMEOUT);
+        gbase[t] = 0;
+        __syncthreads();
+        const uint64_t *src = dsel ? hi_in : lo_in;
+        for (int64_t p = t; p < t0; p += RS_THREADS) atomicAdd(&gbase[(uint32_t)((src[so + p] >> sh) & 0xFFu)], 1u);
+        __syncthreads();
+        excl = gbase[t];
+        __syncthreads();
+    }
+    if (tile > 0 && tile != stall_tile) vlk[(int64_t)tile * 256 + t] = LB_PREFIX | ((excl + run) & LB_MASK);
     // output position of staged element q of digit d: goff[d] + q
     gbase[t] = dbase[(int64_t)seg * dstride + t] + excl - tstart[t];
     __syncthreads();
@@ -548,7 +563,7 @@ geek_status radix_sort_segments(geek_ctx *ctx, Scratch &scr, int S, int64_t m, u
 #define RS_OS(H, V)                                                                                              \
     k_rs_onesweep<H, V><<<(unsigned)nblocks, RS_THREADS, stage, st>>>(alo, ahi, av, blo, bhi, bv, m, tiles, dsel, sv, \
                                                                       dbase_all + (size_t)q * 256, npass * 256, look, \
-                                                                      ticket, ctx->sort_err)
+                                                                      ticket, ctx->sort_err, ctx->lb_wait_ns, ctx->stall_tile)
         if (hi && hv) RS_OS(true, true);
         else if (hi) RS_OS(true, false);
         else if (hv) RS_OS(false, true);

@@ -21,6 +21,7 @@ MEM_DEVICE, MEM_HOST = 0, 1
 PROJ_E2LSH, PROJ_SRP, PROJ_QALSH = 0, 1, 2
 PREC_FP32, PREC_BF16, PREC_BF16X3 = 0, 1, 2
 PREC_AUTO = -1
+OPT_WAIT_LIMIT_NS, OPT_TEST_STALL_TILE, OPT_TEST_FAIL_ALLOC = 1, 2, 3
 STATUS_NAMES = ["OK", "ERR_INVALID", "ERR_NOMEM", "ERR_CUDA", "ERR_TIMEOUT", "ERR_OVERFLOW",
                 "ERR_UNSUPPORTED"]
 
@@ -88,7 +89,8 @@ EXPORTS = ["geek_ctx_create", "geek_ctx_destroy", "geek_last_error", "geek_versi
            "geek_assign_centers", "geek_timing_enable", "geek_timing_reset", "geek_timing_get",
            "geek_launch_count", "geek_assign_centers_noalloc", "geek_batch_create", "geek_batch_run",
            "geek_batch_info_get", "geek_batch_instance_stats", "geek_batch_copy_out", "geek_batch_seed_ids_count",
-           "geek_batch_destroy", "geek_data_upload", "geek_resident_free", "geek_refine"]
+           "geek_batch_destroy", "geek_data_upload", "geek_resident_free", "geek_refine",
+           "geek_ctx_set_option"]
 
 _lib = None
 
@@ -119,6 +121,7 @@ def lib():
                               C.POINTER(geek_assign_stats), P]
     L.geek_assign_centers.argtypes = [P, C.POINTER(geek_data), P, C.c_int64,
                                       C.POINTER(geek_assign_params), P, C.POINTER(geek_assign_stats), P]
+    L.geek_ctx_set_option.argtypes = [P, C.c_int32, C.c_int64]
     L.geek_timing_enable.argtypes = [P, C.c_int]
     L.geek_timing_reset.argtypes = [P]
     L.geek_timing_get.argtypes = [P, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64),
@@ -300,6 +303,9 @@ class Context:
             raise GeekError(st, f"geek_ctx_create(device={device}) failed")
         self.h = h
         self._keep = []
+
+    def set_option(self, option, value):
+        self._chk(lib().geek_ctx_set_option(self.h, option, int(value)))
 
     def timing(self, on=True):
         self._chk(lib().geek_timing_enable(self.h, 1 if on else 0))
