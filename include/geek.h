@@ -288,6 +288,38 @@ geek_status geek_assign(geek_ctx *ctx, const geek_data *data, const geek_buckets
                         const silk_seeds *s, const geek_assign_params *p, int32_t *labels,
                         double *centers, geek_assign_stats *stats, geek_stream stream);
 
+/* geek_assign_ex: geek_assign, and the central vectors it used (Sect. 3.3) kept
+ * in a library-owned handle *centres (sizes vary with the data):
+ *  DENSE: centers k x d float64 (the FP64 centroids).
+ *  HETERO: modes k x n_attr int64, n_attr = L + n_cat: attribute l < L is
+ *    the canonical rank of the mode's numeric E2LSH tuple among table l's
+ *    distinct numeric tuples (ascending lexicographic order, as bucket ids);
+ *    attribute L + j is the mode token of categorical attribute j (the value
+ *    given in geek_data.cat).  Mode = most frequent value, ties to the
+ *    smallest (in tuple order for the numeric attributes).
+ *  SETS: centre j = items item_off[j] .. item_off[j+1] (ascending u32) of
+ *    items, the items present in more than half of seed j's member sets.
+ * Same arguments and errors as geek_assign otherwise (centers output dropped:
+ * the handle holds it).  geek_centres_info_get gives kind, k, d (DENSE),
+ * n_attr (HETERO) and n_items (SETS); geek_centres_copy_out copies the
+ * arrays of the handle's kind into caller device buffers (NULL skips one);
+ * geek_centres_free releases the handle. */
+typedef struct geek_centres geek_centres;
+typedef struct geek_centres_info {
+    int32_t kind;
+    int32_t d;
+    int32_t n_attr;
+    int64_t k;
+    int64_t n_items;
+} geek_centres_info;
+geek_status geek_assign_ex(geek_ctx *ctx, const geek_data *data, const geek_buckets *b, const silk_seeds *s,
+                           const geek_assign_params *p, int32_t *labels, geek_assign_stats *stats,
+                           geek_centres **centres, geek_stream stream);
+geek_status geek_centres_info_get(const geek_centres *c, geek_centres_info *info);
+geek_status geek_centres_copy_out(const geek_centres *c, double *centers, int64_t *modes, int64_t *item_off,
+                                  uint32_t *items, geek_stream stream);
+geek_status geek_centres_free(geek_centres *c);
+
 /* geek_refine: further passes of assignment for more compact clusters
  * (Sect. 5: several passes of data assignment; each pass is Lloyd's update
  * step then the assignment step, Sect. 2).  Dense data only.  On entry

@@ -5,6 +5,19 @@
 
 #include "internal.cuh"
 
+// Result buffers are stream-ordered allocations on the call's stream (no
+// device-wide synchronisation, so copies on other streams keep running).
+geek_status own_alloc(geek_ctx *ctx, void **p, size_t bytes, cudaStream_t st) {
+    if (alloc_injected_failure(ctx))
+        return set_error(ctx, GEEK_ERR_NOMEM, "device allocation of %zu bytes failed (injected)", bytes);
+    cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ctx, GEEK_ERR_NOMEM, "device allocation of %zu bytes failed", bytes);
+    }
+    return GEEK_OK;
+}
+
 namespace {
 
 cudaStream_t S(geek_stream s) { return (cudaStream_t)s; }
@@ -21,19 +34,6 @@ geek_status stage(geek_ctx *ctx, Scratch &scr, const T *src, size_t count, bool 
     GK_TRY(scr.alloc(&d, count));
     GK_CUDA(ctx, cudaMemcpyAsync(d, src, count * sizeof(T), cudaMemcpyHostToDevice, st));
     *dst = d;
-    return GEEK_OK;
-}
-
-// Result buffers are stream-ordered allocations on the call's stream (no
-// device-wide synchronisation, so copies on other streams keep running).
-geek_status own_alloc(geek_ctx *ctx, void **p, size_t bytes, cudaStream_t st) {
-    if (alloc_injected_failure(ctx))
-        return set_error(ctx, GEEK_ERR_NOMEM, "device allocation of %zu bytes failed (injected)", bytes);
-    cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, st);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return set_error(ctx, GEEK_ERR_NOMEM, "device allocation of %zu bytes failed", bytes);
-    }
     return GEEK_OK;
 }
 
@@ -159,12 +159,16 @@ geek_status hash_impl(geek_ctx *ctx, const geek_data *data, const geek_hash_para
             GK_TRY(doph_reduce(ctx, n, off, items, p->doph_bins, p->doph_a, p->doph_b, tok, st));
             GK_TRY(minhash_rows64(ctx, n, p->doph_bins, tok, F2, p->mh_a, p->mh_b, mh, st));
         } else {
+            EvTimer tk(ctx, "kernel.minhash", st);
+            tk.work = (double)n_items * F2;  // hash evaluations
             GK_TRY(minhash_rows(ctx, n, off, 0, items, F2, p->mh_a, p->mh_b, mh, st));
         }
     } else if (kind == GEEK_HETERO) {
         const uint32_t *tok;
         GK_TRY(stage(ctx, scr, data->cat, (size_t)n * data->n_cat, host, &tok, st));
         GK_TRY(scr.alloc(&mh, (size_t)n * F2));
+        EvTimer tk(ctx, "kernel.minhash", st);
+        tk.work = (double)n * data->n_cat * F2;  // hash evaluations
         GK_TRY(minhash_rows(ctx, n, nullptr, data->n_cat, tok, F2, p->mh_a, p->mh_b, mh, st));
     }
     std::vector<int> tbits;
@@ -524,58 +528,141 @@ geek_status geek_refine(geek_ctx *ctx, const geek_data *data, double *centers, i
     }
 }
 
+}  // extern "C"
+
+namespace {
+
+void free_centres(geek_centres *c) {
+    if (!c) return;
+    for (void *p : {(void *)c->centers, (void *)c->modes, (void *)c->item_off, (void *)c->items})
+        if (p) cudaFreeAsync(p, c->st);
+    delete c;
+}
+
+geek_status assign_impl(geek_ctx *ctx, const geek_data *data, const geek_buckets *b, const silk_seeds *s,
+                        const geek_assign_params *p, int32_t *labels, double *centers, geek_assign_stats *stats,
+                        geek_centres *keep, cudaStream_t st) {
+    GK_TRY(check_data(ctx, data));
+    if (!s || !p || !labels) return set_error(ctx, GEEK_ERR_INVALID, "NULL argument");
+    if (stats) *stats = geek_assign_stats{};
+    EvTimer tm(ctx, "assign", st);
+    Scratch scr(ctx, st);
+    const bool host = data->mem == GEEK_MEM_HOST;
+    const int64_t n = data->n;
+    int32_t *lab = labels;
+    if (host) GK_TRY(scr.alloc(&lab, n));
+    if (data->kind == GEEK_DENSE) {
+        const float *x;
+        GK_TRY(stage(ctx, scr, data->x, (size_t)n * data->ldx, host, &x, st));
+        double *c = centers;
+        if (!c || host) GK_TRY(scr.alloc(&c, (size_t)std::max<int64_t>(1, s->k) * data->d));
+        GK_TRY(centroids_from_seeds(ctx, x, data->ldx, data->d, s, c, st));
+        GK_TRY(assign_dense_centres(ctx, scr, x, data->ldx, n, data->d, c, s->k, p->precision, lab, stats, st));
+        if (host && centers)
+            GK_CUDA(ctx, cudaMemcpyAsync(centers, c, sizeof(double) * s->k * data->d, cudaMemcpyDeviceToHost, st));
+        if (keep) {
+            keep->kind = GEEK_DENSE;
+            keep->k = s->k;
+            keep->d = data->d;
+            const size_t bytes = sizeof(double) * (size_t)s->k * data->d;
+            GK_TRY(own_alloc(ctx, (void **)&keep->centers, bytes, st));
+            if (bytes) GK_CUDA(ctx, cudaMemcpyAsync(keep->centers, c, bytes, cudaMemcpyDeviceToDevice, st));
+        }
+    } else if (data->kind == GEEK_HETERO) {
+        if (!b || b->kind != GEEK_HETERO || b->n != n)
+            return set_error(ctx, GEEK_ERR_INVALID, "hetero assignment needs its geek_buckets");
+        const uint32_t *tok;
+        GK_TRY(stage(ctx, scr, data->cat, (size_t)n * data->n_cat, host, &tok, st));
+        GK_TRY(assign_hetero(ctx, scr, b, tok, data->n_cat, s, lab, stats, keep, st));
+    } else {
+        int64_t n_items = 0;
+        if (host) {
+            n_items = data->set_off[n];
+        } else {
+            GK_CUDA(ctx, cudaMemcpyAsync(&n_items, data->set_off + n, 8, cudaMemcpyDeviceToHost, st));
+            GK_CUDA(ctx, cudaStreamSynchronize(st));
+        }
+        const int64_t *off;
+        const uint32_t *items;
+        GK_TRY(stage(ctx, scr, data->set_off, (size_t)n + 1, host, &off, st));
+        GK_TRY(stage(ctx, scr, data->set_items, (size_t)n_items, host, &items, st));
+        GK_TRY(assign_sets(ctx, scr, off, items, n, s, lab, stats, keep, st));
+    }
+    if (host) {
+        GK_CUDA(ctx, cudaMemcpyAsync(labels, lab, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+        GK_CUDA(ctx, cudaStreamSynchronize(st));
+    }
+    return GEEK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 geek_status geek_assign(geek_ctx *ctx, const geek_data *data, const geek_buckets *b,
                         const silk_seeds *s, const geek_assign_params *p, int32_t *labels,
                         double *centers, geek_assign_stats *stats, geek_stream stream) {
     if (!ctx) return GEEK_ERR_INVALID;
     try {
-        GK_TRY(check_data(ctx, data));
-        if (!s || !p || !labels) return set_error(ctx, GEEK_ERR_INVALID, "NULL argument");
-        if (stats) *stats = geek_assign_stats{};
-        cudaStream_t st = S(stream);
-        EvTimer tm(ctx, "assign", st);
-        Scratch scr(ctx, st);
-        const bool host = data->mem == GEEK_MEM_HOST;
-        const int64_t n = data->n;
-        int32_t *lab = labels;
-        if (host) GK_TRY(scr.alloc(&lab, n));
-        if (data->kind == GEEK_DENSE) {
-            const float *x;
-            GK_TRY(stage(ctx, scr, data->x, (size_t)n * data->ldx, host, &x, st));
-            double *c = centers;
-            if (!c || host) GK_TRY(scr.alloc(&c, (size_t)std::max<int64_t>(1, s->k) * data->d));
-            GK_TRY(centroids_from_seeds(ctx, x, data->ldx, data->d, s, c, st));
-            GK_TRY(assign_dense_centres(ctx, scr, x, data->ldx, n, data->d, c, s->k, p->precision, lab, stats, st));
-            if (host && centers)
-                GK_CUDA(ctx, cudaMemcpyAsync(centers, c, sizeof(double) * s->k * data->d, cudaMemcpyDeviceToHost, st));
-        } else if (data->kind == GEEK_HETERO) {
-            if (!b || b->kind != GEEK_HETERO || b->n != n)
-                return set_error(ctx, GEEK_ERR_INVALID, "hetero assignment needs its geek_buckets");
-            const uint32_t *tok;
-            GK_TRY(stage(ctx, scr, data->cat, (size_t)n * data->n_cat, host, &tok, st));
-            GK_TRY(assign_hetero(ctx, scr, b, tok, data->n_cat, s, lab, stats, st));
-        } else {
-            int64_t n_items = 0;
-            if (host) {
-                n_items = data->set_off[n];
-            } else {
-                GK_CUDA(ctx, cudaMemcpyAsync(&n_items, data->set_off + n, 8, cudaMemcpyDeviceToHost, st));
-                GK_CUDA(ctx, cudaStreamSynchronize(st));
-            }
-            const int64_t *off;
-            const uint32_t *items;
-            GK_TRY(stage(ctx, scr, data->set_off, (size_t)n + 1, host, &off, st));
-            GK_TRY(stage(ctx, scr, data->set_items, (size_t)n_items, host, &items, st));
-            GK_TRY(assign_sets(ctx, scr, off, items, n, s, lab, stats, st));
-        }
-        if (host) {
-            GK_CUDA(ctx, cudaMemcpyAsync(labels, lab, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
-            GK_CUDA(ctx, cudaStreamSynchronize(st));
-        }
-        return GEEK_OK;
+        return assign_impl(ctx, data, b, s, p, labels, centers, stats, nullptr, S(stream));
     } catch (...) {
         return set_error(ctx, GEEK_ERR_NOMEM, "host exception in geek_assign");
     }
+}
+
+geek_status geek_assign_ex(geek_ctx *ctx, const geek_data *data, const geek_buckets *b, const silk_seeds *s,
+                           const geek_assign_params *p, int32_t *labels, geek_assign_stats *stats,
+                           geek_centres **centres, geek_stream stream) {
+    if (!ctx) return GEEK_ERR_INVALID;
+    if (!centres) return set_error(ctx, GEEK_ERR_INVALID, "NULL centres handle pointer");
+    *centres = nullptr;
+    geek_centres *c = new (std::nothrow) geek_centres();
+    if (!c) return set_error(ctx, GEEK_ERR_NOMEM, "host allocation failed");
+    c->ctx = ctx;
+    c->st = S(stream);
+    geek_status st;
+    try {
+        st = assign_impl(ctx, data, b, s, p, labels, nullptr, stats, c, S(stream));
+    } catch (...) {
+        st = set_error(ctx, GEEK_ERR_NOMEM, "host exception in geek_assign_ex");
+    }
+    if (st != GEEK_OK) {
+        free_centres(c);
+        return st;
+    }
+    *centres = c;
+    return GEEK_OK;
+}
+
+geek_status geek_centres_info_get(const geek_centres *c, geek_centres_info *info) {
+    if (!c || !info) return GEEK_ERR_INVALID;
+    info->kind = c->kind;
+    info->d = c->d;
+    info->n_attr = c->n_attr;
+    info->k = c->k;
+    info->n_items = c->n_items;
+    return GEEK_OK;
+}
+
+geek_status geek_centres_copy_out(const geek_centres *c, double *centers, int64_t *modes, int64_t *item_off,
+                                  uint32_t *items, geek_stream stream) {
+    if (!c) return GEEK_ERR_INVALID;
+    geek_ctx *ctx = c->ctx;
+    cudaStream_t st = S(stream);
+    const auto D2D = cudaMemcpyDeviceToDevice;
+    if (centers && c->centers && c->k * c->d)
+        GK_CUDA(ctx, cudaMemcpyAsync(centers, c->centers, sizeof(double) * c->k * c->d, D2D, st));
+    if (modes && c->modes && c->k * c->n_attr)
+        GK_CUDA(ctx, cudaMemcpyAsync(modes, c->modes, sizeof(int64_t) * c->k * c->n_attr, D2D, st));
+    if (item_off && c->item_off) GK_CUDA(ctx, cudaMemcpyAsync(item_off, c->item_off, sizeof(int64_t) * (c->k + 1), D2D, st));
+    if (items && c->items && c->n_items)
+        GK_CUDA(ctx, cudaMemcpyAsync(items, c->items, sizeof(uint32_t) * c->n_items, D2D, st));
+    return GEEK_OK;
+}
+
+geek_status geek_centres_free(geek_centres *c) {
+    free_centres(c);
+    return GEEK_OK;
 }
 
 }  // extern "C"

@@ -24,8 +24,10 @@ __global__ void k_build_attrs(int64_t n, int L, int ncat, const uint64_t *__rest
 
 // mode of attribute a over seed j's members: most frequent value, ties to the
 // smallest (one thread per (seed, attribute); quadratic in the seed size)
+// rep (nullable): the first member, in the seed's ascending order, holding
+// the mode value
 __global__ void k_modes(int64_t k, int A, const int64_t *__restrict__ soff, const int32_t *__restrict__ sids,
-                        const uint64_t *__restrict__ attrs, uint64_t *__restrict__ modes) {
+                        const uint64_t *__restrict__ attrs, uint64_t *__restrict__ modes, int32_t *__restrict__ rep) {
     const int64_t total = k * A;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j = e / A;
@@ -33,6 +35,7 @@ __global__ void k_modes(int64_t k, int A, const int64_t *__restrict__ soff, cons
         const int64_t s = soff[j], t = soff[j + 1];
         uint64_t best = 0;
         int64_t bc = 0;
+        int32_t br = -1;
         for (int64_t p = s; p < t; p++) {
             const uint64_t v = attrs[(int64_t)sids[p] * A + a];
             int64_t c = 0;
@@ -40,9 +43,44 @@ __global__ void k_modes(int64_t k, int A, const int64_t *__restrict__ soff, cons
             if (c > bc || (c == bc && v < best)) {
                 bc = c;
                 best = v;
+                br = sids[p];
             }
         }
         modes[e] = best;
+        if (rep) rep[e] = br;
+    }
+}
+
+// flags[g] = 1 where bucket g (global id, in table l's canonical order) starts
+// a new numeric E2LSH tuple: the table keys of heterogeneous rows put the
+// numeric tuple first, so equal numeric tuples form runs of buckets.
+__global__ void k_num_run_flags(int64_t nb, int64_t base, const int64_t *__restrict__ boff,
+                                const uint32_t *__restrict__ members, const uint64_t *__restrict__ num_key_l,
+                                int64_t *__restrict__ flags) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nb; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = base + r;
+        int64_t f = 1;
+        if (r > 0) f = num_key_l[members[boff[g]]] != num_key_l[members[boff[g - 1]]];
+        flags[g] = f;
+    }
+}
+
+// modes as a user sees them: per table, the rank of the mode's numeric tuple
+// among the table's distinct numeric tuples (via the bucket of the member
+// that holds it); then the mode tokens
+__global__ void k_mode_out(int64_t k, int A, int L, int64_t n, const uint64_t *__restrict__ modes,
+                           const int32_t *__restrict__ rep, const int32_t *__restrict__ obj_bucket,
+                           const int64_t *__restrict__ tbase, const int64_t *__restrict__ excl,
+                           int64_t *__restrict__ out) {
+    const int64_t total = k * A;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(e % A);
+        if (a < L) {
+            const int64_t g = tbase[a] + obj_bucket[(int64_t)a * n + rep[e]];
+            out[e] = excl[g] - excl[tbase[a]];
+        } else {
+            out[e] = (int64_t)modes[e];
+        }
     }
 }
 
@@ -343,7 +381,8 @@ geek_status majority_per_group(geek_ctx *ctx, Scratch &scr, int64_t ng, const in
 }
 
 geek_status assign_hetero(geek_ctx *ctx, Scratch &scr, const geek_buckets *b, const uint32_t *tok, int n_cat,
-                          const silk_seeds *s, int32_t *labels, geek_assign_stats *stats, cudaStream_t st) {
+                          const silk_seeds *s, int32_t *labels, geek_assign_stats *stats, geek_centres *keep,
+                          cudaStream_t st) {
     const int64_t n = b->n, k = s->k;
     const int A = b->L + n_cat;
     if (stats) *stats = geek_assign_stats{0.0, 0.0, k, 0};
@@ -354,9 +393,40 @@ geek_status assign_hetero(geek_ctx *ctx, Scratch &scr, const geek_buckets *b, co
     GK_TRY(scr.alloc(&attrs, (size_t)n * A));
     GK_TRY(scr.alloc(&modes, (size_t)std::max<int64_t>(k, 1) * A));
     GK_TRY(scr.alloc(&matches, n));
+    int32_t *rep = nullptr;
+    if (keep && k) GK_TRY(scr.alloc(&rep, (size_t)k * A));
     GK_COUNT();
     k_build_attrs<<<G(ctx, n * A), 256, 0, st>>>(n, b->L, n_cat, b->num_key, tok, attrs);
-    if (k) GK_COUNT(), k_modes<<<G(ctx, k * A), 256, 0, st>>>(k, A, s->off, s->ids, attrs, modes);
+    if (k) GK_COUNT(), k_modes<<<G(ctx, k * A), 256, 0, st>>>(k, A, s->off, s->ids, attrs, modes, rep);
+    GK_LAUNCH(ctx);
+    if (keep) {
+        keep->kind = GEEK_HETERO;
+        keep->k = k;
+        keep->n_attr = A;
+        GK_TRY(own_alloc(ctx, (void **)&keep->modes, sizeof(int64_t) * (size_t)std::max<int64_t>(k, 1) * A, st));
+        if (k) {
+            int64_t *flags, *excl, *tbase;
+            GK_TRY(scr.alloc(&flags, std::max<int64_t>(b->NB, 1)));
+            GK_TRY(scr.alloc(&excl, std::max<int64_t>(b->NB, 1)));
+            GK_TRY(scr.alloc(&tbase, b->L));
+            std::vector<int64_t> hb(b->L, 0);
+            for (int l = 1; l < b->L; l++) hb[l] = hb[l - 1] + b->nb[l - 1];
+            GK_CUDA(ctx, cudaMemcpyAsync(tbase, hb.data(), sizeof(int64_t) * b->L, cudaMemcpyHostToDevice, st));
+            for (int l = 0; l < b->L; l++) {
+                GK_COUNT();
+                k_num_run_flags<<<G(ctx, b->nb[l]), 256, 0, st>>>(b->nb[l], hb[l], b->boff, b->members,
+                                                                 b->num_key + (int64_t)l * n, flags);
+            }
+            GK_LAUNCH(ctx);
+            GK_TRY(exclusive_scan_i64(ctx, scr, flags, excl, b->NB, nullptr, st));
+            GK_COUNT();
+            k_mode_out<<<G(ctx, k * A), 256, 0, st>>>(k, A, b->L, n, modes, rep, b->obj_bucket, tbase, excl,
+                                                      keep->modes);
+            GK_LAUNCH(ctx);
+            // the host vector hb must outlive the copy above
+            GK_CUDA(ctx, cudaStreamSynchronize(st));
+        }
+    }
     GK_COUNT();
     k_assign_cat<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(n, A, k, attrs, modes, labels, matches);
     GK_LAUNCH(ctx);
@@ -379,18 +449,34 @@ geek_status assign_hetero(geek_ctx *ctx, Scratch &scr, const geek_buckets *b, co
 }
 
 geek_status assign_sets(geek_ctx *ctx, Scratch &scr, const int64_t *off, const uint32_t *items, int64_t n,
-                        const silk_seeds *s, int32_t *labels, geek_assign_stats *stats, cudaStream_t st) {
+                        const silk_seeds *s, int32_t *labels, geek_assign_stats *stats, geek_centres *keep,
+                        cudaStream_t st) {
     const int64_t k = s->k;
     if (stats) *stats = geek_assign_stats{0.0, 0.0, k, 0};
-    if (n == 0) return GEEK_OK;
-    if (k == 0) {
-        GK_CUDA(ctx, cudaMemsetAsync(labels, 0xFF, sizeof(int32_t) * n, st));
+    if (keep) {
+        keep->kind = GEEK_SETS;
+        keep->k = k;
+    }
+    if (n == 0 || k == 0) {
+        if (keep) {
+            GK_TRY(own_alloc(ctx, (void **)&keep->item_off, sizeof(int64_t) * (size_t)(k + 1), st));
+            GK_CUDA(ctx, cudaMemsetAsync(keep->item_off, 0, sizeof(int64_t) * (size_t)(k + 1), st));
+        }
+        if (n && k == 0) GK_CUDA(ctx, cudaMemsetAsync(labels, 0xFF, sizeof(int32_t) * n, st));
         return GEEK_OK;
     }
     // centres: majority item sets of the seeds
     int64_t *coff, nci = 0;
     uint32_t *citems;
     GK_TRY(majority_per_group(ctx, scr, k, s->off, s->ids, s->n_ids, off, items, &coff, &citems, &nci, st));
+    if (keep) {
+        keep->n_items = nci;
+        GK_TRY(own_alloc(ctx, (void **)&keep->item_off, sizeof(int64_t) * (size_t)(k + 1), st));
+        GK_TRY(own_alloc(ctx, (void **)&keep->items, sizeof(uint32_t) * (size_t)std::max<int64_t>(nci, 1), st));
+        GK_CUDA(ctx, cudaMemcpyAsync(keep->item_off, coff, sizeof(int64_t) * (size_t)(k + 1), cudaMemcpyDeviceToDevice, st));
+        if (nci)
+            GK_CUDA(ctx, cudaMemcpyAsync(keep->items, citems, sizeof(uint32_t) * (size_t)nci, cudaMemcpyDeviceToDevice, st));
+    }
     // inverted index item -> centres: pairs sorted by (item, centre), runs of
     // equal items; the HEAVY longest posting lists become bitmask items
     uint64_t *pairs, *ikey;

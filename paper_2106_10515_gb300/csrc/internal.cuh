@@ -303,9 +303,25 @@ geek_status refine_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ld
                          cudaStream_t st);
 geek_status centroids_from_seeds(geek_ctx *ctx, const float *x, int64_t ldx, int d,
                                  const silk_seeds *s, double *centres, cudaStream_t st);
+// Library-owned central vectors of one assignment (geek_assign_ex).
+struct geek_centres {
+    geek_ctx *ctx = nullptr;
+    cudaStream_t st = nullptr;     // stream of creation (allocations and frees)
+    int kind = 0;
+    int64_t k = 0;
+    int d = 0, n_attr = 0;
+    int64_t n_items = 0;
+    double *centers = nullptr;     // DENSE: k x d
+    int64_t *modes = nullptr;      // HETERO: k x n_attr
+    int64_t *item_off = nullptr;   // SETS: k + 1
+    uint32_t *items = nullptr;     // SETS: n_items
+};
+// Stream-ordered allocation of a result handle's buffer (NOMEM on failure).
+geek_status own_alloc(geek_ctx *ctx, void **p, size_t bytes, cudaStream_t st);
+// keep (nullable): receives the central vectors the assignment used.
 geek_status assign_hetero(geek_ctx *ctx, Scratch &scr, const geek_buckets *b, const uint32_t *tok,
                           int n_cat, const silk_seeds *s, int32_t *labels, geek_assign_stats *stats,
-                          cudaStream_t st);
+                          geek_centres *keep, cudaStream_t st);
 geek_status assign_sets(geek_ctx *ctx, Scratch &scr, const int64_t *off, const uint32_t *items,
                         int64_t n, const silk_seeds *s, int32_t *labels, geek_assign_stats *stats,
-                        cudaStream_t st);
+                        geek_centres *keep, cudaStream_t st);

@@ -59,6 +59,11 @@ class geek_assign_params(C.Structure):
     _fields_ = [("precision", C.c_int32)]
 
 
+class geek_centres_info(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("d", C.c_int32), ("n_attr", C.c_int32), ("k", C.c_int64),
+                ("n_items", C.c_int64)]
+
+
 class geek_assign_stats(C.Structure):
     _fields_ = [("sse", C.c_double), ("radius_max", C.c_double), ("k", C.c_int64),
                 ("n_recheck_rows", C.c_int64), ("n_fp64_rows", C.c_int64)]
@@ -90,7 +95,8 @@ EXPORTS = ["geek_ctx_create", "geek_ctx_destroy", "geek_last_error", "geek_versi
            "geek_launch_count", "geek_assign_centers_noalloc", "geek_batch_create", "geek_batch_run",
            "geek_batch_info_get", "geek_batch_instance_stats", "geek_batch_copy_out", "geek_batch_seed_ids_count",
            "geek_batch_destroy", "geek_data_upload", "geek_resident_free", "geek_refine",
-           "geek_ctx_set_option"]
+           "geek_ctx_set_option", "geek_assign_ex", "geek_centres_info_get", "geek_centres_copy_out",
+           "geek_centres_free"]
 
 _lib = None
 
@@ -122,6 +128,11 @@ def lib():
     L.geek_assign_centers.argtypes = [P, C.POINTER(geek_data), P, C.c_int64,
                                       C.POINTER(geek_assign_params), P, C.POINTER(geek_assign_stats), P]
     L.geek_ctx_set_option.argtypes = [P, C.c_int32, C.c_int64]
+    L.geek_assign_ex.argtypes = [P, C.POINTER(geek_data), P, P, C.POINTER(geek_assign_params), P,
+                                 C.POINTER(geek_assign_stats), C.POINTER(P), P]
+    L.geek_centres_info_get.argtypes = [P, C.POINTER(geek_centres_info)]
+    L.geek_centres_copy_out.argtypes = [P, P, P, P, P, P]
+    L.geek_centres_free.argtypes = [P]
     L.geek_timing_enable.argtypes = [P, C.c_int]
     L.geek_timing_reset.argtypes = [P]
     L.geek_timing_get.argtypes = [P, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64),
@@ -372,6 +383,37 @@ class Context:
                                     seeds.h, C.byref(p), _ptr(labels), _ptr(centers),
                                     C.byref(s) if stats else None, _stream()))
         return s
+
+    def assign_ex(self, data, buckets, seeds, labels, precision=PREC_FP32):
+        """geek_assign_ex: labels, stats and the central vectors used, as a
+        dict of CUDA tensors ("centers" k x d, or "modes" k x n_attr, or
+        "item_off" / "items")."""
+        p = geek_assign_params()
+        p.precision = precision
+        s = geek_assign_stats()
+        h = C.c_void_p()
+        self._chk(lib().geek_assign_ex(self.h, C.byref(data.c), buckets.h if buckets is not None else None,
+                                       seeds.h, C.byref(p), _ptr(labels), C.byref(s), C.byref(h), _stream()))
+        try:
+            info = geek_centres_info()
+            self._chk(lib().geek_centres_info_get(h, C.byref(info)))
+            out = {"kind": info.kind, "k": info.k}
+            cen = mod = off = items = None
+            if info.kind == DENSE:
+                cen = torch.empty((info.k, info.d), dtype=torch.float64, device="cuda")
+                out["centers"] = cen
+            elif info.kind == HETERO:
+                mod = torch.empty((info.k, info.n_attr), dtype=torch.int64, device="cuda")
+                out["modes"] = mod
+            else:
+                off = torch.empty(info.k + 1, dtype=torch.int64, device="cuda")
+                items = torch.empty(max(info.n_items, 1), dtype=torch.int32, device="cuda")
+                out["item_off"], out["items"] = off, items[: info.n_items]
+            self._chk(lib().geek_centres_copy_out(h, _ptr(cen), _ptr(mod), _ptr(off), _ptr(items), _stream()))
+            torch.cuda.synchronize()
+        finally:
+            lib().geek_centres_free(h)
+        return s, out
 
     def refine(self, data, centers, labels, passes, precision=PREC_FP32, stats=True):
         """Sect. 5's extra passes of assignment: centers (k x d float64) and

@@ -271,13 +271,14 @@ def make(cfg: Config):
 # ---------------------------------------------------------------------------
 def batch_instances(count: int = 256, n_range=(10_000, 500_000), d_choices=(32, 64, 128),
                     comp_range=(10, 2000), seed: int = ROOT_SEED + 5, n_scale: float = 1.0,
-                    threads: int = 1):
+                    threads: int = 1, only=None):
     """``count`` dense instances, n = floor(exp(U[ln 1e4, ln 5e5])) (times
     ``n_scale`` for parity cases), d uniform over {32, 64, 128}, components
     U{10..2000}, centres U[-10,10]^d, sigma = 1, equal weights, E2LSH K=4,
     L=8, w=4 and SILK thresholds as for the small dense workload.  Every
     instance draws from its own stream, so ``threads`` (parallel generation)
-    does not change the values."""
+    does not change the values, and ``only`` (a list of instance indices)
+    returns just those instances, with the same values."""
     rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence(seed)))
     lo, hi = n_range
     ns = np.floor(np.exp(rng.uniform(math.log(lo), math.log(hi), count))).astype(np.int64)
@@ -295,8 +296,9 @@ def batch_instances(count: int = 256, n_range=(10_000, 500_000), d_choices=(32, 
         return dict(cfg=cfg, x=x, labels=lab, centres=centres, a=a, b=b,
                     w=float(cfg.w), silk=silk_params(cfg, rsilk))
 
+    idx = list(range(count)) if only is None else [int(i) for i in only]
     if threads <= 1:
-        return [one(i) for i in range(count)]
+        return [one(i) for i in idx]
     from concurrent.futures import ThreadPoolExecutor
     with ThreadPoolExecutor(threads) as ex:
-        return list(ex.map(one, range(count)))
+        return list(ex.map(one, idx))

@@ -202,9 +202,26 @@ def test_sets_c3_shape_pipeline(G, ctx, over):
     assert seeds.sets() == ref["seeds"].sets()
     assert seeds.k > 0
     labels = torch.empty(cfg.n, dtype=torch.int32, device="cuda")
-    ctx.assign(data, bk, seeds, labels)
-    torch.cuda.synchronize()
+    _, cen = ctx.assign_ex(data, bk, seeds, labels)
     assert np.array_equal(labels.cpu().numpy(), ref["labels"])
+    check_sparse_centres(cen, ref)
+
+
+def check_sparse_centres(cen, ref):
+    """Majority item sets of the seeds (Sect. 3.3), element by element."""
+    assert np.array_equal(cen["item_off"].cpu().numpy(), ref["centre_off"])
+    assert np.array_equal(cen["items"].cpu().numpy().view(np.uint32), ref["centre_items"])
+
+
+def check_modes(cen, ref, wl):
+    """Per-attribute modes (Sect. 3.3): numeric attributes as canonical
+    ranks, categorical ones as tokens (= offset of the attribute + value)."""
+    tok_off = (wl["tokens"][0].astype(np.int64) - wl["cat"][0].astype(np.int64))
+    L = ref["attrs"].shape[1] - tok_off.size
+    m = cen["modes"].cpu().numpy()
+    assert m.shape == ref["modes"].shape
+    assert np.array_equal(m[:, :L], ref["modes"][:, :L])
+    assert np.array_equal(m[:, L:] - tok_off[None, :], ref["modes"][:, L:])
 
 
 @pytest.mark.parametrize("over", [dict(n=20_000, n_comp=100), dict(n=777, n_comp=20, silk=dict(delta=1))])
@@ -223,9 +240,10 @@ def test_hetero_c4_shape_pipeline(G, ctx, over):
     seeds = ctx.silk(bk, **G.silk_args(wl["silk"]))
     assert seeds.sets() == ref["seeds"].sets()
     labels = torch.empty(cfg.n, dtype=torch.int32, device="cuda")
-    ctx.assign(data, bk, seeds, labels)
-    torch.cuda.synchronize()
+    _, cen = ctx.assign_ex(data, bk, seeds, labels)
     assert np.array_equal(labels.cpu().numpy(), ref["labels"])
+    if seeds.k:
+        check_modes(cen, ref, wl)
 
 
 # ------------------------------------------- Alg. 1 (QALSH, even split) --
