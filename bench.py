@@ -31,7 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 TIMED = ["hash", "silk", "assign", "hash.sort", "silk.vbuckets", "silk.bins", "silk.vote", "silk.dedup",
-         "kernel.project_fp32", "kernel.recheck_dot2", "kernel.recheck_fp64",
+         "kernel.project_fp32", "kernel.project_tc", "kernel.recheck_dot2", "kernel.recheck_fp64",
          "kernel.rs_scatter", "kernel.assign_tc", "kernel.assign_fp32", "kernel.assign_recheck"]
 METRIC = "points/sec hash+assign (n=10M,d=128) mixed vs plain FP32; TC util/HBM GB/s"
 UNIT = "points/s"
@@ -198,8 +198,13 @@ def run_ours(args):
 
     info = {}
 
+    def hprec(p):
+        # the mixed form projects on the tensor cores too; the plain form is
+        # FP32 SIMT throughout
+        return geek.PREC_FP32 if p == geek.PREC_FP32 else geek.PREC_BF16X3
+
     def step(p):
-        bk = ctx.hash(data, cfg.K, cfg.L, a=a, b=b, w=wl["w"])
+        bk = ctx.hash(data, cfg.K, cfg.L, a=a, b=b, w=wl["w"], precision=hprec(p))
         seeds = ctx.silk(bk, **silk)
         st = ctx.assign_centers(data, centres, labels, precision=p)
         info.update(k_star=seeds.k, n_multiset=seeds.n_multiset, n_buckets=bk.n_buckets,
@@ -253,7 +258,7 @@ def run_ours(args):
         def step_host():
             dv = res.upload(hdata)
             cdev.copy_(ch, non_blocking=True)
-            bk = ctx.hash(dv, cfg.K, cfg.L, a=a, b=b, w=wl["w"])
+            bk = ctx.hash(dv, cfg.K, cfg.L, a=a, b=b, w=wl["w"], precision=hprec(prec))
             seeds = ctx.silk(bk, **silk)
             ctx.assign_centers(dv, cdev, labels, precision=prec)
             lh.copy_(labels, non_blocking=True)
@@ -291,6 +296,7 @@ def run_ours(args):
     bounds = {"kernel.assign_tc": ("tensor", 1e12, "TFLOP/s", pk["bf16_tflops"], f"{pk_kind} bf16_tflops (burst)"),
               "kernel.assign_fp32": ("alu", 1e12, "TFLOP/s", FP32_SIMT_TFLOPS, FP32_NOTE),
               "kernel.project_fp32": ("alu", 1e12, "TFLOP/s", FP32_SIMT_TFLOPS, FP32_NOTE),
+              "kernel.project_tc": ("hbm", 1e9, "GB/s", pk["hbm_gbs"], f"{pk_kind} hbm_gbs"),
               "kernel.rs_scatter": ("hbm", 1e9, "GB/s", pk["hbm_gbs"], f"{pk_kind} hbm_gbs")}
     roofs = {}
     for kname, (tot_ms, cnt, work) in tm.items():
@@ -322,8 +328,8 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 inputs; " + ("bf16 tensor-core assign + fp64 recheck" if prec == geek.PREC_BF16
-                                   else "fp32 SIMT assign + fp64 recheck"),
+        "dtype": "f32 inputs; " + ("split-bf16 tensor-core projection, bf16 tensor-core assign, fp64 rechecks"
+                                   if prec == geek.PREC_BF16 else "fp32 SIMT projection and assign, fp64 rechecks"),
         "data": "synthetic (Sift10M-shaped Gaussian mixture, seeded)",
         "config": {"workload": f"dense n={cfg.n} d={cfg.d}, {cfg.n_comp} Zipf-weighted Gaussians; "
                                f"E2LSH K={cfg.K} L={cfg.L} w={cfg.w}; SILK Ks={wl['silk']['Ks']} "

@@ -88,8 +88,8 @@ geek_status hash_impl(geek_ctx *ctx, const geek_data *data, const geek_hash_para
         return set_error(ctx, GEEK_ERR_INVALID, "MinHash coefficients missing");
     if (p->doph_bins != 0 && (kind != GEEK_SETS || p->doph_bins < 0 || p->doph_bins > 1024))
         return set_error(ctx, GEEK_ERR_INVALID, "DOPH: sets only, 1 <= bins <= 1024");
-    if (p->precision != GEEK_PREC_FP32)
-        return set_error(ctx, GEEK_ERR_UNSUPPORTED, "projection precision other than FP32");
+    if (p->precision != GEEK_PREC_FP32 && p->precision != GEEK_PREC_BF16X3)
+        return set_error(ctx, GEEK_ERR_UNSUPPORTED, "projection precision other than FP32 or BF16X3");
     const bool host = data->mem == GEEK_MEM_HOST;
 
     Scratch scr(ctx, st);
@@ -138,7 +138,7 @@ geek_status hash_impl(geek_ctx *ctx, const geek_data *data, const geek_hash_para
         GK_TRY(stage(ctx, scr, data->x, (size_t)n * data->ldx, host, &x, st));
         GK_TRY(project_dense(ctx, scr, x, data->ldx, n, data->d, p->a, p->b, F1, p->w,
                              p->proj == GEEK_PROJ_SRP, b->codes, fmin, fmax, &b->n_flagged,
-                             &b->n_flagged_fp64, st));
+                             &b->n_flagged_fp64, st, p->precision));
     }
     if (kind == GEEK_SETS) {
         const int64_t *off;

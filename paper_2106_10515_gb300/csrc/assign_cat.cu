@@ -71,13 +71,14 @@ __global__ void k_num_run_flags(int64_t nb, int64_t base, const int64_t *__restr
 __global__ void k_mode_out(int64_t k, int A, int L, int64_t n, const uint64_t *__restrict__ modes,
                            const int32_t *__restrict__ rep, const int32_t *__restrict__ obj_bucket,
                            const int64_t *__restrict__ tbase, const int64_t *__restrict__ excl,
-                           int64_t *__restrict__ out) {
+                           const int64_t *__restrict__ flags, int64_t *__restrict__ out) {
     const int64_t total = k * A;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int a = (int)(e % A);
         if (a < L) {
+            // runs started at or before g, less the one at the table's start
             const int64_t g = tbase[a] + obj_bucket[(int64_t)a * n + rep[e]];
-            out[e] = excl[g] - excl[tbase[a]];
+            out[e] = excl[g] + flags[g] - 1 - excl[tbase[a]];
         } else {
             out[e] = (int64_t)modes[e];
         }
@@ -420,7 +421,7 @@ geek_status assign_hetero(geek_ctx *ctx, Scratch &scr, const geek_buckets *b, co
             GK_LAUNCH(ctx);
             GK_TRY(exclusive_scan_i64(ctx, scr, flags, excl, b->NB, nullptr, st));
             GK_COUNT();
-            k_mode_out<<<G(ctx, k * A), 256, 0, st>>>(k, A, b->L, n, modes, rep, b->obj_bucket, tbase, excl,
+            k_mode_out<<<G(ctx, k * A), 256, 0, st>>>(k, A, b->L, n, modes, rep, b->obj_bucket, tbase, excl, flags,
                                                       keep->modes);
             GK_LAUNCH(ctx);
             // the host vector hb must outlive the copy above

@@ -650,7 +650,7 @@ static size_t proj_smem(const ProjArgs &A) { return 2 * (size_t)PJ_KC * (proj_ro
 geek_status project_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ldx, int64_t n,
                           int d, const float *a, const float *b, int F, double w, int srp,
                           int32_t *codes, int *fmin, int *fmax, int64_t *n_flagged,
-                          int64_t *n_flagged_fp64, cudaStream_t st) {
+                          int64_t *n_flagged_fp64, cudaStream_t st, int precision) {
     *n_flagged_fp64 = 0;
     if (F > 512) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "more than 512 projections");
     if (d > 100000) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "d > 100000");
@@ -685,8 +685,10 @@ geek_status project_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t l
     unsigned long long *cnt;
     GK_TRY(scr.alloc(&cnt, 1));
     int *status;
-    GK_TRY(scr.alloc(&status, 1));
-    GK_CUDA(ctx, cudaMemsetAsync(status, 0, sizeof(int), st));
+    GK_TRY(scr.alloc(&status, 2));
+    GK_CUDA(ctx, cudaMemsetAsync(status, 0, 2 * sizeof(int), st));
+    int *tc_err = status + 1;  // bounded waits of the tensor-core kernel
+    bool use_tc = precision == GEEK_PREC_BF16X3 && proj_tc_eligible(x, ldx, d, F);
     int64_t *row_off;
     ProjArgs *P;
     GK_TRY(scr.alloc(&row_off, 2));
@@ -701,7 +703,14 @@ geek_status project_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t l
         A.flags = flags; A.n_flags = cnt; A.flag_cap = cap;
         GK_CUDA(ctx, cudaMemcpyAsync(P, &A, sizeof A, cudaMemcpyHostToDevice, st));
         const int64_t blocks = ceil_div(n, TR);
-        {
+        if (use_tc) {
+            EvTimer tk(ctx, "kernel.project_tc", st);
+            tk.work = (double)n * (4.0 * d + 4.0 * F);  // algorithmic bytes: x read, codes written
+            const geek_status ts = proj_tc_launch(ctx, scr, A, tc_err, st);
+            if (ts == GEEK_ERR_UNSUPPORTED) use_tc = false;  // no tensor map for this layout
+            else GK_TRY(ts);
+        }
+        if (!use_tc) {
             EvTimer tk(ctx, "kernel.project_fp32", st);
             tk.work = 2.0 * (double)n * (double)F * (double)d;
             GK_COUNT();
@@ -711,6 +720,12 @@ geek_status project_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t l
         unsigned long long h_cnt = 0;
         GK_CUDA(ctx, cudaMemcpyAsync(&h_cnt, cnt, sizeof h_cnt, cudaMemcpyDeviceToHost, st));
         GK_CUDA(ctx, cudaStreamSynchronize(st));
+        if (use_tc) {
+            int h_err = 0;
+            GK_CUDA(ctx, cudaMemcpyAsync(&h_err, tc_err, sizeof h_err, cudaMemcpyDeviceToHost, st));
+            GK_CUDA(ctx, cudaStreamSynchronize(st));
+            if (h_err) return set_error(ctx, (geek_status)h_err, "tensor-core projection: a bounded wait expired");
+        }
         if ((int64_t)h_cnt > cap) {  // list overflowed: rerun with the exact size
             cap = (int64_t)h_cnt;
             continue;
@@ -740,10 +755,11 @@ geek_status project_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t l
             tk.work = 2.0 * (double)h2 * (double)d;
             *n_flagged_fp64 = (int64_t)h2;
         }
-        int h_status = 0;
-        GK_CUDA(ctx, cudaMemcpyAsync(&h_status, status, sizeof h_status, cudaMemcpyDeviceToHost, st));
+        int h_status[2] = {0, 0};
+        GK_CUDA(ctx, cudaMemcpyAsync(h_status, status, sizeof h_status, cudaMemcpyDeviceToHost, st));
         GK_CUDA(ctx, cudaStreamSynchronize(st));
-        if (h_status) return set_error(ctx, (geek_status)h_status, "E2LSH code outside int32");
+        if (h_status[1]) return set_error(ctx, (geek_status)h_status[1], "tensor-core projection: a bounded wait expired");
+        if (h_status[0]) return set_error(ctx, (geek_status)h_status[0], "E2LSH code outside int32");
         return GEEK_OK;
     }
     return set_error(ctx, GEEK_ERR_CUDA, "projection flag list did not converge");

@@ -90,10 +90,17 @@ geek_status pack_keys_batch(geek_ctx *ctx, int64_t N, int L, const int32_t *code
                             cudaStream_t st);
 
 // hash.cu
+// precision GEEK_PREC_FP32: FP32 SIMT projection; GEEK_PREC_BF16X3: the
+// three-term split BF16 tcgen05 projection (proj_tc.cu) where eligible.
 geek_status project_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ldx, int64_t n,
                           int d, const float *a, const float *b, int F, double w, int srp,
                           int32_t *codes, int *fmin, int *fmax, int64_t *n_flagged,
-                          int64_t *n_flagged_fp64, cudaStream_t st);
+                          int64_t *n_flagged_fp64, cudaStream_t st, int precision = GEEK_PREC_FP32);
+// proj_tc.cu: shapes the tensor-core projection takes (d <= 128, F <= 128,
+// 16-byte aligned rows), and one launch of it with the arguments of the
+// FP32 kernel (codes, min / max, flag list); err: device word for timeouts.
+bool proj_tc_eligible(const float *x, int64_t ldx, int d, int F);
+geek_status proj_tc_launch(geek_ctx *ctx, Scratch &scr, const ProjArgs &P, int *err, cudaStream_t st);
 // MinHash of fixed rows of 64-bit tokens (a DOPH reduction): out n x F.
 geek_status minhash_rows64(geek_ctx *ctx, int64_t n, int row_len, const uint64_t *tokens, int F, const uint64_t *A,
                            const uint64_t *B, uint32_t *out, cudaStream_t st);

@@ -1,9 +1,10 @@
 """Full-size parity at every workload's stated size, against the oracle.
 
 * 10M x 128 dense points, in the configuration bench.py times (E2LSH K=6,
-  L=16, w=4; SILK Ks=3, Ls=10, delta=10; assignment to the 20,000 planted
-  centres in both fast precisions): every code, every canonical bucket id,
-  the SILK seed set, and the labels of 4,096 sampled points.
+  L=16, w=4 on the tensor cores, and on the FP32 path; SILK Ks=3, Ls=10,
+  delta=10; assignment to the 20,000 planted centres in both fast
+  precisions): every code, every canonical bucket id, the SILK seed set,
+  and the labels of 4,096 sampled points.
 * 2M sparse sets (MinHash K=4, L=32; Jaccard assignment): every MinHash
   value, every bucket id, the seed list, every majority-item centre, and
   4,096 sampled labels.
@@ -34,8 +35,12 @@ def test_c2_full_size():
     ctx = geek.Context(0)
     x = geek._dev(wl["x"])
     data = ctx.dense(x)
-    bk = ctx.hash(data, cfg.K, cfg.L, a=geek._dev(wl["a"]), b=geek._dev(wl["b"]), w=wl["w"])
+    bk = ctx.hash(data, cfg.K, cfg.L, a=geek._dev(wl["a"]), b=geek._dev(wl["b"]), w=wl["w"],
+                  precision=geek.PREC_BF16X3)
     seeds = ctx.silk(bk, **geek.silk_args(wl["silk"]))
+    bk32 = ctx.hash(data, cfg.K, cfg.L, a=geek._dev(wl["a"]), b=geek._dev(wl["b"]), w=wl["w"])
+    g_codes32 = bk32.copy_out()["codes"].cpu().numpy()
+    del bk32
     centres = wl["centres"].astype(np.float64)
     labs = {}
     for prec in (geek.PREC_BF16, geek.PREC_FP32):
@@ -50,8 +55,9 @@ def test_c2_full_size():
     torch.cuda.empty_cache()
 
     codes = oracle.e2lsh(wl["x"], wl["a"], wl["b"], wl["w"])
-    assert np.array_equal(g_codes, codes)
-    del g_codes
+    assert np.array_equal(g_codes, codes)        # tcgen05 projection
+    assert np.array_equal(g_codes32, codes)      # FP32 SIMT projection
+    del g_codes, g_codes32
     ref = oracle.group(oracle.table_keys(codes, cfg.L, cfg.K))
     assert np.array_equal(g_ob, ref.obj_bucket)
     del g_ob
