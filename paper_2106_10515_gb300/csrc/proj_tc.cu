@@ -26,14 +26,15 @@
 // instruction's terms with at most a few units of 2^-23 of their magnitude
 // lost), taken with a factor of two beyond that.
 //
-// Persistent kernel, one CTA per SM, 14 warps:
+// Persistent kernel, one CTA per SM, 22 warps:
 //   warp 0      TMA producer: the split image of A once (bulk copy), then X
 //               in FP32 boxes of 128 rows x 32 columns (3-stage ring)
 //   warp 1      MMA issuer: per k-step six tcgen05.mma (M = 128, N = F
 //               padded to 32) into P and Q, double-buffered in TMEM
-//   warps 2-5   epilogue: tcgen05.ld of P and Q, the cell test, codes, the
+//   warps 2-13  epilogue, three per TMEM lane quarter over 16-column groups:
+//               tcgen05.ld of P and Q, the cell test, codes, the
 //               per-function min / max, the flag list
-//   warps 6-13  converters: FP32 box -> three BF16 parts in the 128-byte
+//   warps 14-21 converters: FP32 box -> three BF16 parts in the 128-byte
 //               swizzled K-major layout (2-stage ring), and |x|^2 per row
 // Every mbarrier wait is bounded (2 s): on expiry the kernel records
 // GEEK_ERR_TIMEOUT, stops issuing, drains its own copies and MMAs, frees its
@@ -58,7 +59,8 @@ constexpr int PT_SPLIT_STAGES = 2;
 constexpr int PT_NMAX = 128;                       // functions (padded) per launch
 constexpr int PT_A_MAX = 3 * 96 * 2 * 128;         // image of A: 3 parts x N x nkb x 128 B (N * nkb <= 192)
 constexpr int PT_CONV_WARPS = 8;
-constexpr int PT_EPI_WARPS = 4;
+constexpr int PT_EPI_PER_Q = 3;                    // epilogue warps per TMEM lane quarter
+constexpr int PT_EPI_WARPS = 4 * PT_EPI_PER_Q;
 constexpr int PT_THREADS = 32 * (2 + PT_EPI_WARPS + PT_CONV_WARPS);
 constexpr uint32_t PT_TMEM_COLS = 512;             // 2 buffers x (P, Q) x 128 columns
 constexpr int PT_OFF_SPLIT = PT_A_MAX;
@@ -108,8 +110,18 @@ __device__ __forceinline__ void split3(float v, __nv_bfloat16 &h1, __nv_bfloat16
     h3 = __float2bfloat16_rn(r2);
 }
 
-__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+// the same split for two neighbouring columns, packed as BF16 pairs (the
+// first column in the low half, as it sits at the lower address)
+__device__ __forceinline__ void split3x2(float2 v, uint32_t &w1, uint32_t &w2, uint32_t &w3) {
+    const __nv_bfloat162 h1 = __floats2bfloat162_rn(v.x, v.y);
+    const float2 f1 = __bfloat1622float2(h1);
+    const float2 r1 = make_float2(v.x - f1.x, v.y - f1.y);  // exact
+    const __nv_bfloat162 h2 = __floats2bfloat162_rn(r1.x, r1.y);
+    const float2 f2 = __bfloat1622float2(h2);
+    const __nv_bfloat162 h3 = __floats2bfloat162_rn(r1.x - f2.x, r1.y - f2.y);  // differences exact
+    w1 = *reinterpret_cast<const uint32_t *>(&h1);
+    w2 = *reinterpret_cast<const uint32_t *>(&h2);
+    w3 = *reinterpret_cast<const uint32_t *>(&h3);
 }
 
 // lane 0 waits; __syncwarp then orders the other lanes' reads after its
@@ -245,9 +257,13 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_project_tc(const __grid_const
         __syncwarp();
     } else if (warp < 2 + PT_EPI_WARPS) {
         // ------------------------------------------------------ epilogue
+        // PT_EPI_PER_Q warps share a TMEM lane quarter; warp e of a quarter
+        // takes the 16-column groups e, e + PT_EPI_PER_Q, ...
+        const int ew = warp - 2;
         const int q = warp & 3;  // TMEM lane quarter
+        const int e = ew >> 2;   // column groups of this warp
         const int rloc = 32 * q + lane;
-        const int nch = A.N / 32;
+        const int ngrp = A.N / 16;
         bool ok = true;
         int64_t it = 0;
         for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, it++) {
@@ -261,18 +277,17 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_project_tc(const __grid_const
             const float xn = sqrtf(rownorm[buf * PT_M + rloc]) * (1.f + 1e-4f);
             __syncwarp();
             if (lane == 0) mbar_arrive(&nrm_empty[buf]);
-            for (int ch = 0; ch < nch; ch++) {
-                uint32_t rp[32], rq[32];
-                const uint32_t tb = tmem + (uint32_t)(buf * 256 + ch * 32) + ((uint32_t)(32 * q) << 16);
-                tmem_ld32_async(tb, rp);
-                tmem_ld32_async(tb + 128, rq);
+            for (int gi = e; gi < ngrp; gi += PT_EPI_PER_Q) {
+                uint32_t rp[16], rq[16];
+                const uint32_t tb = tmem + (uint32_t)(buf * 256 + gi * 16) + ((uint32_t)(32 * q) << 16);
+                tmem_ld16_async(tb, rp);
+                tmem_ld16_async(tb + 128, rq);
                 tmem_wait_ld();
-                int32_t out[32];
                 uint32_t flagged = 0;
                 int lmin = INT32_MAX, lmax = INT32_MIN;
 #pragma unroll
-                for (int j = 0; j < 32; j++) {
-                    const int f = ch * 32 + j;
+                for (int j = 0; j < 16; j++) {
+                    const int f = gi * 16 + j;
                     const bool fv = live && f < A.F;
                     const float p = __uint_as_float(rp[j]) + __uint_as_float(rq[j]);
                     const float E = A.coef * s_an[f] * xn + 1e-30f;
@@ -290,7 +305,7 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_project_tc(const __grid_const
                         code = fabsf(tt) < 2.0e9f ? (int)c0 : 0;
                         sure = (tt - Et >= c0) && (tt + Et < c0 + 1.f) && fabsf(tt) < 2.0e9f;
                     }
-                    out[j] = code;
+                    rp[j] = (uint32_t)code;  // the codes replace P in place
                     if (fv && !sure) flagged |= 1u << j;
                     const int mn = __reduce_min_sync(0xffffffffu, fv ? code : INT32_MAX);
                     const int mx = __reduce_max_sync(0xffffffffu, fv ? code : INT32_MIN);
@@ -299,24 +314,25 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_project_tc(const __grid_const
                         lmax = mx;
                     }
                 }
-                if (ch * 32 + lane < A.F && lmin <= lmax) {
-                    atomicMin(&s_min[ch * 32 + lane], lmin);
-                    atomicMax(&s_max[ch * 32 + lane], lmax);
+                if (lane < 16 && gi * 16 + lane < A.F && lmin <= lmax) {
+                    atomicMin(&s_min[gi * 16 + lane], lmin);
+                    atomicMax(&s_max[gi * 16 + lane], lmax);
                 }
                 if (live) {
-                    int32_t *dst = A.codes + row * A.F + ch * 32;
-                    const int cnt = min(32, A.F - ch * 32);
-                    if (cnt == 32 && (A.F & 3) == 0) {
+                    int32_t *dst = A.codes + row * A.F + gi * 16;
+                    const int cnt = min(16, A.F - gi * 16);
+                    if (cnt == 16 && (A.F & 3) == 0) {
 #pragma unroll
-                        for (int j = 0; j < 32; j += 4)
-                            *reinterpret_cast<int4 *>(dst + j) = make_int4(out[j], out[j + 1], out[j + 2], out[j + 3]);
+                        for (int j = 0; j < 16; j += 4)
+                            *reinterpret_cast<int4 *>(dst + j) =
+                                make_int4((int)rp[j], (int)rp[j + 1], (int)rp[j + 2], (int)rp[j + 3]);
                     } else {
 #pragma unroll
-                        for (int j = 0; j < 32; j++)
-                            if (j < cnt) dst[j] = out[j];
+                        for (int j = 0; j < 16; j++)
+                            if (j < cnt) dst[j] = (int)rp[j];
                     }
                 }
-                // flag list: one atomic per warp and chunk
+                // flag list: one atomic per warp and group
                 const unsigned nf = __popc(flagged);
                 unsigned incl = nf;
 #pragma unroll
@@ -325,15 +341,17 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_project_tc(const __grid_const
                     if (lane >= o) incl += y;
                 }
                 const unsigned tot = __shfl_sync(0xffffffffu, incl, 31);
-                unsigned long long pos = 0;
-                if (lane == 31 && tot) pos = atomicAdd(A.n_flags, (unsigned long long)tot);
-                pos = __shfl_sync(0xffffffffu, pos, 31) + (incl - nf);
-                while (flagged) {
-                    const int j = __ffs(flagged) - 1;
-                    flagged &= flagged - 1;
-                    if ((int64_t)pos < A.flag_cap)
-                        A.flags[pos] = ((uint64_t)(A.row_base + row) << 16) | (uint64_t)(ch * 32 + j);
-                    pos++;
+                if (tot) {
+                    unsigned long long pos = 0;
+                    if (lane == 31) pos = atomicAdd(A.n_flags, (unsigned long long)tot);
+                    pos = __shfl_sync(0xffffffffu, pos, 31) + (incl - nf);
+                    while (flagged) {
+                        const int j = __ffs(flagged) - 1;
+                        flagged &= flagged - 1;
+                        if ((int64_t)pos < A.flag_cap)
+                            A.flags[pos] = ((uint64_t)(A.row_base + row) << 16) | (uint64_t)(gi * 16 + j);
+                        pos++;
+                    }
                 }
             }
             fence_before();
@@ -367,13 +385,12 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_project_tc(const __grid_const
                     const int r = cw * 16 + (i & 3) + ((i >> 2) << 3) + ((lane >> 4) << 2);
                     const float2 v = *reinterpret_cast<const float2 *>(src + r * PT_BOX + c0);
                     xs[i] = fmaf(v.x, v.x, fmaf(v.y, v.y, xs[i]));
-                    __nv_bfloat16 p1, p2, p3, q1, q2, q3;
-                    split3(v.x, p1, p2, p3);
-                    split3(v.y, q1, q2, q3);
+                    uint32_t w1, w2, w3;
+                    split3x2(v, w1, w2, w3);
                     const uint32_t o = sw128(r, kc);
-                    *reinterpret_cast<uint32_t *>(dst + o) = pack2(p1, q1);
-                    *reinterpret_cast<uint32_t *>(dst + PT_PART + o) = pack2(p2, q2);
-                    *reinterpret_cast<uint32_t *>(dst + 2 * PT_PART + o) = pack2(p3, q3);
+                    *reinterpret_cast<uint32_t *>(dst + o) = w1;
+                    *reinterpret_cast<uint32_t *>(dst + PT_PART + o) = w2;
+                    *reinterpret_cast<uint32_t *>(dst + 2 * PT_PART + o) = w3;
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&f_empty[fs]);
