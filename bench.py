@@ -355,6 +355,7 @@ def run_ours(args):
     }
     if not args.skip_alg1:
         line["alg1_transform"] = bench_alg1(args, geek, ctx, data, wl, world)
+        line["alg1_pipeline"] = bench_alg1_pipeline(args, geek, ctx, data, wl, world, pk, pk_kind)
     if not args.skip_refine:
         line["refine_passes"] = bench_refine(args, geek, ctx, data, wl, world, prec)
     if not args.skip_doph:
@@ -412,6 +413,62 @@ def bench_alg1(args, geek, ctx, data, wl, world):
                         f"buckets each (paper grid m in {{20,40,60}}, t in [5k, 30k])",
             "value": cfg.n * world / (ms / 1e3), "unit": UNIT, "ms_per_run": ms, "n_buckets": int(nb),
             "phases_ms_per_run": {k: v[0] / args.steps for k, v in tm.items()}}
+
+
+def bench_alg1_pipeline(args, geek, ctx, data, wl, world, pk, pk_kind):
+    """The paper's own dense pipeline on the same resident points: Alg. 1
+    (m QALSH tables of t even buckets), SILK on those buckets, the FP64
+    centroids of its seeds and the one-pass BF16 tcgen05 assignment to them
+    (Sects. 3.1-3.3), so k* comes from SILK, not from the generator."""
+    import torch
+    import synth
+    cfg = wl["cfg"]
+    P = synth.ALG1
+    sp = synth.alg1_silk_params()
+    silk = geek.silk_args(sp)
+    a = geek._dev(np.ascontiguousarray(wl["a"][:P["m"]]))
+    labels = torch.empty(cfg.n, dtype=torch.int32, device="cuda")
+    info = {}
+
+    def run():
+        bk = ctx.hash(data, 1, P["m"], a=a, proj=geek.PROJ_QALSH, t=P["t"])
+        seeds = ctx.silk(bk, **silk)
+        st = ctx.assign(data, bk, seeds, labels, precision=geek.PREC_BF16, stats=True)
+        info.update(k_star=seeds.k, n_multiset=seeds.n_multiset, sse=st.sse, n_recheck_rows=st.n_recheck_rows,
+                    n_fp64_rows=st.n_fp64_rows)
+        del bk, seeds
+
+    for _ in range(max(1, args.warmup)):
+        run()
+    torch.cuda.synchronize()
+    ctx.timing_reset()
+    ctx.timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    ctx.timing(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    names = ["hash", "silk", "assign", "hash.sort", "kernel.project_dot2", "kernel.assign_tc", "kernel.assign_fp32",
+             "kernel.assign_recheck", "silk.vbuckets", "silk.bins", "silk.vote", "silk.dedup"]
+    tm = {k: ctx.timing_get(k) for k in names}
+    atc = tm["kernel.assign_tc"]
+    roof = None
+    if atc[1] and atc[0] > 0:
+        ach = atc[2] / (atc[0] / 1e3) / 1e12
+        roof = {"kernel": "kernel.assign_tc", "bound": "tensor", "achieved": ach, "peak": pk["bf16_tflops"],
+                "unit": "TFLOP/s", "frac": ach / pk["bf16_tflops"], "peak_source": f"{pk_kind} bf16_tflops (burst)",
+                "avg_launch_ms": atc[0] / atc[1]}
+    return {"workload": f"Alg. 1 (m={P['m']} QALSH tables, t={P['t']} buckets) -> SILK (Ks={P['Ks']} Ls={P['Ls']} "
+                        f"delta={P['delta']}) -> FP64 centroids -> BF16 tcgen05 assignment, on the {cfg.n} x {cfg.d} "
+                        f"points above",
+            "value": cfg.n * world / (ms / 1e3), "unit": UNIT, "ms_per_run": ms, "k_star": int(info["k_star"]),
+            "n_multiset": int(info["n_multiset"]), "assign_recheck_rows": int(info["n_recheck_rows"]),
+            "assign_fp64_rows": int(info["n_fp64_rows"]),
+            "phases_ms_per_run": {k: v[0] / args.steps for k, v in tm.items() if v[1]},
+            "roofline_assign_tc": roof}
 
 
 def bench_refine(args, geek, ctx, data, wl, world, prec):

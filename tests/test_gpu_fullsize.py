@@ -208,3 +208,45 @@ def test_c5_batch_full_size():
         seen += 1
     assert seen == 256
     assert sum(g["k"] for g in got) > 0
+
+
+def test_alg1_silk_assign_full_size():
+    """The paper's own pipeline on the 10M x 128 points: Alg. 1 (m = 40
+    QALSH tables, t = 5,000 even buckets each), SILK on those buckets
+    (Ks = 2, Ls = 20, delta = 10), FP64 centroids of the seeds and the
+    one-pass assignment to them.  The seed list and every centroid are
+    compared exactly, and 4,096 sampled labels in both fast precisions."""
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2106_10515_gb300 import geek
+    wl = synth.make(synth.config("c2"))
+    n, d = wl["x"].shape
+    m, t = synth.ALG1["m"], synth.ALG1["t"]
+    sp = synth.alg1_silk_params()
+    a = np.ascontiguousarray(wl["a"][:m])
+    ctx = geek.Context(0)
+    data = ctx.dense(geek._dev(wl["x"]))
+    bk = ctx.hash(data, 1, m, a=geek._dev(a), proj=geek.PROJ_QALSH, t=t)
+    seeds = ctx.silk(bk, **geek.silk_args(sp))
+    g_seeds = seeds.sets()
+    labs = {}
+    cen = torch.empty((max(seeds.k, 1), d), dtype=torch.float64, device="cuda")
+    for prec in (geek.PREC_BF16, geek.PREC_FP32):
+        labels = torch.empty(n, dtype=torch.int32, device="cuda")
+        ctx.assign(data, bk, seeds, labels, centers=cen, precision=prec)
+        labs[prec] = labels.cpu().numpy()
+    g_cen = cen[: seeds.k].cpu().numpy()
+    del bk, data, cen
+    torch.cuda.empty_cache()
+
+    _, ref_bk = oracle.transform_alg1(wl["x"], a, t)
+    ref_seeds = oracle.silk_on(ref_bk, sp)
+    del ref_bk
+    assert len(g_seeds) == ref_seeds.k > 0
+    assert g_seeds == ref_seeds.sets()
+    ref_c = oracle.centroids(wl["x"], ref_seeds)
+    assert np.array_equal(g_cen, ref_c)  # bit-exact FP64
+    rows = _sample(n)
+    lab_ref, _ = oracle.assign_dense(wl["x"][rows], ref_c)
+    for prec, lab in labs.items():
+        assert np.array_equal(lab[rows], lab_ref), prec
