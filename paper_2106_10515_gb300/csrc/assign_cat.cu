@@ -4,6 +4,8 @@
 //    mode as central vector, distance 1 - Jaccard = most matching attributes;
 //  - sparse sets: central vector = items present in more than half of the
 //    members, distance 1 - |A n C| / |A u C| compared exactly as fractions.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace {
@@ -242,18 +244,24 @@ __global__ void k_heavy_masks(int64_t k, const int64_t *__restrict__ coff, const
 // from bitmasks; light items go through the inverted index into a per-warp
 // counter array (cleared after use).  Every centre is then scored exactly:
 // J_j = inter / (|A| + |C_j| - inter), compared by cross-multiplication.
+// (The dense path: every centre is scanned per set.  It serves the sets
+// whose light candidates overflow the shared-memory table of k_jac_light;
+// rows lists them, na_fix >= 0 replaces |A| by a fixed size.)
 __global__ void __launch_bounds__(256) k_assign_jaccard(
     int64_t n, const int64_t *__restrict__ off, const uint32_t *__restrict__ items, int64_t k,
     const int32_t *__restrict__ clen, const uint64_t *__restrict__ cmask, const uint32_t *__restrict__ heavy,
     int nheavy, const uint32_t *__restrict__ post_item, const int64_t *__restrict__ post_off, int64_t n_post_items,
-    const uint32_t *__restrict__ post_centre, int32_t *__restrict__ counts, int32_t *__restrict__ labels) {
+    const uint32_t *__restrict__ post_centre, int32_t *__restrict__ counts, int32_t *__restrict__ labels,
+    const int32_t *__restrict__ rows, const unsigned long long *__restrict__ n_rows, int na_fix) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int32_t *cnt = counts + warp * k;
-    for (int64_t i = warp; i < n; i += nw) {
+    if (rows) n = (int64_t)*n_rows;
+    for (int64_t ii = warp; ii < n; ii += nw) {
+        const int64_t i = rows ? (int64_t)rows[ii] : ii;
         const int64_t s = off[i], e = off[i + 1];
-        const int64_t na = e - s;
+        const int64_t na = na_fix >= 0 ? na_fix : e - s;
         uint64_t amask = 0;
         // light items: binary search in the sorted item list of the index
         for (int64_t p = s + lane; p < e; p += 32) {
@@ -313,6 +321,212 @@ __global__ void __launch_bounds__(256) k_assign_jaccard(
         if (lane == 0) labels[i] = bj == 0x7FFFFFFF ? -1 : bj;
         __syncwarp();
     }
+}
+
+// Light candidates of every set, warp per set.  The set's heavy items give
+// its bitmask; each light item's posting list adds one to its centres in a
+// per-warp open-addressing table in shared memory (keys: centre ids).  Every
+// centre in the table is then scored exactly, J = I / (|A| + |C| - I) with I
+// = table count + popcount(amask & cmask), and the warp keeps the best
+// (larger fraction, then smaller index).  A set with more than JT_MAXU
+// distinct candidates is listed for the dense path instead.
+constexpr int JT_SLOTS = 1024;               // per warp
+constexpr int JT_MAXU = JT_SLOTS / 2;        // distinct candidates kept (load <= 1/2)
+constexpr uint32_t JT_EMPTY = 0xFFFFFFFFu;
+constexpr int JT_WARPS = 4;                  // static shared memory stays under 48 KB
+constexpr int JT_HSLOTS = 256;               // heavy-item lookup table
+
+__global__ void __launch_bounds__(32 * JT_WARPS) k_jac_light(
+    int64_t n, const int64_t *__restrict__ off, const uint32_t *__restrict__ items, int na_fix,
+    const int32_t *__restrict__ clen, const uint64_t *__restrict__ cmask, const uint32_t *__restrict__ heavy,
+    int nheavy, const uint32_t *__restrict__ post_item, const int64_t *__restrict__ post_off, int64_t n_post_items,
+    const uint32_t *__restrict__ post_centre, uint64_t *__restrict__ amask_out, int64_t *__restrict__ best_num,
+    int64_t *__restrict__ best_den, int32_t *__restrict__ best_j, int32_t *__restrict__ ovf_rows,
+    unsigned long long *__restrict__ n_ovf) {
+    __shared__ uint32_t tkey[JT_WARPS][JT_SLOTS];
+    __shared__ uint32_t tcnt[JT_WARPS][JT_SLOTS];
+    __shared__ uint16_t tlist[JT_WARPS][JT_MAXU];
+    __shared__ uint32_t tnum[JT_WARPS];
+    __shared__ uint32_t hkey[JT_HSLOTS];
+    __shared__ int8_t hbit[JT_HSLOTS];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int e = threadIdx.x; e < JT_HSLOTS; e += blockDim.x) {
+        hkey[e] = JT_EMPTY;
+        hbit[e] = -1;
+    }
+    for (int e = lane; e < JT_SLOTS; e += 32) {
+        tkey[w][e] = JT_EMPTY;
+        tcnt[w][e] = 0;
+    }
+    if (lane == 0) tnum[w] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int h = 0; h < nheavy; h++) {
+            uint32_t sl = (heavy[h] * 2654435761u) >> 24;
+            while (hkey[sl] != JT_EMPTY) sl = (sl + 1) & (JT_HSLOTS - 1);  // nheavy < JT_HSLOTS: a free slot exists
+            hkey[sl] = heavy[h];
+            hbit[sl] = (int8_t)h;
+        }
+    __syncthreads();
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < n; i += nw) {
+        const int64_t s = off[i], e = off[i + 1];
+        const int64_t na = na_fix >= 0 ? na_fix : e - s;
+        uint64_t amask = 0;
+        for (int64_t p = s + lane; p < e; p += 32) {
+            const uint32_t it = items[p];
+            uint32_t sl = (it * 2654435761u) >> 24;
+            int hb = -1;
+            for (int probe = 0; probe < JT_HSLOTS; probe++) {
+                const uint32_t kk = hkey[sl];
+                if (kk == it) {
+                    hb = hbit[sl];
+                    break;
+                }
+                if (kk == JT_EMPTY) break;
+                sl = (sl + 1) & (JT_HSLOTS - 1);
+            }
+            if (hb >= 0) {
+                amask |= 1ull << hb;
+                continue;
+            }
+            int64_t lo = 0, hi = n_post_items;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (post_item[mid] < it) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo < n_post_items && post_item[lo] == it)
+                for (int64_t q = post_off[lo]; q < post_off[lo + 1]; q++) {
+                    // once the table holds more than JT_MAXU centres the set
+                    // goes to the dense path: stop counting
+                    if (*(volatile uint32_t *)&tnum[w] > JT_MAXU) break;
+                    const uint32_t c = post_centre[q];
+                    uint32_t h = (c * 2654435761u) >> 22;  // 10 bits: JT_SLOTS
+                    bool placed = false;
+                    for (int probe = 0; probe < 64; probe++) {
+                        const uint32_t old = atomicCAS(&tkey[w][h], JT_EMPTY, c);
+                        if (old == JT_EMPTY || old == c) {
+                            atomicAdd(&tcnt[w][h], 1u);
+                            if (old == JT_EMPTY) {
+                                const uint32_t pos = atomicAdd(&tnum[w], 1u);
+                                if (pos < JT_MAXU) tlist[w][pos] = (uint16_t)h;
+                            }
+                            placed = true;
+                            break;
+                        }
+                        h = (h + 1) & (JT_SLOTS - 1);
+                    }
+                    if (!placed) atomicMax(&tnum[w], (uint32_t)JT_MAXU + 1);  // long probe: overflow
+                }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) amask |= __shfl_xor_sync(0xffffffffu, amask, o);
+        __syncwarp();
+        const uint32_t nu = tnum[w];
+        int64_t bn = 0, bd = 1;
+        int bj = 0x7FFFFFFF;
+        if (nu > JT_MAXU) {  // too many candidates: the dense path decides this set
+            for (int e2 = lane; e2 < JT_SLOTS; e2 += 32) {
+                tkey[w][e2] = JT_EMPTY;
+                tcnt[w][e2] = 0;
+            }
+            if (lane == 0) ovf_rows[atomicAdd(n_ovf, 1ull)] = (int32_t)i;
+        } else {
+            for (uint32_t q = lane; q < nu; q += 32) {
+                const int sl = tlist[w][q];
+                const uint32_t c = tkey[w][sl];
+                const int64_t in = (int64_t)tcnt[w][sl] + __popcll(amask & cmask[c]);
+                tkey[w][sl] = JT_EMPTY;
+                tcnt[w][sl] = 0;
+                const int64_t un = na + clen[c] - in;
+                if (un > 0 && (in * bd > bn * un || (in * bd == bn * un && (int)c < bj))) {
+                    bn = in;
+                    bd = un;
+                    bj = (int)c;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const int64_t on = __shfl_xor_sync(0xffffffffu, bn, o);
+                const int64_t od = __shfl_xor_sync(0xffffffffu, bd, o);
+                const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+                const int64_t l = on * bd, r = bn * od;
+                if (l > r || (l == r && oj < bj)) {
+                    bn = on;
+                    bd = od;
+                    bj = oj;
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {
+            tnum[w] = 0;
+            amask_out[i] = amask;
+            best_num[i] = bn;
+            best_den[i] = bd;
+            best_j[i] = bj;
+        }
+        __syncwarp();
+    }
+}
+
+// Heavy-only scores and the label, thread per set.  Centres are grouped by
+// their heavy bitmask; within a group the best heavy-only score belongs to
+// the smallest |C| (then the smallest index), so one representative per
+// group suffices.  A heavy-only score never exceeds the exact one, so the
+// larger of this scan and the light candidates' exact best (ties to the
+// smaller index) is the exact argmax; with no positive score the label is 0.
+constexpr int JG_TILE = 2048;
+
+__global__ void __launch_bounds__(256) k_jac_heavy(int64_t n, const int64_t *__restrict__ off, int na_fix,
+                                                   int64_t G, const uint64_t *__restrict__ gmask,
+                                                   const int32_t *__restrict__ gcmin, const int32_t *__restrict__ gj,
+                                                   const uint64_t *__restrict__ amask_in,
+                                                   const int64_t *__restrict__ best_num,
+                                                   const int64_t *__restrict__ best_den,
+                                                   const int32_t *__restrict__ best_j, int32_t *__restrict__ labels) {
+    __shared__ uint64_t sm[JG_TILE];
+    __shared__ int32_t sc[JG_TILE], sj[JG_TILE];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i < n;
+    int64_t bn = 0, bd = 1, na = 0;
+    int bj = 0;
+    uint64_t am = 0;
+    if (live) {
+        na = na_fix >= 0 ? na_fix : off[i + 1] - off[i];
+        am = amask_in[i];
+        if (best_j[i] != 0x7FFFFFFF && best_num[i] > 0) {
+            bn = best_num[i];
+            bd = best_den[i];
+            bj = best_j[i];
+        }
+    }
+    for (int64_t g0 = 0; g0 < G; g0 += JG_TILE) {
+        const int tn = (int)min((int64_t)JG_TILE, G - g0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < tn; e += blockDim.x) {
+            sm[e] = gmask[g0 + e];
+            sc[e] = gcmin[g0 + e];
+            sj[e] = gj[g0 + e];
+        }
+        __syncthreads();
+        if (live && am)
+            for (int e = 0; e < tn; e++) {
+                const uint64_t x = am & sm[e];
+                if (!x) continue;
+                const int64_t h = __popcll(x);
+                const int64_t un = na + sc[e] - h;
+                const int64_t l = h * bd, r = bn * un;
+                if (l > r || (l == r && sj[e] < bj)) {
+                    bn = h;
+                    bd = un;
+                    bj = sj[e];
+                }
+            }
+    }
+    if (live) labels[i] = bj;
 }
 
 }  // namespace
@@ -452,6 +666,7 @@ geek_status assign_hetero(geek_ctx *ctx, Scratch &scr, const geek_buckets *b, co
 geek_status assign_sets(geek_ctx *ctx, Scratch &scr, const int64_t *off, const uint32_t *items, int64_t n,
                         const silk_seeds *s, int32_t *labels, geek_assign_stats *stats, geek_centres *keep,
                         cudaStream_t st) {
+    const int na_fix = -1;
     const int64_t k = s->k;
     if (stats) *stats = geek_assign_stats{0.0, 0.0, k, 0};
     if (keep) {
@@ -543,13 +758,71 @@ geek_status assign_sets(geek_ctx *ctx, Scratch &scr, const int64_t *off, const u
     GK_COUNT();
     k_heavy_masks<<<G(ctx, k), 256, 0, st>>>(k, coff, citems, d_heavy, nheavy, cmask, clen);
     GK_LAUNCH(ctx);
-    const int blocks = ctx->num_sms * 4;
-    const int64_t nwarps = (int64_t)blocks * 8;
-    GK_TRY(scr.alloc(&counts, (size_t)nwarps * k));
-    GK_CUDA(ctx, cudaMemsetAsync(counts, 0, sizeof(int32_t) * nwarps * k, st));
-    GK_COUNT();
-    k_assign_jaccard<<<blocks, 256, 0, st>>>(n, off, items, k, clen, cmask, d_heavy, nheavy, d_litem, d_loff,
-                                             h_nlight, d_lcentre, counts, labels);
-    GK_LAUNCH(ctx);
+    // centres grouped by heavy bitmask: one representative per group, the
+    // smallest |C| then the smallest index (host sort; k is small)
+    std::vector<uint64_t> hm(k);
+    std::vector<int32_t> hl(k);
+    GK_CUDA(ctx, cudaMemcpyAsync(hm.data(), cmask, 8 * k, cudaMemcpyDeviceToHost, st));
+    GK_CUDA(ctx, cudaMemcpyAsync(hl.data(), clen, 4 * k, cudaMemcpyDeviceToHost, st));
+    GK_CUDA(ctx, cudaStreamSynchronize(st));
+    std::vector<int32_t> ord(k);
+    for (int64_t j = 0; j < k; j++) ord[j] = (int32_t)j;
+    std::sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) {
+        if (hm[a] != hm[b]) return hm[a] < hm[b];
+        if (hl[a] != hl[b]) return hl[a] < hl[b];
+        return a < b;
+    });
+    std::vector<uint64_t> gmh;
+    std::vector<int32_t> gch, gjh;
+    for (int64_t q = 0; q < k; q++)
+        if (q == 0 || hm[ord[q]] != hm[ord[q - 1]]) {
+            gmh.push_back(hm[ord[q]]);
+            gch.push_back(hl[ord[q]]);
+            gjh.push_back(ord[q]);
+        }
+    const int64_t G = (int64_t)gmh.size();
+    uint64_t *gmask, *amask;
+    int32_t *gcmin, *gj, *bj, *ovf;
+    int64_t *bnum, *bden;
+    unsigned long long *n_ovf;
+    GK_TRY(scr.alloc(&gmask, G));
+    GK_TRY(scr.alloc(&gcmin, G));
+    GK_TRY(scr.alloc(&gj, G));
+    GK_TRY(scr.alloc(&amask, n));
+    GK_TRY(scr.alloc(&bnum, n));
+    GK_TRY(scr.alloc(&bden, n));
+    GK_TRY(scr.alloc(&bj, n));
+    GK_TRY(scr.alloc(&ovf, n));
+    GK_TRY(scr.alloc(&n_ovf, 1));
+    GK_CUDA(ctx, cudaMemcpyAsync(gmask, gmh.data(), 8 * G, cudaMemcpyHostToDevice, st));
+    GK_CUDA(ctx, cudaMemcpyAsync(gcmin, gch.data(), 4 * G, cudaMemcpyHostToDevice, st));
+    GK_CUDA(ctx, cudaMemcpyAsync(gj, gjh.data(), 4 * G, cudaMemcpyHostToDevice, st));
+    GK_CUDA(ctx, cudaMemsetAsync(n_ovf, 0, sizeof(unsigned long long), st));
+    {
+        EvTimer tk(ctx, "kernel.jaccard", st);
+        GK_COUNT();
+        k_jac_light<<<ctx->num_sms * 8, 32 * JT_WARPS, 0, st>>>(n, off, items, na_fix, clen, cmask, d_heavy, nheavy,
+                                                               d_litem, d_loff, h_nlight, d_lcentre, amask, bnum,
+                                                               bden, bj, ovf, n_ovf);
+        GK_COUNT();
+        k_jac_heavy<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(n, off, na_fix, G, gmask, gcmin, gj, amask, bnum,
+                                                                bden, bj, labels);
+        GK_LAUNCH(ctx);
+    }
+    unsigned long long h_ovf = 0;
+    GK_CUDA(ctx, cudaMemcpyAsync(&h_ovf, n_ovf, sizeof h_ovf, cudaMemcpyDeviceToHost, st));
+    GK_CUDA(ctx, cudaStreamSynchronize(st));
+    if (h_ovf) {
+        // sets with too many light candidates: every centre scanned per set
+        const int blocks = (int)std::min<int64_t>(ctx->num_sms * 4, ceil_div((int64_t)h_ovf, 8));
+        const int64_t nwarps = (int64_t)blocks * 8;
+        GK_TRY(scr.alloc(&counts, (size_t)nwarps * k));
+        GK_CUDA(ctx, cudaMemsetAsync(counts, 0, sizeof(int32_t) * nwarps * k, st));
+        GK_COUNT();
+        k_assign_jaccard<<<blocks, 256, 0, st>>>(n, off, items, k, clen, cmask, d_heavy, nheavy, d_litem, d_loff,
+                                                 h_nlight, d_lcentre, counts, labels, ovf, n_ovf, na_fix);
+        GK_LAUNCH(ctx);
+    }
+    if (stats) stats->n_recheck_rows = (int64_t)h_ovf;  // sets decided by the dense path
     return sort_err_check(ctx, st);  // synchronises st
 }
