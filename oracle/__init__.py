@@ -57,6 +57,8 @@ PINS = {
     "modes": "collections.Counter brute force",
     "assign_cat": "brute-force match counts",
     "sparse_centres": "Counter brute force",
+    "doph_modes": "Counter brute force per reduced dimension over hand-built DOPH tokens",
+    "assign_doph": "brute-force count of dimensions equal to each mode",
     "assign_jaccard": "fractions.Fraction brute force",
 }
 
@@ -476,6 +478,21 @@ def assign_jaccard(off, items, coff, citems):
     return lab, inter, uni
 
 
+def doph_modes(tokens, seeds: Seeds):
+    """Central vector of sparse sets reduced by DOPH (Sect. 3.3: the mode of
+    each reduced dimension): for every seed and dimension b, the most
+    frequent token of its members (ties to the smallest).  int64 [k, D']."""
+    return modes(np.asarray(tokens, dtype=np.uint64).view(np.int64), seeds)
+
+
+def assign_doph(tokens, modes_):
+    """One-pass assignment of DOPH-reduced sets (Eq. 1 with 1 - Jaccard of
+    the token sets; every set and centre holds D' tokens, so the label
+    maximises the number of dimensions equal to the mode, ties to the
+    smallest seed index)."""
+    return assign_cat(np.asarray(tokens, dtype=np.uint64).view(np.int64), modes_)
+
+
 def subset_rows(off, items, rows):
     """CSR sub-collection of the given set indices (for sampled checks)."""
     rows = np.asarray(rows, dtype=np.int64)
@@ -496,6 +513,11 @@ def run_workload(wl, assign_rows=None):
     if cfg.kind == "dense":
         codes, bk = hash_dense(wl["x"], wl["a"], wl["b"], wl["w"], cfg.K, cfg.L)
         res.update(codes=codes, buckets=bk)
+    elif cfg.kind == "sets" and wl.get("doph"):
+        dp = wl["doph"]
+        tok, mh, bk = transform_sparse_doph(wl["set_off"], wl["set_items"], dp["bins"], dp["a"], dp["b"],
+                                            wl["mh_a"], wl["mh_b"], cfg.K, cfg.L)
+        res.update(codes=mh, buckets=bk, tokens=tok)
     elif cfg.kind == "sets":
         mh, bk = hash_sets(wl["set_off"], wl["set_items"], wl["mh_a"], wl["mh_b"], cfg.K, cfg.L)
         res.update(codes=mh, buckets=bk)
@@ -514,6 +536,10 @@ def run_workload(wl, assign_rows=None):
         c = centroids(wl["x"], seeds)
         lab, dist = assign_dense(wl["x"][rows], c)
         res.update(centres=c, labels=lab, dist=dist)
+    elif cfg.kind == "sets" and wl.get("doph"):
+        m = doph_modes(res["tokens"], seeds)
+        lab, mt = assign_doph(res["tokens"][rows], m)
+        res.update(modes=m, labels=lab, matches=mt)
     elif cfg.kind == "sets":
         coff, cit = sparse_centres(wl["set_off"], wl["set_items"], seeds)
         so, si = subset_rows(wl["set_off"], wl["set_items"], rows)

@@ -40,7 +40,7 @@ geek_status stage(geek_ctx *ctx, Scratch &scr, const T *src, size_t count, bool 
 void free_buckets(geek_buckets *b) {
     if (!b) return;
     for (void *p : {(void *)b->obj_bucket, (void *)b->boff, (void *)b->members, (void *)b->codes,
-                    (void *)b->num_key})
+                    (void *)b->num_key, (void *)b->doph_tok})
         if (p) cudaFreeAsync(p, b->st);
     delete b;
 }
@@ -154,8 +154,12 @@ geek_status hash_impl(geek_ctx *ctx, const geek_data *data, const geek_hash_para
         GK_TRY(stage(ctx, scr, data->set_items, (size_t)n_items, host, &items, st));
         mh = (uint32_t *)b->codes;
         if (p->doph_bins > 0) {  // Alg. 3: DOPH reduction, then MinHash of the tokens
+            // the reduced objects stay with the buckets: the assignment's
+            // central vectors are modes over them (Sect. 3.3)
             uint64_t *tok;
-            GK_TRY(scr.alloc(&tok, (size_t)n * p->doph_bins));
+            GK_TRY(own_alloc(ctx, (void **)&b->doph_tok, sizeof(uint64_t) * (size_t)std::max<int64_t>(n, 1) * p->doph_bins, st));
+            tok = b->doph_tok;
+            b->doph_bins = p->doph_bins;
             GK_TRY(doph_reduce(ctx, n, off, items, p->doph_bins, p->doph_a, p->doph_b, tok, st));
             GK_TRY(minhash_rows64(ctx, n, p->doph_bins, tok, F2, p->mh_a, p->mh_b, mh, st));
         } else {
@@ -582,11 +586,16 @@ geek_status assign_impl(geek_ctx *ctx, const geek_data *data, const geek_buckets
             GK_CUDA(ctx, cudaMemcpyAsync(&n_items, data->set_off + n, 8, cudaMemcpyDeviceToHost, st));
             GK_CUDA(ctx, cudaStreamSynchronize(st));
         }
-        const int64_t *off;
-        const uint32_t *items;
-        GK_TRY(stage(ctx, scr, data->set_off, (size_t)n + 1, host, &off, st));
-        GK_TRY(stage(ctx, scr, data->set_items, (size_t)n_items, host, &items, st));
-        GK_TRY(assign_sets(ctx, scr, off, items, n, s, lab, stats, keep, st));
+        if (b && b->kind == GEEK_SETS && b->doph_bins > 0) {
+            if (b->n != n) return set_error(ctx, GEEK_ERR_INVALID, "buckets of another data set");
+            GK_TRY(assign_doph(ctx, scr, b, s, lab, stats, keep, st));
+        } else {
+            const int64_t *off;
+            const uint32_t *items;
+            GK_TRY(stage(ctx, scr, data->set_off, (size_t)n + 1, host, &off, st));
+            GK_TRY(stage(ctx, scr, data->set_items, (size_t)n_items, host, &items, st));
+            GK_TRY(assign_sets(ctx, scr, off, items, n, s, lab, stats, keep, st));
+        }
     }
     if (host) {
         GK_CUDA(ctx, cudaMemcpyAsync(labels, lab, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));

@@ -663,10 +663,13 @@ geek_status assign_hetero(geek_ctx *ctx, Scratch &scr, const geek_buckets *b, co
     return GEEK_OK;
 }
 
+geek_status jaccard_core(geek_ctx *ctx, Scratch &scr, const int64_t *off, const uint32_t *items, int64_t n,
+                         int na_fix, int64_t k, const int64_t *coff, const uint32_t *citems, int64_t nci,
+                         int32_t *labels, geek_assign_stats *stats, cudaStream_t st);
+
 geek_status assign_sets(geek_ctx *ctx, Scratch &scr, const int64_t *off, const uint32_t *items, int64_t n,
                         const silk_seeds *s, int32_t *labels, geek_assign_stats *stats, geek_centres *keep,
                         cudaStream_t st) {
-    const int na_fix = -1;
     const int64_t k = s->k;
     if (stats) *stats = geek_assign_stats{0.0, 0.0, k, 0};
     if (keep) {
@@ -693,6 +696,16 @@ geek_status assign_sets(geek_ctx *ctx, Scratch &scr, const int64_t *off, const u
         if (nci)
             GK_CUDA(ctx, cudaMemcpyAsync(keep->items, citems, sizeof(uint32_t) * (size_t)nci, cudaMemcpyDeviceToDevice, st));
     }
+    return jaccard_core(ctx, scr, off, items, n, -1, k, coff, citems, nci, labels, stats, st);
+}
+
+// Exact Jaccard argmax of every set against k centre sets (CSR coff /
+// citems, nci items): J_j = |A n C_j| / |A u C_j|, larger fraction then
+// smaller index; with no positive J the label is 0.  na_fix >= 0 gives every
+// set the size na_fix (rows padded with an id that no centre holds).
+geek_status jaccard_core(geek_ctx *ctx, Scratch &scr, const int64_t *off, const uint32_t *items, int64_t n,
+                         int na_fix, int64_t k, const int64_t *coff, const uint32_t *citems, int64_t nci,
+                         int32_t *labels, geek_assign_stats *stats, cudaStream_t st) {
     // inverted index item -> centres: pairs sorted by (item, centre), runs of
     // equal items; the HEAVY longest posting lists become bitmask items
     uint64_t *pairs, *ikey;
@@ -825,4 +838,110 @@ geek_status assign_sets(geek_ctx *ctx, Scratch &scr, const int64_t *off, const u
     }
     if (stats) stats->n_recheck_rows = (int64_t)h_ovf;  // sets decided by the dense path
     return sort_err_check(ctx, st);  // synchronises st
+}
+
+namespace {
+
+// id of each token in the sorted distinct list U (nu entries), or 2^32 - 1
+// when absent (no centre holds it)
+__global__ void k_map_tokens(int64_t m, const uint64_t *__restrict__ tok, const uint64_t *__restrict__ U, int64_t nu,
+                             uint32_t *__restrict__ out) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t v = tok[e];
+        int64_t lo = 0, hi = nu;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (U[mid] < v) lo = mid + 1;
+            else hi = mid;
+        }
+        out[e] = (lo < nu && U[lo] == v) ? (uint32_t)lo : 0xFFFFFFFFu;
+    }
+}
+
+__global__ void k_fixed_off(int64_t n, int64_t len, int64_t *__restrict__ off) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += (int64_t)gridDim.x * blockDim.x)
+        off[i] = i * len;
+}
+
+// the first token of each run of equal sorted tokens: compacted to U
+__global__ void k_run_firsts(int64_t m, const uint64_t *__restrict__ sorted, const int64_t *__restrict__ rank_excl,
+                             uint64_t *__restrict__ U) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+        if (e == 0 || sorted[e] != sorted[e - 1]) U[rank_excl[e]] = sorted[e];
+}
+
+__global__ void k_run_flags(int64_t m, const uint64_t *__restrict__ sorted, int64_t *__restrict__ flags) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+        flags[e] = (e == 0 || sorted[e] != sorted[e - 1]) ? 1 : 0;
+}
+
+}  // namespace
+
+// Sparse sets reduced by DOPH (Alg. 3): every object is its D' tokens, one per
+// reduced dimension.  Central vector = the mode of each dimension over the
+// seed's members (Sect. 3.3: the mode of sparse data after DOPH; ties to the
+// smallest token); distance 1 - Jaccard of the token sets, i.e. the label
+// maximises the number of dimensions equal to the centre's mode.  Tokens map
+// to 32-bit ids of the distinct mode tokens and the Jaccard engine decides,
+// with |A| = |C| = D'.
+geek_status assign_doph(geek_ctx *ctx, Scratch &scr, const geek_buckets *b, const silk_seeds *s, int32_t *labels,
+                        geek_assign_stats *stats, geek_centres *keep, cudaStream_t st) {
+    const int64_t n = b->n, k = s->k;
+    const int D = b->doph_bins;
+    if (stats) *stats = geek_assign_stats{0.0, 0.0, k, 0};
+    if (keep) {
+        keep->kind = GEEK_SETS;
+        keep->k = k;
+        keep->n_attr = D;
+        GK_TRY(own_alloc(ctx, (void **)&keep->modes, sizeof(int64_t) * (size_t)std::max<int64_t>(k, 1) * D, st));
+    }
+    if (n == 0) return GEEK_OK;
+    if (k == 0) {
+        GK_CUDA(ctx, cudaMemsetAsync(labels, 0xFF, sizeof(int32_t) * n, st));
+        return GEEK_OK;
+    }
+    const int64_t km = k * D;
+    uint64_t *modes, *srt;
+    GK_TRY(scr.alloc(&modes, km));
+    GK_TRY(scr.alloc(&srt, km));
+    GK_COUNT();
+    k_modes<<<G(ctx, km), 256, 0, st>>>(k, D, s->off, s->ids, b->doph_tok, modes, nullptr);
+    GK_LAUNCH(ctx);
+    if (keep) GK_CUDA(ctx, cudaMemcpyAsync(keep->modes, modes, 8 * km, cudaMemcpyDeviceToDevice, st));
+    // distinct mode tokens, ascending
+    GK_CUDA(ctx, cudaMemcpyAsync(srt, modes, 8 * km, cudaMemcpyDeviceToDevice, st));
+    GK_TRY(radix_sort_segments(ctx, scr, 1, km, &srt, nullptr, nullptr, 64, st));
+    int64_t *flags, *rexcl, *nu_dev;
+    GK_TRY(scr.alloc(&flags, km));
+    GK_TRY(scr.alloc(&rexcl, km));
+    GK_TRY(scr.alloc(&nu_dev, 1));
+    GK_COUNT();
+    k_run_flags<<<G(ctx, km), 256, 0, st>>>(km, srt, flags);
+    GK_LAUNCH(ctx);
+    GK_TRY(exclusive_scan_i64(ctx, scr, flags, rexcl, km, nu_dev, st));
+    int64_t nu = 0;
+    GK_CUDA(ctx, cudaMemcpyAsync(&nu, nu_dev, 8, cudaMemcpyDeviceToHost, st));
+    GK_CUDA(ctx, cudaStreamSynchronize(st));
+    if (nu >= 0xFFFFFFFFLL) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "too many distinct mode tokens");
+    uint64_t *U;
+    GK_TRY(scr.alloc(&U, nu));
+    GK_COUNT();
+    k_run_firsts<<<G(ctx, km), 256, 0, st>>>(km, srt, rexcl, U);
+    // centres and rows as id lists of fixed length D
+    uint32_t *cid, *rid;
+    int64_t *coff, *roff;
+    GK_TRY(scr.alloc(&cid, km));
+    GK_TRY(scr.alloc(&rid, n * D));
+    GK_TRY(scr.alloc(&coff, k + 1));
+    GK_TRY(scr.alloc(&roff, n + 1));
+    GK_COUNT();
+    k_map_tokens<<<G(ctx, km), 256, 0, st>>>(km, modes, U, nu, cid);
+    GK_COUNT();
+    k_map_tokens<<<G(ctx, n * D), 256, 0, st>>>(n * D, b->doph_tok, U, nu, rid);
+    GK_COUNT();
+    k_fixed_off<<<G(ctx, k + 1), 256, 0, st>>>(k, D, coff);
+    GK_COUNT();
+    k_fixed_off<<<G(ctx, n + 1), 256, 0, st>>>(n, D, roff);
+    GK_LAUNCH(ctx);
+    return jaccard_core(ctx, scr, roff, rid, n, D, k, coff, cid, km, labels, stats, st);
 }

@@ -143,6 +143,9 @@ struct geek_buckets {
     // HETERO: per table, the packed key of the numeric E2LSH part only (the
     // unified categorical attribute used for assignment), L x n
     uint64_t *num_key = nullptr;
+    // SETS hashed through DOPH: the D' tokens of every object, n x D'
+    uint64_t *doph_tok = nullptr;
+    int doph_bins = 0;
 };
 
 struct silk_seeds {
@@ -326,6 +329,9 @@ struct geek_centres {
 // Stream-ordered allocation of a result handle's buffer (NOMEM on failure).
 geek_status own_alloc(geek_ctx *ctx, void **p, size_t bytes, cudaStream_t st);
 // keep (nullable): receives the central vectors the assignment used.
+// Sets reduced by DOPH (b->doph_bins > 0): per-dimension modes, Jaccard of tokens.
+geek_status assign_doph(geek_ctx *ctx, Scratch &scr, const geek_buckets *b, const silk_seeds *s, int32_t *labels,
+                        geek_assign_stats *stats, geek_centres *keep, cudaStream_t st);
 geek_status assign_hetero(geek_ctx *ctx, Scratch &scr, const geek_buckets *b, const uint32_t *tok,
                           int n_cat, const silk_seeds *s, int32_t *labels, geek_assign_stats *stats,
                           geek_centres *keep, cudaStream_t st);

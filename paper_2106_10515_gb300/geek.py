@@ -402,7 +402,7 @@ class Context:
             if info.kind == DENSE:
                 cen = torch.empty((info.k, info.d), dtype=torch.float64, device="cuda")
                 out["centers"] = cen
-            elif info.kind == HETERO:
+            elif info.kind == HETERO or info.n_attr > 0:  # modes (heterogeneous rows, DOPH-reduced sets)
                 mod = torch.empty((info.k, info.n_attr), dtype=torch.int64, device="cuda")
                 out["modes"] = mod
             else:

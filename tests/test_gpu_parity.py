@@ -369,3 +369,26 @@ def test_sets_doph_transform(G, ctx, Dp):
     got = bk.copy_out()
     assert np.array_equal(got["codes"].cpu().numpy().view(np.uint32), mh)
     check_buckets(got, ref)
+
+
+@pytest.mark.parametrize("Dp", [64, 400])
+def test_sets_doph_pipeline(G, ctx, Dp):
+    """Alg. 3 with DOPH through SILK and the assignment (Sect. 3.3): seeds,
+    the per-dimension modes of the reduced tokens and every label against
+    the oracle."""
+    wl = synth.make(synth.config("c3", n=6000, n_base=60, silk=dict(delta=4)))
+    cfg = wl["cfg"]
+    rng = np.random.default_rng(Dp + 1)
+    Ap, Bp = int(rng.integers(1, 1 << 62)) * 2 + 1, int(rng.integers(0, 1 << 62))
+    wl["doph"] = dict(bins=Dp, a=Ap, b=Bp)
+    data = ctx.sets(G._dev(wl["set_off"]), G._dev(wl["set_items"].astype(np.int32)))
+    bk = ctx.hash(data, cfg.K, cfg.L, mh_a=G._dev(wl["mh_a"]), mh_b=G._dev(wl["mh_b"]), doph_bins=Dp,
+                  doph_a=Ap, doph_b=Bp)
+    seeds = ctx.silk(bk, **G.silk_args(wl["silk"]))
+    ref = oracle.run_workload(wl)
+    assert seeds.sets() == ref["seeds"].sets()
+    assert seeds.k > 0
+    labels = torch.empty(cfg.n, dtype=torch.int32, device="cuda")
+    _, cen = ctx.assign_ex(data, bk, seeds, labels)
+    assert np.array_equal(labels.cpu().numpy(), ref["labels"])
+    assert np.array_equal(cen["modes"].cpu().numpy(), ref["modes"])

@@ -546,3 +546,35 @@ def test_hetero_keys_and_attrs_from_the_formula(orc):
     assert np.array_equal(attrs[:, L:], cat)
     # the split is a real concatenation: some numeric buckets are cut by MinHash
     assert any(bk.n_buckets[l] > nbk.n_buckets[l] for l in range(L))
+
+
+def test_doph_modes_and_assignment(orc):
+    """Sect. 3.3 for sets reduced by DOPH: the centre is the per-dimension
+    mode of the members' tokens; the label maximises the dimensions equal to
+    it (1 - Jaccard of D' tokens against D' tokens), ties to the smallest."""
+    rng = np.random.default_rng(31)
+    n, Dp = 60, 5
+    sets = [sorted(rng.choice(40, size=int(rng.integers(0, 9)), replace=False).tolist()) for _ in range(n)]
+    off = np.zeros(n + 1, np.int64)
+    off[1:] = np.cumsum([len(s) for s in sets])
+    items = np.array([i for s in sets for i in s], np.uint32)
+    Ap, Bp = 0x9E3779B97F4A7C15, 12345
+    tok = orc.doph(off, items, Dp, Ap, Bp)
+    seed_sets = [sorted(rng.choice(n, size=s, replace=False).tolist()) for s in [1, 2, 5, 9, 14]]
+    seeds = orc.Seeds(np.concatenate([[0], np.cumsum([len(s) for s in seed_sets])]).astype(np.int64),
+                      np.array([i for s in seed_sets for i in s], np.int32), len(seed_sets))
+    m = orc.doph_modes(tok, seeds)
+    for j, ss in enumerate(seed_sets):
+        for b in range(Dp):
+            cnt = Counter(int(tok[i, b]) for i in ss)
+            top = max(cnt.values())
+            assert int(m[j, b]) == min(v for v, c in cnt.items() if c == top)
+            assert int(m[j, b]) >> 48 == b  # the mode of dimension b is a dimension-b token
+    lab, mt = orc.assign_doph(tok, m)
+    for i in range(n):
+        sc = [sum(int(tok[i, b]) == int(m[j, b]) for b in range(Dp)) for j in range(len(seed_sets))]
+        assert mt[i] == max(sc) and lab[i] == sc.index(max(sc))
+        # the same label by exact Jaccard of the D' tokens
+        J = [Fraction(len(set(tok[i].tolist()) & set(m[j].astype(np.uint64).tolist())),
+                      len(set(tok[i].tolist()) | set(m[j].astype(np.uint64).tolist()))) for j in range(len(seed_sets))]
+        assert lab[i] == J.index(max(J))
