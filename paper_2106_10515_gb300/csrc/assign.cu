@@ -191,6 +191,136 @@ __global__ void __launch_bounds__(256) k_assign_fp32(FArgs A, GatherUnits U) {
     }
 }
 
+// FP64 decision of the rows a refine pass left uncertain, tiled like
+// k_assign_fp32<true>: units of up to 128 such rows of one instance, all
+// centres streamed through shared memory in tiles, the FP32 fast value of
+// every (row, centre) pair in registers.  A pair whose fast value lies within
+// the row's window lim = m + 2W (m: the row's smallest fast value, from the
+// refine pass, in mrow[global row]) gets the FP64 reference distance, read
+// from the row in shared memory; the row's label is the smallest reference
+// distance, ties to the smaller index (-1 when no value is finite).
+__device__ __forceinline__ double ref_dist_strided(const float *x, int stride, const double *__restrict__ c, int d) {
+    double D = 0.0;
+    for (int t = 0; t < d; t++) {
+        const double e = __dsub_rn((double)x[t * stride], c[t]);
+        D = __dadd_rn(D, __dmul_rn(e, e));
+    }
+    return D;
+}
+
+__global__ void __launch_bounds__(256) k_assign_decide64(GatherUnits U, const float *__restrict__ mrow) {
+    extern __shared__ float sm[];
+    __shared__ float cns[AS_TC];
+    __shared__ int64_t s_rows[AS_TR];
+    const int t = threadIdx.x, cg = t & 15, rg = t >> 4;
+    const int64_t nunits = (int64_t)*U.n_units;
+    for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+        const RInst &I = U.R[U.unit_inst[u]];
+        const int d = I.d;
+        const int64_t k = I.k;
+        const int64_t rbase = I.row_base;
+        const int nrows = U.unit_cnt[u];
+        __syncthreads();  // s_rows and xs of the previous unit fully used
+        if (t < nrows) s_rows[t] = (int64_t)U.grows[U.unit_start[u] + t] - rbase;
+        __syncthreads();
+        float *xs = sm;                      // [d][AS_TR]
+        float *cs = sm + (size_t)d * AS_TR;  // [AS_KC][AS_TC]
+        for (int e = t; e < AS_TR * d; e += 256) {
+            const int r = e / d, kk = e % d;
+            xs[kk * AS_TR + r] = r < nrows ? I.x[s_rows[r] * I.ldx + kk] : 0.f;
+        }
+        __syncthreads();
+        const float cmax = __uint_as_float(*I.cmax_bits);
+        float lim[AS_RPT];
+        double bD[AS_RPT];
+        int bj[AS_RPT];
+#pragma unroll
+        for (int r = 0; r < AS_RPT; r++) {
+            const int rr = rg * AS_RPT + r;
+            float xs2 = 0.f;
+            for (int kk = 0; kk < d; kk++) xs2 = fmaf(xs[kk * AS_TR + rr], xs[kk * AS_TR + rr], xs2);
+            const float xn = sqrtf(xs2) * (1.f + 1.0e-3f);
+            const float m = rr < nrows ? mrow[rbase + s_rows[rr]] : __int_as_float(0x7fc00000);
+            lim[r] = m + 2.f * window_fp32(xn, cmax, d) * (1.f + 1e-6f);
+            bD[r] = DBL_MAX;
+            bj[r] = 0x7FFFFFFF;
+        }
+        for (int64_t j0 = 0; j0 < k; j0 += AS_TC) {
+            float acc[AS_RPT][AS_CPT];
+#pragma unroll
+            for (int r = 0; r < AS_RPT; r++)
+#pragma unroll
+                for (int c = 0; c < AS_CPT; c++) acc[r][c] = 0.f;
+            for (int k0 = 0; k0 < d; k0 += AS_KC) {
+                __syncthreads();
+                for (int e = t; e < AS_TC * AS_KC; e += 256) {
+                    const int c = e / AS_KC, kk = e % AS_KC;
+                    const int64_t j = j0 + c;
+                    cs[kk * AS_TC + c] = (j < k && k0 + kk < d) ? I.c32[j * d + k0 + kk] : 0.f;
+                }
+                if (k0 == 0 && t < AS_TC) cns[t] = j0 + t < k ? I.cn[j0 + t] : FLT_MAX;
+                __syncthreads();
+                const int kmax = min(AS_KC, d - k0);
+                for (int kk = 0; kk < kmax; kk++) {
+                    const float4 x0 = *reinterpret_cast<const float4 *>(&xs[(k0 + kk) * AS_TR + rg * AS_RPT]);
+                    const float4 x1 = *reinterpret_cast<const float4 *>(&xs[(k0 + kk) * AS_TR + rg * AS_RPT + 4]);
+                    const float4 cv = *reinterpret_cast<const float4 *>(&cs[kk * AS_TC + cg * AS_CPT]);
+                    const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+                    const float cc[4] = {cv.x, cv.y, cv.z, cv.w};
+#pragma unroll
+                    for (int r = 0; r < AS_RPT; r++)
+#pragma unroll
+                        for (int c = 0; c < AS_CPT; c++) acc[r][c] = fmaf(xv[r], cc[c], acc[r][c]);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < AS_CPT; c++) {
+                const int64_t j = j0 + cg * AS_CPT + c;
+                if (j >= k) continue;
+                const float cnj = cns[cg * AS_CPT + c];
+#pragma unroll
+                for (int r = 0; r < AS_RPT; r++) {
+                    const int rr = rg * AS_RPT + r;
+                    if (rr < nrows && fmaf(-2.f, acc[r][c], cnj) <= lim[r]) {
+                        const double D = ref_dist_strided(xs + rr, AS_TR, I.c64 + j * d, d);
+                        if (D < bD[r] || (D == bD[r] && (int)j < bj[r])) {
+                            bD[r] = D;
+                            bj[r] = (int)j;
+                        }
+                    }
+                }
+            }
+        }
+        // merge the 16 centre groups of each row (lanes of one half-warp)
+#pragma unroll
+        for (int r = 0; r < AS_RPT; r++) {
+#pragma unroll
+            for (int o = 1; o < 16; o <<= 1) {
+                const double D2 = __shfl_xor_sync(0xffffffffu, bD[r], o);
+                const int j2 = __shfl_xor_sync(0xffffffffu, bj[r], o);
+                if (D2 < bD[r] || (D2 == bD[r] && j2 < bj[r])) {
+                    bD[r] = D2;
+                    bj[r] = j2;
+                }
+            }
+        }
+        if (cg == 0) {
+#pragma unroll
+            for (int r = 0; r < AS_RPT; r++) {
+                const int rr = rg * AS_RPT + r;
+                if (rr < nrows) I.labels[s_rows[rr]] = bj[r] == 0x7FFFFFFF ? -1 : bj[r];
+            }
+        }
+    }
+}
+
+__global__ void k_scatter_m(const int32_t *__restrict__ rows, const float *__restrict__ m,
+                            const unsigned long long *__restrict__ n, float *__restrict__ mrow) {
+    const int64_t nf = (int64_t)*n;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nf; q += (int64_t)gridDim.x * blockDim.x)
+        mrow[rows[q]] = m[q];
+}
+
 // ---- grouping a flag list by instance (device-side, graph friendly) --------
 __global__ void k_flag_count(const int32_t *__restrict__ flags, const unsigned long long *__restrict__ n_flag,
                              const int64_t *__restrict__ row_off, int count, int *__restrict__ cnt) {
@@ -879,6 +1009,7 @@ geek_status decide_bufs_alloc(geek_ctx *ctx, Scratch *scr, int count, int64_t n_
     GK_TRY(al(&B.grows, std::max<int64_t>(n_total, 1)));
     GK_TRY(al(&B.flags2, std::max<int64_t>(n_total, 1)));
     GK_TRY(al(&B.flags2_m, std::max<int64_t>(n_total, 1)));
+    GK_TRY(al(&B.mrow, std::max<int64_t>(n_total, 1)));
     GK_TRY(al(&B.n_flag2, 1));
     return GEEK_OK;
 }
@@ -919,8 +1050,26 @@ geek_status decide_flags(geek_ctx *ctx, const RInst *R, const int64_t *row_off, 
     GatherUnits U{R, B.grows, B.unit_inst, B.unit_start, B.unit_cnt, B.n_units};
     GK_COUNT();
     k_assign_fp32<true><<<ctx->num_sms * 2, 256, smem, st>>>(A, U);
+    GK_LAUNCH(ctx);
+    // the rows still uncertain, grouped by instance again, go to the tiled
+    // FP64 decision with their smallest FP32 value
+    static bool attr64 = false;
+    if (!attr64) {
+        const size_t mx = (size_t)AS_MAXD * AS_TR * sizeof(float) + (size_t)AS_KC * AS_TC * sizeof(float);
+        GK_CUDA(ctx, cudaFuncSetAttribute(k_assign_decide64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
+        attr64 = true;
+    }
+    GK_CUDA(ctx, cudaMemsetAsync(B.cnt, 0, sizeof(int) * count, st));
     GK_COUNT();
-    k_assign_recheck<<<ctx->num_sms * 8, 256, 0, st>>>(R, row_off, count, B.flags2, B.flags2_m, B.n_flag2);
+    k_scatter_m<<<g, 256, 0, st>>>(B.flags2, B.flags2_m, B.n_flag2, B.mrow);
+    GK_COUNT();
+    k_flag_count<<<g, 256, 0, st>>>(B.flags2, B.n_flag2, row_off, count, B.cnt);
+    GK_COUNT();
+    k_flag_units<<<1, 1024, 0, st>>>(B.cnt, count, B.cursor, B.unit_inst, B.unit_start, B.unit_cnt, B.n_units);
+    GK_COUNT();
+    k_flag_scatter<<<g, 256, 0, st>>>(B.flags2, B.n_flag2, row_off, count, B.cursor, B.grows);
+    GK_COUNT();
+    k_assign_decide64<<<ctx->num_sms * 2, 256, smem, st>>>(U, B.mrow);
     GK_LAUNCH(ctx);
     return GEEK_OK;
 }

@@ -173,34 +173,13 @@ __global__ void k_centre_pairs(int64_t k, const int64_t *__restrict__ coff, cons
         for (int64_t p = coff[j]; p < coff[j + 1]; p++) pairs[p] = ((uint64_t)citems[p] << 32) | (uint64_t)j;
 }
 
-// heavy items: the H most frequent centre items get a bit each
-constexpr int HEAVY = 64;
 
 __global__ void k_item_key(int64_t m, const uint64_t *__restrict__ pairs, uint64_t *__restrict__ ikey) {
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += (int64_t)gridDim.x * blockDim.x)
         ikey[q] = pairs[q] >> 32;
 }
 
-// sort key ranking runs by posting length, longest first
-__global__ void k_len_key(int64_t nr, const int64_t *__restrict__ rs, uint64_t *__restrict__ key,
-                          uint32_t *__restrict__ val) {
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t len = (uint64_t)(rs[r + 1] - rs[r]);
-        key[r] = ((0xFFFFFFFFull - len) << 32) | (uint64_t)r;
-        val[r] = (uint32_t)r;
-    }
-}
 
-__global__ void k_mark_heavy(int nheavy, const uint32_t *__restrict__ order, const int64_t *__restrict__ rs,
-                             const uint64_t *__restrict__ ikey, int64_t *__restrict__ is_heavy,
-                             uint32_t *__restrict__ heavy) {
-    const int h = threadIdx.x;
-    if (h < nheavy) {
-        const uint32_t r = order[h];
-        is_heavy[r] = 1;
-        heavy[h] = (uint32_t)ikey[rs[r]];
-    }
-}
 
 __global__ void k_light_flags(int64_t nr, const int64_t *__restrict__ rs, const int64_t *__restrict__ is_heavy,
                               int64_t *__restrict__ lrun, int64_t *__restrict__ lent) {
@@ -323,210 +302,163 @@ __global__ void __launch_bounds__(256) k_assign_jaccard(
     }
 }
 
-// Light candidates of every set, warp per set.  The set's heavy items give
-// its bitmask; each light item's posting list adds one to its centres in a
-// per-warp open-addressing table in shared memory (keys: centre ids).  Every
-// centre in the table is then scored exactly, J = I / (|A| + |C| - I) with I
-// = table count + popcount(amask & cmask), and the warp keeps the best
-// (larger fraction, then smaller index).  A set with more than JT_MAXU
-// distinct candidates is listed for the dense path instead.
-constexpr int JT_SLOTS = 1024;               // per warp
-constexpr int JT_MAXU = JT_SLOTS / 2;        // distinct candidates kept (load <= 1/2)
-constexpr uint32_t JT_EMPTY = 0xFFFFFFFFu;
-constexpr int JT_WARPS = 4;                  // static shared memory stays under 48 KB
-constexpr int JT_HSLOTS = 256;               // heavy-item lookup table
+// Exact Jaccard argmax, tiled over the centres.  A block takes JX_S sets
+// (one warp each) and walks the centres in tiles of JX_KT; per tile, every
+// item of a set advances a cursor along its posting list (centres containing
+// the item, ascending) and adds one to the set's counter of each centre in
+// the tile (two 16-bit counters per shared-memory word).  The counters are
+// then |A n C_j| for every centre of the tile: J_j = I / (|A| + |C_j| - I) is
+// compared exactly (64-bit cross products), larger fraction then smaller
+// index; with no positive J the label is 0.  Sets with more than JX_MAXI
+// items are listed for the dense path.
+constexpr int JX_S = 8;
+constexpr int JX_KT = 4096;
+constexpr int JX_MAXI = 512;
+constexpr int JX_THREADS = 32 * JX_S;
+constexpr size_t JX_SMEM = (size_t)JX_S * (JX_KT / 2) * 4 + (size_t)2 * JX_S * JX_MAXI * 4;
 
-__global__ void __launch_bounds__(32 * JT_WARPS) k_jac_light(
-    int64_t n, const int64_t *__restrict__ off, const uint32_t *__restrict__ items, int na_fix,
-    const int32_t *__restrict__ clen, const uint64_t *__restrict__ cmask, const uint32_t *__restrict__ heavy,
-    int nheavy, const uint32_t *__restrict__ post_item, const int64_t *__restrict__ post_off, int64_t n_post_items,
-    const uint32_t *__restrict__ post_centre, uint64_t *__restrict__ amask_out, int64_t *__restrict__ best_num,
-    int64_t *__restrict__ best_den, int32_t *__restrict__ best_j, int32_t *__restrict__ ovf_rows,
-    unsigned long long *__restrict__ n_ovf) {
-    __shared__ uint32_t tkey[JT_WARPS][JT_SLOTS];
-    __shared__ uint32_t tcnt[JT_WARPS][JT_SLOTS];
-    __shared__ uint16_t tlist[JT_WARPS][JT_MAXU];
-    __shared__ uint32_t tnum[JT_WARPS];
-    __shared__ uint32_t hkey[JT_HSLOTS];
-    __shared__ int8_t hbit[JT_HSLOTS];
+__global__ void __launch_bounds__(JX_THREADS) k_jac_tiled(
+    int64_t n, const int64_t *__restrict__ off, const uint32_t *__restrict__ items, int na_fix, int64_t k,
+    const int32_t *__restrict__ clen, const uint32_t *__restrict__ post_item, const int64_t *__restrict__ post_off,
+    int64_t n_post_items, const uint32_t *__restrict__ post_centre, int32_t *__restrict__ labels,
+    int32_t *__restrict__ ovf_rows, unsigned long long *__restrict__ n_ovf) {
+    extern __shared__ uint32_t jx_smem[];
+    uint32_t *cnt = jx_smem;                                          // [S][KT / 2]
+    int32_t *cur = reinterpret_cast<int32_t *>(cnt + JX_S * (JX_KT / 2));  // [S][MAXI]
+    int32_t *cend = cur + JX_S * JX_MAXI;                             // [S][MAXI]
+    __shared__ int s_ni[JX_S];
+    __shared__ int64_t s_na[JX_S];
+    __shared__ int64_t r_n[JX_S][JX_S], r_d[JX_S][JX_S];
+    __shared__ int r_j[JX_S][JX_S];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int e = threadIdx.x; e < JT_HSLOTS; e += blockDim.x) {
-        hkey[e] = JT_EMPTY;
-        hbit[e] = -1;
-    }
-    for (int e = lane; e < JT_SLOTS; e += 32) {
-        tkey[w][e] = JT_EMPTY;
-        tcnt[w][e] = 0;
-    }
-    if (lane == 0) tnum[w] = 0;
-    __syncthreads();
-    if (threadIdx.x == 0)
-        for (int h = 0; h < nheavy; h++) {
-            uint32_t sl = (heavy[h] * 2654435761u) >> 24;
-            while (hkey[sl] != JT_EMPTY) sl = (sl + 1) & (JT_HSLOTS - 1);  // nheavy < JT_HSLOTS: a free slot exists
-            hkey[sl] = heavy[h];
-            hbit[sl] = (int8_t)h;
-        }
-    __syncthreads();
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = warp; i < n; i += nw) {
-        const int64_t s = off[i], e = off[i + 1];
-        const int64_t na = na_fix >= 0 ? na_fix : e - s;
-        uint64_t amask = 0;
-        for (int64_t p = s + lane; p < e; p += 32) {
-            const uint32_t it = items[p];
-            uint32_t sl = (it * 2654435761u) >> 24;
-            int hb = -1;
-            for (int probe = 0; probe < JT_HSLOTS; probe++) {
-                const uint32_t kk = hkey[sl];
-                if (kk == it) {
-                    hb = hbit[sl];
-                    break;
+    for (int e = threadIdx.x; e < JX_S * (JX_KT / 2); e += blockDim.x) cnt[e] = 0;
+    const int64_t ngroups = (n + JX_S - 1) / JX_S;
+    for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
+        // the warp's set: posting ranges of its items
+        const int64_t i = g * JX_S + w;
+        int ni = 0;
+        if (i < n) {
+            const int64_t s0 = off[i], e0 = off[i + 1];
+            ni = (int)min(e0 - s0, (int64_t)JX_MAXI + 1);
+            if (ni > JX_MAXI) {
+                if (lane == 0) ovf_rows[atomicAdd(n_ovf, 1ull)] = (int32_t)i;
+                ni = 0;
+            }
+            for (int p = lane; p < ni; p += 32) {
+                const uint32_t it = items[s0 + p];
+                int64_t lo = 0, hi = n_post_items;
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi) >> 1;
+                    if (post_item[mid] < it) lo = mid + 1;
+                    else hi = mid;
                 }
-                if (kk == JT_EMPTY) break;
-                sl = (sl + 1) & (JT_HSLOTS - 1);
+                const bool f = lo < n_post_items && post_item[lo] == it;
+                cur[w * JX_MAXI + p] = f ? (int32_t)post_off[lo] : 0;
+                cend[w * JX_MAXI + p] = f ? (int32_t)post_off[lo + 1] : 0;
             }
-            if (hb >= 0) {
-                amask |= 1ull << hb;
-                continue;
+            if (lane == 0) {
+                s_ni[w] = ni;
+                s_na[w] = na_fix >= 0 ? na_fix : e0 - s0;
             }
-            int64_t lo = 0, hi = n_post_items;
-            while (lo < hi) {
-                const int64_t mid = (lo + hi) >> 1;
-                if (post_item[mid] < it) lo = mid + 1;
-                else hi = mid;
-            }
-            if (lo < n_post_items && post_item[lo] == it)
-                for (int64_t q = post_off[lo]; q < post_off[lo + 1]; q++) {
-                    // once the table holds more than JT_MAXU centres the set
-                    // goes to the dense path: stop counting
-                    if (*(volatile uint32_t *)&tnum[w] > JT_MAXU) break;
-                    const uint32_t c = post_centre[q];
-                    uint32_t h = (c * 2654435761u) >> 22;  // 10 bits: JT_SLOTS
-                    bool placed = false;
-                    for (int probe = 0; probe < 64; probe++) {
-                        const uint32_t old = atomicCAS(&tkey[w][h], JT_EMPTY, c);
-                        if (old == JT_EMPTY || old == c) {
-                            atomicAdd(&tcnt[w][h], 1u);
-                            if (old == JT_EMPTY) {
-                                const uint32_t pos = atomicAdd(&tnum[w], 1u);
-                                if (pos < JT_MAXU) tlist[w][pos] = (uint16_t)h;
-                            }
-                            placed = true;
-                            break;
-                        }
-                        h = (h + 1) & (JT_SLOTS - 1);
-                    }
-                    if (!placed) atomicMax(&tnum[w], (uint32_t)JT_MAXU + 1);  // long probe: overflow
-                }
+        } else if (lane == 0) {
+            s_ni[w] = 0;
+            s_na[w] = 0;
         }
+        __syncthreads();
+        int64_t bn[JX_S], bd[JX_S];
+        int bj[JX_S];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) amask |= __shfl_xor_sync(0xffffffffu, amask, o);
-        __syncwarp();
-        const uint32_t nu = tnum[w];
-        int64_t bn = 0, bd = 1;
-        int bj = 0x7FFFFFFF;
-        if (nu > JT_MAXU) {  // too many candidates: the dense path decides this set
-            for (int e2 = lane; e2 < JT_SLOTS; e2 += 32) {
-                tkey[w][e2] = JT_EMPTY;
-                tcnt[w][e2] = 0;
+        for (int q = 0; q < JX_S; q++) {
+            bn[q] = 0;
+            bd[q] = 1;
+            bj[q] = 0x7FFFFFFF;
+        }
+        for (int64_t c0 = 0; c0 < k; c0 += JX_KT) {
+            const int64_t c1 = min(k, c0 + JX_KT);
+            // counting: lanes walk consecutive entries of one posting list
+            const int niw = s_ni[w];
+            uint32_t *cw = cnt + w * (JX_KT / 2);
+            for (int q = 0; q < niw; q++) {
+                int32_t pos = cur[w * JX_MAXI + q];
+                const int32_t end = cend[w * JX_MAXI + q];
+                while (pos < end) {
+                    const int32_t p = pos + lane;
+                    const int64_t c = p < end ? (int64_t)post_centre[p] : INT64_MAX;
+                    const bool in = c < c1;
+                    if (in) {
+                        const int cc = (int)(c - c0);
+                        atomicAdd(&cw[cc >> 1], 1u << ((cc & 1) << 4));
+                    }
+                    const int nin = __popc(__ballot_sync(0xffffffffu, in));
+                    pos += nin;  // the list is ascending: the counted lanes are a prefix
+                    if (nin < 32) break;
+                }
+                if (lane == 0) cur[w * JX_MAXI + q] = pos;
+                __syncwarp();
             }
-            if (lane == 0) ovf_rows[atomicAdd(n_ovf, 1ull)] = (int32_t)i;
-        } else {
-            for (uint32_t q = lane; q < nu; q += 32) {
-                const int sl = tlist[w][q];
-                const uint32_t c = tkey[w][sl];
-                const int64_t in = (int64_t)tcnt[w][sl] + __popcll(amask & cmask[c]);
-                tkey[w][sl] = JT_EMPTY;
-                tcnt[w][sl] = 0;
-                const int64_t un = na + clen[c] - in;
-                if (un > 0 && (in * bd > bn * un || (in * bd == bn * un && (int)c < bj))) {
-                    bn = in;
-                    bd = un;
-                    bj = (int)c;
+            __syncthreads();
+            // scoring: thread per centre of the tile, all JX_S sets
+            for (int cc = threadIdx.x; cc < (int)(c1 - c0); cc += blockDim.x) {
+                const int64_t c = c0 + cc;
+                const int64_t cl = clen[c];
+#pragma unroll
+                for (int q = 0; q < JX_S; q++) {
+                    const int64_t in = (cnt[q * (JX_KT / 2) + (cc >> 1)] >> ((cc & 1) << 4)) & 0xFFFFu;
+                    if (in) {
+                        const int64_t un = s_na[q] + cl - in;
+                        const int64_t l = in * bd[q], r = bn[q] * un;
+                        if (l > r || (l == r && (int)c < bj[q])) {
+                            bn[q] = in;
+                            bd[q] = un;
+                            bj[q] = (int)c;
+                        }
+                    }
                 }
             }
+            __syncthreads();
+            for (int e = threadIdx.x; e < JX_S * (JX_KT / 2); e += blockDim.x) cnt[e] = 0;
+            __syncthreads();
+        }
+        // per set: reduce the threads' bests (warp, then across warps)
+#pragma unroll
+        for (int q = 0; q < JX_S; q++) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                const int64_t on = __shfl_xor_sync(0xffffffffu, bn, o);
-                const int64_t od = __shfl_xor_sync(0xffffffffu, bd, o);
-                const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
-                const int64_t l = on * bd, r = bn * od;
-                if (l > r || (l == r && oj < bj)) {
-                    bn = on;
-                    bd = od;
-                    bj = oj;
+                const int64_t on = __shfl_xor_sync(0xffffffffu, bn[q], o);
+                const int64_t od = __shfl_xor_sync(0xffffffffu, bd[q], o);
+                const int oj = __shfl_xor_sync(0xffffffffu, bj[q], o);
+                const int64_t l = on * bd[q], r = bn[q] * od;
+                if (l > r || (l == r && oj < bj[q])) {
+                    bn[q] = on;
+                    bd[q] = od;
+                    bj[q] = oj;
                 }
             }
-        }
-        __syncwarp();
-        if (lane == 0) {
-            tnum[w] = 0;
-            amask_out[i] = amask;
-            best_num[i] = bn;
-            best_den[i] = bd;
-            best_j[i] = bj;
-        }
-        __syncwarp();
-    }
-}
-
-// Heavy-only scores and the label, thread per set.  Centres are grouped by
-// their heavy bitmask; within a group the best heavy-only score belongs to
-// the smallest |C| (then the smallest index), so one representative per
-// group suffices.  A heavy-only score never exceeds the exact one, so the
-// larger of this scan and the light candidates' exact best (ties to the
-// smaller index) is the exact argmax; with no positive score the label is 0.
-constexpr int JG_TILE = 2048;
-
-__global__ void __launch_bounds__(256) k_jac_heavy(int64_t n, const int64_t *__restrict__ off, int na_fix,
-                                                   int64_t G, const uint64_t *__restrict__ gmask,
-                                                   const int32_t *__restrict__ gcmin, const int32_t *__restrict__ gj,
-                                                   const uint64_t *__restrict__ amask_in,
-                                                   const int64_t *__restrict__ best_num,
-                                                   const int64_t *__restrict__ best_den,
-                                                   const int32_t *__restrict__ best_j, int32_t *__restrict__ labels) {
-    __shared__ uint64_t sm[JG_TILE];
-    __shared__ int32_t sc[JG_TILE], sj[JG_TILE];
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = i < n;
-    int64_t bn = 0, bd = 1, na = 0;
-    int bj = 0;
-    uint64_t am = 0;
-    if (live) {
-        na = na_fix >= 0 ? na_fix : off[i + 1] - off[i];
-        am = amask_in[i];
-        if (best_j[i] != 0x7FFFFFFF && best_num[i] > 0) {
-            bn = best_num[i];
-            bd = best_den[i];
-            bj = best_j[i];
-        }
-    }
-    for (int64_t g0 = 0; g0 < G; g0 += JG_TILE) {
-        const int tn = (int)min((int64_t)JG_TILE, G - g0);
-        __syncthreads();
-        for (int e = threadIdx.x; e < tn; e += blockDim.x) {
-            sm[e] = gmask[g0 + e];
-            sc[e] = gcmin[g0 + e];
-            sj[e] = gj[g0 + e];
+            if (lane == 0) {
+                r_n[q][w] = bn[q];
+                r_d[q][w] = bd[q];
+                r_j[q][w] = bj[q];
+            }
         }
         __syncthreads();
-        if (live && am)
-            for (int e = 0; e < tn; e++) {
-                const uint64_t x = am & sm[e];
-                if (!x) continue;
-                const int64_t h = __popcll(x);
-                const int64_t un = na + sc[e] - h;
-                const int64_t l = h * bd, r = bn * un;
-                if (l > r || (l == r && sj[e] < bj)) {
-                    bn = h;
-                    bd = un;
-                    bj = sj[e];
+        if (threadIdx.x < JX_S) {
+            const int q = threadIdx.x;
+            int64_t n0 = 0, d0 = 1;
+            int j0 = 0x7FFFFFFF;
+            for (int v = 0; v < JX_S; v++) {
+                const int64_t l = r_n[q][v] * d0, r = n0 * r_d[q][v];
+                if (l > r || (l == r && r_j[q][v] < j0)) {
+                    n0 = r_n[q][v];
+                    d0 = r_d[q][v];
+                    j0 = r_j[q][v];
                 }
             }
+            const int64_t ii = g * JX_S + q;
+            // no positive J: every fraction is 0 and the smallest index wins
+            if (ii < n) labels[ii] = (n0 > 0 && j0 != 0x7FFFFFFF) ? j0 : 0;
+        }
+        __syncthreads();
     }
-    if (live) labels[i] = bj;
 }
 
 }  // namespace
@@ -707,7 +639,7 @@ geek_status jaccard_core(geek_ctx *ctx, Scratch &scr, const int64_t *off, const 
                          int na_fix, int64_t k, const int64_t *coff, const uint32_t *citems, int64_t nci,
                          int32_t *labels, geek_assign_stats *stats, cudaStream_t st) {
     // inverted index item -> centres: pairs sorted by (item, centre), runs of
-    // equal items; the HEAVY longest posting lists become bitmask items
+    // equal items, one posting list (ascending centres) per distinct item
     uint64_t *pairs, *ikey;
     GK_TRY(scr.alloc(&pairs, std::max<int64_t>(nci, 1)));
     GK_TRY(scr.alloc(&ikey, std::max<int64_t>(nci, 1)));
@@ -725,16 +657,9 @@ geek_status jaccard_core(geek_ctx *ctx, Scratch &scr, const int64_t *off, const 
     int64_t ni = 0;
     GK_CUDA(ctx, cudaMemcpyAsync(&ni, nr_dev, 8, cudaMemcpyDeviceToHost, st));
     GK_CUDA(ctx, cudaStreamSynchronize(st));
-    // rank runs by posting length (longest first, then item order)
-    uint64_t *lkey;
-    uint32_t *lval;
-    GK_TRY(scr.alloc(&lkey, std::max<int64_t>(ni, 1)));
-    GK_TRY(scr.alloc(&lval, std::max<int64_t>(ni, 1)));
-    GK_COUNT();
-    k_len_key<<<G(ctx, ni), 256, 0, st>>>(ni, rs, lkey, lval);
-    GK_LAUNCH(ctx);
-    GK_TRY(radix_sort_segments(ctx, scr, 1, ni, &lkey, nullptr, &lval, 64, st));
-    const int nheavy = (int)std::min<int64_t>(HEAVY, ni);
+    // every item keeps its posting list (no bitmask items on the tiled path)
+    uint32_t *lval = nullptr;
+    const int nheavy = 0;
     uint32_t *d_heavy, *d_litem, *d_lcentre;
     int64_t *is_heavy, *lrun, *lrun_pos, *lent, *lent_pos, *d_loff, *nlight, *nlent;
     GK_TRY(scr.alloc(&d_heavy, std::max(1, nheavy)));
@@ -746,8 +671,7 @@ geek_status jaccard_core(geek_ctx *ctx, Scratch &scr, const int64_t *off, const 
     GK_TRY(scr.alloc(&nlight, 1));
     GK_TRY(scr.alloc(&nlent, 1));
     GK_CUDA(ctx, cudaMemsetAsync(is_heavy, 0, 8 * std::max<int64_t>(ni, 1), st));
-    GK_COUNT();
-    k_mark_heavy<<<1, 64, 0, st>>>(nheavy, lval, rs, ikey, is_heavy, d_heavy);
+    (void)lval;
     GK_COUNT();
     k_light_flags<<<G(ctx, ni), 256, 0, st>>>(ni, rs, is_heavy, lrun, lent);
     GK_LAUNCH(ctx);
@@ -771,55 +695,23 @@ geek_status jaccard_core(geek_ctx *ctx, Scratch &scr, const int64_t *off, const 
     GK_COUNT();
     k_heavy_masks<<<G(ctx, k), 256, 0, st>>>(k, coff, citems, d_heavy, nheavy, cmask, clen);
     GK_LAUNCH(ctx);
-    // centres grouped by heavy bitmask: one representative per group, the
-    // smallest |C| then the smallest index (host sort; k is small)
-    std::vector<uint64_t> hm(k);
-    std::vector<int32_t> hl(k);
-    GK_CUDA(ctx, cudaMemcpyAsync(hm.data(), cmask, 8 * k, cudaMemcpyDeviceToHost, st));
-    GK_CUDA(ctx, cudaMemcpyAsync(hl.data(), clen, 4 * k, cudaMemcpyDeviceToHost, st));
-    GK_CUDA(ctx, cudaStreamSynchronize(st));
-    std::vector<int32_t> ord(k);
-    for (int64_t j = 0; j < k; j++) ord[j] = (int32_t)j;
-    std::sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) {
-        if (hm[a] != hm[b]) return hm[a] < hm[b];
-        if (hl[a] != hl[b]) return hl[a] < hl[b];
-        return a < b;
-    });
-    std::vector<uint64_t> gmh;
-    std::vector<int32_t> gch, gjh;
-    for (int64_t q = 0; q < k; q++)
-        if (q == 0 || hm[ord[q]] != hm[ord[q - 1]]) {
-            gmh.push_back(hm[ord[q]]);
-            gch.push_back(hl[ord[q]]);
-            gjh.push_back(ord[q]);
-        }
-    const int64_t G = (int64_t)gmh.size();
-    uint64_t *gmask, *amask;
-    int32_t *gcmin, *gj, *bj, *ovf;
-    int64_t *bnum, *bden;
+    if (nci > 0x7FFFFFFFLL) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "more than 2^31 centre items");
+    int32_t *ovf;
     unsigned long long *n_ovf;
-    GK_TRY(scr.alloc(&gmask, G));
-    GK_TRY(scr.alloc(&gcmin, G));
-    GK_TRY(scr.alloc(&gj, G));
-    GK_TRY(scr.alloc(&amask, n));
-    GK_TRY(scr.alloc(&bnum, n));
-    GK_TRY(scr.alloc(&bden, n));
-    GK_TRY(scr.alloc(&bj, n));
     GK_TRY(scr.alloc(&ovf, n));
     GK_TRY(scr.alloc(&n_ovf, 1));
-    GK_CUDA(ctx, cudaMemcpyAsync(gmask, gmh.data(), 8 * G, cudaMemcpyHostToDevice, st));
-    GK_CUDA(ctx, cudaMemcpyAsync(gcmin, gch.data(), 4 * G, cudaMemcpyHostToDevice, st));
-    GK_CUDA(ctx, cudaMemcpyAsync(gj, gjh.data(), 4 * G, cudaMemcpyHostToDevice, st));
     GK_CUDA(ctx, cudaMemsetAsync(n_ovf, 0, sizeof(unsigned long long), st));
     {
+        static bool attr = false;
+        if (!attr) {
+            GK_CUDA(ctx, cudaFuncSetAttribute(k_jac_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)JX_SMEM));
+            attr = true;
+        }
         EvTimer tk(ctx, "kernel.jaccard", st);
+        tk.work = (double)n * (double)k;  // (set, centre) pairs scored
         GK_COUNT();
-        k_jac_light<<<ctx->num_sms * 8, 32 * JT_WARPS, 0, st>>>(n, off, items, na_fix, clen, cmask, d_heavy, nheavy,
-                                                               d_litem, d_loff, h_nlight, d_lcentre, amask, bnum,
-                                                               bden, bj, ovf, n_ovf);
-        GK_COUNT();
-        k_jac_heavy<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(n, off, na_fix, G, gmask, gcmin, gj, amask, bnum,
-                                                                bden, bj, labels);
+        k_jac_tiled<<<(unsigned)std::min<int64_t>(ceil_div(n, JX_S), (int64_t)ctx->num_sms * 2), JX_THREADS, JX_SMEM,
+                      st>>>(n, off, items, na_fix, k, clen, d_litem, d_loff, h_nlight, d_lcentre, labels, ovf, n_ovf);
         GK_LAUNCH(ctx);
     }
     unsigned long long h_ovf = 0;

@@ -295,6 +295,7 @@ struct DecideBufs {
     int32_t *grows = nullptr;      // flagged rows grouped by instance
     int32_t *flags2 = nullptr;     // rows left to the FP64 reference
     float *flags2_m = nullptr;     // their smallest FP32 value (NaN: none)
+    float *mrow = nullptr;         // the same value by global row
     unsigned long long *n_flag2 = nullptr;
     std::vector<void *> owned;
 };
