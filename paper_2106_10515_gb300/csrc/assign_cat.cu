@@ -304,9 +304,10 @@ __global__ void __launch_bounds__(256) k_assign_jaccard(
 
 // Exact Jaccard argmax, tiled over the centres.  A block takes JX_S sets
 // (one warp each) and walks the centres in tiles of JX_KT; per tile, every
-// item of a set advances a cursor along its posting list (centres containing
-// the item, ascending) and adds one to the set's counter of each centre in
-// the tile (two 16-bit counters per shared-memory word).  The counters are
+// item of a set reads the part of its posting list (centres containing the
+// item, ascending) that falls in the tile, found from precomputed per-tile
+// offsets, and adds one to the set's counter of each centre there (two
+// 16-bit counters per shared-memory word).  The counters are
 // then |A n C_j| for every centre of the tile: J_j = I / (|A| + |C_j| - I) is
 // compared exactly (64-bit cross products), larger fraction then smaller
 // index; with no positive J the label is 0.  Sets with more than JX_MAXI
@@ -315,17 +316,35 @@ constexpr int JX_S = 8;
 constexpr int JX_KT = 4096;
 constexpr int JX_MAXI = 512;
 constexpr int JX_THREADS = 32 * JX_S;
-constexpr size_t JX_SMEM = (size_t)JX_S * (JX_KT / 2) * 4 + (size_t)2 * JX_S * JX_MAXI * 4;
+constexpr size_t JX_SMEM = (size_t)JX_S * (JX_KT / 2) * 4 + (size_t)JX_S * JX_MAXI * 4;
+
+// tile_off[r * (ntiles + 1) + t]: the first entry of posting list r whose
+// centre is in tile t or later (ntiles + 1 entries per list)
+__global__ void k_tile_offsets(int64_t nr, const int64_t *__restrict__ post_off,
+                               const uint32_t *__restrict__ post_centre, int ntiles, int32_t *__restrict__ tile_off) {
+    const int64_t tot = nr * (ntiles + 1);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / (ntiles + 1);
+        const int t = (int)(e % (ntiles + 1));
+        const uint64_t lim = (uint64_t)t * JX_KT;
+        int64_t lo = post_off[r], hi = post_off[r + 1];
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((uint64_t)post_centre[mid] < lim) lo = mid + 1;
+            else hi = mid;
+        }
+        tile_off[e] = (int32_t)lo;
+    }
+}
 
 __global__ void __launch_bounds__(JX_THREADS) k_jac_tiled(
     int64_t n, const int64_t *__restrict__ off, const uint32_t *__restrict__ items, int na_fix, int64_t k,
-    const int32_t *__restrict__ clen, const uint32_t *__restrict__ post_item, const int64_t *__restrict__ post_off,
-    int64_t n_post_items, const uint32_t *__restrict__ post_centre, int32_t *__restrict__ labels,
+    const int32_t *__restrict__ clen, const uint32_t *__restrict__ post_item, const int32_t *__restrict__ tile_off,
+    int ntiles, int64_t n_post_items, const uint32_t *__restrict__ post_centre, int32_t *__restrict__ labels,
     int32_t *__restrict__ ovf_rows, unsigned long long *__restrict__ n_ovf) {
     extern __shared__ uint32_t jx_smem[];
     uint32_t *cnt = jx_smem;                                          // [S][KT / 2]
-    int32_t *cur = reinterpret_cast<int32_t *>(cnt + JX_S * (JX_KT / 2));  // [S][MAXI]
-    int32_t *cend = cur + JX_S * JX_MAXI;                             // [S][MAXI]
+    int32_t *ridx = reinterpret_cast<int32_t *>(cnt + JX_S * (JX_KT / 2));  // [S][MAXI]: posting list of each item
     __shared__ int s_ni[JX_S];
     __shared__ int64_t s_na[JX_S];
     __shared__ int64_t r_n[JX_S][JX_S], r_d[JX_S][JX_S];
@@ -353,8 +372,7 @@ __global__ void __launch_bounds__(JX_THREADS) k_jac_tiled(
                     else hi = mid;
                 }
                 const bool f = lo < n_post_items && post_item[lo] == it;
-                cur[w * JX_MAXI + p] = f ? (int32_t)post_off[lo] : 0;
-                cend[w * JX_MAXI + p] = f ? (int32_t)post_off[lo + 1] : 0;
+                ridx[w * JX_MAXI + p] = f ? (int32_t)lo : -1;
             }
             if (lane == 0) {
                 s_ni[w] = ni;
@@ -378,24 +396,20 @@ __global__ void __launch_bounds__(JX_THREADS) k_jac_tiled(
             // counting: lanes walk consecutive entries of one posting list
             const int niw = s_ni[w];
             uint32_t *cw = cnt + w * (JX_KT / 2);
+            const int t = (int)(c0 / JX_KT);
             for (int q = 0; q < niw; q++) {
-                int32_t pos = cur[w * JX_MAXI + q];
-                const int32_t end = cend[w * JX_MAXI + q];
-                while (pos < end) {
-                    const int32_t p = pos + lane;
-                    const int64_t c = p < end ? (int64_t)post_centre[p] : INT64_MAX;
-                    const bool in = c < c1;
-                    if (in) {
-                        const int cc = (int)(c - c0);
-                        atomicAdd(&cw[cc >> 1], 1u << ((cc & 1) << 4));
-                    }
-                    const int nin = __popc(__ballot_sync(0xffffffffu, in));
-                    pos += nin;  // the list is ascending: the counted lanes are a prefix
-                    if (nin < 32) break;
+                const int32_t r = ridx[w * JX_MAXI + q];
+                if (r < 0) continue;
+                const int32_t ps = tile_off[(int64_t)r * (ntiles + 1) + t];
+                const int32_t pe = tile_off[(int64_t)r * (ntiles + 1) + t + 1];
+                // independent loads: every entry of the range is in this tile
+#pragma unroll 4
+                for (int32_t p = ps + lane; p < pe; p += 32) {
+                    const int cc = (int)((int64_t)post_centre[p] - c0);
+                    atomicAdd(&cw[cc >> 1], 1u << ((cc & 1) << 4));
                 }
-                if (lane == 0) cur[w * JX_MAXI + q] = pos;
-                __syncwarp();
             }
+            __syncwarp();
             __syncthreads();
             // scoring: thread per centre of the tile, all JX_S sets
             for (int cc = threadIdx.x; cc < (int)(c1 - c0); cc += blockDim.x) {
@@ -707,11 +721,17 @@ geek_status jaccard_core(geek_ctx *ctx, Scratch &scr, const int64_t *off, const 
             GK_CUDA(ctx, cudaFuncSetAttribute(k_jac_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)JX_SMEM));
             attr = true;
         }
+        const int ntiles = (int)ceil_div(k, JX_KT);
+        int32_t *toff;
+        GK_TRY(scr.alloc(&toff, (size_t)std::max<int64_t>(h_nlight, 1) * (ntiles + 1)));
+        GK_COUNT();
+        k_tile_offsets<<<G(ctx, h_nlight * (ntiles + 1)), 256, 0, st>>>(h_nlight, d_loff, d_lcentre, ntiles, toff);
         EvTimer tk(ctx, "kernel.jaccard", st);
         tk.work = (double)n * (double)k;  // (set, centre) pairs scored
         GK_COUNT();
-        k_jac_tiled<<<(unsigned)std::min<int64_t>(ceil_div(n, JX_S), (int64_t)ctx->num_sms * 2), JX_THREADS, JX_SMEM,
-                      st>>>(n, off, items, na_fix, k, clen, d_litem, d_loff, h_nlight, d_lcentre, labels, ovf, n_ovf);
+        k_jac_tiled<<<(unsigned)std::min<int64_t>(ceil_div(n, JX_S), (int64_t)ctx->num_sms * 3), JX_THREADS, JX_SMEM,
+                      st>>>(n, off, items, na_fix, k, clen, d_litem, toff, ntiles, h_nlight, d_lcentre, labels, ovf,
+                            n_ovf);
         GK_LAUNCH(ctx);
     }
     unsigned long long h_ovf = 0;
