@@ -316,7 +316,7 @@ constexpr int JX_S = 8;
 constexpr int JX_KT = 4096;
 constexpr int JX_MAXI = 512;
 constexpr int JX_THREADS = 32 * JX_S;
-constexpr size_t JX_SMEM = (size_t)JX_S * (JX_KT / 2) * 4 + (size_t)JX_S * JX_MAXI * 4;
+constexpr size_t JX_SMEM = (size_t)JX_S * (JX_KT / 2) * 4 + (size_t)JX_S * JX_MAXI * (4 + 4 + 2);
 
 // tile_off[r * (ntiles + 1) + t]: the first entry of posting list r whose
 // centre is in tile t or later (ntiles + 1 entries per list)
@@ -345,6 +345,8 @@ __global__ void __launch_bounds__(JX_THREADS) k_jac_tiled(
     extern __shared__ uint32_t jx_smem[];
     uint32_t *cnt = jx_smem;                                          // [S][KT / 2]
     int32_t *ridx = reinterpret_cast<int32_t *>(cnt + JX_S * (JX_KT / 2));  // [S][MAXI]: posting list of each item
+    int32_t *rps = ridx + JX_S * JX_MAXI;                                  // [S][MAXI]: its range in the tile
+    uint16_t *rlen = reinterpret_cast<uint16_t *>(rps + JX_S * JX_MAXI);   // [S][MAXI]
     __shared__ int s_ni[JX_S];
     __shared__ int64_t s_na[JX_S];
     __shared__ int64_t r_n[JX_S][JX_S], r_d[JX_S][JX_S];
@@ -397,15 +399,36 @@ __global__ void __launch_bounds__(JX_THREADS) k_jac_tiled(
             const int niw = s_ni[w];
             uint32_t *cw = cnt + w * (JX_KT / 2);
             const int t = (int)(c0 / JX_KT);
-            for (int q = 0; q < niw; q++) {
+            // the items' ranges in this tile, lane per item (independent loads)
+            for (int q = lane; q < niw; q += 32) {
                 const int32_t r = ridx[w * JX_MAXI + q];
-                if (r < 0) continue;
-                const int32_t ps = tile_off[(int64_t)r * (ntiles + 1) + t];
-                const int32_t pe = tile_off[(int64_t)r * (ntiles + 1) + t + 1];
-                // independent loads: every entry of the range is in this tile
+                int32_t ps = 0, pe = 0;
+                if (r >= 0) {
+                    ps = tile_off[(int64_t)r * (ntiles + 1) + t];
+                    pe = tile_off[(int64_t)r * (ntiles + 1) + t + 1];
+                }
+                rps[w * JX_MAXI + q] = ps;
+                rlen[w * JX_MAXI + q] = (uint16_t)(pe - ps);
+            }
+            __syncwarp();
+            // short ranges: a lane walks one item's entries
+            for (int q = lane; q < niw; q += 32) {
+                const int len = rlen[w * JX_MAXI + q];
+                if (len == 0 || len >= 32) continue;
+                const int32_t ps = rps[w * JX_MAXI + q];
+                for (int e = 0; e < len; e++) {
+                    const int cc = (int)((int64_t)post_centre[ps + e] - c0);
+                    atomicAdd(&cw[cc >> 1], 1u << ((cc & 1) << 4));
+                }
+            }
+            // long ranges: the warp walks one item's entries, lane per entry
+            for (int q = 0; q < niw; q++) {
+                const int len = rlen[w * JX_MAXI + q];
+                if (len < 32) continue;
+                const int32_t ps = rps[w * JX_MAXI + q];
 #pragma unroll 4
-                for (int32_t p = ps + lane; p < pe; p += 32) {
-                    const int cc = (int)((int64_t)post_centre[p] - c0);
+                for (int p = lane; p < len; p += 32) {
+                    const int cc = (int)((int64_t)post_centre[ps + p] - c0);
                     atomicAdd(&cw[cc >> 1], 1u << ((cc & 1) << 4));
                 }
             }
