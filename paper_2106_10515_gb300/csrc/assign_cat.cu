@@ -166,6 +166,10 @@ __global__ void k_group_emit(const int64_t *__restrict__ nruns, const int64_t *_
         if (keep[r]) out[pos[r]] = (uint32_t)(pairs[prs[r]] & 0xFFFFFFFFu);
 }
 
+// heavy items: up to 64 * JX_HW of the items with the longest posting lists
+// are counted by bitmasks instead of posting lists
+constexpr int JX_HW = 4;
+
 // item -> centres inverted index helpers
 __global__ void k_centre_pairs(int64_t k, const int64_t *__restrict__ coff, const uint32_t *__restrict__ citems,
                                uint64_t *__restrict__ pairs) {
@@ -206,15 +210,36 @@ __global__ void k_light_emit(int64_t nr, const int64_t *__restrict__ rs, const u
     if (blockIdx.x == 0 && threadIdx.x == 0) loff[nlight] = *nlent;
 }
 
+// item of each listed run (first entry's key)
+__global__ void k_run_items(int nh, const int64_t *__restrict__ runs, const int64_t *__restrict__ rs,
+                            const uint64_t *__restrict__ ikey, uint32_t *__restrict__ out) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nh; q += gridDim.x * blockDim.x)
+        out[q] = (uint32_t)ikey[rs[runs[q]]];
+}
+
+// heavy items: bit b of the HW-word mask stands for the item hv_item[i] with
+// hv_bit[i] = b (hv_item ascending); -1 when x is not heavy
+__device__ __forceinline__ int heavy_bit(uint32_t x, const uint32_t *__restrict__ hv_item,
+                                         const int16_t *__restrict__ hv_bit, int nheavy) {
+    int lo = 0, hi = nheavy;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (hv_item[mid] < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < nheavy && hv_item[lo] == x) ? hv_bit[lo] : -1;
+}
+
 __global__ void k_heavy_masks(int64_t k, const int64_t *__restrict__ coff, const uint32_t *__restrict__ citems,
-                              const uint32_t *__restrict__ heavy, int nheavy, uint64_t *__restrict__ cmask,
-                              int32_t *__restrict__ clen) {
+                              const uint32_t *__restrict__ hv_item, const int16_t *__restrict__ hv_bit, int nheavy,
+                              int HW, uint64_t *__restrict__ cmask, int32_t *__restrict__ clen) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t m = 0;
-        for (int64_t p = coff[j]; p < coff[j + 1]; p++)
-            for (int h = 0; h < nheavy; h++)
-                if (citems[p] == heavy[h]) m |= 1ull << h;
-        cmask[j] = m;
+        uint64_t m[JX_HW] = {0, 0, 0, 0};
+        for (int64_t p = coff[j]; p < coff[j + 1]; p++) {
+            const int b = heavy_bit(citems[p], hv_item, hv_bit, nheavy);
+            if (b >= 0) m[b >> 6] |= 1ull << (b & 63);
+        }
+        for (int w = 0; w < HW; w++) cmask[j * HW + w] = m[w];
         clen[j] = (int32_t)(coff[j + 1] - coff[j]);
     }
 }
@@ -228,10 +253,11 @@ __global__ void k_heavy_masks(int64_t k, const int64_t *__restrict__ coff, const
 // rows lists them, na_fix >= 0 replaces |A| by a fixed size.)
 __global__ void __launch_bounds__(256) k_assign_jaccard(
     int64_t n, const int64_t *__restrict__ off, const uint32_t *__restrict__ items, int64_t k,
-    const int32_t *__restrict__ clen, const uint64_t *__restrict__ cmask, const uint32_t *__restrict__ heavy,
-    int nheavy, const uint32_t *__restrict__ post_item, const int64_t *__restrict__ post_off, int64_t n_post_items,
-    const uint32_t *__restrict__ post_centre, int32_t *__restrict__ counts, int32_t *__restrict__ labels,
-    const int32_t *__restrict__ rows, const unsigned long long *__restrict__ n_rows, int na_fix) {
+    const int32_t *__restrict__ clen, const uint64_t *__restrict__ cmask, const uint32_t *__restrict__ hv_item,
+    const int16_t *__restrict__ hv_bit, int nheavy, int HW, const uint32_t *__restrict__ post_item,
+    const int64_t *__restrict__ post_off, int64_t n_post_items, const uint32_t *__restrict__ post_centre,
+    int32_t *__restrict__ counts, int32_t *__restrict__ labels, const int32_t *__restrict__ rows,
+    const unsigned long long *__restrict__ n_rows, int na_fix) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -241,17 +267,15 @@ __global__ void __launch_bounds__(256) k_assign_jaccard(
         const int64_t i = rows ? (int64_t)rows[ii] : ii;
         const int64_t s = off[i], e = off[i + 1];
         const int64_t na = na_fix >= 0 ? na_fix : e - s;
-        uint64_t amask = 0;
+        uint64_t am[JX_HW] = {0, 0, 0, 0};
         // light items: binary search in the sorted item list of the index
         for (int64_t p = s + lane; p < e; p += 32) {
             const uint32_t it = items[p];
-            bool hv = false;
-            for (int h = 0; h < nheavy; h++)
-                if (heavy[h] == it) {
-                    amask |= 1ull << h;
-                    hv = true;
-                }
-            if (hv) continue;
+            const int hb = heavy_bit(it, hv_item, hv_bit, nheavy);
+            if (hb >= 0) {
+                am[hb >> 6] |= 1ull << (hb & 63);
+                continue;
+            }
             int64_t lo = 0, hi = n_post_items;
             while (lo < hi) {
                 const int64_t mid = (lo + hi) >> 1;
@@ -262,13 +286,16 @@ __global__ void __launch_bounds__(256) k_assign_jaccard(
                 for (int64_t q = post_off[lo]; q < post_off[lo + 1]; q++) atomicAdd(&cnt[post_centre[q]], 1);
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) amask |= __shfl_xor_sync(0xffffffffu, amask, o);
+        for (int w = 0; w < JX_HW; w++)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) am[w] |= __shfl_xor_sync(0xffffffffu, am[w], o);
         __syncwarp();
         __threadfence_block();
         int64_t bn = -1, bd = 1;
         int bj = 0x7FFFFFFF;
         for (int64_t j = lane; j < k; j += 32) {
-            const int64_t in = (int64_t)__popcll(amask & cmask[j]) + cnt[j];
+            int64_t in = cnt[j];
+            for (int w = 0; w < HW; w++) in += __popcll(am[w] & cmask[j * HW + w]);
             cnt[j] = 0;
             const int64_t un = na + clen[j] - in;
             const int64_t num = un ? in : 0, den = un ? un : 1;
@@ -339,9 +366,11 @@ __global__ void k_tile_offsets(int64_t nr, const int64_t *__restrict__ post_off,
 
 __global__ void __launch_bounds__(JX_THREADS) k_jac_tiled(
     int64_t n, const int64_t *__restrict__ off, const uint32_t *__restrict__ items, int na_fix, int64_t k,
-    const int32_t *__restrict__ clen, const uint32_t *__restrict__ post_item, const int32_t *__restrict__ tile_off,
-    int ntiles, int64_t n_post_items, const uint32_t *__restrict__ post_centre, int32_t *__restrict__ labels,
-    int32_t *__restrict__ ovf_rows, unsigned long long *__restrict__ n_ovf) {
+    const int32_t *__restrict__ clen, const uint64_t *__restrict__ cmask, const uint32_t *__restrict__ hv_item,
+    const int16_t *__restrict__ hv_bit, int nheavy, int HW, const uint32_t *__restrict__ post_item,
+    const int32_t *__restrict__ tile_off, int ntiles, int64_t n_post_items, const uint32_t *__restrict__ post_centre,
+    int32_t *__restrict__ labels, int32_t *__restrict__ ovf_rows, unsigned long long *__restrict__ n_ovf) {
+    __shared__ unsigned long long s_am[JX_S][JX_HW];  // the sets' heavy-item masks
     extern __shared__ uint32_t jx_smem[];
     uint32_t *cnt = jx_smem;                                          // [S][KT / 2]
     int32_t *ridx = reinterpret_cast<int32_t *>(cnt + JX_S * (JX_KT / 2));  // [S][MAXI]: posting list of each item
@@ -365,8 +394,16 @@ __global__ void __launch_bounds__(JX_THREADS) k_jac_tiled(
                 if (lane == 0) ovf_rows[atomicAdd(n_ovf, 1ull)] = (int32_t)i;
                 ni = 0;
             }
+            if (lane < JX_HW) s_am[w][lane] = 0ull;
+            __syncwarp();
             for (int p = lane; p < ni; p += 32) {
                 const uint32_t it = items[s0 + p];
+                const int hb = heavy_bit(it, hv_item, hv_bit, nheavy);
+                if (hb >= 0) {
+                    atomicOr(&s_am[w][hb >> 6], 1ull << (hb & 63));
+                    ridx[w * JX_MAXI + p] = -1;
+                    continue;
+                }
                 int64_t lo = 0, hi = n_post_items;
                 while (lo < hi) {
                     const int64_t mid = (lo + hi) >> 1;
@@ -383,6 +420,7 @@ __global__ void __launch_bounds__(JX_THREADS) k_jac_tiled(
         } else if (lane == 0) {
             s_ni[w] = 0;
             s_na[w] = 0;
+            for (int h = 0; h < JX_HW; h++) s_am[w][h] = 0ull;
         }
         __syncthreads();
         int64_t bn[JX_S], bd[JX_S];
@@ -438,9 +476,14 @@ __global__ void __launch_bounds__(JX_THREADS) k_jac_tiled(
             for (int cc = threadIdx.x; cc < (int)(c1 - c0); cc += blockDim.x) {
                 const int64_t c = c0 + cc;
                 const int64_t cl = clen[c];
+                uint64_t cm[JX_HW];
+#pragma unroll
+                for (int h = 0; h < JX_HW; h++) cm[h] = h < HW ? cmask[c * HW + h] : 0ull;
 #pragma unroll
                 for (int q = 0; q < JX_S; q++) {
-                    const int64_t in = (cnt[q * (JX_KT / 2) + (cc >> 1)] >> ((cc & 1) << 4)) & 0xFFFFu;
+                    int64_t in = (cnt[q * (JX_KT / 2) + (cc >> 1)] >> ((cc & 1) << 4)) & 0xFFFFu;
+#pragma unroll
+                    for (int h = 0; h < JX_HW; h++) in += __popcll(s_am[q][h] & cm[h]);
                     if (in) {
                         const int64_t un = s_na[q] + cl - in;
                         const int64_t l = in * bd[q], r = bn[q] * un;
@@ -694,21 +737,55 @@ geek_status jaccard_core(geek_ctx *ctx, Scratch &scr, const int64_t *off, const 
     int64_t ni = 0;
     GK_CUDA(ctx, cudaMemcpyAsync(&ni, nr_dev, 8, cudaMemcpyDeviceToHost, st));
     GK_CUDA(ctx, cudaStreamSynchronize(st));
-    // every item keeps its posting list (no bitmask items on the tiled path)
-    uint32_t *lval = nullptr;
-    const int nheavy = 0;
-    uint32_t *d_heavy, *d_litem, *d_lcentre;
-    int64_t *is_heavy, *lrun, *lrun_pos, *lent, *lent_pos, *d_loff, *nlight, *nlent;
-    GK_TRY(scr.alloc(&d_heavy, std::max(1, nheavy)));
+    // heavy items: the (up to 64 JX_HW) longest posting lists of length >= 2,
+    // chosen on the host from the run lengths; the others keep posting lists
+    std::vector<int64_t> hrs(ni + 1);
+    GK_CUDA(ctx, cudaMemcpyAsync(hrs.data(), rs, 8 * (ni + 1), cudaMemcpyDeviceToHost, st));
+    std::vector<int32_t> ord(ni);
+    GK_CUDA(ctx, cudaStreamSynchronize(st));
+    for (int64_t r = 0; r < ni; r++) ord[r] = (int32_t)r;
+    const int64_t hmax = std::min<int64_t>(64 * JX_HW, ni);
+    std::partial_sort(ord.begin(), ord.begin() + hmax, ord.end(), [&](int32_t a, int32_t b) {
+        const int64_t la = hrs[a + 1] - hrs[a], lb = hrs[b + 1] - hrs[b];
+        return la != lb ? la > lb : a < b;
+    });
+    int nheavy = 0;
+    while (nheavy < hmax && hrs[ord[nheavy] + 1] - hrs[ord[nheavy]] >= 2) nheavy++;
+    const int HW = (nheavy + 63) / 64;
+    std::vector<int64_t> h_is(ni, 0);
+    std::vector<int32_t> hv_runs(ord.begin(), ord.begin() + nheavy);
+    std::sort(hv_runs.begin(), hv_runs.end());  // runs ascend with the item value
+    std::vector<int16_t> h_bit(nheavy);
+    std::vector<int32_t> rank_of(ni, -1);
+    for (int b = 0; b < nheavy; b++) rank_of[ord[b]] = b;  // bit = rank by posting length
+    for (int q = 0; q < nheavy; q++) {
+        h_is[hv_runs[q]] = 1;
+        h_bit[q] = (int16_t)rank_of[hv_runs[q]];
+    }
+    uint32_t *d_litem, *d_lcentre, *hv_item;
+    int16_t *hv_bit;
+    int64_t *is_heavy, *lrun, *lrun_pos, *lent, *lent_pos, *d_loff, *nlight, *nlent, *hv_run_dev;
     GK_TRY(scr.alloc(&is_heavy, std::max<int64_t>(ni, 1)));
+    GK_TRY(scr.alloc(&hv_item, std::max(1, nheavy)));
+    GK_TRY(scr.alloc(&hv_bit, std::max(1, nheavy)));
+    GK_TRY(scr.alloc(&hv_run_dev, std::max(1, nheavy)));
     GK_TRY(scr.alloc(&lrun, std::max<int64_t>(ni, 1)));
     GK_TRY(scr.alloc(&lrun_pos, std::max<int64_t>(ni, 1)));
     GK_TRY(scr.alloc(&lent, std::max<int64_t>(ni, 1)));
     GK_TRY(scr.alloc(&lent_pos, std::max<int64_t>(ni, 1)));
     GK_TRY(scr.alloc(&nlight, 1));
     GK_TRY(scr.alloc(&nlent, 1));
-    GK_CUDA(ctx, cudaMemsetAsync(is_heavy, 0, 8 * std::max<int64_t>(ni, 1), st));
-    (void)lval;
+    GK_CUDA(ctx, cudaMemcpyAsync(is_heavy, h_is.data(), 8 * ni, cudaMemcpyHostToDevice, st));
+    if (nheavy) {
+        std::vector<int64_t> hv_r64(hv_runs.begin(), hv_runs.end());
+        GK_CUDA(ctx, cudaMemcpyAsync(hv_run_dev, hv_r64.data(), 8 * nheavy, cudaMemcpyHostToDevice, st));
+        GK_CUDA(ctx, cudaMemcpyAsync(hv_bit, h_bit.data(), 2 * nheavy, cudaMemcpyHostToDevice, st));
+        GK_COUNT();
+        k_run_items<<<G(ctx, nheavy), 256, 0, st>>>(nheavy, hv_run_dev, rs, ikey, hv_item);
+        GK_LAUNCH(ctx);
+    }
+    // the host vectors above must outlive their copies
+    GK_CUDA(ctx, cudaStreamSynchronize(st));
     GK_COUNT();
     k_light_flags<<<G(ctx, ni), 256, 0, st>>>(ni, rs, is_heavy, lrun, lent);
     GK_LAUNCH(ctx);
@@ -727,10 +804,10 @@ geek_status jaccard_core(geek_ctx *ctx, Scratch &scr, const int64_t *off, const 
     GK_LAUNCH(ctx);
     uint64_t *cmask;
     int32_t *clen, *counts;
-    GK_TRY(scr.alloc(&cmask, k));
+    GK_TRY(scr.alloc(&cmask, (size_t)k * std::max(HW, 1)));
     GK_TRY(scr.alloc(&clen, k));
     GK_COUNT();
-    k_heavy_masks<<<G(ctx, k), 256, 0, st>>>(k, coff, citems, d_heavy, nheavy, cmask, clen);
+    k_heavy_masks<<<G(ctx, k), 256, 0, st>>>(k, coff, citems, hv_item, hv_bit, nheavy, HW, cmask, clen);
     GK_LAUNCH(ctx);
     if (nci > 0x7FFFFFFFLL) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "more than 2^31 centre items");
     int32_t *ovf;
@@ -753,8 +830,8 @@ geek_status jaccard_core(geek_ctx *ctx, Scratch &scr, const int64_t *off, const 
         tk.work = (double)n * (double)k;  // (set, centre) pairs scored
         GK_COUNT();
         k_jac_tiled<<<(unsigned)std::min<int64_t>(ceil_div(n, JX_S), (int64_t)ctx->num_sms * 3), JX_THREADS, JX_SMEM,
-                      st>>>(n, off, items, na_fix, k, clen, d_litem, toff, ntiles, h_nlight, d_lcentre, labels, ovf,
-                            n_ovf);
+                      st>>>(n, off, items, na_fix, k, clen, cmask, hv_item, hv_bit, nheavy, HW, d_litem, toff, ntiles,
+                            h_nlight, d_lcentre, labels, ovf, n_ovf);
         GK_LAUNCH(ctx);
     }
     unsigned long long h_ovf = 0;
@@ -767,8 +844,8 @@ geek_status jaccard_core(geek_ctx *ctx, Scratch &scr, const int64_t *off, const 
         GK_TRY(scr.alloc(&counts, (size_t)nwarps * k));
         GK_CUDA(ctx, cudaMemsetAsync(counts, 0, sizeof(int32_t) * nwarps * k, st));
         GK_COUNT();
-        k_assign_jaccard<<<blocks, 256, 0, st>>>(n, off, items, k, clen, cmask, d_heavy, nheavy, d_litem, d_loff,
-                                                 h_nlight, d_lcentre, counts, labels, ovf, n_ovf, na_fix);
+        k_assign_jaccard<<<blocks, 256, 0, st>>>(n, off, items, k, clen, cmask, hv_item, hv_bit, nheavy, HW, d_litem,
+                                                 d_loff, h_nlight, d_lcentre, counts, labels, ovf, n_ovf, na_fix);
         GK_LAUNCH(ctx);
     }
     if (stats) stats->n_recheck_rows = (int64_t)h_ovf;  // sets decided by the dense path
