@@ -168,7 +168,7 @@ __global__ void k_group_emit(const int64_t *__restrict__ nruns, const int64_t *_
 
 // heavy items: up to 64 * JX_HW of the items with the longest posting lists
 // are counted by bitmasks instead of posting lists
-constexpr int JX_HW = 4;
+constexpr int JX_HW = 1;
 
 // item -> centres inverted index helpers
 __global__ void k_centre_pairs(int64_t k, const int64_t *__restrict__ coff, const uint32_t *__restrict__ citems,
@@ -210,6 +210,12 @@ __global__ void k_light_emit(int64_t nr, const int64_t *__restrict__ rs, const u
     if (blockIdx.x == 0 && threadIdx.x == 0) loff[nlight] = *nlent;
 }
 
+__global__ void k_iota_rows(int64_t n, int32_t *__restrict__ rows, unsigned long long *__restrict__ cnt) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        rows[i] = (int32_t)i;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *cnt = (unsigned long long)n;
+}
+
 // item of each listed run (first entry's key)
 __global__ void k_run_items(int nh, const int64_t *__restrict__ runs, const int64_t *__restrict__ rs,
                             const uint64_t *__restrict__ ikey, uint32_t *__restrict__ out) {
@@ -234,7 +240,7 @@ __global__ void k_heavy_masks(int64_t k, const int64_t *__restrict__ coff, const
                               const uint32_t *__restrict__ hv_item, const int16_t *__restrict__ hv_bit, int nheavy,
                               int HW, uint64_t *__restrict__ cmask, int32_t *__restrict__ clen) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t m[JX_HW] = {0, 0, 0, 0};
+        uint64_t m[JX_HW] = {};
         for (int64_t p = coff[j]; p < coff[j + 1]; p++) {
             const int b = heavy_bit(citems[p], hv_item, hv_bit, nheavy);
             if (b >= 0) m[b >> 6] |= 1ull << (b & 63);
@@ -267,7 +273,7 @@ __global__ void __launch_bounds__(256) k_assign_jaccard(
         const int64_t i = rows ? (int64_t)rows[ii] : ii;
         const int64_t s = off[i], e = off[i + 1];
         const int64_t na = na_fix >= 0 ? na_fix : e - s;
-        uint64_t am[JX_HW] = {0, 0, 0, 0};
+        uint64_t am[JX_HW] = {};
         // light items: binary search in the sorted item list of the index
         for (int64_t p = s + lane; p < e; p += 32) {
             const uint32_t it = items[p];
@@ -378,7 +384,7 @@ __global__ void __launch_bounds__(JX_THREADS) k_jac_tiled(
     uint16_t *rlen = reinterpret_cast<uint16_t *>(rps + JX_S * JX_MAXI);   // [S][MAXI]
     __shared__ int s_ni[JX_S];
     __shared__ int64_t s_na[JX_S];
-    __shared__ int64_t r_n[JX_S][JX_S], r_d[JX_S][JX_S];
+    __shared__ uint32_t r_n[JX_S][JX_S], r_d[JX_S][JX_S];
     __shared__ int r_j[JX_S][JX_S];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int e = threadIdx.x; e < JX_S * (JX_KT / 2); e += blockDim.x) cnt[e] = 0;
@@ -423,13 +429,17 @@ __global__ void __launch_bounds__(JX_THREADS) k_jac_tiled(
             for (int h = 0; h < JX_HW; h++) s_am[w][h] = 0ull;
         }
         __syncthreads();
-        int64_t bn[JX_S], bd[JX_S];
+        uint32_t bn[JX_S], bd[JX_S], na[JX_S];
+        uint64_t am[JX_S][JX_HW];
         int bj[JX_S];
 #pragma unroll
         for (int q = 0; q < JX_S; q++) {
             bn[q] = 0;
             bd[q] = 1;
             bj[q] = 0x7FFFFFFF;
+            na[q] = (uint32_t)s_na[q];
+#pragma unroll
+            for (int h = 0; h < JX_HW; h++) am[q][h] = s_am[q][h];
         }
         for (int64_t c0 = 0; c0 < k; c0 += JX_KT) {
             const int64_t c1 = min(k, c0 + JX_KT);
@@ -481,12 +491,13 @@ __global__ void __launch_bounds__(JX_THREADS) k_jac_tiled(
                 for (int h = 0; h < JX_HW; h++) cm[h] = h < HW ? cmask[c * HW + h] : 0ull;
 #pragma unroll
                 for (int q = 0; q < JX_S; q++) {
-                    int64_t in = (cnt[q * (JX_KT / 2) + (cc >> 1)] >> ((cc & 1) << 4)) & 0xFFFFu;
+                    uint32_t in = (cnt[q * (JX_KT / 2) + (cc >> 1)] >> ((cc & 1) << 4)) & 0xFFFFu;
 #pragma unroll
-                    for (int h = 0; h < JX_HW; h++) in += __popcll(s_am[q][h] & cm[h]);
+                    for (int h = 0; h < JX_HW; h++) in += __popcll(am[q][h] & cm[h]);
                     if (in) {
-                        const int64_t un = s_na[q] + cl - in;
-                        const int64_t l = in * bd[q], r = bn[q] * un;
+                        // |A| + |C| < 2^16: both cross products fit 32 bits
+                        const uint32_t un = na[q] + (uint32_t)cl - in;
+                        const uint32_t l = in * bd[q], r = bn[q] * un;
                         if (l > r || (l == r && (int)c < bj[q])) {
                             bn[q] = in;
                             bd[q] = un;
@@ -504,10 +515,10 @@ __global__ void __launch_bounds__(JX_THREADS) k_jac_tiled(
         for (int q = 0; q < JX_S; q++) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                const int64_t on = __shfl_xor_sync(0xffffffffu, bn[q], o);
-                const int64_t od = __shfl_xor_sync(0xffffffffu, bd[q], o);
+                const uint32_t on = __shfl_xor_sync(0xffffffffu, bn[q], o);
+                const uint32_t od = __shfl_xor_sync(0xffffffffu, bd[q], o);
                 const int oj = __shfl_xor_sync(0xffffffffu, bj[q], o);
-                const int64_t l = on * bd[q], r = bn[q] * od;
+                const uint32_t l = on * bd[q], r = bn[q] * od;
                 if (l > r || (l == r && oj < bj[q])) {
                     bn[q] = on;
                     bd[q] = od;
@@ -523,10 +534,10 @@ __global__ void __launch_bounds__(JX_THREADS) k_jac_tiled(
         __syncthreads();
         if (threadIdx.x < JX_S) {
             const int q = threadIdx.x;
-            int64_t n0 = 0, d0 = 1;
+            uint32_t n0 = 0, d0 = 1;
             int j0 = 0x7FFFFFFF;
             for (int v = 0; v < JX_S; v++) {
-                const int64_t l = r_n[q][v] * d0, r = n0 * r_d[q][v];
+                const uint32_t l = r_n[q][v] * d0, r = n0 * r_d[q][v];
                 if (l > r || (l == r && r_j[q][v] < j0)) {
                     n0 = r_n[q][v];
                     d0 = r_d[q][v];
@@ -810,6 +821,15 @@ geek_status jaccard_core(geek_ctx *ctx, Scratch &scr, const int64_t *off, const 
     k_heavy_masks<<<G(ctx, k), 256, 0, st>>>(k, coff, citems, hv_item, hv_bit, nheavy, HW, cmask, clen);
     GK_LAUNCH(ctx);
     if (nci > 0x7FFFFFFFLL) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "more than 2^31 centre items");
+    // the tiled kernel compares fractions in 32 bits: |A| <= JX_MAXI (else the
+    // dense path) and every |C| below 2^15
+    bool tiled_ok = na_fix < 32768;
+    {
+        std::vector<int64_t> hco(k + 1);
+        GK_CUDA(ctx, cudaMemcpyAsync(hco.data(), coff, 8 * (k + 1), cudaMemcpyDeviceToHost, st));
+        GK_CUDA(ctx, cudaStreamSynchronize(st));
+        for (int64_t j = 0; j < k && tiled_ok; j++) tiled_ok = hco[j + 1] - hco[j] < 32768;
+    }
     int32_t *ovf;
     unsigned long long *n_ovf;
     GK_TRY(scr.alloc(&ovf, n));
@@ -828,11 +848,17 @@ geek_status jaccard_core(geek_ctx *ctx, Scratch &scr, const int64_t *off, const 
         k_tile_offsets<<<G(ctx, h_nlight * (ntiles + 1)), 256, 0, st>>>(h_nlight, d_loff, d_lcentre, ntiles, toff);
         EvTimer tk(ctx, "kernel.jaccard", st);
         tk.work = (double)n * (double)k;  // (set, centre) pairs scored
+        if (!tiled_ok) {  // very large central sets: every set takes the dense path
+            GK_COUNT();
+            k_iota_rows<<<G(ctx, n), 256, 0, st>>>(n, ovf, n_ovf);
+            GK_LAUNCH(ctx);
+        } else {
         GK_COUNT();
         k_jac_tiled<<<(unsigned)std::min<int64_t>(ceil_div(n, JX_S), (int64_t)ctx->num_sms * 3), JX_THREADS, JX_SMEM,
                       st>>>(n, off, items, na_fix, k, clen, cmask, hv_item, hv_bit, nheavy, HW, d_litem, toff, ntiles,
                             h_nlight, d_lcentre, labels, ovf, n_ovf);
         GK_LAUNCH(ctx);
+        }
     }
     unsigned long long h_ovf = 0;
     GK_CUDA(ctx, cudaMemcpyAsync(&h_ovf, n_ovf, sizeof h_ovf, cudaMemcpyDeviceToHost, st));
