@@ -589,7 +589,8 @@ def bench_pipeline(args, geek, ctx, name, world, pk, pk_kind):
     import torch
     import synth
     t0 = time.time()
-    wl = synth.make(synth.config(name))
+    n_over = args.sets_n if name == "c3" else args.hetero_n
+    wl = synth.make(synth.config(name, **({} if n_over is None else dict(n=n_over))))
     t_gen = time.time() - t0
     cfg = wl["cfg"]
     mh_a, mh_b = geek._dev(wl["mh_a"]), geek._dev(wl["mh_b"])
@@ -814,6 +815,8 @@ def main():
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--skip-sets", action="store_true", help="skip the 2M sparse-set pipeline measurement")
     ap.add_argument("--skip-hetero", action="store_true", help="skip the 2M heterogeneous pipeline measurement")
+    ap.add_argument("--sets-n", type=int, default=None, help="sets pipeline: smaller n (profiling runs)")
+    ap.add_argument("--hetero-n", type=int, default=None, help="heterogeneous pipeline: smaller n (profiling runs)")
     ap.add_argument("--skip-alg1", action="store_true", help="skip the Alg. 1 transform measurement")
     ap.add_argument("--skip-refine", action="store_true", help="skip the extra-passes measurement")
     ap.add_argument("--skip-doph", action="store_true", help="skip the DOPH sets measurement")
