@@ -129,3 +129,45 @@ def test_tc_projection_cell_edges_and_cancellation(G, ctx):
         codes, ref = oracle.hash_dense(x, a, b, w, K, L, proj=name)
         check(bk, codes, ref)
         assert bk.n_flagged >= n // 4, name
+
+
+def _tc_coef(d):
+    """The kernel's window coefficient (three-term split, per-instruction
+    accumulation model): E = coef |a| |x|."""
+    nk = (d + 15) // 16
+    u20 = 2.0 ** -20
+    c = nk * u20 * 1.0079 + 5 * nk * u20 * 0.0079 + 2.0 ** -24 * 1.01 + 2.0 ** -22 * 1.01 + d * 1.12e-16
+    return 1.01 * c
+
+
+def test_tc_projection_just_outside_the_window(G, ctx):
+    """Elements placed 1.05-1.6 windows from a cell edge, on both sides, with
+    |x| ~ 3e3: the kernel settles them without a recheck, so a tensor-core
+    accumulation error beyond the modelled bound would show as a wrong code."""
+    rng = np.random.default_rng(99)
+    n, d, K, L, w = 6000, 128, 4, 8, 4.0
+    F = K * L
+    a = rng.standard_normal((F, d)).astype(np.float32)
+    b = (rng.random(F) * 4).astype(np.float32)
+    x = rng.standard_normal((n, d)) * 250.0
+    f = rng.integers(0, F, n)
+    af = a[f].astype(np.float64)
+    an = np.sqrt((af * af).sum(1))
+    xn = np.sqrt((x * x).sum(1))
+    Et = _tc_coef(d) * an * xn / w                       # the window in cell units
+    s = (af * x).sum(1)
+    m = np.floor((s + b[f]) / w)
+    side = np.where(rng.random(n) < 0.5, -1.0, 1.0)
+    frac = np.where(side > 0, 0.0, 1.0) + side * rng.uniform(1.05, 1.6, n) * Et
+    tgt = (m + frac) * w - b[f]
+    x += ((tgt - s) / (an * an))[:, None] * af
+    x = x.astype(np.float32)
+    bk = hash_tc(G, ctx, x, a, b, w, K, L)
+    codes, ref = oracle.hash_dense(x, a, b, w, K, L)
+    check(bk, codes, ref)
+    # most of the placed elements stay outside the window after rounding
+    # the rows to FP32: they were decided by the tensor-core pass alone
+    xs = x.astype(np.float64)
+    t_exact = ((af * xs).sum(1) + b[f]) / w
+    margin = np.minimum(t_exact - np.floor(t_exact), np.ceil(t_exact) - t_exact) / Et
+    assert np.mean((margin > 1.0) & (margin < 2.0)) > 0.5
