@@ -748,43 +748,77 @@ __global__ void k_label_keys(int64_t n, const int32_t *__restrict__ labels, int6
     }
 }
 
+// sort key of centre j: descending member count, then ascending index
+__global__ void k_size_order(int64_t k, const unsigned long long *__restrict__ cnt, uint64_t *__restrict__ key) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t cj = cnt[j] > 0xFFFFFFFFull ? 0xFFFFFFFFull : cnt[j];
+        key[j] = ((0xFFFFFFFFull - cj) << 32) | (uint64_t)j;
+    }
+}
+
 // centre j <- mean of its members (ascending id, the seeds' centroid sum);
-// no member: unchanged.  Block per centre, thread per coordinate: member
-// ids staged 128 at a time in shared memory, 32 row values loaded together
-// (rows read coalesced across the coordinates), then added in order -- the
-// sum stays sequential in ascending id, so a centre's cost is a chain of
-// its member count (the largest cluster bounds the pass).
-constexpr int UC_T = 128, UC_CH = 128, UC_IN = 32;  // ids per chunk, loads in flight per thread
+// no member: unchanged.  Block per centre, thread per coordinate, the sum
+// sequential in ascending id, so a centre's cost is a chain of its member
+// count.  Member rows are gathered by asynchronous 4-byte copies into a
+// ring of UC_S stages of UC_G rows in shared memory (each thread copies and
+// later adds only its own coordinate, so its own cp.async waits order them):
+// (UC_S - 1) UC_G row loads stay in flight while the adds run.  Blocks take
+// the centres largest first (order: centre indices by descending member
+// count), so the largest clusters, which bound the pass, start at once.
+constexpr int UC_T = 128, UC_CH = 1024, UC_G = 32, UC_S = 4;
+constexpr size_t UC_SMEM = (size_t)UC_S * UC_G * UC_T * sizeof(float);
+
+__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 __global__ void __launch_bounds__(UC_T) k_update_centres(const float *__restrict__ x, int64_t ldx, int d, int64_t k,
                                                          const int64_t *__restrict__ off,
                                                          const unsigned long long *__restrict__ cnt,
-                                                         const int32_t *__restrict__ ids, double *__restrict__ c) {
+                                                         const int32_t *__restrict__ ids, const uint64_t *__restrict__ order,
+                                                         double *__restrict__ c) {
     __shared__ int32_t sid[UC_CH];
-    for (int64_t j = blockIdx.x; j < k; j += gridDim.x) {
+    extern __shared__ float stg[];  // [UC_S][UC_G][UC_T]
+    for (int64_t jq = blockIdx.x; jq < k; jq += gridDim.x) {
+        const int64_t j = (int64_t)(order[jq] & 0xFFFFFFFFull);
         const int64_t cj = (int64_t)cnt[j];
         if (cj == 0) continue;  // block-uniform
         const int64_t s0 = off[j];
         for (int t0 = 0; t0 < d; t0 += UC_T) {
             const int t = t0 + threadIdx.x;
+            const bool act = t < d;
             double s = 0.0;
             for (int64_t p0 = 0; p0 < cj; p0 += UC_CH) {
                 const int len = (int)min((int64_t)UC_CH, cj - p0);
+                __syncthreads();  // the previous chunk's ids are no longer read
+                for (int e = threadIdx.x; e < len; e += UC_T) sid[e] = ids[s0 + p0 + e];
                 __syncthreads();
-                if (threadIdx.x < len) sid[threadIdx.x] = ids[s0 + p0 + threadIdx.x];
-                __syncthreads();
-                if (t < d) {
-                    int q0 = 0;
-                    for (; q0 + UC_IN <= len; q0 += UC_IN) {  // full groups: every load issued first
-                        float v[UC_IN];
-#pragma unroll
-                        for (int q = 0; q < UC_IN; q++) v[q] = __ldg(x + (int64_t)sid[q0 + q] * ldx + t);
-#pragma unroll
-                        for (int q = 0; q < UC_IN; q++) s = __dadd_rn(s, (double)v[q]);
+                const int ng = (len + UC_G - 1) / UC_G;
+                auto issue = [&](int g) {
+                    if (g < ng && act) {
+                        float *dst = stg + (size_t)(g % UC_S) * UC_G * UC_T + threadIdx.x;
+                        const int q1 = min(UC_G, len - g * UC_G);
+                        for (int q = 0; q < q1; q++) cp_async4(dst + q * UC_T, x + (int64_t)sid[g * UC_G + q] * ldx + t);
                     }
-                    for (; q0 < len; q0++) s = __dadd_rn(s, (double)__ldg(x + (int64_t)sid[q0] * ldx + t));
+                    cp_async_commit();  // empty groups keep the count uniform
+                };
+                for (int g = 0; g < UC_S - 1; g++) issue(g);
+                for (int g = 0; g < ng; g++) {
+                    issue(g + UC_S - 1);
+                    cp_async_wait<UC_S - 1>();
+                    if (act) {
+                        const float *src = stg + (size_t)(g % UC_S) * UC_G * UC_T + threadIdx.x;
+                        const int q1 = min(UC_G, len - g * UC_G);
+                        for (int q = 0; q < q1; q++) s = __dadd_rn(s, (double)src[q * UC_T]);
+                    }
                 }
+                cp_async_wait<0>();
             }
-            if (t < d) c[j * d + t] = __ddiv_rn(s, (double)cj);
+            if (act) c[j * d + t] = __ddiv_rn(s, (double)cj);
         }
     }
 }
@@ -811,9 +845,20 @@ geek_status refine_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ld
         GK_LAUNCH(ctx);
         GK_TRY(radix_sort_segments(ctx, ps, 1, n, &key, nullptr, &ids, bit_length_u64((uint64_t)k), st));
         GK_TRY(exclusive_scan_i64(ctx, ps, (const int64_t *)cnt, off, k, nullptr, st));
+        uint64_t *order;
+        GK_TRY(ps.alloc(&order, k));
         GK_COUNT();
-        k_update_centres<<<(unsigned)std::min<int64_t>(k, (int64_t)ctx->num_sms * 16), UC_T, 0, st>>>(
-            x, ldx, d, k, off, cnt, (const int32_t *)ids, centres);
+        k_size_order<<<grid_for(k, 256, ctx->num_sms), 256, 0, st>>>(k, cnt, order);
+        GK_LAUNCH(ctx);
+        GK_TRY(radix_sort_segments(ctx, ps, 1, k, &order, nullptr, nullptr, 64, st));
+        static bool uc_attr = false;
+        if (!uc_attr) {
+            GK_CUDA(ctx, cudaFuncSetAttribute(k_update_centres, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UC_SMEM));
+            uc_attr = true;
+        }
+        GK_COUNT();
+        k_update_centres<<<(unsigned)std::min<int64_t>(k, (int64_t)ctx->num_sms * 8), UC_T, UC_SMEM, st>>>(
+            x, ldx, d, k, off, cnt, (const int32_t *)ids, order, centres);
         GK_LAUNCH(ctx);
         int h_bad = 0;
         GK_CUDA(ctx, cudaMemcpyAsync(&h_bad, bad, sizeof h_bad, cudaMemcpyDeviceToHost, st));
