@@ -498,7 +498,7 @@ __device__ __forceinline__ void shl_or(uint64_t &hi, uint64_t &lo, int b, uint64
 // a block first copies its objects' code rows to shared memory with
 // coalesced loads (row stride F1 | 1 words: conflict-free row reads), when
 // they fit (PK_STAGE_MAX codes per row).
-constexpr int PK_THREADS = 128, PK_STAGE_MAX = 128;
+constexpr int PK_THREADS = 256, PK_STAGE_MAX = 128;
 
 // copies `rows` consecutive code rows (F1 codes each, from row r0) to shared
 // rows of stride F1 | 1; the (row, column) of element e advance by fixed
@@ -506,10 +506,37 @@ constexpr int PK_THREADS = 128, PK_STAGE_MAX = 128;
 __device__ __forceinline__ void pk_stage_rows(int32_t *cs, const int32_t *__restrict__ codes, int64_t r0, int rows,
                                               int F1) {
     const int rs = F1 | 1;
+    const int32_t *src = codes + r0 * F1;
+    const int total = rows * F1;
+    if ((F1 & 3) == 0 && ((uintptr_t)src & 15) == 0) {
+        // 16-byte loads, four in flight per thread: a row holds a whole
+        // number of them, so each vector's (row, column) comes from one
+        // division
+        const int nv = total >> 2, fv = F1 >> 2;
+        for (int v0 = threadIdx.x; v0 < nv; v0 += 4 * PK_THREADS) {
+            int4 q[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int v = v0 + u * PK_THREADS;
+                q[u] = v < nv ? reinterpret_cast<const int4 *>(src)[v] : make_int4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int v = v0 + u * PK_THREADS;
+                if (v >= nv) break;
+                const int r = v / fv, c = (v - r * fv) * 4;
+                int32_t *d = cs + r * rs + c;
+                d[0] = q[u].x;
+                d[1] = q[u].y;
+                d[2] = q[u].z;
+                d[3] = q[u].w;
+            }
+        }
+        return;
+    }
     const int dr = PK_THREADS / F1, dc = PK_THREADS % F1;
     int r = threadIdx.x / F1, c = threadIdx.x % F1;
-    const int32_t *src = codes + r0 * F1;
-    for (int e = threadIdx.x; e < rows * F1; e += PK_THREADS) {
+    for (int e = threadIdx.x; e < total; e += PK_THREADS) {
         cs[r * rs + c] = src[e];
         r += dr;
         c += dc;
