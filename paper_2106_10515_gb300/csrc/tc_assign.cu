@@ -87,6 +87,7 @@ struct TcArgs {
     int32_t *flag_rows;          // global rows whose argmin needs the FP64 decision
     unsigned long long *n_flag;
     int *err;
+    int lg_ns;                   // log2 of the centre-tile ring's stages (1..3)
 };
 
 // three-input minimum
@@ -211,9 +212,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *sA0 = base, *sB0 = base + 2 * A_ST;
     uint64_t *bars = (uint64_t *)(base + 2 * TC_A_STAGE + 2 * TC_B_STAGE);
-    uint64_t *full_a = bars, *empty_a = bars + 2, *full_b = bars + 4, *empty_b = bars + 6;
-    uint64_t *full_acc = bars + 8, *empty_acc = bars + 10, *done_bar = bars + 12;
-    uint32_t *tmem_slot = (uint32_t *)(bars + 17);
+    uint64_t *full_a = bars, *empty_a = bars + 2, *full_acc = bars + 4, *empty_acc = bars + 6;
+    uint64_t *done_bar = bars + 8, *full_b = bars + 9, *empty_b = bars + 17;  // B ring: up to 8 stages
+    uint32_t *tmem_slot = (uint32_t *)(bars + 25);
+    // the centre-tile ring: the same bytes cut into NS stages (narrower tiles,
+    // more stages in flight)
+    const int NS = 1 << A.lg_ns;
+    const int BSTR = 2 * B_ST / NS, XSTR = 2 * TC_N * 32 / NS;
     float *mrg = (float *)(bars + 32);  // [groups-1][128][3] results of column groups 1..
     // |c|^2 columns: an all-ones X block (128 x 16) and per stage the centres'
     // (hi, mid, lo, 0...) rows (N x 16), 32-byte swizzled; one extra K = 16
@@ -226,10 +231,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
         for (int i = 0; i < 2; i++) {
             mbar_init(&full_a[i], 1);
             mbar_init(&empty_a[i], 1);
-            mbar_init(&full_b[i], 1);
-            mbar_init(&empty_b[i], 1);
             mbar_init(&full_acc[i], 1);
             mbar_init(&empty_acc[i], TC_EPI_WARPS);
+        }
+        for (int i = 0; i < 8; i++) {
+            mbar_init(&full_b[i], 1);
+            mbar_init(&empty_b[i], 1);
         }
         mbar_init(done_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -256,7 +263,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
             uint64_t ct = 0;
-            uint32_t issued_b[2] = {0, 0};
+            uint32_t issued_b[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             bool ok = true;
             int64_t it = 0;
             for (int64_t u = blockIdx.x; u < A.nunits && ok; u += gridDim.x, it++) {
@@ -272,18 +279,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
                     tma_load_2d(su32(sA0 + ab * A_ST + kb * TC_M * 128), &I.tmA, kb * TC_KB, un.y * TC_M,
                                 &full_a[ab]);
                 for (int c = 0; c < I.ntiles_c; c++, ct++) {
-                    const int s = (int)(ct & 1);
-                    const uint32_t uu = (uint32_t)(ct >> 1);
+                    const int s = (int)(ct & (uint64_t)(NS - 1));
+                    const uint32_t uu = (uint32_t)(ct >> A.lg_ns);
                     if (!(ok = mbar_wait(&empty_b[s], (uu & 1) ^ 1, A.err))) break;
                     mbar_expect_tx(&full_b[s], b_bytes + (uint32_t)N * 32);
                     for (int kb = 0; kb < nkb; kb++)
-                        tma_load_2d(su32(sB0 + s * B_ST + kb * N * 128), &I.tmB, kb * TC_KB, c * N, &full_b[s]);
-                    tma_load_2d(su32(sX0 + s * TC_N * 32), &I.tmX, 0, c * N, &full_b[s]);
+                        tma_load_2d(su32(sB0 + s * BSTR + kb * N * 128), &I.tmB, kb * TC_KB, c * N, &full_b[s]);
+                    tma_load_2d(su32(sX0 + s * XSTR), &I.tmX, 0, c * N, &full_b[s]);
                     issued_b[s] = uu + 1;
                 }
             }
             // drain: every centre-tile copy this thread issued has landed
-            for (int s = 0; s < 2; s++)
+            for (int s = 0; s < NS; s++)
                 if (issued_b[s]) mbar_wait(&full_b[s], (issued_b[s] - 1) & 1, A.err, true);
         }
         __syncwarp();
@@ -303,12 +310,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
                 if (!(ok = mbar_wait(&full_a[ab], ua & 1, A.err))) break;
                 const uint32_t a_base = su32(sA0 + ab * A_ST);
                 for (int c = 0; c < I.ntiles_c; c++, ct++) {
-                    const int s = (int)(ct & 1);
+                    const int sb = (int)(ct & (uint64_t)(NS - 1));  // centre-tile stage
+                    const uint32_t ub = (uint32_t)(ct >> A.lg_ns);
+                    const int s = (int)(ct & 1);                     // accumulator buffer
                     const uint32_t uu = (uint32_t)(ct >> 1);
-                    if (!(ok = mbar_wait(&full_b[s], uu & 1, A.err))) break;
+                    if (!(ok = mbar_wait(&full_b[sb], ub & 1, A.err))) break;
                     if (!(ok = mbar_wait(&empty_acc[s], (uu & 1) ^ 1, A.err))) break;
                     fence_after();
-                    const uint32_t b_base = su32(sB0 + s * B_ST);
+                    const uint32_t b_base = su32(sB0 + sb * BSTR);
                     const uint32_t dtm = tmem + (uint32_t)(s * TC_N);
                     for (int kb = 0; kb < nkb; kb++)
 #pragma unroll
@@ -322,8 +331,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_assign_tc(const __grid_consta
                             }
                         }
                     // + |c|^2: ones (128 x 16) times the centres' (hi, mid, lo, 0...)
-                    mma_bf16(dtm, sdesc32(su32(sOnes)), sdesc32(su32(sX0 + s * TC_N * 32)), idesc, 1);
-                    mma_commit(&empty_b[s]);
+                    mma_bf16(dtm, sdesc32(su32(sOnes)), sdesc32(su32(sX0 + sb * XSTR)), idesc, 1);
+                    mma_commit(&empty_b[sb]);
                     mma_commit(&full_acc[s]);
                 }
                 mma_commit(&empty_a[ab]);
@@ -735,8 +744,30 @@ geek_status tc_plan_convert(geek_ctx *ctx, const TcPlan &P, cudaStream_t st) {
 
 namespace {
 
+// log2 of the centre-tile ring's stages for the instances of one mode in a
+// launch: the widest stage among them fixes the stage size; the ring's bytes
+// are cut into as many stages as fit (2 .. 8)
+int ring_lg(const TcPlan &P, const std::vector<int> *which, int split) {
+    int64_t mx = 0;
+    auto consider = [&](int i) {
+        const TcPlanInst &I = P.desc[i];
+        if ((I.split != 0) != (split != 0)) return;
+        const int64_t Kp = I.d <= 64 ? 64 : 128;
+        mx = std::max<int64_t>(mx, (int64_t)I.N * Kp * 2 * (split ? 2 : 1));
+    };
+    if (which)
+        for (int i : *which) consider(i);
+    else
+        for (int i = 0; i < P.count; i++) consider(i);
+    const int64_t ring = 2 * (int64_t)(split ? TC_B_STAGE_X3 : TC_B_STAGE);
+    int lg = 1;
+    while (lg < 3 && mx > 0 && (ring >> (lg + 1)) >= mx) lg++;
+    return lg;
+}
+
 geek_status launch_units(geek_ctx *ctx, const TcInst *inst, const int2 *units, int64_t n0, int64_t n1,
-                         int32_t *flag_rows, unsigned long long *n_flag, int *err, double work, cudaStream_t st) {
+                         int32_t *flag_rows, unsigned long long *n_flag, int *err, double work, int lg0, int lg1,
+                         cudaStream_t st) {
     TcArgs A;
     A.inst = inst;
     A.flag_rows = flag_rows;
@@ -747,12 +778,14 @@ geek_status launch_units(geek_ctx *ctx, const TcInst *inst, const int2 *units, i
     if (n0 > 0) {
         A.units = units;
         A.nunits = n0;
+        A.lg_ns = lg0;
         GK_COUNT();
         k_assign_tc<false><<<(int)std::min<int64_t>(n0, ctx->num_sms), TC_THREADS, tc_smem(), st>>>(A);
     }
     if (n1 > 0) {
         A.units = units + n0;
         A.nunits = n1;
+        A.lg_ns = lg1;
         GK_COUNT();
         k_assign_tc<true><<<(int)std::min<int64_t>(n1, ctx->num_sms), TC_THREADS, tc_smem(), st>>>(A);
     }
@@ -769,7 +802,8 @@ geek_status tc_plan_launch(geek_ctx *ctx, const TcPlan &P, int32_t *flag_rows, u
                            cudaStream_t st) {
     double work = 0.0;
     for (const TcPlanInst &I : P.desc) work += 2.0 * (double)I.n * (double)I.k * (double)I.d;
-    return launch_units(ctx, P.inst, P.units, P.nunits, P.nunits_x3, flag_rows, n_flag, P.err, work, st);
+    return launch_units(ctx, P.inst, P.units, P.nunits, P.nunits_x3, flag_rows, n_flag, P.err, work,
+                        ring_lg(P, nullptr, 0), ring_lg(P, nullptr, 1), st);
 }
 
 geek_status tc_plan_enqueue(geek_ctx *ctx, const TcPlan &P, int32_t *flag_rows, unsigned long long *n_flag,
@@ -818,7 +852,8 @@ geek_status tc_plan_launch_subset(geek_ctx *ctx, TcPlan *P, const std::vector<in
     GK_CUDA(ctx, cudaMemcpyAsync(P->tune_units, u0.data(), sizeof(int2) * u0.size(), cudaMemcpyHostToDevice, st));
     GK_CUDA(ctx, cudaStreamSynchronize(st));  // u0 is pageable and about to go out of scope
     (void)im;
-    return launch_units(ctx, P->inst, P->tune_units, n0, n1, flag_rows, n_flag, P->err, 0.0, st);
+    return launch_units(ctx, P->inst, P->tune_units, n0, n1, flag_rows, n_flag, P->err, 0.0, ring_lg(*P, &which, 0),
+                        ring_lg(*P, &which, 1), st);
 }
 
 geek_status tc_plan_check(geek_ctx *ctx, const TcPlan &P, cudaStream_t st) {
@@ -848,7 +883,8 @@ geek_status assign_tc_bf16(geek_ctx *ctx, Scratch &scr, const float *x, int64_t 
     if (d > 128) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "BF16 tensor-core assignment supports d <= 128");
     TcPlan P;
     std::vector<TcPlanInst> one(1);
-    const int N = split ? (d <= 64 ? 128 : 64) : TC_N;
+    // N = 128: four centre tiles in flight (N = 256 fits two)
+    const int N = split ? (d <= 64 ? 128 : 64) : 128;
     one[0] = TcPlanInst{x, ldx, n, d, centres, k, labels, 0, N, split};
     struct Free {
         TcPlan *p;
