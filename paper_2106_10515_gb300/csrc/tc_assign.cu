@@ -746,14 +746,17 @@ namespace {
 
 // log2 of the centre-tile ring's stages for the instances of one mode in a
 // launch: the widest stage among them fixes the stage size; the ring's bytes
-// are cut into as many stages as fit (2 .. 8)
+// are cut into as many stages as fit (2 .. 8). Two regions are cut: the
+// centre tiles (N x Kp BF16, twice that when split) and the |c|^2 rows
+// (N x 32 bytes out of 2 * TC_N * 32), so both bound the stage count.
 int ring_lg(const TcPlan &P, const std::vector<int> *which, int split) {
-    int64_t mx = 0;
+    int64_t mx = 0, nmax = 0;
     auto consider = [&](int i) {
         const TcPlanInst &I = P.desc[i];
         if ((I.split != 0) != (split != 0)) return;
         const int64_t Kp = I.d <= 64 ? 64 : 128;
         mx = std::max<int64_t>(mx, (int64_t)I.N * Kp * 2 * (split ? 2 : 1));
+        nmax = std::max<int64_t>(nmax, (int64_t)I.N);
     };
     if (which)
         for (int i : *which) consider(i);
@@ -761,7 +764,8 @@ int ring_lg(const TcPlan &P, const std::vector<int> *which, int split) {
         for (int i = 0; i < P.count; i++) consider(i);
     const int64_t ring = 2 * (int64_t)(split ? TC_B_STAGE_X3 : TC_B_STAGE);
     int lg = 1;
-    while (lg < 3 && mx > 0 && (ring >> (lg + 1)) >= mx) lg++;
+    const int64_t xring = 2 * (int64_t)TC_N * 32;
+    while (lg < 3 && mx > 0 && (ring >> (lg + 1)) >= mx && (xring >> (lg + 1)) >= nmax * 32) lg++;
     return lg;
 }
 
