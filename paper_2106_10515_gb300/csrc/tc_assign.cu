@@ -887,8 +887,10 @@ geek_status assign_tc_bf16(geek_ctx *ctx, Scratch &scr, const float *x, int64_t 
     if (d > 128) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "BF16 tensor-core assignment supports d <= 128");
     TcPlan P;
     std::vector<TcPlanInst> one(1);
-    // N = 128: four centre tiles in flight (N = 256 fits two)
-    const int N = split ? (d <= 64 ? 128 : 64) : 128;
+    // BF16: N = 256 (two stages; 128-wide tiles read A from shared memory
+    // twice as often per flop and measured ~60% slower at d = 128).  Split:
+    // the widest tile whose hi|lo stage fits
+    const int N = split ? (d <= 64 ? 128 : 64) : TC_N;
     one[0] = TcPlanInst{x, ldx, n, d, centres, k, labels, 0, N, split};
     struct Free {
         TcPlan *p;
