@@ -527,7 +527,8 @@ def bench_refine(args, geek, ctx, data, wl, world, prec):
     torch.cuda.synchronize()
     ctx.timing(False)
     ms = e0.elapsed_time(e1) / args.steps
-    tm = {k: ctx.timing_get(k)[0] / args.steps for k in ("refine", "assign", "kernel.assign_tc", "kernel.assign_fp32",
+    tm = {k: ctx.timing_get(k)[0] / args.steps for k in ("refine", "refine.group", "kernel.update_centres",
+                                                        "refine.assign", "kernel.assign_tc", "kernel.assign_fp32",
                                                         "kernel.assign_recheck")}
     return {"workload": f"{P} extra passes of assignment (centre update + exact reassignment) on the dense points "
                         f"above, k={c0.shape[0]} planted centres",

@@ -757,69 +757,254 @@ __global__ void k_size_order(int64_t k, const unsigned long long *__restrict__ c
 }
 
 // centre j <- mean of its members (ascending id, the seeds' centroid sum);
-// no member: unchanged.  Block per centre, thread per coordinate, the sum
-// sequential in ascending id, so a centre's cost is a chain of its member
-// count.  Member rows are gathered by asynchronous 4-byte copies into a
-// ring of UC_S stages of UC_G rows in shared memory (each thread copies and
-// later adds only its own coordinate, so its own cp.async waits order them):
-// (UC_S - 1) UC_G row loads stay in flight while the adds run.  Blocks take
-// the centres largest first (order: centre indices by descending member
-// count), so the largest clusters, which bound the pass, start at once.
-constexpr int UC_T = 128, UC_CH = 1024, UC_G = 32, UC_S = 4;
-constexpr size_t UC_SMEM = (size_t)UC_S * UC_G * UC_T * sizeof(float);
+// no member: unchanged.  Work item = (centre, slice of 32 coordinates), one
+// warp per item, lane = coordinate; each lane's sum is the sequential FP64
+// chain s <- RN(s + x_i) over the centre's members in ascending id.
+//
+// An FP64 add on this part takes 60-170 cycles in a dependent chain (longer
+// for operands of mixed exponents), which would bound the pass by the
+// largest cluster's member count times that latency.  So each 32-member
+// chunk first runs the chain in 64-bit integers, in a unit 2^g that divides
+// s and every x_i of the chunk (the finer of s's lowest set bit and the
+// finest ulp among the x_i): s = T 2^g.  While every partial sum T + R_1 +
+// ... + R_i (R_i = x_i / 2^g) stays below 2^53 in magnitude, each partial
+// sum is exactly representable in FP64, so each RN step is exact and the
+// chain equals the integer sum (binade and sign changes included).  The
+// first step that breaks this (a sum reaching 2^53 units, where rounding may
+// start; an x_i too far above the unit or not finite), and every step after
+// it in the chunk, runs as the FP64 add itself; so the result is the FP64
+// chain bit for bit.  The integer sum is accumulated unconditionally (a
+// 64-bit add is the only loop-carried step) and the failures collected in a
+// bit mask.
+//
+// Member rows reach shared memory through a per-warp ring of UC_S stages of
+// 32 rows (16-byte cp.async per lane, 4 rows per instruction; the ids of a
+// stage are loaded four stages before its copies are issued).  The first wave of items goes to
+// warps warp-in-block major, so the slices of one centre start on different
+// SMs; later items come from an atomic counter, largest centre first
+// (order: centre indices by descending member count).
+constexpr int UC_W = 4, UC_T = 32 * UC_W, UC_B = 32, UC_S = 8;
+constexpr int UC_STAGE = UC_B * 32;                              // floats per stage
+constexpr int UC_SMEM = UC_W * UC_S * UC_STAGE * (int)sizeof(float);  // 128 KB
 
-__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
-                 : "memory");
+// exact FP32 -> FP64 widening in integer operations (normal, subnormal, zero,
+// infinity; a NaN stays a NaN)
+__device__ __forceinline__ double widen_f32(float v) {
+    const uint32_t b = __float_as_uint(v);
+    const uint32_t sg = b & 0x80000000u, e = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
+    // subnormal: m = 1.f x 2^(p - 23) with p the top set bit, value m 2^-149
+    const int sh = __clz((int)m) - 8;  // brings the top bit of m to bit 23
+    const uint32_t ms = (m << (sh & 31)) & 0x7FFFFFu;
+    const uint32_t es = (uint32_t)(1023 - 126 - sh);
+    uint32_t hi, lo;
+    if (e == 0u) {
+        hi = m == 0u ? sg : (sg | (es << 20) | (ms >> 3));
+        lo = m == 0u ? 0u : (ms << 29);
+    } else {
+        const uint32_t ed = e == 0xFFu ? 0x7FFu : e + 896u;
+        hi = sg | (ed << 20) | (m >> 3);
+        lo = m << 29;
+    }
+    return __hiloint2double((int)hi, (int)lo);
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// x / 2^g as a signed integer, x = +-mx 2^u with base = 150 + g and u >= g:
+// exact for u - g <= 38 (then |x / 2^g| < 2^62); bad beyond that or when x
+// is not finite
+__device__ __forceinline__ int64_t units_of(float x, int base, bool &bad) {
+    const uint32_t b = __float_as_uint(x);
+    const int e = (int)((b >> 23) & 0xFFu);
+    const uint32_t mx = (b & 0x7FFFFFu) | ((uint32_t)min(e, 1) << 23);
+    const int lsh = max(e, 1) - base;  // u - g >= 0
+    bad = lsh > 38 || e == 0xFF;
+    const int64_t R = (int64_t)((uint64_t)mx << (lsh & 63));
+    return (b >> 31) ? -R : R;
+}
+
+// s <- RN(...RN(RN(s + v[0]) + v[1]) ... + v[ma - 1]) in FP64, ma <= 32 (a
+// lane with act = false, past the last coordinate, takes no FP64 step and
+// so holds up no other lane)
+__device__ __forceinline__ double chain_chunk(double s, const float (&v)[UC_B], int ma, bool act) {
+    constexpr uint64_t M52 = (1ull << 52) - 1;
+    const uint64_t bits = (uint64_t)__double_as_longlong(s);
+    const int E = (int)((bits >> 52) & 0x7FF);
+    const bool zero = bits == 0;  // +0 (the running sum never becomes -0)
+    // integer steps from +0 or from a normal s well inside the range
+    bool fast = zero || (E > 64 && E < 0x7FE - 64);
+    const uint64_t M = (bits & M52) | (1ull << 52);
+    // the unit 2^g: the finest ulp among the chunk's values and s's lowest set bit
+    int umin = 0x7FFFFFFF, emax = 0;
+#pragma unroll
+    for (int m = 0; m < UC_B; m++)
+        if (m < ma) {
+            const int e = (int)((__float_as_uint(v[m]) >> 23) & 0xFFu);
+            umin = min(umin, max(e, 1));
+            emax = max(emax, e);
+        }
+    const int qs = E - 1075;
+    const int g = zero ? umin - 150 : min(umin - 150, qs + __ffsll((long long)M) - 1);
+    int64_t T0 = 0;
+    if (!zero) {
+        const int sh = qs - g;  // > 0: s's ulp is coarser than a value's (s then needs more than 53 bits)
+        fast = fast && sh <= 10;
+        const uint64_t a0 = sh >= 0 ? (M << min(sh, 10)) : (M >> min(-sh, 63));  // exact: g <= s's lowest set bit
+        T0 = (bits >> 63) ? -(int64_t)a0 : (int64_t)a0;
+    }
+    const int base = 150 + g;
+    // every |x_i / 2^g| < 2^(24 + lmax) (0 <= lmax): if |T0| + 32 2^(24 + lmax)
+    // < 2^53, no partial sum can reach 2^53 and the chunk is one exact
+    // integer sum (any order); otherwise each partial sum is checked
+    const int lmax = max(emax, 1) - base;
+    const uint64_t aT0 = (uint64_t)(T0 < 0 ? -T0 : T0);
+    const bool easy = fast && emax != 0xFF && lmax <= 23 && aT0 + (1ull << (29 + lmax)) < (1ull << 53);
+    int64_t T = T0;
+    int f = ma;  // first step that takes the FP64 add
+    if (easy) {
+        int64_t p1 = 0, p2 = 0, p3 = 0;
+#pragma unroll
+        for (int m = 0; m < UC_B; m += 4) {
+            bool bad;
+            if (m < ma) T += units_of(v[m], base, bad);
+            if (m + 1 < ma) p1 += units_of(v[m + 1], base, bad);
+            if (m + 2 < ma) p2 += units_of(v[m + 2], base, bad);
+            if (m + 3 < ma) p3 += units_of(v[m + 3], base, bad);
+        }
+        T += p1 + p2 + p3;
+    } else if (act) {
+        uint32_t fail = fast ? 0u : 1u;
+#pragma unroll
+        for (int m = 0; m < UC_B; m++) {
+            if (m < ma) {
+                bool bad;
+                T += units_of(v[m], base, bad);
+                // |T| < 2^53: every partial sum is an FP64 value, each RN step exact
+                const bool ok = !bad && (uint64_t)(T + (int64_t)((1ull << 53) - 1)) < (1ull << 54) - 1;
+                if (!ok) fail |= 1u << m;
+            }
+        }
+        f = fail ? __ffs((int)fail) - 1 : ma;
+    }
+    if (f < ma && f > 0) {  // the integer sum up to step f - 1
+        T = T0;
+#pragma unroll
+        for (int m = 0; m < UC_B; m++)
+            if (m < f) {
+                bool bad;
+                T += units_of(v[m], base, bad);
+            }
+    }
+    double t = s;
+    if (f > 0 && act) {  // T 2^g, |T| < 2^53, as an FP64 value (exact)
+        const uint64_t a = (uint64_t)(T < 0 ? -T : T);
+        if (a == 0) {
+            t = 0.0;  // an exactly cancelling sum is +0 under RN
+        } else {
+            const int p = 64 - __clzll((long long)a);  // <= 53
+            const uint64_t mant = (a << (53 - p)) & M52;
+            t = __longlong_as_double(
+                (long long)(((uint64_t)(T < 0) << 63) | ((uint64_t)(g + 1075 + p - 53) << 52) | mant));
+        }
+    }
+    int fw = f;  // warp-uniform bound of the FP64 tail
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) fw = min(fw, __shfl_xor_sync(0xffffffffu, fw, o));
+    if (fw < ma) {
+#pragma unroll
+        for (int m = 0; m < UC_B; m++)
+            if (m >= fw && m < ma && m >= f) t = __dadd_rn(t, widen_f32(v[m]));
+    }
+    return t;
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, int bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src, int bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
 
 __global__ void __launch_bounds__(UC_T) k_update_centres(const float *__restrict__ x, int64_t ldx, int d, int64_t k,
                                                          const int64_t *__restrict__ off,
                                                          const unsigned long long *__restrict__ cnt,
                                                          const int32_t *__restrict__ ids, const uint64_t *__restrict__ order,
-                                                         double *__restrict__ c) {
-    __shared__ int32_t sid[UC_CH];
-    extern __shared__ float stg[];  // [UC_S][UC_G][UC_T]
-    for (int64_t jq = blockIdx.x; jq < k; jq += gridDim.x) {
-        const int64_t j = (int64_t)(order[jq] & 0xFFFFFFFFull);
+                                                         unsigned long long *__restrict__ next, double *__restrict__ c) {
+    extern __shared__ float uc_ring[];  // [UC_W][UC_S][32 rows][32 floats]
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float *ring = uc_ring + (size_t)wib * UC_S * UC_STAGE;
+    const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring);
+    const int nsl = (d + 31) >> 5;
+    const int64_t nitems = k * nsl;
+    const bool vec = (((uintptr_t)x & 15) == 0) && ((ldx & 3) == 0);
+    const int64_t nw = (int64_t)gridDim.x * UC_W;
+    int64_t it = (int64_t)wib * gridDim.x + blockIdx.x;  // first wave: slices of a centre on different SMs
+    while (it < nitems) {
+        const int64_t j = (int64_t)(order[it / nsl] & 0xFFFFFFFFull);
+        const int t0 = (int)(it % nsl) * 32, t = t0 + lane;
+        const int width = min(32, d - t0);
         const int64_t cj = (int64_t)cnt[j];
-        if (cj == 0) continue;  // block-uniform
-        const int64_t s0 = off[j];
-        for (int t0 = 0; t0 < d; t0 += UC_T) {
-            const int t = t0 + threadIdx.x;
-            const bool act = t < d;
-            double s = 0.0;
-            for (int64_t p0 = 0; p0 < cj; p0 += UC_CH) {
-                const int len = (int)min((int64_t)UC_CH, cj - p0);
-                __syncthreads();  // the previous chunk's ids are no longer read
-                for (int e = threadIdx.x; e < len; e += UC_T) sid[e] = ids[s0 + p0 + e];
-                __syncthreads();
-                const int ng = (len + UC_G - 1) / UC_G;
-                auto issue = [&](int g) {
-                    if (g < ng && act) {
-                        float *dst = stg + (size_t)(g % UC_S) * UC_G * UC_T + threadIdx.x;
-                        const int q1 = min(UC_G, len - g * UC_G);
-                        for (int q = 0; q < q1; q++) cp_async4(dst + q * UC_T, x + (int64_t)sid[g * UC_G + q] * ldx + t);
-                    }
-                    cp_async_commit();  // empty groups keep the count uniform
-                };
-                for (int g = 0; g < UC_S - 1; g++) issue(g);
-                for (int g = 0; g < ng; g++) {
-                    issue(g + UC_S - 1);
-                    cp_async_wait<UC_S - 1>();
-                    if (act) {
-                        const float *src = stg + (size_t)(g % UC_S) * UC_G * UC_T + threadIdx.x;
-                        const int q1 = min(UC_G, len - g * UC_G);
-                        for (int q = 0; q < q1; q++) s = __dadd_rn(s, (double)src[q * UC_T]);
+        if (cj > 0) {  // warp-uniform
+            const int32_t *mid = ids + off[j];
+            const float *xs = x + t0;
+            const int col = (lane & 7) * 4;  // this lane's 16 bytes of a row slice (vector copies)
+            const int nbytes = max(0, min(16, (width - col) * 4));
+            const int64_t ng = (cj + UC_B - 1) / UC_B;
+            // ids of the next four groups to issue (loaded four stages ahead)
+            auto ld_id = [&](int64_t g) -> int32_t {
+                const int64_t q = g * UC_B + lane;
+                return q < cj ? mid[q] : 0;
+            };
+            int32_t id0 = ld_id(0), id1 = ld_id(1), id2 = ld_id(2), id3 = ld_id(3);
+            auto issue = [&](int64_t g) {
+                if (g < ng) {
+                    const int32_t my = id0;
+                    id0 = id1;
+                    id1 = id2;
+                    id2 = id3;
+                    id3 = ld_id(g + 4);
+                    const int rows = (int)min((int64_t)UC_B, cj - g * UC_B);
+                    const uint32_t sb = ring_s + (uint32_t)((g & (UC_S - 1)) * UC_STAGE * sizeof(float));
+                    if (vec) {
+#pragma unroll
+                        for (int i = 0; i < UC_B / 4; i++) {
+                            const int rr = 4 * i + (lane >> 3);
+                            const int32_t r = __shfl_sync(0xffffffffu, my, rr);
+                            if (rr < rows)
+                                cp_async16(sb + (uint32_t)(rr * 32 + col) * 4u, xs + (int64_t)r * ldx + (nbytes ? col : 0),
+                                           nbytes);
+                        }
+                    } else {
+#pragma unroll 8
+                        for (int rr = 0; rr < UC_B; rr++) {
+                            const int32_t r = __shfl_sync(0xffffffffu, my, rr);
+                            if (rr < rows)
+                                cp_async4(sb + (uint32_t)(rr * 32 + lane) * 4u, xs + (int64_t)r * ldx + (lane < width ? lane : 0),
+                                          lane < width ? 4 : 0);
+                        }
                     }
                 }
-                cp_async_wait<0>();
+                asm volatile("cp.async.commit_group;" ::: "memory");  // empty groups keep the count uniform
+            };
+#pragma unroll 1
+            for (int g = 0; g < UC_S - 1; g++) issue(g);
+            double s = 0.0;
+            for (int64_t g = 0; g < ng; g++) {
+                issue(g + UC_S - 1);
+                asm volatile("cp.async.wait_group %0;" ::"n"(UC_S - 1) : "memory");
+                __syncwarp();  // the stage's rows, copied by all lanes, are visible to all
+                const float *src = ring + (g & (UC_S - 1)) * UC_STAGE + lane;
+                float v[UC_B];
+#pragma unroll
+                for (int m = 0; m < UC_B; m++) v[m] = src[m * 32];
+                s = chain_chunk(s, v, (int)min((int64_t)UC_B, cj - g * UC_B), lane < width);
+                __syncwarp();  // reads done before the stage is refilled
             }
-            if (act) c[j * d + t] = __ddiv_rn(s, (double)cj);
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            __syncwarp();
+            if (lane < width) c[j * d + t] = __ddiv_rn(s, (double)cj);
         }
+        unsigned long long got = 0;
+        if (lane == 0) got = atomicAdd(next, 1ull);
+        it = nw + (int64_t)__shfl_sync(0xffffffffu, got, 0);
     }
 }
 
@@ -838,6 +1023,7 @@ geek_status refine_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ld
         GK_TRY(ps.alloc(&cnt, k));
         GK_TRY(ps.alloc(&off, k));
         GK_TRY(ps.alloc(&bad, 1));
+        EvTimer tg(ctx, "refine.group", st);
         GK_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * k, st));
         GK_CUDA(ctx, cudaMemsetAsync(bad, 0, sizeof(int), st));
         GK_COUNT();
@@ -851,19 +1037,26 @@ geek_status refine_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ld
         k_size_order<<<grid_for(k, 256, ctx->num_sms), 256, 0, st>>>(k, cnt, order);
         GK_LAUNCH(ctx);
         GK_TRY(radix_sort_segments(ctx, ps, 1, k, &order, nullptr, nullptr, 64, st));
+        tg.stop();
+        unsigned long long *next;
+        GK_TRY(ps.alloc(&next, 1));
+        GK_CUDA(ctx, cudaMemsetAsync(next, 0, sizeof(unsigned long long), st));
         static bool uc_attr = false;
         if (!uc_attr) {
-            GK_CUDA(ctx, cudaFuncSetAttribute(k_update_centres, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UC_SMEM));
+            GK_CUDA(ctx, cudaFuncSetAttribute(k_update_centres, cudaFuncAttributeMaxDynamicSharedMemorySize, UC_SMEM));
             uc_attr = true;
         }
+        EvTimer tu(ctx, "kernel.update_centres", st);
         GK_COUNT();
-        k_update_centres<<<(unsigned)std::min<int64_t>(k, (int64_t)ctx->num_sms * 8), UC_T, UC_SMEM, st>>>(
-            x, ldx, d, k, off, cnt, (const int32_t *)ids, order, centres);
+        k_update_centres<<<(unsigned)std::min<int64_t>((k * ((d + 31) / 32) + UC_W - 1) / UC_W, (int64_t)ctx->num_sms),
+                           UC_T, UC_SMEM, st>>>(x, ldx, d, k, off, cnt, (const int32_t *)ids, order, next, centres);
         GK_LAUNCH(ctx);
+        tu.stop();
         int h_bad = 0;
         GK_CUDA(ctx, cudaMemcpyAsync(&h_bad, bad, sizeof h_bad, cudaMemcpyDeviceToHost, st));
         GK_TRY(sort_err_check(ctx, st));  // synchronises st
         if (h_bad) return set_error(ctx, GEEK_ERR_INVALID, "a label outside [-1, k)");
+        EvTimer ta(ctx, "refine.assign", st);
         GK_TRY(assign_dense_centres(ctx, ps, x, ldx, n, d, centres, k, precision, labels, stats, st));
     }
     return GEEK_OK;

@@ -341,6 +341,67 @@ def test_refine_passes_exact(G, ctx, prec):
     assert abs(st.sse - sse) <= 1e-6 * sse
 
 
+@pytest.mark.parametrize("d", [70, 128])
+def test_refine_ragged_slices_and_large_clusters(G, ctx, d):
+    """The centre update works on 32-coordinate slices of a centre: d = 70
+    leaves a ragged slice of 6; one cluster holds most rows (its member list
+    spans many 32-row batches and ends mid-batch); rows come from a strided
+    view (row pitch d + 10)."""
+    rng = np.random.default_rng(11 + d)
+    n, k = 7001, 6
+    full = rng.standard_normal((n, d + 10)).astype(np.float32)
+    full[: n - 300, :d] += 4.0  # the big cluster
+    x = full[:, :d]
+    c0 = rng.standard_normal((k, d)) * 2
+    c0[0] += 4.0
+    lab0, _ = oracle.assign_dense(np.ascontiguousarray(x), c0)
+    xt = G._dev(full)[:, :d]
+    cd = G._dev(c0)
+    labels = G._dev(lab0.astype(np.int32))
+    ctx.refine(ctx.dense(xt), cd, labels, 2, precision=G.PREC_BF16)
+    torch.cuda.synchronize()
+    lab_ref, c_ref, _ = oracle.refine_passes(np.ascontiguousarray(x), c0, lab0, 2)
+    assert np.bincount(lab_ref, minlength=k).max() > 5000
+    assert np.array_equal(labels.cpu().numpy(), lab_ref)
+    assert np.array_equal(cd.cpu().numpy(), c_ref)
+
+
+def _hard_sum_rows(n, rng):
+    """Rows whose coordinates make the centre update's running FP64 sums
+    change binade often, hit exact half-ulp ties, span FP32 exponents from
+    -149 to 20 (subnormals included), or hold signed zeros."""
+    d = 96
+    x = np.zeros((n, d), dtype=np.float32)
+    x[:, 0:16] = rng.standard_normal((n, 16))                        # random walks around 0
+    x[:, 16:24] = np.where(np.arange(n)[:, None] % 2 == 0, 1.0, 2.0 ** -53)  # ties at s near 1
+    x[:, 24:32] = np.where(np.arange(n)[:, None] % 3 == 0, 3.0, -(2.0 ** -52) * 3)
+    e = rng.integers(-149, 21, (n, 24))
+    x[:, 32:56] = (rng.uniform(1, 2, (n, 24)) * rng.choice([-1.0, 1.0], (n, 24)) * np.exp2(e.astype(np.float64)))
+    x[:, 56:64] = np.where(rng.random((n, 8)) < 0.5, 0.0, -0.0)       # signed zeros
+    x[:, 64:72] = rng.uniform(-1e-38, 1e-38, (n, 8))                   # around the FP32 subnormal range
+    x[:, 72:96] = rng.normal(20.0, 1.0, (n, 24))                       # linear growth
+    return x
+
+
+def test_refine_centre_update_hard_sums(G, ctx):
+    """The centre update's integer steps and their FP64 fallback: one live
+    cluster of rows built to change binade, tie and underflow; its FP64 mean
+    (ascending id) must equal the oracle's bit for bit."""
+    rng = np.random.default_rng(23)
+    n = 5003
+    x = _hard_sum_rows(n, rng)
+    c0 = np.zeros((2, x.shape[1]))
+    c0[1] = 1e6  # nobody's nearest: stays unchanged
+    lab0 = np.zeros(n, dtype=np.int32)
+    cd = G._dev(c0)
+    labels = G._dev(lab0)
+    ctx.refine(ctx.dense(G._dev(x)), cd, labels, 1, precision=G.PREC_FP32)
+    torch.cuda.synchronize()
+    _, c_ref, _ = oracle.refine_passes(x, c0, lab0, 1)
+    got = cd.cpu().numpy()
+    assert np.array_equal(got.view(np.uint64), c_ref.view(np.uint64))
+
+
 def test_refine_invalid_labels(G, ctx):
     wl = synth.make(synth.config("c1", n=500))
     c = G._dev(wl["centres"].astype(np.float64))
