@@ -66,7 +66,7 @@ constexpr uint32_t PT_TMEM_COLS = 512;             // 2 buffers x (P, Q) x 128 c
 constexpr int PT_OFF_SPLIT = PT_A_MAX;
 constexpr int PT_OFF_F32 = PT_OFF_SPLIT + PT_SPLIT_STAGES * PT_SPLIT_STAGE;
 constexpr int PT_OFF_MISC = PT_OFF_F32 + PT_F32_STAGES * PT_F32_STAGE;
-constexpr int PT_MISC = 4096;
+constexpr int PT_MISC = 6144;
 constexpr int PT_SMEM = PT_OFF_MISC + PT_MISC + 1024;  // + alignment slack
 static_assert(PT_SMEM <= 232448, "shared memory of one CTA");
 static_assert(PT_A_MAX % 1024 == 0 && PT_OFF_F32 % 1024 == 0, "1 KB alignment of the swizzled tiles");
@@ -149,10 +149,10 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_project_tc(const __grid_const
     uint64_t *done_bar = bars + 19;
     uint32_t *tmem_slot = (uint32_t *)(bars + 20);
     float *rownorm = (float *)(base + PT_OFF_MISC + 256);   // [2][128]
-    float *s_b = rownorm + 2 * PT_M;                         // [128]
-    float *s_an = s_b + PT_NMAX;                             // [128]
-    int *s_min = (int *)(s_an + PT_NMAX);                    // [128]
+    int *s_min = (int *)(rownorm + 2 * PT_M);                // [128]
     int *s_max = s_min + PT_NMAX;                            // [128]
+    float4 *s_pk = (float4 *)(s_max + PT_NMAX);              // [128] {b, alpha, beta, 0} of the cell test
+    float *s_lim = (float *)(s_pk + PT_NMAX);                // max |a_f| / w, max |b_f| / w
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -173,10 +173,32 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_project_tc(const __grid_const
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     for (int f = threadIdx.x; f < PT_NMAX; f += blockDim.x) {
-        s_b[f] = f < A.F ? A.b[f] : 0.f;
-        s_an[f] = f < A.F ? A.anorm[f] : 0.f;
+        const float bb = f < A.F ? A.b[f] : 0.f, an = f < A.F ? A.anorm[f] : 0.f;
         s_min[f] = INT32_MAX;
         s_max[f] = INT32_MIN;
+        // One FFMA bound of the cell test's window (fast loop of the epilogue),
+        // Et = alpha |x| + beta >= the general loop's Et + 6e-8 for every p
+        // the accumulator can hold (|p| <= |a_f| |x| + E): alpha and beta
+        // carry 1e-5 for their own and the FFMA's FP32 rounding, the 6e-8
+        // the rounding of tt - floor(tt) and of 1 - Et.
+        float al, be;
+        if (A.srp) {
+            al = an * (A.coef * 1.000001f + 1.21e-7f) * 1.00001f;
+            be = 1.1e-30f;
+        } else {
+            al = A.inv_w * an * (A.coef * 1.000001f + 5.02e-7f) * 1.00001f;
+            be = A.inv_w * (fabsf(bb) * 5.02e-7f + 1.1e-30f) * 1.00001f + 6e-8f;
+        }
+        s_pk[f] = make_float4(bb, al, be, 0.f);
+    }
+    if (threadIdx.x == 0) {
+        float am = 0.f, bm = 0.f;
+        for (int f = 0; f < A.F; f++) {
+            am = fmaxf(am, A.anorm[f]);
+            bm = fmaxf(bm, fabsf(A.b[f]));
+        }
+        s_lim[0] = am * A.inv_w * 1.00001f;
+        s_lim[1] = bm * A.inv_w * 1.00001f;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
@@ -275,6 +297,9 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_project_tc(const __grid_const
             const int64_t row = t * PT_M + rloc;
             const bool live = row < A.n;
             const float xn = sqrtf(rownorm[buf * PT_M + rloc]) * (1.f + 1e-4f);
+            // |tt| <= (|a_f| |x| (1 + E) + |b_f|) / w stays far below 2^31 in every
+            // row of the tile (E2LSH; SRP has no tt)
+            const bool fastrows = __all_sync(0xffffffffu, live && (A.srp || s_lim[0] * xn + s_lim[1] < 1e9f));
             __syncwarp();
             if (lane == 0) mbar_arrive(&nrm_empty[buf]);
             for (int gi = e; gi < ngrp; gi += PT_EPI_PER_Q) {
@@ -285,33 +310,64 @@ __global__ void __launch_bounds__(PT_THREADS, 1) k_project_tc(const __grid_const
                 tmem_wait_ld();
                 uint32_t flagged = 0;
                 int lmin = INT32_MAX, lmax = INT32_MIN;
+                if (fastrows && gi * 16 + 16 <= A.F) {
+                    // every row live, every column a function, no |tt| near 2^31:
+                    // the cell test with the one-FFMA window, no guards
 #pragma unroll
-                for (int j = 0; j < 16; j++) {
-                    const int f = gi * 16 + j;
-                    const bool fv = live && f < A.F;
-                    const float p = __uint_as_float(rp[j]) + __uint_as_float(rq[j]);
-                    const float E = A.coef * s_an[f] * xn + 1e-30f;
-                    int code;
-                    bool sure;
-                    if (A.srp) {
-                        const float Es = E + fabsf(p) * 1.2e-7f;
-                        code = p >= 0.f ? 1 : 0;
-                        sure = (p - Es > 0.f) || (p + Es < 0.f);
-                    } else {
-                        const float bb = s_b[f];
-                        const float tt = (p + bb) * A.inv_w;
-                        const float Et = (E + (fabsf(p) + fabsf(bb) + E) * 2.5e-7f) * A.inv_w + fabsf(tt) * 2.5e-7f;
-                        const float c0 = floorf(tt);
-                        code = fabsf(tt) < 2.0e9f ? (int)c0 : 0;
-                        sure = (tt - Et >= c0) && (tt + Et < c0 + 1.f) && fabsf(tt) < 2.0e9f;
+                    for (int j = 0; j < 16; j++) {
+                        const float4 pk = s_pk[gi * 16 + j];
+                        const float p = __uint_as_float(rp[j]) + __uint_as_float(rq[j]);
+                        const float Et = fmaf(pk.y, xn, pk.z);
+                        int code;
+                        bool sure;
+                        if (A.srp) {
+                            code = p >= 0.f ? 1 : 0;
+                            sure = fabsf(p) > Et;
+                        } else {
+                            const float tt = (p + pk.x) * A.inv_w;
+                            const float c0 = floorf(tt);
+                            const float fr = tt - c0;
+                            code = (int)c0;
+                            sure = fr >= Et && fr < 1.f - Et;
+                        }
+                        rp[j] = (uint32_t)code;
+                        if (!sure) flagged |= 1u << j;
+                        const int mn = __reduce_min_sync(0xffffffffu, code);
+                        const int mx = __reduce_max_sync(0xffffffffu, code);
+                        if (lane == j) {
+                            lmin = mn;
+                            lmax = mx;
+                        }
                     }
-                    rp[j] = (uint32_t)code;  // the codes replace P in place
-                    if (fv && !sure) flagged |= 1u << j;
-                    const int mn = __reduce_min_sync(0xffffffffu, fv ? code : INT32_MAX);
-                    const int mx = __reduce_max_sync(0xffffffffu, fv ? code : INT32_MIN);
-                    if (lane == j) {
-                        lmin = mn;
-                        lmax = mx;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; j++) {
+                        const int f = gi * 16 + j;
+                        const bool fv = live && f < A.F;
+                        const float4 pk = s_pk[f];
+                        const float p = __uint_as_float(rp[j]) + __uint_as_float(rq[j]);
+                        const float Et = fmaf(pk.y, xn, pk.z);
+                        int code;
+                        bool sure;
+                        if (A.srp) {
+                            code = p >= 0.f ? 1 : 0;
+                            sure = fabsf(p) > Et;
+                        } else {
+                            const float tt = (p + pk.x) * A.inv_w;
+                            const float c0 = floorf(tt);
+                            const float fr = tt - c0;
+                            const bool small = fabsf(tt) < 2.0e9f;
+                            code = small ? (int)c0 : 0;
+                            sure = small && fr >= Et && fr < 1.f - Et;
+                        }
+                        rp[j] = (uint32_t)code;  // the codes replace P in place
+                        if (fv && !sure) flagged |= 1u << j;
+                        const int mn = __reduce_min_sync(0xffffffffu, fv ? code : INT32_MAX);
+                        const int mx = __reduce_max_sync(0xffffffffu, fv ? code : INT32_MIN);
+                        if (lane == j) {
+                            lmin = mn;
+                            lmax = mx;
+                        }
                     }
                 }
                 if (lane < 16 && gi * 16 + lane < A.F && lmin <= lmax) {
