@@ -479,7 +479,8 @@ def bench_alg1_pipeline(args, geek, ctx, data, wl, world, pk, pk_kind):
     ctx.timing(False)
     ms = e0.elapsed_time(e1) / args.steps
     names = ["hash", "silk", "assign", "hash.sort", "kernel.project_dot2", "kernel.assign_tc", "kernel.assign_fp32",
-             "kernel.assign_recheck", "silk.vbuckets", "silk.bins", "silk.vote", "silk.dedup"]
+             "kernel.assign_recheck", "kernel.assign_refine32", "kernel.assign_decide64", "silk.vbuckets",
+             "silk.bins", "silk.vote", "silk.dedup"]
     tm = {k: ctx.timing_get(k) for k in names}
     atc = tm["kernel.assign_tc"]
     roof = None

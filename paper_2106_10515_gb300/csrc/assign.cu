@@ -191,18 +191,50 @@ __global__ void __launch_bounds__(256) k_assign_fp32(FArgs A, GatherUnits U) {
     }
 }
 
-// FP64 decision of the rows a refine pass left uncertain, tiled like
-// k_assign_fp32<true>: units of up to 128 such rows of one instance, all
+// The tiled FP64 decision of the rows the FP32 refine leaves uncertain: the
 // centres streamed through shared memory in tiles, the FP32 fast value of
 // every (row, centre) pair in registers.  A pair whose fast value lies within
 // the row's window lim = m + 2W (m: the row's smallest fast value, from the
 // refine pass, in mrow[global row]) gets the FP64 reference distance, read
 // from the row in shared memory; the row's label is the smallest reference
 // distance, ties to the smaller index (-1 when no value is finite).
+//
+// The FP64 distances are a chain of d dependent adds each, and the FP64 pipe
+// issues one warp-wide operation about every 19 cycles per SM: computed by
+// the thread that found the pair, one active lane would pay for a whole
+// warp.  So the tile's pairs go to a shared-memory queue and the block takes
+// them a lane each (in rounds of at most DQ_CAP pairs); each row's best is
+// kept in shared memory as the smallest D (an atomic minimum on its bits: D
+// >= 0, so the bit order is the value order), then the smallest index among
+// the pairs that reach it.
+constexpr int DQ_CAP = 2048;
+constexpr size_t DQ_BYTES = (size_t)DQ_CAP * (sizeof(double) + sizeof(uint16_t));
+
+// exact FP32 -> FP64 widening in integer operations (normal, subnormal, zero,
+// infinity; a NaN stays a NaN): keeps the conversion off the FP64 pipe
+__device__ __forceinline__ double widen_f32(float v) {
+    const uint32_t b = __float_as_uint(v);
+    const uint32_t sg = b & 0x80000000u, e = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
+    // subnormal: m = 1.f x 2^(p - 23) with p the top set bit, value m 2^-149
+    const int sh = __clz((int)m) - 8;  // brings the top bit of m to bit 23
+    const uint32_t ms = (m << (sh & 31)) & 0x7FFFFFu;
+    const uint32_t es = (uint32_t)(1023 - 126 - sh);
+    uint32_t hi, lo;
+    if (e == 0u) {
+        hi = m == 0u ? sg : (sg | (es << 20) | (ms >> 3));
+        lo = m == 0u ? 0u : (ms << 29);
+    } else {
+        const uint32_t ed = e == 0xFFu ? 0x7FFu : e + 896u;
+        hi = sg | (ed << 20) | (m >> 3);
+        lo = m << 29;
+    }
+    return __hiloint2double((int)hi, (int)lo);
+}
+
 __device__ __forceinline__ double ref_dist_strided(const float *x, int stride, const double *__restrict__ c, int d) {
     double D = 0.0;
     for (int t = 0; t < d; t++) {
-        const double e = __dsub_rn((double)x[t * stride], c[t]);
+        const double e = __dsub_rn(widen_f32(x[t * stride]), c[t]);
         D = __dadd_rn(D, __dmul_rn(e, e));
     }
     return D;
@@ -212,6 +244,10 @@ __global__ void __launch_bounds__(256) k_assign_decide64(GatherUnits U, const fl
     extern __shared__ float sm[];
     __shared__ float cns[AS_TC];
     __shared__ int64_t s_rows[AS_TR];
+    __shared__ unsigned long long sbD[AS_TR], prevD[AS_TR];
+    __shared__ int sbJ[AS_TR], tJ[AS_TR];
+    __shared__ int s_qn;
+    constexpr unsigned long long DINF = 0x7FF0000000000000ull;  // above every finite D
     const int t = threadIdx.x, cg = t & 15, rg = t >> 4;
     const int64_t nunits = (int64_t)*U.n_units;
     for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
@@ -222,9 +258,18 @@ __global__ void __launch_bounds__(256) k_assign_decide64(GatherUnits U, const fl
         const int nrows = U.unit_cnt[u];
         __syncthreads();  // s_rows and xs of the previous unit fully used
         if (t < nrows) s_rows[t] = (int64_t)U.grows[U.unit_start[u] + t] - rbase;
+        if (t < AS_TR) {
+            sbD[t] = DINF;
+            prevD[t] = DINF;
+            sbJ[t] = 0x7FFFFFFF;
+            tJ[t] = 0x7FFFFFFF;
+        }
+        if (t == 0) s_qn = 0;
         __syncthreads();
         float *xs = sm;                      // [d][AS_TR]
         float *cs = sm + (size_t)d * AS_TR;  // [AS_KC][AS_TC]
+        double *qd = reinterpret_cast<double *>(cs + AS_KC * AS_TC);  // [DQ_CAP]
+        uint16_t *qi = reinterpret_cast<uint16_t *>(qd + DQ_CAP);     // [DQ_CAP]: row * AS_TC + column
         for (int e = t; e < AS_TR * d; e += 256) {
             const int r = e / d, kk = e % d;
             xs[kk * AS_TR + r] = r < nrows ? I.x[s_rows[r] * I.ldx + kk] : 0.f;
@@ -232,8 +277,6 @@ __global__ void __launch_bounds__(256) k_assign_decide64(GatherUnits U, const fl
         __syncthreads();
         const float cmax = __uint_as_float(*I.cmax_bits);
         float lim[AS_RPT];
-        double bD[AS_RPT];
-        int bj[AS_RPT];
 #pragma unroll
         for (int r = 0; r < AS_RPT; r++) {
             const int rr = rg * AS_RPT + r;
@@ -242,8 +285,6 @@ __global__ void __launch_bounds__(256) k_assign_decide64(GatherUnits U, const fl
             const float xn = sqrtf(xs2) * (1.f + 1.0e-3f);
             const float m = rr < nrows ? mrow[rbase + s_rows[rr]] : __int_as_float(0x7fc00000);
             lim[r] = m + 2.f * window_fp32(xn, cmax, d) * (1.f + 1e-6f);
-            bD[r] = DBL_MAX;
-            bj[r] = 0x7FFFFFFF;
         }
         for (int64_t j0 = 0; j0 < k; j0 += AS_TC) {
             float acc[AS_RPT][AS_CPT];
@@ -273,44 +314,63 @@ __global__ void __launch_bounds__(256) k_assign_decide64(GatherUnits U, const fl
                         for (int c = 0; c < AS_CPT; c++) acc[r][c] = fmaf(xv[r], cc[c], acc[r][c]);
                 }
             }
+            // this thread's pairs inside the window: bit r * AS_CPT + c
+            uint32_t pend = 0;
 #pragma unroll
             for (int c = 0; c < AS_CPT; c++) {
                 const int64_t j = j0 + cg * AS_CPT + c;
-                if (j >= k) continue;
                 const float cnj = cns[cg * AS_CPT + c];
 #pragma unroll
                 for (int r = 0; r < AS_RPT; r++) {
                     const int rr = rg * AS_RPT + r;
-                    if (rr < nrows && fmaf(-2.f, acc[r][c], cnj) <= lim[r]) {
-                        const double D = ref_dist_strided(xs + rr, AS_TR, I.c64 + j * d, d);
-                        if (D < bD[r] || (D == bD[r] && (int)j < bj[r])) {
-                            bD[r] = D;
-                            bj[r] = (int)j;
-                        }
+                    if (j < k && rr < nrows && fmaf(-2.f, acc[r][c], cnj) <= lim[r]) pend |= 1u << (r * AS_CPT + c);
+                }
+            }
+            if (!__syncthreads_or(pend != 0)) continue;
+            for (;;) {
+                // queue what fits; the rest waits for the next round
+                const int np = __popc(pend);
+                int pos = np ? atomicAdd(&s_qn, np) : 0;
+                uint32_t rest = 0;
+                for (uint32_t m = pend; m; m &= m - 1) {
+                    const int bt = __ffs((int)m) - 1;
+                    if (pos < DQ_CAP)
+                        qi[pos] = (uint16_t)((rg * AS_RPT + bt / AS_CPT) * AS_TC + cg * AS_CPT + bt % AS_CPT);
+                    else
+                        rest |= 1u << bt;
+                    pos++;
+                }
+                pend = rest;
+                __syncthreads();
+                const int nq = min(s_qn, DQ_CAP);
+                for (int e = t; e < nq; e += 256) {
+                    const int ee = qi[e];
+                    const int rr = ee / AS_TC;
+                    const double D = ref_dist_strided(xs + rr, AS_TR, I.c64 + (j0 + ee % AS_TC) * d, d);
+                    qd[e] = D;
+                    atomicMin(&sbD[rr], (unsigned long long)__double_as_longlong(D));
+                }
+                __syncthreads();
+                for (int e = t; e < nq; e += 256) {
+                    const int ee = qi[e];
+                    const int rr = ee / AS_TC;
+                    if ((unsigned long long)__double_as_longlong(qd[e]) == sbD[rr])
+                        atomicMin(&tJ[rr], (int)(j0 + ee % AS_TC));
+                }
+                __syncthreads();
+                if (t < AS_TR) {
+                    if (tJ[t] != 0x7FFFFFFF) {
+                        // a new smallest D: its smallest index; the same D again: the smaller index
+                        sbJ[t] = sbD[t] < prevD[t] ? tJ[t] : min(sbJ[t], tJ[t]);
+                        tJ[t] = 0x7FFFFFFF;
                     }
+                    prevD[t] = sbD[t];
                 }
+                if (t == 0) s_qn = 0;
+                if (!__syncthreads_or(pend != 0)) break;
             }
         }
-        // merge the 16 centre groups of each row (lanes of one half-warp)
-#pragma unroll
-        for (int r = 0; r < AS_RPT; r++) {
-#pragma unroll
-            for (int o = 1; o < 16; o <<= 1) {
-                const double D2 = __shfl_xor_sync(0xffffffffu, bD[r], o);
-                const int j2 = __shfl_xor_sync(0xffffffffu, bj[r], o);
-                if (D2 < bD[r] || (D2 == bD[r] && j2 < bj[r])) {
-                    bD[r] = D2;
-                    bj[r] = j2;
-                }
-            }
-        }
-        if (cg == 0) {
-#pragma unroll
-            for (int r = 0; r < AS_RPT; r++) {
-                const int rr = rg * AS_RPT + r;
-                if (rr < nrows) I.labels[s_rows[rr]] = bj[r] == 0x7FFFFFFF ? -1 : bj[r];
-            }
-        }
+        if (t < nrows) I.labels[s_rows[t]] = sbJ[t] == 0x7FFFFFFF ? -1 : sbJ[t];
     }
 }
 
@@ -786,27 +846,6 @@ __global__ void k_size_order(int64_t k, const unsigned long long *__restrict__ c
 constexpr int UC_W = 4, UC_T = 32 * UC_W, UC_B = 32, UC_S = 8;
 constexpr int UC_STAGE = UC_B * 32;                              // floats per stage
 constexpr int UC_SMEM = UC_W * UC_S * UC_STAGE * (int)sizeof(float);  // 128 KB
-
-// exact FP32 -> FP64 widening in integer operations (normal, subnormal, zero,
-// infinity; a NaN stays a NaN)
-__device__ __forceinline__ double widen_f32(float v) {
-    const uint32_t b = __float_as_uint(v);
-    const uint32_t sg = b & 0x80000000u, e = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
-    // subnormal: m = 1.f x 2^(p - 23) with p the top set bit, value m 2^-149
-    const int sh = __clz((int)m) - 8;  // brings the top bit of m to bit 23
-    const uint32_t ms = (m << (sh & 31)) & 0x7FFFFFu;
-    const uint32_t es = (uint32_t)(1023 - 126 - sh);
-    uint32_t hi, lo;
-    if (e == 0u) {
-        hi = m == 0u ? sg : (sg | (es << 20) | (ms >> 3));
-        lo = m == 0u ? 0u : (ms << 29);
-    } else {
-        const uint32_t ed = e == 0xFFu ? 0x7FFu : e + 896u;
-        hi = sg | (ed << 20) | (m >> 3);
-        lo = m << 29;
-    }
-    return __hiloint2double((int)hi, (int)lo);
-}
 
 // x / 2^g as a signed integer, x = +-mx 2^u with base = 150 + g and u >= g:
 // exact for u - g <= 38 (then |x / 2^g| < 2^62); bad beyond that or when x
@@ -1286,14 +1325,17 @@ geek_status decide_flags(geek_ctx *ctx, const RInst *R, const int64_t *row_off, 
     A.flag_m = B.flags2_m;
     A.n_flag = B.n_flag2;
     GatherUnits U{R, B.grows, B.unit_inst, B.unit_start, B.unit_cnt, B.n_units};
+    EvTimer t32(ctx, "kernel.assign_refine32", st);
     GK_COUNT();
     k_assign_fp32<true><<<ctx->num_sms * 2, 256, smem, st>>>(A, U);
     GK_LAUNCH(ctx);
+    t32.stop();
     // the rows still uncertain, grouped by instance again, go to the tiled
     // FP64 decision with their smallest FP32 value
     static bool attr64 = false;
     if (!attr64) {
-        const size_t mx = (size_t)AS_MAXD * AS_TR * sizeof(float) + (size_t)AS_KC * AS_TC * sizeof(float);
+        const size_t mx =
+            (size_t)AS_MAXD * AS_TR * sizeof(float) + (size_t)AS_KC * AS_TC * sizeof(float) + DQ_BYTES;
         GK_CUDA(ctx, cudaFuncSetAttribute(k_assign_decide64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
         attr64 = true;
     }
@@ -1306,8 +1348,9 @@ geek_status decide_flags(geek_ctx *ctx, const RInst *R, const int64_t *row_off, 
     k_flag_units<<<1, 1024, 0, st>>>(B.cnt, count, B.cursor, B.unit_inst, B.unit_start, B.unit_cnt, B.n_units);
     GK_COUNT();
     k_flag_scatter<<<g, 256, 0, st>>>(B.flags2, B.n_flag2, row_off, count, B.cursor, B.grows);
+    EvTimer t64(ctx, "kernel.assign_decide64", st);
     GK_COUNT();
-    k_assign_decide64<<<ctx->num_sms * 2, 256, smem, st>>>(U, B.mrow);
+    k_assign_decide64<<<ctx->num_sms * 2, 256, smem + DQ_BYTES, st>>>(U, B.mrow);
     GK_LAUNCH(ctx);
     return GEEK_OK;
 }

@@ -317,6 +317,26 @@ def test_alg1_invalid(G, ctx):
         assert e.value.status == G.ERR_INVALID
 
 
+def test_assign_all_centres_in_the_window(G, ctx):
+    """Every centre nearly equal: each flagged row has every centre of a tile
+    inside its window (128 x 64 pairs per tile, several rounds of the FP64
+    decision's queue), with exact duplicates for the index tie-break."""
+    rng = np.random.default_rng(17)
+    n, d, k = 3000, 32, 200
+    x = (rng.standard_normal((n, d)) * 2).astype(np.float32)
+    base = rng.standard_normal(d) * 2
+    c = base[None, :] + rng.standard_normal((k, d)) * 1e-9
+    c[100:] = c[:100]  # exact duplicates
+    lab_ref, _ = oracle.assign_dense(x, c)
+    for prec in (G.PREC_FP32, G.PREC_BF16, G.PREC_BF16X3):
+        labels = torch.empty(n, dtype=torch.int32, device="cuda")
+        st = ctx.assign_centers(ctx.dense(G._dev(x)), G._dev(c), labels, precision=prec)
+        torch.cuda.synchronize()
+        if prec != G.PREC_FP32:  # the tensor-core forms end in the tiled FP64 decision
+            assert st.n_fp64_rows > n // 2
+        assert np.array_equal(labels.cpu().numpy(), lab_ref)
+
+
 # ------------------------------------- extra passes of assignment (Sect. 5) --
 @pytest.mark.parametrize("prec", ["bf16", "fp32"])
 def test_refine_passes_exact(G, ctx, prec):
