@@ -594,6 +594,10 @@ __global__ void __launch_bounds__(256) k_assign_stats(const float *__restrict__ 
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double s = 0.0;
     float mx = 0.f;
+    // rows, centre halves and the row pitch 16-byte aligned: a lane takes 4
+    // consecutive coordinates per load (same summation depth per row)
+    const bool vec = ((d & 3) == 0) && ((ldx & 3) == 0) && (((uintptr_t)x & 15) == 0) &&
+                     (((uintptr_t)chi & 15) == 0) && (((uintptr_t)clo & 15) == 0);
     // four rows in flight per warp (independent loads and reductions)
     for (int64_t i0 = warp; i0 < n; i0 += 4 * nw) {
         float D[4];
@@ -608,9 +612,20 @@ __global__ void __launch_bounds__(256) k_assign_stats(const float *__restrict__ 
                 const float *xr = x + i * ldx;
                 const float *h = chi + (int64_t)j * d;
                 const float *l = clo + (int64_t)j * d;
-                for (int t = lane; t < d; t += 32) {
-                    const float e = (xr[t] - h[t]) - l[t];
-                    D[q] = fmaf(e, e, D[q]);
+                if (vec) {
+                    for (int t = 4 * lane; t < d; t += 128) {
+                        const float4 xv = *reinterpret_cast<const float4 *>(xr + t);
+                        const float4 hv = *reinterpret_cast<const float4 *>(h + t);
+                        const float4 lv = *reinterpret_cast<const float4 *>(l + t);
+                        const float e0 = (xv.x - hv.x) - lv.x, e1 = (xv.y - hv.y) - lv.y;
+                        const float e2 = (xv.z - hv.z) - lv.z, e3 = (xv.w - hv.w) - lv.w;
+                        D[q] = fmaf(e3, e3, fmaf(e2, e2, fmaf(e1, e1, fmaf(e0, e0, D[q]))));
+                    }
+                } else {
+                    for (int t = lane; t < d; t += 32) {
+                        const float e = (xr[t] - h[t]) - l[t];
+                        D[q] = fmaf(e, e, D[q]);
+                    }
                 }
             }
         }

@@ -93,6 +93,78 @@ __global__ void k_set_sig(int64_t nsets, const int64_t *__restrict__ soff,
     }
 }
 
+// The same signatures for sets of many members: a thread takes one set for
+// all S tables (its first SS_REG member ids stay in registers, the per-set
+// lookups are paid once), where k_set_sig spends a thread per (set, table).
+// With a few members per set the thread per (set, table) keeps more loads in
+// flight and is the faster form; with hundreds this one is.
+constexpr int SS_REG = 8;
+constexpr int64_t SS_WIDE = 32;  // members per set (mean) from which k_set_sig_sets is used
+__global__ void k_set_sig_sets(int64_t nsets, int S, const int64_t *__restrict__ soff,
+                          const uint32_t *__restrict__ sids, int Ks, const uint64_t *__restrict__ A,
+                          const uint64_t *__restrict__ B, const int64_t *__restrict__ row_off, int count,
+                          const uint32_t *__restrict__ set_inst, int64_t coef_stride, uint64_t *__restrict__ klo,
+                          uint64_t *__restrict__ khi, uint32_t *__restrict__ vals, uint32_t *__restrict__ tag,
+                          uint32_t *__restrict__ seen1 = nullptr, uint32_t *__restrict__ seen2 = nullptr,
+                          uint64_t seen_mask = 0) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nsets;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s0 = soff[g], s1 = soff[g + 1];
+        int inst = 0;
+        uint32_t base = 0;
+        if (count > 1 && s1 > s0) {
+            inst = set_inst ? (int)set_inst[g] : find_inst(row_off, count, (int64_t)sids[s0]);
+            base = (uint32_t)row_off[inst];
+        }
+        const uint64_t *Ai = A + (count > 1 ? (int64_t)inst * coef_stride : 0);
+        const uint64_t *Bi = B + (count > 1 ? (int64_t)inst * coef_stride : 0);
+        const int64_t len = s1 - s0;
+        uint32_t mc[SS_REG];
+#pragma unroll
+        for (int i = 0; i < SS_REG; i++) mc[i] = i < len ? sids[s0 + i] - base : 0u;
+        for (int t = 0; t < S; t++) {
+            uint64_t a[4], b[4];
+            uint32_t m[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                if (k < Ks) {
+                    a[k] = __ldg(Ai + t * Ks + k);
+                    b[k] = __ldg(Bi + t * Ks + k);
+                }
+#pragma unroll
+            for (int i = 0; i < SS_REG; i++)
+                if (i < len) {
+#pragma unroll
+                    for (int k = 0; k < 4; k++)
+                        if (k < Ks) m[k] = min(m[k], mh_hash32(a[k], b[k], mc[i]));
+                }
+            for (int64_t p = s0 + SS_REG; p < s1; p++) {
+                const uint32_t id = sids[p] - base;
+#pragma unroll
+                for (int k = 0; k < 4; k++)
+                    if (k < Ks) m[k] = min(m[k], mh_hash32(a[k], b[k], id));
+            }
+            uint64_t hi = 0, lo = 0;
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                if (k < Ks) {
+                    hi = (hi << 32) | (lo >> 32);
+                    lo = (lo << 32) | m[k];
+                }
+            const int64_t so = (int64_t)t * nsets;
+            klo[so + g] = lo;
+            if (khi) khi[so + g] = hi;
+            if (vals) vals[so + g] = (uint32_t)g;
+            if (tag) tag[so + g] = (uint32_t)inst;
+            if (seen1) {
+                const uint64_t pos = seen_pos(sig_hash(lo, hi, (uint32_t)inst), t, seen_mask);
+                const uint32_t bit = 1u << (pos & 31);
+                if (atomicOr(&seen1[pos >> 5], bit) & bit) atomicOr(&seen2[pos >> 5], bit);
+            }
+        }
+    }
+}
+
 // first signature component (the most significant 32 bits of the packed
 // key), with the instance tag (if any) above it
 __global__ void k_first_component(int64_t n, const uint64_t *__restrict__ klo, const uint64_t *__restrict__ khi,
@@ -687,7 +759,7 @@ geek_status d2h_i64(geek_ctx *ctx, const int64_t *dev, int64_t *host, cudaStream
 // all S*nsets positions: perm (set index), rank (global bin id), rs (global
 // bin starts, nbins + 1) and nbins; bins of table t precede those of t + 1.
 geek_status make_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const int64_t *soff,
-                      const uint32_t *sids, int Ks, const uint64_t *A, const uint64_t *B, const SilkBatch *bt,
+                      const uint32_t *sids, int64_t nids, int Ks, const uint64_t *A, const uint64_t *B, const SilkBatch *bt,
                       int64_t coef_stride, uint32_t **perm, int32_t **rank, int64_t **rs, int64_t *nbins,
                       cudaStream_t st) {
     const int64_t tot = (int64_t)S * nsets;
@@ -706,8 +778,12 @@ geek_status make_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const i
     GK_TRY(scr.alloc(perm, tot));
     const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nsets, 256), (int64_t)ctx->num_sms * 8));
     GK_COUNT();
-    k_set_sig<<<dim3(gx, S), 256, 0, st>>>(nsets, soff, sids, Ks, A, B, tagged ? bt->row_off : nullptr,
+    if (nids >= SS_WIDE * nsets)
+        k_set_sig_sets<<<gx, 256, 0, st>>>(nsets, S, soff, sids, Ks, A, B, tagged ? bt->row_off : nullptr,
                                            tagged ? bt->count : 1, nullptr, coef_stride, klo, khi, *perm, tag);
+    else
+        k_set_sig<<<dim3(gx, S), 256, 0, st>>>(nsets, soff, sids, Ks, A, B, tagged ? bt->row_off : nullptr,
+                                               tagged ? bt->count : 1, nullptr, coef_stride, klo, khi, *perm, tag);
     GK_COUNT();
     k_first_component<<<G(ctx, tot), 256, 0, st>>>(tot, klo, khi, tag, Ks, k0);
     GK_LAUNCH(ctx);
@@ -764,6 +840,7 @@ geek_status make_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const i
 // bin starts, nbins; positions grouped by bin, bins in arbitrary order -- the
 // seeds do not depend on bin order) and the single-bin buckets (singles).
 geek_status group_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const int64_t *soff, const uint32_t *sids,
+                       int64_t nids,
                        const int32_t *vw, int delta, int Ks, const uint64_t *A, const uint64_t *B, const SilkBatch *bt,
                        int64_t coef_stride, uint32_t **perm, int32_t **rank, int64_t **rs, int64_t *npos,
                        int64_t *nbins, int64_t **singles, int64_t *n_singles, cudaStream_t st) {
@@ -806,9 +883,15 @@ geek_status group_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const 
     GK_CUDA(ctx, cudaMemsetAsync(seen, 0, sizeof(uint32_t) * (size_t)(M / 32) * 2, st));
     uint32_t *seen1 = seen, *seen2 = seen + M / 32;
     GK_COUNT();
-    k_set_sig<<<dim3(gx, S), 256, 0, st>>>(nsets, soff, sids, Ks, A, B, tagged ? bt->row_off : nullptr,
+    if (nids >= SS_WIDE * nsets)
+        k_set_sig_sets<<<gx, 256, 0, st>>>(nsets, S, soff, sids, Ks, A, B, tagged ? bt->row_off : nullptr,
                                            tagged ? bt->count : 1, tagged ? bt->set_inst : nullptr, coef_stride,
                                            klo, khi, nullptr, tag, seen1, seen2, (uint64_t)(Mt - 1));
+    else
+        k_set_sig<<<dim3(gx, S), 256, 0, st>>>(nsets, soff, sids, Ks, A, B, tagged ? bt->row_off : nullptr,
+                                               tagged ? bt->count : 1, tagged ? bt->set_inst : nullptr,
+                                               coef_stride, klo, khi, nullptr, tag, seen1, seen2,
+                                               (uint64_t)(Mt - 1));
     GK_COUNT();
     k_group_insert<<<dim3(gx, S), 256, 0, st>>>(nsets, C, klo, khi, tag, roff, rcap, slot, mkey, mval, counts, seen2,
                                                 (uint64_t)(Mt - 1), vw, soff, delta, *singles, counts + 1);
@@ -1154,7 +1237,7 @@ geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p,
         int64_t *rs, nbins = 0, *singles, nh = 0, npos = 0;
         {
             EvTimer tb(ctx, "silk.bins", st);
-            GK_TRY(group_bins(ctx, tscr, S, NV, voff, vmem, vw, delta, Ks, p->mh_a + (int64_t)t * Ks,
+            GK_TRY(group_bins(ctx, tscr, S, NV, voff, vmem, VT, vw, delta, Ks, p->mh_a + (int64_t)t * Ks,
                               p->mh_b + (int64_t)t * Ks, bt, (int64_t)Ls * Ks, &perm, &rank, &rs, &npos, &nbins,
                               &singles, &nh, st));
         }
@@ -1200,7 +1283,7 @@ geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p,
         uint32_t *perm;
         int32_t *rank;
         int64_t *rs, nbins = 0;
-        GK_TRY(make_bins(ctx, scr, 1, C.n, C.off, C.ids, Ks, p->dd_a, p->dd_b, bt, Ks, &perm, &rank, &rs, &nbins,
+        GK_TRY(make_bins(ctx, scr, 1, C.n, C.off, C.ids, C.nids, Ks, p->dd_a, p->dd_b, bt, Ks, &perm, &rank, &rs, &nbins,
                          st));
         Csr V;
         int64_t *ok;
