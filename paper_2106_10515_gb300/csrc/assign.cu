@@ -11,6 +11,7 @@
 #include <type_traits>
 
 #include "internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace {
 
@@ -852,15 +853,27 @@ __global__ void k_size_order(int64_t k, const unsigned long long *__restrict__ c
 // 64-bit add is the only loop-carried step) and the failures collected in a
 // bit mask.
 //
-// Member rows reach shared memory through a per-warp ring of UC_S stages of
-// 32 rows (16-byte cp.async per lane, 4 rows per instruction; the ids of a
-// stage are loaded four stages before its copies are issued).  The first wave of items goes to
-// warps warp-in-block major, so the slices of one centre start on different
-// SMs; later items come from an atomic counter, largest centre first
-// (order: centre indices by descending member count).
-constexpr int UC_W = 4, UC_T = 32 * UC_W, UC_B = 32, UC_S = 8;
-constexpr int UC_STAGE = UC_B * 32;                              // floats per stage
-constexpr int UC_SMEM = UC_W * UC_S * UC_STAGE * (int)sizeof(float);  // 128 KB
+// Each work item is served by a pair of warps: a producer (fetches the item,
+// loads the member ids four stages ahead, copies 32 member rows per stage
+// into the pair's ring of UC_S stages with 16-byte cp.async, 4 rows per
+// instruction) and a consumer (the chain above, a stage at a time), so the
+// consumer's single instruction stream carries only the sums.  Stage hand-off
+// by mbarriers: "full" completes when the producer's 32 lanes' copies have
+// landed (cp.async.mbarrier.arrive.noinc) and its header is written, "empty"
+// when the consumer is done with the stage; every wait is bounded (on expiry
+// the kernel records GEEK_ERR_TIMEOUT and both warps stop).  The first wave of
+// items goes to pairs pair-in-block major, so the slices of one centre start
+// on different SMs; later items come from an atomic counter, largest centre
+// first (order: centre indices by descending member count).
+constexpr int UC_P = 4, UC_T = 64 * UC_P, UC_B = 32, UC_S = 8;
+constexpr int UC_STAGE = UC_B * 32;                                    // floats per stage
+constexpr int UC_SMEM = UC_P * UC_S * UC_STAGE * (int)sizeof(float);   // 128 KB of rings
+
+// a stage's header: which item and which 32 members
+struct UcHdr {
+    int64_t j, cj;  // centre, its member count (cj < 0: no more items)
+    int32_t t0, g;  // first coordinate of the slice, member group
+};
 
 // x / 2^g as a signed integer, x = +-mx 2^u with base = 150 + g and u >= g:
 // exact for u - g <= 38 (then |x / 2^g| < 2^62); bad beyond that or when x
@@ -878,7 +891,10 @@ __device__ __forceinline__ int64_t units_of(float x, int base, bool &bad) {
 // s <- RN(...RN(RN(s + v[0]) + v[1]) ... + v[ma - 1]) in FP64, ma <= 32 (a
 // lane with act = false, past the last coordinate, takes no FP64 step and
 // so holds up no other lane)
+// FULL: ma == UC_B, every step unpredicated and the one-check sum a tree.
+template <bool FULL>
 __device__ __forceinline__ double chain_chunk(double s, const float (&v)[UC_B], int ma, bool act) {
+    if (FULL) ma = UC_B;
     constexpr uint64_t M52 = (1ull << 52) - 1;
     const uint64_t bits = (uint64_t)__double_as_longlong(s);
     const int E = (int)((bits >> 52) & 0x7FF);
@@ -887,14 +903,22 @@ __device__ __forceinline__ double chain_chunk(double s, const float (&v)[UC_B], 
     bool fast = zero || (E > 64 && E < 0x7FE - 64);
     const uint64_t M = (bits & M52) | (1ull << 52);
     // the unit 2^g: the finest ulp among the chunk's values and s's lowest set bit
-    int umin = 0x7FFFFFFF, emax = 0;
+    // (tree reductions: no 32-long dependency chain)
+    int ua[UC_B], ea[UC_B];
 #pragma unroll
-    for (int m = 0; m < UC_B; m++)
-        if (m < ma) {
-            const int e = (int)((__float_as_uint(v[m]) >> 23) & 0xFFu);
-            umin = min(umin, max(e, 1));
-            emax = max(emax, e);
+    for (int m = 0; m < UC_B; m++) {
+        const int e = (int)((__float_as_uint(v[m]) >> 23) & 0xFFu);
+        ua[m] = m < ma ? max(e, 1) : 0x7FFFFFFF;
+        ea[m] = m < ma ? e : 0;
+    }
+#pragma unroll
+    for (int w = 1; w < UC_B; w <<= 1)
+#pragma unroll
+        for (int m = 0; m < UC_B; m += 2 * w) {
+            ua[m] = min(ua[m], ua[m + w]);
+            ea[m] = max(ea[m], ea[m + w]);
         }
+    const int umin = ua[0], emax = ea[0];
     const int qs = E - 1075;
     const int g = zero ? umin - 150 : min(umin - 150, qs + __ffsll((long long)M) - 1);
     int64_t T0 = 0;
@@ -913,7 +937,19 @@ __device__ __forceinline__ double chain_chunk(double s, const float (&v)[UC_B], 
     const bool easy = fast && emax != 0xFF && lmax <= 23 && aT0 + (1ull << (29 + lmax)) < (1ull << 53);
     int64_t T = T0;
     int f = ma;  // first step that takes the FP64 add
-    if (easy) {
+    if (easy && FULL) {
+        int64_t r[UC_B];
+#pragma unroll
+        for (int m = 0; m < UC_B; m++) {
+            bool bad;
+            r[m] = units_of(v[m], base, bad);
+        }
+#pragma unroll
+        for (int w = 1; w < UC_B; w <<= 1)
+#pragma unroll
+            for (int m = 0; m < UC_B; m += 2 * w) r[m] += r[m + w];
+        T += r[0];
+    } else if (easy) {
         int64_t p1 = 0, p2 = 0, p3 = 0;
 #pragma unroll
         for (int m = 0; m < UC_B; m += 4) {
@@ -959,14 +995,11 @@ __device__ __forceinline__ double chain_chunk(double s, const float (&v)[UC_B], 
                 (long long)(((uint64_t)(T < 0) << 63) | ((uint64_t)(g + 1075 + p - 53) << 52) | mant));
         }
     }
-    int fw = f;  // warp-uniform bound of the FP64 tail
+    if (__all_sync(0xffffffffu, f >= ma)) return t;
+    const int fw = __reduce_min_sync(0xffffffffu, f);  // warp-uniform bound of the FP64 tail
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) fw = min(fw, __shfl_xor_sync(0xffffffffu, fw, o));
-    if (fw < ma) {
-#pragma unroll
-        for (int m = 0; m < UC_B; m++)
-            if (m >= fw && m < ma && m >= f) t = __dadd_rn(t, widen_f32(v[m]));
-    }
+    for (int m = 0; m < UC_B; m++)
+        if (m >= fw && m < ma && m >= f) t = __dadd_rn(t, widen_f32(v[m]));
     return t;
 }
 
@@ -977,46 +1010,72 @@ __device__ __forceinline__ void cp_async4(uint32_t dst, const void *src, int byt
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
 }
 
+__device__ __forceinline__ void cp_async_bar_arrive(uint64_t *bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(su32(bar)) : "memory");
+}
+
 __global__ void __launch_bounds__(UC_T) k_update_centres(const float *__restrict__ x, int64_t ldx, int d, int64_t k,
                                                          const int64_t *__restrict__ off,
                                                          const unsigned long long *__restrict__ cnt,
                                                          const int32_t *__restrict__ ids, const uint64_t *__restrict__ order,
-                                                         unsigned long long *__restrict__ next, double *__restrict__ c) {
-    extern __shared__ float uc_ring[];  // [UC_W][UC_S][32 rows][32 floats]
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    float *ring = uc_ring + (size_t)wib * UC_S * UC_STAGE;
-    const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring);
+                                                         unsigned long long *__restrict__ next, double *__restrict__ c,
+                                                         int *__restrict__ err) {
+    extern __shared__ float uc_ring[];  // [UC_P][UC_S][32 rows][32 floats]
+    __shared__ UcHdr hdr[UC_P][UC_S];
+    __shared__ uint64_t full[UC_P][UC_S], empty[UC_P][UC_S];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool producer = warp >= UC_P;
+    const int pr = producer ? warp - UC_P : warp;  // the pair
+    float *ring = uc_ring + (size_t)pr * UC_S * UC_STAGE;
+    if (threadIdx.x < UC_P * UC_S) {
+        mbar_init(&full[threadIdx.x / UC_S][threadIdx.x % UC_S], 33);  // 32 copy arrivals + the header
+        mbar_init(&empty[threadIdx.x / UC_S][threadIdx.x % UC_S], 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncthreads();
     const int nsl = (d + 31) >> 5;
     const int64_t nitems = k * nsl;
-    const bool vec = (((uintptr_t)x & 15) == 0) && ((ldx & 3) == 0);
-    const int64_t nw = (int64_t)gridDim.x * UC_W;
-    int64_t it = (int64_t)wib * gridDim.x + blockIdx.x;  // first wave: slices of a centre on different SMs
-    while (it < nitems) {
-        const int64_t j = (int64_t)(order[it / nsl] & 0xFFFFFFFFull);
-        const int t0 = (int)(it % nsl) * 32, t = t0 + lane;
-        const int width = min(32, d - t0);
-        const int64_t cj = (int64_t)cnt[j];
-        if (cj > 0) {  // warp-uniform
-            const int32_t *mid = ids + off[j];
-            const float *xs = x + t0;
+    if (producer) {
+        const uint32_t ring_s = su32(ring);
+        const bool vec = (((uintptr_t)x & 15) == 0) && ((ldx & 3) == 0);
+        const int64_t np = (int64_t)gridDim.x * UC_P;
+        int64_t it = (int64_t)pr * gridDim.x + blockIdx.x;  // first wave: slices of a centre on different SMs
+        uint32_t sn = 0;                                    // stages issued by this pair
+        bool ok = true;
+        for (;;) {
+            const bool done = it >= nitems;
+            int64_t j = 0, cj = 0;
+            int t0 = 0;
+            if (!done) {
+                j = (int64_t)(order[it / nsl] & 0xFFFFFFFFull);
+                t0 = (int)(it % nsl) * 32;
+                cj = (int64_t)cnt[j];
+            }
+            const int width = min(32, d - t0);
             const int col = (lane & 7) * 4;  // this lane's 16 bytes of a row slice (vector copies)
             const int nbytes = max(0, min(16, (width - col) * 4));
-            const int64_t ng = (cj + UC_B - 1) / UC_B;
-            // ids of the next four groups to issue (loaded four stages ahead)
+            const int32_t *mid = ids + (done ? 0 : off[j]);
+            const float *xs = x + t0;
+            const int64_t ng = done ? 1 : (cj + UC_B - 1) / UC_B;  // the end marker takes one stage
             auto ld_id = [&](int64_t g) -> int32_t {
                 const int64_t q = g * UC_B + lane;
-                return q < cj ? mid[q] : 0;
+                return (!done && q < cj) ? mid[q] : 0;
             };
             int32_t id0 = ld_id(0), id1 = ld_id(1), id2 = ld_id(2), id3 = ld_id(3);
-            auto issue = [&](int64_t g) {
-                if (g < ng) {
-                    const int32_t my = id0;
-                    id0 = id1;
-                    id1 = id2;
-                    id2 = id3;
-                    id3 = ld_id(g + 4);
+            for (int64_t g = 0; g < ng && ok; g++, sn++) {
+                const int st = (int)(sn % UC_S);
+                const uint32_t use = sn / UC_S;
+                if (lane == 0) ok = mbar_wait(&empty[pr][st], (use & 1) ^ 1, err);
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) break;
+                const int32_t my = id0;
+                id0 = id1;
+                id1 = id2;
+                id2 = id3;
+                id3 = ld_id(g + 4);
+                if (!done) {
                     const int rows = (int)min((int64_t)UC_B, cj - g * UC_B);
-                    const uint32_t sb = ring_s + (uint32_t)((g & (UC_S - 1)) * UC_STAGE * sizeof(float));
+                    const uint32_t sb = ring_s + (uint32_t)(st * UC_STAGE * sizeof(float));
                     if (vec) {
 #pragma unroll
                         for (int i = 0; i < UC_B / 4; i++) {
@@ -1036,29 +1095,44 @@ __global__ void __launch_bounds__(UC_T) k_update_centres(const float *__restrict
                         }
                     }
                 }
-                asm volatile("cp.async.commit_group;" ::: "memory");  // empty groups keep the count uniform
-            };
-#pragma unroll 1
-            for (int g = 0; g < UC_S - 1; g++) issue(g);
-            double s = 0.0;
-            for (int64_t g = 0; g < ng; g++) {
-                issue(g + UC_S - 1);
-                asm volatile("cp.async.wait_group %0;" ::"n"(UC_S - 1) : "memory");
-                __syncwarp();  // the stage's rows, copied by all lanes, are visible to all
-                const float *src = ring + (g & (UC_S - 1)) * UC_STAGE + lane;
-                float v[UC_B];
-#pragma unroll
-                for (int m = 0; m < UC_B; m++) v[m] = src[m * 32];
-                s = chain_chunk(s, v, (int)min((int64_t)UC_B, cj - g * UC_B), lane < width);
-                __syncwarp();  // reads done before the stage is refilled
+                cp_async_bar_arrive(&full[pr][st]);  // when this lane's copies have landed
+                if (lane == 0) {
+                    hdr[pr][st] = UcHdr{j, done ? -1 : cj, t0, (int32_t)g};
+                    mbar_arrive(&full[pr][st]);
+                }
             }
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
-            __syncwarp();
-            if (lane < width) c[j * d + t] = __ddiv_rn(s, (double)cj);
+            if (done || !ok) break;
+            unsigned long long got = 0;
+            if (lane == 0) got = atomicAdd(next, 1ull);
+            it = np + (int64_t)__shfl_sync(0xffffffffu, got, 0);
         }
-        unsigned long long got = 0;
-        if (lane == 0) got = atomicAdd(next, 1ull);
-        it = nw + (int64_t)__shfl_sync(0xffffffffu, got, 0);
+        asm volatile("cp.async.wait_all;" ::: "memory");  // own copies landed before the block ends
+    } else {
+        double s = 0.0;
+        for (uint32_t sn = 0;; sn++) {
+            const int st = (int)(sn % UC_S);
+            const uint32_t use = sn / UC_S;
+            // lane 0 waits; __syncwarp then orders the other lanes' reads after
+            // its acquire of the phase (the copies were the producer's)
+            int okw = 0;
+            if (lane == 0) okw = mbar_wait(&full[pr][st], use & 1, err);
+            okw = __shfl_sync(0xffffffffu, okw, 0);
+            __syncwarp();
+            if (!okw) break;
+            const UcHdr h = hdr[pr][st];
+            if (h.cj < 0) break;
+            const int width = min(32, d - h.t0);
+            if (h.g == 0) s = 0.0;
+            const float *src = ring + st * UC_STAGE + lane;
+            float v[UC_B];
+#pragma unroll
+            for (int m = 0; m < UC_B; m++) v[m] = src[m * 32];
+            const int ma = (int)min((int64_t)UC_B, h.cj - (int64_t)h.g * UC_B);
+            s = ma == UC_B ? chain_chunk<true>(s, v, ma, lane < width) : chain_chunk<false>(s, v, ma, lane < width);
+            __syncwarp();  // every lane's reads done before the stage is refilled
+            if (lane == 0) mbar_arrive(&empty[pr][st]);
+            if ((int64_t)(h.g + 1) * UC_B >= h.cj && lane < width) c[h.j * d + h.t0 + lane] = __ddiv_rn(s, (double)h.cj);
+        }
     }
 }
 
@@ -1093,8 +1167,11 @@ geek_status refine_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ld
         GK_TRY(radix_sort_segments(ctx, ps, 1, k, &order, nullptr, nullptr, 64, st));
         tg.stop();
         unsigned long long *next;
+        int *uc_err;
         GK_TRY(ps.alloc(&next, 1));
+        GK_TRY(ps.alloc(&uc_err, 1));
         GK_CUDA(ctx, cudaMemsetAsync(next, 0, sizeof(unsigned long long), st));
+        GK_CUDA(ctx, cudaMemsetAsync(uc_err, 0, sizeof(int), st));
         static bool uc_attr = false;
         if (!uc_attr) {
             GK_CUDA(ctx, cudaFuncSetAttribute(k_update_centres, cudaFuncAttributeMaxDynamicSharedMemorySize, UC_SMEM));
@@ -1102,14 +1179,17 @@ geek_status refine_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ld
         }
         EvTimer tu(ctx, "kernel.update_centres", st);
         GK_COUNT();
-        k_update_centres<<<(unsigned)std::min<int64_t>((k * ((d + 31) / 32) + UC_W - 1) / UC_W, (int64_t)ctx->num_sms),
-                           UC_T, UC_SMEM, st>>>(x, ldx, d, k, off, cnt, (const int32_t *)ids, order, next, centres);
+        k_update_centres<<<(unsigned)std::min<int64_t>((k * ((d + 31) / 32) + UC_P - 1) / UC_P, (int64_t)ctx->num_sms),
+                           UC_T, UC_SMEM, st>>>(x, ldx, d, k, off, cnt, (const int32_t *)ids, order, next, centres,
+                                                uc_err);
         GK_LAUNCH(ctx);
         tu.stop();
-        int h_bad = 0;
+        int h_bad = 0, h_uc = 0;
         GK_CUDA(ctx, cudaMemcpyAsync(&h_bad, bad, sizeof h_bad, cudaMemcpyDeviceToHost, st));
+        GK_CUDA(ctx, cudaMemcpyAsync(&h_uc, uc_err, sizeof h_uc, cudaMemcpyDeviceToHost, st));
         GK_TRY(sort_err_check(ctx, st));  // synchronises st
         if (h_bad) return set_error(ctx, GEEK_ERR_INVALID, "a label outside [-1, k)");
+        if (h_uc) return set_error(ctx, (geek_status)h_uc, "centre update: a pipeline wait timed out");
         EvTimer ta(ctx, "refine.assign", st);
         GK_TRY(assign_dense_centres(ctx, ps, x, ldx, n, d, centres, k, precision, labels, stats, st));
     }
