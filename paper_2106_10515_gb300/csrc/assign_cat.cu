@@ -336,30 +336,51 @@ __global__ void __launch_bounds__(256) k_assign_jaccard(
 }
 
 // Exact Jaccard argmax, tiled over the centres.  A block takes JX_S sets
-// (one warp each) and walks the centres in tiles of JX_KT; per tile, every
+// (one warp each) and walks the centres in tiles of KT; per tile, every
 // item of a set reads the part of its posting list (centres containing the
 // item, ascending) that falls in the tile, found from precomputed per-tile
-// offsets, and adds one to the set's counter of each centre there (two
-// 16-bit counters per shared-memory word).  The counters are
+// offsets, and adds one to the set's counter of each centre there (packed
+// 8- or 16-bit counters in shared memory: a counter counts the set's light
+// items in one centre, at most the variant's MAXI).  The counters are
 // then |A n C_j| for every centre of the tile: J_j = I / (|A| + |C_j| - I) is
 // compared exactly (64-bit cross products), larger fraction then smaller
-// index; with no positive J the label is 0.  Sets with more than JX_MAXI
+// index; with no positive J the label is 0.  Sets with more than MAXI
 // items are listed for the dense path.
 constexpr int JX_S = 8;
-constexpr int JX_KT = 4096;
-constexpr int JX_MAXI = 512;
 constexpr int JX_THREADS = 32 * JX_S;
-constexpr size_t JX_SMEM = (size_t)JX_S * (JX_KT / 2) * 4 + (size_t)JX_S * JX_MAXI * (4 + 4 + 2);
+// NARROW: sets of at most 128 items, 8-bit counters, tiles of 8192 centres
+// (74 KB of shared memory: three blocks per SM); otherwise up to 512 items,
+// 16-bit counters, tiles of 4096 centres (104 KB).
+template <bool NARROW> struct Jx {
+    static constexpr int KT = NARROW ? 8192 : 4096;  // centres per tile
+    static constexpr int MAXI = NARROW ? 128 : 512;  // items per set on the tiled path
+    static constexpr int LG = NARROW ? 2 : 1;        // log2 counters per word
+    static constexpr int CBITS = 32 >> LG;
+    static constexpr uint32_t CMASK = NARROW ? 0xFFu : 0xFFFFu;
+    static constexpr int CW = KT >> LG;              // counter words per set
+    static constexpr size_t SMEM = (size_t)JX_S * CW * 4 + (size_t)JX_S * MAXI * (4 + 4 + 2);
+};
+
+// the largest set: max over i of off[i + 1] - off[i]
+__global__ void k_max_len(int64_t n, const int64_t *__restrict__ off, unsigned long long *__restrict__ out) {
+    unsigned long long m = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, (unsigned long long)(off[i + 1] - off[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
 
 // tile_off[r * (ntiles + 1) + t]: the first entry of posting list r whose
 // centre is in tile t or later (ntiles + 1 entries per list)
 __global__ void k_tile_offsets(int64_t nr, const int64_t *__restrict__ post_off,
-                               const uint32_t *__restrict__ post_centre, int ntiles, int32_t *__restrict__ tile_off) {
+                               const uint32_t *__restrict__ post_centre, int ntiles, int kt,
+                               int32_t *__restrict__ tile_off) {
     const int64_t tot = nr * (ntiles + 1);
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = e / (ntiles + 1);
         const int t = (int)(e % (ntiles + 1));
-        const uint64_t lim = (uint64_t)t * JX_KT;
+        const uint64_t lim = (uint64_t)t * kt;
         int64_t lo = post_off[r], hi = post_off[r + 1];
         while (lo < hi) {
             const int64_t mid = (lo + hi) >> 1;
@@ -370,24 +391,26 @@ __global__ void k_tile_offsets(int64_t nr, const int64_t *__restrict__ post_off,
     }
 }
 
+template <bool NARROW>
 __global__ void __launch_bounds__(JX_THREADS) k_jac_tiled(
     int64_t n, const int64_t *__restrict__ off, const uint32_t *__restrict__ items, int na_fix, int64_t k,
     const int32_t *__restrict__ clen, const uint64_t *__restrict__ cmask, const uint32_t *__restrict__ hv_item,
     const int16_t *__restrict__ hv_bit, int nheavy, int HW, const uint32_t *__restrict__ post_item,
     const int32_t *__restrict__ tile_off, int ntiles, int64_t n_post_items, const uint32_t *__restrict__ post_centre,
     int32_t *__restrict__ labels, int32_t *__restrict__ ovf_rows, unsigned long long *__restrict__ n_ovf) {
+    using C = Jx<NARROW>;
     __shared__ unsigned long long s_am[JX_S][JX_HW];  // the sets' heavy-item masks
     extern __shared__ uint32_t jx_smem[];
     uint32_t *cnt = jx_smem;                                          // [S][KT / 2]
-    int32_t *ridx = reinterpret_cast<int32_t *>(cnt + JX_S * (JX_KT / 2));  // [S][MAXI]: posting list of each item
-    int32_t *rps = ridx + JX_S * JX_MAXI;                                  // [S][MAXI]: its range in the tile
-    uint16_t *rlen = reinterpret_cast<uint16_t *>(rps + JX_S * JX_MAXI);   // [S][MAXI]
+    int32_t *ridx = reinterpret_cast<int32_t *>(cnt + JX_S * C::CW);        // [S][MAXI]: posting list of each item
+    int32_t *rps = ridx + JX_S * C::MAXI;                                  // [S][MAXI]: its range in the tile
+    uint16_t *rlen = reinterpret_cast<uint16_t *>(rps + JX_S * C::MAXI);   // [S][MAXI]
     __shared__ int s_ni[JX_S];
     __shared__ int64_t s_na[JX_S];
     __shared__ uint32_t r_n[JX_S][JX_S], r_d[JX_S][JX_S];
     __shared__ int r_j[JX_S][JX_S];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int e = threadIdx.x; e < JX_S * (JX_KT / 2); e += blockDim.x) cnt[e] = 0;
+    for (int e = threadIdx.x; e < JX_S * C::CW; e += blockDim.x) cnt[e] = 0;
     const int64_t ngroups = (n + JX_S - 1) / JX_S;
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
         // the warp's set: posting ranges of its items
@@ -395,8 +418,8 @@ __global__ void __launch_bounds__(JX_THREADS) k_jac_tiled(
         int ni = 0;
         if (i < n) {
             const int64_t s0 = off[i], e0 = off[i + 1];
-            ni = (int)min(e0 - s0, (int64_t)JX_MAXI + 1);
-            if (ni > JX_MAXI) {
+            ni = (int)min(e0 - s0, (int64_t)C::MAXI + 1);
+            if (ni > C::MAXI) {
                 if (lane == 0) ovf_rows[atomicAdd(n_ovf, 1ull)] = (int32_t)i;
                 ni = 0;
             }
@@ -407,7 +430,7 @@ __global__ void __launch_bounds__(JX_THREADS) k_jac_tiled(
                 const int hb = heavy_bit(it, hv_item, hv_bit, nheavy);
                 if (hb >= 0) {
                     atomicOr(&s_am[w][hb >> 6], 1ull << (hb & 63));
-                    ridx[w * JX_MAXI + p] = -1;
+                    ridx[w * C::MAXI + p] = -1;
                     continue;
                 }
                 int64_t lo = 0, hi = n_post_items;
@@ -417,7 +440,7 @@ __global__ void __launch_bounds__(JX_THREADS) k_jac_tiled(
                     else hi = mid;
                 }
                 const bool f = lo < n_post_items && post_item[lo] == it;
-                ridx[w * JX_MAXI + p] = f ? (int32_t)lo : -1;
+                ridx[w * C::MAXI + p] = f ? (int32_t)lo : -1;
             }
             if (lane == 0) {
                 s_ni[w] = ni;
@@ -441,43 +464,43 @@ __global__ void __launch_bounds__(JX_THREADS) k_jac_tiled(
 #pragma unroll
             for (int h = 0; h < JX_HW; h++) am[q][h] = s_am[q][h];
         }
-        for (int64_t c0 = 0; c0 < k; c0 += JX_KT) {
-            const int64_t c1 = min(k, c0 + JX_KT);
+        for (int64_t c0 = 0; c0 < k; c0 += C::KT) {
+            const int64_t c1 = min(k, c0 + C::KT);
             // counting: lanes walk consecutive entries of one posting list
             const int niw = s_ni[w];
-            uint32_t *cw = cnt + w * (JX_KT / 2);
-            const int t = (int)(c0 / JX_KT);
+            uint32_t *cw = cnt + w * C::CW;
+            const int t = (int)(c0 / C::KT);
             // the items' ranges in this tile, lane per item (independent loads)
             for (int q = lane; q < niw; q += 32) {
-                const int32_t r = ridx[w * JX_MAXI + q];
+                const int32_t r = ridx[w * C::MAXI + q];
                 int32_t ps = 0, pe = 0;
                 if (r >= 0) {
                     ps = tile_off[(int64_t)r * (ntiles + 1) + t];
                     pe = tile_off[(int64_t)r * (ntiles + 1) + t + 1];
                 }
-                rps[w * JX_MAXI + q] = ps;
-                rlen[w * JX_MAXI + q] = (uint16_t)(pe - ps);
+                rps[w * C::MAXI + q] = ps;
+                rlen[w * C::MAXI + q] = (uint16_t)(pe - ps);
             }
             __syncwarp();
             // short ranges: a lane walks one item's entries
             for (int q = lane; q < niw; q += 32) {
-                const int len = rlen[w * JX_MAXI + q];
+                const int len = rlen[w * C::MAXI + q];
                 if (len == 0 || len >= 32) continue;
-                const int32_t ps = rps[w * JX_MAXI + q];
+                const int32_t ps = rps[w * C::MAXI + q];
                 for (int e = 0; e < len; e++) {
                     const int cc = (int)((int64_t)post_centre[ps + e] - c0);
-                    atomicAdd(&cw[cc >> 1], 1u << ((cc & 1) << 4));
+                    atomicAdd(&cw[cc >> C::LG], 1u << ((cc & ((1 << C::LG) - 1)) * C::CBITS));
                 }
             }
             // long ranges: the warp walks one item's entries, lane per entry
             for (int q = 0; q < niw; q++) {
-                const int len = rlen[w * JX_MAXI + q];
+                const int len = rlen[w * C::MAXI + q];
                 if (len < 32) continue;
-                const int32_t ps = rps[w * JX_MAXI + q];
+                const int32_t ps = rps[w * C::MAXI + q];
 #pragma unroll 4
                 for (int p = lane; p < len; p += 32) {
                     const int cc = (int)((int64_t)post_centre[ps + p] - c0);
-                    atomicAdd(&cw[cc >> 1], 1u << ((cc & 1) << 4));
+                    atomicAdd(&cw[cc >> C::LG], 1u << ((cc & ((1 << C::LG) - 1)) * C::CBITS));
                 }
             }
             __syncwarp();
@@ -491,7 +514,7 @@ __global__ void __launch_bounds__(JX_THREADS) k_jac_tiled(
                 for (int h = 0; h < JX_HW; h++) cm[h] = h < HW ? cmask[c * HW + h] : 0ull;
 #pragma unroll
                 for (int q = 0; q < JX_S; q++) {
-                    uint32_t in = (cnt[q * (JX_KT / 2) + (cc >> 1)] >> ((cc & 1) << 4)) & 0xFFFFu;
+                    uint32_t in = (cnt[q * C::CW + (cc >> C::LG)] >> ((cc & ((1 << C::LG) - 1)) * C::CBITS)) & C::CMASK;
 #pragma unroll
                     for (int h = 0; h < JX_HW; h++) in += __popcll(am[q][h] & cm[h]);
                     if (in) {
@@ -507,7 +530,7 @@ __global__ void __launch_bounds__(JX_THREADS) k_jac_tiled(
                 }
             }
             __syncthreads();
-            for (int e = threadIdx.x; e < JX_S * (JX_KT / 2); e += blockDim.x) cnt[e] = 0;
+            for (int e = threadIdx.x; e < JX_S * C::CW; e += blockDim.x) cnt[e] = 0;
             __syncthreads();
         }
         // per set: reduce the threads' bests (warp, then across warps)
@@ -821,15 +844,26 @@ geek_status jaccard_core(geek_ctx *ctx, Scratch &scr, const int64_t *off, const 
     k_heavy_masks<<<G(ctx, k), 256, 0, st>>>(k, coff, citems, hv_item, hv_bit, nheavy, HW, cmask, clen);
     GK_LAUNCH(ctx);
     if (nci > 0x7FFFFFFFLL) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "more than 2^31 centre items");
-    // the tiled kernel compares fractions in 32 bits: |A| <= JX_MAXI (else the
-    // dense path) and every |C| below 2^15
+    // the tiled kernel compares fractions in 32 bits: |A| <= MAXI (else the
+    // dense path) and every |C| below 2^15; the narrow variant when no set has
+    // more than its MAXI items
     bool tiled_ok = na_fix < 32768;
+    unsigned long long h_amax = 0, *d_amax;
+    GK_TRY(scr.alloc(&d_amax, 1));
+    GK_CUDA(ctx, cudaMemsetAsync(d_amax, 0, sizeof(unsigned long long), st));
+    if (na_fix < 0 && n > 0) {
+        GK_COUNT();
+        k_max_len<<<G(ctx, n), 256, 0, st>>>(n, off, d_amax);
+        GK_LAUNCH(ctx);
+    }
     {
         std::vector<int64_t> hco(k + 1);
         GK_CUDA(ctx, cudaMemcpyAsync(hco.data(), coff, 8 * (k + 1), cudaMemcpyDeviceToHost, st));
+        GK_CUDA(ctx, cudaMemcpyAsync(&h_amax, d_amax, sizeof h_amax, cudaMemcpyDeviceToHost, st));
         GK_CUDA(ctx, cudaStreamSynchronize(st));
         for (int64_t j = 0; j < k && tiled_ok; j++) tiled_ok = hco[j + 1] - hco[j] < 32768;
     }
+    const bool narrow = (na_fix >= 0 ? (int64_t)na_fix : (int64_t)h_amax) <= Jx<true>::MAXI;
     int32_t *ovf;
     unsigned long long *n_ovf;
     GK_TRY(scr.alloc(&ovf, n));
@@ -838,14 +872,18 @@ geek_status jaccard_core(geek_ctx *ctx, Scratch &scr, const int64_t *off, const 
     {
         static bool attr = false;
         if (!attr) {
-            GK_CUDA(ctx, cudaFuncSetAttribute(k_jac_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)JX_SMEM));
+            GK_CUDA(ctx, cudaFuncSetAttribute(k_jac_tiled<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)Jx<true>::SMEM));
+            GK_CUDA(ctx, cudaFuncSetAttribute(k_jac_tiled<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)Jx<false>::SMEM));
             attr = true;
         }
-        const int ntiles = (int)ceil_div(k, JX_KT);
+        const int kt = narrow ? Jx<true>::KT : Jx<false>::KT;
+        const int ntiles = (int)ceil_div(k, kt);
         int32_t *toff;
         GK_TRY(scr.alloc(&toff, (size_t)std::max<int64_t>(h_nlight, 1) * (ntiles + 1)));
         GK_COUNT();
-        k_tile_offsets<<<G(ctx, h_nlight * (ntiles + 1)), 256, 0, st>>>(h_nlight, d_loff, d_lcentre, ntiles, toff);
+        k_tile_offsets<<<G(ctx, h_nlight * (ntiles + 1)), 256, 0, st>>>(h_nlight, d_loff, d_lcentre, ntiles, kt, toff);
         EvTimer tk(ctx, "kernel.jaccard", st);
         tk.work = (double)n * (double)k;  // (set, centre) pairs scored
         if (!tiled_ok) {  // very large central sets: every set takes the dense path
@@ -854,9 +892,16 @@ geek_status jaccard_core(geek_ctx *ctx, Scratch &scr, const int64_t *off, const 
             GK_LAUNCH(ctx);
         } else {
         GK_COUNT();
-        k_jac_tiled<<<(unsigned)std::min<int64_t>(ceil_div(n, JX_S), (int64_t)ctx->num_sms * 3), JX_THREADS, JX_SMEM,
-                      st>>>(n, off, items, na_fix, k, clen, cmask, hv_item, hv_bit, nheavy, HW, d_litem, toff, ntiles,
-                            h_nlight, d_lcentre, labels, ovf, n_ovf);
+        const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(n, JX_S), (int64_t)ctx->num_sms * 3);
+        if (narrow)
+            k_jac_tiled<true><<<grid, JX_THREADS, Jx<true>::SMEM, st>>>(n, off, items, na_fix, k, clen, cmask, hv_item,
+                                                                      hv_bit, nheavy, HW, d_litem, toff, ntiles,
+                                                                      h_nlight, d_lcentre, labels, ovf, n_ovf);
+        else
+            k_jac_tiled<false><<<grid, JX_THREADS, Jx<false>::SMEM, st>>>(n, off, items, na_fix, k, clen, cmask,
+                                                                        hv_item, hv_bit, nheavy, HW, d_litem, toff,
+                                                                        ntiles, h_nlight, d_lcentre, labels, ovf,
+                                                                        n_ovf);
         GK_LAUNCH(ctx);
         }
     }
