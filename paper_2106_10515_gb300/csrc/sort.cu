@@ -347,21 +347,39 @@ __global__ void __launch_bounds__(RS_THREADS)
 // the object's bucket id in its table is r, and a run start records the
 // run's global offset.  Writes obj_bucket[seg][ids[p]] = r and, at starts,
 // boff[base[seg] + r] = seg * m + p; boff[NB] = S * m closes the list.
+// The tile's keys and ids are first copied to shared memory with coalesced
+// loads (a thread then walks RS_ITEMS consecutive positions there); the key
+// before the tile comes along for the first run-start test.
 __global__ void __launch_bounds__(RS_THREADS)
     k_runs_buckets(const uint64_t *__restrict__ lo, const uint64_t *__restrict__ hi, int64_t m, int tiles,
                    const uint32_t *__restrict__ tile_off, const uint32_t *__restrict__ ids,
                    const int64_t *__restrict__ base, int32_t *__restrict__ obj_bucket,
                    int64_t *__restrict__ boff, int64_t NB) {
+    extern __shared__ uint64_t rb_sm[];  // lo [RS_TILE + 1], hi [RS_TILE + 1] (when hi), ids [RS_TILE]
     __shared__ uint32_t wsum[32];
     const int seg = blockIdx.y, tile = blockIdx.x;
     const int64_t so = (int64_t)seg * m;
     const uint64_t *l = lo + so;
     const uint64_t *h = hi ? hi + so : nullptr;
-    const int64_t p0 = (int64_t)tile * RS_TILE + (int64_t)threadIdx.x * RS_ITEMS;
+    uint64_t *sl = rb_sm, *sh = rb_sm + (RS_TILE + 1);
+    uint32_t *sid = reinterpret_cast<uint32_t *>(rb_sm + (h ? 2 : 1) * (RS_TILE + 1));
+    const int64_t t0 = (int64_t)tile * RS_TILE;
+    const int cnt = (int)min((int64_t)RS_TILE, m - t0);
+    for (int e = threadIdx.x; e < cnt; e += RS_THREADS) {
+        sl[e + 1] = l[t0 + e];
+        if (h) sh[e + 1] = h[t0 + e];
+        sid[e] = ids[so + t0 + e];
+    }
+    if (threadIdx.x == 0 && t0 > 0) {
+        sl[0] = l[t0 - 1];
+        if (h) sh[0] = h[t0 - 1];
+    }
+    __syncthreads();
+    const int e0 = threadIdx.x * RS_ITEMS;
     uint32_t flags = 0, c = 0;
     for (int i = 0; i < RS_ITEMS; i++) {
-        const int64_t p = p0 + i;
-        if (p < m && run_start_at(l, h, nullptr, p)) {
+        const int e = e0 + i;
+        if (e < cnt && (t0 + e == 0 || sl[e + 1] != sl[e] || (h && sh[e + 1] != sh[e]))) {
             flags |= 1u << i;
             c++;
         }
@@ -371,13 +389,13 @@ __global__ void __launch_bounds__(RS_THREADS)
     int64_t r = (int64_t)ex - 1;
     const int64_t bb = base[seg];
     for (int i = 0; i < RS_ITEMS; i++) {
-        const int64_t p = p0 + i;
-        if (p >= m) break;
+        const int e = e0 + i;
+        if (e >= cnt) break;
         if (flags >> i & 1u) {
             r++;
-            boff[bb + r] = so + p;
+            boff[bb + r] = so + t0 + e;
         }
-        obj_bucket[so + ids[so + p]] = (int32_t)r;
+        obj_bucket[so + sid[e]] = (int32_t)r;
     }
     if (seg == 0 && tile == 0 && threadIdx.x == 0) boff[NB] = (int64_t)gridDim.y * m;
 }
@@ -653,8 +671,15 @@ geek_status segment_buckets(geek_ctx *ctx, Scratch &scr, int S, int64_t m, const
         GK_TRY(scr.alloc(&d_base, S));
         GK_CUDA(ctx, cudaMemcpyAsync(d_base, base.data(), sizeof(int64_t) * S, cudaMemcpyHostToDevice, st));
         GK_COUNT();
-        k_runs_buckets<<<dim3(tiles, S), RS_THREADS, 0, st>>>(key_lo, key_hi, m, tiles, tile_cnt, ids, d_base,
-                                                             obj_bucket, boff, NB);
+        const size_t rb_smem = (size_t)(key_hi ? 2 : 1) * (RS_TILE + 1) * sizeof(uint64_t) + RS_TILE * sizeof(uint32_t);
+        static bool rb_attr = false;
+        if (!rb_attr) {
+            GK_CUDA(ctx, cudaFuncSetAttribute(k_runs_buckets, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)(2 * (RS_TILE + 1) * sizeof(uint64_t) + RS_TILE * sizeof(uint32_t))));
+            rb_attr = true;
+        }
+        k_runs_buckets<<<dim3(tiles, S), RS_THREADS, rb_smem, st>>>(key_lo, key_hi, m, tiles, tile_cnt, ids, d_base,
+                                                                   obj_bucket, boff, NB);
         GK_LAUNCH(ctx);
     }
     *boff_out = boff;
