@@ -404,10 +404,13 @@ __global__ void __launch_bounds__(RS_THREADS)
 __global__ void __launch_bounds__(RS_THREADS) k_i64_tile_sum(const int64_t *__restrict__ in,
                                                              int64_t n, int64_t *__restrict__ sums) {
     __shared__ int64_t red[RS_THREADS];
-    const int64_t p0 = (int64_t)blockIdx.x * RS_TILE + (int64_t)threadIdx.x * RS_ITEMS;
+    // the tile's sum in any order (integers): lane-contiguous, coalesced loads
+    const int64_t t0 = (int64_t)blockIdx.x * RS_TILE;
     int64_t s = 0;
-    for (int i = 0; i < RS_ITEMS; i++)
-        if (p0 + i < n) s += in[p0 + i];
+    for (int i = 0; i < RS_ITEMS; i++) {
+        const int64_t p = t0 + (int64_t)i * RS_THREADS + threadIdx.x;
+        if (p < n) s += in[p];
+    }
     red[threadIdx.x] = s;
     __syncthreads();
     for (int o = RS_THREADS / 2; o > 0; o >>= 1) {
@@ -444,11 +447,16 @@ __global__ void __launch_bounds__(RS_THREADS) k_i64_tile_apply(const int64_t *__
                                                                int64_t *__restrict__ out, int64_t n,
                                                                const int64_t *__restrict__ sums) {
     __shared__ int64_t red[RS_THREADS];
-    const int64_t p0 = (int64_t)blockIdx.x * RS_TILE + (int64_t)threadIdx.x * RS_ITEMS;
+    __shared__ int64_t tv[RS_TILE];  // the tile, loaded and stored coalesced
+    const int64_t t0 = (int64_t)blockIdx.x * RS_TILE;
+    const int cnt = (int)min((int64_t)RS_TILE, n - t0);
+    for (int e = threadIdx.x; e < RS_TILE; e += RS_THREADS) tv[e] = e < cnt ? in[t0 + e] : 0;
+    __syncthreads();
+    const int e0 = threadIdx.x * RS_ITEMS;
     int64_t v[RS_ITEMS];
     int64_t s = 0;
     for (int i = 0; i < RS_ITEMS; i++) {
-        v[i] = p0 + i < n ? in[p0 + i] : 0;
+        v[i] = tv[e0 + i];
         s += v[i];
     }
     red[threadIdx.x] = s;
@@ -462,9 +470,11 @@ __global__ void __launch_bounds__(RS_THREADS) k_i64_tile_apply(const int64_t *__
     }
     int64_t ex = red[threadIdx.x] - s + sums[blockIdx.x];
     for (int i = 0; i < RS_ITEMS; i++) {
-        if (p0 + i < n) out[p0 + i] = ex;
+        tv[e0 + i] = ex;
         ex += v[i];
     }
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt; e += RS_THREADS) out[t0 + e] = tv[e];
 }
 
 __global__ void k_iota_u32(uint32_t *v, int64_t n, int64_t period) {
