@@ -290,12 +290,15 @@ def test_alg1_ties_and_near_ties(G, ctx):
     check_alg1(bk.copy_out(), ref)
 
 
-def test_alg1_feeds_silk_and_assignment(G, ctx):
-    """Alg. 1 buckets through SILK seeding and the one-pass assignment."""
+@pytest.mark.parametrize("t", [400, 100])
+def test_alg1_feeds_silk_and_assignment(G, ctx, t):
+    """Alg. 1 buckets through SILK seeding and the one-pass assignment
+    (t = 100: buckets of 120 objects, so the SILK signatures take the
+    thread-per-set kernel; t = 400: 30 objects, the thread per (set, table))."""
     wl = synth.make(synth.config("c1", n=12000))
     x, a = wl["x"], wl["a"][:16]
-    bk = qalsh_buckets(G, ctx, x, a, 400)
-    _, ref_b = oracle.transform_alg1(x, a, 400)
+    bk = qalsh_buckets(G, ctx, x, a, t)
+    _, ref_b = oracle.transform_alg1(x, a, t)
     seeds = ctx.silk(bk, **G.silk_args(wl["silk"]))
     ref_s = oracle.silk_on(ref_b, wl["silk"])
     assert seeds.sets() == ref_s.sets()

@@ -60,6 +60,22 @@ def test_tc_projection_small_dense(G, ctx, n):
     check(bk, codes, ref)
 
 
+@pytest.mark.parametrize("w", [2.7, 0.5])
+def test_projection_bucket_widths(G, ctx, w):
+    """Bucket widths other than the configs' 4: w = 0.5 (a power of two, the
+    rechecks divide by an exact multiplication) and w = 2.7 (a true FP64
+    division), on both projection forms; many elements land near cell edges."""
+    wl = synth.make(synth.config("c1", n=9000))
+    cfg = wl["cfg"]
+    b = (wl["b"] / 4.0 * w).astype(np.float32)
+    codes, ref = oracle.hash_dense(wl["x"], wl["a"], b, w, cfg.K, cfg.L)
+    check(hash_tc(G, ctx, wl["x"], wl["a"], b, w, cfg.K, cfg.L), codes, ref)
+    bk32 = ctx.hash(ctx.dense(G._dev(wl["x"])), cfg.K, cfg.L, a=G._dev(wl["a"]), b=G._dev(b), w=w)
+    torch.cuda.synchronize()
+    check(bk32, codes, ref)
+    assert bk32.n_flagged > 0
+
+
 def test_tc_projection_c2_shape(G, ctx):
     """d = 128, 96 functions (K = 6, L = 16), 60,001 rows: several row
     tiles per CTA, a ragged last tile, and elements the window flags."""
