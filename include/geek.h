@@ -288,6 +288,18 @@ geek_status geek_assign(geek_ctx *ctx, const geek_data *data, const geek_buckets
                         const silk_seeds *s, const geek_assign_params *p, int32_t *labels,
                         double *centers, geek_assign_stats *stats, geek_stream stream);
 
+/* geek_cluster_radius: the radius of every cluster (Sect. 4.1 reports the
+ * radius of the clusters): radius[j] = sqrt(max over objects i with
+ * labels[i] == j of sum_t (x_it - c_jt)^2), 0 for a cluster with no object.
+ * DENSE device data only; centers k x d float64, labels n int32 (values
+ * outside [0, k) are skipped) and radius k float64 are device buffers.  The
+ * distances are those of geek_assign_stats (FP32 with the centres split into
+ * two FP32 parts, within 1e-6 relative of the FP64 value).  Stream-ordered,
+ * no host synchronisation.  Errors: INVALID (NULL arguments, data not DENSE
+ * or in host memory, k out of range), NOMEM, CUDA. */
+geek_status geek_cluster_radius(geek_ctx *ctx, const geek_data *data, const double *centers, int64_t k,
+                                const int32_t *labels, double *radius, geek_stream stream);
+
 /* geek_assign_ex: geek_assign, and the central vectors it used (Sect. 3.3) kept
  * in a library-owned handle *centres (sizes vary with the data):
  *  DENSE: centers k x d float64 (the FP64 centroids).

@@ -511,6 +511,23 @@ geek_status geek_assign_centers(geek_ctx *ctx, const geek_data *data, const doub
     }
 }
 
+geek_status geek_cluster_radius(geek_ctx *ctx, const geek_data *data, const double *centers, int64_t k,
+                                const int32_t *labels, double *radius, geek_stream stream) {
+    if (!ctx) return GEEK_ERR_INVALID;
+    try {
+        GK_TRY(check_data(ctx, data));
+        if (data->kind != GEEK_DENSE) return set_error(ctx, GEEK_ERR_INVALID, "dense data only");
+        if (!labels || !radius || (k > 0 && !centers) || k < 0 || k > 0x7FFFFFFFLL)
+            return set_error(ctx, GEEK_ERR_INVALID, "bad radius arguments");
+        if (data->mem == GEEK_MEM_HOST) return set_error(ctx, GEEK_ERR_INVALID, "device data only");
+        cudaStream_t st = S(stream);
+        Scratch scr(ctx, st);
+        return cluster_radius(ctx, scr, data->x, data->ldx, data->n, data->d, centers, k, labels, radius, st);
+    } catch (...) {
+        return set_error(ctx, GEEK_ERR_NOMEM, "host exception in geek_cluster_radius");
+    }
+}
+
 geek_status geek_refine(geek_ctx *ctx, const geek_data *data, double *centers, int64_t k, int32_t passes,
                         const geek_assign_params *p, int32_t *labels, geek_assign_stats *stats,
                         geek_stream stream) {

@@ -776,6 +776,39 @@ __global__ void __launch_bounds__(256) k_assign_stats_batch(const SInst *__restr
     }
 }
 
+// Per-cluster radius (Sect. 4.1): for every object its distance to its
+// centre as in k_assign_stats (warp per object, diff = (x - c_hi) - c_lo,
+// squares in FP32), and per label the largest one by an atomic maximum on the
+// bits of the non-negative float.
+__global__ void __launch_bounds__(256) k_cluster_rmax(const float *__restrict__ x, int64_t ldx, int64_t n, int d,
+                                                      const float *__restrict__ chi, const float *__restrict__ clo,
+                                                      int64_t k, const int32_t *__restrict__ labels,
+                                                      unsigned *__restrict__ rmax) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < n; i += nw) {
+        const int j = labels[i];
+        if (j < 0 || j >= k) continue;  // warp-uniform
+        const float *xr = x + i * ldx;
+        const float *h = chi + (int64_t)j * d;
+        const float *l = clo + (int64_t)j * d;
+        float D = 0.f;
+        for (int t = lane; t < d; t += 32) {
+            const float e = (xr[t] - h[t]) - l[t];
+            D = fmaf(e, e, D);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) D += __shfl_xor_sync(0xffffffffu, D, o);
+        if (lane == 0) atomicMax(&rmax[j], __float_as_uint(D));
+    }
+}
+
+__global__ void k_cluster_sqrt(int64_t k, const unsigned *__restrict__ rmax, double *__restrict__ radius) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += (int64_t)gridDim.x * blockDim.x)
+        radius[j] = sqrt((double)__uint_as_float(rmax[j]));
+}
+
 // per instance: its units' partials in unit order (deterministic)
 __global__ void k_stats_final_batch(const double *__restrict__ ps, const float *__restrict__ pm,
                                     const int64_t *__restrict__ unit_off, int count, double *__restrict__ sse,
@@ -1446,6 +1479,29 @@ geek_status decide_flags(geek_ctx *ctx, const RInst *R, const int64_t *row_off, 
     EvTimer t64(ctx, "kernel.assign_decide64", st);
     GK_COUNT();
     k_assign_decide64<<<ctx->num_sms * 2, 256, smem + DQ_BYTES, st>>>(U, B.mrow);
+    GK_LAUNCH(ctx);
+    return GEEK_OK;
+}
+
+// radius[j] = sqrt(max over objects labelled j of their distance to centre
+// j), 0 for a centre nobody is nearest to; labels outside [0, k) are skipped.
+geek_status cluster_radius(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ldx, int64_t n, int d,
+                           const double *centres, int64_t k, const int32_t *labels, double *radius, cudaStream_t st) {
+    if (k == 0) return GEEK_OK;
+    float *chi, *clo;
+    unsigned *rmax;
+    GK_TRY(scr.alloc(&chi, (size_t)k * d));
+    GK_TRY(scr.alloc(&clo, (size_t)k * d));
+    GK_TRY(scr.alloc(&rmax, k));
+    GK_CUDA(ctx, cudaMemsetAsync(rmax, 0, sizeof(unsigned) * k, st));
+    GK_COUNT();
+    k_centre_split<<<grid_for(k * d, 256, ctx->num_sms), 256, 0, st>>>(centres, k * d, chi, clo);
+    if (n > 0) {
+        GK_COUNT();
+        k_cluster_rmax<<<grid_for(n * 32, 256, ctx->num_sms), 256, 0, st>>>(x, ldx, n, d, chi, clo, k, labels, rmax);
+    }
+    GK_COUNT();
+    k_cluster_sqrt<<<grid_for(k, 256, ctx->num_sms), 256, 0, st>>>(k, rmax, radius);
     GK_LAUNCH(ctx);
     return GEEK_OK;
 }

@@ -307,6 +307,8 @@ geek_status decide_flags(geek_ctx *ctx, const RInst *R, const int64_t *row_off, 
 geek_status assign_dense_centres(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ldx,
                                  int64_t n, int d, const double *centres, int64_t k, int precision,
                                  int32_t *labels, geek_assign_stats *stats, cudaStream_t st);
+geek_status cluster_radius(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ldx, int64_t n, int d,
+                           const double *centres, int64_t k, const int32_t *labels, double *radius, cudaStream_t st);
 // Sect. 5's extra passes: per pass, centre j <- FP64 mean of the objects
 // labelled j (unchanged without members), then the exact reassignment.
 geek_status refine_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ldx, int64_t n, int d, double *centres,

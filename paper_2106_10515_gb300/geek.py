@@ -96,7 +96,7 @@ EXPORTS = ["geek_ctx_create", "geek_ctx_destroy", "geek_last_error", "geek_versi
            "geek_batch_info_get", "geek_batch_instance_stats", "geek_batch_copy_out", "geek_batch_seed_ids_count",
            "geek_batch_destroy", "geek_data_upload", "geek_resident_free", "geek_refine",
            "geek_ctx_set_option", "geek_assign_ex", "geek_centres_info_get", "geek_centres_copy_out",
-           "geek_centres_free"]
+           "geek_centres_free", "geek_cluster_radius"]
 
 _lib = None
 
@@ -128,6 +128,7 @@ def lib():
     L.geek_assign_centers.argtypes = [P, C.POINTER(geek_data), P, C.c_int64,
                                       C.POINTER(geek_assign_params), P, C.POINTER(geek_assign_stats), P]
     L.geek_ctx_set_option.argtypes = [P, C.c_int32, C.c_int64]
+    L.geek_cluster_radius.argtypes = [P, C.POINTER(geek_data), P, C.c_int64, P, P, P]
     L.geek_assign_ex.argtypes = [P, C.POINTER(geek_data), P, P, C.POINTER(geek_assign_params), P,
                                  C.POINTER(geek_assign_stats), C.POINTER(P), P]
     L.geek_centres_info_get.argtypes = [P, C.POINTER(geek_centres_info)]
@@ -433,6 +434,12 @@ class Context:
         self._chk(lib().geek_assign_centers(self.h, C.byref(data.c), _ptr(centers), k, C.byref(p), _ptr(labels),
                                             C.byref(s) if stats else None, _stream()))
         return s
+
+    def cluster_radius(self, data, centers, labels, radius):
+        """radius[j] = largest distance of an object labelled j to centre j
+        (device buffers; radius: k float64)."""
+        self._chk(lib().geek_cluster_radius(self.h, C.byref(data.c), _ptr(centers), centers.shape[0], _ptr(labels),
+                                            _ptr(radius), _stream()))
 
 
 def silk_args(sp):

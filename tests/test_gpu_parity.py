@@ -340,6 +340,30 @@ def test_assign_all_centres_in_the_window(G, ctx):
         assert np.array_equal(labels.cpu().numpy(), lab_ref)
 
 
+def test_cluster_radius(G, ctx):
+    """Per-cluster radius (Sect. 4.1): sqrt of the largest FP64 distance of a
+    member to its centre, within 1e-6 relative of the oracle's; 0 for a
+    cluster with no member; a label of -1 is skipped."""
+    wl = synth.make(synth.config("c1", n=20_000))
+    x = wl["x"]
+    c = np.concatenate([wl["centres"].astype(np.float64), np.full((1, x.shape[1]), 1e5)])  # an empty cluster
+    lab, dist = oracle.assign_dense(x, c)
+    lab = lab.astype(np.int32)
+    lab[::97] = -1
+    k = c.shape[0]
+    ref = np.zeros(k)
+    for j in range(k):
+        m = lab == j
+        if m.any():
+            ref[j] = np.sqrt(dist[m].max())
+    radius = torch.full((k,), -1.0, dtype=torch.float64, device="cuda")
+    ctx.cluster_radius(ctx.dense(G._dev(x)), G._dev(c), G._dev(lab), radius)
+    torch.cuda.synchronize()
+    got = radius.cpu().numpy()
+    assert got[-1] == 0.0
+    assert np.all(np.abs(got - ref) <= RTOL_SSE * ref)
+
+
 # ------------------------------------- extra passes of assignment (Sect. 5) --
 @pytest.mark.parametrize("prec", ["bf16", "fp32"])
 def test_refine_passes_exact(G, ctx, prec):
