@@ -340,6 +340,48 @@ def test_assign_all_centres_in_the_window(G, ctx):
         assert np.array_equal(labels.cpu().numpy(), lab_ref)
 
 
+def _w_bf16x3(xn, cmax, d):
+    """The split-BF16 assignment's half-window (the kernel's rigorous bound,
+    per-product accumulation model), evaluated in float64."""
+    ub = 2.0 ** -8
+    xc, c2 = xn * cmax, cmax * cmax
+    e = (6 * ub * ub * (1 + ub) * xc + 2.0 ** -24 * c2
+         + (3 * d + 19) * 2.0 ** -21 * (2 * xc * (1 + 4 * ub) + c2 * (1 + 2 * ub)))
+    s = xn + cmax
+    return 1.01 * (e + (d + 3) * 2.0 ** -53 * s * s)
+
+
+def test_assign_just_outside_the_window(G, ctx):
+    """Rows placed 1.05-1.6 windows from a tie between the two centres of a
+    pair, with |x| |c| ~ 6e5 against distance gaps of a few hundred (heavy
+    cancellation in |c|^2 - 2 x.c): the split-BF16 tensor-core pass settles
+    most of them alone, so an accumulation error beyond the modelled bound
+    would show as a wrong label."""
+    rng = np.random.default_rng(31)
+    n, d, P, off = 20000, 64, 50, 100.0
+    B = rng.standard_normal((P, d)) * 30 + off
+    u = rng.standard_normal((P, d))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    c = np.empty((2 * P, d))
+    c[0::2], c[1::2] = B + u, B - u
+    cmax = np.sqrt((c.astype(np.float32).astype(np.float64) ** 2).sum(1).max()) * (1 + 1e-5)
+    p = rng.integers(0, P, n)
+    x = B[p] + rng.standard_normal((n, d))
+    g = rng.uniform(1.05, 1.6, n)
+    for _ in range(4):  # the window grows with |x|: place, then re-place
+        W = 2 * _w_bf16x3(np.sqrt((x ** 2).sum(1)) * (1 + 1e-3), cmax, d) * (1 + 1e-6)
+        gap = ((x - c[2 * p + 1]) ** 2).sum(1) - ((x - c[2 * p]) ** 2).sum(1)
+        x += ((g * W - gap) / 4.0)[:, None] * u[p]  # |c1 - c2| = 2: the gap moves 4 per unit along u
+    x = x.astype(np.float32)
+    lab_ref, _ = oracle.assign_dense(x, c)
+    assert np.array_equal(lab_ref, 2 * p)
+    labels = torch.empty(n, dtype=torch.int32, device="cuda")
+    st = ctx.assign_centers(ctx.dense(G._dev(x)), G._dev(c), labels, precision=G.PREC_BF16X3)
+    torch.cuda.synchronize()
+    assert np.array_equal(labels.cpu().numpy(), lab_ref)
+    assert st.n_recheck_rows < n // 2
+
+
 def test_cluster_radius(G, ctx):
     """Per-cluster radius (Sect. 4.1): sqrt of the largest FP64 distance of a
     member to its centre, within 1e-6 relative of the oracle's; 0 for a
