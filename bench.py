@@ -75,23 +75,32 @@ def max_over_ranks(x, world):
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling (every 50 ms, started before the warm-up so that
+    sampling is running when the timed region begins); only the samples whose
+    timestamps fall inside the timed region are kept."""
 
-    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, dev):
         self.dev, self.proc, self.lines = dev, None, []
+        self.t_start = self.t_end = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.dev), "-lms", "200"], stdout=subprocess.PIPE,
+                                          "-i", str(self.dev), "-lms", "50"], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
             threading.Thread(target=self._read, daemon=True).start()
         except OSError:
             self.proc = None
+
+    def mark_start(self):
+        self.t_start = time.time()
+
+    def mark_end(self):
+        self.t_end = time.time()
 
     def _read(self):
         for ln in self.proc.stdout:
@@ -104,18 +113,27 @@ class Clocks:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+        import datetime
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
-            if len(f) < 7:
+            if len(f) < 8:
                 continue
             try:
-                sm.append(float(f[0]))
-                mx.append(float(f[1]))
+                s_mhz, m_mhz = float(f[1]), float(f[2])
             except ValueError:
                 continue
-            for nm, v in zip(names, f[3:7]):
+            try:
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = None  # an unexpected timestamp format: keep the sample
+            if (ts is not None and self.t_start is not None and self.t_end is not None
+                    and not (self.t_start <= ts <= self.t_end)):
+                continue
+            sm.append(s_mhz)
+            mx.append(m_mhz)
+            for nm, v in zip(names, f[4:8]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         if not sm:
@@ -213,6 +231,8 @@ def run_ours(args):
         del bk, seeds
 
     def timed(p, steps, warmup, clocks=None):
+        if clocks:
+            clocks.start()
         for _ in range(warmup):
             step(p)
         torch.cuda.synchronize()
@@ -221,15 +241,17 @@ def run_ours(args):
         ctx.timing_reset()
         ctx.timing(True)
         l0 = geek.launch_count()
-        if clocks:
-            clocks.start()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
+        if clocks:
+            clocks.mark_start()
         e0.record()
         for _ in range(steps):
             step(p)
         e1.record()
         torch.cuda.synchronize()
+        if clocks:
+            clocks.mark_end()
         cl = clocks.stop() if clocks else None
         ms = e0.elapsed_time(e1) / steps
         ctx.timing(False)

@@ -226,6 +226,7 @@ geek_status geek_timing_enable(geek_ctx *ctx, int on) {
 
 geek_status geek_timing_reset(geek_ctx *ctx) {
     if (!ctx) return GEEK_ERR_INVALID;
+    ctx->resolve_timers();
     ctx->times.clear();
     return GEEK_OK;
 }
@@ -233,6 +234,7 @@ geek_status geek_timing_reset(geek_ctx *ctx) {
 geek_status geek_timing_get(const geek_ctx *ctx, const char *name, double *total_ms, int64_t *count,
                             double *total_work) {
     if (!ctx || !name) return GEEK_ERR_INVALID;
+    ctx->resolve_timers();
     auto it = ctx->times.find(name);
     const bool f = it != ctx->times.end();
     if (total_ms) *total_ms = f ? it->second.ms : 0.0;

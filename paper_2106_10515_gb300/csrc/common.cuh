@@ -25,7 +25,30 @@ struct geek_ctx {
         long long count = 0;
         double work = 0.0;  // algorithmic bytes or flops of the bracketed work
     };
-    std::map<std::string, Timed> times;
+    mutable std::map<std::string, Timed> times;
+    // brackets whose end event has been recorded but not yet read: resolved
+    // (waited for and added to times) when the timings are read or reset, so
+    // a bracket adds no host synchronisation to the work it measures
+    struct Pending {
+        const char *name;
+        cudaEvent_t a, b;
+        double work;
+    };
+    mutable std::vector<Pending> pending;
+    void resolve_timers() const {
+        for (const Pending &q : pending) {
+            float ms = 0.f;
+            if (cudaEventSynchronize(q.b) == cudaSuccess && cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) {
+                auto &e = times[q.name];
+                e.ms += ms;
+                e.count += 1;
+                e.work += q.work;
+            }
+            cudaEventDestroy(q.a);
+            cudaEventDestroy(q.b);
+        }
+        pending.clear();
+    }
     // (centre-tile width | split-BF16 << 16) chosen by the batch autotuner per
     // (precision setting, padded d, seed-count class)
     std::map<int, int> tile_cache;
@@ -39,13 +62,17 @@ struct geek_ctx {
     int stall_tile = -1;
     long long fail_alloc_after = -1;
     ~geek_ctx() {
+        for (const Pending &q : pending) {
+            cudaEventDestroy(q.a);
+            cudaEventDestroy(q.b);
+        }
         if (sort_err) cudaFree(sort_err);
     }
 };
 
 // Brackets work on a stream with CUDA events when ctx->timing is on; the
-// elapsed time is added to ctx->times[name] when the bracket ends (which
-// waits for the end event).
+// event pair is queued on the context when the bracket ends and its elapsed
+// time added to ctx->times[name] when the timings are read (no wait here).
 struct EvTimer {
     geek_ctx *ctx;
     const char *name;
@@ -60,16 +87,7 @@ struct EvTimer {
     void stop() {
         if (!b) return;
         cudaEventRecord(b, st);
-        cudaEventSynchronize(b);
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, a, b) == cudaSuccess) {
-            auto &e = ctx->times[name];
-            e.ms += ms;
-            e.count += 1;
-            e.work += work;
-        }
-        cudaEventDestroy(a);
-        cudaEventDestroy(b);
+        ctx->pending.push_back(geek_ctx::Pending{name, a, b, work});
         a = b = nullptr;
     }
     ~EvTimer() { stop(); }
