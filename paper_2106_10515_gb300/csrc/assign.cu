@@ -1224,7 +1224,9 @@ geek_status refine_dense(geek_ctx *ctx, Scratch &scr, const float *x, int64_t ld
         if (h_bad) return set_error(ctx, GEEK_ERR_INVALID, "a label outside [-1, k)");
         if (h_uc) return set_error(ctx, (geek_status)h_uc, "centre update: a pipeline wait timed out");
         EvTimer ta(ctx, "refine.assign", st);
-        GK_TRY(assign_dense_centres(ctx, ps, x, ldx, n, d, centres, k, precision, labels, stats, st));
+        // the statistics describe the last pass only
+        GK_TRY(assign_dense_centres(ctx, ps, x, ldx, n, d, centres, k, precision, labels,
+                                    pass + 1 == passes ? stats : nullptr, st));
     }
     return GEEK_OK;
 }
