@@ -153,7 +153,8 @@ def workload(args):
     return wl, time.time() - t0
 
 
-TRAFFIC_PROFILES = {"kernel.assign_tc": "k_assign_tc_dense_n1M_d128_k20000.md"}
+TRAFFIC_PROFILES = {"kernel.assign_tc": "k_assign_tc_dense_n1M_d128_k20000.md",
+                    "kernel.project_tc": "k_project_tc_dense_n1M_d128_F96.md"}
 
 
 def traffic_for(kernel):
