@@ -581,9 +581,21 @@ __global__ void k_centre_split(const double *__restrict__ c64, int64_t kd, float
     }
 }
 
+// running sum sh + sl of non-negative FP32 values with each addition's
+// rounding error kept (TwoSum): relative error about 2^-23 for any count,
+// in FP32 operations only
+__device__ __forceinline__ void csum_add(float &sh, float &sl, float v) {
+    const float t = __fadd_rn(sh, v);
+    const float bb = __fsub_rn(t, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(v, bb));
+    sh = t;
+    sl = __fadd_rn(sl, err);
+}
+
 // per-object distance to its centre, warp per object, lanes over
-// coordinates: diff = (x - c_hi) - c_lo, squares accumulated in FP32; block
-// partial sums (FP64) and maxima, reduced on one block in a fixed order
+// coordinates: diff = (x - c_hi) - c_lo, squares accumulated in FP32; the
+// warp's distances in a compensated FP32 sum, block partial sums (FP64) and
+// maxima, reduced on one block in a fixed order
 __global__ void __launch_bounds__(256) k_assign_stats(const float *__restrict__ x, int64_t ldx, int64_t n, int d,
                                                       const float *__restrict__ chi, const float *__restrict__ clo,
                                                       int64_t k, const int32_t *__restrict__ labels,
@@ -593,7 +605,7 @@ __global__ void __launch_bounds__(256) k_assign_stats(const float *__restrict__ 
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    double s = 0.0;
+    float sh = 0.f, sl = 0.f;  // compensated FP32 sum of the warp's distances
     float mx = 0.f;
     // rows, centre halves and the row pitch 16-byte aligned: a lane takes 4
     // consecutive coordinates per load (same summation depth per row)
@@ -638,12 +650,12 @@ __global__ void __launch_bounds__(256) k_assign_stats(const float *__restrict__ 
 #pragma unroll
         for (int q = 0; q < 4; q++)
             if (ok[q]) {
-                s += (double)D[q];
+                csum_add(sh, sl, D[q]);
                 mx = fmaxf(mx, D[q]);
             }
     }
     if (lane == 0) {
-        ss[wib] = s;
+        ss[wib] = (double)sh + (double)sl;
         sm_[wib] = mx;
     }
     __syncthreads();
@@ -723,7 +735,7 @@ __global__ void __launch_bounds__(256) k_assign_stats_batch(const SInst *__restr
     for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
         const int2 un = units[u];
         const SInst &I = S[un.x];
-        double s = 0.0;
+        float sh = 0.f, sl = 0.f;  // compensated FP32 sum of the warp's distances
         float mx = 0.f;
         // rows wib, wib + 8, ... of the unit, four in flight per warp
         for (int r0 = wib; r0 < 128; r0 += 32) {
@@ -753,13 +765,13 @@ __global__ void __launch_bounds__(256) k_assign_stats_batch(const SInst *__restr
 #pragma unroll
             for (int q = 0; q < 4; q++)
                 if (ok[q]) {
-                    s += (double)D[q];
+                    csum_add(sh, sl, D[q]);
                     mx = fmaxf(mx, D[q]);
                 }
         }
         __syncthreads();
         if (lane == 0) {
-            ss[wib] = s;
+            ss[wib] = (double)sh + (double)sl;
             sm_[wib] = mx;
         }
         __syncthreads();
