@@ -45,8 +45,9 @@ __global__ void k_set_sig(int64_t nsets, const int64_t *__restrict__ soff,
                           const uint32_t *__restrict__ set_inst, int64_t coef_stride, uint64_t *__restrict__ klo,
                           uint64_t *__restrict__ khi, uint32_t *__restrict__ vals, uint32_t *__restrict__ tag,
                           uint32_t *__restrict__ seen1 = nullptr, uint32_t *__restrict__ seen2 = nullptr,
-                          uint64_t seen_mask = 0) {
-    // blockIdx.y = SILK table of this segment (functions t*Ks .. t*Ks+Ks-1)
+                          uint64_t seen_mask = 0, int64_t g0 = 0) {
+    // blockIdx.y = SILK table of this segment (functions t*Ks .. t*Ks+Ks-1);
+    // sets g0 .. nsets-1 (nsets is also the segment stride)
     const int t = blockIdx.y;
     const int64_t so = (int64_t)t * nsets;
     uint64_t a[4], b[4];
@@ -55,7 +56,7 @@ __global__ void k_set_sig(int64_t nsets, const int64_t *__restrict__ soff,
         b[k] = B[t * Ks + k];
     }
     int have = count > 1 ? -1 : 0;  // instance whose coefficients are in a / b
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nsets;
+    for (int64_t g = g0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nsets;
          g += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s0 = soff[g], s1 = soff[g + 1];
         int inst = 0;
@@ -106,8 +107,8 @@ __global__ void k_set_sig_sets(int64_t nsets, int S, const int64_t *__restrict__
                           const uint32_t *__restrict__ set_inst, int64_t coef_stride, uint64_t *__restrict__ klo,
                           uint64_t *__restrict__ khi, uint32_t *__restrict__ vals, uint32_t *__restrict__ tag,
                           uint32_t *__restrict__ seen1 = nullptr, uint32_t *__restrict__ seen2 = nullptr,
-                          uint64_t seen_mask = 0) {
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nsets;
+                          uint64_t seen_mask = 0, int64_t g0 = 0) {
+    for (int64_t g = g0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nsets;
          g += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s0 = soff[g], s1 = soff[g + 1];
         int inst = 0;
@@ -621,7 +622,9 @@ __global__ void k_group_insert(int64_t NV, int64_t C, const uint64_t *__restrict
                                uint64_t *__restrict__ slot, uint64_t *__restrict__ mkey, uint32_t *__restrict__ mval,
                                unsigned long long *__restrict__ n_multi, const uint32_t *__restrict__ seen2,
                                uint64_t seen_mask, const int32_t *__restrict__ vw, const int64_t *__restrict__ voff,
-                               int delta, int64_t *__restrict__ singles, unsigned long long *__restrict__ n_single) {
+                               int delta, int64_t *__restrict__ singles, unsigned long long *__restrict__ n_single,
+                               int64_t g0) {
+    // sets g0 .. NV-1 of segment t = blockIdx.y (NV is the segment stride)
     const int t = blockIdx.y;
     const int64_t so = (int64_t)t * NV;
     uint64_t *sl = slot + (int64_t)t * C;
@@ -629,7 +632,7 @@ __global__ void k_group_insert(int64_t NV, int64_t C, const uint64_t *__restrict
     __shared__ unsigned s_wc[AP_THREADS / 32];
     __shared__ unsigned long long s_base;
     // the whole block iterates together (the append is a block collective)
-    for (int64_t gb = (int64_t)blockIdx.x * blockDim.x; gb < NV; gb += stride) {
+    for (int64_t gb = g0 + (int64_t)blockIdx.x * blockDim.x; gb < NV; gb += stride) {
         const int64_t g = gb + threadIdx.x;
         bool joined = false, first = false, single = false;
         uint32_t rep = 0;
@@ -690,6 +693,123 @@ __global__ void k_group_insert(int64_t NV, int64_t C, const uint64_t *__restrict
         if (delta <= 1 && __syncthreads_or(single)) {  // (block-uniform)
             const unsigned long long qs = block_append(single, n_single, s_wc, &s_base);
             if (single) singles[qs] = g;
+        }
+    }
+}
+
+// One-object virtual buckets {i} (sets 0 .. NS1-1) of a chunk in which every
+// table has, in every instance, a MinHash function injective on the
+// instance's ids (k_mh_injective): two of them never share a signature, so
+// such a set shares its bin only with sets of two or more objects, which
+// marked the seen-once map beforehand (k_set_sig on sets NS1 .. NV-1).  With
+// its seen-once bit clear the set is alone in its bin (no atomic, no
+// signature written); otherwise it marks the seen-twice map (so that the
+// larger sets at that position probe), writes its signature and claims a
+// slot of its own: every earlier claimant is another one-object set, which
+// cannot share its signature, so it joins none.
+__global__ void k_single_insert(int64_t NS1, int64_t NV, const int64_t *__restrict__ soff,
+                                const uint32_t *__restrict__ sids, int Ks, const uint64_t *__restrict__ A,
+                                const uint64_t *__restrict__ B, const int64_t *__restrict__ row_off, int count,
+                                const uint32_t *__restrict__ set_inst, int64_t coef_stride,
+                                uint64_t *__restrict__ klo, uint64_t *__restrict__ khi, uint32_t *__restrict__ tag,
+                                const uint32_t *__restrict__ seen1, uint32_t *__restrict__ seen2, uint64_t seen_mask,
+                                const int64_t *__restrict__ roff, const int64_t *__restrict__ rcap, int64_t C,
+                                uint64_t *__restrict__ slot, const int32_t *__restrict__ vw, int delta,
+                                int64_t *__restrict__ singles, unsigned long long *__restrict__ n_single) {
+    const int t = blockIdx.y;
+    const int64_t so = (int64_t)t * NV;
+    uint64_t *sl = slot + (int64_t)t * C;
+    uint64_t a[4] = {0, 0, 0, 0}, b[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+        if (k < Ks) {
+            a[k] = A[t * Ks + k];
+            b[k] = B[t * Ks + k];
+        }
+    int have = count > 1 ? -1 : 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    __shared__ unsigned s_wc[AP_THREADS / 32];
+    __shared__ unsigned long long s_base;
+    for (int64_t gb = (int64_t)blockIdx.x * blockDim.x; gb < NS1; gb += stride) {
+        const int64_t g = gb + threadIdx.x;
+        bool single = false;
+        if (g < NS1) {
+            const int64_t s0 = soff[g];
+            int inst = 0;
+            uint32_t base = 0;
+            if (count > 1) {
+                inst = (int)set_inst[g];
+                base = (uint32_t)row_off[inst];
+                if (inst != have) {
+#pragma unroll
+                    for (int k = 0; k < 4; k++)
+                        if (k < Ks) {
+                            a[k] = A[inst * coef_stride + t * Ks + k];
+                            b[k] = B[inst * coef_stride + t * Ks + k];
+                        }
+                    have = inst;
+                }
+            }
+            const uint32_t id = sids[s0] - base;
+            uint64_t hi = 0, lo = 0;
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                if (k < Ks) {
+                    hi = (hi << 32) | (lo >> 32);
+                    lo = (lo << 32) | mh_hash32(a[k], b[k], id);
+                }
+            const uint32_t tg = tag ? (uint32_t)inst : 0u;
+            const uint64_t hf = sig_hash(lo, hi, tg);
+            const uint64_t pos = seen_pos(hf, t, seen_mask);
+            const uint32_t bit = 1u << (pos & 31);
+            if (seen1[pos >> 5] & bit) {
+                atomicOr(&seen2[pos >> 5], bit);
+                klo[so + g] = lo;
+                if (khi) khi[so + g] = hi;
+                if (tag) tag[so + g] = tg;
+                const int64_t rb = tag ? roff[tg] : 0;
+                const uint64_t mask = (uint64_t)(tag ? rcap[tg] : C) - 1;
+                const uint64_t mine = ((uint64_t)(uint32_t)(hf >> 32) << 32) | (uint64_t)g;
+                uint64_t h = hf & mask;
+                for (uint64_t probe = 0; probe <= mask; probe++) {
+                    unsigned long long *ps = (unsigned long long *)&sl[rb + h];
+                    if (*ps == SLOT_EMPTY &&
+                        atomicCAS(ps, (unsigned long long)SLOT_EMPTY, (unsigned long long)mine) == SLOT_EMPTY)
+                        break;
+                    h = (h + 1) & mask;
+                }
+            } else {
+                single = delta <= 1 && vw[g] >= 2 && soff[g + 1] - s0 >= delta;
+            }
+        }
+        if (delta <= 1 && __syncthreads_or(single)) {  // (block-uniform)
+            const unsigned long long qs = block_append(single, n_single, s_wc, &s_base);
+            if (single) singles[qs] = g;
+        }
+    }
+}
+
+// MinHash function h(x) = floor(((A x + B) mod 2^64) / 2^32) (Eq. 2's
+// permutation) can take one value at ids x and x + q only if the two 64-bit
+// values share their high word, which needs A q mod 2^64 within 2^32 of a
+// multiple of 2^64.  So h is injective on ids [0, n) when no q in [1, n) has
+// that property; a thread takes one q (global row r, q = r - the first row of
+// its instance) and tests every function (t, k) of the instance, setting
+// bit k of fb[instance * Ls + t] when one may repeat a value.
+__global__ void k_mh_injective(int64_t N, const int64_t *__restrict__ row_off, int count,
+                               const uint64_t *__restrict__ A, int64_t coef_stride, int Ls, int Ks,
+                               uint32_t *__restrict__ fb) {
+    const int nf = Ls * Ks;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < N; r += (int64_t)gridDim.x * blockDim.x) {
+        const int inst = count > 1 ? find_inst(row_off, count, r) : 0;
+        const uint64_t q = (uint64_t)(r - (count > 1 ? row_off[inst] : 0));
+        if (q == 0) continue;
+        const uint64_t *Ai = A + (int64_t)inst * coef_stride;
+        for (int f = 0; f < nf; f++) {
+            const uint64_t p = Ai[f] * q;
+            const uint32_t ph = (uint32_t)(p >> 32);
+            if (ph == 0u || (ph == 0xFFFFFFFFu && (uint32_t)p != 0u))
+                atomicOr(&fb[inst * Ls + f / Ks], 1u << (f % Ks));
         }
     }
 }
@@ -839,8 +959,10 @@ geek_status make_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const i
 // vote's bins (perm: virtual bucket per position, rank: bin per position, rs:
 // bin starts, nbins; positions grouped by bin, bins in arbitrary order -- the
 // seeds do not depend on bin order) and the single-bin buckets (singles).
+// ns1 > 0: sets 0 .. ns1-1 hold one object each and no two of them can share
+// a signature in these tables (k_single_insert); ns1 = 0: no such guarantee.
 geek_status group_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const int64_t *soff, const uint32_t *sids,
-                       int64_t nids,
+                       int64_t nids, int64_t ns1,
                        const int32_t *vw, int delta, int Ks, const uint64_t *A, const uint64_t *B, const SilkBatch *bt,
                        int64_t coef_stride, uint32_t **perm, int32_t **rank, int64_t **rs, int64_t *npos,
                        int64_t *nbins, int64_t **singles, int64_t *n_singles, cudaStream_t st) {
@@ -872,7 +994,6 @@ geek_status group_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const 
     GK_TRY(scr.alloc(singles, tot));
     GK_TRY(scr.alloc(&counts, 2));
     GK_CUDA(ctx, cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), st));
-    const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nsets, 256), (int64_t)ctx->num_sms * 8));
     // seen-once / seen-twice maps: per table about four bits per set, at
     // most 2^28 bits (two parts of at most 32 MB)
     int64_t Mt = 1 << 10;
@@ -882,19 +1003,36 @@ geek_status group_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const 
     GK_TRY(scr.alloc(&seen, (size_t)(M / 32) * 2));
     GK_CUDA(ctx, cudaMemsetAsync(seen, 0, sizeof(uint32_t) * (size_t)(M / 32) * 2, st));
     uint32_t *seen1 = seen, *seen2 = seen + M / 32;
-    GK_COUNT();
-    if (nids >= SS_WIDE * nsets)
-        k_set_sig_sets<<<gx, 256, 0, st>>>(nsets, S, soff, sids, Ks, A, B, tagged ? bt->row_off : nullptr,
-                                           tagged ? bt->count : 1, tagged ? bt->set_inst : nullptr, coef_stride,
-                                           klo, khi, nullptr, tag, seen1, seen2, (uint64_t)(Mt - 1));
-    else
-        k_set_sig<<<dim3(gx, S), 256, 0, st>>>(nsets, soff, sids, Ks, A, B, tagged ? bt->row_off : nullptr,
-                                               tagged ? bt->count : 1, tagged ? bt->set_inst : nullptr,
-                                               coef_stride, klo, khi, nullptr, tag, seen1, seen2,
-                                               (uint64_t)(Mt - 1));
-    GK_COUNT();
-    k_group_insert<<<dim3(gx, S), 256, 0, st>>>(nsets, C, klo, khi, tag, roff, rcap, slot, mkey, mval, counts, seen2,
-                                                (uint64_t)(Mt - 1), vw, soff, delta, *singles, counts + 1);
+    // sets g0 .. nsets-1 go through the seen maps and the grouping tables;
+    // one-object sets 0 .. ns1-1 (if any) only read the seen-once map
+    const int64_t g0 = ns1, nm = nsets - g0;
+    const int gm = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nm, 256), (int64_t)ctx->num_sms * 8));
+    if (nm > 0) {
+        GK_COUNT();
+        if (nids - g0 >= SS_WIDE * nm)
+            k_set_sig_sets<<<gm, 256, 0, st>>>(nsets, S, soff, sids, Ks, A, B, tagged ? bt->row_off : nullptr,
+                                               tagged ? bt->count : 1, tagged ? bt->set_inst : nullptr, coef_stride,
+                                               klo, khi, nullptr, tag, seen1, seen2, (uint64_t)(Mt - 1), g0);
+        else
+            k_set_sig<<<dim3(gm, S), 256, 0, st>>>(nsets, soff, sids, Ks, A, B, tagged ? bt->row_off : nullptr,
+                                                   tagged ? bt->count : 1, tagged ? bt->set_inst : nullptr,
+                                                   coef_stride, klo, khi, nullptr, tag, seen1, seen2,
+                                                   (uint64_t)(Mt - 1), g0);
+    }
+    if (g0 > 0) {
+        const int gs = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(g0, 256), (int64_t)ctx->num_sms * 8));
+        GK_COUNT();
+        k_single_insert<<<dim3(gs, S), 256, 0, st>>>(g0, nsets, soff, sids, Ks, A, B, tagged ? bt->row_off : nullptr,
+                                                     tagged ? bt->count : 1, tagged ? bt->set_inst : nullptr,
+                                                     coef_stride, klo, khi, tag, seen1, seen2, (uint64_t)(Mt - 1),
+                                                     roff, rcap, C, slot, vw, delta, *singles, counts + 1);
+    }
+    if (nm > 0) {
+        GK_COUNT();
+        k_group_insert<<<dim3(gm, S), 256, 0, st>>>(nsets, C, klo, khi, tag, roff, rcap, slot, mkey, mval, counts,
+                                                    seen2, (uint64_t)(Mt - 1), vw, soff, delta, *singles, counts + 1,
+                                                    g0);
+    }
     if (delta <= 1) {
         GK_COUNT();
         k_group_singles<<<G(ctx, S * C), 256, 0, st>>>(C, S, slot, vw, soff, delta, *singles, counts + 1);
@@ -1216,6 +1354,29 @@ geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p,
     GK_COUNT();
     k_vb_members<<<G(ctx, NV), 256, 0, st>>>(NV, NS1, vsrc, voff, b->boff, b->members, vmem);
     GK_LAUNCH(ctx);
+    // SILK tables in which no two one-object virtual buckets can share a
+    // signature: in every instance one of the table's Ks functions is
+    // injective on the instance's ids (k_mh_injective)
+    std::vector<char> tab_one(Ls, 0);
+    if (NS1 > 0) {
+        const int cnt = (bt && bt->count > 1) ? bt->count : 1;
+        uint32_t *fb;
+        GK_TRY(scr.alloc(&fb, (size_t)cnt * Ls));
+        GK_CUDA(ctx, cudaMemsetAsync(fb, 0, sizeof(uint32_t) * (size_t)cnt * Ls, st));
+        GK_COUNT();
+        k_mh_injective<<<G(ctx, n), 256, 0, st>>>(n, cnt > 1 ? bt->row_off : nullptr, cnt, p->mh_a,
+                                                  (int64_t)Ls * Ks, Ls, Ks, fb);
+        GK_LAUNCH(ctx);
+        std::vector<uint32_t> hfb((size_t)cnt * Ls);
+        GK_CUDA(ctx, cudaMemcpyAsync(hfb.data(), fb, sizeof(uint32_t) * hfb.size(), cudaMemcpyDeviceToHost, st));
+        GK_CUDA(ctx, cudaStreamSynchronize(st));
+        const uint32_t all = (1u << Ks) - 1u;
+        for (int t = 0; t < Ls; t++) {
+            bool ok = true;
+            for (int i = 0; i < cnt && ok; i++) ok = (hfb[(size_t)i * Ls + t] & all) != all;
+            tab_one[t] = ok;
+        }
+    }
 
     t_vb.stop();
     SilkBatch btl;  // batched: per-instance slot regions of the grouping tables
@@ -1235,9 +1396,11 @@ geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p,
         uint32_t *perm;
         int32_t *rank;
         int64_t *rs, nbins = 0, *singles, nh = 0, npos = 0;
+        bool one = true;
+        for (int u = t; u < t + S; u++) one = one && tab_one[u];
         {
             EvTimer tb(ctx, "silk.bins", st);
-            GK_TRY(group_bins(ctx, tscr, S, NV, voff, vmem, VT, vw, delta, Ks, p->mh_a + (int64_t)t * Ks,
+            GK_TRY(group_bins(ctx, tscr, S, NV, voff, vmem, VT, one ? NS1 : 0, vw, delta, Ks, p->mh_a + (int64_t)t * Ks,
                               p->mh_b + (int64_t)t * Ks, bt, (int64_t)Ls * Ks, &perm, &rank, &rs, &npos, &nbins,
                               &singles, &nh, st));
         }

@@ -174,6 +174,21 @@ def silk_params(cfg: Config, rng):
                 dd_a=dA, dd_b=dB)
 
 
+def silk_params_slow(sp: dict, mode: str, seed: int = ROOT_SEED + 61) -> dict:
+    """A copy of SILK parameters with some multipliers A replaced by values
+    in [2^31, 2^31 + 2^20): such a hash climbs by about one half per id, so
+    neighbouring ids share its values.  mode "all": every function of the
+    even-numbered tables; "first": the first function of every table."""
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence(seed)))
+    A = np.array(sp["mh_a"], dtype=np.uint64).copy()
+    Ks, Ls = sp["Ks"], sp["Ls"]
+    for t in range(Ls):
+        for k in range(Ks):
+            if (mode == "all" and t % 2 == 0) or (mode == "first" and k == 0):
+                A[t * Ks + k] = np.uint64((1 << 31) + int(rng.integers(0, 1 << 20)))
+    return dict(sp, mh_a=A)
+
+
 # The paper's own dense pipeline on the 10M x 128 points: Alg. 1 with m = 40
 # QALSH tables of t = 5,000 even buckets (both in the paper's grid), then
 # SILK with Ls = 20 (grid) and delta = 10 (default) but Ks = 2: on these

@@ -89,6 +89,27 @@ def test_batch_matches_oracle_per_instance(G, ctx):
     assert sum(g["k"] for g in got) > 0
 
 
+@pytest.mark.parametrize("mode", ["all", "first"])
+def test_batch_minhash_functions_that_repeat_values(G, ctx, mode):
+    """SILK hashes that repeat values on neighbouring ids (multipliers near
+    2^31): "all" gives one instance repeating functions in every even table
+    (one-object virtual buckets share signatures: the general grouping path
+    for the whole batch), "first" makes every instance's first function of
+    every table repeat (the one-object path stays on).  Seeds equal the
+    oracle's instance by instance."""
+    insts = small_batch()
+    for i, I in enumerate(insts):
+        if mode == "first" or i == 2:
+            I["silk"] = synth.silk_params_slow(I["silk"], mode, seed=synth.ROOT_SEED + 70 + i)
+    b, _ = make_batch(G, ctx, insts)
+    run_batch(b)
+    got = b.copy_out()
+    for i, I in enumerate(insts):
+        cfg = I["cfg"]
+        _, ref_b = oracle.hash_dense(I["x"], I["a"], I["b"], I["w"], cfg.K, cfg.L)
+        assert got[i]["seeds"] == oracle.silk_on(ref_b, I["silk"]).sets(), i
+
+
 def test_batch_tiles_replay_and_sequential_agree(G, ctx):
     insts = synth.batch_instances(count=14, n_range=(2000, 40000), comp_range=(10, 400), seed=synth.ROOT_SEED + 53)
     b, dev = make_batch(G, ctx, insts)

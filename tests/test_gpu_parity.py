@@ -67,6 +67,27 @@ def test_dense_c1_full_pipeline(G, ctx, over):
         assert abs(st.radius_max - np.sqrt(ref["dist"].max())) <= RTOL_SSE * np.sqrt(ref["dist"].max())
 
 
+@pytest.mark.parametrize("mode", ["all", "first"])
+@pytest.mark.parametrize("delta", [2, 1])
+def test_silk_minhash_functions_that_repeat_values(G, ctx, mode, delta):
+    """SILK hashes that repeat values on neighbouring ids (multipliers near
+    2^31).  "all": every function of the even tables repeats, so one-object
+    virtual buckets share signatures and take the general grouping path;
+    "first": one function per table stays injective on the ids (the
+    one-object path) while first components collide everywhere.  Seeds
+    equal the oracle's."""
+    wl = synth.make(synth.config("c1"))
+    cfg = wl["cfg"]
+    sp = dict(synth.silk_params_slow(wl["silk"], mode), delta=delta)
+    x, bk = run_dense(G, ctx, wl)
+    _, ref_b = oracle.hash_dense(wl["x"], wl["a"], wl["b"], wl["w"], cfg.K, cfg.L)
+    ref_s = oracle.silk_on(ref_b, sp)
+    assert ref_s.n_multiset > 0
+    seeds = ctx.silk(bk, **G.silk_args(sp))
+    assert seeds.n_multiset == ref_s.n_multiset
+    assert seeds.sets() == ref_s.sets()
+
+
 def test_dense_c2_shape_hash_and_assign(G, ctx):
     """The 10M x 128 workload's shape at n = 60,000 (several tiles, ragged
     tail): E2LSH K=6, L=16 codes and buckets, then assignment to the planted
