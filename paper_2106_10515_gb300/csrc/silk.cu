@@ -43,11 +43,8 @@ __global__ void k_set_sig(int64_t nsets, const int64_t *__restrict__ soff,
                           const uint32_t *__restrict__ sids, int Ks, const uint64_t *__restrict__ A,
                           const uint64_t *__restrict__ B, const int64_t *__restrict__ row_off, int count,
                           const uint32_t *__restrict__ set_inst, int64_t coef_stride, uint64_t *__restrict__ klo,
-                          uint64_t *__restrict__ khi, uint32_t *__restrict__ vals, uint32_t *__restrict__ tag,
-                          uint32_t *__restrict__ seen1 = nullptr, uint32_t *__restrict__ seen2 = nullptr,
-                          uint64_t seen_mask = 0, int64_t g0 = 0) {
-    // blockIdx.y = SILK table of this segment (functions t*Ks .. t*Ks+Ks-1);
-    // sets g0 .. nsets-1 (nsets is also the segment stride)
+                          uint64_t *__restrict__ khi, uint32_t *__restrict__ vals, uint32_t *__restrict__ tag) {
+    // blockIdx.y = SILK table of this segment (functions t*Ks .. t*Ks+Ks-1)
     const int t = blockIdx.y;
     const int64_t so = (int64_t)t * nsets;
     uint64_t a[4], b[4];
@@ -56,7 +53,7 @@ __global__ void k_set_sig(int64_t nsets, const int64_t *__restrict__ soff,
         b[k] = B[t * Ks + k];
     }
     int have = count > 1 ? -1 : 0;  // instance whose coefficients are in a / b
-    for (int64_t g = g0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nsets;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nsets;
          g += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s0 = soff[g], s1 = soff[g + 1];
         int inst = 0;
@@ -86,11 +83,109 @@ __global__ void k_set_sig(int64_t nsets, const int64_t *__restrict__ soff,
         if (khi) khi[so + g] = hi;
         if (vals) vals[so + g] = (uint32_t)g;
         if (tag) tag[so + g] = (uint32_t)inst;
-        if (seen1) {
-            const uint64_t pos = seen_pos(sig_hash(lo, hi, (uint32_t)inst), t, seen_mask);
-            const uint32_t bit = 1u << (pos & 31);
-            if (atomicOr(&seen1[pos >> 5], bit) & bit) atomicOr(&seen2[pos >> 5], bit);
+    }
+}
+
+// The signatures of sets g0 .. nsets-1 (as k_set_sig; set_inst required for
+// batched instances) for the grouping tables, with the seen-once /
+// seen-twice marks: a set marks its position (a hash of signature and
+// instance) in the seen-once map and, when the bit was already set, in the
+// seen-twice map.  A thread takes SM_U sets at a time, loads their bounds and
+// first two members together, and issues the seen-once atomics of all SM_U
+// sets before it waits for any of them.
+constexpr int SM_U = 4;
+__global__ void __launch_bounds__(256, 4)
+    k_set_sig_marks(int64_t nsets, const int64_t *__restrict__ soff, const uint32_t *__restrict__ sids, int Ks,
+                    const uint64_t *__restrict__ A, const uint64_t *__restrict__ B,
+                    const int64_t *__restrict__ row_off, int count, const uint32_t *__restrict__ set_inst,
+                    int64_t coef_stride, uint64_t *__restrict__ klo, uint64_t *__restrict__ khi,
+                    uint32_t *__restrict__ tag, uint32_t *__restrict__ seen1, uint32_t *__restrict__ seen2,
+                    uint64_t seen_mask, int64_t g0) {
+    const int t = blockIdx.y;
+    const int64_t so = (int64_t)t * nsets;
+    uint64_t a[4] = {0, 0, 0, 0}, b[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+        if (k < Ks) {
+            a[k] = A[t * Ks + k];
+            b[k] = B[t * Ks + k];
         }
+    int have = count > 1 ? -1 : 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * SM_U;
+    for (int64_t gb = g0 + (int64_t)blockIdx.x * blockDim.x * SM_U; gb < nsets; gb += stride) {
+        int64_t s0[SM_U], s1[SM_U];
+        uint32_t inst[SM_U], m0[SM_U], m1[SM_U];
+#pragma unroll
+        for (int u = 0; u < SM_U; u++) {
+            const int64_t g = gb + u * blockDim.x + threadIdx.x;
+            const bool in = g < nsets;
+            s0[u] = in ? soff[g] : 0;
+            s1[u] = in ? soff[g + 1] : 0;
+            inst[u] = (in && count > 1) ? set_inst[g] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < SM_U; u++) {
+            m0[u] = s1[u] > s0[u] ? sids[s0[u]] : 0u;
+            m1[u] = s1[u] > s0[u] + 1 ? sids[s0[u] + 1] : 0u;
+        }
+        uint32_t wpos[SM_U], bit[SM_U];
+#pragma unroll
+        for (int u = 0; u < SM_U; u++) {
+            const int64_t g = gb + u * blockDim.x + threadIdx.x;
+            wpos[u] = 0;
+            bit[u] = 0;
+            if (g >= nsets) continue;
+            uint32_t base = 0;
+            if (count > 1 && s1[u] > s0[u]) {
+                if ((int)inst[u] != have) {
+#pragma unroll
+                    for (int k = 0; k < 4; k++)
+                        if (k < Ks) {
+                            a[k] = A[(int64_t)inst[u] * coef_stride + t * Ks + k];
+                            b[k] = B[(int64_t)inst[u] * coef_stride + t * Ks + k];
+                        }
+                    have = (int)inst[u];
+                }
+                base = (uint32_t)row_off[inst[u]];
+            }
+            uint32_t m[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+            if (s1[u] > s0[u]) {
+#pragma unroll
+                for (int k = 0; k < 4; k++)
+                    if (k < Ks) m[k] = mh_hash32(a[k], b[k], m0[u] - base);
+            }
+            if (s1[u] > s0[u] + 1) {
+#pragma unroll
+                for (int k = 0; k < 4; k++)
+                    if (k < Ks) m[k] = min(m[k], mh_hash32(a[k], b[k], m1[u] - base));
+            }
+            for (int64_t p = s0[u] + 2; p < s1[u]; p++) {
+                const uint32_t id = sids[p] - base;
+#pragma unroll
+                for (int k = 0; k < 4; k++)
+                    if (k < Ks) m[k] = min(m[k], mh_hash32(a[k], b[k], id));
+            }
+            uint64_t hi = 0, lo = 0;
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                if (k < Ks) {
+                    hi = (hi << 32) | (lo >> 32);
+                    lo = (lo << 32) | m[k];
+                }
+            const uint32_t tg = count > 1 && s1[u] > s0[u] ? inst[u] : 0u;
+            klo[so + g] = lo;
+            if (khi) khi[so + g] = hi;
+            if (tag) tag[so + g] = tg;
+            const uint64_t pos = seen_pos(sig_hash(lo, hi, tg), t, seen_mask);
+            wpos[u] = (uint32_t)(pos >> 5);
+            bit[u] = 1u << (pos & 31);
+        }
+        uint32_t old[SM_U];
+#pragma unroll
+        for (int u = 0; u < SM_U; u++) old[u] = bit[u] ? atomicOr(&seen1[wpos[u]], bit[u]) : 0u;
+#pragma unroll
+        for (int u = 0; u < SM_U; u++)
+            if (old[u] & bit[u]) atomicOr(&seen2[wpos[u]], bit[u]);
     }
 }
 
@@ -616,52 +711,83 @@ __device__ __forceinline__ unsigned long long block_append(bool want, unsigned l
 // existing group appends itself to the multi list (key = segment * C + slot);
 // the one joiner that sets the group's SLOT_MULTI bit also appends the
 // group's first set, so every group of >= 2 sets is listed whole.
-__global__ void k_group_insert(int64_t NV, int64_t C, const uint64_t *__restrict__ klo,
-                               const uint64_t *__restrict__ khi, const uint32_t *__restrict__ tag,
-                               const int64_t *__restrict__ roff, const int64_t *__restrict__ rcap,
-                               uint64_t *__restrict__ slot, uint64_t *__restrict__ mkey, uint32_t *__restrict__ mval,
-                               unsigned long long *__restrict__ n_multi, const uint32_t *__restrict__ seen2,
-                               uint64_t seen_mask, const int32_t *__restrict__ vw, const int64_t *__restrict__ voff,
-                               int delta, int64_t *__restrict__ singles, unsigned long long *__restrict__ n_single,
-                               int64_t g0) {
+// A thread takes GI_U sets at a time: their signature loads, seen-twice
+// reads and first slot reads are in flight together.
+constexpr int GI_U = 4;
+__global__ void __launch_bounds__(AP_THREADS, 4)
+    k_group_insert(int64_t NV, int64_t C, const uint64_t *__restrict__ klo, const uint64_t *__restrict__ khi,
+                   const uint32_t *__restrict__ tag, const int64_t *__restrict__ roff,
+                   const int64_t *__restrict__ rcap, uint64_t *__restrict__ slot, uint64_t *__restrict__ mkey,
+                   uint32_t *__restrict__ mval, unsigned long long *__restrict__ n_multi,
+                   const uint32_t *__restrict__ seen2, uint64_t seen_mask, const int32_t *__restrict__ vw,
+                   const int64_t *__restrict__ voff, int delta, int64_t *__restrict__ singles,
+                   unsigned long long *__restrict__ n_single, int64_t g0) {
     // sets g0 .. NV-1 of segment t = blockIdx.y (NV is the segment stride)
     const int t = blockIdx.y;
     const int64_t so = (int64_t)t * NV;
     uint64_t *sl = slot + (int64_t)t * C;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * GI_U;
     __shared__ unsigned s_wc[AP_THREADS / 32];
     __shared__ unsigned long long s_base;
     // the whole block iterates together (the append is a block collective)
-    for (int64_t gb = g0 + (int64_t)blockIdx.x * blockDim.x; gb < NV; gb += stride) {
-        const int64_t g = gb + threadIdx.x;
-        bool joined = false, first = false, single = false;
-        uint32_t rep = 0;
-        uint64_t key = 0;
-        bool go = g < NV;
-        uint64_t lo = 0, hi = 0, hf = 0;
-        uint32_t tg = 0;
-        if (go) {
-            lo = klo[so + g];
-            hi = khi ? khi[so + g] : 0;
-            tg = tag ? tag[so + g] : 0;
-            hf = sig_hash(lo, hi, tg);
-            if (seen2) {
-                const uint64_t pos = seen_pos(hf, t, seen_mask);
-                if (!((seen2[pos >> 5] >> (pos & 31)) & 1u)) {
-                    go = false;  // alone in its bin
-                    single = delta <= 1 && vw[g] >= 2 && voff[g + 1] - voff[g] >= delta;
-                }
+    for (int64_t gb = g0 + (int64_t)blockIdx.x * blockDim.x * GI_U; gb < NV; gb += stride) {
+        uint64_t lo[GI_U], hi[GI_U], hf[GI_U];
+        uint32_t tg[GI_U];
+#pragma unroll
+        for (int u = 0; u < GI_U; u++) {
+            const int64_t g = gb + u * blockDim.x + threadIdx.x;
+            const bool in = g < NV;
+            lo[u] = in ? klo[so + g] : 0;
+            hi[u] = (in && khi) ? khi[so + g] : 0;
+            tg[u] = (in && tag) ? tag[so + g] : 0;
+        }
+        unsigned go = 0;  // bit u: set u probes the grouping table
+        uint32_t bits[GI_U];
+#pragma unroll
+        for (int u = 0; u < GI_U; u++) {
+            hf[u] = sig_hash(lo[u], hi[u], tg[u]);
+            bits[u] = 0;
+            if (gb + u * blockDim.x + threadIdx.x < NV) {
+                if (seen2) bits[u] = seen2[seen_pos(hf[u], t, seen_mask) >> 5];
+                go |= 1u << u;
             }
         }
-        if (go) {
-            const int64_t base = tag ? roff[tg] : 0;
-            const uint64_t mask = (uint64_t)(tag ? rcap[tg] : C) - 1;
-            const uint32_t fp = (uint32_t)(hf >> 32);
+        unsigned sm = 0;  // bit u: set u is alone in its bin and a single-bin candidate
+#pragma unroll
+        for (int u = 0; u < GI_U; u++)
+            if (((go >> u) & 1u) && seen2 && !((bits[u] >> (seen_pos(hf[u], t, seen_mask) & 31)) & 1u)) {
+                go &= ~(1u << u);  // alone in its bin
+                const int64_t g = gb + u * blockDim.x + threadIdx.x;
+                if (delta <= 1 && vw[g] >= 2 && voff[g + 1] - voff[g] >= delta) sm |= 1u << u;
+            }
+        uint64_t cur0[GI_U];
+#pragma unroll
+        for (int u = 0; u < GI_U; u++) {
+            cur0[u] = SLOT_EMPTY;
+            if ((go >> u) & 1u) {
+                const int64_t base = tag ? roff[tg[u]] : 0;
+                const uint64_t mask = (uint64_t)(tag ? rcap[tg[u]] : C) - 1;
+                cur0[u] = sl[base + (hf[u] & mask)];
+            }
+        }
+        unsigned jm = 0, fm = 0;  // joined / first joiner
+        uint64_t key[GI_U];
+        uint32_t rep[GI_U];
+#pragma unroll
+        for (int u = 0; u < GI_U; u++) {
+            key[u] = 0;
+            rep[u] = 0;
+            if (!((go >> u) & 1u)) continue;
+            const int64_t g = gb + u * blockDim.x + threadIdx.x;
+            const int64_t base = tag ? roff[tg[u]] : 0;
+            const uint64_t mask = (uint64_t)(tag ? rcap[tg[u]] : C) - 1;
+            const uint32_t fp = (uint32_t)(hf[u] >> 32);
             const uint64_t mine = ((uint64_t)fp << 32) | (uint64_t)g;
-            uint64_t h = hf & mask;
+            uint64_t h = hf[u] & mask;
+            uint64_t cur = cur0[u];
             for (uint64_t probe = 0; probe <= mask; probe++) {
                 unsigned long long *ps = (unsigned long long *)&sl[base + h];
-                uint64_t cur = *ps;
+                if (probe) cur = *ps;
                 if (cur == SLOT_EMPTY) {
                     const uint64_t prev = atomicCAS(ps, (unsigned long long)SLOT_EMPTY, (unsigned long long)mine);
                     if (prev == SLOT_EMPTY) break;  // first set of a new group
@@ -669,53 +795,64 @@ __global__ void k_group_insert(int64_t NV, int64_t C, const uint64_t *__restrict
                 }
                 if ((uint32_t)(cur >> 32) == fp) {
                     const uint32_t r = (uint32_t)cur & ~SLOT_MULTI;
-                    if (klo[so + r] == lo && (!khi || khi[so + r] == hi) && (!tag || tag[so + r] == tg)) {
-                        if (!(cur & SLOT_MULTI))
-                            first = !(atomicOr(ps, (unsigned long long)SLOT_MULTI) & SLOT_MULTI);
-                        rep = r;
-                        joined = true;
-                        key = (uint64_t)t * (uint64_t)C + (uint64_t)(base + h);
+                    if (klo[so + r] == lo[u] && (!khi || khi[so + r] == hi[u]) && (!tag || tag[so + r] == tg[u])) {
+                        if (!(cur & SLOT_MULTI) && !(atomicOr(ps, (unsigned long long)SLOT_MULTI) & SLOT_MULTI))
+                            fm |= 1u << u;
+                        rep[u] = r;
+                        jm |= 1u << u;
+                        key[u] = (uint64_t)t * (uint64_t)C + (uint64_t)(base + h);
                         break;
                     }
                 }
                 h = (h + 1) & mask;
             }
         }
-        const unsigned long long q = block_append_n((joined ? 1u : 0u) + (first ? 1u : 0u), n_multi, s_wc, &s_base);
-        if (joined) {
-            mkey[q] = key;
-            mval[q] = (uint32_t)g;
+        const unsigned long long q = block_append_n(__popc(jm) + __popc(fm), n_multi, s_wc, &s_base);
+        int w = 0;
+#pragma unroll
+        for (int u = 0; u < GI_U; u++) {
+            if ((jm >> u) & 1u) {
+                mkey[q + w] = key[u];
+                mval[q + w] = (uint32_t)(gb + u * blockDim.x + threadIdx.x);
+                w++;
+            }
+            if ((fm >> u) & 1u) {
+                mkey[q + w] = key[u];
+                mval[q + w] = rep[u];
+                w++;
+            }
         }
-        if (first) {
-            mkey[q + 1] = key;
-            mval[q + 1] = rep;
-        }
-        if (delta <= 1 && __syncthreads_or(single)) {  // (block-uniform)
-            const unsigned long long qs = block_append(single, n_single, s_wc, &s_base);
-            if (single) singles[qs] = g;
+        if (delta <= 1 && __syncthreads_or(sm)) {  // (block-uniform)
+            const unsigned long long qs = block_append_n(__popc(sm), n_single, s_wc, &s_base);
+            int ws = 0;
+#pragma unroll
+            for (int u = 0; u < GI_U; u++)
+                if ((sm >> u) & 1u) singles[qs + ws++] = gb + u * blockDim.x + threadIdx.x;
         }
     }
 }
 
-// One-object virtual buckets {i} (sets 0 .. NS1-1) of a chunk in which every
-// table has, in every instance, a MinHash function injective on the
-// instance's ids (k_mh_injective): two of them never share a signature, so
-// such a set shares its bin only with sets of two or more objects, which
-// marked the seen-once map beforehand (k_set_sig on sets NS1 .. NV-1).  With
-// its seen-once bit clear the set is alone in its bin (no atomic, no
-// signature written); otherwise it marks the seen-twice map (so that the
-// larger sets at that position probe), writes its signature and claims a
-// slot of its own: every earlier claimant is another one-object set, which
-// cannot share its signature, so it joins none.
-__global__ void k_single_insert(int64_t NS1, int64_t NV, const int64_t *__restrict__ soff,
-                                const uint32_t *__restrict__ sids, int Ks, const uint64_t *__restrict__ A,
-                                const uint64_t *__restrict__ B, const int64_t *__restrict__ row_off, int count,
-                                const uint32_t *__restrict__ set_inst, int64_t coef_stride,
-                                uint64_t *__restrict__ klo, uint64_t *__restrict__ khi, uint32_t *__restrict__ tag,
-                                const uint32_t *__restrict__ seen1, uint32_t *__restrict__ seen2, uint64_t seen_mask,
-                                const int64_t *__restrict__ roff, const int64_t *__restrict__ rcap, int64_t C,
-                                uint64_t *__restrict__ slot, const int32_t *__restrict__ vw, int delta,
-                                int64_t *__restrict__ singles, unsigned long long *__restrict__ n_single) {
+// One-object virtual buckets {i} (sets 0 .. NS1-1, set g holding the one
+// object sids[g]) of a chunk in which every table has, in every instance, a
+// MinHash function injective on the instance's ids (k_mh_injective): two of
+// them never share a signature, so such a set shares its bin only with sets
+// of two or more objects, which marked the seen-once map beforehand
+// (k_set_sig on sets NS1 .. NV-1).  With its seen-once bit clear the set is
+// alone in its bin (no atomic, no signature written); otherwise it marks the
+// seen-twice map (so that the larger sets at that position probe), writes
+// its signature and claims a slot of its own: every earlier claimant is
+// another one-object set, which cannot share its signature, so it joins
+// none.  A thread takes SI_U sets at a time, their loads in flight together.
+constexpr int SI_U = 4;
+__global__ void __launch_bounds__(AP_THREADS, 4) k_single_insert(int64_t NS1, int64_t NV, const uint32_t *__restrict__ sids, int Ks,
+                                const uint64_t *__restrict__ A, const uint64_t *__restrict__ B,
+                                const int64_t *__restrict__ row_off, int count, const uint32_t *__restrict__ set_inst,
+                                int64_t coef_stride, uint64_t *__restrict__ klo, uint64_t *__restrict__ khi,
+                                uint32_t *__restrict__ tag, const uint32_t *__restrict__ seen1,
+                                uint32_t *__restrict__ seen2, uint64_t seen_mask, const int64_t *__restrict__ roff,
+                                const int64_t *__restrict__ rcap, int64_t C, uint64_t *__restrict__ slot,
+                                const int32_t *__restrict__ vw, int delta, int64_t *__restrict__ singles,
+                                unsigned long long *__restrict__ n_single) {
     const int t = blockIdx.y;
     const int64_t so = (int64_t)t * NV;
     uint64_t *sl = slot + (int64_t)t * C;
@@ -727,50 +864,81 @@ __global__ void k_single_insert(int64_t NS1, int64_t NV, const int64_t *__restri
             b[k] = B[t * Ks + k];
         }
     int have = count > 1 ? -1 : 0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * SI_U;
     __shared__ unsigned s_wc[AP_THREADS / 32];
     __shared__ unsigned long long s_base;
-    for (int64_t gb = (int64_t)blockIdx.x * blockDim.x; gb < NS1; gb += stride) {
-        const int64_t g = gb + threadIdx.x;
-        bool single = false;
-        if (g < NS1) {
-            const int64_t s0 = soff[g];
-            int inst = 0;
-            uint32_t base = 0;
+    for (int64_t gb = (int64_t)blockIdx.x * blockDim.x * SI_U; gb < NS1; gb += stride) {
+        uint32_t id[SI_U], inst[SI_U];
+#pragma unroll
+        for (int u = 0; u < SI_U; u++) {
+            const int64_t g = gb + u * blockDim.x + threadIdx.x;
+            id[u] = g < NS1 ? sids[g] : 0u;
+            inst[u] = (g < NS1 && count > 1) ? set_inst[g] : 0u;
+        }
+        uint64_t hf[SI_U];
+        uint32_t word[SI_U];
+#pragma unroll
+        for (int u = 0; u < SI_U; u++) {
             if (count > 1) {
-                inst = (int)set_inst[g];
-                base = (uint32_t)row_off[inst];
-                if (inst != have) {
+                if ((int)inst[u] != have) {
 #pragma unroll
                     for (int k = 0; k < 4; k++)
                         if (k < Ks) {
-                            a[k] = A[inst * coef_stride + t * Ks + k];
-                            b[k] = B[inst * coef_stride + t * Ks + k];
+                            a[k] = A[(int64_t)inst[u] * coef_stride + t * Ks + k];
+                            b[k] = B[(int64_t)inst[u] * coef_stride + t * Ks + k];
                         }
-                    have = inst;
+                    have = (int)inst[u];
                 }
+                id[u] -= (uint32_t)row_off[inst[u]];
             }
-            const uint32_t id = sids[s0] - base;
             uint64_t hi = 0, lo = 0;
 #pragma unroll
             for (int k = 0; k < 4; k++)
                 if (k < Ks) {
                     hi = (hi << 32) | (lo >> 32);
-                    lo = (lo << 32) | mh_hash32(a[k], b[k], id);
+                    lo = (lo << 32) | mh_hash32(a[k], b[k], id[u]);
                 }
-            const uint32_t tg = tag ? (uint32_t)inst : 0u;
-            const uint64_t hf = sig_hash(lo, hi, tg);
-            const uint64_t pos = seen_pos(hf, t, seen_mask);
+            hf[u] = sig_hash(lo, hi, tag ? inst[u] : 0u);
+            word[u] = (uint32_t)(seen_pos(hf[u], t, seen_mask) >> 5);
+        }
+        uint32_t bits[SI_U];
+#pragma unroll
+        for (int u = 0; u < SI_U; u++) bits[u] = gb + u * blockDim.x + threadIdx.x < NS1 ? seen1[word[u]] : 0u;
+        int nsingle = 0;
+#pragma unroll
+        for (int u = 0; u < SI_U; u++) {
+            const int64_t g = gb + u * blockDim.x + threadIdx.x;
+            if (g >= NS1) continue;
+            const uint64_t pos = seen_pos(hf[u], t, seen_mask);
             const uint32_t bit = 1u << (pos & 31);
-            if (seen1[pos >> 5] & bit) {
-                atomicOr(&seen2[pos >> 5], bit);
+            if (bits[u] & bit) {
+                // recompute the signature (rare: sets whose position another set marked)
+                const uint32_t tg = tag ? inst[u] : 0u;
+                if (count > 1 && (int)tg != have) {
+#pragma unroll
+                    for (int k = 0; k < 4; k++)
+                        if (k < Ks) {
+                            a[k] = A[(int64_t)tg * coef_stride + t * Ks + k];
+                            b[k] = B[(int64_t)tg * coef_stride + t * Ks + k];
+                        }
+                    have = (int)tg;
+                }
+                const uint32_t x = sids[g] - (count > 1 ? (uint32_t)row_off[tg] : 0u);
+                uint64_t hi = 0, lo = 0;
+#pragma unroll
+                for (int k = 0; k < 4; k++)
+                    if (k < Ks) {
+                        hi = (hi << 32) | (lo >> 32);
+                        lo = (lo << 32) | mh_hash32(a[k], b[k], x);
+                    }
+                atomicOr(&seen2[word[u]], bit);
                 klo[so + g] = lo;
                 if (khi) khi[so + g] = hi;
                 if (tag) tag[so + g] = tg;
                 const int64_t rb = tag ? roff[tg] : 0;
                 const uint64_t mask = (uint64_t)(tag ? rcap[tg] : C) - 1;
-                const uint64_t mine = ((uint64_t)(uint32_t)(hf >> 32) << 32) | (uint64_t)g;
-                uint64_t h = hf & mask;
+                const uint64_t mine = ((uint64_t)(uint32_t)(hf[u] >> 32) << 32) | (uint64_t)g;
+                uint64_t h = hf[u] & mask;
                 for (uint64_t probe = 0; probe <= mask; probe++) {
                     unsigned long long *ps = (unsigned long long *)&sl[rb + h];
                     if (*ps == SLOT_EMPTY &&
@@ -778,13 +946,21 @@ __global__ void k_single_insert(int64_t NS1, int64_t NV, const int64_t *__restri
                         break;
                     h = (h + 1) & mask;
                 }
-            } else {
-                single = delta <= 1 && vw[g] >= 2 && soff[g + 1] - s0 >= delta;
+            } else if (delta <= 1 && vw[g] >= 2) {
+                nsingle++;  // alone in its bin, weight >= 2, one object >= delta
             }
         }
-        if (delta <= 1 && __syncthreads_or(single)) {  // (block-uniform)
-            const unsigned long long qs = block_append(single, n_single, s_wc, &s_base);
-            if (single) singles[qs] = g;
+        if (delta <= 1 && __syncthreads_or(nsingle)) {  // (block-uniform)
+            const unsigned long long qs = block_append_n((unsigned)nsingle, n_single, s_wc, &s_base);
+            int w = 0;
+#pragma unroll
+            for (int u = 0; u < SI_U; u++) {
+                const int64_t g = gb + u * blockDim.x + threadIdx.x;
+                if (g < NS1) {
+                    const uint64_t pos = seen_pos(hf[u], t, seen_mask);
+                    if (!(bits[u] & (1u << (pos & 31))) && vw[g] >= 2) singles[qs + w++] = g;
+                }
+            }
         }
     }
 }
@@ -959,8 +1135,9 @@ geek_status make_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const i
 // vote's bins (perm: virtual bucket per position, rank: bin per position, rs:
 // bin starts, nbins; positions grouped by bin, bins in arbitrary order -- the
 // seeds do not depend on bin order) and the single-bin buckets (singles).
-// ns1 > 0: sets 0 .. ns1-1 hold one object each and no two of them can share
-// a signature in these tables (k_single_insert); ns1 = 0: no such guarantee.
+// ns1 > 0: sets 0 .. ns1-1 hold one object each (set g: sids[g]) and no two
+// of them can share a signature in these tables (k_single_insert); ns1 = 0:
+// no such guarantee.
 geek_status group_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const int64_t *soff, const uint32_t *sids,
                        int64_t nids, int64_t ns1,
                        const int32_t *vw, int delta, int Ks, const uint64_t *A, const uint64_t *B, const SilkBatch *bt,
@@ -1007,6 +1184,8 @@ geek_status group_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const 
     // one-object sets 0 .. ns1-1 (if any) only read the seen-once map
     const int64_t g0 = ns1, nm = nsets - g0;
     const int gm = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nm, 256), (int64_t)ctx->num_sms * 8));
+    const int gi = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nm, 256 * 4), (int64_t)ctx->num_sms * 8));
+    static_assert(SM_U == 4 && GI_U == 4, "grid of the four-sets-per-thread kernels");
     if (nm > 0) {
         GK_COUNT();
         if (nids - g0 >= SS_WIDE * nm)
@@ -1014,22 +1193,23 @@ geek_status group_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const 
                                                tagged ? bt->count : 1, tagged ? bt->set_inst : nullptr, coef_stride,
                                                klo, khi, nullptr, tag, seen1, seen2, (uint64_t)(Mt - 1), g0);
         else
-            k_set_sig<<<dim3(gm, S), 256, 0, st>>>(nsets, soff, sids, Ks, A, B, tagged ? bt->row_off : nullptr,
-                                                   tagged ? bt->count : 1, tagged ? bt->set_inst : nullptr,
-                                                   coef_stride, klo, khi, nullptr, tag, seen1, seen2,
-                                                   (uint64_t)(Mt - 1), g0);
+            k_set_sig_marks<<<dim3(gi, S), 256, 0, st>>>(nsets, soff, sids, Ks, A, B,
+                                                         tagged ? bt->row_off : nullptr, tagged ? bt->count : 1,
+                                                         tagged ? bt->set_inst : nullptr, coef_stride, klo, khi, tag,
+                                                         seen1, seen2, (uint64_t)(Mt - 1), g0);
     }
     if (g0 > 0) {
-        const int gs = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(g0, 256), (int64_t)ctx->num_sms * 8));
+        const int gs =
+            (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(g0, 256 * SI_U), (int64_t)ctx->num_sms * 8));
         GK_COUNT();
-        k_single_insert<<<dim3(gs, S), 256, 0, st>>>(g0, nsets, soff, sids, Ks, A, B, tagged ? bt->row_off : nullptr,
+        k_single_insert<<<dim3(gs, S), 256, 0, st>>>(g0, nsets, sids, Ks, A, B, tagged ? bt->row_off : nullptr,
                                                      tagged ? bt->count : 1, tagged ? bt->set_inst : nullptr,
                                                      coef_stride, klo, khi, tag, seen1, seen2, (uint64_t)(Mt - 1),
                                                      roff, rcap, C, slot, vw, delta, *singles, counts + 1);
     }
     if (nm > 0) {
         GK_COUNT();
-        k_group_insert<<<dim3(gm, S), 256, 0, st>>>(nsets, C, klo, khi, tag, roff, rcap, slot, mkey, mval, counts,
+        k_group_insert<<<dim3(gi, S), 256, 0, st>>>(nsets, C, klo, khi, tag, roff, rcap, slot, mkey, mval, counts,
                                                     seen2, (uint64_t)(Mt - 1), vw, soff, delta, *singles, counts + 1,
                                                     g0);
     }
