@@ -90,19 +90,32 @@ __global__ void k_set_sig(int64_t nsets, const int64_t *__restrict__ soff,
 // batched instances) for the grouping tables, with the seen-once /
 // seen-twice marks: a set marks its position (a hash of signature and
 // instance) in the seen-once map and, when the bit was already set, in the
-// seen-twice map.  A thread takes SM_U sets at a time, loads their bounds and
-// first two members together, and issues the seen-once atomics of all SM_U
-// sets before it waits for any of them.
+// seen-twice map.
+//
+// With ms given, sets 0 .. g0-1 are the one-object virtual buckets and
+// function kst[instance * kst_stride + t] of the table is injective on the
+// instance's ids (k_mh_injective).  Set B then shares its signature with the
+// one-object bucket {a} exactly when a is B's argmin under that function
+// (unique, the function being injective), a attains B's minimum under every
+// other function too, and a has a one-object bucket (single_of): the
+// injective component forces a to be that argmin, and the others then agree.
+// ms[t * (nsets - g0) + g - g0] receives that bucket (or -1), and a set with
+// one marks the seen-twice map directly (its bin holds two sets).
+//
+// A thread takes SM_U sets at a time, loads their bounds and first two
+// members together, and issues the seen-once atomics of all SM_U sets before
+// it waits for any of them.
 constexpr int SM_U = 4;
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, 3)
     k_set_sig_marks(int64_t nsets, const int64_t *__restrict__ soff, const uint32_t *__restrict__ sids, int Ks,
                     const uint64_t *__restrict__ A, const uint64_t *__restrict__ B,
                     const int64_t *__restrict__ row_off, int count, const uint32_t *__restrict__ set_inst,
                     int64_t coef_stride, uint64_t *__restrict__ klo, uint64_t *__restrict__ khi,
                     uint32_t *__restrict__ tag, uint32_t *__restrict__ seen1, uint32_t *__restrict__ seen2,
-                    uint64_t seen_mask, int64_t g0) {
+                    uint64_t seen_mask, int64_t g0, const uint8_t *__restrict__ kst, int kst_stride,
+                    const int32_t *__restrict__ single_of, int32_t *__restrict__ ms) {
     const int t = blockIdx.y;
-    const int64_t so = (int64_t)t * nsets;
+    const int64_t so = (int64_t)t * nsets, nm = nsets - g0;
     uint64_t a[4] = {0, 0, 0, 0}, b[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int k = 0; k < 4; k++)
@@ -110,6 +123,7 @@ __global__ void __launch_bounds__(256, 4)
             a[k] = A[t * Ks + k];
             b[k] = B[t * Ks + k];
         }
+    int ks = ms ? (int)kst[t] : -1;  // injective function of the instance in a / b
     int have = count > 1 ? -1 : 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x * SM_U;
     for (int64_t gb = g0 + (int64_t)blockIdx.x * blockDim.x * SM_U; gb < nsets; gb += stride) {
@@ -129,11 +143,13 @@ __global__ void __launch_bounds__(256, 4)
             m1[u] = s1[u] > s0[u] + 1 ? sids[s0[u] + 1] : 0u;
         }
         uint32_t wpos[SM_U], bit[SM_U];
+        int64_t cand[SM_U];  // global id of the matching one-object bucket's object, or -1
 #pragma unroll
         for (int u = 0; u < SM_U; u++) {
             const int64_t g = gb + u * blockDim.x + threadIdx.x;
             wpos[u] = 0;
             bit[u] = 0;
+            cand[u] = -1;
             if (g >= nsets) continue;
             uint32_t base = 0;
             if (count > 1 && s1[u] > s0[u]) {
@@ -144,26 +160,25 @@ __global__ void __launch_bounds__(256, 4)
                             a[k] = A[(int64_t)inst[u] * coef_stride + t * Ks + k];
                             b[k] = B[(int64_t)inst[u] * coef_stride + t * Ks + k];
                         }
+                    if (ms) ks = (int)kst[(int64_t)inst[u] * kst_stride + t];
                     have = (int)inst[u];
                 }
                 base = (uint32_t)row_off[inst[u]];
             }
             uint32_t m[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
-            if (s1[u] > s0[u]) {
+            uint32_t hs = 0xFFFFFFFFu, as = 0;  // injective function: minimum and argmin
+            for (int64_t p = s0[u]; p < s1[u]; p++) {
+                const uint32_t id = (p == s0[u] ? m0[u] : p == s0[u] + 1 ? m1[u] : sids[p]) - base;
 #pragma unroll
                 for (int k = 0; k < 4; k++)
-                    if (k < Ks) m[k] = mh_hash32(a[k], b[k], m0[u] - base);
-            }
-            if (s1[u] > s0[u] + 1) {
-#pragma unroll
-                for (int k = 0; k < 4; k++)
-                    if (k < Ks) m[k] = min(m[k], mh_hash32(a[k], b[k], m1[u] - base));
-            }
-            for (int64_t p = s0[u] + 2; p < s1[u]; p++) {
-                const uint32_t id = sids[p] - base;
-#pragma unroll
-                for (int k = 0; k < 4; k++)
-                    if (k < Ks) m[k] = min(m[k], mh_hash32(a[k], b[k], id));
+                    if (k < Ks) {
+                        const uint32_t h = mh_hash32(a[k], b[k], id);
+                        if (k == ks && h < hs) {
+                            hs = h;
+                            as = id;
+                        }
+                        m[k] = min(m[k], h);
+                    }
             }
             uint64_t hi = 0, lo = 0;
 #pragma unroll
@@ -179,13 +194,26 @@ __global__ void __launch_bounds__(256, 4)
             const uint64_t pos = seen_pos(sig_hash(lo, hi, tg), t, seen_mask);
             wpos[u] = (uint32_t)(pos >> 5);
             bit[u] = 1u << (pos & 31);
+            if (ms && s1[u] > s0[u] && ks >= 0 && ks < Ks) {
+                bool all = true;
+#pragma unroll
+                for (int k = 0; k < 4; k++)
+                    if (k < Ks) all = all && mh_hash32(a[k], b[k], as) == m[k];
+                if (all) cand[u] = (int64_t)as + base;
+            }
         }
+        int32_t gi[SM_U];
+#pragma unroll
+        for (int u = 0; u < SM_U; u++) gi[u] = cand[u] >= 0 ? single_of[cand[u]] : -1;
         uint32_t old[SM_U];
 #pragma unroll
         for (int u = 0; u < SM_U; u++) old[u] = bit[u] ? atomicOr(&seen1[wpos[u]], bit[u]) : 0u;
 #pragma unroll
-        for (int u = 0; u < SM_U; u++)
-            if (old[u] & bit[u]) atomicOr(&seen2[wpos[u]], bit[u]);
+        for (int u = 0; u < SM_U; u++) {
+            const int64_t g = gb + u * blockDim.x + threadIdx.x;
+            if ((old[u] & bit[u]) || gi[u] >= 0) atomicOr(&seen2[wpos[u]], bit[u]);
+            if (ms && g < nsets) ms[t * nm + (g - g0)] = gi[u];
+        }
     }
 }
 
@@ -540,15 +568,19 @@ __global__ void k_pos_flag(int64_t n, const int32_t *__restrict__ mult, int64_t 
         f[i] = mult[i] > 0;
 }
 
+// (single_of[i]: the one-object virtual bucket {i}, or -1)
 __global__ void k_vb_fill_s(int64_t n, const int32_t *__restrict__ mult, const int64_t *__restrict__ pos,
-                            int64_t *__restrict__ vsz, int32_t *__restrict__ vw, int64_t *__restrict__ vsrc) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+                            int64_t *__restrict__ vsz, int32_t *__restrict__ vw, int64_t *__restrict__ vsrc,
+                            int32_t *__restrict__ single_of) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        single_of[i] = mult[i] > 0 ? (int32_t)pos[i] : -1;
         if (mult[i] > 0) {
             const int64_t v = pos[i];
             vsz[v] = 1;
             vw[v] = mult[i];
             vsrc[v] = i;
         }
+    }
 }
 
 __global__ void k_vb_fill_n(int64_t NB, const int64_t *__restrict__ boff, const int64_t *__restrict__ ns_flag,
@@ -711,20 +743,26 @@ __device__ __forceinline__ unsigned long long block_append(bool want, unsigned l
 // existing group appends itself to the multi list (key = segment * C + slot);
 // the one joiner that sets the group's SLOT_MULTI bit also appends the
 // group's first set, so every group of >= 2 sets is listed whole.
+// With ms given (k_set_sig_marks), a set whose signature equals that of the
+// one-object bucket ms[...] claims it in the claimed map (one bit per table
+// and one-object bucket): the one claimant appends the bucket to its group,
+// which then holds >= 2 sets, with the group's first set as above.
+//
 // A thread takes GI_U sets at a time: their signature loads, seen-twice
 // reads and first slot reads are in flight together.
 constexpr int GI_U = 4;
-__global__ void __launch_bounds__(AP_THREADS, 4)
+__global__ void __launch_bounds__(AP_THREADS, 3)
     k_group_insert(int64_t NV, int64_t C, const uint64_t *__restrict__ klo, const uint64_t *__restrict__ khi,
                    const uint32_t *__restrict__ tag, const int64_t *__restrict__ roff,
                    const int64_t *__restrict__ rcap, uint64_t *__restrict__ slot, uint64_t *__restrict__ mkey,
                    uint32_t *__restrict__ mval, unsigned long long *__restrict__ n_multi,
                    const uint32_t *__restrict__ seen2, uint64_t seen_mask, const int32_t *__restrict__ vw,
                    const int64_t *__restrict__ voff, int delta, int64_t *__restrict__ singles,
-                   unsigned long long *__restrict__ n_single, int64_t g0) {
+                   unsigned long long *__restrict__ n_single, int64_t g0, const int32_t *__restrict__ ms,
+                   uint32_t *__restrict__ claimed, int64_t claimed_words) {
     // sets g0 .. NV-1 of segment t = blockIdx.y (NV is the segment stride)
     const int t = blockIdx.y;
-    const int64_t so = (int64_t)t * NV;
+    const int64_t so = (int64_t)t * NV, nm = NV - g0;
     uint64_t *sl = slot + (int64_t)t * C;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x * GI_U;
     __shared__ unsigned s_wc[AP_THREADS / 32];
@@ -733,6 +771,7 @@ __global__ void __launch_bounds__(AP_THREADS, 4)
     for (int64_t gb = g0 + (int64_t)blockIdx.x * blockDim.x * GI_U; gb < NV; gb += stride) {
         uint64_t lo[GI_U], hi[GI_U], hf[GI_U];
         uint32_t tg[GI_U];
+        int32_t gi[GI_U];
 #pragma unroll
         for (int u = 0; u < GI_U; u++) {
             const int64_t g = gb + u * blockDim.x + threadIdx.x;
@@ -740,6 +779,7 @@ __global__ void __launch_bounds__(AP_THREADS, 4)
             lo[u] = in ? klo[so + g] : 0;
             hi[u] = (in && khi) ? khi[so + g] : 0;
             tg[u] = (in && tag) ? tag[so + g] : 0;
+            gi[u] = (in && ms) ? ms[t * nm + (g - g0)] : -1;
         }
         unsigned go = 0;  // bit u: set u probes the grouping table
         uint32_t bits[GI_U];
@@ -770,7 +810,7 @@ __global__ void __launch_bounds__(AP_THREADS, 4)
                 cur0[u] = sl[base + (hf[u] & mask)];
             }
         }
-        unsigned jm = 0, fm = 0;  // joined / first joiner
+        unsigned jm = 0, fm = 0, cm = 0;  // joined / appends the group's first set / claimed gi
         uint64_t key[GI_U];
         uint32_t rep[GI_U];
 #pragma unroll
@@ -790,12 +830,18 @@ __global__ void __launch_bounds__(AP_THREADS, 4)
                 if (probe) cur = *ps;
                 if (cur == SLOT_EMPTY) {
                     const uint64_t prev = atomicCAS(ps, (unsigned long long)SLOT_EMPTY, (unsigned long long)mine);
-                    if (prev == SLOT_EMPTY) break;  // first set of a new group
+                    if (prev == SLOT_EMPTY) {  // first set of a new group
+                        rep[u] = (uint32_t)g;
+                        key[u] = (uint64_t)t * (uint64_t)C + (uint64_t)(base + h);
+                        break;
+                    }
                     cur = prev;
                 }
                 if ((uint32_t)(cur >> 32) == fp) {
                     const uint32_t r = (uint32_t)cur & ~SLOT_MULTI;
-                    if (klo[so + r] == lo[u] && (!khi || khi[so + r] == hi[u]) && (!tag || tag[so + r] == tg[u])) {
+                    const uint64_t rlo = klo[so + r], rhi = khi ? khi[so + r] : 0;
+                    const uint32_t rtg = tag ? tag[so + r] : 0;
+                    if (rlo == lo[u] && rhi == hi[u] && rtg == tg[u]) {
                         if (!(cur & SLOT_MULTI) && !(atomicOr(ps, (unsigned long long)SLOT_MULTI) & SLOT_MULTI))
                             fm |= 1u << u;
                         rep[u] = r;
@@ -806,8 +852,17 @@ __global__ void __launch_bounds__(AP_THREADS, 4)
                 }
                 h = (h + 1) & mask;
             }
+            if (gi[u] >= 0) {  // claim the one-object bucket with this signature
+                const uint32_t cb = 1u << (gi[u] & 31);
+                if (!(atomicOr(&claimed[t * claimed_words + (gi[u] >> 5)], cb) & cb)) {
+                    cm |= 1u << u;
+                    if (!(atomicOr((unsigned long long *)&slot[key[u]], (unsigned long long)SLOT_MULTI) & SLOT_MULTI))
+                        fm |= 1u << u;
+                }
+            }
         }
-        const unsigned long long q = block_append_n(__popc(jm) + __popc(fm), n_multi, s_wc, &s_base);
+        const unsigned long long q =
+            block_append_n(__popc(jm) + __popc(fm) + __popc(cm), n_multi, s_wc, &s_base);
         int w = 0;
 #pragma unroll
         for (int u = 0; u < GI_U; u++) {
@@ -821,6 +876,11 @@ __global__ void __launch_bounds__(AP_THREADS, 4)
                 mval[q + w] = rep[u];
                 w++;
             }
+            if ((cm >> u) & 1u) {
+                mkey[q + w] = key[u];
+                mval[q + w] = (uint32_t)gi[u];
+                w++;
+            }
         }
         if (delta <= 1 && __syncthreads_or(sm)) {  // (block-uniform)
             const unsigned long long qs = block_append_n(__popc(sm), n_single, s_wc, &s_base);
@@ -832,135 +892,23 @@ __global__ void __launch_bounds__(AP_THREADS, 4)
     }
 }
 
-// One-object virtual buckets {i} (sets 0 .. NS1-1, set g holding the one
-// object sids[g]) of a chunk in which every table has, in every instance, a
-// MinHash function injective on the instance's ids (k_mh_injective): two of
-// them never share a signature, so such a set shares its bin only with sets
-// of two or more objects, which marked the seen-once map beforehand
-// (k_set_sig on sets NS1 .. NV-1).  With its seen-once bit clear the set is
-// alone in its bin (no atomic, no signature written); otherwise it marks the
-// seen-twice map (so that the larger sets at that position probe), writes
-// its signature and claims a slot of its own: every earlier claimant is
-// another one-object set, which cannot share its signature, so it joins
-// none.  A thread takes SI_U sets at a time, their loads in flight together.
-constexpr int SI_U = 4;
-__global__ void __launch_bounds__(AP_THREADS, 4) k_single_insert(int64_t NS1, int64_t NV, const uint32_t *__restrict__ sids, int Ks,
-                                const uint64_t *__restrict__ A, const uint64_t *__restrict__ B,
-                                const int64_t *__restrict__ row_off, int count, const uint32_t *__restrict__ set_inst,
-                                int64_t coef_stride, uint64_t *__restrict__ klo, uint64_t *__restrict__ khi,
-                                uint32_t *__restrict__ tag, const uint32_t *__restrict__ seen1,
-                                uint32_t *__restrict__ seen2, uint64_t seen_mask, const int64_t *__restrict__ roff,
-                                const int64_t *__restrict__ rcap, int64_t C, uint64_t *__restrict__ slot,
-                                const int32_t *__restrict__ vw, int delta, int64_t *__restrict__ singles,
-                                unsigned long long *__restrict__ n_single) {
+// delta <= 1 with one-object buckets claimed (k_group_insert): a one-object
+// bucket that no set of table t claimed is alone in its bin, and with weight
+// >= 2 that bin keeps it (one object >= delta).
+__global__ void k_single_unclaimed(int64_t ns1, const uint32_t *__restrict__ claimed, int64_t claimed_words,
+                                   const int32_t *__restrict__ vw, int64_t *__restrict__ singles,
+                                   unsigned long long *__restrict__ n_single) {
     const int t = blockIdx.y;
-    const int64_t so = (int64_t)t * NV;
-    uint64_t *sl = slot + (int64_t)t * C;
-    uint64_t a[4] = {0, 0, 0, 0}, b[4] = {0, 0, 0, 0};
-#pragma unroll
-    for (int k = 0; k < 4; k++)
-        if (k < Ks) {
-            a[k] = A[t * Ks + k];
-            b[k] = B[t * Ks + k];
-        }
-    int have = count > 1 ? -1 : 0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x * SI_U;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     __shared__ unsigned s_wc[AP_THREADS / 32];
     __shared__ unsigned long long s_base;
-    for (int64_t gb = (int64_t)blockIdx.x * blockDim.x * SI_U; gb < NS1; gb += stride) {
-        uint32_t id[SI_U], inst[SI_U];
-#pragma unroll
-        for (int u = 0; u < SI_U; u++) {
-            const int64_t g = gb + u * blockDim.x + threadIdx.x;
-            id[u] = g < NS1 ? sids[g] : 0u;
-            inst[u] = (g < NS1 && count > 1) ? set_inst[g] : 0u;
-        }
-        uint64_t hf[SI_U];
-        uint32_t word[SI_U];
-#pragma unroll
-        for (int u = 0; u < SI_U; u++) {
-            if (count > 1) {
-                if ((int)inst[u] != have) {
-#pragma unroll
-                    for (int k = 0; k < 4; k++)
-                        if (k < Ks) {
-                            a[k] = A[(int64_t)inst[u] * coef_stride + t * Ks + k];
-                            b[k] = B[(int64_t)inst[u] * coef_stride + t * Ks + k];
-                        }
-                    have = (int)inst[u];
-                }
-                id[u] -= (uint32_t)row_off[inst[u]];
-            }
-            uint64_t hi = 0, lo = 0;
-#pragma unroll
-            for (int k = 0; k < 4; k++)
-                if (k < Ks) {
-                    hi = (hi << 32) | (lo >> 32);
-                    lo = (lo << 32) | mh_hash32(a[k], b[k], id[u]);
-                }
-            hf[u] = sig_hash(lo, hi, tag ? inst[u] : 0u);
-            word[u] = (uint32_t)(seen_pos(hf[u], t, seen_mask) >> 5);
-        }
-        uint32_t bits[SI_U];
-#pragma unroll
-        for (int u = 0; u < SI_U; u++) bits[u] = gb + u * blockDim.x + threadIdx.x < NS1 ? seen1[word[u]] : 0u;
-        int nsingle = 0;
-#pragma unroll
-        for (int u = 0; u < SI_U; u++) {
-            const int64_t g = gb + u * blockDim.x + threadIdx.x;
-            if (g >= NS1) continue;
-            const uint64_t pos = seen_pos(hf[u], t, seen_mask);
-            const uint32_t bit = 1u << (pos & 31);
-            if (bits[u] & bit) {
-                // recompute the signature (rare: sets whose position another set marked)
-                const uint32_t tg = tag ? inst[u] : 0u;
-                if (count > 1 && (int)tg != have) {
-#pragma unroll
-                    for (int k = 0; k < 4; k++)
-                        if (k < Ks) {
-                            a[k] = A[(int64_t)tg * coef_stride + t * Ks + k];
-                            b[k] = B[(int64_t)tg * coef_stride + t * Ks + k];
-                        }
-                    have = (int)tg;
-                }
-                const uint32_t x = sids[g] - (count > 1 ? (uint32_t)row_off[tg] : 0u);
-                uint64_t hi = 0, lo = 0;
-#pragma unroll
-                for (int k = 0; k < 4; k++)
-                    if (k < Ks) {
-                        hi = (hi << 32) | (lo >> 32);
-                        lo = (lo << 32) | mh_hash32(a[k], b[k], x);
-                    }
-                atomicOr(&seen2[word[u]], bit);
-                klo[so + g] = lo;
-                if (khi) khi[so + g] = hi;
-                if (tag) tag[so + g] = tg;
-                const int64_t rb = tag ? roff[tg] : 0;
-                const uint64_t mask = (uint64_t)(tag ? rcap[tg] : C) - 1;
-                const uint64_t mine = ((uint64_t)(uint32_t)(hf[u] >> 32) << 32) | (uint64_t)g;
-                uint64_t h = hf[u] & mask;
-                for (uint64_t probe = 0; probe <= mask; probe++) {
-                    unsigned long long *ps = (unsigned long long *)&sl[rb + h];
-                    if (*ps == SLOT_EMPTY &&
-                        atomicCAS(ps, (unsigned long long)SLOT_EMPTY, (unsigned long long)mine) == SLOT_EMPTY)
-                        break;
-                    h = (h + 1) & mask;
-                }
-            } else if (delta <= 1 && vw[g] >= 2) {
-                nsingle++;  // alone in its bin, weight >= 2, one object >= delta
-            }
-        }
-        if (delta <= 1 && __syncthreads_or(nsingle)) {  // (block-uniform)
-            const unsigned long long qs = block_append_n((unsigned)nsingle, n_single, s_wc, &s_base);
-            int w = 0;
-#pragma unroll
-            for (int u = 0; u < SI_U; u++) {
-                const int64_t g = gb + u * blockDim.x + threadIdx.x;
-                if (g < NS1) {
-                    const uint64_t pos = seen_pos(hf[u], t, seen_mask);
-                    if (!(bits[u] & (1u << (pos & 31))) && vw[g] >= 2) singles[qs + w++] = g;
-                }
-            }
+    for (int64_t gb = (int64_t)blockIdx.x * blockDim.x; gb < ns1; gb += stride) {
+        const int64_t g = gb + threadIdx.x;
+        const bool single =
+            g < ns1 && vw[g] >= 2 && !((claimed[t * claimed_words + (g >> 5)] >> (g & 31)) & 1u);
+        if (__syncthreads_or(single)) {  // (block-uniform)
+            const unsigned long long qs = block_append(single, n_single, s_wc, &s_base);
+            if (single) singles[qs] = g;
         }
     }
 }
@@ -1135,11 +1083,14 @@ geek_status make_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const i
 // vote's bins (perm: virtual bucket per position, rank: bin per position, rs:
 // bin starts, nbins; positions grouped by bin, bins in arbitrary order -- the
 // seeds do not depend on bin order) and the single-bin buckets (singles).
-// ns1 > 0: sets 0 .. ns1-1 hold one object each (set g: sids[g]) and no two
-// of them can share a signature in these tables (k_single_insert); ns1 = 0:
-// no such guarantee.
+// ns1 > 0: sets 0 .. ns1-1 hold one object each, single_of maps an object
+// to its one-object set, and function kst[instance * kst_stride + t] of
+// table t is injective on the instance's ids, so that no two one-object sets
+// share a signature and each other set finds the one that shares its own
+// (k_set_sig_marks); ns1 = 0: no such guarantee, every set goes through the
+// seen maps and the grouping tables.
 geek_status group_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const int64_t *soff, const uint32_t *sids,
-                       int64_t nids, int64_t ns1,
+                       int64_t nids, int64_t ns1, const uint8_t *kst, int kst_stride, const int32_t *single_of,
                        const int32_t *vw, int delta, int Ks, const uint64_t *A, const uint64_t *B, const SilkBatch *bt,
                        int64_t coef_stride, uint32_t **perm, int32_t **rank, int64_t **rs, int64_t *npos,
                        int64_t *nbins, int64_t **singles, int64_t *n_singles, cudaStream_t st) {
@@ -1181,41 +1132,47 @@ geek_status group_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const 
     GK_CUDA(ctx, cudaMemsetAsync(seen, 0, sizeof(uint32_t) * (size_t)(M / 32) * 2, st));
     uint32_t *seen1 = seen, *seen2 = seen + M / 32;
     // sets g0 .. nsets-1 go through the seen maps and the grouping tables;
-    // one-object sets 0 .. ns1-1 (if any) only read the seen-once map
-    const int64_t g0 = ns1, nm = nsets - g0;
+    // one-object sets 0 .. ns1-1, on the claim path, are claimed by the sets
+    // that share their signature (sets of many members take k_set_sig_sets
+    // and no claims)
+    const bool wide = nids >= SS_WIDE * nsets;
+    const bool claims = ns1 > 0 && !wide && kst && single_of;
+    const int64_t g0 = claims ? ns1 : 0, nm = nsets - g0;
     const int gm = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nm, 256), (int64_t)ctx->num_sms * 8));
     const int gi = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nm, 256 * 4), (int64_t)ctx->num_sms * 8));
     static_assert(SM_U == 4 && GI_U == 4, "grid of the four-sets-per-thread kernels");
+    int32_t *ms = nullptr;
+    uint32_t *claimed = nullptr;
+    const int64_t cwords = ceil_div(std::max<int64_t>(g0, 1), 32);
+    if (claims) {
+        GK_TRY(scr.alloc(&ms, std::max<int64_t>((int64_t)S * nm, 1)));
+        GK_TRY(scr.alloc(&claimed, (size_t)S * cwords));
+        GK_CUDA(ctx, cudaMemsetAsync(claimed, 0, sizeof(uint32_t) * (size_t)S * cwords, st));
+    }
     if (nm > 0) {
         GK_COUNT();
-        if (nids - g0 >= SS_WIDE * nm)
+        if (wide)
             k_set_sig_sets<<<gm, 256, 0, st>>>(nsets, S, soff, sids, Ks, A, B, tagged ? bt->row_off : nullptr,
                                                tagged ? bt->count : 1, tagged ? bt->set_inst : nullptr, coef_stride,
                                                klo, khi, nullptr, tag, seen1, seen2, (uint64_t)(Mt - 1), g0);
         else
-            k_set_sig_marks<<<dim3(gi, S), 256, 0, st>>>(nsets, soff, sids, Ks, A, B,
-                                                         tagged ? bt->row_off : nullptr, tagged ? bt->count : 1,
-                                                         tagged ? bt->set_inst : nullptr, coef_stride, klo, khi, tag,
-                                                         seen1, seen2, (uint64_t)(Mt - 1), g0);
-    }
-    if (g0 > 0) {
-        const int gs =
-            (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(g0, 256 * SI_U), (int64_t)ctx->num_sms * 8));
-        GK_COUNT();
-        k_single_insert<<<dim3(gs, S), 256, 0, st>>>(g0, nsets, sids, Ks, A, B, tagged ? bt->row_off : nullptr,
-                                                     tagged ? bt->count : 1, tagged ? bt->set_inst : nullptr,
-                                                     coef_stride, klo, khi, tag, seen1, seen2, (uint64_t)(Mt - 1),
-                                                     roff, rcap, C, slot, vw, delta, *singles, counts + 1);
-    }
-    if (nm > 0) {
+            k_set_sig_marks<<<dim3(gi, S), 256, 0, st>>>(
+                nsets, soff, sids, Ks, A, B, tagged ? bt->row_off : nullptr, tagged ? bt->count : 1,
+                tagged ? bt->set_inst : nullptr, coef_stride, klo, khi, tag, seen1, seen2, (uint64_t)(Mt - 1), g0,
+                kst, kst_stride, single_of, ms);
         GK_COUNT();
         k_group_insert<<<dim3(gi, S), 256, 0, st>>>(nsets, C, klo, khi, tag, roff, rcap, slot, mkey, mval, counts,
                                                     seen2, (uint64_t)(Mt - 1), vw, soff, delta, *singles, counts + 1,
-                                                    g0);
+                                                    g0, ms, claimed, cwords);
     }
     if (delta <= 1) {
         GK_COUNT();
-        k_group_singles<<<G(ctx, S * C), 256, 0, st>>>(C, S, slot, vw, soff, delta, *singles, counts + 1);
+        if (claims) {
+            const int gs = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(g0, 256), (int64_t)ctx->num_sms * 8));
+            k_single_unclaimed<<<dim3(gs, S), 256, 0, st>>>(g0, claimed, cwords, vw, *singles, counts + 1);
+        } else {
+            k_group_singles<<<G(ctx, S * C), 256, 0, st>>>(C, S, slot, vw, soff, delta, *singles, counts + 1);
+        }
     }
     GK_LAUNCH(ctx);
     unsigned long long h[2];
@@ -1514,15 +1471,16 @@ geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p,
     GK_TRY(d2h_i64(ctx, d_ns2, &NS2, st));
     const int64_t NV = NS1 + NS2;
     int64_t *vsz, *vsrc, *voff, *d_vtot;
-    int32_t *vw;
+    int32_t *vw, *single_of;
     uint32_t *vmem;
+    GK_TRY(scr.alloc(&single_of, std::max<int64_t>(n, 1)));
     GK_TRY(scr.alloc(&vsz, std::max<int64_t>(NV, 1)));
     GK_TRY(scr.alloc(&vsrc, std::max<int64_t>(NV, 1)));
     GK_TRY(scr.alloc(&vw, std::max<int64_t>(NV, 1)));
     GK_TRY(scr.alloc(&voff, NV + 1));
     GK_TRY(scr.alloc(&d_vtot, 1));
     GK_COUNT();
-    k_vb_fill_s<<<G(ctx, n), 256, 0, st>>>(n, mult, s_pos, vsz, vw, vsrc);
+    k_vb_fill_s<<<G(ctx, n), 256, 0, st>>>(n, mult, s_pos, vsz, vw, vsrc, single_of);
     GK_COUNT();
     k_vb_fill_n<<<G(ctx, NB), 256, 0, st>>>(NB, b->boff, ns_flag, n_pos, NS1, vsz, vw, vsrc);
     GK_LAUNCH(ctx);
@@ -1536,8 +1494,10 @@ geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p,
     GK_LAUNCH(ctx);
     // SILK tables in which no two one-object virtual buckets can share a
     // signature: in every instance one of the table's Ks functions is
-    // injective on the instance's ids (k_mh_injective)
+    // injective on the instance's ids (k_mh_injective); kst holds the first
+    // such function per (instance, table), 255 where there is none
     std::vector<char> tab_one(Ls, 0);
+    uint8_t *kst = nullptr;
     if (NS1 > 0) {
         const int cnt = (bt && bt->count > 1) ? bt->count : 1;
         uint32_t *fb;
@@ -1550,12 +1510,18 @@ geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p,
         std::vector<uint32_t> hfb((size_t)cnt * Ls);
         GK_CUDA(ctx, cudaMemcpyAsync(hfb.data(), fb, sizeof(uint32_t) * hfb.size(), cudaMemcpyDeviceToHost, st));
         GK_CUDA(ctx, cudaStreamSynchronize(st));
-        const uint32_t all = (1u << Ks) - 1u;
+        std::vector<uint8_t> hk((size_t)cnt * Ls, 255);
+        for (size_t e = 0; e < hk.size(); e++)
+            for (int k = Ks - 1; k >= 0; k--)
+                if (!((hfb[e] >> k) & 1u)) hk[e] = (uint8_t)k;
         for (int t = 0; t < Ls; t++) {
             bool ok = true;
-            for (int i = 0; i < cnt && ok; i++) ok = (hfb[(size_t)i * Ls + t] & all) != all;
+            for (int i = 0; i < cnt && ok; i++) ok = hk[(size_t)i * Ls + t] != 255;
             tab_one[t] = ok;
         }
+        GK_TRY(scr.alloc(&kst, hk.size()));
+        GK_CUDA(ctx, cudaMemcpyAsync(kst, hk.data(), hk.size(), cudaMemcpyHostToDevice, st));
+        GK_CUDA(ctx, cudaStreamSynchronize(st));
     }
 
     t_vb.stop();
@@ -1580,7 +1546,8 @@ geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p,
         for (int u = t; u < t + S; u++) one = one && tab_one[u];
         {
             EvTimer tb(ctx, "silk.bins", st);
-            GK_TRY(group_bins(ctx, tscr, S, NV, voff, vmem, VT, one ? NS1 : 0, vw, delta, Ks, p->mh_a + (int64_t)t * Ks,
+            GK_TRY(group_bins(ctx, tscr, S, NV, voff, vmem, VT, one ? NS1 : 0, kst ? kst + t : nullptr, Ls,
+                              single_of, vw, delta, Ks, p->mh_a + (int64_t)t * Ks,
                               p->mh_b + (int64_t)t * Ks, bt, (int64_t)Ls * Ks, &perm, &rank, &rs, &npos, &nbins,
                               &singles, &nh, st));
         }
