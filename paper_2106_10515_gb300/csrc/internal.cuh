@@ -165,9 +165,12 @@ struct silk_seeds {
 struct SilkBatch {
     const int64_t *row_off = nullptr;
     int count = 1;
-    // set inside silk_run: per-instance slot regions of the grouping tables
+    // set inside silk_run: per-instance slot regions of the grouping tables,
+    // for all sets and (_m) for the sets of two or more objects
     const int64_t *slot_off = nullptr, *slot_cap = nullptr;
     int64_t slots = 0;
+    const int64_t *slot_off_m = nullptr, *slot_cap_m = nullptr;
+    int64_t slots_m = 0;
     const uint32_t *set_inst = nullptr;  // instance of every virtual bucket
 };
 geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p, silk_seeds *out,

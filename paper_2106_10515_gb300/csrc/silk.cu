@@ -965,9 +965,10 @@ __global__ void k_group_singles(int64_t C, int S, const uint64_t *__restrict__ s
 
 // sets per instance (the instance of a set is that of its first member);
 // lanes of a warp with the same instance add once
+// (cnt[count + i]: the sets of instance i from set g_multi on)
 __global__ void k_sets_per_inst(int64_t nsets, const int64_t *__restrict__ soff, const uint32_t *__restrict__ sids,
-                                const int64_t *__restrict__ row_off, int count, unsigned long long *__restrict__ cnt,
-                                uint32_t *__restrict__ set_inst) {
+                                const int64_t *__restrict__ row_off, int count, int64_t g_multi,
+                                unsigned long long *__restrict__ cnt, uint32_t *__restrict__ set_inst) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nsets; base += stride) {
@@ -976,6 +977,9 @@ __global__ void k_sets_per_inst(int64_t nsets, const int64_t *__restrict__ soff,
         if (g < nsets) set_inst[g] = (uint32_t)i;
         const unsigned peers = __match_any_sync(0xffffffffu, i);
         if (i >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[i], (unsigned long long)__popc(peers));
+        const int im = g >= g_multi ? i : -1;
+        const unsigned pm = __match_any_sync(0xffffffffu, im);
+        if (im >= 0 && lane == __ffs(pm) - 1) atomicAdd(&cnt[count + im], (unsigned long long)__popc(pm));
     }
 }
 
@@ -1096,14 +1100,22 @@ geek_status group_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const 
                        int64_t *nbins, int64_t **singles, int64_t *n_singles, cudaStream_t st) {
     const int64_t tot = (int64_t)S * nsets;
     const bool tagged = bt && bt->count > 1;
+    // sets g0 .. nsets-1 go through the seen maps and the grouping tables;
+    // one-object sets 0 .. ns1-1, on the claim path, are claimed by the sets
+    // that share their signature (sets of many members take k_set_sig_sets
+    // and no claims)
+    const bool wide = nids >= SS_WIDE * nsets;
+    const bool claims = ns1 > 0 && !wide && kst && single_of;
+    const int64_t g0 = claims ? ns1 : 0, nm = nsets - g0;
     int64_t C = 64;
-    while (C < 2 * nsets) C <<= 1;
+    while (C < 2 * nm) C <<= 1;
     const int64_t *roff = nullptr, *rcap = nullptr;
     if (tagged) {
-        if (!bt->slot_off || !bt->slot_cap) return set_error(ctx, GEEK_ERR_INVALID, "slot regions missing");
-        roff = bt->slot_off;
-        rcap = bt->slot_cap;
-        C = bt->slots;
+        if (!bt->slot_off || !bt->slot_cap || !bt->slot_off_m || !bt->slot_cap_m)
+            return set_error(ctx, GEEK_ERR_INVALID, "slot regions missing");
+        roff = claims ? bt->slot_off_m : bt->slot_off;
+        rcap = claims ? bt->slot_cap_m : bt->slot_cap;
+        C = claims ? bt->slots_m : bt->slots;
     }
     uint64_t *klo, *khi = nullptr;
     if (nsets >= (int64_t)SLOT_MULTI - 1) return set_error(ctx, GEEK_ERR_UNSUPPORTED, "more than 2^31 SILK sets");
@@ -1131,13 +1143,6 @@ geek_status group_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const 
     GK_TRY(scr.alloc(&seen, (size_t)(M / 32) * 2));
     GK_CUDA(ctx, cudaMemsetAsync(seen, 0, sizeof(uint32_t) * (size_t)(M / 32) * 2, st));
     uint32_t *seen1 = seen, *seen2 = seen + M / 32;
-    // sets g0 .. nsets-1 go through the seen maps and the grouping tables;
-    // one-object sets 0 .. ns1-1, on the claim path, are claimed by the sets
-    // that share their signature (sets of many members take k_set_sig_sets
-    // and no claims)
-    const bool wide = nids >= SS_WIDE * nsets;
-    const bool claims = ns1 > 0 && !wide && kst && single_of;
-    const int64_t g0 = claims ? ns1 : 0, nm = nsets - g0;
     const int gm = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nm, 256), (int64_t)ctx->num_sms * 8));
     const int gi = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nm, 256 * 4), (int64_t)ctx->num_sms * 8));
     static_assert(SM_U == 4 && GI_U == 4, "grid of the four-sets-per-thread kernels");
@@ -1198,41 +1203,49 @@ geek_status group_bins(geek_ctx *ctx, Scratch &scr, int S, int64_t nsets, const 
 }
 
 // One slot region per instance for group_bins: a power of two >= 2x the
-// instance's sets (device arrays from scr, total in bt->slots).
+// instance's sets (device arrays from scr, total in bt->slots), and one sized
+// for its sets from g_multi on (bt->slot_off_m ...: the claim path, on which
+// only those sets enter the grouping tables).
 geek_status slot_regions(geek_ctx *ctx, Scratch &scr, int64_t nsets, const int64_t *soff, const uint32_t *sids,
-                         SilkBatch *bt, cudaStream_t st) {
+                         int64_t g_multi, SilkBatch *bt, cudaStream_t st) {
     const int count = bt->count;
     unsigned long long *cnt;
     uint32_t *set_inst;
-    GK_TRY(scr.alloc(&cnt, count));
+    GK_TRY(scr.alloc(&cnt, 2 * (size_t)count));
     GK_TRY(scr.alloc(&set_inst, std::max<int64_t>(nsets, 1)));
-    GK_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * count, st));
+    GK_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * 2 * count, st));
     if (nsets) {
         GK_COUNT();
-        k_sets_per_inst<<<G(ctx, nsets), 256, 0, st>>>(nsets, soff, sids, bt->row_off, count, cnt, set_inst);
+        k_sets_per_inst<<<G(ctx, nsets), 256, 0, st>>>(nsets, soff, sids, bt->row_off, count, g_multi, cnt,
+                                                       set_inst);
         GK_LAUNCH(ctx);
     }
     bt->set_inst = set_inst;
-    std::vector<unsigned long long> hc(count);
-    GK_CUDA(ctx, cudaMemcpyAsync(hc.data(), cnt, sizeof(unsigned long long) * count, cudaMemcpyDeviceToHost, st));
+    std::vector<unsigned long long> hc(2 * (size_t)count);
+    GK_CUDA(ctx, cudaMemcpyAsync(hc.data(), cnt, sizeof(unsigned long long) * hc.size(), cudaMemcpyDeviceToHost, st));
     GK_CUDA(ctx, cudaStreamSynchronize(st));
-    std::vector<int64_t> ho(count), hp(count);
-    int64_t C = 0;
-    for (int i = 0; i < count; i++) {
-        int64_t c = 32;
-        while (c < 2 * (int64_t)hc[i]) c <<= 1;
-        ho[i] = C;
-        hp[i] = c;
-        C += c;
-    }
+    std::vector<int64_t> ho(2 * (size_t)count), hp(2 * (size_t)count);
+    int64_t Cs[2] = {0, 0};
+    for (int r = 0; r < 2; r++)
+        for (int i = 0; i < count; i++) {
+            int64_t c = 32;
+            while (c < 2 * (int64_t)hc[(size_t)r * count + i]) c <<= 1;
+            ho[(size_t)r * count + i] = Cs[r];
+            hp[(size_t)r * count + i] = c;
+            Cs[r] += c;
+        }
     int64_t *roff, *rcap;
-    GK_TRY(scr.alloc(&roff, count));
-    GK_TRY(scr.alloc(&rcap, count));
-    GK_CUDA(ctx, cudaMemcpyAsync(roff, ho.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice, st));
-    GK_CUDA(ctx, cudaMemcpyAsync(rcap, hp.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice, st));
+    GK_TRY(scr.alloc(&roff, 2 * (size_t)count));
+    GK_TRY(scr.alloc(&rcap, 2 * (size_t)count));
+    GK_CUDA(ctx, cudaMemcpyAsync(roff, ho.data(), sizeof(int64_t) * ho.size(), cudaMemcpyHostToDevice, st));
+    GK_CUDA(ctx, cudaMemcpyAsync(rcap, hp.data(), sizeof(int64_t) * hp.size(), cudaMemcpyHostToDevice, st));
+    GK_CUDA(ctx, cudaStreamSynchronize(st));  // ho / hp leave scope
     bt->slot_off = roff;
     bt->slot_cap = rcap;
-    bt->slots = C;
+    bt->slots = Cs[0];
+    bt->slot_off_m = roff + count;
+    bt->slot_cap_m = rcap + count;
+    bt->slots_m = Cs[1];
     return GEEK_OK;
 }
 
@@ -1528,7 +1541,7 @@ geek_status silk_run(geek_ctx *ctx, const geek_buckets *b, const silk_params *p,
     SilkBatch btl;  // batched: per-instance slot regions of the grouping tables
     if (bt && bt->count > 1) {
         btl = *bt;
-        GK_TRY(slot_regions(ctx, scr, NV, voff, vmem, &btl, st));
+        GK_TRY(slot_regions(ctx, scr, NV, voff, vmem, NS1, &btl, st));
         bt = &btl;
     }
     // ---- Alg. 4: Ls SILK tables over the (virtual) buckets ------------------
