@@ -592,6 +592,39 @@ __device__ __forceinline__ void csum_add(float &sh, float &sl, float v) {
     sl = __fadd_rn(sl, err);
 }
 
+// Lane partials of four rows' distances to their labelled centres (rows
+// i[q] < n; d <= 128, rows and centre halves 16-byte aligned): lane l holds
+// coordinates 4l .. 4l+3, diff = (x - c_hi) - c_lo, squares summed in FP32.
+// Every row's label and coordinates are requested before any centre, so the
+// four rows' loads are in flight together.
+__device__ __forceinline__ void dist4_vec(const float *__restrict__ x, int64_t ldx, int64_t n, int d,
+                                          const float *__restrict__ chi, const float *__restrict__ clo, int64_t k,
+                                          const int32_t *__restrict__ labels, const int64_t (&i)[4], float (&D)[4],
+                                          bool (&ok)[4]) {
+    const int lane = threadIdx.x & 31;
+    const bool mine = 4 * lane < d;
+    int j[4];
+    float4 xv[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        j[q] = i[q] < n ? labels[i[q]] : -1;
+        xv[q] = (i[q] < n && mine) ? *reinterpret_cast<const float4 *>(x + i[q] * ldx + 4 * lane)
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        ok[q] = j[q] >= 0 && j[q] < k;  // uniform across the warp
+        const bool use = ok[q] && mine;
+        const float4 hv = use ? *reinterpret_cast<const float4 *>(chi + (int64_t)j[q] * d + 4 * lane)
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 lv = use ? *reinterpret_cast<const float4 *>(clo + (int64_t)j[q] * d + 4 * lane)
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float e0 = (xv[q].x - hv.x) - lv.x, e1 = (xv[q].y - hv.y) - lv.y;
+        const float e2 = (xv[q].z - hv.z) - lv.z, e3 = (xv[q].w - hv.w) - lv.w;
+        D[q] = use ? fmaf(e3, e3, fmaf(e2, e2, fmaf(e1, e1, fmaf(e0, e0, 0.f)))) : 0.f;
+    }
+}
+
 // per-object distance to its centre, warp per object, lanes over
 // coordinates: diff = (x - c_hi) - c_lo, squares accumulated in FP32; the
 // warp's distances in a compensated FP32 sum, block partial sums (FP64) and
@@ -615,6 +648,10 @@ __global__ void __launch_bounds__(256) k_assign_stats(const float *__restrict__ 
     for (int64_t i0 = warp; i0 < n; i0 += 4 * nw) {
         float D[4];
         bool ok[4];
+        if (vec && d <= 128) {
+            const int64_t iq[4] = {i0, i0 + nw, i0 + 2 * nw, i0 + 3 * nw};
+            dist4_vec(x, ldx, n, d, chi, clo, k, labels, iq, D, ok);
+        } else {
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             const int64_t i = i0 + q * nw;
@@ -641,6 +678,7 @@ __global__ void __launch_bounds__(256) k_assign_stats(const float *__restrict__ 
                     }
                 }
             }
+        }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -726,7 +764,7 @@ __global__ void k_centroids_batch(const CenInst *__restrict__ C, const int64_t *
 
 // batched SSE / radius partials: block per 128-row unit (instance, tile),
 // warp per row, squares of (x - c_hi) - c_lo accumulated in FP32
-__global__ void __launch_bounds__(256) k_assign_stats_batch(const SInst *__restrict__ S, const int2 *__restrict__ units,
+__global__ void __launch_bounds__(256, 4) k_assign_stats_batch(const SInst *__restrict__ S, const int2 *__restrict__ units,
                                                             int64_t nunits, double *__restrict__ part_sum,
                                                             float *__restrict__ part_max) {
     __shared__ double ss[8];
@@ -737,10 +775,17 @@ __global__ void __launch_bounds__(256) k_assign_stats_batch(const SInst *__restr
         const SInst &I = S[un.x];
         float sh = 0.f, sl = 0.f;  // compensated FP32 sum of the warp's distances
         float mx = 0.f;
+        const bool vec = I.d <= 128 && ((I.d & 3) == 0) && ((I.ldx & 3) == 0) && (((uintptr_t)I.x & 15) == 0) &&
+                         (((uintptr_t)I.chi & 15) == 0) && (((uintptr_t)I.clo & 15) == 0);
         // rows wib, wib + 8, ... of the unit, four in flight per warp
         for (int r0 = wib; r0 < 128; r0 += 32) {
             float D[4];
             bool ok[4];
+            if (vec) {
+                const int64_t b = (int64_t)un.y * 128 + r0;
+                const int64_t iq[4] = {b, b + 8, b + 16, b + 24};
+                dist4_vec(I.x, I.ldx, I.n, I.d, I.chi, I.clo, I.k, I.labels, iq, D, ok);
+            } else {
 #pragma unroll
             for (int q = 0; q < 4; q++) {
                 const int64_t i = (int64_t)un.y * 128 + r0 + 8 * q;
@@ -756,6 +801,7 @@ __global__ void __launch_bounds__(256) k_assign_stats_batch(const SInst *__restr
                         D[q] = fmaf(e, e, D[q]);
                     }
                 }
+            }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
