@@ -288,13 +288,21 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
 }
 
-// A thread takes one flagged element and runs Dot2 over j = 0..d-1 in
-// order: TwoProduct p + h = a_j x_j, TwoSum sh + er = sh + p, and the error
-// terms er + h accumulated in sc.  sh + sc equals the exact dot product up
-// to the float summation of the 2d error terms, at most
-// gamma_d^2 sum|a_j x_j| <= 2.2 (2d)(d+1) u^2 |a||x| (Ogita, Rump and Oishi).
-// Rows are read with 16-byte loads when aligned; neighbouring flags mostly
-// share a row, so the re-reads hit L1.
+// Eight lanes take one flagged element: lane s runs Dot2 over its
+// coordinates 4s..4s+3, 4s+32.. (in order), TwoProduct p + h = a_j x_j,
+// TwoSum sh + er = sh + p, error terms er + h summed in sc; the eight
+// (sh, sc) pairs then merge in a tree of TwoSums (sh + sh', the new error
+// added to sc + sc').  Every TwoSum and TwoProduct is error-free, so sh + the
+// exact sum of all error terms is the exact dot product, and sc carries
+// those 2d - 1 terms summed in floating point; each product's partial sums
+// pass through at most d - 1 non-trivial TwoSums, as in the sequential
+// order, so Ogita, Rump and Oishi's bound for Dot2 still holds: |sh + sc -
+// a.x| <= u |a.x| + gamma_d^2 sum|a_j x_j| <= 2.2 (2d)(d+1) u^2 |a||x| beyond
+// the final rounding.  A warp takes 32 flags: in round r its four lane groups
+// take flags 4r .. 4r+3, and the result of flag m goes to lane m, which
+// then makes the decision for its own flag (the FP64 part runs with 32
+// flags per warp instruction).  The groups' loads of a row are 128 bytes
+// apiece, where a thread per flag spread a warp's loads over 32 rows.
 // Flag entries carry global rows (row_base + local row); instance i holds
 // global rows [row_off[i], row_off[i + 1]).
 __global__ void __launch_bounds__(256) k_recheck_dot2(
@@ -303,41 +311,76 @@ __global__ void __launch_bounds__(256) k_recheck_dot2(
     uint64_t *__restrict__ flags2, unsigned long long *__restrict__ n_flags2) {
     const int64_t nf = min((int64_t)*n_flags, cap);
     const double u = 5.9604644775390625e-08;  // 2^-24
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nf;
-         q += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31, grp = lane >> 3, sub = lane & 7;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t q0 = warp * 32; q0 < nf; q0 += nwarps * 32) {
+        float msh = 0.f, msc = 0.f, mxx = 0.f;  // this lane's own flag q0 + lane
+        for (int r = 0; r < 8; r++) {
+            const int64_t q = q0 + 4 * r + grp;
+            float sh = 0.f, sc = 0.f, xx = 0.f;
+            if (q < nf) {
+                const uint64_t e = flags[q];
+                const ProjArgs &A = P[find_inst(row_off, count, (int64_t)(e >> 16))];
+                const int d = A.d;
+                const float *xr = A.x + ((int64_t)(e >> 16) - A.row_base) * A.ldx;
+                const float *ar = A.a + (int64_t)(e & 0xFFFF) * d;
+                auto term = [&](float av, float xv) {
+                    const float p = __fmul_rn(av, xv);
+                    const float h = fmaf(av, xv, -p);  // exact product error
+                    float t, er;
+                    two_sum(sh, p, t, er);
+                    sh = t;
+                    sc = __fadd_rn(sc, __fadd_rn(er, h));
+                    xx = fmaf(xv, xv, xx);
+                };
+                if (((d & 3) == 0) && ((((uintptr_t)xr) | ((uintptr_t)ar)) & 15) == 0) {
+                    for (int j = 4 * sub; j < d; j += 32) {
+                        const float4 av = *reinterpret_cast<const float4 *>(ar + j);
+                        const float4 xv = *reinterpret_cast<const float4 *>(xr + j);
+                        term(av.x, xv.x);
+                        term(av.y, xv.y);
+                        term(av.z, xv.z);
+                        term(av.w, xv.w);
+                    }
+                } else {
+                    for (int b = 4 * sub; b < d; b += 32)
+                        for (int j = b; j < min(b + 4, d); j++) term(ar[j], xr[j]);
+                }
+            }
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                const float sh2 = __shfl_xor_sync(0xffffffffu, sh, o);
+                const float sc2 = __shfl_xor_sync(0xffffffffu, sc, o);
+                const float xx2 = __shfl_xor_sync(0xffffffffu, xx, o);
+                float t, er;
+                two_sum(sh, sh2, t, er);
+                sh = t;
+                sc = __fadd_rn(__fadd_rn(sc, sc2), er);
+                xx = __fadd_rn(xx, xx2);
+            }
+            // flag 4r + g (group g) belongs to lane 4r + g
+            const int src = (lane & 3) << 3;
+            const float vsh = __shfl_sync(0xffffffffu, sh, src);
+            const float vsc = __shfl_sync(0xffffffffu, sc, src);
+            const float vxx = __shfl_sync(0xffffffffu, xx, src);
+            if ((lane >> 2) == r) {
+                msh = vsh;
+                msc = vsc;
+                mxx = vxx;
+            }
+        }
+        const int64_t q = q0 + lane;
+        if (q >= nf) continue;
         const uint64_t e = flags[q];
         const ProjArgs &A = P[find_inst(row_off, count, (int64_t)(e >> 16))];
         const int d = A.d;
         const int64_t row = (int64_t)(e >> 16) - A.row_base;
         const int f = (int)(e & 0xFFFF);
-        const float *xr = A.x + row * A.ldx;
-        const float *ar = A.a + (int64_t)f * d;
-        float sh = 0.f, sc = 0.f, xx = 0.f;
-        auto term = [&](float av, float xv) {
-            const float p = __fmul_rn(av, xv);
-            const float h = fmaf(av, xv, -p);  // exact product error
-            float t, er;
-            two_sum(sh, p, t, er);
-            sh = t;
-            sc = __fadd_rn(sc, __fadd_rn(er, h));
-            xx = fmaf(xv, xv, xx);
-        };
-        if (((d & 3) == 0) && ((((uintptr_t)xr) | ((uintptr_t)ar)) & 15) == 0) {
-            for (int j = 0; j < d; j += 4) {
-                const float4 av = *reinterpret_cast<const float4 *>(ar + j);
-                const float4 xv = *reinterpret_cast<const float4 *>(xr + j);
-                term(av.x, xv.x);
-                term(av.y, xv.y);
-                term(av.z, xv.z);
-                term(av.w, xv.w);
-            }
-        } else {
-            for (int j = 0; j < d; j++) term(ar[j], xr[j]);
-        }
         const double w = A.wd;
         const double cfac = 2.2 * (2.0 * d) * (d + 1.0) * u * u + (double)d * 2.220446049250313e-16;
-        const double S = (double)sh + (double)sc;
-        const double an = (double)A.anorm[f], xn = (double)(sqrtf(xx) * (1.0f + 1.0e-3f));
+        const double S = (double)msh + (double)msc;
+        const double an = (double)A.anorm[f], xn = (double)(sqrtf(mxx) * (1.0f + 1.0e-3f));
         const double E = cfac * an * xn + fabs(S) * 8.881784197001252e-16 + (double)d * 1e-40 + 1e-300;
         const double lo = S - E, hi = S + E;
         bool sure;
