@@ -1,11 +1,15 @@
 // SILK seeding (Sect. 3.2, Alg. 4) on the device.
 //
-// For each SILK table: the MinHash signature of every bucket (a bucket is a
-// set of object ids), bins = runs of equal signatures after a radix sort,
-// majority voting by sorting (bin, id) pairs and counting runs, the delta
-// filter, then compaction into a CSR multiset.  The near-duplicate removal
-// pass reuses the same machinery on the multiset, followed by a canonical
-// lexicographic sort and removal of exact duplicates.
+// The buckets of all transform tables become virtual buckets (identical
+// one-object buckets merged, with a weight).  For each SILK table: the
+// MinHash signature of every virtual bucket, bins = groups of equal
+// signatures found by hashing (seen-once / seen-twice maps, then
+// fingerprinted grouping tables; one-object buckets joined to a group by a
+// claim where a one-to-one MinHash function makes that exact), majority
+// voting by sorting (bin, id) pairs and counting runs, the delta filter, then
+// compaction into a CSR multiset.  The near-duplicate removal pass groups the
+// multiset's sets by sorted signatures, followed by a canonical lexicographic
+// sort and removal of exact duplicates.
 #include "internal.cuh"
 
 namespace {
