@@ -298,7 +298,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
 // pass through at most d - 1 non-trivial TwoSums, as in the sequential
 // order, so Ogita, Rump and Oishi's bound for Dot2 still holds: |sh + sc -
 // a.x| <= u |a.x| + gamma_d^2 sum|a_j x_j| <= 2.2 (2d)(d+1) u^2 |a||x| beyond
-// the final rounding.  A warp takes 32 flags: in round r its four lane groups
+// the final rounding.  A warp takes 32 flags: in step r its four lane groups
 // take flags 4r .. 4r+3, and the result of flag m goes to lane m, which
 // then makes the decision for its own flag (the FP64 part runs with 32
 // flags per warp instruction).  The groups' loads of a row are 128 bytes
